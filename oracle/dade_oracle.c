@@ -1,0 +1,574 @@
+/*
+ * dade_oracle.c -- plain FP64 CPU oracle for DADE inside an IVF scan.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load this file.  It shares no code with
+ * the CUDA library: nothing here is included by, linked into or generated for
+ * the GPU path, and it includes nothing of it.
+ *
+ * Every routine follows the paper (Deng et al., "Efficient Data-aware Distance
+ * Comparison Operations for High-Dimensional Approximate Nearest Neighbor
+ * Search") step by step, in double precision, with no blocking or reordering
+ * beyond what the cited definition states.  Sums run in index order.
+ * OpenMP is used only across independent outputs (rows of the covariance,
+ * base points in an assignment step, queries), never inside one sum.
+ *
+ * Notation: D dimensions, W = [w_1..w_D] the PCA basis (column k of W is w_k),
+ * lambda_1 >= ... >= lambda_D, Lambda_d = sum_{k<=d} lambda_k,
+ * P_d(q,o) = sum_{k<=d} (q'_k - o'_k)^2 in the rotated space, r the current
+ * K-th nearest distance.  Row-major arrays throughout.
+ *
+ * Parity status: every routine is pinned by the CPU tests (closed forms,
+ * library routines on special cases, brute force on tiny inputs, statistical
+ * checks).  The recall level of the whole search has no printed value in the
+ * paper and is reported, not pinned ("parity unpinned" for absolute recall).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_API __attribute__((visibility("default")))
+
+OR_API void or_set_threads(int t) {
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+OR_API int or_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 3.2, Eq. 10-12: PCA of E[X X^T] over all data objects, after      */
+/* centring (Lemma 1 makes the mean free: distances are unchanged).          */
+/* ------------------------------------------------------------------------ */
+
+/* mu_j = (1/n) sum_i x_ij ;  C_jk = (1/n) sum_i (x_ij - mu_j)(x_ik - mu_k). */
+OR_API void or_mean_cov(const float *X, int64_t n, int d, double *mu, double *C)
+{
+    for (int j = 0; j < d; ++j) mu[j] = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int j = 0; j < d; ++j) mu[j] += (double)X[i * d + j];
+    for (int j = 0; j < d; ++j) mu[j] /= (double)n;
+
+    /* one covariance row per thread; each entry sums over i in order */
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int j = 0; j < d; ++j) {
+        double *row = C + (int64_t)j * d;
+        for (int k = 0; k < d; ++k) row[k] = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            const float *x = X + i * d;
+            double yj = (double)x[j] - mu[j];
+            for (int k = j; k < d; ++k) row[k] += yj * ((double)x[k] - mu[k]);
+        }
+        for (int k = j; k < d; ++k) row[k] /= (double)n;
+    }
+    for (int j = 0; j < d; ++j)
+        for (int k = 0; k < j; ++k) C[(int64_t)j * d + k] = C[(int64_t)k * d + j];
+}
+
+/*
+ * Cyclic Jacobi eigendecomposition of the symmetric d x d matrix A (Jacobi's
+ * method: repeated plane rotations that zero one off-diagonal entry at a
+ * time).  On return the eigenvalues are in lam (descending, Eq. 11: lambda_k
+ * is the k-th largest) and column k of V is the matching unit eigenvector w_k.
+ * A is overwritten.  Returns the number of sweeps, or -1 if not converged.
+ */
+OR_API int or_jacobi_eig(double *A, int d, double *lam, double *V)
+{
+    double fro = 0.0;
+    for (int64_t t = 0; t < (int64_t)d * d; ++t) fro += A[t] * A[t];
+    fro = sqrt(fro);
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) V[(int64_t)i * d + j] = (i == j) ? 1.0 : 0.0;
+
+    int sweep;
+    for (sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < d; ++p)
+            for (int q = p + 1; q < d; ++q) off += 2.0 * A[(int64_t)p * d + q] * A[(int64_t)p * d + q];
+        if (sqrt(off) <= 1e-14 * fro || fro == 0.0) break;
+        for (int p = 0; p < d - 1; ++p) {
+            for (int q = p + 1; q < d; ++q) {
+                double apq = A[(int64_t)p * d + q];
+                if (apq == 0.0) continue;
+                double app = A[(int64_t)p * d + p], aqq = A[(int64_t)q * d + q];
+                /* rotation angle that annihilates a_pq */
+                double theta = (aqq - app) / (2.0 * apq);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < d; ++k) {      /* A <- A J  (columns p, q) */
+                    double akp = A[(int64_t)k * d + p], akq = A[(int64_t)k * d + q];
+                    A[(int64_t)k * d + p] = c * akp - s * akq;
+                    A[(int64_t)k * d + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < d; ++k) {      /* A <- J^T A  (rows p, q) */
+                    double apk = A[(int64_t)p * d + k], aqk = A[(int64_t)q * d + k];
+                    A[(int64_t)p * d + k] = c * apk - s * aqk;
+                    A[(int64_t)q * d + k] = s * apk + c * aqk;
+                }
+                A[(int64_t)p * d + q] = 0.0;
+                A[(int64_t)q * d + p] = 0.0;
+                for (int k = 0; k < d; ++k) {      /* V <- V J */
+                    double vkp = V[(int64_t)k * d + p], vkq = V[(int64_t)k * d + q];
+                    V[(int64_t)k * d + p] = c * vkp - s * vkq;
+                    V[(int64_t)k * d + q] = s * vkp + c * vkq;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < d; ++i) lam[i] = A[(int64_t)i * d + i];
+    /* order eigenpairs by descending eigenvalue (selection sort: plain) */
+    for (int i = 0; i < d; ++i) {
+        int best = i;
+        for (int j = i + 1; j < d; ++j) if (lam[j] > lam[best]) best = j;
+        if (best != i) {
+            double tl = lam[i]; lam[i] = lam[best]; lam[best] = tl;
+            for (int k = 0; k < d; ++k) {
+                double tv = V[(int64_t)k * d + i];
+                V[(int64_t)k * d + i] = V[(int64_t)k * d + best];
+                V[(int64_t)k * d + best] = tv;
+            }
+        }
+    }
+    return sweep < 100 ? sweep : -1;
+}
+
+/* PCA: mean, covariance and its eigendecomposition (Eq. 11, Eq. 12). */
+OR_API int or_pca(const float *X, int64_t n, int d, double *mu, double *W, double *lam)
+{
+    double *C = (double *)malloc(sizeof(double) * (size_t)d * d);
+    if (!C) return -1;
+    or_mean_cov(X, n, d, mu, C);
+    int s = or_jacobi_eig(C, d, lam, W);
+    free(C);
+    return s;
+}
+
+/* Rotation x' = W^T (x - mu): out_ik = sum_j W_jk (x_ij - mu_j)  (Lemma 1). */
+OR_API void or_rotate(const float *X, int64_t n, int d, const double *mu, const double *W, double *out)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        const float *x = X + i * d;
+        for (int k = 0; k < d; ++k) {
+            double s = 0.0;
+            for (int j = 0; j < d; ++j) s += W[(int64_t)j * d + k] * ((double)x[j] - mu[j]);
+            out[i * d + k] = s;
+        }
+    }
+}
+
+/* Squared Euclidean distance between two FP64 vectors, summed in order. */
+static double sqdist(const double *a, const double *b, int d)
+{
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) { double t = a[k] - b[k]; s += t * t; }
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* IVF (Section 3.4): k-means centroids, inverted lists, probing.            */
+/* ------------------------------------------------------------------------ */
+
+/* Nearest centroid of x; ties go to the lower centroid index.  *gap gets the
+ * relative gap between the best and second-best squared distances. */
+static int nearest(const double *x, const double *cent, int nc, int d, double *best_out, double *gap)
+{
+    int best = 0;
+    double b1 = INFINITY, b2 = INFINITY;
+    for (int c = 0; c < nc; ++c) {
+        double t = sqdist(x, cent + (int64_t)c * d, d);
+        if (t < b1) { b2 = b1; b1 = t; best = c; }
+        else if (t < b2) b2 = t;
+    }
+    if (best_out) *best_out = b1;
+    if (gap) *gap = (b2 - b1) / (b1 > 0.0 ? b1 : 1.0);
+    return best;
+}
+
+/*
+ * Lloyd k-means: centroids start at the given base points; each iteration
+ * assigns every point to its nearest centroid and moves every centroid to
+ * the mean of its members (an empty cluster keeps its previous centroid).
+ * obj[it] = sum of squared distances in iteration it's assignment step.
+ * min_gap = smallest relative best/second-best gap seen (near-tie indicator).
+ * assign holds the last iteration's assignment (before the final update).
+ */
+OR_API void or_kmeans(const double *Xr, int64_t n, int d, int nc, const int64_t *init, int iters,
+                      double *cent, int32_t *assign, double *obj, double *min_gap)
+{
+    for (int c = 0; c < nc; ++c)
+        memcpy(cent + (int64_t)c * d, Xr + init[c] * d, sizeof(double) * d);
+    double *sum = (double *)malloc(sizeof(double) * (size_t)nc * d);
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)nc);
+    double gmin = INFINITY;
+    for (int it = 0; it < iters; ++it) {
+        double o = 0.0, g = INFINITY;
+        #pragma omp parallel for schedule(static) reduction(min:g)
+        for (int64_t i = 0; i < n; ++i) {
+            double gi;
+            assign[i] = nearest(Xr + i * d, cent, nc, d, NULL, &gi);
+            if (gi < g) g = gi;
+        }
+        for (int64_t i = 0; i < n; ++i) o += sqdist(Xr + i * d, cent + (int64_t)assign[i] * d, d);
+        if (obj) obj[it] = o;
+        if (g < gmin) gmin = g;
+        memset(sum, 0, sizeof(double) * (size_t)nc * d);
+        memset(cnt, 0, sizeof(int64_t) * (size_t)nc);
+        for (int64_t i = 0; i < n; ++i) {
+            int c = assign[i];
+            cnt[c] += 1;
+            for (int k = 0; k < d; ++k) sum[(int64_t)c * d + k] += Xr[i * d + k];
+        }
+        for (int c = 0; c < nc; ++c)
+            if (cnt[c] > 0)
+                for (int k = 0; k < d; ++k) cent[(int64_t)c * d + k] = sum[(int64_t)c * d + k] / (double)cnt[c];
+    }
+    if (min_gap) *min_gap = gmin;
+    free(sum);
+    free(cnt);
+}
+
+/* Inverted lists: every point goes to its nearest centroid (ties to the lower
+ * index).  Returns the smallest relative best/second-best gap. */
+OR_API double or_assign(const double *Xr, int64_t n, int d, const double *cent, int nc, int32_t *assign)
+{
+    double g = INFINITY;
+    #pragma omp parallel for schedule(static) reduction(min:g)
+    for (int64_t i = 0; i < n; ++i) {
+        double gi;
+        assign[i] = nearest(Xr + i * d, cent, nc, d, NULL, &gi);
+        if (gi < g) g = gi;
+    }
+    return g;
+}
+
+/* Centroid of every list = mean of its members; an empty list gets zeros. */
+OR_API void or_list_means(const double *Xr, int64_t n, int d, const int32_t *assign, int nc, double *cent)
+{
+    int64_t *cnt = (int64_t *)calloc((size_t)nc, sizeof(int64_t));
+    memset(cent, 0, sizeof(double) * (size_t)nc * d);
+    for (int64_t i = 0; i < n; ++i) {
+        cnt[assign[i]] += 1;
+        for (int k = 0; k < d; ++k) cent[(int64_t)assign[i] * d + k] += Xr[i * d + k];
+    }
+    for (int c = 0; c < nc; ++c)
+        if (cnt[c] > 0)
+            for (int k = 0; k < d; ++k) cent[(int64_t)c * d + k] /= (double)cnt[c];
+    free(cnt);
+}
+
+typedef struct { double key; int64_t id; } kv_t;
+
+static int kv_cmp(const void *a, const void *b)
+{
+    const kv_t *x = (const kv_t *)a, *y = (const kv_t *)b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+static int dbl_cmp(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+static int near_tie(double a, double b, double tol)
+{
+    double m = fabs(a) > fabs(b) ? fabs(a) : fabs(b);
+    return fabs(a - b) <= tol * m;
+}
+
+/* Probe: the nprobe centroids nearest to each query, ordered by (distance,
+ * centroid id).  tie[q] = 1 when two of the first nprobe+1 centroid distances
+ * are within tol of each other (the order could flip at lower precision). */
+OR_API void or_probe(const double *Qr, int64_t nq, int d, const double *cent, int nc, int nprobe,
+                     int32_t *probe, int32_t *tie, double tol)
+{
+    #pragma omp parallel
+    {
+        kv_t *buf = (kv_t *)malloc(sizeof(kv_t) * (size_t)nc);
+        #pragma omp for schedule(dynamic, 4)
+        for (int64_t q = 0; q < nq; ++q) {
+            for (int c = 0; c < nc; ++c) {
+                buf[c].key = sqdist(Qr + q * d, cent + (int64_t)c * d, d);
+                buf[c].id = c;
+            }
+            qsort(buf, (size_t)nc, sizeof(kv_t), kv_cmp);
+            int t = 0;
+            for (int j = 0; j < nprobe; ++j) {
+                probe[q * nprobe + j] = (int32_t)buf[j].id;
+                if (j + 1 < nc && near_tie(buf[j].key, buf[j + 1].key, tol)) t = 1;
+            }
+            if (tie) tie[q] = t;
+        }
+        free(buf);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 3.3, Eq. 14: epsilon_d from uniformly sampled pairs of objects.   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * For each pair (i, j) with nonzero distance, and each d in dlist,
+ *   rho_d = dis'_d / dis = sqrt( Lambda_D / Lambda_d * P_d(o_i, o_j) / P_D(o_i, o_j) ),
+ * the ratio of the Eq. 13 estimate to the exact distance.  rho is written
+ * sorted ascending per d: rho[t * m_kept + s].  Pairs with zero distance are
+ * dropped (the ratio is undefined).  Returns m_kept.
+ */
+OR_API int64_t or_eps_sample(const double *Xr, int64_t n, int d, const double *lam,
+                             const int64_t *pairs, int64_t m, const int32_t *dlist, int nd, double *rho)
+{
+    (void)n;
+    double LD = 0.0;
+    for (int k = 0; k < d; ++k) LD += lam[k];
+    double *Pd = (double *)malloc(sizeof(double) * (size_t)d);
+    int64_t kept = 0;
+    for (int64_t s = 0; s < m; ++s) {
+        const double *a = Xr + pairs[2 * s] * d, *b = Xr + pairs[2 * s + 1] * d;
+        double acc = 0.0;
+        for (int k = 0; k < d; ++k) { double t = a[k] - b[k]; acc += t * t; Pd[k] = acc; }
+        double PD = acc;
+        if (!(PD > 0.0)) continue;
+        for (int t = 0; t < nd; ++t) {
+            int dd = dlist[t];
+            double Ld = 0.0;
+            for (int k = 0; k < dd; ++k) Ld += lam[k];
+            rho[(int64_t)t * m + kept] = sqrt(LD / Ld * Pd[dd - 1] / PD);
+        }
+        ++kept;
+    }
+    free(Pd);
+    for (int t = 0; t < nd; ++t) qsort(rho + (int64_t)t * m, (size_t)kept, sizeof(double), dbl_cmp);
+    return kept;
+}
+
+/*
+ * epsilon_d for significance level P_s = alpha (Eq. 14): the threshold that
+ * rho_d - 1 exceeds with probability alpha, estimated from the sorted sample
+ * by the higher order statistic, eps = rho_(ceil((1 - alpha) M)) - 1 (1-based),
+ * so that at most a fraction alpha of the sample lies above it.
+ */
+OR_API double or_eps_quantile(const double *rho_sorted, int64_t m, double alpha)
+{
+    int64_t idx = (int64_t)ceil((1.0 - alpha) * (double)m);
+    if (idx < 1) idx = 1;
+    if (idx > m) idx = m;
+    return rho_sorted[idx - 1] - 1.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 (Section 3.4) with the hypothesis test of Section 3.3.        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One DCO.  q, o: rotated vectors (D dims).  r: the current K-th distance
+ * (+inf while fewer than K are held), r2 = r^2 as stored.  Lam[d] = Lambda_d
+ * (Lam[0] = 0).  eps[d] = epsilon_d for the tested d.  prune = 0 gives
+ * FDScanning (no test before d = D).
+ *   d <- 0; while d < D: d <- min(d + delta_d, D);
+ *     dis' = sqrt(Lambda_D / Lambda_d * P_d)                      (Eq. 13)
+ *     d < D : reject H0 (prune, return 0) iff dis' > (1 + eps_d) r (Section 3.3)
+ *     d = D : dis' is the exact distance; accept iff dis <= r      (Definition 1)
+ * Returns 1 on accept with *dist2 = P_D.  *dims = dimensions used.
+ * *tie |= 1 when a test at d < D had its two sides within tol (relative, on
+ * the squared values), |= 2 when the final compare did.
+ */
+/* Eq. 13 applied to one pair: the squared estimate dis'^2 = Lambda_D / Lambda_d * P_d. */
+static double estimate_sq(double Pd, const double *Lam, int D, int d)
+{
+    return Lam[D] / Lam[d] * Pd;
+}
+
+static int dco(const double *q, const double *o, int D, int delta_d, double r, double r2,
+               const double *Lam, const double *eps, int prune, double tol,
+               double *dist2, int *dims, int *tie)
+{
+    int d = 0;
+    double P = 0.0;
+    while (d < D) {
+        int dn = d + delta_d;
+        if (dn > D) dn = D;
+        for (int k = d; k < dn; ++k) { double t = q[k] - o[k]; P += t * t; }
+        d = dn;
+        if (d < D) {
+            if (!prune) continue;
+            double est = sqrt(estimate_sq(P, Lam, D, d));
+            double bound = (1.0 + eps[d]) * r;
+            if (isfinite(r) && near_tie(est * est, bound * bound, tol)) *tie |= 1;
+            if (est > bound) { *dims = d; return 0; }
+        } else {
+            *dims = D;
+            *dist2 = P;
+            if (isfinite(r2) && near_tie(P, r2, tol)) *tie |= 2;
+            return P <= r2;
+        }
+    }
+    *dims = D;
+    *dist2 = P;
+    return P <= r2;
+}
+
+static double *prefix_lambda(const double *lam, int D)
+{
+    double *Lam = (double *)malloc(sizeof(double) * (size_t)(D + 1));
+    Lam[0] = 0.0;
+    for (int k = 0; k < D; ++k) Lam[k + 1] = Lam[k] + lam[k];
+    return Lam;
+}
+
+/* The squared estimate of Eq. 13 for one pair from its first d dimensions. */
+OR_API double or_estimate_sq(const double *q, const double *o, int D, int d, const double *lam)
+{
+    double *Lam = prefix_lambda(lam, D);
+    double P = 0.0;
+    for (int k = 0; k < d; ++k) { double t = q[k] - o[k]; P += t * t; }
+    double e = estimate_sq(P, Lam, D, d);
+    free(Lam);
+    return e;
+}
+
+/* One DCO (Algorithm 1) for one pair; r is the threshold distance (+inf
+ * allowed).  Returns 1 on accept; *dist2 gets P_D when accepted; *dims the
+ * dimensions used; *tie the near-tie bits of dco(). */
+OR_API int or_dco(const double *q, const double *o, int D, int delta_d, double r, const double *lam,
+                  const double *eps, int prune, double tol, double *dist2, int *dims, int *tie)
+{
+    double *Lam = prefix_lambda(lam, D);
+    *tie = 0;
+    *dist2 = INFINITY;
+    int acc = dco(q, o, D, delta_d, r, r * r, Lam, eps, prune, tol, dist2, dims, tie);
+    free(Lam);
+    return acc;
+}
+
+/*
+ * IVF search with DADE DCOs (Section 3.4): probe the nprobe nearest lists,
+ * scan their members keeping the K nearest (a max-heap in the paper; here a
+ * sorted array with the same content), and run one DCO per candidate against
+ * the current K-th distance.
+ *
+ * Candidate order: probe order, then ascending base id within a list.
+ * Threshold schedule: candidates form consecutive epochs, and every candidate
+ * of an epoch is tested against r taken after all earlier epochs:
+ *   schedule 0  SEQUENTIAL      one candidate per epoch (the paper's order);
+ *   schedule 1  TILE(tile)      up to `tile` consecutive members of one list;
+ *   schedule 2  PROBE_ROUNDS    one whole list per epoch.
+ * Results are ordered by (squared distance, id); missing slots are (-1, +inf).
+ * eps == NULL runs FDScanning.  eps is indexed by d (eps[d], d < D).
+ * stats (nq x 4, may be NULL): candidates, sum of dims used, accepted, pruned.
+ * flags (nq, may be NULL): 1|2 test near-ties (see dco), 4 near-tie at the
+ * K-th place of a merge, 8 near-tie in the probe order.
+ */
+OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, int nc,
+                     const double *cent, const double *lam, const double *Qr, int64_t nq,
+                     int K, int nprobe, int delta_d, const double *eps, int schedule, int tile,
+                     double tol, int64_t *ids, double *dists, int64_t *stats, int32_t *flags)
+{
+    if (K < 1 || nprobe < 1 || nprobe > nc || delta_d < 1 || (schedule == 1 && tile < 1)) return -1;
+    /* inverted lists, members in ascending id */
+    int64_t *start = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+    int64_t *members = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *fill = (int64_t *)calloc((size_t)nc, sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) start[assign[i] + 1] += 1;
+    for (int c = 0; c < nc; ++c) start[c + 1] += start[c];
+    for (int64_t i = 0; i < n; ++i) members[start[assign[i]] + fill[assign[i]]++] = i;
+    free(fill);
+    double *Lam = prefix_lambda(lam, D);
+
+    int32_t *probe = (int32_t *)malloc(sizeof(int32_t) * (size_t)nq * nprobe);
+    int32_t *ptie = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nq > 0 ? nq : 1));
+    or_probe(Qr, nq, D, cent, nc, nprobe, probe, ptie, tol);
+
+    #pragma omp parallel
+    {
+        int64_t maxlen = 0;
+        for (int c = 0; c < nc; ++c) if (start[c + 1] - start[c] > maxlen) maxlen = start[c + 1] - start[c];
+        kv_t *buf = (kv_t *)malloc(sizeof(kv_t) * (size_t)(K + maxlen + 1));
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t qi = 0; qi < nq; ++qi) {
+            const double *q = Qr + qi * D;
+            int ntop = 0, tie = 0;
+            int64_t st[4] = {0, 0, 0, 0};
+            for (int j = 0; j < nprobe; ++j) {
+                int c = probe[qi * nprobe + j];
+                int64_t len = start[c + 1] - start[c];
+                int64_t elen = schedule == 0 ? 1 : schedule == 1 ? tile : (len > 0 ? len : 1);
+                for (int64_t e0 = 0; e0 < len; e0 += elen) {
+                    double r2 = ntop == K ? buf[K - 1].key : INFINITY;
+                    double r = sqrt(r2);
+                    int npend = 0;
+                    int64_t e1 = e0 + elen < len ? e0 + elen : len;
+                    for (int64_t t = e0; t < e1; ++t) {
+                        int64_t id = members[start[c] + t];
+                        double d2 = 0.0;
+                        int dims = 0;
+                        int acc = dco(q, Xr + id * D, D, delta_d, r, r2, Lam, eps, eps != NULL, tol,
+                                      &d2, &dims, &tie);
+                        st[0] += 1;
+                        st[1] += dims;
+                        if (acc) { st[2] += 1; buf[ntop + npend].key = d2; buf[ntop + npend].id = id; ++npend; }
+                        else if (dims < D) st[3] += 1;
+                    }
+                    if (npend > 0) {
+                        int u = ntop + npend;
+                        qsort(buf, (size_t)u, sizeof(kv_t), kv_cmp);
+                        if (u > K && near_tie(buf[K - 1].key, buf[K].key, tol)) tie |= 4;
+                        ntop = u < K ? u : K;
+                    }
+                }
+            }
+            for (int s = 0; s < K; ++s) {
+                ids[qi * K + s] = s < ntop ? buf[s].id : -1;
+                dists[qi * K + s] = s < ntop ? buf[s].key : INFINITY;
+            }
+            if (stats) for (int s = 0; s < 4; ++s) stats[qi * 4 + s] = st[s];
+            if (flags) flags[qi] = tie | (ptie[qi] ? 8 : 0);
+        }
+        free(buf);
+    }
+    free(probe); free(ptie); free(Lam); free(start); free(members);
+    return 0;
+}
+
+/* Exact K nearest neighbours by brute force in FP64 (ground truth), ordered by
+ * (squared distance, id).  X, Q are FP32 inputs in any common coordinates. */
+OR_API void or_exact_knn(const float *X, int64_t n, int d, const float *Q, int64_t nq, int K,
+                         int64_t *ids, double *dists)
+{
+    #pragma omp parallel
+    {
+        kv_t *buf = (kv_t *)malloc(sizeof(kv_t) * (size_t)(n > 0 ? n : 1));
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t qi = 0; qi < nq; ++qi) {
+            const float *q = Q + qi * d;
+            for (int64_t i = 0; i < n; ++i) {
+                const float *x = X + i * d;
+                double s = 0.0;
+                for (int k = 0; k < d; ++k) { double t = (double)q[k] - (double)x[k]; s += t * t; }
+                buf[i].key = s;
+                buf[i].id = i;
+            }
+            qsort(buf, (size_t)n, sizeof(kv_t), kv_cmp);
+            for (int s = 0; s < K; ++s) {
+                ids[qi * K + s] = s < n ? buf[s].id : -1;
+                dists[qi * K + s] = s < n ? buf[s].key : INFINITY;
+            }
+        }
+        free(buf);
+    }
+}

@@ -1,0 +1,156 @@
+"""Seeded synthetic workloads for DADE-IVF.
+
+This module draws inputs only: base vectors, queries, mixture labels, the
+k-means initial centroid ids and the pairs used to estimate epsilon_d.  It
+holds none of the method's arithmetic (no PCA, no distances, no k-means, no
+estimates), so both the CUDA path and the CPU oracle may consume what it
+produces.
+
+The paper's datasets (Table 1: MSong, DEEP, Word2Vec, GIST, GloVe, Tiny5M)
+are not available here; these generators stand in for them with the shapes,
+spectra and cluster structure listed in ``WORKLOADS``.  Nothing from those
+datasets is reproduced.
+
+Recipe shared by every workload (numpy PCG64, fixed seeds):
+  * spectrum  lambda_i = i^-p, rescaled so that sum(lambda) = D;
+  * basis     a Haar-random orthogonal matrix (QR of a Gaussian, sign fixed
+              so that R has a positive diagonal);
+  * component x = m + s * Q (sqrt(lambda) * z),  z ~ N(0, I).
+Seeds: 0 base, 1 queries, 2 basis/means, 3 k-means init, 4 epsilon pairs.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+SEED_BASE, SEED_QUERY, SEED_BASIS, SEED_KMEANS, SEED_PAIRS = 0, 1, 2, 3, 4
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    n: int              # base vectors
+    d: int              # dimension
+    nq: int             # queries
+    p: float            # spectrum exponent, lambda_i ~ i^-p
+    n_comp: int         # mixture components (1 = single Gaussian)
+    mean_offset: float  # component means m_c = mean_offset + mean_scale * g_c
+    mean_scale: float
+    within_scale: float
+    integer: bool       # round and clip to 0..255 (stored as float32)
+    normalise: bool     # L2-normalise every vector
+    n_clusters: int
+    nprobe: tuple
+    k: int
+    delta_d: tuple
+    alpha: float
+    kmeans_iters: int = 10
+
+
+# Constants proposed for the workloads (sizes from the benchmark configs; the
+# paper fixes P_s = 0.1, delta_d = 32, N_c ~ sqrt(N) = 4096 in Section 4.1).
+WORKLOADS = {
+    "c1_gauss_10k_d128": Workload("c1_gauss_10k_d128", 10_000, 128, 100, 1.2, 1,
+                                  0.0, 0.0, 1.0, False, False, 64, (8,), 10, (32,), 0.05),
+    "c2_mix_1m_d128": Workload("c2_mix_1m_d128", 1_000_000, 128, 10_000, 1.0, 64,
+                               40.0, 25.0, 20.0, True, False, 4096,
+                               (16, 32, 64, 128, 256), 100, (16, 32, 64), 0.05),
+    "c3_mix_1m_d960": Workload("c3_mix_1m_d960", 1_000_000, 960, 1_000, 0.8, 64,
+                               0.0, 2.0, 1.0, False, False, 4096,
+                               (32, 64, 128), 10, (32,), 0.05),
+    "c5_mix_5m_d256": Workload("c5_mix_5m_d256", 5_000_000, 256, 10_000, 1.0, 32,
+                               0.0, 2.0, 1.0, False, False, 8192,
+                               (16, 64, 128), 10, (32,), 0.05),
+}
+
+
+def spectrum(d: int, p: float) -> np.ndarray:
+    """lambda_i = i^-p (i = 1..d), rescaled so that the sum is d."""
+    lam = np.arange(1, d + 1, dtype=np.float64) ** (-float(p))
+    return lam * (d / lam.sum())
+
+
+def haar(d: int, rng: np.random.Generator) -> np.ndarray:
+    """Haar-random orthogonal d x d matrix (QR of a Gaussian with sign fix)."""
+    g = rng.standard_normal((d, d))
+    q, r = np.linalg.qr(g)
+    return q * np.sign(np.diag(r))[None, :]
+
+
+def _components(w: Workload):
+    """Component means and rotations, all drawn from the basis seed."""
+    rng = np.random.default_rng(SEED_BASIS)
+    lam = spectrum(w.d, w.p)
+    if w.n_comp == 1:
+        means = np.zeros((1, w.d))
+    else:
+        means = w.mean_offset + w.mean_scale * rng.standard_normal((w.n_comp, w.d))
+    rots = [haar(w.d, rng) for _ in range(w.n_comp)]
+    return lam, means, rots
+
+
+def _draw(w: Workload, n: int, seed: int, comps=None):
+    lam, means, rots = comps if comps is not None else _components(w)
+    rng = np.random.default_rng(seed)
+    labels = rng.integers(0, w.n_comp, size=n).astype(np.int32) if w.n_comp > 1 \
+        else np.zeros(n, np.int32)
+    out = np.empty((n, w.d), np.float32)
+    sl = np.sqrt(lam)
+    chunk = 1 << 16
+    for c in range(w.n_comp):
+        idx = np.nonzero(labels == c)[0]
+        for s in range(0, idx.size, chunk):
+            sub = idx[s:s + chunk]
+            z = rng.standard_normal((sub.size, w.d)) * sl[None, :]
+            x = means[c][None, :] + w.within_scale * (z @ rots[c].T)
+            if w.integer:
+                x = np.clip(np.rint(x), 0.0, 255.0)
+            if w.normalise:
+                x = x / np.linalg.norm(x, axis=1, keepdims=True)
+            out[sub] = x.astype(np.float32)
+    return out, labels
+
+
+def make(name_or_w, n: int | None = None, nq: int | None = None):
+    """Return (base float32 [n,d], queries float32 [nq,d], base labels int32 [n]).
+
+    ``n`` / ``nq`` shrink a workload (same distribution, fewer draws)."""
+    w = WORKLOADS[name_or_w] if isinstance(name_or_w, str) else name_or_w
+    comps = _components(w)
+    base, labels = _draw(w, w.n if n is None else n, SEED_BASE, comps)
+    queries, _ = _draw(w, w.nq if nq is None else nq, SEED_QUERY, comps)
+    return base, queries, labels
+
+
+def gaussian(n: int, d: int, p: float, seed: int = SEED_BASE, basis_seed: int = SEED_BASIS):
+    """Single zero-mean Gaussian with lambda_i ~ i^-p in a Haar basis."""
+    lam = spectrum(d, p)
+    q = haar(d, np.random.default_rng(basis_seed))
+    z = np.random.default_rng(seed).standard_normal((n, d)) * np.sqrt(lam)[None, :]
+    return (z @ q.T).astype(np.float32), lam, q
+
+
+def kmeans_init(n: int, n_clusters: int, seed: int = SEED_KMEANS) -> np.ndarray:
+    """n_clusters distinct base ids drawn by a seeded permutation."""
+    rng = np.random.default_rng(seed)
+    return rng.permutation(n)[:n_clusters].astype(np.int64)
+
+
+def eps_pairs(n: int, m: int, seed: int = SEED_PAIRS) -> np.ndarray:
+    """m pairs (i, j), i != j, drawn uniformly; returned as int64 [m, 2]."""
+    rng = np.random.default_rng(seed)
+    i = rng.integers(0, n, size=m)
+    j = rng.integers(0, n - 1, size=m)
+    j = j + (j >= i)
+    return np.stack([i, j], axis=1).astype(np.int64)
+
+
+def zipf_assign(n: int, n_lists: int, s: float = 1.1, seed: int = SEED_BASE + 7) -> np.ndarray:
+    """Random list labels with Zipf(s)-skewed list sizes (a seeded rank
+    permutation decides which list gets which rank).  Used to exercise
+    uneven inverted lists."""
+    rng = np.random.default_rng(seed)
+    wts = np.arange(1, n_lists + 1, dtype=np.float64) ** (-s)
+    wts = wts[rng.permutation(n_lists)]
+    wts /= wts.sum()
+    return rng.choice(n_lists, size=n, p=wts).astype(np.int32)

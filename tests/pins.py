@@ -1,0 +1,420 @@
+"""Pins of the FP64 oracle to facts fixed outside it.
+
+Every pin takes an ``Oracle`` instance so the same checks can be run against
+builds of the oracle with a deliberately planted mistake (see
+test_oracle_plants.py).  Each pin cites the passage of the paper it checks and
+compares against something other than the oracle itself: a closed form, a
+hand-worked value under tests/golden/, a library routine on a special case,
+brute force on tiny inputs, or a statistical property with its error bar.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+
+from paper_2411_17229_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return float(np.max(np.abs(a - b)) / max(1e-300, float(np.max(np.abs(b)))))
+
+
+# --------------------------------------------------------------------------
+# Section 3.2: PCA (Eq. 10-12), Lemma 1, Lemma 2, Lemma 4
+# --------------------------------------------------------------------------
+
+def pin_eigen_closed_form(o):
+    """Eq. 11: eigenpairs of matrices with closed-form spectra."""
+    g = golden("eigen_closed_form.json")
+    for case in g["cases"]:
+        A = np.array(case["A"], float)
+        lam, V = o.jacobi_eig(A)
+        assert _rel(lam, case["lam"]) < 1e-12, (lam, case["lam"])
+        assert np.all(np.diff(lam) <= 0), "eigenvalues must be descending (Eq. 11)"
+        assert np.allclose(A @ V, V * lam[None, :], atol=1e-12)
+        assert np.allclose(V.T @ V, np.eye(A.shape[0]), atol=1e-12)
+
+
+def pin_pca_cross(o):
+    """Eq. 10-12 with Lemma 1's centring on a hand-derived point set."""
+    g = golden("pca_cross.json")
+    X = np.array(g["X"], np.float32)
+    mu, W, lam = o.pca(X)
+    # the inputs are FP32-rounded, so the closed form holds to ~1e-6
+    assert np.allclose(mu, g["mu"], atol=1e-5)
+    assert np.allclose(lam, g["lam"], rtol=1e-5)
+    assert abs(abs(float(W[:, 0] @ np.array(g["w1"]))) - 1.0) < 1e-6
+
+
+def pin_pca_vs_library(o):
+    """Mean/covariance vs numpy, spectrum vs LAPACK eigh, Lemma 2 trace."""
+    X, _, _ = synth.gaussian(3000, 24, 1.0, seed=11, basis_seed=12)
+    X = X + np.float32(3.0)
+    mu, Cm = o.mean_cov(X)
+    Xd = X.astype(np.float64)
+    assert _rel(mu, Xd.mean(0)) < 1e-12
+    assert _rel(Cm, np.cov(Xd.T, bias=True)) < 1e-11
+    mu2, W, lam = o.pca(X)
+    ref = np.sort(np.linalg.eigvalsh(np.cov(Xd.T, bias=True)))[::-1]
+    assert _rel(lam, ref) < 1e-10
+    assert np.all(np.diff(lam) < 0)
+    assert np.allclose(W.T @ W, np.eye(24), atol=1e-12)
+    assert np.allclose(Cm @ W, W * lam[None, :], atol=1e-10 * lam[0])
+    # Lemma 2: an orthogonal transform keeps the sum of variances
+    assert abs(np.trace(Cm) - lam.sum()) < 1e-12 * lam.sum()
+
+
+def pin_ky_fan(o):
+    """Eq. 10 / Lemma 4: the PCA basis maximises sigma^2(1, d) for every d,
+    so any other orthogonal basis has a smaller or equal prefix variance."""
+    X, _, _ = synth.gaussian(4000, 32, 1.2, seed=21, basis_seed=22)
+    mu, W, lam = o.pca(X)
+    Cm = np.cov(X.astype(np.float64).T, bias=True)
+    Lam = np.cumsum(lam)
+    for s in range(3):
+        R = synth.haar(32, np.random.default_rng(100 + s))
+        var = np.einsum("ij,jk,ki->i", R.T, Cm, R)
+        assert np.all(np.cumsum(var) <= Lam * (1 + 1e-12))
+    # the spectrum recovered from data matches the generator's shape
+    true = synth.spectrum(32, 1.2)
+    assert np.all(np.abs(lam / lam.sum() - true / true.sum()) < 0.02)
+
+
+def pin_rotation_isometry(o):
+    """Lemma 1: W^T(x - mu) keeps every pairwise distance; mu maps to 0."""
+    X, _, _ = synth.gaussian(200, 16, 1.0, seed=31, basis_seed=32)
+    X = X + np.float32(5.0)
+    mu, W, lam = o.pca(X)
+    Xr = o.rotate(X, mu, W)
+    Xd = X.astype(np.float64)
+    d0 = ((Xd[:, None, :] - Xd[None, :, :]) ** 2).sum(-1)
+    d1 = ((Xr[:, None, :] - Xr[None, :, :]) ** 2).sum(-1)
+    assert _rel(d1, d0) < 1e-12
+    assert np.allclose(Xr.mean(0), 0.0, atol=1e-12 * np.abs(Xr).max())
+    assert np.allclose(Xr.T @ Xr / X.shape[0], np.diag(lam), atol=1e-11 * lam[0])
+
+
+# --------------------------------------------------------------------------
+# Section 3.1 / 3.2: the estimator (Lemma 3, Eq. 3, Eq. 4, Eq. 13)
+# --------------------------------------------------------------------------
+
+def pin_estimator_identity(o):
+    """Eq. 13 at d = D: Lambda_D / Lambda_D = 1, so the estimate is the exact
+    squared distance, bit for bit."""
+    rng = np.random.default_rng(41)
+    lam = synth.spectrum(24, 1.0)
+    for _ in range(20):
+        q, x = rng.standard_normal(24), rng.standard_normal(24)
+        exact = 0.0
+        for k in range(24):
+            exact += (q[k] - x[k]) ** 2
+        assert o.estimate_sq(q, x, 24, lam) == exact
+
+
+def pin_estimator_unbiased(o):
+    """Lemma 3 / Eq. 4 / Eq. 13: E[Lambda_D / Lambda_d * P_d] = E||X1 - X2||^2
+    = 2 Lambda_D for iid X1, X2 with covariance diag(lambda) (PCA basis = I).
+    Also checks the variance of the estimate's error against its closed form
+    Var = sum_{k<=d} 2 (a-1)^2 (2 lambda_k)^2 + sum_{k>d} 2 (2 lambda_k)^2,
+    a = Lambda_D / Lambda_d (Delta_k ~ N(0, 2 lambda_k) independent)."""
+    D = 16
+    lam = synth.spectrum(D, 1.0)
+    rng = np.random.default_rng(43)
+    m = 40000
+    A = rng.standard_normal((m, D)) * np.sqrt(lam)
+    B = rng.standard_normal((m, D)) * np.sqrt(lam)
+    exact = ((A - B) ** 2).sum(1)
+    for d in (2, 5, 9):
+        est = np.array([o.estimate_sq(A[i], B[i], d, lam) for i in range(m)])
+        mean, se = est.mean(), est.std(ddof=1) / math.sqrt(m)
+        assert abs(mean - 2 * lam.sum()) < 5 * se, (d, mean, 2 * lam.sum(), se)
+        a = lam.sum() / lam[:d].sum()
+        var_cf = (2 * (a - 1) ** 2 * (2 * lam[:d]) ** 2).sum() + (2 * (2 * lam[d:]) ** 2).sum()
+        var_mc = np.var(est - exact, ddof=1)
+        assert abs(var_mc / var_cf - 1.0) < 0.06, (d, var_mc, var_cf)
+
+
+# --------------------------------------------------------------------------
+# Section 3.3: epsilon_d (Eq. 14) and the failure bound (Lemma 5)
+# --------------------------------------------------------------------------
+
+def pin_eps_quantile_golden(o):
+    g = golden("eps_quantile.json")
+    row = np.array(g["rho_sorted"])
+    for case in g["cases"]:
+        e = o.eps_quantile(row, case["alpha"])
+        assert abs(e - case["eps"]) < 1e-15, (case, e)
+        # library cross-check: inverted-CDF quantile = smallest x with F(x) >= 1 - alpha
+        lib = np.quantile(row, 1.0 - case["alpha"], method="inverted_cdf") - 1.0
+        assert abs(e - lib) < 1e-15
+        assert np.mean(row - 1.0 > e) <= case["alpha"] + 1e-12
+
+
+def pin_eps_ratio_golden(o):
+    g = golden("eps_ratio.json")
+    Xr = np.array([g["a"], g["b"]], float)
+    rho = o.eps_sample(Xr, np.array(g["lam"], float), np.array([[0, 1]]), g["dlist"])
+    assert rho.shape == (len(g["dlist"]), 1)
+    assert _rel(rho[:, 0], g["rho"]) < 1e-15
+    # a pair at distance zero has no ratio and is dropped
+    rho0 = o.eps_sample(np.array([g["a"], g["a"]], float), np.array(g["lam"], float),
+                        np.array([[0, 1]]), g["dlist"])
+    assert rho0.shape[1] == 0
+
+
+def _calib_setup(o, n=12000, D=32, p=1.0):
+    X, _, _ = synth.gaussian(n, D, p, seed=51, basis_seed=52)
+    mu, W, lam = o.pca(X)
+    Xr = o.rotate(X, mu, W)
+    return Xr, lam
+
+
+def pin_eps_calibration(o):
+    """Eq. 14: on held-out pairs the fraction with rho_d - 1 > eps_d is P_s
+    within binomial error; rho_D = 1 exactly."""
+    Xr, lam = _calib_setup(o)
+    n, D = Xr.shape
+    dl = [4, 8, 16, 24, D]
+    cal = o.eps_sample(Xr, lam, synth.eps_pairs(n, 20000, seed=61), dl)
+    held = o.eps_sample(Xr, lam, synth.eps_pairs(n, 20000, seed=62), dl)
+    assert np.all(cal[-1] == 1.0) and np.all(held[-1] == 1.0)
+    for alpha in (0.05, 0.1, 0.3):
+        for t, d in enumerate(dl[:-1]):
+            e = o.eps_quantile(cal[t], alpha)
+            frac = float(np.mean(held[t] - 1.0 > e))
+            sd = math.sqrt(alpha * (1 - alpha) / held.shape[1]) * math.sqrt(2)
+            assert abs(frac - alpha) < 4 * sd, (alpha, d, frac)
+
+
+def pin_failure_bound(o):
+    """Lemma 5: when dis <= r a DCO fails (prunes) with probability at most
+    floor((D-1)/delta_d) * P_s.  With r = dis for held-out pairs drawn like
+    the calibration pairs, every failure is a test whose rho_d exceeded
+    1 + eps_d, so the measured rate obeys the bound within binomial error."""
+    Xr, lam = _calib_setup(o)
+    n, D = Xr.shape
+    dd = 8
+    dl = list(range(dd, D, dd))
+    cal = o.eps_sample(Xr, lam, synth.eps_pairs(n, 20000, seed=71), dl)
+    alpha = 0.05
+    eps = np.full(D + 1, np.nan)
+    for t, d in enumerate(dl):
+        eps[d] = o.eps_quantile(cal[t], alpha)
+    pairs = synth.eps_pairs(n, 3000, seed=72)
+    fails = 0
+    for i, j in pairs:
+        r = math.sqrt(((Xr[i] - Xr[j]) ** 2).sum()) * (1 + 1e-12)
+        acc, d2, dims, _ = o.dco(Xr[i], Xr[j], dd, r, lam, eps)
+        fails += (not acc)
+        if acc:
+            assert dims == D
+    rate = fails / len(pairs)
+    bound = ((D - 1) // dd) * alpha
+    assert rate <= bound + 4 * math.sqrt(bound * (1 - bound) / len(pairs)), (rate, bound)
+    assert rate > 0.0  # the test is active at this alpha
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1 (Section 3.4), Definition 1
+# --------------------------------------------------------------------------
+
+def pin_dco_golden(o):
+    g = golden("dco_traces.json")
+    for case in g["cases"]:
+        r = math.inf if case["r"] == "inf" else float(case["r"])
+        acc, d2, dims, _ = o.dco(case["q"], case["o"], case["delta_d"], r, np.array(case["lam"], float),
+                                 np.array(case["eps"], float), prune=case["prune"])
+        assert acc == case["accept"], case["name"]
+        assert dims == case["dims"], (case["name"], dims)
+        if acc:
+            assert d2 == case["dist2"], case["name"]
+
+
+def _tiny_index(o, n=900, D=32, nc=7, dup=True, seed=81):
+    X, _, _ = synth.gaussian(n, D, 1.0, seed=seed, basis_seed=seed + 1)
+    if dup and n > 601:  # exact duplicates: distance ties that the (dist, id) order must break
+        X[5] = X[17]
+        X[300] = X[17]
+        X[600] = X[401]
+    mu, W, lam = o.pca(X)
+    Xr = o.rotate(X, mu, W)
+    init = synth.kmeans_init(n, nc, seed=seed + 2)
+    cent, _, _, _ = o.kmeans(Xr, init, 5)
+    assign, _ = o.assign(Xr, cent)
+    Q, _, _ = synth.gaussian(25, D, 1.0, seed=seed + 3, basis_seed=seed + 1)
+    Q[3] = X[17]
+    Qr = o.rotate(Q, mu, W)
+    return X, Xr, lam, cent, assign, Q, Qr
+
+
+def _brute(Xr, Qr, K):
+    d = ((Qr[:, None, :] - Xr[None, :, :]) ** 2).sum(-1)
+    ids = np.empty((Qr.shape[0], K), np.int64)
+    for i in range(Qr.shape[0]):
+        order = np.lexsort((np.arange(Xr.shape[0]), d[i]))
+        ids[i] = order[:K]
+    return ids, np.take_along_axis(d, ids, 1)
+
+
+def pin_search_fd_bruteforce(o):
+    """IVF + FDScanning over every list (nprobe = N_c) is exact KNN; ordered
+    by (distance, id), duplicates included."""
+    X, Xr, lam, cent, assign, Q, Qr = _tiny_index(o)
+    K = 12
+    ids, dists, stats, _ = o.search(Xr, assign, cent, lam, Qr, K, cent.shape[0], 8, None, schedule=0)
+    bid, bd = _brute(Xr, Qr, K)
+    assert np.array_equal(ids, bid)
+    assert _rel(dists, bd) < 1e-12
+    assert np.all(stats[:, 0] == X.shape[0]) and np.all(stats[:, 1] == X.shape[0] * X.shape[1])
+    # ground truth in the original coordinates agrees (Lemma 1)
+    gid, _ = o.exact_knn(X, Q, K)
+    assert np.mean(gid == bid) > 0.99
+
+
+def _eps_for(o, Xr, lam, delta_d, alpha, seed=91):
+    n, D = Xr.shape
+    dl = list(range(delta_d, D, delta_d))
+    rho = o.eps_sample(Xr, lam, synth.eps_pairs(n, 5000, seed=seed), dl)
+    return o.eps_table(rho, dl, D, alpha)
+
+
+def pin_search_dade_valid(o):
+    """DADE results are exact distances of members of the probed lists, in
+    (distance, id) order; an infinite eps reproduces FDScanning."""
+    X, Xr, lam, cent, assign, Q, Qr = _tiny_index(o)
+    K, nprobe = 10, 3
+    eps = _eps_for(o, Xr, lam, 8, 0.1)
+    ids, dists, stats, _ = o.search(Xr, assign, cent, lam, Qr, K, nprobe, 8, eps, schedule=1, tile=16)
+    probe, _ = o.probe(Qr, cent, nprobe)
+    for i in range(Qr.shape[0]):
+        assert np.all(np.isin(assign[ids[i]], probe[i]))
+        ex = ((Xr[ids[i]] - Qr[i]) ** 2).sum(1)
+        assert _rel(dists[i], ex) < 1e-12
+        key = list(zip(dists[i], ids[i]))
+        assert key == sorted(key)
+    assert np.all(stats[:, 1] < stats[:, 0] * X.shape[1])  # pruning saved dimensions
+    fd = o.search(Xr, assign, cent, lam, Qr, K, nprobe, 8, None, schedule=1, tile=16)
+    inf = o.search(Xr, assign, cent, lam, Qr, K, nprobe, 8, np.full(X.shape[1] + 1, np.inf),
+                   schedule=1, tile=16)
+    assert np.array_equal(fd[0], inf[0])
+    # the same lists searched exhaustively: DADE recall close to FDScanning's
+    assert np.mean([len(set(a) & set(b)) / K for a, b in zip(ids, fd[0])]) > 0.8
+
+
+def pin_search_trace(o):
+    """Brute-force re-run of the paper's sequential IVF loop: probe order,
+    ascending ids, one DCO per candidate against the heap's current maximum,
+    heap of the K best by (distance, id).  Built from single-pair DCO calls and
+    a Python sorted list; must equal or_search's SEQUENTIAL schedule."""
+    X, Xr, lam, cent, assign, Q, Qr = _tiny_index(o)
+    K, nprobe, dd = 6, 3, 8
+    eps = _eps_for(o, Xr, lam, dd, 0.2)
+    ids, dists, _, _ = o.search(Xr, assign, cent, lam, Qr, K, nprobe, dd, eps, schedule=0)
+    probe, _ = o.probe(Qr, cent, nprobe)
+    for i in range(Qr.shape[0]):
+        heap = []
+        for c in probe[i]:
+            for m in np.nonzero(assign == c)[0]:
+                r = math.sqrt(heap[-1][0]) if len(heap) == K else math.inf
+                acc, d2, _, _ = o.dco(Qr[i], Xr[m], dd, r, lam, eps)
+                if acc:
+                    heap = sorted(heap + [(d2, int(m))])[:K]
+        assert [h[1] for h in heap] == list(ids[i][:len(heap)])
+        assert np.allclose([h[0] for h in heap], dists[i][:len(heap)], rtol=0, atol=0)
+
+
+def pin_search_schedules(o):
+    """Epoch schedules: TILE(1) is SEQUENTIAL; a tile longer than every list
+    is PROBE_ROUNDS."""
+    X, Xr, lam, cent, assign, Q, Qr = _tiny_index(o)
+    eps = _eps_for(o, Xr, lam, 8, 0.2)
+    a = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, eps, schedule=0)
+    b = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, eps, schedule=1, tile=1)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    c = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, eps, schedule=2)
+    d = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, eps, schedule=1, tile=X.shape[0])
+    assert np.array_equal(c[0], d[0]) and np.array_equal(c[2], d[2])
+
+
+def pin_search_short_lists(o):
+    """Fewer candidates than K: the missing slots are (-1, +inf)."""
+    X, Xr, lam, cent, assign, Q, Qr = _tiny_index(o, n=40, nc=7, dup=False)
+    K = 64
+    ids, dists, stats, _ = o.search(Xr, assign, cent, lam, Qr, K, 2, 8, None, schedule=1, tile=4)
+    for i in range(Qr.shape[0]):
+        m = int(stats[i, 0])
+        assert m < K
+        assert np.all(ids[i, m:] == -1) and np.all(np.isinf(dists[i, m:]))
+        assert np.all(ids[i, :m] >= 0)
+
+
+# --------------------------------------------------------------------------
+# IVF building blocks (Section 3.4) against library routines
+# --------------------------------------------------------------------------
+
+def pin_kmeans_vs_scipy(o):
+    """Lloyd iterations from given initial points vs scipy's kmeans2 with the
+    same initial matrix (ties to the lower index, empty clusters keep their
+    centroid); the objective never increases."""
+    from scipy.cluster.vq import kmeans2, vq
+    X, _, _ = synth.gaussian(1500, 8, 0.5, seed=101, basis_seed=102)
+    Xd = X.astype(np.float64)
+    init = synth.kmeans_init(1500, 12, seed=103)
+    init[5] = init[4]  # duplicated start: one cluster stays empty, ties resolved low
+    cent, assign, obj, _ = o.kmeans(Xd, init, 6)
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        ref_c, ref_l = kmeans2(Xd, Xd[init].copy(), iter=6, minit="matrix", missing="warn")
+    assert np.allclose(cent, ref_c, rtol=0, atol=1e-12 * np.abs(Xd).max())
+    assert np.array_equal(assign, ref_l)
+    assert np.all(np.diff(obj) <= 1e-9 * obj[0])
+    a2, _ = o.assign(Xd, cent)
+    assert np.array_equal(a2, vq(Xd, cent)[0])
+
+
+def pin_list_means(o):
+    X, _, _ = synth.gaussian(500, 6, 1.0, seed=111, basis_seed=112)
+    Xd = X.astype(np.float64)
+    lab = synth.zipf_assign(500, 9, seed=113)
+    cent = o.list_means(Xd, lab, 10)
+    for c in range(10):
+        m = lab == c
+        ref = Xd[m].mean(0) if m.any() else np.zeros(6)
+        assert np.allclose(cent[c], ref, atol=1e-13)
+
+
+def pin_probe_order(o):
+    rng = np.random.default_rng(121)
+    Qr = rng.standard_normal((30, 10))
+    cent = rng.standard_normal((40, 10))
+    cent[7] = cent[3]  # equal distances: order by centroid id
+    pr, _ = o.probe(Qr, cent, 9)
+    d = ((Qr[:, None, :] - cent[None, :, :]) ** 2).sum(-1)
+    for i in range(30):
+        assert list(pr[i]) == list(np.lexsort((np.arange(40), d[i]))[:9])
+
+
+def pin_exact_knn(o):
+    X, _, _ = synth.gaussian(400, 12, 1.0, seed=131, basis_seed=132)
+    X[10] = X[20]
+    Q, _, _ = synth.gaussian(15, 12, 1.0, seed=133, basis_seed=132)
+    Q[0] = X[20]
+    ids, dists = o.exact_knn(X, Q, 7)
+    bid, bd = _brute(X.astype(np.float64), Q.astype(np.float64), 7)
+    assert np.array_equal(ids, bid)
+    assert _rel(dists, bd) < 1e-12
+
+
+ALL = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

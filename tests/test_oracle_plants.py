@@ -1,0 +1,73 @@
+"""Every plausible mistake planted in the oracle must trip at least one pin.
+
+Each case copies dade_oracle.c, applies one textual change (a dropped term, a
+wrong sign, an inverted ratio, a transposed operand, an off-by-one ...),
+builds it on the CPU into a temporary directory and runs the pins against it.
+The original file is never modified.
+"""
+import os
+import tempfile
+
+import pytest
+
+import oracle
+import pins
+
+PLANTS = [
+    ("estimate_ratio_inverted", "return Lam[D] / Lam[d] * Pd;", "return Lam[d] / Lam[D] * Pd;"),
+    ("one_minus_eps", "double bound = (1.0 + eps[d]) * r;", "double bound = (1.0 - eps[d]) * r;"),
+    ("eps_not_applied", "double bound = (1.0 + eps[d]) * r;", "double bound = r;"),
+    ("reject_on_equality", "if (est > bound) { *dims = d; return 0; }",
+     "if (est >= bound) { *dims = d; return 0; }"),
+    ("strict_accept", "            return P <= r2;\n        }", "            return P < r2;\n        }"),
+    ("rotation_transposed", "s += W[(int64_t)j * d + k] * ((double)x[j] - mu[j]);",
+     "s += W[(int64_t)k * d + j] * ((double)x[j] - mu[j]);"),
+    # E[X X^T] without the centring of Lemma 1 (both factors uncentred; one
+    # uncentred factor alone is not a mistake since sum_i (x_ij - mu_j) = 0)
+    ("covariance_not_centred", ["double yj = (double)x[j] - mu[j];", "row[k] += yj * ((double)x[k] - mu[k]);"],
+     ["double yj = (double)x[j];", "row[k] += yj * ((double)x[k]);"]),
+    ("eigen_ascending", "if (lam[j] > lam[best]) best = j;", "if (lam[j] < lam[best]) best = j;"),
+    ("jacobi_sign", "A[(int64_t)k * d + p] = c * akp - s * akq;", "A[(int64_t)k * d + p] = c * akp + s * akq;"),
+    ("quantile_floor", "(int64_t)ceil((1.0 - alpha) * (double)m);", "(int64_t)floor((1.0 - alpha) * (double)m);"),
+    ("quantile_alpha_side", "(int64_t)ceil((1.0 - alpha) * (double)m);", "(int64_t)ceil(alpha * (double)m);"),
+    ("rho_without_sqrt", "rho[(int64_t)t * m + kept] = sqrt(LD / Ld * Pd[dd - 1] / PD);",
+     "rho[(int64_t)t * m + kept] = LD / Ld * Pd[dd - 1] / PD;"),
+    ("rho_prefix_off_by_one", "for (int k = 0; k < dd; ++k) Ld += lam[k];",
+     "for (int k = 0; k <= dd && k < d; ++k) Ld += lam[k];"),
+    ("increment_drops_a_dim", "for (int k = d; k < dn; ++k) { double t = q[k] - o[k]; P += t * t; }",
+     "for (int k = d; k < dn - 1; ++k) { double t = q[k] - o[k]; P += t * t; }"),
+    ("heap_tie_reversed", "return (x->id > y->id) - (x->id < y->id);", "return (x->id < y->id) - (x->id > y->id);"),
+    ("nearest_tie_high", "if (t < b1) { b2 = b1; b1 = t; best = c; }", "if (t <= b1) { b2 = b1; b1 = t; best = c; }"),
+    ("empty_cluster_zeroed", "            if (cnt[c] > 0)\n                for (int k = 0; k < d; ++k) cent[(int64_t)c * d + k] = sum",
+     "            if (cnt[c] >= 0)\n                for (int k = 0; k < d; ++k) cent[(int64_t)c * d + k] = sum"),
+    ("threshold_not_refreshed", "double r2 = ntop == K ? buf[K - 1].key : INFINITY;", "double r2 = INFINITY;"),
+    ("threshold_is_first_not_kth", "double r2 = ntop == K ? buf[K - 1].key : INFINITY;",
+     "double r2 = ntop == K ? buf[0].key : INFINITY;"),
+    ("probe_descending", "for (int j = 0; j < nprobe; ++j) {\n                probe[q * nprobe + j] = (int32_t)buf[j].id;",
+     "for (int j = 0; j < nprobe; ++j) {\n                probe[q * nprobe + j] = (int32_t)buf[nc - 1 - j].id;"),
+]
+
+
+def _first_failure(o):
+    for pin in pins.ALL:
+        try:
+            pin(o)
+        except Exception as e:  # noqa: BLE001 - any failure counts as caught
+            return pin.__name__, type(e).__name__
+    return None
+
+
+@pytest.mark.parametrize("name,old,new", PLANTS, ids=[p[0] for p in PLANTS])
+def test_plant_is_caught(name, old, new):
+    src = open(oracle.SRC).read()
+    olds, news = (old, new) if isinstance(old, list) else ([old], [new])
+    for a, b in zip(olds, news):
+        assert src.count(a) == 1, f"plant site for {name} not found exactly once"
+        src = src.replace(a, b)
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "planted.c")
+        with open(path, "w") as f:
+            f.write(src)
+        lib = oracle.build(src=path, out=os.path.join(tmp, "libplanted.so"))
+        caught = _first_failure(oracle.Oracle(lib))
+    assert caught is not None, f"planted mistake {name} passed every pin"
