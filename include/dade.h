@@ -1,0 +1,231 @@
+/*
+ * dade.h -- C ABI of libdade: DADE distance comparisons inside an IVF scan on
+ * one GB300 (sm_103a).
+ *
+ * The method is DADE (Deng et al., "Efficient Data-aware Distance Comparison
+ * Operations for High-Dimensional Approximate Nearest Neighbor Search"):
+ * data objects are rotated once by the PCA basis W (Section 3.2, Eq. 10-12);
+ * a distance comparison operation (DCO, Definition 1) between a query q and a
+ * candidate o accumulates the squared distance over the leading dimensions in
+ * steps of delta_d, forms the estimate dis'^2 = Lambda_D / Lambda_d * P_d
+ * (Eq. 13) and rejects the candidate as soon as dis' > (1 + eps_d) r, where r
+ * is the query's current K-th nearest distance and eps_d is set by the
+ * significance level P_s (= alpha here) from sampled pairs (Section 3.3,
+ * Eq. 14); a candidate that is never rejected gets its exact distance at
+ * d = D (Algorithm 1).  IVF (Section 3.4) supplies the candidates: the
+ * members of the nprobe inverted lists nearest to the query.
+ *
+ * Conventions for every entry point
+ *   - Plain pointers and sizes only.  Row-major arrays.  Sizes are element
+ *     counts unless named *_bytes.
+ *   - Array arguments marked "host or device" may point to host memory
+ *     (pageable or pinned) or to CUDA device memory; the library detects which
+ *     and stages host data through its own device workspace.  Host results are
+ *     complete when the call returns; device results are complete when work
+ *     queued on `stream` before the next synchronisation has finished.
+ *   - The caller owns every array it passes; the library owns the index.
+ *   - Nothing throws across the ABI.  Every failure returns a dade_status and
+ *     leaves a message for dade_last_error() (thread-local).  Invalid
+ *     arguments are rejected before any GPU work is queued.
+ *   - All GPU work runs on `stream` (a cudaStream_t; NULL = legacy default).
+ *     One index serves one call at a time: concurrent calls on the same index
+ *     from several host threads are not supported (they share its workspace).
+ *   - Distances returned are squared Euclidean distances (monotone in the
+ *     paper's dis; no square root on the hot path).  Result lists are ordered
+ *     by (squared distance, id) ascending; slots beyond the candidates found
+ *     hold id -1 and distance +inf.
+ */
+#ifndef DADE_H
+#define DADE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dade_index dade_index;      /* opaque; resident in device memory */
+typedef struct CUstream_st *dade_stream;   /* same type as cudaStream_t */
+
+typedef enum {
+    DADE_OK = 0,
+    DADE_EINVAL = 1,        /* an argument is out of range or inconsistent */
+    DADE_ENOMEM = 2,        /* a host or device allocation failed */
+    DADE_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    DADE_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+    DADE_EUNSUPPORTED = 5,  /* valid request this build does not implement */
+    DADE_EIO = 6            /* file could not be read or written */
+} dade_status;
+
+enum {
+    DADE_MAX_DIM = 1024,    /* D <= 1024 */
+    DADE_MAX_K = 256,       /* K <= 256 */
+    DADE_BLOCK = 16         /* dimensions per stored block; delta_d is a multiple */
+};
+
+/* Threshold schedule / DCO kind of a search. */
+typedef enum {
+    DADE_MODE_DADE = 0,     /* Algorithm 1 with the Section 3.3 test */
+    DADE_MODE_FD = 1        /* FDScanning (Section 4.1): exact full-D distance for every candidate */
+} dade_mode;
+
+/* Index construction options.  Zero-initialise, then call dade_build_opts_default(). */
+typedef struct {
+    int32_t n_clusters;        /* N_c, number of inverted lists (>= 1) */
+    int32_t kmeans_iters;      /* Lloyd iterations (default 10); ignored when assign != NULL */
+    uint64_t seed;             /* key of the SplitMix64 draws used when kmeans_init / pairs are NULL */
+    int64_t eps_pairs;         /* M, sampled pairs for eps_d (default 100000) */
+    const int32_t *assign;     /* host, optional [n]: list of every base vector (0..n_clusters-1);
+                                  list centroids become member means; no k-means runs */
+    const int64_t *kmeans_init;/* host, optional [n_clusters]: distinct base ids that seed k-means */
+    const int64_t *pairs;      /* host, optional [2 * eps_pairs]: pair ids (i != j) for eps_d */
+    int32_t reserved[8];
+} dade_build_opts;
+
+/* Search options; NULL means all defaults. */
+typedef struct {
+    int32_t mode;              /* dade_mode (default DADE_MODE_DADE) */
+    int32_t tile;              /* candidates per threshold refresh (default 128; 32..256, multiple of 32) */
+    int64_t *stats;            /* device, optional [nq * 4]: per query candidates scanned, sum of
+                                  dimensions used, candidates accepted by the DCO, candidates pruned */
+    int32_t reserved[8];
+} dade_search_opts;
+
+/* Description of a built index. */
+typedef struct {
+    int64_t n;                 /* base vectors */
+    int32_t d;                 /* dimension D */
+    int32_t d_pad;             /* D rounded up to a multiple of 16 (storage width) */
+    int32_t n_clusters;
+    int32_t max_list;          /* longest inverted list */
+    int64_t eps_kept;          /* sampled pairs kept for eps_d (nonzero distance) */
+    int64_t device_bytes;      /* device memory held by the index (excluding workspace) */
+    int64_t data_bytes;        /* packed rotated vectors */
+    int32_t kmeans_iters;      /* Lloyd iterations run (0 when lists were given) */
+    int32_t reserved;
+} dade_info;
+
+/* Fields for dade_index_export (host copies, for inspection and tests). */
+typedef enum {
+    DADE_FIELD_MEAN = 0,       /* double [d]          mu */
+    DADE_FIELD_BASIS = 1,      /* double [d * d]      W, column k = w_k (row-major: W[j*d + k]) */
+    DADE_FIELD_EIGVAL = 2,     /* double [d]          lambda_1 >= ... >= lambda_D */
+    DADE_FIELD_CENTROIDS = 3,  /* float  [n_clusters * d]  rotated list centroids */
+    DADE_FIELD_ASSIGN = 4,     /* int32  [n]          list of every base vector */
+    DADE_FIELD_ROTATED = 5,    /* float  [n * d]      rotated base vectors, by base id */
+    DADE_FIELD_RHO = 6,        /* double [(d_pad/16 - 1) * eps_kept]  sorted rho_d samples, row t is d = 16 (t+1) */
+    DADE_FIELD_KMEANS_OBJ = 7  /* double [kmeans_iters] objective of each assignment step */
+} dade_field;
+
+void dade_build_opts_default(dade_build_opts *opts);
+
+/*
+ * Build an index over n base vectors of dimension d (Section 3.2 and 3.4):
+ *   mean and covariance of the data (FP64 on the GPU), eigendecomposition
+ *   (FP64 on the host), rotation o' = W^T (o - mu) of every vector (FP32 on
+ *   the GPU), inverted lists (given `assign`, or seeded k-means on the rotated
+ *   vectors), and the sorted rho_d sample for eps_d (Eq. 14) at every d that is
+ *   a multiple of 16 below D.  Vectors are stored rotated, once, in a
+ *   dimension-blocked layout: per list, per 16-dimension block, a contiguous
+ *   [list length][16] FP32 slab.
+ * base: host or device, [n * d] FP32.  n >= 2, 1 <= d <= DADE_MAX_DIM,
+ * 1 <= n_clusters <= n.  On success *out receives the index (free it with
+ * dade_free_index).  Synchronises `stream` before returning.
+ */
+dade_status dade_build_index(const float *base, int64_t n, int32_t d, const dade_build_opts *opts,
+                             dade_index **out, dade_stream stream);
+
+/* Release an index and its workspace.  NULL is ignored. */
+void dade_free_index(dade_index *ix);
+
+/*
+ * Query rotation q' = W^T (q - mu) (Lemma 1, Section 3.2): the transformed
+ * query that Algorithm 1 takes as input.  q: host or device [nq * d] FP32;
+ * q_rot: host or device [nq * d] FP32 output.  nq = 0 is a no-op.
+ */
+dade_status dade_rotate_queries(const dade_index *ix, const float *q, int64_t nq, float *q_rot,
+                                dade_stream stream);
+
+/*
+ * IVF probe (Section 3.4): for every rotated query, the ids of the nprobe
+ * lists whose centroids are nearest, ordered by (squared distance, list id).
+ * q_rot: host or device [nq * d]; probe: host or device [nq * nprobe] int32.
+ */
+dade_status dade_probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t nprobe,
+                       int32_t *probe, dade_stream stream);
+
+/*
+ * DADE-IVF search on rotated queries: probe, then scan the probed lists with
+ * one DCO per candidate (Algorithm 1 and the Section 3.3 test at
+ * significance alpha) against the query's current K-th distance, keeping the
+ * K nearest.  Lists are scanned in probe order, members in ascending base id,
+ * in tiles of opts->tile candidates; every candidate of a tile is tested
+ * against the K-th distance held before the tile (the threshold is refreshed
+ * once per tile; a stale threshold can only prune less).
+ * q_rot: host or device [nq * d]; ids: host or device [nq * k] int64; dists:
+ * host or device [nq * k] FP32 squared distances.  1 <= k <= DADE_MAX_K,
+ * 1 <= nprobe <= n_clusters, 0 < alpha < 1, delta_d a multiple of 16 in
+ * [16, DADE_MAX_DIM].  alpha and delta_d are ignored in DADE_MODE_FD.
+ */
+dade_status dade_search(const dade_index *ix, const float *q_rot, int64_t nq, int32_t k,
+                        int32_t nprobe, float alpha, int32_t delta_d, const dade_search_opts *opts,
+                        int64_t *ids, float *dists, dade_stream stream);
+
+/*
+ * End-to-end query: dade_rotate_queries followed by dade_search, on raw
+ * queries.  q: host or device [nq * d].  Same outputs and limits as
+ * dade_search.  With host buffers the call copies inputs in and results out
+ * and returns when the results are on the host.
+ */
+dade_status dade_query(const dade_index *ix, const float *q, int64_t nq, int32_t k, int32_t nprobe,
+                       float alpha, int32_t delta_d, const dade_search_opts *opts, int64_t *ids,
+                       float *dists, dade_stream stream);
+
+/*
+ * Reserve workspace for searches of up to max_nq queries with up to
+ * max_nprobe lists, so that later calls within these limits allocate nothing
+ * (e.g. before capturing them in a CUDA graph).
+ */
+dade_status dade_reserve(dade_index *ix, int64_t max_nq, int32_t max_nprobe);
+
+/*
+ * eps_d (Eq. 14) and the per-increment pruning coefficients used by the scan
+ * for significance alpha and step delta_d.  eps: host [d + 1], eps[dd] set for
+ * every tested dd = delta_d, 2 delta_d, ... < D (others NaN).  coef: host
+ * [d + 1] or NULL, coef[dd] = (1 + eps_dd)^2 * Lambda_dd / Lambda_D rounded to
+ * FP32 (prune iff P_dd > coef[dd] * r^2, the squared form of the test).
+ */
+dade_status dade_eps_table(const dade_index *ix, float alpha, int32_t delta_d, double *eps, float *coef);
+
+/*
+ * Wait for the work queued on `stream`, then report and clear any failure
+ * that the index's kernels recorded on the device since the last check
+ * (DADE_ETIMEOUT from a bounded wait).  Calls with host outputs check this
+ * themselves.
+ */
+dade_status dade_sync(const dade_index *ix, dade_stream stream);
+
+dade_status dade_index_info(const dade_index *ix, dade_info *info);
+
+/* Host copy of one field (see dade_field); bytes must equal the field's size. */
+dade_status dade_index_export(const dade_index *ix, int32_t field, void *dst, size_t bytes);
+
+/*
+ * Host FP64 symmetric eigendecomposition used by dade_build_index
+ * (Householder tridiagonalisation, then implicit symmetric QR with Wilkinson
+ * shifts).  a: host [n * n] symmetric (overwritten); w: host [n] eigenvalues,
+ * descending; v: host [n * n], column k = unit eigenvector of w[k].
+ */
+dade_status dade_host_sym_eig(double *a, int32_t n, double *w, double *v);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *dade_last_error(void);
+
+/* Library version string. */
+const char *dade_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DADE_H */

@@ -471,8 +471,11 @@ OR_API int or_dco(const double *q, const double *o, int D, int delta_d, double r
  * Results are ordered by (squared distance, id); missing slots are (-1, +inf).
  * eps == NULL runs FDScanning.  eps is indexed by d (eps[d], d < D).
  * stats (nq x 4, may be NULL): candidates, sum of dims used, accepted, pruned.
- * flags (nq, may be NULL): 1|2 test near-ties (see dco), 4 near-tie at the
- * K-th place of a merge, 8 near-tie in the probe order.
+ * flags (nq, may be NULL): 1|2 test near-ties (see dco), 4 near-tie between
+ * the final K-th result and the best accepted candidate that did not stay
+ * (a candidate pushed to place K+1 of a merge already has K better ones and
+ * can never return, so only the final boundary can change the result),
+ * 8 near-tie in the probe order.
  */
 OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, int nc,
                      const double *cent, const double *lam, const double *Qr, int64_t nq,
@@ -503,6 +506,7 @@ OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, 
         for (int64_t qi = 0; qi < nq; ++qi) {
             const double *q = Qr + qi * D;
             int ntop = 0, tie = 0;
+            double dropped = INFINITY;   /* best squared distance accepted but not kept */
             int64_t st[4] = {0, 0, 0, 0};
             for (int j = 0; j < nprobe; ++j) {
                 int c = probe[qi * nprobe + j];
@@ -527,11 +531,12 @@ OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, 
                     if (npend > 0) {
                         int u = ntop + npend;
                         qsort(buf, (size_t)u, sizeof(kv_t), kv_cmp);
-                        if (u > K && near_tie(buf[K - 1].key, buf[K].key, tol)) tie |= 4;
+                        if (u > K && buf[K].key < dropped) dropped = buf[K].key;
                         ntop = u < K ? u : K;
                     }
                 }
             }
+            if (ntop == K && isfinite(dropped) && near_tie(buf[K - 1].key, dropped, tol)) tie |= 4;
             for (int s = 0; s < K; ++s) {
                 ids[qi * K + s] = s < ntop ? buf[s].id : -1;
                 dists[qi * K + s] = s < ntop ? buf[s].key : INFINITY;

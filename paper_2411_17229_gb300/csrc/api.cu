@@ -1,0 +1,434 @@
+// api.cu -- the extern "C" entry points declared in include/dade.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace dade {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+dade_status launch_check(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("launch of ") + what + " failed: " + cudaGetErrorString(e));
+        return DADE_ECUDA;
+    }
+    return DADE_OK;
+}
+
+dade_status DevBuf::alloc(size_t b) {
+    release();
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        set_error(std::string("cudaMalloc of ") + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+        return DADE_ENOMEM;
+    }
+    bytes = b;
+    return DADE_OK;
+}
+
+dade_status DevBuf::ensure(size_t b) {
+    if (p && bytes >= b) return DADE_OK;
+    return alloc(b + b / 4);
+}
+
+dade_status build_index(const float *base, int64_t n, int32_t d, const dade_build_opts &o, dade_index *ix,
+                        cudaStream_t s);
+
+int coef_table(const dade_index *ix, float alpha, int32_t delta_d, double *eps, float *coef) {
+    const int D = ix->d;
+    const int gb = std::min(delta_d / 16, ix->nb);
+    const int n_inc = (ix->nb + gb - 1) / gb;
+    const double a = (double)alpha;   // alpha is an FP32 value; both sides of a comparison use it as such
+    for (int j = 0; j + 1 < n_inc; ++j) {
+        const int dd = (j + 1) * gb * 16;          // tested d < D
+        double e = std::numeric_limits<double>::infinity();
+        const int64_t m = ix->eps_kept;
+        if (m > 0) {
+            int64_t idx = (int64_t)std::ceil((1.0 - a) * (double)m);
+            idx = std::min<int64_t>(std::max<int64_t>(idx, 1), m);
+            e = ix->rho[(size_t)(dd / 16 - 1) * m + (idx - 1)] - 1.0;
+        }
+        if (eps) eps[dd] = e;
+        const double c = (1.0 + e) * (1.0 + e) * ix->Lam[dd] / ix->Lam[D];
+        coef[j] = (float)c;
+    }
+    return n_inc;
+}
+
+} // namespace dade
+
+using namespace dade;
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes attr{};
+    cudaError_t e = cudaPointerGetAttributes(&attr, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+dade_status check_device_errors(const dade_index *ix, cudaStream_t s) {
+    int h = 0;
+    DADE_TRY_CUDA(cudaMemcpyAsync(&h, ix->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DADE_TRY_CUDA(cudaStreamSynchronize(s));
+    if (h != 0) {
+        DADE_TRY_CUDA(cudaMemsetAsync(ix->errflag.p, 0, sizeof(int), s));
+        set_error("a bounded device-side wait gave up (status recorded by the scan kernel)");
+        return (dade_status)h;
+    }
+    return DADE_OK;
+}
+
+dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t nprobe, float alpha,
+                            int32_t delta_d, const dade_search_opts *opts) {
+    DADE_CHECK_ARG(ix != nullptr, "index is NULL");
+    DADE_CHECK_ARG(nq >= 0, "nq < 0");
+    DADE_CHECK_ARG(k >= 1 && k <= DADE_MAX_K, "k outside 1..DADE_MAX_K");
+    DADE_CHECK_ARG(nprobe >= 1 && nprobe <= ix->nc, "nprobe outside 1..n_clusters");
+    DADE_CHECK_ARG(nprobe <= 8192, "nprobe > 8192");
+    const int mode = opts ? opts->mode : DADE_MODE_DADE;
+    DADE_CHECK_ARG(mode == DADE_MODE_DADE || mode == DADE_MODE_FD, "unknown mode");
+    if (mode == DADE_MODE_DADE) {
+        DADE_CHECK_ARG(alpha > 0.f && alpha < 1.f, "alpha outside (0, 1)");
+        DADE_CHECK_ARG(delta_d >= 16 && delta_d <= DADE_MAX_DIM && delta_d % 16 == 0,
+                       "delta_d must be a multiple of 16 in [16, 1024]");
+    }
+    const int tile = opts && opts->tile ? opts->tile : 128;
+    DADE_CHECK_ARG(tile >= 32 && tile <= 256 && tile % 32 == 0, "tile must be a multiple of 32 in [32, 256]");
+    return DADE_OK;
+}
+
+// Device copies of host inputs / host destinations of device outputs.
+struct Staged {
+    const float *q = nullptr;
+    int64_t *ids = nullptr;
+    float *dists = nullptr;
+    bool ids_host = false, dists_host = false;
+};
+
+dade_status run_search(const dade_index *ix, const float *q_dev, int64_t nq, int32_t k, int32_t nprobe, float alpha,
+                       int32_t delta_d, const dade_search_opts *opts, int64_t *ids, float *dists, cudaStream_t s) {
+    const bool ids_host = !is_device_ptr(ids), dists_host = !is_device_ptr(dists);
+    int64_t *ids_d = ids;
+    float *dists_d = dists;
+    if (ids_host) {
+        DADE_TRY(ix->ws_ids.ensure(sizeof(int64_t) * (size_t)nq * k));
+        ids_d = ix->ws_ids.as<int64_t>();
+    }
+    if (dists_host) {
+        DADE_TRY(ix->ws_dists.ensure(sizeof(float) * (size_t)nq * k));
+        dists_d = ix->ws_dists.as<float>();
+    }
+    DADE_TRY(ix->ws_probe.ensure(sizeof(int32_t) * (size_t)nq * nprobe));
+    DADE_TRY(dade::probe(ix, q_dev, nq, ix->d, nprobe, ix->ws_probe.as<int32_t>(), s));
+    ScanParams p{};
+    p.q_rot = q_dev;
+    p.q_stride = ix->d;
+    p.probe = ix->ws_probe.as<int32_t>();
+    p.nprobe = nprobe;
+    p.k = k;
+    p.tile = opts && opts->tile ? opts->tile : 128;
+    p.mode = opts ? opts->mode : DADE_MODE_DADE;
+    p.delta_d = delta_d;
+    if (p.mode == DADE_MODE_DADE) p.n_inc = coef_table(ix, alpha, delta_d, nullptr, p.coef);
+    else p.n_inc = 0;
+    p.ids = ids_d;
+    p.dists = dists_d;
+    p.stats = opts ? opts->stats : nullptr;
+    DADE_TRY(dade::scan(ix, nq, p, s));
+    if (ids_host)
+        DADE_TRY_CUDA(cudaMemcpyAsync(ids, ids_d, sizeof(int64_t) * (size_t)nq * k, cudaMemcpyDeviceToHost, s));
+    if (dists_host)
+        DADE_TRY_CUDA(cudaMemcpyAsync(dists, dists_d, sizeof(float) * (size_t)nq * k, cudaMemcpyDeviceToHost, s));
+    if (ids_host || dists_host) return check_device_errors(ix, s);
+    return DADE_OK;
+}
+
+const float *stage_in(const dade_index *ix, const float *src, size_t count, DevBuf &buf, cudaStream_t s,
+                      dade_status *st) {
+    *st = DADE_OK;
+    if (is_device_ptr(src)) return src;
+    if ((*st = buf.ensure(sizeof(float) * count)) != DADE_OK) return nullptr;
+    cudaError_t e = cudaMemcpyAsync(buf.p, src, sizeof(float) * count, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+        *st = DADE_ECUDA;
+        return nullptr;
+    }
+    (void)ix;
+    return buf.as<float>();
+}
+
+} // namespace
+
+extern "C" {
+
+const char *dade_last_error(void) { return g_err.c_str(); }
+
+const char *dade_version(void) { return "dade-gb300 0.1 (sm_103a)"; }
+
+void dade_build_opts_default(dade_build_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->n_clusters = 1;
+    o->kmeans_iters = 10;
+    o->seed = 0;
+    o->eps_pairs = 100000;
+}
+
+dade_status dade_build_index(const float *base, int64_t n, int32_t d, const dade_build_opts *opts, dade_index **out,
+                             dade_stream stream) {
+    g_err.clear();
+    DADE_CHECK_ARG(base != nullptr && out != nullptr && opts != nullptr, "NULL pointer");
+    DADE_CHECK_ARG(n >= 2, "n < 2");
+    DADE_CHECK_ARG(d >= 1 && d <= DADE_MAX_DIM, "d outside 1..DADE_MAX_DIM");
+    DADE_CHECK_ARG(n <= 0x7fffffffLL, "n must fit in 31 bits (ids are stored as int32)");
+    DADE_CHECK_ARG(opts->n_clusters >= 1 && opts->n_clusters <= n, "n_clusters outside 1..n");
+    DADE_CHECK_ARG(opts->kmeans_iters >= 0 && opts->kmeans_iters <= 1000, "kmeans_iters outside 0..1000");
+    DADE_CHECK_ARG(opts->eps_pairs >= 1, "eps_pairs < 1");
+    *out = nullptr;
+    dade_index *ix = new (std::nothrow) dade_index();
+    if (!ix) {
+        set_error("host allocation of the index failed");
+        return DADE_ENOMEM;
+    }
+    dade_status st = build_index(base, n, d, *opts, ix, (cudaStream_t)stream);
+    if (st != DADE_OK) {
+        delete ix;
+        return st;
+    }
+    *out = ix;
+    return DADE_OK;
+}
+
+void dade_free_index(dade_index *ix) { delete ix; }
+
+dade_status dade_rotate_queries(const dade_index *ix, const float *q, int64_t nq, float *q_rot, dade_stream stream) {
+    g_err.clear();
+    DADE_CHECK_ARG(ix != nullptr, "index is NULL");
+    DADE_CHECK_ARG(nq >= 0, "nq < 0");
+    if (nq == 0) return DADE_OK;
+    DADE_CHECK_ARG(q != nullptr && q_rot != nullptr, "NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    dade_status st;
+    const float *qd = stage_in(ix, q, (size_t)nq * ix->d, ix->ws_qin, s, &st);
+    if (!qd) return st;
+    const bool out_host = !is_device_ptr(q_rot);
+    float *od = q_rot;
+    if (out_host) {
+        DADE_TRY(ix->ws_qrot.ensure(sizeof(float) * (size_t)nq * ix->d));
+        od = ix->ws_qrot.as<float>();
+    }
+    DADE_TRY(dade::rotate(qd, nq, ix->d, ix->d, ix->W32.as<float>(), ix->mu32.as<float>(), ix->dp, od, s));
+    if (out_host) {
+        DADE_TRY_CUDA(cudaMemcpyAsync(q_rot, od, sizeof(float) * (size_t)nq * ix->d, cudaMemcpyDeviceToHost, s));
+        DADE_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    return DADE_OK;
+}
+
+dade_status dade_probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t nprobe, int32_t *probe,
+                       dade_stream stream) {
+    g_err.clear();
+    DADE_CHECK_ARG(ix != nullptr, "index is NULL");
+    DADE_CHECK_ARG(nq >= 0, "nq < 0");
+    DADE_CHECK_ARG(nprobe >= 1 && nprobe <= ix->nc && nprobe <= 8192, "nprobe outside 1..min(n_clusters, 8192)");
+    if (nq == 0) return DADE_OK;
+    DADE_CHECK_ARG(q_rot != nullptr && probe != nullptr, "NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    dade_status st;
+    const float *qd = stage_in(ix, q_rot, (size_t)nq * ix->d, ix->ws_qrot, s, &st);
+    if (!qd) return st;
+    const bool out_host = !is_device_ptr(probe);
+    int32_t *pd = probe;
+    if (out_host) {
+        DADE_TRY(ix->ws_probe.ensure(sizeof(int32_t) * (size_t)nq * nprobe));
+        pd = ix->ws_probe.as<int32_t>();
+    }
+    DADE_TRY(dade::probe(ix, qd, nq, ix->d, nprobe, pd, s));
+    if (out_host) {
+        DADE_TRY_CUDA(cudaMemcpyAsync(probe, pd, sizeof(int32_t) * (size_t)nq * nprobe, cudaMemcpyDeviceToHost, s));
+        DADE_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    return DADE_OK;
+}
+
+dade_status dade_search(const dade_index *ix, const float *q_rot, int64_t nq, int32_t k, int32_t nprobe, float alpha,
+                        int32_t delta_d, const dade_search_opts *opts, int64_t *ids, float *dists,
+                        dade_stream stream) {
+    g_err.clear();
+    DADE_TRY(validate_search(ix, nq, k, nprobe, alpha, delta_d, opts));
+    if (nq == 0) return DADE_OK;
+    DADE_CHECK_ARG(q_rot != nullptr && ids != nullptr && dists != nullptr, "NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    dade_status st;
+    const float *qd = stage_in(ix, q_rot, (size_t)nq * ix->d, ix->ws_qrot, s, &st);
+    if (!qd) return st;
+    return run_search(ix, qd, nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
+}
+
+dade_status dade_query(const dade_index *ix, const float *q, int64_t nq, int32_t k, int32_t nprobe, float alpha,
+                       int32_t delta_d, const dade_search_opts *opts, int64_t *ids, float *dists, dade_stream stream) {
+    g_err.clear();
+    DADE_TRY(validate_search(ix, nq, k, nprobe, alpha, delta_d, opts));
+    if (nq == 0) return DADE_OK;
+    DADE_CHECK_ARG(q != nullptr && ids != nullptr && dists != nullptr, "NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    dade_status st;
+    const float *qd = stage_in(ix, q, (size_t)nq * ix->d, ix->ws_qin, s, &st);
+    if (!qd) return st;
+    DADE_TRY(ix->ws_qrot.ensure(sizeof(float) * (size_t)nq * ix->d));
+    DADE_TRY(dade::rotate(qd, nq, ix->d, ix->d, ix->W32.as<float>(), ix->mu32.as<float>(), ix->dp,
+                          ix->ws_qrot.as<float>(), s));
+    return run_search(ix, ix->ws_qrot.as<float>(), nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
+}
+
+dade_status dade_reserve(dade_index *ix, int64_t max_nq, int32_t max_nprobe) {
+    g_err.clear();
+    DADE_CHECK_ARG(ix != nullptr, "index is NULL");
+    DADE_CHECK_ARG(max_nq >= 0 && max_nprobe >= 1 && max_nprobe <= ix->nc, "bad limits");
+    DADE_TRY(ix->ws_dist.ensure(sizeof(float) * (size_t)max_nq * ix->nc));
+    DADE_TRY(ix->ws_probe.ensure(sizeof(int32_t) * (size_t)max_nq * max_nprobe));
+    DADE_TRY(ix->ws_qrot.ensure(sizeof(float) * (size_t)max_nq * ix->d));
+    DADE_TRY(ix->ws_qin.ensure(sizeof(float) * (size_t)max_nq * ix->d));
+    return DADE_OK;
+}
+
+dade_status dade_eps_table(const dade_index *ix, float alpha, int32_t delta_d, double *eps, float *coef) {
+    g_err.clear();
+    DADE_CHECK_ARG(ix != nullptr && eps != nullptr, "NULL pointer");
+    DADE_CHECK_ARG(alpha > 0.f && alpha < 1.f, "alpha outside (0, 1)");
+    DADE_CHECK_ARG(delta_d >= 16 && delta_d % 16 == 0 && delta_d <= DADE_MAX_DIM, "bad delta_d");
+    for (int i = 0; i <= ix->d; ++i) eps[i] = std::numeric_limits<double>::quiet_NaN();
+    float c[DADE_MAX_DIM / DADE_BLOCK];
+    int n_inc = coef_table(ix, alpha, delta_d, eps, c);
+    if (coef) {
+        for (int i = 0; i <= ix->d; ++i) coef[i] = std::numeric_limits<float>::quiet_NaN();
+        const int gb = std::min(delta_d / 16, ix->nb);
+        for (int j = 0; j + 1 < n_inc; ++j) coef[(j + 1) * gb * 16] = c[j];
+    }
+    return DADE_OK;
+}
+
+dade_status dade_sync(const dade_index *ix, dade_stream stream) {
+    g_err.clear();
+    DADE_CHECK_ARG(ix != nullptr, "index is NULL");
+    return check_device_errors(ix, (cudaStream_t)stream);
+}
+
+dade_status dade_index_info(const dade_index *ix, dade_info *info) {
+    g_err.clear();
+    DADE_CHECK_ARG(ix != nullptr && info != nullptr, "NULL pointer");
+    info->n = ix->n;
+    info->d = ix->d;
+    info->d_pad = ix->dp;
+    info->n_clusters = ix->nc;
+    info->max_list = ix->max_list;
+    info->eps_kept = ix->eps_kept;
+    info->data_bytes = (int64_t)ix->data.bytes;
+    info->device_bytes = (int64_t)(ix->data.bytes + ix->ids.bytes + ix->meta.bytes + ix->cent.bytes + ix->W32.bytes +
+                                   ix->mu32.bytes + ix->errflag.bytes);
+    info->kmeans_iters = (int32_t)ix->kmeans_obj.size();
+    info->reserved = 0;
+    return DADE_OK;
+}
+
+dade_status dade_index_export(const dade_index *ix, int32_t field, void *dst, size_t bytes) {
+    g_err.clear();
+    DADE_CHECK_ARG(ix != nullptr && dst != nullptr, "NULL pointer");
+    const int d = ix->d;
+    auto need = [&](size_t b) -> dade_status {
+        if (bytes != b) {
+            set_error("invalid argument: export size mismatch (expected " + std::to_string(b) + " bytes)");
+            return DADE_EINVAL;
+        }
+        return DADE_OK;
+    };
+    switch (field) {
+    case DADE_FIELD_MEAN:
+        DADE_TRY(need(sizeof(double) * d));
+        std::memcpy(dst, ix->mu.data(), bytes);
+        return DADE_OK;
+    case DADE_FIELD_BASIS:
+        DADE_TRY(need(sizeof(double) * (size_t)d * d));
+        std::memcpy(dst, ix->W.data(), bytes);
+        return DADE_OK;
+    case DADE_FIELD_EIGVAL:
+        DADE_TRY(need(sizeof(double) * d));
+        std::memcpy(dst, ix->lam.data(), bytes);
+        return DADE_OK;
+    case DADE_FIELD_ASSIGN:
+        DADE_TRY(need(sizeof(int32_t) * (size_t)ix->n));
+        std::memcpy(dst, ix->assign.data(), bytes);
+        return DADE_OK;
+    case DADE_FIELD_RHO:
+        DADE_TRY(need(sizeof(double) * ix->rho.size()));
+        if (bytes) std::memcpy(dst, ix->rho.data(), bytes);
+        return DADE_OK;
+    case DADE_FIELD_KMEANS_OBJ:
+        DADE_TRY(need(sizeof(double) * ix->kmeans_obj.size()));
+        if (bytes) std::memcpy(dst, ix->kmeans_obj.data(), bytes);
+        return DADE_OK;
+    case DADE_FIELD_CENTROIDS: {
+        DADE_TRY(need(sizeof(float) * (size_t)ix->nc * d));
+        std::vector<float> c((size_t)ix->nc * ix->dp);
+        DADE_TRY_CUDA(cudaMemcpy(c.data(), ix->cent.p, sizeof(float) * c.size(), cudaMemcpyDeviceToHost));
+        float *o = static_cast<float *>(dst);
+        for (int r = 0; r < ix->nc; ++r) std::memcpy(o + (size_t)r * d, c.data() + (size_t)r * ix->dp, sizeof(float) * d);
+        return DADE_OK;
+    }
+    case DADE_FIELD_ROTATED: {
+        DADE_TRY(need(sizeof(float) * (size_t)ix->n * d));
+        std::vector<float> packed((size_t)ix->data_floats);
+        std::vector<int32_t> ids((size_t)ix->slots);
+        DADE_TRY_CUDA(cudaMemcpy(packed.data(), ix->data.p, sizeof(float) * packed.size(), cudaMemcpyDeviceToHost));
+        DADE_TRY_CUDA(cudaMemcpy(ids.data(), ix->ids.p, sizeof(int32_t) * ids.size(), cudaMemcpyDeviceToHost));
+        float *o = static_cast<float *>(dst);
+        for (int c = 0; c < ix->nc; ++c) {
+            const ListMeta &m = ix->lists[c];
+            for (int i = 0; i < m.len; ++i) {
+                int64_t id = ids[m.slot + i];
+                for (int k = 0; k < d; ++k)
+                    o[id * d + k] = packed[m.base + (int64_t)(k / 16) * m.np * 16 + (int64_t)i * 16 + k % 16];
+            }
+        }
+        return DADE_OK;
+    }
+    default:
+        set_error("invalid argument: unknown field");
+        return DADE_EINVAL;
+    }
+}
+
+dade_status dade_host_sym_eig(double *a, int32_t n, double *w, double *v) {
+    g_err.clear();
+    DADE_CHECK_ARG(a != nullptr && w != nullptr && v != nullptr, "NULL pointer");
+    DADE_CHECK_ARG(n >= 1 && n <= 4096, "n outside 1..4096");
+    std::vector<double> A(a, a + (size_t)n * n), W, V;
+    if (!dade::sym_eig(n, A, W, V)) {
+        set_error("symmetric QR did not converge");
+        return DADE_EUNSUPPORTED;
+    }
+    std::memcpy(w, W.data(), sizeof(double) * n);
+    std::memcpy(v, V.data(), sizeof(double) * (size_t)n * n);
+    std::memcpy(a, A.data(), sizeof(double) * (size_t)n * n);
+    return DADE_OK;
+}
+
+} // extern "C"

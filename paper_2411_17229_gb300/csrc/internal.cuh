@@ -1,0 +1,123 @@
+// internal.cuh -- shared declarations of libdade (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dade.h"
+
+namespace dade {
+
+// ---------------------------------------------------------------- errors ----
+void set_error(const std::string &msg);
+
+#define DADE_TRY_CUDA(expr)                                                              \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess) {                                                         \
+            ::dade::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));       \
+            return DADE_ECUDA;                                                           \
+        }                                                                                \
+    } while (0)
+
+#define DADE_TRY(expr)                                                                   \
+    do {                                                                                 \
+        dade_status _s = (expr);                                                         \
+        if (_s != DADE_OK) return _s;                                                    \
+    } while (0)
+
+#define DADE_CHECK_ARG(cond, msg)                                                        \
+    do {                                                                                 \
+        if (!(cond)) {                                                                   \
+            ::dade::set_error(std::string("invalid argument: ") + (msg));                \
+            return DADE_EINVAL;                                                          \
+        }                                                                                \
+    } while (0)
+
+dade_status launch_check(const char *what);
+
+// ----------------------------------------------------------- list layout ----
+// Per inverted list: offset of its region in the packed data (in floats,
+// 256-byte aligned), offset of its first slot in the id array, member count
+// and padded count (a multiple of 4).  Block b of the list is the slab
+// data[base + b * np * 16 ... + np * 16), candidate i at + i * 16.
+struct ListMeta {
+    int64_t base;
+    int64_t slot;
+    int32_t len;
+    int32_t np;
+};
+
+// Device allocation that frees itself.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    dade_status alloc(size_t b);          // exact size, contents undefined
+    dade_status ensure(size_t b);         // grow-only
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+} // namespace dade
+
+struct dade_index {
+    int64_t n = 0;
+    int32_t d = 0, dp = 0, nb = 0, nc = 0, max_list = 0;
+    // host copies (FP64 from the offline steps)
+    std::vector<double> mu, W, lam, Lam;    // Lam[d] = lambda_1 + ... + lambda_d, Lam[0] = 0
+    std::vector<double> rho;                // [(nb - 1) rows][eps_kept], each row sorted
+    int64_t eps_kept = 0;
+    std::vector<int32_t> assign;            // [n]
+    std::vector<dade::ListMeta> lists;      // [nc]
+    std::vector<double> kmeans_obj;
+    // device
+    dade::DevBuf W32;       // float [d][dp]: W^T applied as x' = sum_j (x_j - mu_j) W[j][k]
+    dade::DevBuf mu32;      // float [d]
+    dade::DevBuf cent;      // float [nc][dp] rotated centroids (zero padded)
+    dade::DevBuf data;      // packed rotated vectors
+    dade::DevBuf ids;       // int32 per slot (padding slots -1)
+    dade::DevBuf meta;      // ListMeta [nc]
+    dade::DevBuf errflag;   // int32 device error word (bounded waits)
+    int64_t data_floats = 0, slots = 0;
+    // workspace (grown on demand, reused across calls)
+    mutable dade::DevBuf ws_dist, ws_probe, ws_qrot, ws_qin, ws_ids, ws_dists;
+};
+
+namespace dade {
+
+// Kernel launchers (each returns DADE_OK or DADE_ECUDA after checking the launch).
+dade_status rotate(const float *x, int64_t n, int32_t d, int32_t out_stride, const float *W32,
+                   const float *mu32, int32_t dp, float *out, cudaStream_t s);
+dade_status probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t q_stride,
+                  int32_t nprobe, int32_t *probe_out, cudaStream_t s);
+
+struct ScanParams {
+    const float *q_rot;      // [nq][q_stride]
+    int32_t q_stride;
+    const int32_t *probe;    // [nq][nprobe]
+    int32_t nprobe, k, tile, mode, delta_d, n_inc;
+    float coef[DADE_MAX_DIM / DADE_BLOCK];   // per increment; prune iff P > coef[j] * r2
+    int64_t *ids;            // [nq][k]
+    float *dists;            // [nq][k]
+    int64_t *stats;          // [nq][4] or null
+};
+dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s);
+
+// Host FP64 symmetric eigensolver (descending eigenvalues, column eigenvectors).
+bool sym_eig(int n, std::vector<double> &a, std::vector<double> &w, std::vector<double> &v);
+
+// Pruning coefficients of one (alpha, delta_d); returns the number of increments.
+int coef_table(const dade_index *ix, float alpha, int32_t delta_d, double *eps, float *coef);
+
+} // namespace dade

@@ -1,0 +1,126 @@
+// probe.cu -- IVF coarse probe (Section 3.4): the nprobe inverted lists whose
+// centroids are nearest to each rotated query, ordered by (distance, list id).
+//
+// Step 1 writes the query x centroid squared-distance matrix with the
+// register-tiled kernel of tiles.cuh (exact sum of squared differences).
+// Step 2 selects, per query, the nprobe smallest 64-bit keys
+// (float bits of the distance << 32 | list id) by an 8-pass radix select over
+// 8-bit digits; keys are unique, so exactly nprobe keys are <= the selected
+// one, and a final rank sort orders them.  The result is deterministic.
+#include "internal.cuh"
+#include "tiles.cuh"
+
+namespace dade {
+
+namespace {
+
+__global__ void __launch_bounds__(L2T_THREADS) k_probe_dist(const float *__restrict__ Q, int64_t nq, int ldq, int kdim,
+                                                            const float *__restrict__ cent, int nc, int ldc,
+                                                            float *__restrict__ dist) {
+    __shared__ L2TileSmem sm;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t r0 = (int64_t)blockIdx.x * L2T_ROWS;
+    const int c0 = blockIdx.y * L2T_COLS;
+    float acc[4][4];
+    l2_tile(Q, nq, ldq, cent, nc, ldc, kdim, r0, c0, acc, sm);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t r = r0 + ty * 4 + i;
+        if (r >= nq) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int c = c0 + tx * 4 + j;
+            if (c < nc) dist[r * nc + c] = acc[i][j];
+        }
+    }
+}
+
+constexpr int SEL_THREADS = 256;
+
+__device__ __forceinline__ unsigned long long probe_key(const float *row, int j) {
+    return ((unsigned long long)__float_as_uint(row[j]) << 32) | (unsigned)j;
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_probe_select(const float *__restrict__ dist, int nc, int nprobe,
+                                                              int32_t *__restrict__ out) {
+    extern __shared__ unsigned long long sel[];        // [nprobe]
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long s_prefix;
+    __shared__ unsigned s_rank, s_cnt;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const float *row = dist + (int64_t)blockIdx.x * nc;
+    unsigned long long prefix = 0, mask = 0;
+    unsigned rank = (unsigned)nprobe;                  // 1-based rank sought among keys matching prefix
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 56 - 8 * pass;
+        hist[tid] = 0;
+        __syncthreads();
+        for (int j = tid; j < nc; j += SEL_THREADS) {
+            unsigned long long k = probe_key(row, j);
+            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {   // warp 0: find the digit where the cumulative count reaches rank
+            unsigned loc[8], s = 0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) { loc[t] = hist[lane * 8 + t]; s += loc[t]; }
+            unsigned inc = s;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                unsigned v = __shfl_up_sync(0xffffffffu, inc, off);
+                if (lane >= off) inc += v;
+            }
+            unsigned before = inc - s;
+            bool here = before < rank && inc >= rank;
+            if (here) {
+                unsigned c = before;
+                int t = 0;
+                while (c + loc[t] < rank) { c += loc[t]; ++t; }
+                s_prefix = prefix | ((unsigned long long)(lane * 8 + t) << shift);
+                s_rank = rank - c;
+            }
+        }
+        __syncthreads();
+        prefix = s_prefix;
+        rank = s_rank;
+        mask |= 255ull << shift;
+        __syncthreads();
+    }
+    // prefix is now the nprobe-th smallest key; gather the keys <= it
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    for (int j = tid; j < nc; j += SEL_THREADS) {
+        unsigned long long k = probe_key(row, j);
+        if (k <= prefix) {
+            const unsigned slot = atomicAdd(&s_cnt, 1u);
+            if (slot < (unsigned)nprobe) sel[slot] = k;   // exactly nprobe keys qualify (keys are unique)
+        }
+    }
+    __syncthreads();
+    const int nsel = min((int)s_cnt, nprobe);
+    for (int t = tid; t < nsel; t += SEL_THREADS) {
+        unsigned long long k = sel[t];
+        int r = 0;
+        for (int u = 0; u < nsel; ++u) r += sel[u] < k;
+        out[(int64_t)blockIdx.x * nprobe + r] = (int32_t)(k & 0xffffffffu);
+    }
+}
+
+} // namespace
+
+dade_status probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t q_stride, int32_t nprobe,
+                  int32_t *probe_out, cudaStream_t s) {
+    if (nq == 0) return DADE_OK;
+    DADE_TRY(ix->ws_dist.ensure(sizeof(float) * (size_t)nq * ix->nc));
+    dim3 g((unsigned)((nq + L2T_ROWS - 1) / L2T_ROWS), (unsigned)((ix->nc + L2T_COLS - 1) / L2T_COLS));
+    k_probe_dist<<<g, L2T_THREADS, 0, s>>>(q_rot, nq, q_stride, ix->d, ix->cent.as<float>(), ix->nc, ix->dp,
+                                           ix->ws_dist.as<float>());
+    DADE_TRY(launch_check("k_probe_dist"));
+    size_t smem = sizeof(unsigned long long) * (size_t)nprobe;
+    if (smem > 48 * 1024)
+        DADE_TRY_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_probe_select<<<(unsigned)nq, SEL_THREADS, smem, s>>>(ix->ws_dist.as<float>(), ix->nc, nprobe, probe_out);
+    return launch_check("k_probe_select");
+}
+
+} // namespace dade

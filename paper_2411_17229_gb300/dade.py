@@ -1,0 +1,208 @@
+"""ctypes binding of libdade (include/dade.h): argument marshalling only.
+
+Every function takes torch tensors (CUDA or CPU) or numpy arrays and passes
+raw pointers, sizes and the current CUDA stream to the C ABI; all arithmetic
+of the path runs in the library's CUDA kernels.  Loading fails loudly when
+the library is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdade.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EIO = range(7)
+MODE_DADE, MODE_FD = 0, 1
+FIELD_MEAN, FIELD_BASIS, FIELD_EIGVAL, FIELD_CENTROIDS, FIELD_ASSIGN, FIELD_ROTATED, FIELD_RHO, FIELD_KMEANS_OBJ = range(8)
+MAX_DIM, MAX_K = 1024, 256
+
+
+class DadeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libdade status {status}: {msg}")
+        self.status = status
+
+
+class BuildOpts(C.Structure):
+    _fields_ = [("n_clusters", C.c_int32), ("kmeans_iters", C.c_int32), ("seed", C.c_uint64),
+                ("eps_pairs", C.c_int64), ("assign", C.c_void_p), ("kmeans_init", C.c_void_p),
+                ("pairs", C.c_void_p), ("reserved", C.c_int32 * 8)]
+
+
+class SearchOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("tile", C.c_int32), ("stats", C.c_void_p), ("reserved", C.c_int32 * 8)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("d_pad", C.c_int32), ("n_clusters", C.c_int32),
+                ("max_list", C.c_int32), ("eps_kept", C.c_int64), ("device_bytes", C.c_int64),
+                ("data_bytes", C.c_int64), ("kmeans_iters", C.c_int32), ("reserved", C.c_int32)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/dade.h
+_vp, _i64, _i32, _f32 = C.c_void_p, C.c_int64, C.c_int32, C.c_float
+SIGNATURES = {
+    "dade_build_opts_default": (None, [_vp]),
+    "dade_build_index": (_i32, [_vp, _i64, _i32, _vp, _vp, _vp]),
+    "dade_free_index": (None, [_vp]),
+    "dade_rotate_queries": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "dade_probe": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
+    "dade_search": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
+    "dade_query": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
+    "dade_reserve": (_i32, [_vp, _i64, _i32]),
+    "dade_eps_table": (_i32, [_vp, _f32, _i32, _vp, _vp]),
+    "dade_index_info": (_i32, [_vp, _vp]),
+    "dade_index_export": (_i32, [_vp, _i32, _vp, C.c_size_t]),
+    "dade_host_sym_eig": (_i32, [_vp, _i32, _vp, _vp]),
+    "dade_sync": (_i32, [_vp, _vp]),
+    "dade_last_error": (C.c_char_p, []),
+    "dade_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libdade.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libdade.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise DadeError(status, lib().dade_last_error().decode())
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or numpy array (contiguous)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    assert x.is_contiguous()
+    return x.data_ptr()
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return stream
+    import torch
+    if torch.cuda.is_available():
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+class Index:
+    """A libdade index resident in device memory."""
+
+    def __init__(self, base, n_clusters: int, kmeans_iters: int = 10, seed: int = 0, eps_pairs: int = 100000,
+                 assign=None, kmeans_init=None, pairs=None, stream=None):
+        L = lib()
+        o = BuildOpts()
+        L.dade_build_opts_default(C.byref(o))
+        o.n_clusters, o.kmeans_iters, o.seed, o.eps_pairs = int(n_clusters), int(kmeans_iters), int(seed), int(eps_pairs)
+        keep = []
+        if assign is not None:
+            a = np.ascontiguousarray(assign, np.int32)
+            keep.append(a)
+            o.assign = a.ctypes.data
+        if kmeans_init is not None:
+            a = np.ascontiguousarray(kmeans_init, np.int64)
+            keep.append(a)
+            o.kmeans_init = a.ctypes.data
+        if pairs is not None:
+            a = np.ascontiguousarray(pairs, np.int64).reshape(-1)
+            keep.append(a)
+            o.pairs = a.ctypes.data
+            o.eps_pairs = a.size // 2
+        n, d = base.shape
+        h = C.c_void_p()
+        _check(L.dade_build_index(_ptr(base), n, d, C.byref(o), C.byref(h), _stream(stream)))
+        self._h = h
+        info = Info()
+        _check(L.dade_index_info(h, C.byref(info)))
+        self.info = info
+        self.n, self.d, self.n_clusters = info.n, info.d, info.n_clusters
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dade_free_index(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- query path ---------------------------------------------------------
+    def rotate(self, q, out, stream=None):
+        _check(lib().dade_rotate_queries(self._h, _ptr(q), q.shape[0], _ptr(out), _stream(stream)))
+        return out
+
+    def probe(self, q_rot, nprobe, out, stream=None):
+        _check(lib().dade_probe(self._h, _ptr(q_rot), q_rot.shape[0], int(nprobe), _ptr(out), _stream(stream)))
+        return out
+
+    def search(self, q_rot, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, stream=None):
+        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats))
+        _check(lib().dade_search(self._h, _ptr(q_rot), q_rot.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
+                                 C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
+        return ids, dists
+
+    def query(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, stream=None):
+        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats))
+        _check(lib().dade_query(self._h, _ptr(q), q.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
+                                C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
+        return ids, dists
+
+    def reserve(self, max_nq, max_nprobe):
+        _check(lib().dade_reserve(self._h, int(max_nq), int(max_nprobe)))
+
+    def sync(self, stream=None):
+        _check(lib().dade_sync(self._h, _stream(stream)))
+
+    # -- inspection -----------------------------------------------------------
+    def eps_table(self, alpha, delta_d):
+        eps = np.empty(self.d + 1)
+        coef = np.empty(self.d + 1, np.float32)
+        _check(lib().dade_eps_table(self._h, float(alpha), int(delta_d), eps.ctypes.data, coef.ctypes.data))
+        return eps, coef
+
+    def export(self, field):
+        d, n, nc = self.d, self.n, self.n_clusters
+        shapes = {FIELD_MEAN: ((d,), np.float64), FIELD_BASIS: ((d, d), np.float64), FIELD_EIGVAL: ((d,), np.float64),
+                  FIELD_CENTROIDS: ((nc, d), np.float32), FIELD_ASSIGN: ((n,), np.int32),
+                  FIELD_ROTATED: ((n, d), np.float32),
+                  FIELD_RHO: ((max(0, self.info.d_pad // 16 - 1), self.info.eps_kept), np.float64)}
+        shapes[FIELD_KMEANS_OBJ] = ((self.info.kmeans_iters,), np.float64)
+        shape, dt = shapes[field]
+        out = np.empty(shape, dt)
+        _check(lib().dade_index_export(self._h, field, out.ctypes.data, out.nbytes))
+        return out
+
+
+def host_sym_eig(a):
+    a = np.array(a, np.float64, order="C")
+    n = a.shape[0]
+    w, v = np.empty(n), np.empty((n, n))
+    _check(lib().dade_host_sym_eig(a.ctypes.data, n, w.ctypes.data, v.ctypes.data))
+    return w, v

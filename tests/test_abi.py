@@ -1,0 +1,90 @@
+"""The C-ABI library on the CPU: it builds, loads, exports every symbol that
+include/dade.h declares, rejects invalid arguments before any GPU work, and
+its host-side FP64 eigensolver (the PCA step of Section 3.2, Eq. 11) is
+correct.  No GPU compute is called here."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2411_17229_gb300 import build as libbuild
+from paper_2411_17229_gb300 import dade
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    libbuild.build()
+    return dade.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "dade.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dade_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    names = declared_functions()
+    assert len(names) >= 15
+    assert set(names) == set(dade.SIGNATURES), set(names) ^ set(dade.SIGNATURES)
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    assert b"sm_103a" in L.dade_version()
+
+
+def test_struct_layouts_match_header(L):
+    assert C.sizeof(dade.BuildOpts) == 4 + 4 + 8 + 8 + 8 * 3 + 4 * 8
+    assert C.sizeof(dade.SearchOpts) == 4 + 4 + 8 + 4 * 8
+    assert C.sizeof(dade.Info) == 8 + 4 * 4 + 8 * 3 + 8
+
+
+def test_invalid_arguments_rejected_without_gpu(L):
+    o = dade.BuildOpts()
+    L.dade_build_opts_default(C.byref(o))
+    assert o.kmeans_iters == 10 and o.eps_pairs == 100000
+    h = C.c_void_p()
+    x = np.zeros((4, 8), np.float32)
+    assert L.dade_build_index(x.ctypes.data, 1, 8, C.byref(o), C.byref(h), None) == dade.EINVAL
+    assert b"n < 2" in L.dade_last_error()
+    assert L.dade_build_index(x.ctypes.data, 4, 0, C.byref(o), C.byref(h), None) == dade.EINVAL
+    assert L.dade_build_index(x.ctypes.data, 4, 2048, C.byref(o), C.byref(h), None) == dade.EINVAL
+    o.n_clusters = 5
+    assert L.dade_build_index(x.ctypes.data, 4, 8, C.byref(o), C.byref(h), None) == dade.EINVAL
+    assert L.dade_build_index(None, 4, 8, C.byref(o), C.byref(h), None) == dade.EINVAL
+    ids = np.zeros(10, np.int64)
+    dists = np.zeros(10, np.float32)
+    assert L.dade_search(None, x.ctypes.data, 1, 10, 1, 0.1, 32, None, ids.ctypes.data, dists.ctypes.data,
+                         None) == dade.EINVAL
+    assert L.dade_sync(None, None) == dade.EINVAL
+    assert L.dade_free_index(None) is None
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 16, 64, 129])
+def test_host_eigensolver_vs_lapack(L, n):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    A = A + A.T
+    w, v = dade.host_sym_eig(A)
+    ref = np.sort(np.linalg.eigvalsh(A))[::-1]
+    assert np.allclose(w, ref, atol=1e-12 * max(1.0, np.abs(ref).max()))
+    assert np.all(np.diff(w) <= 0)
+    assert np.allclose(v.T @ v, np.eye(n), atol=1e-12)
+    assert np.allclose(A @ v, v * w[None, :], atol=1e-11 * max(1.0, np.abs(ref).max()))
+
+
+def test_host_eigensolver_degenerate_and_diagonal(L):
+    A = np.diag([3.0, 1.0, 3.0, 2.0, 0.0])
+    w, v = dade.host_sym_eig(A)
+    assert np.allclose(w, [3, 3, 2, 1, 0])
+    assert np.allclose(A @ v, v * w[None, :], atol=1e-14)
+    B = np.ones((6, 6))
+    w, v = dade.host_sym_eig(B)
+    assert np.allclose(w, [6, 0, 0, 0, 0, 0], atol=1e-12)
+    assert np.allclose(B @ v, v * w[None, :], atol=1e-12)

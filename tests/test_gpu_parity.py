@@ -1,0 +1,244 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (GPU only).
+
+Each test builds the same seeded inputs for both sides; the oracle never sees
+anything the CUDA path produced.  Inverted lists are fixed by a seeded input
+assignment (uneven random lists, or mixture labels), so both sides scan the
+same lists; k-means itself is compared separately (test_kmeans_parity).
+Tolerances are those of tests/parity.py.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import parity
+from paper_2411_17229_gb300 import dade, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_17229_gb300 import build
+    build.build()
+    dade.lib()
+
+
+class Case:
+    """A workload built on both sides with the same lists and eps pairs."""
+
+    def __init__(self, base, queries, assign, n_clusters, n_pairs=20000, seed=4):
+        self.base, self.queries = base, queries
+        self.assign = np.ascontiguousarray(assign, np.int32)
+        self.nc = n_clusters
+        self.pairs = synth.eps_pairs(base.shape[0], n_pairs, seed=seed)
+        self.orc = oracle.Index(base, n_clusters=n_clusters, assign=self.assign, pairs=self.pairs)
+        self.gpu = dade.Index(torch.from_numpy(base).cuda(), n_clusters, assign=self.assign, pairs=self.pairs)
+        self.q_dev = torch.from_numpy(queries).cuda()
+        self.q_rot = torch.empty_like(self.q_dev)
+        self.gpu.rotate(self.q_dev, self.q_rot)
+        self.Qr = self.orc.rotate(queries)
+        self.scale = float(np.mean((self.orc.Xr ** 2).sum(1)))
+
+    def gpu_search(self, k, nprobe, alpha, delta_d, mode=dade.MODE_DADE, tile=128, stats=False):
+        nq = self.queries.shape[0]
+        ids = torch.empty(nq, k, dtype=torch.int64, device="cuda")
+        d = torch.empty(nq, k, dtype=torch.float32, device="cuda")
+        st = torch.zeros(nq, 4, dtype=torch.int64, device="cuda") if stats else None
+        self.gpu.search(self.q_rot, k, nprobe, alpha, delta_d, ids, d, mode=mode, tile=tile, stats=st)
+        self.gpu.sync()
+        out = ids.cpu().numpy(), d.cpu().numpy()
+        return out + ((st.cpu().numpy(),) if stats else ())
+
+    def oracle_search(self, k, nprobe, alpha, delta_d, fd=False, tile=128):
+        eps = None if fd else self.orc.eps(np.float32(alpha), delta_d)
+        return self.orc.o.search(self.orc.Xr, self.assign, self.orc.cent, self.orc.lam, self.Qr, k, nprobe,
+                                 delta_d if not fd else 64, eps, schedule=oracle.TILE, tile=tile)
+
+    def exact_d(self, q, ids):
+        return ((self.orc.Xr[ids] - self.Qr[q]) ** 2).sum(1)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    """10,000 x 128 Gaussian, lambda_i ~ i^-1.2, 100 queries, 64 uneven lists."""
+    base, queries, _ = synth.make("c1_gauss_10k_d128")
+    assign = synth.zipf_assign(base.shape[0], 64, s=0.6)
+    return Case(base, queries, assign, 64)
+
+
+@pytest.fixture(scope="module")
+def mix():
+    """20,000 x 64 mixture of 24 anisotropic Gaussians, lists = components."""
+    w = synth.Workload("mix_test", 20000, 64, 120, 1.0, 24, 0.0, 3.0, 1.0, False, False, 24, (4,), 10, (16,), 0.1)
+    base, queries, labels = synth.make(w)
+    return Case(base, queries, labels, 24)
+
+
+def test_pca_parity(c1):
+    g, o = c1.gpu, c1.orc
+    assert np.allclose(g.export(dade.FIELD_MEAN), o.mu, rtol=0, atol=1e-12 * np.abs(o.mu).max() + 1e-15)
+    lam = g.export(dade.FIELD_EIGVAL)
+    assert np.max(np.abs(lam - o.lam) / o.lam[0]) < 1e-9
+    W = g.export(dade.FIELD_BASIS)
+    M = W.T @ o.W
+    assert np.allclose(np.abs(np.diag(M)), 1.0, atol=1e-6)   # same eigenvectors up to sign
+
+
+def test_rotation_parity(c1):
+    Xg = c1.gpu.export(dade.FIELD_ROTATED).astype(np.float64)
+    scale = np.sqrt(c1.scale)
+    assert np.abs(Xg - c1.orc.Xr).max() < 2e-6 * scale
+    Qg = c1.q_rot.cpu().numpy().astype(np.float64)
+    assert np.abs(Qg - c1.Qr).max() < 2e-6 * scale
+    # host buffers in, host buffers out give the same bits
+    qh = np.empty_like(c1.queries)
+    c1.gpu.rotate(c1.queries, qh)
+    assert np.array_equal(qh, c1.q_rot.cpu().numpy())
+
+
+def test_assignment_and_centroids(c1):
+    assert np.array_equal(c1.gpu.export(dade.FIELD_ASSIGN), c1.assign)
+    cg = c1.gpu.export(dade.FIELD_CENTROIDS).astype(np.float64)
+    assert np.abs(cg - c1.orc.cent).max() < 2e-6 * np.sqrt(c1.scale)
+
+
+def test_eps_parity(c1):
+    rho_g = c1.gpu.export(dade.FIELD_RHO)
+    dl = c1.orc.dlist
+    assert rho_g.shape == (len(dl), c1.orc.rho.shape[1])
+    assert np.abs(rho_g - c1.orc.rho).max() < 1e-5
+    for alpha in (0.05, 0.1, 0.3):
+        for dd in (16, 32, 64):
+            eg, cg = c1.gpu.eps_table(alpha, dd)
+            eo = c1.orc.eps(np.float32(alpha), dd)
+            for d in oracle.increments(128, dd):
+                assert abs(eg[d] - eo[d]) < 2e-5, (alpha, dd, d)
+                lam = c1.orc.lam
+                coef = (1 + eo[d]) ** 2 * lam[:d].sum() / lam.sum()
+                assert abs(cg[d] - coef) < 1e-4 * coef
+
+
+@pytest.mark.parametrize("nprobe", [1, 8, 64])
+def test_probe_parity(c1, mix, nprobe):
+    for case in (c1, mix):
+        if nprobe > case.nc:
+            continue
+        pg = np.empty((case.queries.shape[0], nprobe), np.int32)
+        pg_dev = torch.empty(case.queries.shape[0], nprobe, dtype=torch.int32, device="cuda")
+        case.gpu.probe(case.q_rot, nprobe, pg_dev)
+        case.gpu.sync()
+        pg = pg_dev.cpu().numpy()
+        po, tie = case.orc.o.probe(case.Qr, case.orc.cent, nprobe)
+        ok = np.all(pg == po, axis=1)
+        assert np.all(ok | (tie != 0)), np.nonzero(~ok & (tie == 0))
+
+
+@pytest.mark.parametrize("k,nprobe,alpha,delta_d,tile", [
+    (10, 8, 0.05, 32, 128),      # the 10k x 128 configuration
+    (10, 8, 0.1, 16, 128),
+    (10, 8, 0.3, 64, 64),
+    (1, 4, 0.05, 32, 32),
+    (100, 16, 0.05, 32, 256),
+    (256, 8, 0.2, 32, 96),
+])
+def test_search_parity_c1(c1, k, nprobe, alpha, delta_d, tile):
+    g_ids, g_d, g_st = c1.gpu_search(k, nprobe, alpha, delta_d, tile=tile, stats=True)
+    o_ids, o_d, o_st, flags = c1.oracle_search(k, nprobe, alpha, delta_d, tile=tile)
+    parity.compare(g_ids, g_d, o_ids, o_d, flags, c1.scale, c1.exact_d)
+    # the work done is the same: candidates exactly, the rest where no near-tie occurred
+    assert np.array_equal(g_st[:, 0], o_st[:, 0])
+    clean = flags == 0
+    assert np.array_equal(g_st[clean, 1:], o_st[clean, 1:])
+    assert np.all(g_st[:, 1] < g_st[:, 0] * 128)   # DADE used fewer dimensions than FDScanning
+
+
+@pytest.mark.parametrize("k,nprobe,alpha,delta_d", [(10, 4, 0.1, 16), (10, 2, 0.05, 32), (50, 6, 0.2, 64)])
+def test_search_parity_mixture(mix, k, nprobe, alpha, delta_d):
+    g_ids, g_d = mix.gpu_search(k, nprobe, alpha, delta_d)
+    o_ids, o_d, _, flags = mix.oracle_search(k, nprobe, alpha, delta_d)
+    parity.compare(g_ids, g_d, o_ids, o_d, flags, mix.scale, mix.exact_d)
+
+
+@pytest.mark.parametrize("k,nprobe", [(10, 8), (100, 16)])
+def test_fd_parity(c1, k, nprobe):
+    g_ids, g_d, g_st = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD, stats=True)
+    o_ids, o_d, o_st, flags = c1.oracle_search(k, nprobe, 0.1, 32, fd=True)
+    parity.compare(g_ids, g_d, o_ids, o_d, flags, c1.scale, c1.exact_d)
+    assert np.array_equal(g_st[:, 0], o_st[:, 0])
+    assert np.all(g_st[:, 1] == g_st[:, 0] * 128)
+
+
+def test_host_buffers_match_device(c1):
+    k, nprobe = 10, 8
+    d_ids, d_d = c1.gpu_search(k, nprobe, 0.05, 32)
+    ids = np.empty((c1.queries.shape[0], k), np.int64)
+    dist = np.empty((c1.queries.shape[0], k), np.float32)
+    c1.gpu.query(c1.queries, k, nprobe, 0.05, 32, ids, dist)
+    assert np.array_equal(ids, d_ids) and np.array_equal(dist, d_d)
+
+
+def test_exhaustive_fd_is_exact_knn():
+    """nprobe = N_c with FDScanning is exact KNN (oracle brute force in the
+    original space), including ties between duplicated vectors."""
+    base, queries, _ = synth.make("c1_gauss_10k_d128", n=3000, nq=40)
+    base[7] = base[1500]
+    queries[5] = base[1500]
+    assign = synth.zipf_assign(3000, 10, s=1.1)
+    g = dade.Index(torch.from_numpy(base).cuda(), 10, assign=assign, eps_pairs=2000)
+    ids = torch.empty(40, 20, dtype=torch.int64, device="cuda")
+    d = torch.empty(40, 20, dtype=torch.float32, device="cuda")
+    g.query(torch.from_numpy(queries).cuda(), 20, 10, 0.1, 32, ids, d, mode=dade.MODE_FD)
+    g.sync()
+    o_ids, o_d = oracle.get().exact_knn(base, queries, 20)
+    gi = ids.cpu().numpy()
+    for q in range(40):
+        for a, b in parity._runs(o_d[q]):
+            assert set(gi[q, a:b]) == set(o_ids[q, a:b]), q
+    assert gi[5, 0] == 7 and gi[5, 1] == 1500   # equal distance 0: lower id first
+
+
+@pytest.mark.parametrize("d,nlists,delta_d", [(16, 3, 16), (20, 5, 16), (40, 4, 32), (48, 6, 32), (64, 2, 64),
+                                              (33, 7, 1024)])
+def test_odd_shapes(d, nlists, delta_d):
+    """D not a multiple of 16 or of delta_d, delta_d >= D, empty lists, K > candidates."""
+    rng = np.random.default_rng(d)
+    base = (rng.standard_normal((700, d)) * np.linspace(2.0, 0.2, d)).astype(np.float32)
+    queries = (rng.standard_normal((25, d)) * np.linspace(2.0, 0.2, d)).astype(np.float32)
+    assign = synth.zipf_assign(700, nlists, s=1.5)
+    assign[assign == nlists - 1] = 0          # one empty list
+    case = Case(base, queries, assign, nlists, n_pairs=3000)
+    for k, nprobe in ((5, 1), (200, 2), (10, nlists)):
+        g_ids, g_d = case.gpu_search(k, nprobe, 0.1, delta_d, tile=32)
+        o_ids, o_d, _, flags = case.oracle_search(k, nprobe, 0.1, delta_d, tile=32)
+        parity.compare(g_ids, g_d, o_ids, o_d, flags, case.scale, case.exact_d)
+
+
+def test_empty_batch_and_invalid(c1):
+    ids = torch.empty(0, 10, dtype=torch.int64, device="cuda")
+    d = torch.empty(0, 10, dtype=torch.float32, device="cuda")
+    c1.gpu.search(c1.q_rot[:0], 10, 8, 0.05, 32, ids, d)
+    with pytest.raises(dade.DadeError) as e:
+        c1.gpu.search(c1.q_rot, 10, 65, 0.05, 32, torch.empty(100, 10, dtype=torch.int64, device="cuda"),
+                      torch.empty(100, 10, device="cuda"))
+    assert e.value.status == dade.EINVAL
+    with pytest.raises(dade.DadeError):
+        c1.gpu.search(c1.q_rot, 10, 8, 0.05, 24, ids, d)
+    with pytest.raises(dade.DadeError):
+        c1.gpu.search(c1.q_rot, 10, 8, 1.5, 32, ids, d)
+
+
+def test_kmeans_parity():
+    """GPU k-means (FP32 distances, FP64 sums) vs the oracle's FP64 Lloyd
+    iterations from the same initial ids: per-iteration objectives agree to
+    1e-5 and the final lists agree on almost every vector."""
+    base, _, _ = synth.make("c1_gauss_10k_d128", n=6000, nq=1)
+    init = synth.kmeans_init(6000, 32, seed=3)
+    g = dade.Index(torch.from_numpy(base).cuda(), 32, kmeans_iters=6, kmeans_init=init, eps_pairs=1000)
+    o = oracle.Index(base, init=init, iters=6, pairs=synth.eps_pairs(6000, 1000))
+    obj_g = g.export(dade.FIELD_KMEANS_OBJ)
+    assert np.allclose(obj_g, o.kmeans_obj, rtol=1e-5)
+    agree = np.mean(g.export(dade.FIELD_ASSIGN) == o.assign)
+    assert agree > 0.995, agree
