@@ -89,7 +89,10 @@ typedef struct {
     int32_t tile;              /* candidates per threshold refresh (default 128; 32..256, multiple of 32) */
     int64_t *stats;            /* device, optional [nq * 4]: per query candidates scanned, sum of
                                   dimensions used, candidates accepted by the DCO, candidates pruned */
-    int32_t reserved[8];
+    int32_t stage;             /* increments per tile streamed whole into shared memory (default 1);
+                                  later increments fetch only the surviving candidates' rows */
+    int32_t threads;           /* threads per query's CTA: 0 (default 128), 128 or 256 */
+    int32_t reserved[6];
 } dade_search_opts;
 
 /* Description of a built index. */
@@ -171,6 +174,16 @@ dade_status dade_probe(const dade_index *ix, const float *q_rot, int64_t nq, int
 dade_status dade_search(const dade_index *ix, const float *q_rot, int64_t nq, int32_t k,
                         int32_t nprobe, float alpha, int32_t delta_d, const dade_search_opts *opts,
                         int64_t *ids, float *dists, dade_stream stream);
+
+/*
+ * The scan step alone: DADE (or FDScanning) over given probe lists, e.g. the
+ * output of dade_probe or of another candidate generator.  probe: host or
+ * device [nq * nprobe] int32 list ids, each in 0..n_clusters-1, scanned in
+ * the order given.  Other arguments, limits and outputs as dade_search.
+ */
+dade_status dade_scan(const dade_index *ix, const float *q_rot, const int32_t *probe, int64_t nq, int32_t k,
+                      int32_t nprobe, float alpha, int32_t delta_d, const dade_search_opts *opts, int64_t *ids,
+                      float *dists, dade_stream stream);
 
 /*
  * End-to-end query: dade_rotate_queries followed by dade_search, on raw

@@ -27,7 +27,7 @@ TIE_TOL = 1e-5
 def build(src: str = SRC, out: str = LIB, extra: tuple = ()) -> str:
     """Compile the oracle with gcc (OpenMP across independent outputs only)."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
-    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", *extra, "-o", out, src, "-lm"]
+    cmd = ["gcc", "-O3", "-fopenmp", "-fPIC", "-shared", "-std=c11", *extra, "-o", out, src, "-lm"]
     subprocess.run(cmd, check=True)
     return out
 

@@ -182,20 +182,64 @@ static double sqdist(const double *a, const double *b, int d)
 /* IVF (Section 3.4): k-means centroids, inverted lists, probing.            */
 /* ------------------------------------------------------------------------ */
 
-/* Nearest centroid of x; ties go to the lower centroid index.  *gap gets the
- * relative gap between the best and second-best squared distances. */
-static int nearest(const double *x, const double *cent, int nc, int d, double *best_out, double *gap)
+/* Argmin of one row of squared distances; ties go to the lower centroid
+ * index.  *gap gets the relative gap between the best and second best. */
+static int argmin_row(const double *row, int nc, double *gap)
 {
     int best = 0;
     double b1 = INFINITY, b2 = INFINITY;
     for (int c = 0; c < nc; ++c) {
-        double t = sqdist(x, cent + (int64_t)c * d, d);
+        double t = row[c];
         if (t < b1) { b2 = b1; b1 = t; best = c; }
         else if (t < b2) b2 = t;
     }
-    if (best_out) *best_out = b1;
     if (gap) *gap = (b2 - b1) / (b1 > 0.0 ? b1 : 1.0);
     return best;
+}
+
+/* Squared distances from points X[0..np) to every centroid.  Each distance
+ * is the sum over k of (x_k - c_k)^2 in index order; the loops run over the
+ * centroids innermost (centroids stored transposed, CT[k * nc + c]) so that
+ * many independent sums advance together. */
+#define OR_PB 8
+static void block_dists(const double *X, int np, int d, const double *CT, int nc, double *acc)
+{
+    for (int64_t t = 0; t < (int64_t)np * nc; ++t) acc[t] = 0.0;
+    for (int k = 0; k < d; ++k) {
+        const double *ct = CT + (int64_t)k * nc;
+        for (int b = 0; b < np; ++b) {
+            const double xk = X[(int64_t)b * d + k];
+            double *a = acc + (int64_t)b * nc;
+            for (int c = 0; c < nc; ++c) { double t = xk - ct[c]; a[c] += t * t; }
+        }
+    }
+}
+
+/* assign[i] = nearest centroid of every point (ties to the lower index);
+ * returns the smallest relative best/second-best gap. */
+static double assign_all(const double *Xr, int64_t n, int d, const double *cent, int nc, int32_t *assign)
+{
+    double *CT = (double *)malloc(sizeof(double) * (size_t)nc * d);
+    for (int c = 0; c < nc; ++c)
+        for (int k = 0; k < d; ++k) CT[(int64_t)k * nc + c] = cent[(int64_t)c * d + k];
+    double g = INFINITY;
+    #pragma omp parallel reduction(min:g)
+    {
+        double *acc = (double *)malloc(sizeof(double) * (size_t)OR_PB * nc);
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t i0 = 0; i0 < n; i0 += OR_PB) {
+            int np = (int)(n - i0 < OR_PB ? n - i0 : OR_PB);
+            block_dists(Xr + i0 * d, np, d, CT, nc, acc);
+            for (int b = 0; b < np; ++b) {
+                double gi;
+                assign[i0 + b] = argmin_row(acc + (int64_t)b * nc, nc, &gi);
+                if (gi < g) g = gi;
+            }
+        }
+        free(acc);
+    }
+    free(CT);
+    return g;
 }
 
 /*
@@ -215,13 +259,8 @@ OR_API void or_kmeans(const double *Xr, int64_t n, int d, int nc, const int64_t 
     int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)nc);
     double gmin = INFINITY;
     for (int it = 0; it < iters; ++it) {
-        double o = 0.0, g = INFINITY;
-        #pragma omp parallel for schedule(static) reduction(min:g)
-        for (int64_t i = 0; i < n; ++i) {
-            double gi;
-            assign[i] = nearest(Xr + i * d, cent, nc, d, NULL, &gi);
-            if (gi < g) g = gi;
-        }
+        double o = 0.0;
+        double g = assign_all(Xr, n, d, cent, nc, assign);
         for (int64_t i = 0; i < n; ++i) o += sqdist(Xr + i * d, cent + (int64_t)assign[i] * d, d);
         if (obj) obj[it] = o;
         if (g < gmin) gmin = g;
@@ -245,14 +284,7 @@ OR_API void or_kmeans(const double *Xr, int64_t n, int d, int nc, const int64_t 
  * index).  Returns the smallest relative best/second-best gap. */
 OR_API double or_assign(const double *Xr, int64_t n, int d, const double *cent, int nc, int32_t *assign)
 {
-    double g = INFINITY;
-    #pragma omp parallel for schedule(static) reduction(min:g)
-    for (int64_t i = 0; i < n; ++i) {
-        double gi;
-        assign[i] = nearest(Xr + i * d, cent, nc, d, NULL, &gi);
-        if (gi < g) g = gi;
-    }
-    return g;
+    return assign_all(Xr, n, d, cent, nc, assign);
 }
 
 /* Centroid of every list = mean of its members; an empty list gets zeros. */

@@ -111,6 +111,9 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
     }
     const int tile = opts && opts->tile ? opts->tile : 128;
     DADE_CHECK_ARG(tile >= 32 && tile <= 256 && tile % 32 == 0, "tile must be a multiple of 32 in [32, 256]");
+    DADE_CHECK_ARG(!opts || (opts->stage >= 0 && opts->stage <= 64), "stage outside 0..64");
+    DADE_CHECK_ARG(!opts || opts->threads == 0 || opts->threads == 128 || opts->threads == 256,
+                   "threads must be 0 (default), 128 or 256");
     return DADE_OK;
 }
 
@@ -122,8 +125,20 @@ struct Staged {
     bool ids_host = false, dists_host = false;
 };
 
+dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *probe_dev, int64_t nq, int32_t k,
+                     int32_t nprobe, float alpha, int32_t delta_d, const dade_search_opts *opts, int64_t *ids,
+                     float *dists, cudaStream_t s);
+
 dade_status run_search(const dade_index *ix, const float *q_dev, int64_t nq, int32_t k, int32_t nprobe, float alpha,
                        int32_t delta_d, const dade_search_opts *opts, int64_t *ids, float *dists, cudaStream_t s) {
+    DADE_TRY(ix->ws_probe.ensure(sizeof(int32_t) * (size_t)nq * nprobe));
+    DADE_TRY(dade::probe(ix, q_dev, nq, ix->d, nprobe, ix->ws_probe.as<int32_t>(), s));
+    return run_scan(ix, q_dev, ix->ws_probe.as<int32_t>(), nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
+}
+
+dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *probe_dev, int64_t nq, int32_t k,
+                     int32_t nprobe, float alpha, int32_t delta_d, const dade_search_opts *opts, int64_t *ids,
+                     float *dists, cudaStream_t s) {
     const bool ids_host = !is_device_ptr(ids), dists_host = !is_device_ptr(dists);
     int64_t *ids_d = ids;
     float *dists_d = dists;
@@ -135,16 +150,16 @@ dade_status run_search(const dade_index *ix, const float *q_dev, int64_t nq, int
         DADE_TRY(ix->ws_dists.ensure(sizeof(float) * (size_t)nq * k));
         dists_d = ix->ws_dists.as<float>();
     }
-    DADE_TRY(ix->ws_probe.ensure(sizeof(int32_t) * (size_t)nq * nprobe));
-    DADE_TRY(dade::probe(ix, q_dev, nq, ix->d, nprobe, ix->ws_probe.as<int32_t>(), s));
     ScanParams p{};
     p.q_rot = q_dev;
     p.q_stride = ix->d;
-    p.probe = ix->ws_probe.as<int32_t>();
+    p.probe = probe_dev;
     p.nprobe = nprobe;
     p.k = k;
     p.tile = opts && opts->tile ? opts->tile : 128;
     p.mode = opts ? opts->mode : DADE_MODE_DADE;
+    p.stage = opts && opts->stage > 0 ? opts->stage : 1;
+    p.threads = opts && opts->threads ? opts->threads : 128;
     p.delta_d = delta_d;
     if (p.mode == DADE_MODE_DADE) p.n_inc = coef_table(ix, alpha, delta_d, nullptr, p.coef);
     else p.n_inc = 0;
@@ -281,6 +296,29 @@ dade_status dade_search(const dade_index *ix, const float *q_rot, int64_t nq, in
     const float *qd = stage_in(ix, q_rot, (size_t)nq * ix->d, ix->ws_qrot, s, &st);
     if (!qd) return st;
     return run_search(ix, qd, nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
+}
+
+dade_status dade_scan(const dade_index *ix, const float *q_rot, const int32_t *probe, int64_t nq, int32_t k,
+                      int32_t nprobe, float alpha, int32_t delta_d, const dade_search_opts *opts, int64_t *ids,
+                      float *dists, dade_stream stream) {
+    g_err.clear();
+    DADE_TRY(validate_search(ix, nq, k, nprobe, alpha, delta_d, opts));
+    if (nq == 0) return DADE_OK;
+    DADE_CHECK_ARG(q_rot != nullptr && probe != nullptr && ids != nullptr && dists != nullptr, "NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    dade_status st;
+    const float *qd = stage_in(ix, q_rot, (size_t)nq * ix->d, ix->ws_qrot, s, &st);
+    if (!qd) return st;
+    const int32_t *pd = probe;
+    if (!is_device_ptr(probe)) {
+        for (int64_t t = 0; t < nq * (int64_t)nprobe; ++t)
+            DADE_CHECK_ARG(probe[t] >= 0 && probe[t] < ix->nc, "probe[] holds a list id outside 0..n_clusters-1");
+        DADE_TRY(ix->ws_probe.ensure(sizeof(int32_t) * (size_t)nq * nprobe));
+        DADE_TRY_CUDA(cudaMemcpyAsync(ix->ws_probe.p, probe, sizeof(int32_t) * (size_t)nq * nprobe,
+                                      cudaMemcpyHostToDevice, s));
+        pd = ix->ws_probe.as<int32_t>();
+    }
+    return run_scan(ix, qd, pd, nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
 }
 
 dade_status dade_query(const dade_index *ix, const float *q, int64_t nq, int32_t k, int32_t nprobe, float alpha,

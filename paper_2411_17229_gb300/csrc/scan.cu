@@ -33,9 +33,8 @@ namespace dade {
 
 namespace {
 
-constexpr int NT = 256;            // threads per CTA
-constexpr int NQUAD = NT / 4;      // candidates per pass
-constexpr int MAXIT = 4;           // tile <= 256 = MAXIT * NQUAD
+constexpr int MAX_TILE = 256;
+constexpr int GCHUNK = 4;          // survivors per lane whose loads are issued together
 constexpr uint64_t WAIT_NS = 2000000000ull;
 
 struct Surv {
@@ -53,7 +52,7 @@ struct ScanArgs {
     float *out_d;
     int64_t *stats;
     int *err;
-    int q_stride, nprobe, d, dp, nb, k, tile, gb, n_inc, ns, delta_d;
+    int q_stride, nprobe, d, dp, nb, k, tile, gb, n_inc, ns, delta_d, stage;
     float coef[DADE_MAX_DIM / DADE_BLOCK];
 };
 
@@ -110,38 +109,53 @@ __device__ __forceinline__ void push(bool want, Surv *list, int *cnt, int idx, f
     if (want) list[base + __popc(m & ((1u << lane) - 1u))] = Surv{idx, p};
 }
 
+// Per-probe list descriptor kept in shared memory: x = base / 64 (the data
+// offset in 256-byte units), y = first id slot, z = length, w = padded length.
+constexpr int PMETA = 1024;   // probes whose descriptors are preloaded
+
+__device__ __forceinline__ int4 meta_of(const ScanArgs &a, const int4 *sm, const int32_t *plist, int p) {
+    if (p < PMETA) return sm[p];
+    const ListMeta m = a.meta[plist[p]];
+    return make_int4((int)(m.base >> 6), (int)m.slot, m.len, m.np);
+}
+
 // Tile cursor: probe position p, first candidate i0, increment j.
 struct Cur {
     int p, i0, j;
 };
 
-__device__ __forceinline__ void normalize(Cur &c, const ScanArgs &a, const int32_t *plist) {
-    while (c.p < a.nprobe && c.i0 >= a.meta[plist[c.p]].len) {
+__device__ __forceinline__ void normalize(Cur &c, const ScanArgs &a, const int4 *sm, const int32_t *plist) {
+    while (c.p < a.nprobe && c.i0 >= meta_of(a, sm, plist, c.p).z) {
         ++c.p;
         c.i0 = 0;
         c.j = 0;
     }
 }
 
-template <bool FD>
-__device__ __forceinline__ void advance(Cur &c, const ScanArgs &a, const int32_t *plist) {
-    if (FD && ++c.j < a.n_inc) return;
+// Advance over units: `units` staged increments per tile.
+__device__ __forceinline__ void advance(Cur &c, int units, const ScanArgs &a, const int4 *sm, const int32_t *plist) {
+    if (++c.j < units) return;
     c.j = 0;
     c.i0 += a.tile;
-    normalize(c, a, plist);
+    normalize(c, a, sm, plist);
 }
 
-// Queue the bulk copies of one unit (a tile's increment c.j) into `slot`.
-__device__ void issue(const ScanArgs &a, const int32_t *plist, const Cur &c, int slot, float *stage, uint64_t *bars) {
-    const ListMeta m = a.meta[plist[c.p]];
-    const int tn = min(a.tile, m.len - c.i0);
+__device__ __forceinline__ const float *list_base(const ScanArgs &a, int4 m) {
+    return a.data + ((int64_t)(unsigned)m.x << 6);
+}
+
+// Queue the bulk copies of one unit (tile c.i0 of probe c.p, increment c.j) into `slot`.
+__device__ void issue(const ScanArgs &a, const int4 *sm, const int32_t *plist, const Cur &c, int slot, float *stage,
+                      uint64_t *bars) {
+    const int4 m = meta_of(a, sm, plist, c.p);
+    const int tn = min(a.tile, m.z - c.i0);
     const int b0 = c.j * a.gb, b1 = min(b0 + a.gb, a.nb);
     const uint32_t bar = su32(&bars[slot]);
     mbar_expect_tx(bar, (uint32_t)((b1 - b0) * tn * 64));
     float *dst = stage + (size_t)slot * a.tile * a.gb * 16;
+    const float *src = list_base(a, m) + (int64_t)c.i0 * 16;
     for (int b = b0; b < b1; ++b)
-        bulk_g2s(su32(dst + (size_t)(b - b0) * a.tile * 16),
-                 a.data + m.base + (int64_t)b * m.np * 16 + (int64_t)c.i0 * 16, (uint32_t)(tn * 64), bar);
+        bulk_g2s(su32(dst + (size_t)(b - b0) * a.tile * 16), src + (int64_t)b * m.w * 16, (uint32_t)(tn * 64), bar);
 }
 
 __device__ __forceinline__ int lower_bound_u64(const unsigned long long *v, int n, unsigned long long key) {
@@ -155,14 +169,15 @@ __device__ __forceinline__ int lower_bound_u64(const unsigned long long *v, int 
 }
 
 struct SmemLayout {
-    size_t qv, stage, l0, l1, fl, fraw, fsort, top, total;
+    size_t meta, qv, stage, l0, l1, fl, fraw, fsort, top, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout layout(int dp, int tile, int gb, int ns, int k) {
+__host__ __device__ inline SmemLayout layout(int dp, int tile, int gb, int ns, int k, int nprobe) {
     SmemLayout L;
     size_t o = 64;                                  // mbarriers (up to 8)
+    L.meta = o;  o = align_up(o + sizeof(int4) * (size_t)min(nprobe, PMETA), 16);
     L.qv = o;    o = align_up(o + sizeof(float) * dp, 128);
     L.stage = o; o = align_up(o + sizeof(float) * (size_t)ns * tile * gb * 16, 128);
     L.l0 = o;    o += sizeof(Surv) * tile;
@@ -175,8 +190,23 @@ __host__ __device__ inline SmemLayout layout(int dp, int tile, int gb, int ns, i
     return L;
 }
 
-template <bool FD, bool STATS>
-__global__ void __launch_bounds__(NT) k_scan(const ScanArgs a) {
+// Partial squared distance of one candidate row over blocks [b0, b1) (4 dims per lane).
+__device__ __forceinline__ float row_part(const float *row, int64_t bstride, const float *qv, int b0, int b1, int lq,
+                                          bool global_mem) {
+    float p = 0.f;
+    for (int b = b0; b < b1; ++b) {
+        const float *src = row + (int64_t)(b - (global_mem ? 0 : b0)) * bstride;
+        float4 o = global_mem ? __ldg(reinterpret_cast<const float4 *>(src)) : *reinterpret_cast<const float4 *>(src);
+        float4 q = *reinterpret_cast<const float4 *>(qv + b * 16 + lq * 4);
+        p += sqd4(q, o);
+    }
+    return p;
+}
+
+template <int NT, bool FD, bool STATS>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_scan(const ScanArgs a) {
+    constexpr int NQUAD = NT / 4;              // candidates per pass
+    constexpr int MAXIT = MAX_TILE / NQUAD;    // passes over a full tile
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_cnt[2], s_cntF, s_ntop, s_cur;
     __shared__ float s_r2;
@@ -184,18 +214,25 @@ __global__ void __launch_bounds__(NT) k_scan(const ScanArgs a) {
 
     const int tid = threadIdx.x, quad = tid >> 2, lq = tid & 3;
     const int64_t qi = blockIdx.x;
-    const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k);
+    const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k, a.nprobe);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    int4 *smeta = reinterpret_cast<int4 *>(smem + L.meta);
     float *qv = reinterpret_cast<float *>(smem + L.qv);
     float *stage = reinterpret_cast<float *>(smem + L.stage);
-    Surv *lst[2] = {reinterpret_cast<Surv *>(smem + L.l0), reinterpret_cast<Surv *>(smem + L.l1)};
+    Surv *l0 = reinterpret_cast<Surv *>(smem + L.l0);
+    Surv *l1 = reinterpret_cast<Surv *>(smem + L.l1);
     Surv *fl = reinterpret_cast<Surv *>(smem + L.fl);
     unsigned long long *fraw = reinterpret_cast<unsigned long long *>(smem + L.fraw);
     unsigned long long *fsort = reinterpret_cast<unsigned long long *>(smem + L.fsort);
-    unsigned long long *top[2] = {reinterpret_cast<unsigned long long *>(smem + L.top),
-                                  reinterpret_cast<unsigned long long *>(smem + L.top) + a.k};
+    unsigned long long *top0 = reinterpret_cast<unsigned long long *>(smem + L.top);
+    unsigned long long *top1 = top0 + a.k;
 
+    const int32_t *plist = a.probe + qi * a.nprobe;
     for (int k = tid; k < a.dp; k += NT) qv[k] = k < a.d ? a.q_rot[qi * a.q_stride + k] : 0.f;
+    for (int p = tid; p < min(a.nprobe, PMETA); p += NT) {
+        const ListMeta m = a.meta[plist[p]];
+        smeta[p] = make_int4((int)(m.base >> 6), (int)m.slot, m.len, m.np);
+    }
     if (tid == 0) {
         for (int s = 0; s < a.ns; ++s) mbar_init(su32(&bars[s]), 1);
         fence_mbar_init();
@@ -206,15 +243,15 @@ __global__ void __launch_bounds__(NT) k_scan(const ScanArgs a) {
     if (STATS && tid < 4) s_stats[tid] = 0;
     __syncthreads();
 
-    const int32_t *plist = a.probe + qi * a.nprobe;
+    const int units = FD ? a.n_inc : min(a.stage, a.n_inc);   // staged increments per tile
     Cur cc{0, 0, 0};
-    normalize(cc, a, plist);
+    normalize(cc, a, smeta, plist);
     Cur ic = cc;          // issue cursor (thread 0 only)
     int issued = 0;       // units issued (thread 0 only)
     if (tid == 0)
         for (int s = 0; s < a.ns && ic.p < a.nprobe; ++s) {
-            issue(a, plist, ic, s, stage, bars);
-            advance<FD>(ic, a, plist);
+            issue(a, smeta, plist, ic, s, stage, bars);
+            advance(ic, units, a, smeta, plist);
             ++issued;
         }
     unsigned long long st_cand = 0, st_dims = 0, st_acc = 0, st_prn = 0;
@@ -222,9 +259,11 @@ __global__ void __launch_bounds__(NT) k_scan(const ScanArgs a) {
     bool aborted = false;
 
     while (cc.p < a.nprobe) {
-        const ListMeta m = a.meta[plist[cc.p]];
-        const int tn = min(a.tile, m.len - cc.i0);
+        const int4 m = meta_of(a, smeta, plist, cc.p);
+        const int tn = min(a.tile, m.z - cc.i0);
         const int nit = (tn + NQUAD - 1) / NQUAD;
+        const float *lbase = list_base(a, m);
+        const int64_t bstride = (int64_t)m.w * 16;     // floats between block slabs of this list
         if (tid == 0) {
             s_cnt[0] = 0;
             s_cntF = 0;
@@ -242,21 +281,16 @@ __global__ void __launch_bounds__(NT) k_scan(const ScanArgs a) {
                 if (__syncthreads_or(!ok)) { aborted = true; break; }
                 if (j == 0) r2 = s_r2;
                 const float *st = stage + (size_t)slot * a.tile * a.gb * 16;
-                const int b0 = j * a.gb, nbj = min(a.gb, a.nb - b0);
+                const int b0 = j * a.gb, b1 = min(b0 + a.gb, a.nb);
 #pragma unroll
                 for (int it = 0; it < MAXIT; ++it) {
                     const int c = quad + it * NQUAD;
-                    if (it < nit && c < tn)
-                        for (int b = 0; b < nbj; ++b) {
-                            float4 o = *reinterpret_cast<const float4 *>(st + ((size_t)b * a.tile + c) * 16 + lq * 4);
-                            float4 q = *reinterpret_cast<const float4 *>(qv + (b0 + b) * 16 + lq * 4);
-                            acc[it] += sqd4(q, o);
-                        }
+                    if (it < nit && c < tn) acc[it] += row_part(st + c * 16 + lq * 4, (int64_t)a.tile * 16, qv, b0, b1, lq, false);
                 }
                 __syncthreads();
                 if (tid == 0 && ic.p < a.nprobe) {
-                    issue(a, plist, ic, slot, stage, bars);
-                    advance<FD>(ic, a, plist);
+                    issue(a, smeta, plist, ic, slot, stage, bars);
+                    advance(ic, units, a, smeta, plist);
                     ++issued;
                 }
                 ++unit;
@@ -274,87 +308,112 @@ __global__ void __launch_bounds__(NT) k_scan(const ScanArgs a) {
             }
             __syncthreads();
         } else {
-            // ---- DADE: first increment from the staged blocks ---------------------
-            const int slot = unit % a.ns;
-            const bool ok = wait_bounded(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1), WAIT_NS);
+            // ---- DADE, increment 0 over the whole tile (staged) --------------------
+            int slot = unit % a.ns;
+            bool ok = wait_bounded(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1), WAIT_NS);
             if (__syncthreads_or(!ok)) { aborted = true; break; }
             r2 = s_r2;
-            const float *st = stage + (size_t)slot * a.tile * a.gb * 16;
-            const int nb0 = min(a.gb, a.nb);
-            const bool last0 = a.n_inc == 1;
-            const int d0 = min(a.delta_d, a.d);
-            const float c0 = a.coef[0] * r2;
-            for (int it = 0; it < nit; ++it) {
-                const int c = quad + it * NQUAD;
-                const bool act = c < tn;
-                float p = 0.f;
-                if (act)
-                    for (int b = 0; b < nb0; ++b) {
-                        float4 o = *reinterpret_cast<const float4 *>(st + ((size_t)b * a.tile + c) * 16 + lq * 4);
-                        float4 q = *reinterpret_cast<const float4 *>(qv + b * 16 + lq * 4);
-                        p += sqd4(q, o);
+            {
+                const float *st = stage + (size_t)slot * a.tile * a.gb * 16;
+                const int b1 = min(a.gb, a.nb);
+                const bool last0 = a.n_inc == 1;
+                const int d0 = min(a.delta_d, a.d);
+                const float c0 = a.coef[0] * r2;
+                for (int it = 0; it < nit; ++it) {
+                    const int c = quad + it * NQUAD;
+                    const bool act = c < tn;
+                    float p = act ? row_part(st + c * 16 + lq * 4, (int64_t)a.tile * 16, qv, 0, b1, lq, false) : 0.f;
+                    p += __shfl_xor_sync(0xffffffffu, p, 1);
+                    p += __shfl_xor_sync(0xffffffffu, p, 2);
+                    const bool lead = act && lq == 0;
+                    const bool toF = lead && last0 && p <= r2;
+                    const bool toN = lead && !last0 && !(p > c0);
+                    push(toF, fl, &s_cntF, c, p);
+                    push(toN, l0, &s_cnt[0], c, p);
+                    if (STATS && lead) {
+                        ++st_cand;
+                        if (last0) { st_dims += a.d; st_acc += toF; }
+                        else if (!toN) { st_dims += d0; ++st_prn; }
                     }
-                p += __shfl_xor_sync(0xffffffffu, p, 1);
-                p += __shfl_xor_sync(0xffffffffu, p, 2);
-                const bool lead = act && lq == 0;
-                const bool toF = lead && last0 && p <= r2;
-                const bool toN = lead && !last0 && !(p > c0);
-                push(toF, fl, &s_cntF, c, p);
-                push(toN, lst[0], &s_cnt[0], c, p);
-                if (STATS && lead) {
-                    ++st_cand;
-                    if (last0) { st_dims += a.d; st_acc += toF; }
-                    else if (!toN) { st_dims += d0; ++st_prn; }
                 }
             }
             __syncthreads();
             if (tid == 0 && ic.p < a.nprobe) {
-                issue(a, plist, ic, slot, stage, bars);
-                advance<FD>(ic, a, plist);
+                issue(a, smeta, plist, ic, slot, stage, bars);
+                advance(ic, units, a, smeta, plist);
                 ++issued;
             }
             ++unit;
-            // ---- later increments: gather survivors' block rows ------------------
+            // ---- later increments: staged (j < units) or gathered ------------------
             int ns_cur = s_cnt[0];
-            for (int j = 1; j < a.n_inc && ns_cur > 0; ++j) {
+            for (int j = 1; j < a.n_inc; ++j) {
+                const bool staged = j < units;
+                if (!staged && ns_cur == 0) break;
                 const int src = (j - 1) & 1, dst = j & 1;
                 if (tid == 0) s_cnt[dst] = 0;
-                __syncthreads();
-                const int b0 = j * a.gb, b1 = min(b0 + a.gb, a.nb);
-                const bool last = j == a.n_inc - 1;
-                const int dj = min((j + 1) * a.delta_d, a.d);
-                const float cj = a.coef[j] * r2;
-                const Surv *in = lst[src];
-                const int nits = (ns_cur + NQUAD - 1) / NQUAD;
-                for (int it = 0; it < nits; ++it) {
-                    const int s = quad + it * NQUAD;
-                    const bool act = s < ns_cur;
-                    Surv sv = act ? in[s] : Surv{0, 0.f};
-                    float part = 0.f;
-                    if (act) {
-                        const float *row = a.data + m.base + (int64_t)(cc.i0 + sv.idx) * 16 + lq * 4;
-                        for (int b = b0; b < b1; ++b) {
-                            float4 o = __ldg(reinterpret_cast<const float4 *>(row + (int64_t)b * m.np * 16));
-                            float4 q = *reinterpret_cast<const float4 *>(qv + b * 16 + lq * 4);
-                            part += sqd4(q, o);
+                if (staged) {
+                    slot = unit % a.ns;
+                    ok = wait_bounded(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1), WAIT_NS);
+                    if (__syncthreads_or(!ok)) { aborted = true; break; }
+                } else {
+                    __syncthreads();
+                }
+                if (ns_cur > 0) {
+                    const int b0 = j * a.gb, b1 = min(b0 + a.gb, a.nb);
+                    const bool last = j == a.n_inc - 1;
+                    const int dj = min((j + 1) * a.delta_d, a.d);
+                    const float cj = a.coef[j] * r2;
+                    const Surv *in = src ? l1 : l0;
+                    Surv *out = dst ? l1 : l0;
+                    const float *st = stage + (size_t)slot * a.tile * a.gb * 16;
+                    const int nits = (ns_cur + NQUAD - 1) / NQUAD;
+                    for (int it0 = 0; it0 < nits; it0 += GCHUNK) {
+                        // all loads of this lane's survivors first, then the reductions
+                        Surv sv[GCHUNK];
+                        float part[GCHUNK];
+#pragma unroll
+                        for (int u = 0; u < GCHUNK; ++u) {
+                            const int s = quad + (it0 + u) * NQUAD;
+                            const bool act = it0 + u < nits && s < ns_cur;
+                            sv[u] = act ? in[s] : Surv{-1, 0.f};
+                            part[u] = 0.f;
+                            if (act)
+                                part[u] = staged
+                                    ? row_part(st + sv[u].idx * 16 + lq * 4, (int64_t)a.tile * 16, qv, b0, b1, lq, false)
+                                    : row_part(lbase + (int64_t)(cc.i0 + sv[u].idx) * 16 + lq * 4, bstride, qv, b0, b1,
+                                               lq, true);
                         }
-                    }
-                    part += __shfl_xor_sync(0xffffffffu, part, 1);
-                    part += __shfl_xor_sync(0xffffffffu, part, 2);
-                    const float p = sv.p + part;
-                    const bool lead = act && lq == 0;
-                    const bool toF = lead && last && p <= r2;
-                    const bool toN = lead && !last && !(p > cj);
-                    push(toF, fl, &s_cntF, sv.idx, p);
-                    push(toN, lst[dst], &s_cnt[dst], sv.idx, p);
-                    if (STATS && lead) {
-                        if (last) { st_dims += a.d; st_acc += toF; }
-                        else if (!toN) { st_dims += dj; ++st_prn; }
+#pragma unroll
+                        for (int u = 0; u < GCHUNK; ++u) {
+                            if (it0 + u >= nits) break;
+                            float pp = part[u];
+                            pp += __shfl_xor_sync(0xffffffffu, pp, 1);
+                            pp += __shfl_xor_sync(0xffffffffu, pp, 2);
+                            const float p = sv[u].p + pp;
+                            const bool lead = sv[u].idx >= 0 && lq == 0;
+                            const bool toF = lead && last && p <= r2;
+                            const bool toN = lead && !last && !(p > cj);
+                            push(toF, fl, &s_cntF, sv[u].idx, p);
+                            push(toN, out, &s_cnt[dst], sv[u].idx, p);
+                            if (STATS && lead) {
+                                if (last) { st_dims += a.d; st_acc += toF; }
+                                else if (!toN) { st_dims += dj; ++st_prn; }
+                            }
+                        }
                     }
                 }
                 __syncthreads();
-                ns_cur = last ? 0 : s_cnt[dst];
+                if (staged) {
+                    if (tid == 0 && ic.p < a.nprobe) {
+                        issue(a, smeta, plist, ic, slot, stage, bars);
+                        advance(ic, units, a, smeta, plist);
+                        ++issued;
+                    }
+                    ++unit;
+                }
+                ns_cur = j == a.n_inc - 1 ? 0 : s_cnt[dst];
             }
+            if (aborted) break;
         }
 
         // ---- merge accepted candidates into the K best ------------------------------
@@ -362,7 +421,7 @@ __global__ void __launch_bounds__(NT) k_scan(const ScanArgs a) {
         if (nF > 0) {
             for (int t = tid; t < nF; t += NT) {
                 const Surv f = fl[t];
-                const unsigned id = (unsigned)a.ids[m.slot + cc.i0 + f.idx];
+                const unsigned id = (unsigned)a.ids[(int64_t)(unsigned)m.y + cc.i0 + f.idx];
                 fraw[t] = ((unsigned long long)__float_as_uint(f.p) << 32) | id;
             }
             __syncthreads();
@@ -374,8 +433,8 @@ __global__ void __launch_bounds__(NT) k_scan(const ScanArgs a) {
             }
             __syncthreads();
             const int nt = s_ntop, cur = s_cur;
-            const unsigned long long *A = top[cur];
-            unsigned long long *O = top[cur ^ 1];
+            const unsigned long long *A = cur ? top1 : top0;
+            unsigned long long *O = cur ? top0 : top1;
             for (int t = tid; t < nt; t += NT) {
                 const int pos = t + lower_bound_u64(fsort, nF, A[t]);
                 if (pos < a.k) O[pos] = A[t];
@@ -393,8 +452,9 @@ __global__ void __launch_bounds__(NT) k_scan(const ScanArgs a) {
             }
         }
         __syncthreads();
-        if (!FD) advance<FD>(cc, a, plist);
-        else { cc.j = 0; cc.i0 += a.tile; normalize(cc, a, plist); }
+        cc.j = 0;
+        cc.i0 += a.tile;
+        normalize(cc, a, smeta, plist);
     }
 
     if (aborted) {
@@ -406,7 +466,7 @@ __global__ void __launch_bounds__(NT) k_scan(const ScanArgs a) {
         return;
     }
     const int nt = s_ntop;
-    const unsigned long long *R = top[s_cur];
+    const unsigned long long *R = s_cur ? top1 : top0;
     for (int t = tid; t < a.k; t += NT) {
         int64_t id = -1;
         float dv = INFINITY;
@@ -429,15 +489,22 @@ __global__ void __launch_bounds__(NT) k_scan(const ScanArgs a) {
     }
 }
 
-template <bool FD, bool STATS>
+template <int NT, bool FD, bool STATS>
 dade_status launch(const ScanArgs &a, int64_t nq, size_t smem, cudaStream_t s) {
     static size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
-        DADE_TRY_CUDA(cudaFuncSetAttribute(k_scan<FD, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        DADE_TRY_CUDA(cudaFuncSetAttribute(k_scan<NT, FD, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
         configured = smem;
     }
-    k_scan<FD, STATS><<<(unsigned)nq, NT, smem, s>>>(a);
+    k_scan<NT, FD, STATS><<<(unsigned)nq, NT, smem, s>>>(a);
     return launch_check(FD ? "k_scan<FD>" : "k_scan<DADE>");
+}
+
+template <int NT>
+dade_status launch_nt(const ScanArgs &a, int64_t nq, size_t smem, bool fd, bool stats, cudaStream_t s) {
+    if (fd) return stats ? launch<NT, true, true>(a, nq, smem, s) : launch<NT, true, false>(a, nq, smem, s);
+    return stats ? launch<NT, false, true>(a, nq, smem, s) : launch<NT, false, false>(a, nq, smem, s);
 }
 
 } // namespace
@@ -462,6 +529,7 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     a.k = p.k;
     a.tile = p.tile;
     a.ns = 2;
+    a.stage = p.stage;
     const bool fd = p.mode == DADE_MODE_FD;
     if (fd) {
         a.gb = std::min(4, ix->nb);
@@ -472,13 +540,13 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     }
     a.n_inc = (ix->nb + a.gb - 1) / a.gb;
     for (int j = 0; j < DADE_MAX_DIM / DADE_BLOCK; ++j) a.coef[j] = j < p.n_inc ? p.coef[j] : INFINITY;
-    const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k);
+    const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k, a.nprobe);
     if (L.total > 227 * 1024) {
         set_error("scan configuration needs more than 227 KB of shared memory (reduce tile or delta_d)");
         return DADE_EUNSUPPORTED;
     }
-    if (fd) return p.stats ? launch<true, true>(a, nq, L.total, s) : launch<true, false>(a, nq, L.total, s);
-    return p.stats ? launch<false, true>(a, nq, L.total, s) : launch<false, false>(a, nq, L.total, s);
+    if (p.threads == 256) return launch_nt<256>(a, nq, L.total, fd, p.stats != nullptr, s);
+    return launch_nt<128>(a, nq, L.total, fd, p.stats != nullptr, s);
 }
 
 } // namespace dade

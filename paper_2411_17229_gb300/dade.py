@@ -34,7 +34,8 @@ class BuildOpts(C.Structure):
 
 
 class SearchOpts(C.Structure):
-    _fields_ = [("mode", C.c_int32), ("tile", C.c_int32), ("stats", C.c_void_p), ("reserved", C.c_int32 * 8)]
+    _fields_ = [("mode", C.c_int32), ("tile", C.c_int32), ("stats", C.c_void_p), ("stage", C.c_int32),
+                ("threads", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class Info(C.Structure):
@@ -53,6 +54,7 @@ SIGNATURES = {
     "dade_probe": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
     "dade_search": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
     "dade_query": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
+    "dade_scan": (_i32, [_vp, _vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
     "dade_reserve": (_i32, [_vp, _i64, _i32]),
     "dade_eps_table": (_i32, [_vp, _f32, _i32, _vp, _vp]),
     "dade_index_info": (_i32, [_vp, _vp]),
@@ -162,14 +164,23 @@ class Index:
         _check(lib().dade_probe(self._h, _ptr(q_rot), q_rot.shape[0], int(nprobe), _ptr(out), _stream(stream)))
         return out
 
-    def search(self, q_rot, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, stream=None):
-        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats))
+    def search(self, q_rot, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, stage=0,
+               threads=0, stream=None):
+        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), stage=stage, threads=threads)
         _check(lib().dade_search(self._h, _ptr(q_rot), q_rot.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                  C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
-    def query(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, stream=None):
-        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats))
+    def scan(self, q_rot, probe, k, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, stage=0,
+             threads=0, stream=None):
+        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), stage=stage, threads=threads)
+        _check(lib().dade_scan(self._h, _ptr(q_rot), _ptr(probe), q_rot.shape[0], int(k), probe.shape[1],
+                               float(alpha), int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
+        return ids, dists
+
+    def query(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, stage=0,
+              threads=0, stream=None):
+        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), stage=stage, threads=threads)
         _check(lib().dade_query(self._h, _ptr(q), q.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                 C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists

@@ -15,7 +15,13 @@ Recipe shared by every workload (numpy PCG64, fixed seeds):
   * spectrum  lambda_i = i^-p, rescaled so that sum(lambda) = D;
   * basis     a Haar-random orthogonal matrix (QR of a Gaussian, sign fixed
               so that R has a positive diagonal);
-  * component x = m + s * Q (sqrt(lambda) * z),  z ~ N(0, I).
+  * component x = m_c + s * Q (sqrt(lambda) * z),  z ~ N(0, I).
+Mixtures are anisotropic as a whole: every component shares the basis Q, and
+the component means are drawn along the same spectrum,
+m_c = offset + t * Q (sqrt(lambda) * g_c), so the mixture's covariance has the
+power-law spectrum in the basis Q (``shared_basis=True``, the default).  With
+``shared_basis=False`` every component gets its own Haar basis and the means
+are isotropic, which averages the mixture's covariance towards isotropy.
 Seeds: 0 base, 1 queries, 2 basis/means, 3 k-means init, 4 epsilon pairs.
 """
 from __future__ import annotations
@@ -45,6 +51,7 @@ class Workload:
     delta_d: tuple
     alpha: float
     kmeans_iters: int = 10
+    shared_basis: bool = True
 
 
 # Constants proposed for the workloads (sizes from the benchmark configs; the
@@ -81,11 +88,14 @@ def _components(w: Workload):
     """Component means and rotations, all drawn from the basis seed."""
     rng = np.random.default_rng(SEED_BASIS)
     lam = spectrum(w.d, w.p)
-    if w.n_comp == 1:
-        means = np.zeros((1, w.d))
+    if w.shared_basis or w.n_comp == 1:
+        Q = haar(w.d, rng)
+        rots = [Q] * w.n_comp
+        g = rng.standard_normal((w.n_comp, w.d)) * np.sqrt(lam)[None, :]
+        means = np.zeros((1, w.d)) if w.n_comp == 1 else w.mean_offset + w.mean_scale * (g @ Q.T)
     else:
         means = w.mean_offset + w.mean_scale * rng.standard_normal((w.n_comp, w.d))
-    rots = [haar(w.d, rng) for _ in range(w.n_comp)]
+        rots = [haar(w.d, rng) for _ in range(w.n_comp)]
     return lam, means, rots
 
 

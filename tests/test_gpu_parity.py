@@ -87,11 +87,18 @@ def test_pca_parity(c1):
     assert np.allclose(np.abs(np.diag(M)), 1.0, atol=1e-6)   # same eigenvectors up to sign
 
 
+def _signs(c):
+    """Eigenvectors are defined up to sign; align the GPU basis to the oracle's."""
+    W = c.gpu.export(dade.FIELD_BASIS)
+    return np.sign(np.einsum("jk,jk->k", W, c.orc.W))
+
+
 def test_rotation_parity(c1):
-    Xg = c1.gpu.export(dade.FIELD_ROTATED).astype(np.float64)
+    sg = _signs(c1)
+    Xg = c1.gpu.export(dade.FIELD_ROTATED).astype(np.float64) * sg
     scale = np.sqrt(c1.scale)
     assert np.abs(Xg - c1.orc.Xr).max() < 2e-6 * scale
-    Qg = c1.q_rot.cpu().numpy().astype(np.float64)
+    Qg = c1.q_rot.cpu().numpy().astype(np.float64) * sg
     assert np.abs(Qg - c1.Qr).max() < 2e-6 * scale
     # host buffers in, host buffers out give the same bits
     qh = np.empty_like(c1.queries)
@@ -101,7 +108,7 @@ def test_rotation_parity(c1):
 
 def test_assignment_and_centroids(c1):
     assert np.array_equal(c1.gpu.export(dade.FIELD_ASSIGN), c1.assign)
-    cg = c1.gpu.export(dade.FIELD_CENTROIDS).astype(np.float64)
+    cg = c1.gpu.export(dade.FIELD_CENTROIDS).astype(np.float64) * _signs(c1)
     assert np.abs(cg - c1.orc.cent).max() < 2e-6 * np.sqrt(c1.scale)
 
 
