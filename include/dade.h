@@ -70,6 +70,24 @@ typedef enum {
     DADE_MODE_FD = 1        /* FDScanning (Section 4.1): exact full-D distance for every candidate */
 } dade_mode;
 
+/*
+ * Threshold schedule of a DADE search.  Lists are scanned in probe order and
+ * each list in tiles of opts->tile candidates (ascending base id; a tile
+ * never spans two lists).  Every candidate of a tile is tested against the
+ * K-th distance r held when the tile starts:
+ *   DADE_SCHED_TILE       r after all earlier tiles (tile-synchronous);
+ *   DADE_SCHED_PIPELINED  r after all tiles but the n_inc - 1 just before it,
+ *                         where n_inc = ceil(ceil(D/16) / (delta_d/16)) is the
+ *                         number of increments: up to n_inc tiles are in flight
+ *                         at once, one per increment.  Used when n_inc <= 8,
+ *                         otherwise the tile schedule runs.
+ * A staler threshold can only prune less.  FDScanning ignores the schedule.
+ */
+typedef enum {
+    DADE_SCHED_PIPELINED = 0,
+    DADE_SCHED_TILE = 1
+} dade_schedule;
+
 /* Index construction options.  Zero-initialise, then call dade_build_opts_default(). */
 typedef struct {
     int32_t n_clusters;        /* N_c, number of inverted lists (>= 1) */
@@ -89,10 +107,11 @@ typedef struct {
     int32_t tile;              /* candidates per threshold refresh (default 128; 32..256, multiple of 32) */
     int64_t *stats;            /* device, optional [nq * 4]: per query candidates scanned, sum of
                                   dimensions used, candidates accepted by the DCO, candidates pruned */
-    int32_t stage;             /* increments per tile streamed whole into shared memory (default 1);
-                                  later increments fetch only the surviving candidates' rows */
+    int32_t spec;              /* tile schedule: 16-dim blocks of a candidate that survived the first
+                                  increment loaded together ahead of its tests (1..8, default 8) */
     int32_t threads;           /* threads per query's CTA: 0 (default 128), 128 or 256 */
-    int32_t reserved[6];
+    int32_t schedule;          /* dade_schedule (default DADE_SCHED_PIPELINED) */
+    int32_t reserved[5];
 } dade_search_opts;
 
 /* Description of a built index. */
@@ -163,9 +182,8 @@ dade_status dade_probe(const dade_index *ix, const float *q_rot, int64_t nq, int
  * one DCO per candidate (Algorithm 1 and the Section 3.3 test at
  * significance alpha) against the query's current K-th distance, keeping the
  * K nearest.  Lists are scanned in probe order, members in ascending base id,
- * in tiles of opts->tile candidates; every candidate of a tile is tested
- * against the K-th distance held before the tile (the threshold is refreshed
- * once per tile; a stale threshold can only prune less).
+ * in tiles of opts->tile candidates, each tile tested against the K-th
+ * distance of the threshold schedule opts->schedule (see dade_schedule).
  * q_rot: host or device [nq * d]; ids: host or device [nq * k] int64; dists:
  * host or device [nq * k] FP32 squared distances.  1 <= k <= DADE_MAX_K,
  * 1 <= nprobe <= n_clusters, 0 < alpha < 1, delta_d a multiple of 16 in

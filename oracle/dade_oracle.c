@@ -500,6 +500,10 @@ OR_API int or_dco(const double *q, const double *o, int D, int delta_d, double r
  *   schedule 0  SEQUENTIAL      one candidate per epoch (the paper's order);
  *   schedule 1  TILE(tile)      up to `tile` consecutive members of one list;
  *   schedule 2  PROBE_ROUNDS    one whole list per epoch.
+ * With schedule 1 and lag L > 0, tile t (tiles numbered over the query's
+ * whole scan) is tested against r taken after tiles 0..t-1-L only: the
+ * threshold of a pipeline that keeps L later tiles in flight.  L = 0 is the
+ * plain tile schedule.
  * Results are ordered by (squared distance, id); missing slots are (-1, +inf).
  * eps == NULL runs FDScanning.  eps is indexed by d (eps[d], d < D).
  * stats (nq x 4, may be NULL): candidates, sum of dims used, accepted, pruned.
@@ -511,10 +515,10 @@ OR_API int or_dco(const double *q, const double *o, int D, int delta_d, double r
  */
 OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, int nc,
                      const double *cent, const double *lam, const double *Qr, int64_t nq,
-                     int K, int nprobe, int delta_d, const double *eps, int schedule, int tile,
+                     int K, int nprobe, int delta_d, const double *eps, int schedule, int tile, int lag,
                      double tol, int64_t *ids, double *dists, int64_t *stats, int32_t *flags)
 {
-    if (K < 1 || nprobe < 1 || nprobe > nc || delta_d < 1 || (schedule == 1 && tile < 1)) return -1;
+    if (K < 1 || nprobe < 1 || nprobe > nc || delta_d < 1 || (schedule == 1 && tile < 1) || lag < 0) return -1;
     /* inverted lists, members in ascending id */
     int64_t *start = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
     int64_t *members = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -534,10 +538,12 @@ OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, 
         int64_t maxlen = 0;
         for (int c = 0; c < nc; ++c) if (start[c + 1] - start[c] > maxlen) maxlen = start[c + 1] - start[c];
         kv_t *buf = (kv_t *)malloc(sizeof(kv_t) * (size_t)(K + maxlen + 1));
+        double *hist = (double *)malloc(sizeof(double) * (size_t)(lag + 1));   /* r^2 after recent epochs */
         #pragma omp for schedule(dynamic, 1)
         for (int64_t qi = 0; qi < nq; ++qi) {
             const double *q = Qr + qi * D;
             int ntop = 0, tie = 0;
+            int64_t epoch = 0;
             double dropped = INFINITY;   /* best squared distance accepted but not kept */
             int64_t st[4] = {0, 0, 0, 0};
             for (int j = 0; j < nprobe; ++j) {
@@ -546,6 +552,7 @@ OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, 
                 int64_t elen = schedule == 0 ? 1 : schedule == 1 ? tile : (len > 0 ? len : 1);
                 for (int64_t e0 = 0; e0 < len; e0 += elen) {
                     double r2 = ntop == K ? buf[K - 1].key : INFINITY;
+                    if (lag > 0) r2 = epoch - 1 - lag >= 0 ? hist[(epoch - 1 - lag) % (lag + 1)] : INFINITY;
                     double r = sqrt(r2);
                     int npend = 0;
                     int64_t e1 = e0 + elen < len ? e0 + elen : len;
@@ -566,6 +573,8 @@ OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, 
                         if (u > K && buf[K].key < dropped) dropped = buf[K].key;
                         ntop = u < K ? u : K;
                     }
+                    if (lag > 0) hist[epoch % (lag + 1)] = ntop == K ? buf[K - 1].key : INFINITY;
+                    ++epoch;
                 }
             }
             if (ntop == K && isfinite(dropped) && near_tie(buf[K - 1].key, dropped, tol)) tie |= 4;
@@ -577,6 +586,7 @@ OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, 
             if (flags) flags[qi] = tie | (ptie[qi] ? 8 : 0);
         }
         free(buf);
+        free(hist);
     }
     free(probe); free(ptie); free(Lam); free(start); free(members);
     return 0;

@@ -111,9 +111,11 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
     }
     const int tile = opts && opts->tile ? opts->tile : 128;
     DADE_CHECK_ARG(tile >= 32 && tile <= 256 && tile % 32 == 0, "tile must be a multiple of 32 in [32, 256]");
-    DADE_CHECK_ARG(!opts || (opts->stage >= 0 && opts->stage <= 64), "stage outside 0..64");
+    DADE_CHECK_ARG(!opts || (opts->spec >= 0 && opts->spec <= 8), "spec outside 0..8");
     DADE_CHECK_ARG(!opts || opts->threads == 0 || opts->threads == 128 || opts->threads == 256,
                    "threads must be 0 (default), 128 or 256");
+    DADE_CHECK_ARG(!opts || opts->schedule == DADE_SCHED_PIPELINED || opts->schedule == DADE_SCHED_TILE,
+                   "unknown schedule");
     return DADE_OK;
 }
 
@@ -158,8 +160,9 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.k = k;
     p.tile = opts && opts->tile ? opts->tile : 128;
     p.mode = opts ? opts->mode : DADE_MODE_DADE;
-    p.stage = opts && opts->stage > 0 ? opts->stage : 1;
+    p.spec = opts && opts->spec > 0 ? opts->spec : 8;
     p.threads = opts && opts->threads ? opts->threads : 128;
+    p.schedule = opts ? opts->schedule : DADE_SCHED_PIPELINED;
     p.delta_d = delta_d;
     if (p.mode == DADE_MODE_DADE) p.n_inc = coef_table(ix, alpha, delta_d, nullptr, p.coef);
     else p.n_inc = 0;

@@ -28,183 +28,15 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "scan_common.cuh"
 
 namespace dade {
 
 namespace {
-
-constexpr int MAX_TILE = 256;
-constexpr int GCHUNK = 4;          // survivors per lane whose loads are issued together
-constexpr uint64_t WAIT_NS = 2000000000ull;
-
-struct Surv {
-    int idx;      // candidate index within the tile
-    float p;      // partial squared distance so far
-};
-
-struct ScanArgs {
-    const float *data;
-    const int32_t *ids;
-    const ListMeta *meta;
-    const float *q_rot;
-    const int32_t *probe;
-    int64_t *out_ids;
-    float *out_d;
-    int64_t *stats;
-    int *err;
-    int q_stride, nprobe, d, dp, nb, k, tile, gb, n_inc, ns, delta_d, stage;
-    float coef[DADE_MAX_DIM / DADE_BLOCK];
-};
-
-// ---------------------------------------------------------- PTX helpers ----
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ bool wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = gtimer();
-    while (!mbar_try_wait(bar, parity))
-        if (gtimer() - t0 > limit_ns) return false;
-    return true;
-}
-
-__device__ __forceinline__ float sqd4(float4 q, float4 o) {
-    float a = q.x - o.x, b = q.y - o.y, c = q.z - o.z, e = q.w - o.w;
-    return fmaf(a, a, fmaf(b, b, fmaf(c, c, e * e)));
-}
-
-// Append (idx, p) for every quad leader with `want`; one atomic per warp.
-__device__ __forceinline__ void push(bool want, Surv *list, int *cnt, int idx, float p) {
-    const int lane = threadIdx.x & 31;
-    const unsigned m = __ballot_sync(0xffffffffu, want);
-    if (m == 0) return;
-    int base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(cnt, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-    if (want) list[base + __popc(m & ((1u << lane) - 1u))] = Surv{idx, p};
-}
-
-// Per-probe list descriptor kept in shared memory: x = base / 64 (the data
-// offset in 256-byte units), y = first id slot, z = length, w = padded length.
-constexpr int PMETA = 1024;   // probes whose descriptors are preloaded
-
-__device__ __forceinline__ int4 meta_of(const ScanArgs &a, const int4 *sm, const int32_t *plist, int p) {
-    if (p < PMETA) return sm[p];
-    const ListMeta m = a.meta[plist[p]];
-    return make_int4((int)(m.base >> 6), (int)m.slot, m.len, m.np);
-}
-
-// Tile cursor: probe position p, first candidate i0, increment j.
-struct Cur {
-    int p, i0, j;
-};
-
-__device__ __forceinline__ void normalize(Cur &c, const ScanArgs &a, const int4 *sm, const int32_t *plist) {
-    while (c.p < a.nprobe && c.i0 >= meta_of(a, sm, plist, c.p).z) {
-        ++c.p;
-        c.i0 = 0;
-        c.j = 0;
-    }
-}
-
-// Advance over units: `units` staged increments per tile.
-__device__ __forceinline__ void advance(Cur &c, int units, const ScanArgs &a, const int4 *sm, const int32_t *plist) {
-    if (++c.j < units) return;
-    c.j = 0;
-    c.i0 += a.tile;
-    normalize(c, a, sm, plist);
-}
-
-__device__ __forceinline__ const float *list_base(const ScanArgs &a, int4 m) {
-    return a.data + ((int64_t)(unsigned)m.x << 6);
-}
-
-// Queue the bulk copies of one unit (tile c.i0 of probe c.p, increment c.j) into `slot`.
-__device__ void issue(const ScanArgs &a, const int4 *sm, const int32_t *plist, const Cur &c, int slot, float *stage,
-                      uint64_t *bars) {
-    const int4 m = meta_of(a, sm, plist, c.p);
-    const int tn = min(a.tile, m.z - c.i0);
-    const int b0 = c.j * a.gb, b1 = min(b0 + a.gb, a.nb);
-    const uint32_t bar = su32(&bars[slot]);
-    mbar_expect_tx(bar, (uint32_t)((b1 - b0) * tn * 64));
-    float *dst = stage + (size_t)slot * a.tile * a.gb * 16;
-    const float *src = list_base(a, m) + (int64_t)c.i0 * 16;
-    for (int b = b0; b < b1; ++b)
-        bulk_g2s(su32(dst + (size_t)(b - b0) * a.tile * 16), src + (int64_t)b * m.w * 16, (uint32_t)(tn * 64), bar);
-}
-
-__device__ __forceinline__ int lower_bound_u64(const unsigned long long *v, int n, unsigned long long key) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (v[mid] < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-struct SmemLayout {
-    size_t meta, qv, stage, l0, l1, fl, fraw, fsort, top, total;
-};
-
-__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-__host__ __device__ inline SmemLayout layout(int dp, int tile, int gb, int ns, int k, int nprobe) {
-    SmemLayout L;
-    size_t o = 64;                                  // mbarriers (up to 8)
-    L.meta = o;  o = align_up(o + sizeof(int4) * (size_t)min(nprobe, PMETA), 16);
-    L.qv = o;    o = align_up(o + sizeof(float) * dp, 128);
-    L.stage = o; o = align_up(o + sizeof(float) * (size_t)ns * tile * gb * 16, 128);
-    L.l0 = o;    o += sizeof(Surv) * tile;
-    L.l1 = o;    o += sizeof(Surv) * tile;
-    L.fl = o;    o += sizeof(Surv) * tile;
-    L.fraw = o;  o += 8 * (size_t)tile;
-    L.fsort = o; o += 8 * (size_t)tile;
-    L.top = o;   o += 16 * (size_t)k;
-    L.total = align_up(o, 128);
-    return L;
-}
-
-// Partial squared distance of one candidate row over blocks [b0, b1) (4 dims per lane).
-__device__ __forceinline__ float row_part(const float *row, int64_t bstride, const float *qv, int b0, int b1, int lq,
-                                          bool global_mem) {
-    float p = 0.f;
-    for (int b = b0; b < b1; ++b) {
-        const float *src = row + (int64_t)(b - (global_mem ? 0 : b0)) * bstride;
-        float4 o = global_mem ? __ldg(reinterpret_cast<const float4 *>(src)) : *reinterpret_cast<const float4 *>(src);
-        float4 q = *reinterpret_cast<const float4 *>(qv + b * 16 + lq * 4);
-        p += sqd4(q, o);
-    }
-    return p;
-}
+using namespace scanning;
 
 template <int NT, bool FD, bool STATS>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_scan(const ScanArgs a) {
+__global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const ScanArgs a) {
     constexpr int NQUAD = NT / 4;              // candidates per pass
     constexpr int MAXIT = MAX_TILE / NQUAD;    // passes over a full tile
     extern __shared__ __align__(128) unsigned char smem[];
@@ -243,7 +75,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_scan(const ScanArgs a) {
     if (STATS && tid < 4) s_stats[tid] = 0;
     __syncthreads();
 
-    const int units = FD ? a.n_inc : min(a.stage, a.n_inc);   // staged increments per tile
+    const int units = FD ? a.n_inc : 1;   // staged units per tile
     Cur cc{0, 0, 0};
     normalize(cc, a, smeta, plist);
     Cur ic = cc;          // issue cursor (thread 0 only)
@@ -277,8 +109,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_scan(const ScanArgs a) {
             for (int it = 0; it < MAXIT; ++it) acc[it] = 0.f;
             for (int j = 0; j < a.n_inc; ++j) {
                 const int slot = unit % a.ns;
-                const bool ok = wait_bounded(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1), WAIT_NS);
-                if (__syncthreads_or(!ok)) { aborted = true; break; }
+                if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1))) { aborted = true; break; }
                 if (j == 0) r2 = s_r2;
                 const float *st = stage + (size_t)slot * a.tile * a.gb * 16;
                 const int b0 = j * a.gb, b1 = min(b0 + a.gb, a.nb);
@@ -296,7 +127,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_scan(const ScanArgs a) {
                 ++unit;
             }
             if (aborted) break;
-            for (int it = 0; it < nit; ++it) {
+#pragma unroll
+            for (int it = 0; it < MAXIT; ++it) {
+                if (it >= nit) break;
                 const int c = quad + it * NQUAD;
                 float p = acc[it];
                 p += __shfl_xor_sync(0xffffffffu, p, 1);
@@ -308,10 +141,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_scan(const ScanArgs a) {
             }
             __syncthreads();
         } else {
-            // ---- DADE, increment 0 over the whole tile (staged) --------------------
-            int slot = unit % a.ns;
-            bool ok = wait_bounded(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1), WAIT_NS);
-            if (__syncthreads_or(!ok)) { aborted = true; break; }
+            // ---- phase A: increment 0 of the whole tile, streamed (bulk copy) ----------
+            const int slot = unit % a.ns;
+            if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1))) { aborted = true; break; }
             r2 = s_r2;
             {
                 const float *st = stage + (size_t)slot * a.tile * a.gb * 16;
@@ -344,76 +176,58 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_scan(const ScanArgs a) {
                 ++issued;
             }
             ++unit;
-            // ---- later increments: staged (j < units) or gathered ------------------
-            int ns_cur = s_cnt[0];
-            for (int j = 1; j < a.n_inc; ++j) {
-                const bool staged = j < units;
-                if (!staged && ns_cur == 0) break;
-                const int src = (j - 1) & 1, dst = j & 1;
-                if (tid == 0) s_cnt[dst] = 0;
-                if (staged) {
-                    slot = unit % a.ns;
-                    ok = wait_bounded(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1), WAIT_NS);
-                    if (__syncthreads_or(!ok)) { aborted = true; break; }
-                } else {
-                    __syncthreads();
-                }
-                if (ns_cur > 0) {
-                    const int b0 = j * a.gb, b1 = min(b0 + a.gb, a.nb);
-                    const bool last = j == a.n_inc - 1;
-                    const int dj = min((j + 1) * a.delta_d, a.d);
-                    const float cj = a.coef[j] * r2;
-                    const Surv *in = src ? l1 : l0;
-                    Surv *out = dst ? l1 : l0;
-                    const float *st = stage + (size_t)slot * a.tile * a.gb * 16;
-                    const int nits = (ns_cur + NQUAD - 1) / NQUAD;
-                    for (int it0 = 0; it0 < nits; it0 += GCHUNK) {
-                        // all loads of this lane's survivors first, then the reductions
-                        Surv sv[GCHUNK];
-                        float part[GCHUNK];
+            // ---- phase B: the survivors' remaining blocks, loaded ahead in registers -----
+            // Each quad owns one survivor and loads up to SPECB blocks of it at once (one
+            // round trip), then runs the increments in order on registers: partial sum
+            // over the increment's blocks, quad reduction, test P_d > coef_j r^2.  A
+            // pruned candidate stops loading; a warp whose candidates are all pruned
+            // stops early.  Candidates alive at d = D are accepted iff P_D <= r^2.
+            const int nS = s_cnt[0];
+            for (int r0 = 0; r0 < nS; r0 += NQUAD) {
+                const int sidx = r0 + quad;
+                const bool act = sidx < nS;
+                const Surv sv = act ? l0[sidx] : Surv{0, 0.f};
+                float p = sv.p, part = 0.f;
+                bool alive = act;
+                const float *row = lbase + (int64_t)(cc.i0 + sv.idx) * 16 + lq * 4;
+                int jj = 1, bend = min(2 * a.gb, a.nb);
+                for (int wb = a.gb; wb < a.nb; wb += a.spec) {
+                    if (!__any_sync(0xffffffffu, alive)) break;
+                    float4 o[SPECB];
 #pragma unroll
-                        for (int u = 0; u < GCHUNK; ++u) {
-                            const int s = quad + (it0 + u) * NQUAD;
-                            const bool act = it0 + u < nits && s < ns_cur;
-                            sv[u] = act ? in[s] : Surv{-1, 0.f};
-                            part[u] = 0.f;
-                            if (act)
-                                part[u] = staged
-                                    ? row_part(st + sv[u].idx * 16 + lq * 4, (int64_t)a.tile * 16, qv, b0, b1, lq, false)
-                                    : row_part(lbase + (int64_t)(cc.i0 + sv[u].idx) * 16 + lq * 4, bstride, qv, b0, b1,
-                                               lq, true);
-                        }
+                    for (int u = 0; u < SPECB; ++u) {
+                        const int bb = wb + u;
+                        o[u] = (u < a.spec && bb < a.nb && alive)
+                                   ? __ldg(reinterpret_cast<const float4 *>(row + (int64_t)bb * bstride))
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
 #pragma unroll
-                        for (int u = 0; u < GCHUNK; ++u) {
-                            if (it0 + u >= nits) break;
-                            float pp = part[u];
-                            pp += __shfl_xor_sync(0xffffffffu, pp, 1);
-                            pp += __shfl_xor_sync(0xffffffffu, pp, 2);
-                            const float p = sv[u].p + pp;
-                            const bool lead = sv[u].idx >= 0 && lq == 0;
-                            const bool toF = lead && last && p <= r2;
-                            const bool toN = lead && !last && !(p > cj);
-                            push(toF, fl, &s_cntF, sv[u].idx, p);
-                            push(toN, out, &s_cnt[dst], sv[u].idx, p);
-                            if (STATS && lead) {
-                                if (last) { st_dims += a.d; st_acc += toF; }
-                                else if (!toN) { st_dims += dj; ++st_prn; }
+                    for (int u = 0; u < SPECB; ++u) {
+                        const int bb = wb + u;
+                        if (u < a.spec && bb < a.nb) {
+                            part += sqd4(*reinterpret_cast<const float4 *>(qv + bb * 16 + lq * 4), o[u]);
+                            if (bb + 1 == bend) {        // end of increment jj
+                                part += __shfl_xor_sync(0xffffffffu, part, 1);
+                                part += __shfl_xor_sync(0xffffffffu, part, 2);
+                                if (alive) {
+                                    p += part;
+                                    if (jj < a.n_inc - 1 && p > a.coef[jj] * r2) {
+                                        alive = false;
+                                        if (STATS && lq == 0) { st_dims += min((jj + 1) * a.delta_d, a.d); ++st_prn; }
+                                    }
+                                }
+                                part = 0.f;
+                                ++jj;
+                                bend = min(bend + a.gb, a.nb);
                             }
                         }
                     }
                 }
-                __syncthreads();
-                if (staged) {
-                    if (tid == 0 && ic.p < a.nprobe) {
-                        issue(a, smeta, plist, ic, slot, stage, bars);
-                        advance(ic, units, a, smeta, plist);
-                        ++issued;
-                    }
-                    ++unit;
-                }
-                ns_cur = j == a.n_inc - 1 ? 0 : s_cnt[dst];
+                const bool take = alive && lq == 0 && p <= r2;
+                if (STATS && alive && lq == 0) { st_dims += a.d; st_acc += take; }
+                push(take, fl, &s_cntF, sv.idx, p);
             }
-            if (aborted) break;
+            __syncthreads();
         }
 
         // ---- merge accepted candidates into the K best ------------------------------
@@ -509,6 +323,9 @@ dade_status launch_nt(const ScanArgs &a, int64_t nq, size_t smem, bool fd, bool 
 
 } // namespace
 
+dade_status scan_pipelined(const scanning::ScanArgs &a, int64_t nq, int threads, cudaStream_t s);
+int pipe_depth_limit();
+
 dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s) {
     if (nq == 0) return DADE_OK;
     ScanArgs a{};
@@ -529,7 +346,7 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     a.k = p.k;
     a.tile = p.tile;
     a.ns = 2;
-    a.stage = p.stage;
+    a.spec = std::min(std::max(p.spec, 1), SPECB);
     const bool fd = p.mode == DADE_MODE_FD;
     if (fd) {
         a.gb = std::min(4, ix->nb);
@@ -540,6 +357,8 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     }
     a.n_inc = (ix->nb + a.gb - 1) / a.gb;
     for (int j = 0; j < DADE_MAX_DIM / DADE_BLOCK; ++j) a.coef[j] = j < p.n_inc ? p.coef[j] : INFINITY;
+    if (!fd && p.schedule == DADE_SCHED_PIPELINED && a.n_inc <= pipe_depth_limit())
+        return scan_pipelined(a, nq, p.threads, s);
     const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k, a.nprobe);
     if (L.total > 227 * 1024) {
         set_error("scan configuration needs more than 227 KB of shared memory (reduce tile or delta_d)");

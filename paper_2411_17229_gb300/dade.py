@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libdade.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EIO = range(7)
 MODE_DADE, MODE_FD = 0, 1
+SCHED_PIPELINED, SCHED_TILE = 0, 1
+PIPE_MAX = 8
 FIELD_MEAN, FIELD_BASIS, FIELD_EIGVAL, FIELD_CENTROIDS, FIELD_ASSIGN, FIELD_ROTATED, FIELD_RHO, FIELD_KMEANS_OBJ = range(8)
 MAX_DIM, MAX_K = 1024, 256
 
@@ -34,8 +36,8 @@ class BuildOpts(C.Structure):
 
 
 class SearchOpts(C.Structure):
-    _fields_ = [("mode", C.c_int32), ("tile", C.c_int32), ("stats", C.c_void_p), ("stage", C.c_int32),
-                ("threads", C.c_int32), ("reserved", C.c_int32 * 6)]
+    _fields_ = [("mode", C.c_int32), ("tile", C.c_int32), ("stats", C.c_void_p), ("spec", C.c_int32),
+                ("threads", C.c_int32), ("schedule", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class Info(C.Structure):
@@ -164,23 +166,23 @@ class Index:
         _check(lib().dade_probe(self._h, _ptr(q_rot), q_rot.shape[0], int(nprobe), _ptr(out), _stream(stream)))
         return out
 
-    def search(self, q_rot, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, stage=0,
-               threads=0, stream=None):
-        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), stage=stage, threads=threads)
+    def search(self, q_rot, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
+               threads=0, schedule=SCHED_PIPELINED, stream=None):
+        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule)
         _check(lib().dade_search(self._h, _ptr(q_rot), q_rot.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                  C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
-    def scan(self, q_rot, probe, k, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, stage=0,
-             threads=0, stream=None):
-        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), stage=stage, threads=threads)
+    def scan(self, q_rot, probe, k, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
+             threads=0, schedule=SCHED_PIPELINED, stream=None):
+        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule)
         _check(lib().dade_scan(self._h, _ptr(q_rot), _ptr(probe), q_rot.shape[0], int(k), probe.shape[1],
                                float(alpha), int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
-    def query(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, stage=0,
-              threads=0, stream=None):
-        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), stage=stage, threads=threads)
+    def query(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
+              threads=0, schedule=SCHED_PIPELINED, stream=None):
+        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule)
         _check(lib().dade_query(self._h, _ptr(q), q.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                 C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
@@ -209,6 +211,14 @@ class Index:
         out = np.empty(shape, dt)
         _check(lib().dade_index_export(self._h, field, out.ctypes.data, out.nbytes))
         return out
+
+
+def schedule_lag(d: int, delta_d: int, schedule: int = SCHED_PIPELINED) -> int:
+    """Tiles of threshold lag of a DADE search (see dade_schedule)."""
+    nb = (d + 15) // 16
+    gb = min(delta_d // 16, nb)
+    n_inc = (nb + gb - 1) // gb
+    return n_inc - 1 if schedule == SCHED_PIPELINED and n_inc <= PIPE_MAX else 0
 
 
 def host_sym_eig(a):

@@ -13,8 +13,10 @@ Tolerance (stated here, used by every parity test):
     norms involved, so the absolute term only matters for distances far
     below the data's scale (near-duplicates).
   * flagged queries are validated instead: ids distinct and from the
-    database, distances exact for those ids, ascending order; their count
-    must stay small.
+    database, distances exact for those ids, ascending order, and at least
+    90% of the oracle's ids present (a flipped near-tie decision moves a few
+    results, not the list).  A query runs thousands of threshold tests, so
+    the flagged fraction grows with nprobe and K; it must stay below 30%.
 """
 from __future__ import annotations
 
@@ -36,7 +38,7 @@ def _runs(d, tol=TIE_TOL):
     return runs
 
 
-def compare(g_ids, g_d, o_ids, o_d, flags, scale, exact_d=None, max_flagged_frac=0.1):
+def compare(g_ids, g_d, o_ids, o_d, flags, scale, exact_d=None, max_flagged_frac=0.3):
     """Assert GPU results (g_*) match the oracle's (o_*).  exact_d(q, ids) -> FP64
     distances, used to validate flagged queries.  Returns a summary dict."""
     nq, K = o_ids.shape
@@ -58,6 +60,8 @@ def compare(g_ids, g_d, o_ids, o_d, flags, scale, exact_d=None, max_flagged_frac
                 ex = exact_d(q, g_ids[q][valid])
                 assert np.all(np.abs(g_d[q][valid] - ex) <= RTOL * ex + atol)
                 assert np.all(np.diff(g_d[q][valid]) >= 0)
+            ov = len(set(g_ids[q].tolist()) & set(o_ids[q].tolist()))
+            assert ov >= int(np.ceil(0.9 * int((o_ids[q] >= 0).sum()))), f"query {q}: overlap {ov} of {K}"
             continue
         assert ok_ids, f"query {q}: ids differ\n gpu {g_ids[q]}\n orc {o_ids[q]}\n gd {g_d[q]}\n od {o_d[q]}"
         fin = np.isfinite(o_d[q])

@@ -347,6 +347,23 @@ def pin_search_schedules(o):
     assert np.array_equal(c[0], d[0]) and np.array_equal(c[2], d[2])
 
 
+def pin_search_lagged_tiles(o):
+    """Lagged tile schedule: lag 0 is the plain tile schedule; a lag longer
+    than the scan never refreshes the threshold, so nothing is pruned and the
+    result is FDScanning's over the same lists; a lag only prunes less."""
+    X, Xr, lam, cent, assign, Q, Qr = _tiny_index(o)
+    eps = _eps_for(o, Xr, lam, 8, 0.2)
+    a = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, eps, schedule=1, tile=16)
+    b = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, eps, schedule=1, tile=16, lag=0)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    fd = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, None, schedule=1, tile=16)
+    big = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, eps, schedule=1, tile=16, lag=10**6)
+    assert np.array_equal(big[0], fd[0]) and np.all(big[2][:, 3] == 0)
+    lagged = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, eps, schedule=1, tile=16, lag=3)
+    assert np.all(lagged[2][:, 0] == a[2][:, 0])
+    assert lagged[2][:, 3].sum() <= a[2][:, 3].sum()
+
+
 def pin_search_short_lists(o):
     """Fewer candidates than K: the missing slots are (-1, +inf)."""
     X, Xr, lam, cent, assign, Q, Qr = _tiny_index(o, n=40, nc=7, dup=False)

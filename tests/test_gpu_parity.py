@@ -42,20 +42,23 @@ class Case:
         self.Qr = self.orc.rotate(queries)
         self.scale = float(np.mean((self.orc.Xr ** 2).sum(1)))
 
-    def gpu_search(self, k, nprobe, alpha, delta_d, mode=dade.MODE_DADE, tile=128, stats=False):
+    def gpu_search(self, k, nprobe, alpha, delta_d, mode=dade.MODE_DADE, tile=128, stats=False,
+                   schedule=dade.SCHED_TILE, threads=0):
         nq = self.queries.shape[0]
         ids = torch.empty(nq, k, dtype=torch.int64, device="cuda")
         d = torch.empty(nq, k, dtype=torch.float32, device="cuda")
         st = torch.zeros(nq, 4, dtype=torch.int64, device="cuda") if stats else None
-        self.gpu.search(self.q_rot, k, nprobe, alpha, delta_d, ids, d, mode=mode, tile=tile, stats=st)
+        self.gpu.search(self.q_rot, k, nprobe, alpha, delta_d, ids, d, mode=mode, tile=tile, stats=st,
+                        schedule=schedule, threads=threads)
         self.gpu.sync()
         out = ids.cpu().numpy(), d.cpu().numpy()
         return out + ((st.cpu().numpy(),) if stats else ())
 
-    def oracle_search(self, k, nprobe, alpha, delta_d, fd=False, tile=128):
+    def oracle_search(self, k, nprobe, alpha, delta_d, fd=False, tile=128, schedule=dade.SCHED_TILE):
         eps = None if fd else self.orc.eps(np.float32(alpha), delta_d)
+        lag = 0 if fd else dade.schedule_lag(self.base.shape[1], delta_d, schedule)
         return self.orc.o.search(self.orc.Xr, self.assign, self.orc.cent, self.orc.lam, self.Qr, k, nprobe,
-                                 delta_d if not fd else 64, eps, schedule=oracle.TILE, tile=tile)
+                                 delta_d if not fd else 64, eps, schedule=oracle.TILE, tile=tile, lag=lag)
 
     def exact_d(self, q, ids):
         return ((self.orc.Xr[ids] - self.Qr[q]) ** 2).sum(1)
@@ -151,21 +154,26 @@ def test_probe_parity(c1, mix, nprobe):
     (100, 16, 0.05, 32, 256),
     (256, 8, 0.2, 32, 96),
 ])
-def test_search_parity_c1(c1, k, nprobe, alpha, delta_d, tile):
-    g_ids, g_d, g_st = c1.gpu_search(k, nprobe, alpha, delta_d, tile=tile, stats=True)
-    o_ids, o_d, o_st, flags = c1.oracle_search(k, nprobe, alpha, delta_d, tile=tile)
+@pytest.mark.parametrize("schedule,threads", [(dade.SCHED_TILE, 128), (dade.SCHED_PIPELINED, 128),
+                                              (dade.SCHED_PIPELINED, 256)])
+def test_search_parity_c1(c1, k, nprobe, alpha, delta_d, tile, schedule, threads):
+    g_ids, g_d, g_st = c1.gpu_search(k, nprobe, alpha, delta_d, tile=tile, stats=True, schedule=schedule,
+                                     threads=threads)
+    o_ids, o_d, o_st, flags = c1.oracle_search(k, nprobe, alpha, delta_d, tile=tile, schedule=schedule)
     parity.compare(g_ids, g_d, o_ids, o_d, flags, c1.scale, c1.exact_d)
     # the work done is the same: candidates exactly, the rest where no near-tie occurred
     assert np.array_equal(g_st[:, 0], o_st[:, 0])
     clean = flags == 0
     assert np.array_equal(g_st[clean, 1:], o_st[clean, 1:])
-    assert np.all(g_st[:, 1] < g_st[:, 0] * 128)   # DADE used fewer dimensions than FDScanning
+    if schedule == dade.SCHED_TILE:   # a deep pipeline on a short scan may never refresh its threshold
+        assert np.all(g_st[:, 1] < g_st[:, 0] * 128)   # DADE used fewer dimensions than FDScanning
 
 
 @pytest.mark.parametrize("k,nprobe,alpha,delta_d", [(10, 4, 0.1, 16), (10, 2, 0.05, 32), (50, 6, 0.2, 64)])
-def test_search_parity_mixture(mix, k, nprobe, alpha, delta_d):
-    g_ids, g_d = mix.gpu_search(k, nprobe, alpha, delta_d)
-    o_ids, o_d, _, flags = mix.oracle_search(k, nprobe, alpha, delta_d)
+@pytest.mark.parametrize("schedule", [dade.SCHED_TILE, dade.SCHED_PIPELINED])
+def test_search_parity_mixture(mix, k, nprobe, alpha, delta_d, schedule):
+    g_ids, g_d = mix.gpu_search(k, nprobe, alpha, delta_d, schedule=schedule)
+    o_ids, o_d, _, flags = mix.oracle_search(k, nprobe, alpha, delta_d, schedule=schedule)
     parity.compare(g_ids, g_d, o_ids, o_d, flags, mix.scale, mix.exact_d)
 
 
@@ -207,20 +215,22 @@ def test_exhaustive_fd_is_exact_knn():
     assert gi[5, 0] == 7 and gi[5, 1] == 1500   # equal distance 0: lower id first
 
 
-@pytest.mark.parametrize("d,nlists,delta_d", [(16, 3, 16), (20, 5, 16), (40, 4, 32), (48, 6, 32), (64, 2, 64),
-                                              (33, 7, 1024)])
+@pytest.mark.parametrize("d,nlists,delta_d", [(16, 3, 16), (20, 5, 16), (40, 4, 32), (48, 6, 32), (64, 3, 64),
+                                              (33, 7, 1024), (160, 5, 16)])
 def test_odd_shapes(d, nlists, delta_d):
     """D not a multiple of 16 or of delta_d, delta_d >= D, empty lists, K > candidates."""
     rng = np.random.default_rng(d)
     base = (rng.standard_normal((700, d)) * np.linspace(2.0, 0.2, d)).astype(np.float32)
     queries = (rng.standard_normal((25, d)) * np.linspace(2.0, 0.2, d)).astype(np.float32)
     assign = synth.zipf_assign(700, nlists, s=1.5)
-    assign[assign == nlists - 1] = 0          # one empty list
+    if nlists >= 3:
+        assign[assign == 1] = 2               # one empty list (its centroid is the origin)
     case = Case(base, queries, assign, nlists, n_pairs=3000)
     for k, nprobe in ((5, 1), (200, 2), (10, nlists)):
-        g_ids, g_d = case.gpu_search(k, nprobe, 0.1, delta_d, tile=32)
-        o_ids, o_d, _, flags = case.oracle_search(k, nprobe, 0.1, delta_d, tile=32)
-        parity.compare(g_ids, g_d, o_ids, o_d, flags, case.scale, case.exact_d)
+        for schedule in (dade.SCHED_TILE, dade.SCHED_PIPELINED):
+            g_ids, g_d = case.gpu_search(k, nprobe, 0.1, delta_d, tile=32, schedule=schedule)
+            o_ids, o_d, _, flags = case.oracle_search(k, nprobe, 0.1, delta_d, tile=32, schedule=schedule)
+            parity.compare(g_ids, g_d, o_ids, o_d, flags, case.scale, case.exact_d)
 
 
 def test_empty_batch_and_invalid(c1):
