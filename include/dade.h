@@ -213,6 +213,28 @@ dade_status dade_query(const dade_index *ix, const float *q, int64_t nq, int32_t
                        float alpha, int32_t delta_d, const dade_search_opts *opts, int64_t *ids,
                        float *dists, dade_stream stream);
 
+/* Largest nq * n_clusters one dade_probe_noalloc call accepts (16 MiB of floats). */
+enum { DADE_PROBE_NOALLOC_MAX = 4194304 };
+
+/*
+ * dade_probe without any device memory allocation (the paper has no
+ * counterpart; this is a library facility).  For callers that must not call
+ * cudaMalloc: code running while a stream is being captured into a CUDA
+ * graph, a serving path that must not block on or fail in the allocator in
+ * the middle of a request, or a process whose device memory belongs to
+ * another framework's arena.  Same inputs, outputs and results as
+ * dade_probe, but q_rot and probe must be device pointers, and the query x
+ * list distance matrix lives in a fixed 16 MiB array that the library holds
+ * on every GPU that loads it (until exit) instead of in the index workspace.
+ * nq * n_clusters above DADE_PROBE_NOALLOC_MAX is rejected with DADE_EINVAL.
+ * The first call on a device looks up that array's device address (with the
+ * device current), so make it before capturing a stream.  All calls share
+ * the array: calls whose work can overlap on the GPU (unordered streams)
+ * race and must be serialised by the caller.
+ */
+dade_status dade_probe_noalloc(const dade_index *ix, const float *q_rot, int64_t nq, int32_t nprobe,
+                               int32_t *probe, dade_stream stream);
+
 /*
  * Reserve workspace for searches of up to max_nq queries with up to
  * max_nprobe lists, so that later calls within these limits allocate nothing

@@ -7,6 +7,9 @@
 // (float bits of the distance << 32 | list id) by an 8-pass radix select over
 // 8-bit digits; keys are unique, so exactly nprobe keys are <= the selected
 // one, and a final rank sort orders them.  The result is deterministic.
+#include <mutex>
+#include <string>
+
 #include "internal.cuh"
 #include "tiles.cuh"
 
@@ -123,4 +126,93 @@ dade_status probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t 
     return launch_check("k_probe_select");
 }
 
+// ------------------------------------------------------------------------------
+// Probe without device allocations.
+//
+// dade_probe() keeps its query x centroid distance matrix in the index's
+// workspace, which grows with cudaMalloc on demand.  Some callers must not
+// allocate device memory at all: a call made while a stream is being captured
+// into a CUDA graph (cudaMalloc is not allowed during capture), a serving
+// path that must not block on or fail in the allocator in the middle of a
+// request, or a process whose device memory is owned by another framework's
+// arena.  dade_probe_noalloc() runs the same two kernels with the distance
+// matrix in the fixed array below instead.
+//
+// The array is a file-scope device variable: every GPU that loads this
+// library reserves DADE_PROBE_NOALLOC_MAX floats (16 MiB) for it until the
+// process exits.  Host code cannot pass the variable's name to a kernel (in
+// host code it is only a stand-in for the symbol), so the first call on each
+// device looks up the array's device address with cudaGetSymbolAddress, with
+// that device current, and caches it.  All calls share the one array: calls
+// whose work overlaps on the GPU (different streams, no ordering between
+// them) race on it.  Every entry that a call reads was written by the same
+// call first, so nothing needs clearing between calls.
+static __device__ __align__(256) float g_probe_scratch[DADE_PROBE_NOALLOC_MAX];
+
+namespace {
+constexpr int kMaxDevices = 64;
+float *g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+
+dade_status scratch_address(float **out) {
+    int dev = 0;
+    DADE_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("dade_probe_noalloc: device ordinal beyond the supported range");
+        return DADE_EUNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_probe_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            set_error(std::string("dade_probe_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+            return DADE_ECUDA;
+        }
+        g_scratch_addr[dev] = static_cast<float *>(p);
+    }
+    *out = g_scratch_addr[dev];
+    return DADE_OK;
+}
+
+bool on_device(const void *p) {
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+} // namespace
+
 } // namespace dade
+
+extern "C" dade_status dade_probe_noalloc(const dade_index *ix, const float *q_rot, int64_t nq, int32_t nprobe,
+                                          int32_t *probe, dade_stream stream) {
+    using namespace dade;
+    set_error("");
+    DADE_CHECK_ARG(ix != nullptr, "index is NULL");
+    DADE_CHECK_ARG(nq >= 0, "nq < 0");
+    DADE_CHECK_ARG(nprobe >= 1 && nprobe <= ix->nc && nprobe <= 8192, "nprobe outside 1..min(n_clusters, 8192)");
+    if (nq == 0) return DADE_OK;
+    DADE_CHECK_ARG(q_rot != nullptr && probe != nullptr, "NULL pointer");
+    if (nq * (int64_t)ix->nc > (int64_t)DADE_PROBE_NOALLOC_MAX) {
+        set_error("invalid argument: dade_probe_noalloc handles at most DADE_PROBE_NOALLOC_MAX (4194304) "
+                  "query x list distances per call (nq * n_clusters = " + std::to_string(nq * (int64_t)ix->nc) +
+                  "); split the batch");
+        return DADE_EINVAL;
+    }
+    DADE_CHECK_ARG(on_device(q_rot) && on_device(probe),
+                   "dade_probe_noalloc takes device pointers only (host buffers would need staging memory)");
+    float *dist = nullptr;
+    DADE_TRY(scratch_address(&dist));
+    cudaStream_t s = (cudaStream_t)stream;
+    dim3 g((unsigned)((nq + L2T_ROWS - 1) / L2T_ROWS), (unsigned)((ix->nc + L2T_COLS - 1) / L2T_COLS));
+    k_probe_dist<<<g, L2T_THREADS, 0, s>>>(q_rot, nq, ix->d, ix->d, ix->cent.as<float>(), ix->nc, ix->dp, dist);
+    DADE_TRY(launch_check("k_probe_dist"));
+    size_t smem = sizeof(unsigned long long) * (size_t)nprobe;
+    if (smem > 48 * 1024)
+        DADE_TRY_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_probe_select<<<(unsigned)nq, SEL_THREADS, smem, s>>>(dist, ix->nc, nprobe, probe);
+    return launch_check("k_probe_select");
+}

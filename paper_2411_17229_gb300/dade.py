@@ -21,6 +21,7 @@ SCHED_PIPELINED, SCHED_TILE = 0, 1
 PIPE_MAX = 8
 FIELD_MEAN, FIELD_BASIS, FIELD_EIGVAL, FIELD_CENTROIDS, FIELD_ASSIGN, FIELD_ROTATED, FIELD_RHO, FIELD_KMEANS_OBJ = range(8)
 MAX_DIM, MAX_K = 1024, 256
+PROBE_NOALLOC_MAX = 4194304
 
 
 class DadeError(RuntimeError):
@@ -63,6 +64,7 @@ SIGNATURES = {
     "dade_index_export": (_i32, [_vp, _i32, _vp, C.c_size_t]),
     "dade_host_sym_eig": (_i32, [_vp, _i32, _vp, _vp]),
     "dade_sync": (_i32, [_vp, _vp]),
+    "dade_probe_noalloc": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
     "dade_last_error": (C.c_char_p, []),
     "dade_version": (C.c_char_p, []),
 }
