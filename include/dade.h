@@ -75,7 +75,7 @@ typedef enum {
  * each list in tiles of opts->tile candidates (ascending base id; a tile
  * never spans two lists).  Every candidate of a tile is tested against the
  * K-th distance r held when the tile starts:
- *   DADE_SCHED_TILE       r after all earlier tiles (tile-synchronous);
+ *   DADE_SCHED_TILE       r after all earlier tiles (tile-synchronous; default);
  *   DADE_SCHED_PIPELINED  r after all tiles but the n_inc - 1 just before it,
  *                         where n_inc = ceil(ceil(D/16) / (delta_d/16)) is the
  *                         number of increments: up to n_inc tiles are in flight
@@ -84,9 +84,14 @@ typedef enum {
  * A staler threshold can only prune less.  FDScanning ignores the schedule.
  */
 typedef enum {
-    DADE_SCHED_PIPELINED = 0,
-    DADE_SCHED_TILE = 1
+    DADE_SCHED_TILE = 0,
+    DADE_SCHED_PIPELINED = 1
 } dade_schedule;
+
+/* dade_search_opts.flags */
+enum {
+    DADE_FLAG_GENERIC_KERNEL = 1   /* skip the kernels specialised for D <= 128 (testing) */
+};
 
 /* Index construction options.  Zero-initialise, then call dade_build_opts_default(). */
 typedef struct {
@@ -110,8 +115,9 @@ typedef struct {
     int32_t spec;              /* tile schedule: 16-dim blocks of a candidate that survived the first
                                   increment loaded together ahead of its tests (1..8, default 8) */
     int32_t threads;           /* threads per query's CTA: 0 (default 128), 128 or 256 */
-    int32_t schedule;          /* dade_schedule (default DADE_SCHED_PIPELINED) */
-    int32_t reserved[5];
+    int32_t schedule;          /* dade_schedule (default DADE_SCHED_TILE) */
+    int32_t flags;             /* DADE_FLAG_* bits */
+    int32_t reserved[4];
 } dade_search_opts;
 
 /* Description of a built index. */

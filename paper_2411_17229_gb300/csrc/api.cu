@@ -162,7 +162,8 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.mode = opts ? opts->mode : DADE_MODE_DADE;
     p.spec = opts && opts->spec > 0 ? opts->spec : 8;
     p.threads = opts && opts->threads ? opts->threads : 128;
-    p.schedule = opts ? opts->schedule : DADE_SCHED_PIPELINED;
+    p.schedule = opts ? opts->schedule : DADE_SCHED_TILE;
+    p.generic = opts ? (opts->flags & DADE_FLAG_GENERIC_KERNEL) != 0 : 0;
     p.delta_d = delta_d;
     if (p.mode == DADE_MODE_DADE) p.n_inc = coef_table(ix, alpha, delta_d, nullptr, p.coef);
     else p.n_inc = 0;

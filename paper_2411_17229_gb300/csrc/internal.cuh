@@ -106,7 +106,7 @@ struct ScanParams {
     const float *q_rot;      // [nq][q_stride]
     int32_t q_stride;
     const int32_t *probe;    // [nq][nprobe]
-    int32_t nprobe, k, tile, mode, delta_d, n_inc, spec, threads, schedule;
+    int32_t nprobe, k, tile, mode, delta_d, n_inc, spec, threads, schedule, generic;
     float coef[DADE_MAX_DIM / DADE_BLOCK];   // per increment; prune iff P > coef[j] * r2
     int64_t *ids;            // [nq][k]
     float *dists;            // [nq][k]

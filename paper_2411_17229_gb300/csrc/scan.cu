@@ -325,6 +325,8 @@ dade_status launch_nt(const ScanArgs &a, int64_t nq, size_t smem, bool fd, bool 
 
 dade_status scan_pipelined(const scanning::ScanArgs &a, int64_t nq, int threads, cudaStream_t s);
 int pipe_depth_limit();
+bool scan_fast_applies(const scanning::ScanArgs &a, bool fd);
+dade_status scan_fast(const scanning::ScanArgs &a, int64_t nq, bool fd, int threads, cudaStream_t s);
 
 dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s) {
     if (nq == 0) return DADE_OK;
@@ -359,6 +361,7 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     for (int j = 0; j < DADE_MAX_DIM / DADE_BLOCK; ++j) a.coef[j] = j < p.n_inc ? p.coef[j] : INFINITY;
     if (!fd && p.schedule == DADE_SCHED_PIPELINED && a.n_inc <= pipe_depth_limit())
         return scan_pipelined(a, nq, p.threads, s);
+    if (scan_fast_applies(a, fd) && !p.generic) return scan_fast(a, nq, fd, p.threads, s);
     const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k, a.nprobe);
     if (L.total > 227 * 1024) {
         set_error("scan configuration needs more than 227 KB of shared memory (reduce tile or delta_d)");

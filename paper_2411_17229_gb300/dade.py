@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libdade.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EIO = range(7)
 MODE_DADE, MODE_FD = 0, 1
-SCHED_PIPELINED, SCHED_TILE = 0, 1
+SCHED_TILE, SCHED_PIPELINED = 0, 1
+FLAG_GENERIC_KERNEL = 1
 PIPE_MAX = 8
 FIELD_MEAN, FIELD_BASIS, FIELD_EIGVAL, FIELD_CENTROIDS, FIELD_ASSIGN, FIELD_ROTATED, FIELD_RHO, FIELD_KMEANS_OBJ = range(8)
 MAX_DIM, MAX_K = 1024, 256
@@ -38,7 +39,8 @@ class BuildOpts(C.Structure):
 
 class SearchOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tile", C.c_int32), ("stats", C.c_void_p), ("spec", C.c_int32),
-                ("threads", C.c_int32), ("schedule", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("threads", C.c_int32), ("schedule", C.c_int32), ("flags", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class Info(C.Structure):
@@ -169,22 +171,25 @@ class Index:
         return out
 
     def search(self, q_rot, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-               threads=0, schedule=SCHED_PIPELINED, stream=None):
-        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule)
+               threads=0, schedule=SCHED_TILE, flags=0, stream=None):
+        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
+                       flags=flags)
         _check(lib().dade_search(self._h, _ptr(q_rot), q_rot.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                  C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def scan(self, q_rot, probe, k, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-             threads=0, schedule=SCHED_PIPELINED, stream=None):
-        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule)
+             threads=0, schedule=SCHED_TILE, flags=0, stream=None):
+        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
+                       flags=flags)
         _check(lib().dade_scan(self._h, _ptr(q_rot), _ptr(probe), q_rot.shape[0], int(k), probe.shape[1],
                                float(alpha), int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def query(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-              threads=0, schedule=SCHED_PIPELINED, stream=None):
-        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule)
+              threads=0, schedule=SCHED_TILE, flags=0, stream=None):
+        o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
+                       flags=flags)
         _check(lib().dade_query(self._h, _ptr(q), q.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                 C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
@@ -215,7 +220,7 @@ class Index:
         return out
 
 
-def schedule_lag(d: int, delta_d: int, schedule: int = SCHED_PIPELINED) -> int:
+def schedule_lag(d: int, delta_d: int, schedule: int = SCHED_TILE) -> int:
     """Tiles of threshold lag of a DADE search (see dade_schedule)."""
     nb = (d + 15) // 16
     gb = min(delta_d // 16, nb)

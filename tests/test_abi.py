@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(L):
 
 def test_struct_layouts_match_header(L):
     assert C.sizeof(dade.BuildOpts) == 4 + 4 + 8 + 8 + 8 * 3 + 4 * 8
-    assert C.sizeof(dade.SearchOpts) == 4 + 4 + 8 + 4 + 4 + 4 * 6
+    assert C.sizeof(dade.SearchOpts) == 4 + 4 + 8 + 4 * 8
     assert C.sizeof(dade.Info) == 8 + 4 * 4 + 8 * 3 + 8
 
 

@@ -43,13 +43,13 @@ class Case:
         self.scale = float(np.mean((self.orc.Xr ** 2).sum(1)))
 
     def gpu_search(self, k, nprobe, alpha, delta_d, mode=dade.MODE_DADE, tile=128, stats=False,
-                   schedule=dade.SCHED_TILE, threads=0):
+                   schedule=dade.SCHED_TILE, threads=0, flags=0):
         nq = self.queries.shape[0]
         ids = torch.empty(nq, k, dtype=torch.int64, device="cuda")
         d = torch.empty(nq, k, dtype=torch.float32, device="cuda")
         st = torch.zeros(nq, 4, dtype=torch.int64, device="cuda") if stats else None
         self.gpu.search(self.q_rot, k, nprobe, alpha, delta_d, ids, d, mode=mode, tile=tile, stats=st,
-                        schedule=schedule, threads=threads)
+                        schedule=schedule, threads=threads, flags=flags)
         self.gpu.sync()
         out = ids.cpu().numpy(), d.cpu().numpy()
         return out + ((st.cpu().numpy(),) if stats else ())
@@ -154,11 +154,12 @@ def test_probe_parity(c1, mix, nprobe):
     (100, 16, 0.05, 32, 256),
     (256, 8, 0.2, 32, 96),
 ])
-@pytest.mark.parametrize("schedule,threads", [(dade.SCHED_TILE, 128), (dade.SCHED_PIPELINED, 128),
-                                              (dade.SCHED_PIPELINED, 256)])
-def test_search_parity_c1(c1, k, nprobe, alpha, delta_d, tile, schedule, threads):
+@pytest.mark.parametrize("schedule,threads,flags", [(dade.SCHED_TILE, 128, 0), (dade.SCHED_TILE, 256, 0),
+                                                    (dade.SCHED_TILE, 128, dade.FLAG_GENERIC_KERNEL),
+                                                    (dade.SCHED_PIPELINED, 128, 0), (dade.SCHED_PIPELINED, 256, 0)])
+def test_search_parity_c1(c1, k, nprobe, alpha, delta_d, tile, schedule, threads, flags):
     g_ids, g_d, g_st = c1.gpu_search(k, nprobe, alpha, delta_d, tile=tile, stats=True, schedule=schedule,
-                                     threads=threads)
+                                     threads=threads, flags=flags)
     o_ids, o_d, o_st, flags = c1.oracle_search(k, nprobe, alpha, delta_d, tile=tile, schedule=schedule)
     parity.compare(g_ids, g_d, o_ids, o_d, flags, c1.scale, c1.exact_d)
     # the work done is the same: candidates exactly, the rest where no near-tie occurred
@@ -178,8 +179,10 @@ def test_search_parity_mixture(mix, k, nprobe, alpha, delta_d, schedule):
 
 
 @pytest.mark.parametrize("k,nprobe", [(10, 8), (100, 16)])
-def test_fd_parity(c1, k, nprobe):
-    g_ids, g_d, g_st = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD, stats=True)
+@pytest.mark.parametrize("threads,flags", [(128, 0), (256, 0), (256, dade.FLAG_GENERIC_KERNEL)])
+def test_fd_parity(c1, k, nprobe, threads, flags):
+    g_ids, g_d, g_st = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD, stats=True, threads=threads,
+                                     flags=flags)
     o_ids, o_d, o_st, flags = c1.oracle_search(k, nprobe, 0.1, 32, fd=True)
     parity.compare(g_ids, g_d, o_ids, o_d, flags, c1.scale, c1.exact_d)
     assert np.array_equal(g_st[:, 0], o_st[:, 0])
