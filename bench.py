@@ -351,6 +351,8 @@ def run_ours(args):
                             if dade_best is None or ms < dade_best[0]:
                                 dade_best = (ms, rc, pt)
                             break
+    for ms_, rc_, pt_ in sorted(tried, key=lambda t: t[0])[:12]:
+        log(f"[bench]   {ms_:.3f} ms recall {rc_:.4f} {pt_}")
     log(f"[bench] autotune {time.time() - t0:.1f}s: FD {fd_best[2] if fd_best else None} "
         f"{fd_best[0] if fd_best else 0:.3f} ms; DADE {dade_best[2] if dade_best else None} "
         f"{dade_best[0] if dade_best else 0:.3f} ms")
@@ -372,6 +374,7 @@ def run_ours(args):
 
     def step(ev):
         ix.rotate(q, qr, stream=sh)
+        ev[3].record(stream)
         ix.probe(qr, point["nprobe"], pr_step, stream=sh)
         ev[1].record(stream)
         ix.scan(qr, pr_step, K, point["alpha"], point["delta_d"], ids, dists, mode=point["mode"],
@@ -379,7 +382,7 @@ def run_ours(args):
                 stream=sh)
 
     for _ in range(args.warmup):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         flush.zero_()
         ev[0].record(stream)
         step(ev)
@@ -393,7 +396,7 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             ev[0].record(stream)
             step(ev)
             ev[2].record(stream)
@@ -405,6 +408,8 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     step_ms = [e[0].elapsed_time(e[2]) for e in events]
     scan_ms = [e[1].elapsed_time(e[2]) for e in events]
+    rot_ms = [e[0].elapsed_time(e[3]) for e in events]
+    probe_ms = [e[3].elapsed_time(e[1]) for e in events]
     lib.dade_sync(ix.handle, sh)
     total_ms = sum(step_ms)
     if world > 1:
@@ -476,6 +481,8 @@ def run_ours(args):
                        "l2": "index 512 MB > L2; 256 MB flush written between timed steps",
                        "parallelism": f"replicas x{world}"},
             "recall": round(rc_timed, 5),
+            "breakdown_ms": {"rotate": round(statistics.mean(rot_ms), 4), "probe": round(statistics.mean(probe_ms), 4),
+                             "scan": round(statistics.mean(scan_ms), 4)},
             "latency_ms": {"p50": round(float(np.percentile(step_ms, 50)), 4),
                            "p99": round(float(np.percentile(step_ms, 99)), 4), "per": "batch step"},
             "fd_baseline": {"value": round(fd_qps, 1), "unit": UNIT, "recall": round(fd_recall, 5),

@@ -384,7 +384,8 @@ dade_status dade_index_info(const dade_index *ix, dade_info *info) {
     info->max_list = ix->max_list;
     info->eps_kept = ix->eps_kept;
     info->data_bytes = (int64_t)ix->data.bytes;
-    info->device_bytes = (int64_t)(ix->data.bytes + ix->ids.bytes + ix->meta.bytes + ix->cent.bytes + ix->W32.bytes +
+    info->device_bytes = (int64_t)(ix->data.bytes + ix->ids.bytes + ix->meta.bytes + ix->cent.bytes + ix->cnorm.bytes +
+                                   ix->W32.bytes +
                                    ix->mu32.bytes + ix->errflag.bytes);
     info->kmeans_iters = (int32_t)ix->kmeans_obj.size();
     info->reserved = 0;

@@ -440,6 +440,7 @@ dade_status build_index(const float *base, int64_t n, int32_t d, const dade_buil
     }
     lsum.release();
     lcnt.release();
+    DADE_TRY(centroid_norms(ix, s));
     ix->assign.resize(n);
     DADE_TRY_CUDA(cudaMemcpyAsync(ix->assign.data(), asg.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
     DADE_TRY_CUDA(cudaStreamSynchronize(s));

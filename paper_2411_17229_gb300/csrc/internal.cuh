@@ -85,6 +85,7 @@ struct dade_index {
     dade::DevBuf W32;       // float [d][dp]: W^T applied as x' = sum_j (x_j - mu_j) W[j][k]
     dade::DevBuf mu32;      // float [d]
     dade::DevBuf cent;      // float [nc][dp] rotated centroids (zero padded)
+    dade::DevBuf cnorm;     // float [nc] squared norms of the centroids
     dade::DevBuf data;      // packed rotated vectors
     dade::DevBuf ids;       // int32 per slot (padding slots -1)
     dade::DevBuf meta;      // ListMeta [nc]
@@ -101,6 +102,7 @@ dade_status rotate(const float *x, int64_t n, int32_t d, int32_t out_stride, con
                    const float *mu32, int32_t dp, float *out, cudaStream_t s);
 dade_status probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t q_stride,
                   int32_t nprobe, int32_t *probe_out, cudaStream_t s);
+dade_status centroid_norms(dade_index *ix, cudaStream_t s);
 
 struct ScanParams {
     const float *q_rot;      // [nq][q_stride]

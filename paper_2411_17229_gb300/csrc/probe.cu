@@ -1,8 +1,8 @@
 // probe.cu -- IVF coarse probe (Section 3.4): the nprobe inverted lists whose
 // centroids are nearest to each rotated query, ordered by (distance, list id).
 //
-// Step 1 writes the query x centroid squared-distance matrix with the
-// register-tiled kernel of tiles.cuh (exact sum of squared differences).
+// Step 1 writes the query x centroid squared-distance matrix with a
+// register-blocked FP32 GEMM tile (||q||^2 + ||c||^2 - 2 <q, c>).
 // Step 2 selects, per query, the nprobe smallest 64-bit keys
 // (float bits of the distance << 32 | list id) by an 8-pass radix select over
 // 8-bit digits; keys are unique, so exactly nprobe keys are <= the selected
@@ -17,25 +17,124 @@ namespace dade {
 
 namespace {
 
-__global__ void __launch_bounds__(L2T_THREADS) k_probe_dist(const float *__restrict__ Q, int64_t nq, int ldq, int kdim,
-                                                            const float *__restrict__ cent, int nc, int ldc,
-                                                            float *__restrict__ dist) {
-    __shared__ L2TileSmem sm;
+// Squared distance of every query to every centroid as
+// ||q||^2 + ||c||^2 - 2 <q, c> (FP32; cnorm precomputed at build), clamped at
+// 0.  Register-blocked GEMM tile: a CTA of 256 threads covers 128 queries x
+// 128 centroids, each thread 8 x 8 outputs; K advances in steps of 16 through
+// double-buffered shared memory (stored k-major, padded against bank
+// conflicts), so every pair of float4 shared loads feeds 64 FMAs.
+constexpr int PQ = 128, PC = 128, PBK = 16, PPAD = 4;
+
+__global__ void __launch_bounds__(256) k_probe_gemm(const float *__restrict__ Q, int64_t nq, int ldq, int kdim,
+                                                    const float *__restrict__ cent, int nc, int ldc,
+                                                    const float *__restrict__ cnorm, float *__restrict__ dist) {
+    __shared__ __align__(16) float As[2][PBK][PQ + PPAD];
+    __shared__ __align__(16) float Bs[2][PBK][PC + PPAD];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t r0 = (int64_t)blockIdx.x * L2T_ROWS;
-    const int c0 = blockIdx.y * L2T_COLS;
-    float acc[4][4];
-    l2_tile(Q, nq, ldq, cent, nc, ldc, kdim, r0, c0, acc, sm);
+    const int64_t q0 = (int64_t)blockIdx.x * PQ;
+    const int c0 = blockIdx.y * PC;
+    float acc[8][8], qn[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int64_t r = r0 + ty * 4 + i;
-        if (r >= nq) continue;
+    for (int i = 0; i < 8; ++i) {
+        qn[i] = 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int c = c0 + tx * 4 + j;
-            if (c < nc) dist[r * nc + c] = acc[i][j];
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    }
+    // each thread moves 2 float4 of A and 2 of B per K step: rows r = e / 4, k4 = (e % 4) * 4
+    float4 ra[2], rb[2];
+    auto gload = [&](int k0) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int e = tid + t * 256, row = e >> 2, k4 = (e & 3) * 4;
+            const int64_t qr = q0 + row;
+            const int cr = c0 + row;
+            float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
+            if (qr < nq) {
+                const float *src = Q + qr * ldq + k0 + k4;
+                va.x = k0 + k4 + 0 < kdim ? src[0] : 0.f;
+                va.y = k0 + k4 + 1 < kdim ? src[1] : 0.f;
+                va.z = k0 + k4 + 2 < kdim ? src[2] : 0.f;
+                va.w = k0 + k4 + 3 < kdim ? src[3] : 0.f;
+            }
+            if (cr < nc) {
+                const float *src = cent + (int64_t)cr * ldc + k0 + k4;
+                vb.x = k0 + k4 + 0 < kdim ? src[0] : 0.f;
+                vb.y = k0 + k4 + 1 < kdim ? src[1] : 0.f;
+                vb.z = k0 + k4 + 2 < kdim ? src[2] : 0.f;
+                vb.w = k0 + k4 + 3 < kdim ? src[3] : 0.f;
+            }
+            ra[t] = va;
+            rb[t] = vb;
+        }
+    };
+    auto sstore = [&](int buf) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int e = tid + t * 256, row = e >> 2, k4 = (e & 3) * 4;
+            As[buf][k4 + 0][row] = ra[t].x;
+            As[buf][k4 + 1][row] = ra[t].y;
+            As[buf][k4 + 2][row] = ra[t].z;
+            As[buf][k4 + 3][row] = ra[t].w;
+            Bs[buf][k4 + 0][row] = rb[t].x;
+            Bs[buf][k4 + 1][row] = rb[t].y;
+            Bs[buf][k4 + 2][row] = rb[t].z;
+            Bs[buf][k4 + 3][row] = rb[t].w;
+        }
+    };
+    gload(0);
+    sstore(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < kdim; k0 += PBK) {
+        const bool more = k0 + PBK < kdim;
+        if (more) gload(k0 + PBK);
+#pragma unroll
+        for (int kk = 0; kk < PBK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 8 + 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                qn[i] = fmaf(av[i], av[i], qn[i]);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            }
+        }
+        if (more) {
+            sstore(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
         }
     }
+    float cn[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = c0 + tx * 8 + j;
+        cn[j] = c < nc ? cnorm[c] : 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t r = q0 + ty * 8 + i;
+        if (r >= nq) continue;
+        float *out = dist + r * nc + c0 + tx * 8;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (c0 + tx * 8 + j < nc) out[j] = fmaxf(0.f, fmaf(-2.f, acc[i][j], qn[i] + cn[j]));
+    }
+}
+
+// ||c||^2 of every centroid row (one warp per row).
+__global__ void k_row_sqnorm(const float *__restrict__ X, int n, int ld, int kdim, float *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= n) return;
+    float s = 0.f;
+    for (int k = lane; k < kdim; k += 32) s = fmaf(X[(int64_t)w * ld + k], X[(int64_t)w * ld + k], s);
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) out[w] = s;
 }
 
 constexpr int SEL_THREADS = 256;
@@ -58,9 +157,15 @@ __global__ void __launch_bounds__(SEL_THREADS) k_probe_select(const float *__res
         const int shift = 56 - 8 * pass;
         hist[tid] = 0;
         __syncthreads();
-        for (int j = tid; j < nc; j += SEL_THREADS) {
-            unsigned long long k = probe_key(row, j);
-            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        // Distances of one query share their leading bytes, so most keys of a
+        // pass fall into a few bins: lanes with equal bins add once per warp.
+        for (int j0 = 0; j0 < nc; j0 += SEL_THREADS) {
+            const int j = j0 + tid;
+            const unsigned long long k = j < nc ? probe_key(row, j) : 0ull;
+            const bool in = j < nc && (k & mask) == prefix;
+            const unsigned bin = in ? (unsigned)((k >> shift) & 255u) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
         }
         __syncthreads();
         if (tid < 32) {   // warp 0: find the digit where the cumulative count reaches rank
@@ -87,7 +192,15 @@ __global__ void __launch_bounds__(SEL_THREADS) k_probe_select(const float *__res
         prefix = s_prefix;
         rank = s_rank;
         mask |= 255ull << shift;
+        const unsigned here_cnt = hist[(prefix >> shift) & 255u];
         __syncthreads();
+        // After the four distance bytes: if every key with the selected
+        // distance is needed (no tie to break by id), select all keys whose
+        // distance is at most it.
+        if (pass == 3 && here_cnt == rank) {
+            prefix |= 0xffffffffull;
+            break;
+        }
     }
     // prefix is now the nprobe-th smallest key; gather the keys <= it
     if (tid == 0) s_cnt = 0;
@@ -111,14 +224,21 @@ __global__ void __launch_bounds__(SEL_THREADS) k_probe_select(const float *__res
 
 } // namespace
 
+dade_status centroid_norms(dade_index *ix, cudaStream_t s) {
+    DADE_TRY(ix->cnorm.alloc(sizeof(float) * (size_t)ix->nc));
+    k_row_sqnorm<<<(unsigned)((ix->nc * 32 + 255) / 256), 256, 0, s>>>(ix->cent.as<float>(), ix->nc, ix->dp, ix->d,
+                                                                      ix->cnorm.as<float>());
+    return launch_check("k_row_sqnorm");
+}
+
 dade_status probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t q_stride, int32_t nprobe,
                   int32_t *probe_out, cudaStream_t s) {
     if (nq == 0) return DADE_OK;
     DADE_TRY(ix->ws_dist.ensure(sizeof(float) * (size_t)nq * ix->nc));
-    dim3 g((unsigned)((nq + L2T_ROWS - 1) / L2T_ROWS), (unsigned)((ix->nc + L2T_COLS - 1) / L2T_COLS));
-    k_probe_dist<<<g, L2T_THREADS, 0, s>>>(q_rot, nq, q_stride, ix->d, ix->cent.as<float>(), ix->nc, ix->dp,
-                                           ix->ws_dist.as<float>());
-    DADE_TRY(launch_check("k_probe_dist"));
+    dim3 g((unsigned)((nq + PQ - 1) / PQ), (unsigned)((ix->nc + PC - 1) / PC));
+    k_probe_gemm<<<g, 256, 0, s>>>(q_rot, nq, q_stride, ix->d, ix->cent.as<float>(), ix->nc, ix->dp,
+                                   ix->cnorm.as<float>(), ix->ws_dist.as<float>());
+    DADE_TRY(launch_check("k_probe_gemm"));
     size_t smem = sizeof(unsigned long long) * (size_t)nprobe;
     if (smem > 48 * 1024)
         DADE_TRY_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -207,9 +327,10 @@ extern "C" dade_status dade_probe_noalloc(const dade_index *ix, const float *q_r
     float *dist = nullptr;
     DADE_TRY(scratch_address(&dist));
     cudaStream_t s = (cudaStream_t)stream;
-    dim3 g((unsigned)((nq + L2T_ROWS - 1) / L2T_ROWS), (unsigned)((ix->nc + L2T_COLS - 1) / L2T_COLS));
-    k_probe_dist<<<g, L2T_THREADS, 0, s>>>(q_rot, nq, ix->d, ix->d, ix->cent.as<float>(), ix->nc, ix->dp, dist);
-    DADE_TRY(launch_check("k_probe_dist"));
+    dim3 g((unsigned)((nq + PQ - 1) / PQ), (unsigned)((ix->nc + PC - 1) / PC));
+    k_probe_gemm<<<g, 256, 0, s>>>(q_rot, nq, ix->d, ix->d, ix->cent.as<float>(), ix->nc, ix->dp, ix->cnorm.as<float>(),
+                                   dist);
+    DADE_TRY(launch_check("k_probe_gemm"));
     size_t smem = sizeof(unsigned long long) * (size_t)nprobe;
     if (smem > 48 * 1024)
         DADE_TRY_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -1,5 +1,5 @@
-// tiles.cuh -- register-tiled squared-distance block shared by the coarse
-// probe (queries x centroids) and the k-means assignment (points x centroids).
+// tiles.cuh -- register-tiled squared-distance block used by the k-means
+// assignment (points x centroids).
 #pragma once
 
 #include <cuda_runtime.h>
