@@ -65,11 +65,14 @@ def parse():
                     help="profiling run: fixed --point, no autotune, ground truth, baselines or e2e")
     ap.add_argument("--point", default="nprobe=20,alpha=0.3,delta_d=64,tile=256,threads=128",
                     help="operating point of --profile (comma-separated key=value)")
+    ap.add_argument("--lead", default="bf16", choices=["none", "bf16", "fp8"],
+                    help="low-precision copy of the leading 64 dims built into the index; the autotuner "
+                         "tries the prefilter on it beside the FP32 path")
     return ap.parse_args()
 
 
 def parse_point(text, dade):
-    pt = {"mode": dade.MODE_DADE, "spec": 8, "schedule": dade.SCHED_TILE, "tile": 128, "threads": 128}
+    pt = {"mode": dade.MODE_DADE, "spec": 8, "schedule": dade.SCHED_TILE, "tile": 128, "threads": 128, "flags": 0}
     for kv in text.split(","):
         k, v = kv.split("=")
         pt[k.strip()] = float(v) if k.strip() == "alpha" else int(v)
@@ -86,7 +89,9 @@ def run_profile(args):
     n, nq = args.n or w.n, args.nq or w.nq
     nc = w.n_clusters if n == w.n else max(16, n // 244)
     base, queries, _ = synth.make(w, n=n, nq=nq)
-    ix = dade.Index(torch.from_numpy(base).cuda(), nc, kmeans_iters=w.kmeans_iters, seed=synth.SEED_KMEANS)
+    lf, ld = lead_opts(args, dade, w.d)
+    ix = dade.Index(torch.from_numpy(base).cuda(), nc, kmeans_iters=w.kmeans_iters, seed=synth.SEED_KMEANS,
+                    lead_format=lf, lead_dims=ld)
     q = torch.from_numpy(queries).cuda()
     pt = parse_point(args.point, dade)
     qr = torch.empty_like(q)
@@ -102,7 +107,8 @@ def run_profile(args):
         ix.rotate(q, qr)
         ix.probe(qr, pt["nprobe"], pr)
         ix.scan(qr, pr, w.k, pt.get("alpha", 0.1), pt.get("delta_d", 32), ids, dists, mode=pt["mode"],
-                tile=pt["tile"], spec=pt["spec"], threads=pt["threads"], schedule=pt["schedule"])
+                tile=pt["tile"], spec=pt["spec"], threads=pt["threads"], schedule=pt["schedule"],
+                flags=pt["flags"])
         e1.record()
         torch.cuda.synchronize()
         if i >= args.warmup:
@@ -112,6 +118,12 @@ def run_profile(args):
 
 
 # ----------------------------------------------------------------- helpers --
+def lead_opts(args, dade, d):
+    """Index build options of --lead: (format, leading dims)."""
+    lf = {"none": dade.LEAD_NONE, "bf16": dade.LEAD_BF16, "fp8": dade.LEAD_FP8}[args.lead]
+    return lf, (min(64, (d + 15) // 16 * 16) if lf else 0)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -176,7 +188,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-SCAN_SOURCES = ("scan.cu", "scan_fast.cu", "scan_pipe.cu", "scan_common.cuh")
+SCAN_SOURCES = ("scan.cu", "scan_fast.cu", "scan_fast.cuh", "scan_lead.cu", "scan_pipe.cu", "scan_common.cuh")
 
 
 def scan_source_hash():
@@ -191,9 +203,12 @@ def scan_kernel_name(point, d):
     nb = (d + 15) // 16
     if point["mode"] == 1:
         return f"k_fd_fast<{point['threads']}, 8>" if nb == 8 else "k_scan<FD>"
-    if point.get("schedule", 0) == 0 and nb == 8:
-        return f"k_dade_fast<{point['threads']}, 8, {min(point['delta_d'] // 16, 8)}>"
-    return "k_scan_pipe" if point.get("schedule", 0) == 1 else "k_scan<DADE>"
+    lead = point.get("flags", 0) & 2
+    if point.get("schedule", 0) == 0 and nb == 8 and point["delta_d"] // 16 in (1, 2, 4, 8):
+        return f"k_dade_fast<{point['threads']}, 8, {min(point['delta_d'] // 16, 8)}{', lead' if lead else ''}>"
+    if point.get("schedule", 0) == 1:
+        return "k_scan_pipe"
+    return "k_scan<DADE, lead>" if lead else "k_scan<DADE>"
 
 
 def recorded_traffic(point, workload):
@@ -208,7 +223,7 @@ def recorded_traffic(point, workload):
     if rec.get("scan_cu_sha256_16") != scan_source_hash() or rec.get("workload") != workload:
         return None
     if any(rec.get("point", {}).get(k) != point.get(k) for k in ("nprobe", "alpha", "delta_d", "spec", "threads",
-                                                                  "tile", "mode", "schedule")):
+                                                                  "tile", "mode", "schedule", "flags")):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -282,7 +297,8 @@ def run_ours(args):
     xb = torch.from_numpy(base).cuda()
     q = torch.from_numpy(queries).cuda()
     t0 = time.time()
-    ix = dade.Index(xb, nc, kmeans_iters=w.kmeans_iters, seed=synth.SEED_KMEANS)
+    lf, ld = lead_opts(args, dade, w.d)
+    ix = dade.Index(xb, nc, kmeans_iters=w.kmeans_iters, seed=synth.SEED_KMEANS, lead_format=lf, lead_dims=ld)
     torch.cuda.synchronize()
     log(f"[bench] index built in {time.time() - t0:.1f}s (max list {ix.info.max_list}, "
         f"{ix.info.data_bytes / 2**20:.0f} MiB packed)")
@@ -305,10 +321,10 @@ def run_ours(args):
             probes[nprobe] = pr
         return probes[nprobe]
 
-    def scan(pt, st=None):
+    def scan(pt, st=None, lead_st=None):
         ix.scan(qr, probe_for(pt["nprobe"]), K, pt.get("alpha", 0.1), pt.get("delta_d", 32), ids, dists,
                 mode=pt["mode"], tile=pt["tile"], stats=st, spec=pt.get("spec", 8), threads=pt["threads"],
-                schedule=pt.get("schedule", 0), stream=sh)
+                schedule=pt.get("schedule", 0), flags=pt.get("flags", 0), lead_stats=lead_st, stream=sh)
 
     def measure(pt, reps=4):
         scan(pt)
@@ -338,13 +354,14 @@ def run_ours(args):
     n0 = min(p for p in grid if fd_rec.get(p, 0) >= RECALL_TARGET) if fd_best else grid[-1]
     dade_best = None
     tried = []
-    variants = [(dade.SCHED_TILE, 8, tile, 128) for tile in (128, 192, 256)]
+    lead_flags = (0, dade.FLAG_LEAD) if lf else (0,)
+    variants = [(dade.SCHED_TILE, 8, tile, 128, fl) for tile in (128, 192, 256) for fl in lead_flags]
     for dd in (16, 32, 64):
         for alpha in (0.05, 0.1, 0.2, 0.3):
-            for schedule, spec, tile, threads in variants:
+            for schedule, spec, tile, threads, fl in variants:
                     for nprobe in [p for p in grid if p >= n0][:3]:
                         pt = {"mode": dade.MODE_DADE, "nprobe": nprobe, "alpha": alpha, "delta_d": dd,
-                              "spec": spec, "tile": tile, "threads": threads, "schedule": schedule}
+                              "spec": spec, "tile": tile, "threads": threads, "schedule": schedule, "flags": fl}
                         ms, rc = measure(pt)
                         tried.append((ms, rc, pt))
                         if rc >= RECALL_TARGET:
@@ -362,11 +379,22 @@ def run_ours(args):
 
     # ---- algorithmic bytes of the chosen point (stats pass, untimed) -----------------
     stats.zero_()
-    scan(point, st=stats)
+    use_lead = bool(point.get("flags", 0) & dade.FLAG_LEAD)
+    lead_st = torch.zeros(nq, dtype=torch.int64, device="cuda") if use_lead else None
+    scan(point, st=stats, lead_st=lead_st)
     torch.cuda.synchronize()
     st = stats.sum(0).cpu().numpy()
     cand, dims_sum, accepted = int(st[0]), int(st[1]), int(st[2])
-    alg_bytes = 4 * dims_sum + 4 * accepted   # FP32 rows touched + ids of accepted candidates
+    # FP32 rows touched + ids of accepted candidates; with the prefilter, every
+    # candidate reads its low-precision first increment and error norm, and the
+    # candidates it drops read no FP32 row at all
+    alg_bytes = 4 * dims_sum + 4 * accepted
+    lead_dropped = 0
+    if use_lead:
+        lead_dropped = int(lead_st.sum().item())
+        d0 = min(point["delta_d"], w.d)
+        es = 2 if lf == dade.LEAD_BF16 else 1
+        alg_bytes += (es * d0 + 4) * cand - 4 * d0 * lead_dropped
 
     # ---- timed region: K steps of rotate + probe + scan -------------------------------
     flush = torch.empty(64 * 2**20, dtype=torch.float32, device="cuda")
@@ -379,7 +407,7 @@ def run_ours(args):
         ev[1].record(stream)
         ix.scan(qr, pr_step, K, point["alpha"], point["delta_d"], ids, dists, mode=point["mode"],
                 tile=point["tile"], spec=point["spec"], threads=point["threads"], schedule=point["schedule"],
-                stream=sh)
+                flags=point["flags"], stream=sh)
 
     for _ in range(args.warmup):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -448,7 +476,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         ix.query(q_host, K, point["nprobe"], point["alpha"], point["delta_d"], ids_host, d_host, mode=point["mode"],
                  tile=point["tile"], spec=point["spec"], threads=point["threads"], schedule=point["schedule"],
-                 stream=sh)
+                 flags=point["flags"], stream=sh)
         if i >= args.warmup:
             e2e_s.append(time.perf_counter() - t1)
     e2e_qps = world * nq / statistics.mean(e2e_s)
@@ -478,6 +506,7 @@ def run_ours(args):
                        "nprobe": point["nprobe"], "alpha": point.get("alpha"), "delta_d": point.get("delta_d"),
                        "spec": point.get("spec"), "tile": point["tile"], "threads": point["threads"],
                        "schedule": "tile" if point.get("schedule", 0) == 0 else "pipelined",
+                       "lead_prefilter": ({"format": args.lead, "dims": ld} if use_lead else None),
                        "l2": "index 512 MB > L2; 256 MB flush written between timed steps",
                        "parallelism": f"replicas x{world}"},
             "recall": round(rc_timed, 5),
@@ -490,7 +519,7 @@ def run_ours(args):
                             "ms_per_step": round(statistics.mean(fd_ms), 4)},
             "dade_vs_fd": round(value / world / fd_qps, 3),
             "work": {"candidates": cand, "dims_per_candidate": round(dims_sum / max(1, cand), 2),
-                     "accepted": accepted},
+                     "accepted": accepted, "lead_dropped": lead_dropped},
             "roofline": roof,
             "e2e": {"value": round(e2e_qps, 1), "unit": UNIT, "h2d_bytes_per_step": nq * w.d * 4,
                     "d2h_bytes_per_step": nq * K * 12 + 4},

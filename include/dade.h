@@ -90,8 +90,35 @@ typedef enum {
 
 /* dade_search_opts.flags */
 enum {
-    DADE_FLAG_GENERIC_KERNEL = 1   /* skip the kernels specialised for D <= 128 (testing) */
+    DADE_FLAG_GENERIC_KERNEL = 1,  /* skip the kernels specialised for D <= 128 (testing) */
+    DADE_FLAG_LEAD = 2             /* prefilter the first increment on the index's low-precision copy
+                                      (DADE mode, tile schedule, min(delta_d, D_pad) <= lead_dims) */
 };
+
+/*
+ * Low-precision copy of the leading dimensions, a conservative prefilter for
+ * the first increment of a search (DADE_FLAG_LEAD).  The paper reads FP32
+ * throughout; this copy is an addition of this library.  For base vector o
+ * in list c the index stores, over the first lead_dims rotated dims, the
+ * residual r = o' - c' quantised (BF16 round to nearest even, or FP8 e4m3
+ * of r / s with one FP32 scale s per (list, 16-dim block), saturating), and
+ * per 16-dim block b the error norm e_b = || r - dequant(code) || over the
+ * blocks 0..b (FP64, rounded up).  By the triangle inequality the exact
+ * partial distance satisfies sqrt(P_d) >= sqrt(P~_d) - e, with P~_d formed
+ * from q' - c' and the dequantised codes.  The scan drops a candidate at the
+ * first increment only when that lower bound, less FP32 rounding, exceeds
+ * coef_d r^2 (Section 3.3 test) with a margin above rounding, so the exact
+ * test would drop it too; every other candidate reloads its FP32 rows and
+ * runs Algorithm 1 from the first increment.  Results and per-query
+ * statistics equal those of the FP32 path; only the bytes read change.
+ * Extra memory: lead_dims * (2 B BF16 | 1 B FP8) + 4 * lead_dims / 16 B per
+ * vector (padded slots included).
+ */
+typedef enum {
+    DADE_LEAD_NONE = 0,
+    DADE_LEAD_BF16 = 1,        /* bfloat16, round to nearest even */
+    DADE_LEAD_FP8 = 2          /* FP8 e4m3 with one FP32 scale per (list, 16-dim block) */
+} dade_lead_format;
 
 /* Index construction options.  Zero-initialise, then call dade_build_opts_default(). */
 typedef struct {
@@ -103,7 +130,9 @@ typedef struct {
                                   list centroids become member means; no k-means runs */
     const int64_t *kmeans_init;/* host, optional [n_clusters]: distinct base ids that seed k-means */
     const int64_t *pairs;      /* host, optional [2 * eps_pairs]: pair ids (i != j) for eps_d */
-    int32_t reserved[8];
+    int32_t lead_format;       /* dade_lead_format: extra low-precision copy of the leading dims */
+    int32_t lead_dims;         /* leading dims in that copy (multiple of 16, <= D; 0 = none) */
+    int32_t reserved[6];
 } dade_build_opts;
 
 /* Search options; NULL means all defaults. */
@@ -117,7 +146,9 @@ typedef struct {
     int32_t threads;           /* threads per query's CTA: 0 (default 128), 128 or 256 */
     int32_t schedule;          /* dade_schedule (default DADE_SCHED_TILE) */
     int32_t flags;             /* DADE_FLAG_* bits */
-    int32_t reserved[4];
+    int64_t *lead_stats;       /* device, optional [nq]: candidates dropped by the low-precision prefilter
+                                  (needs DADE_FLAG_LEAD) */
+    int32_t reserved[2];
 } dade_search_opts;
 
 /* Description of a built index. */
@@ -131,6 +162,8 @@ typedef struct {
     int64_t device_bytes;      /* device memory held by the index (excluding workspace) */
     int64_t data_bytes;        /* packed rotated vectors */
     int32_t kmeans_iters;      /* Lloyd iterations run (0 when lists were given) */
+    int32_t lead_format;       /* dade_lead_format of the index */
+    int32_t lead_dims;
     int32_t reserved;
 } dade_info;
 
@@ -143,7 +176,10 @@ typedef enum {
     DADE_FIELD_ASSIGN = 4,     /* int32  [n]          list of every base vector */
     DADE_FIELD_ROTATED = 5,    /* float  [n * d]      rotated base vectors, by base id */
     DADE_FIELD_RHO = 6,        /* double [(d_pad/16 - 1) * eps_kept]  sorted rho_d samples, row t is d = 16 (t+1) */
-    DADE_FIELD_KMEANS_OBJ = 7  /* double [kmeans_iters] objective of each assignment step */
+    DADE_FIELD_KMEANS_OBJ = 7, /* double [kmeans_iters] objective of each assignment step */
+    DADE_FIELD_LEAD_DEQ = 8,   /* float  [n * lead_dims] dequantised lead residuals, by base id */
+    DADE_FIELD_LEAD_ERR = 9,   /* float  [lead_dims/16 * n] row b: error norm over blocks 0..b, by base id */
+    DADE_FIELD_LEAD_SCALE = 10 /* float  [n_clusters * lead_dims/16] FP8 block scales (1 for BF16) */
 } dade_field;
 
 void dade_build_opts_default(dade_build_opts *opts);

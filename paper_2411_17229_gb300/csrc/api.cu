@@ -7,6 +7,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "internal.cuh"
 
 namespace dade {
@@ -116,6 +119,15 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
                    "threads must be 0 (default), 128 or 256");
     DADE_CHECK_ARG(!opts || opts->schedule == DADE_SCHED_PIPELINED || opts->schedule == DADE_SCHED_TILE,
                    "unknown schedule");
+    DADE_CHECK_ARG(!opts || (opts->flags & ~(DADE_FLAG_GENERIC_KERNEL | DADE_FLAG_LEAD)) == 0, "unknown flag bits");
+    if (opts && (opts->flags & DADE_FLAG_LEAD)) {
+        DADE_CHECK_ARG(mode == DADE_MODE_DADE, "DADE_FLAG_LEAD needs mode DADE_MODE_DADE");
+        DADE_CHECK_ARG(ix->lead_format != DADE_LEAD_NONE, "DADE_FLAG_LEAD on an index built without a lead copy");
+        DADE_CHECK_ARG(opts->schedule == DADE_SCHED_TILE, "DADE_FLAG_LEAD needs the tile schedule");
+        DADE_CHECK_ARG(std::min(delta_d, ix->dp) <= ix->lead_dims,
+                       "DADE_FLAG_LEAD needs min(delta_d, D rounded up to 16) <= the index's lead_dims");
+    }
+    DADE_CHECK_ARG(!opts || !opts->lead_stats || (opts->flags & DADE_FLAG_LEAD), "lead_stats needs DADE_FLAG_LEAD");
     return DADE_OK;
 }
 
@@ -164,6 +176,8 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.threads = opts && opts->threads ? opts->threads : 128;
     p.schedule = opts ? opts->schedule : DADE_SCHED_TILE;
     p.generic = opts ? (opts->flags & DADE_FLAG_GENERIC_KERNEL) != 0 : 0;
+    p.use_lead = opts ? (opts->flags & DADE_FLAG_LEAD) != 0 : 0;
+    p.lead_stats = opts ? opts->lead_stats : nullptr;
     p.delta_d = delta_d;
     if (p.mode == DADE_MODE_DADE) p.n_inc = coef_table(ix, alpha, delta_d, nullptr, p.coef);
     else p.n_inc = 0;
@@ -221,6 +235,14 @@ dade_status dade_build_index(const float *base, int64_t n, int32_t d, const dade
     DADE_CHECK_ARG(opts->n_clusters >= 1 && opts->n_clusters <= n, "n_clusters outside 1..n");
     DADE_CHECK_ARG(opts->kmeans_iters >= 0 && opts->kmeans_iters <= 1000, "kmeans_iters outside 0..1000");
     DADE_CHECK_ARG(opts->eps_pairs >= 1, "eps_pairs < 1");
+    DADE_CHECK_ARG(opts->lead_format == DADE_LEAD_NONE || opts->lead_format == DADE_LEAD_BF16 ||
+                       opts->lead_format == DADE_LEAD_FP8,
+                   "unknown lead_format");
+    if (opts->lead_format == DADE_LEAD_NONE)
+        DADE_CHECK_ARG(opts->lead_dims == 0, "lead_dims given without a lead_format");
+    else
+        DADE_CHECK_ARG(opts->lead_dims >= 16 && opts->lead_dims % 16 == 0 && opts->lead_dims <= (d + 15) / 16 * 16,
+                       "lead_dims must be a multiple of 16 in [16, D rounded up to 16]");
     *out = nullptr;
     dade_index *ix = new (std::nothrow) dade_index();
     if (!ix) {
@@ -385,9 +407,11 @@ dade_status dade_index_info(const dade_index *ix, dade_info *info) {
     info->eps_kept = ix->eps_kept;
     info->data_bytes = (int64_t)ix->data.bytes;
     info->device_bytes = (int64_t)(ix->data.bytes + ix->ids.bytes + ix->meta.bytes + ix->cent.bytes + ix->cnorm.bytes +
-                                   ix->W32.bytes +
-                                   ix->mu32.bytes + ix->errflag.bytes);
+                                   ix->W32.bytes + ix->mu32.bytes + ix->errflag.bytes + ix->lead.bytes +
+                                   ix->lead_err.bytes + ix->lead_scale.bytes);
     info->kmeans_iters = (int32_t)ix->kmeans_obj.size();
+    info->lead_format = ix->lead_format;
+    info->lead_dims = ix->lead_dims;
     info->reserved = 0;
     return DADE_OK;
 }
@@ -449,6 +473,57 @@ dade_status dade_index_export(const dade_index *ix, int32_t field, void *dst, si
                 int64_t id = ids[m.slot + i];
                 for (int k = 0; k < d; ++k)
                     o[id * d + k] = packed[m.base + (int64_t)(k / 16) * m.np * 16 + (int64_t)i * 16 + k % 16];
+            }
+        }
+        return DADE_OK;
+    }
+    case DADE_FIELD_LEAD_DEQ:
+    case DADE_FIELD_LEAD_ERR:
+    case DADE_FIELD_LEAD_SCALE: {
+        DADE_CHECK_ARG(ix->lead_format != DADE_LEAD_NONE, "the index has no lead copy");
+        const int lnb = ix->lead_nb, es = ix->lead_format == DADE_LEAD_BF16 ? 2 : 1;
+        std::vector<float> scale((size_t)ix->nc * lnb);
+        DADE_TRY_CUDA(cudaMemcpy(scale.data(), ix->lead_scale.p, sizeof(float) * scale.size(), cudaMemcpyDeviceToHost));
+        if (field == DADE_FIELD_LEAD_SCALE) {
+            DADE_TRY(need(sizeof(float) * scale.size()));
+            std::memcpy(dst, scale.data(), bytes);
+            return DADE_OK;
+        }
+        std::vector<int32_t> ids((size_t)ix->slots);
+        DADE_TRY_CUDA(cudaMemcpy(ids.data(), ix->ids.p, sizeof(int32_t) * ids.size(), cudaMemcpyDeviceToHost));
+        float *o = static_cast<float *>(dst);
+        if (field == DADE_FIELD_LEAD_ERR) {
+            DADE_TRY(need(sizeof(float) * (size_t)lnb * ix->n));
+            std::vector<float> err((size_t)ix->slots * lnb);
+            DADE_TRY_CUDA(cudaMemcpy(err.data(), ix->lead_err.p, sizeof(float) * err.size(), cudaMemcpyDeviceToHost));
+            for (int c = 0; c < ix->nc; ++c) {
+                const ListMeta &m = ix->lists[c];
+                for (int i = 0; i < m.len; ++i)
+                    for (int b = 0; b < lnb; ++b) o[(size_t)b * ix->n + ids[m.slot + i]] = err[(size_t)b * ix->slots + m.slot + i];
+            }
+            return DADE_OK;
+        }
+        DADE_TRY(need(sizeof(float) * (size_t)ix->n * ix->lead_dims));
+        std::vector<unsigned char> codes(ix->lead.bytes);
+        DADE_TRY_CUDA(cudaMemcpy(codes.data(), ix->lead.p, codes.size(), cudaMemcpyDeviceToHost));
+        for (int c = 0; c < ix->nc; ++c) {
+            const ListMeta &m = ix->lists[c];
+            for (int i = 0; i < m.len; ++i) {
+                const int64_t id = ids[m.slot + i];
+                for (int b = 0; b < lnb; ++b) {
+                    const unsigned char *src = codes.data() + (m.slot * lnb * 16 + (int64_t)b * m.np * 16 + (int64_t)i * 16) * es;
+                    for (int k = 0; k < 16; ++k) {
+                        float v;
+                        if (es == 2) {
+                            uint32_t bits = (uint32_t)(src[2 * k] | (src[2 * k + 1] << 8)) << 16;
+                            std::memcpy(&v, &bits, 4);
+                        } else {
+                            const __half h(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)src[k], __NV_E4M3));
+                            v = scale[(size_t)c * lnb + b] * __half2float(h);
+                        }
+                        o[(size_t)id * ix->lead_dims + b * 16 + k] = v;
+                    }
+                }
             }
         }
         return DADE_OK;

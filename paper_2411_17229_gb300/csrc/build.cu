@@ -8,6 +8,10 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "internal.cuh"
 #include "tiles.cuh"
 
@@ -184,6 +188,79 @@ __global__ void k_pack(const float *__restrict__ X, int64_t n, int dp, int nb, c
 #pragma unroll
         for (int t = 0; t < 4; ++t) dst[t] = src[t];
         if (b == 0) ids[m.slot + pos[i]] = (int32_t)i;
+    }
+}
+
+// ---- low-precision copy of the leading dims (prefilter codes) -----------------------
+// FP8 only: per (list, lead block) maximum |o' - c'| over the list's members,
+// as the bits of a nonnegative float (ordered like the values).
+__global__ void k_lead_absmax(const float *__restrict__ X, int64_t n, int dp, int lead_nb,
+                              const int32_t *__restrict__ assign, const float *__restrict__ cent,
+                              unsigned *__restrict__ amax) {
+    int64_t total = n * (int64_t)lead_nb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / lead_nb;
+        const int b = (int)(e % lead_nb), c = assign[i];
+        float m = 0.f;
+        for (int k = 0; k < 16; ++k)
+            m = fmaxf(m, fabsf(__fsub_rn(X[i * dp + b * 16 + k], cent[(int64_t)c * dp + b * 16 + k])));
+        atomicMax(&amax[(int64_t)c * lead_nb + b], __float_as_uint(m));
+    }
+}
+
+// FP8 scale of a (list, block): the largest residual maps to 448, the
+// largest finite e4m3 value; an all-zero block gets scale 1.
+__global__ void k_lead_scale(const unsigned *__restrict__ amax, int64_t cnt, float *__restrict__ scale) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+        const float m = __uint_as_float(amax[e]);
+        scale[e] = m > 0.f ? m / 448.f : 1.f;
+    }
+}
+
+// Codes of vector i (list c, slot pos[i]): residual r = o' - c' per lead dim,
+// BF16 round-to-nearest-even, or FP8 e4m3 of r / scale (saturating).  The
+// list's codes start at byte slot(c) * lead_nb * 16 * ES; block b of it is a
+// slab of np x 16 codes.  err[b][slot] is || r - dequant(code) || over the
+// blocks 0..b, accumulated in FP64 from the exact differences and rounded up,
+// where dequant is the scan's own widening (times the scale, rounded once).
+__global__ void k_pack_lead(const float *__restrict__ X, int64_t n, int dp, int lead_nb, int lf,
+                            const int32_t *__restrict__ assign, const int32_t *__restrict__ pos,
+                            const ListMeta *__restrict__ meta, const float *__restrict__ cent,
+                            const float *__restrict__ scale, unsigned char *__restrict__ lead, float *__restrict__ err,
+                            int64_t slots) {
+    const int es = lf == DADE_LEAD_BF16 ? 2 : 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = assign[i];
+        const ListMeta m = meta[c];
+        const int64_t slot = m.slot + pos[i];
+        double acc = 0.0;
+        for (int b = 0; b < lead_nb; ++b) {
+            const float sc = lf == DADE_LEAD_FP8 ? scale[(int64_t)c * lead_nb + b] : 1.f;
+            unsigned char *dst = lead + (m.slot * lead_nb * 16 + (int64_t)b * m.np * 16 + (int64_t)pos[i] * 16) * es;
+            for (int k = 0; k < 16; k += 2) {
+                const float o0 = X[i * dp + b * 16 + k], o1 = X[i * dp + b * 16 + k + 1];
+                const float c0 = cent[(int64_t)c * dp + b * 16 + k], c1 = cent[(int64_t)c * dp + b * 16 + k + 1];
+                const float r0 = __fsub_rn(o0, c0), r1 = __fsub_rn(o1, c1);
+                float q0, q1;
+                if (lf == DADE_LEAD_BF16) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(r0), h1 = __float2bfloat16_rn(r1);
+                    reinterpret_cast<unsigned short *>(dst)[k] = __bfloat16_as_ushort(h0);
+                    reinterpret_cast<unsigned short *>(dst)[k + 1] = __bfloat16_as_ushort(h1);
+                    q0 = __bfloat162float(h0);
+                    q1 = __bfloat162float(h1);
+                } else {
+                    const __nv_fp8x2_storage_t v = __nv_cvt_float2_to_fp8x2(
+                        make_float2(__fdiv_rn(r0, sc), __fdiv_rn(r1, sc)), __NV_SATFINITE, __NV_E4M3);
+                    reinterpret_cast<unsigned short *>(dst)[k / 2] = v;
+                    const float2 f = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(v, __NV_E4M3)));
+                    q0 = __fmul_rn(sc, f.x);
+                    q1 = __fmul_rn(sc, f.y);
+                }
+                const double e0 = ((double)o0 - (double)c0) - (double)q0, e1 = ((double)o1 - (double)c1) - (double)q1;
+                acc += e0 * e0 + e1 * e1;
+            }
+            err[(int64_t)b * slots + slot] = __double2float_ru(__dsqrt_ru(acc));
+        }
     }
 }
 
@@ -478,6 +555,40 @@ dade_status build_index(const float *base, int64_t n, int32_t d, const dade_buil
         k_pack<<<grid_for(n * nb, 256), 256, 0, s>>>(rot.as<float>(), n, dp, nb, asg.as<int32_t>(), posb.as<int32_t>(),
                                                     ix->meta.as<ListMeta>(), ix->data.as<float>(), ix->ids.as<int32_t>());
         DADE_TRY(launch_check("k_pack"));
+        if (o.lead_format != DADE_LEAD_NONE) {
+            const int lnb = o.lead_dims / 16, es = o.lead_format == DADE_LEAD_BF16 ? 2 : 1;
+            ix->lead_format = o.lead_format;
+            ix->lead_dims = o.lead_dims;
+            ix->lead_nb = lnb;
+            const size_t code_bytes = (size_t)ix->slots * lnb * 16 * es;
+            DADE_TRY(ix->lead.alloc(code_bytes));
+            DADE_TRY(ix->lead_err.alloc(sizeof(float) * (size_t)ix->slots * lnb));
+            DADE_TRY(ix->lead_scale.alloc(sizeof(float) * (size_t)nc * lnb));
+            DADE_TRY_CUDA(cudaMemsetAsync(ix->lead.p, 0, code_bytes, s));
+            DADE_TRY_CUDA(cudaMemsetAsync(ix->lead_err.p, 0, sizeof(float) * (size_t)ix->slots * lnb, s));
+            if (o.lead_format == DADE_LEAD_FP8) {
+                DevBuf amax;
+                DADE_TRY(amax.alloc(sizeof(unsigned) * (size_t)nc * lnb));
+                DADE_TRY_CUDA(cudaMemsetAsync(amax.p, 0, sizeof(unsigned) * (size_t)nc * lnb, s));
+                k_lead_absmax<<<grid_for(n * lnb, 256), 256, 0, s>>>(rot.as<float>(), n, dp, lnb, asg.as<int32_t>(),
+                                                                     ix->cent.as<float>(), amax.as<unsigned>());
+                DADE_TRY(launch_check("k_lead_absmax"));
+                k_lead_scale<<<grid_for((int64_t)nc * lnb, 256), 256, 0, s>>>(amax.as<unsigned>(), (int64_t)nc * lnb,
+                                                                              ix->lead_scale.as<float>());
+                DADE_TRY(launch_check("k_lead_scale"));
+                DADE_TRY_CUDA(cudaStreamSynchronize(s));
+            } else {
+                std::vector<float> ones((size_t)nc * lnb, 1.f);
+                DADE_TRY_CUDA(cudaMemcpyAsync(ix->lead_scale.p, ones.data(), sizeof(float) * ones.size(),
+                                              cudaMemcpyHostToDevice, s));
+                DADE_TRY_CUDA(cudaStreamSynchronize(s));
+            }
+            k_pack_lead<<<grid_for(n, 256), 256, 0, s>>>(rot.as<float>(), n, dp, lnb, o.lead_format, asg.as<int32_t>(),
+                                                         posb.as<int32_t>(), ix->meta.as<ListMeta>(), ix->cent.as<float>(),
+                                                         ix->lead_scale.as<float>(), ix->lead.as<unsigned char>(),
+                                                         ix->lead_err.as<float>(), ix->slots);
+            DADE_TRY(launch_check("k_pack_lead"));
+        }
         DADE_TRY_CUDA(cudaStreamSynchronize(s));
     }
 

@@ -90,6 +90,11 @@ struct dade_index {
     dade::DevBuf ids;       // int32 per slot (padding slots -1)
     dade::DevBuf meta;      // ListMeta [nc]
     dade::DevBuf errflag;   // int32 device error word (bounded waits)
+    // low-precision copy of the leading dims (prefilter), see dade_lead_format
+    int32_t lead_format = 0, lead_dims = 0, lead_nb = 0;
+    dade::DevBuf lead;      // codes; list c at slot_c * lead_nb * 16 * ES bytes, block b at + b * np * 16 * ES
+    dade::DevBuf lead_scale;// float [nc][lead_nb] (FP8 only)
+    dade::DevBuf lead_err;  // float [lead_nb][slots]: error norm over blocks 0..b (rounded up)
     int64_t data_floats = 0, slots = 0;
     // workspace (grown on demand, reused across calls)
     mutable dade::DevBuf ws_dist, ws_probe, ws_qrot, ws_qin, ws_ids, ws_dists;
@@ -108,7 +113,8 @@ struct ScanParams {
     const float *q_rot;      // [nq][q_stride]
     int32_t q_stride;
     const int32_t *probe;    // [nq][nprobe]
-    int32_t nprobe, k, tile, mode, delta_d, n_inc, spec, threads, schedule, generic;
+    int32_t nprobe, k, tile, mode, delta_d, n_inc, spec, threads, schedule, generic, use_lead;
+    int64_t *lead_stats;     // [nq] or null
     float coef[DADE_MAX_DIM / DADE_BLOCK];   // per increment; prune iff P > coef[j] * r2
     int64_t *ids;            // [nq][k]
     float *dists;            // [nq][k]

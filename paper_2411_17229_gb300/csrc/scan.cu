@@ -21,6 +21,11 @@
 // FDScanning (exact full-D distance for every candidate) streams every
 // increment through the same bulk-copy ring and applies only the final test.
 //
+// With a low-precision copy of the leading dims (LF = 1 BF16, 2 FP8), step 1
+// stages that copy and its error norms instead, step 2 drops a candidate only
+// on the certified margin test (lead_prunes), and step 3 starts again at the
+// first increment on FP32 rows, so results equal those of the FP32 path.
+//
 // Every mbarrier wait is bounded (2 s on %globaltimer); on expiry the CTA
 // records DADE_ETIMEOUT in the index's error word, waits (bounded) for its
 // own copies in flight and exits without writing results.
@@ -35,21 +40,22 @@ namespace dade {
 namespace {
 using namespace scanning;
 
-template <int NT, bool FD, bool STATS>
+template <int NT, bool FD, bool STATS, int LF>
 __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const ScanArgs a) {
     constexpr int NQUAD = NT / 4;              // candidates per pass
     constexpr int MAXIT = MAX_TILE / NQUAD;    // passes over a full tile
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_cnt[2], s_cntF, s_ntop, s_cur;
     __shared__ float s_r2;
-    __shared__ unsigned long long s_stats[4];
+    __shared__ unsigned long long s_stats[4], s_lead;
 
     const int tid = threadIdx.x, quad = tid >> 2, lq = tid & 3;
     const int64_t qi = blockIdx.x;
-    const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k, a.nprobe);
+    const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k, a.nprobe, LF != 0);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     int4 *smeta = reinterpret_cast<int4 *>(smem + L.meta);
     float *qv = reinterpret_cast<float *>(smem + L.qv);
+    float *qc = reinterpret_cast<float *>(smem + L.qc);      // LF: q' - c' of the first increment, then scales
     float *stage = reinterpret_cast<float *>(smem + L.stage);
     Surv *l0 = reinterpret_cast<Surv *>(smem + L.l0);
     Surv *l1 = reinterpret_cast<Surv *>(smem + L.l1);
@@ -73,20 +79,32 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
         s_r2 = INFINITY;
     }
     if (STATS && tid < 4) s_stats[tid] = 0;
+    if (tid == 0) s_lead = 0;
     __syncthreads();
 
     const int units = FD ? a.n_inc : 1;   // staged units per tile
+    constexpr int ES = LeadFmt<LF>::ES;
+    auto issue_unit = [&](const Cur &c, int slot) {
+        if constexpr (LF != 0) {
+            const int4 m = meta_of(a, smeta, plist, c.p);
+            issue_lead<LF>(a, m, c.i0, min(a.tile, m.z - c.i0), a.gb, a.tile,
+                           reinterpret_cast<unsigned char *>(stage + (size_t)slot * a.tile * a.gb * 16),
+                           su32(&bars[slot]));
+        } else {
+            issue(a, smeta, plist, c, slot, stage, bars);
+        }
+    };
     Cur cc{0, 0, 0};
     normalize(cc, a, smeta, plist);
     Cur ic = cc;          // issue cursor (thread 0 only)
     int issued = 0;       // units issued (thread 0 only)
     if (tid == 0)
         for (int s = 0; s < a.ns && ic.p < a.nprobe; ++s) {
-            issue(a, smeta, plist, ic, s, stage, bars);
+            issue_unit(ic, s);
             advance(ic, units, a, smeta, plist);
             ++issued;
         }
-    unsigned long long st_cand = 0, st_dims = 0, st_acc = 0, st_prn = 0;
+    unsigned long long st_cand = 0, st_dims = 0, st_acc = 0, st_prn = 0, st_lead = 0;
     int unit = 0;
     bool aborted = false;
 
@@ -120,7 +138,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
                 }
                 __syncthreads();
                 if (tid == 0 && ic.p < a.nprobe) {
-                    issue(a, smeta, plist, ic, slot, stage, bars);
+                    issue_unit(ic, slot);
                     advance(ic, units, a, smeta, plist);
                     ++issued;
                 }
@@ -143,9 +161,49 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
         } else {
             // ---- phase A: increment 0 of the whole tile, streamed (bulk copy) ----------
             const int slot = unit % a.ns;
+            if constexpr (LF != 0) {   // q' - c' of the first increment and its scales
+                const int list = plist[cc.p];
+                for (int k = tid; k < a.gb * 16; k += NT) qc[k] = __fsub_rn(qv[k], a.cent[(int64_t)list * a.dp + k]);
+                for (int b = tid; b < a.gb; b += NT)
+                    qc[a.dp + b] = LF == 2 ? a.lead_scale[(int64_t)list * a.lead_nb + b] : 1.f;
+            }
             if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1))) { aborted = true; break; }
             r2 = s_r2;
-            {
+            if constexpr (LF != 0) {
+                const unsigned char *st = reinterpret_cast<const unsigned char *>(stage + (size_t)slot * a.tile * a.gb * 16);
+                const float *se = reinterpret_cast<const float *>(st + (size_t)a.gb * a.tile * 16 * ES);
+                const bool last0 = a.n_inc == 1;
+                const int d0 = min(a.delta_d, a.d);
+                const float thr = last0 ? r2 : a.coef[0] * r2;
+                float qn = 0.f;
+                for (int b = 0; b < a.gb; ++b) {
+                    const float4 v = *reinterpret_cast<const float4 *>(qc + b * 16 + lq * 4);
+                    qn = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, qn))));
+                }
+                qn += __shfl_xor_sync(0xffffffffu, qn, 1);
+                qn += __shfl_xor_sync(0xffffffffu, qn, 2);
+                const float qcn = sqrtf(qn);
+                for (int it = 0; it < nit; ++it) {
+                    const int c = quad + it * NQUAD;
+                    const bool act = c < tn;
+                    float p = 0.f;
+                    if (act)
+                        for (int b = 0; b < a.gb; ++b)
+                            p += sqd4(*reinterpret_cast<const float4 *>(qc + b * 16 + lq * 4),
+                                      lead4<LF>(st + ((size_t)b * a.tile * 16 + c * 16 + lq * 4) * ES, qc[a.dp + b]));
+                    p += __shfl_xor_sync(0xffffffffu, p, 1);
+                    p += __shfl_xor_sync(0xffffffffu, p, 2);
+                    const bool lead = act && lq == 0;
+                    const bool drop = lead && lead_prunes(p, se[c], qcn, thr);
+                    push(lead && !drop, l0, &s_cnt[0], c, 0.f);
+                    if (drop) {   // counted as the exact path counts it: pruned at d0, or rejected at D
+                        ++st_lead;
+                        if (STATS) { ++st_cand; st_dims += last0 ? a.d : d0; st_prn += !last0; }
+                    } else if (STATS && lead) {
+                        ++st_cand;
+                    }
+                }
+            } else {
                 const float *st = stage + (size_t)slot * a.tile * a.gb * 16;
                 const int b1 = min(a.gb, a.nb);
                 const bool last0 = a.n_inc == 1;
@@ -171,7 +229,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
             }
             __syncthreads();
             if (tid == 0 && ic.p < a.nprobe) {
-                issue(a, smeta, plist, ic, slot, stage, bars);
+                issue_unit(ic, slot);
                 advance(ic, units, a, smeta, plist);
                 ++issued;
             }
@@ -187,11 +245,12 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
                 const int sidx = r0 + quad;
                 const bool act = sidx < nS;
                 const Surv sv = act ? l0[sidx] : Surv{0, 0.f};
-                float p = sv.p, part = 0.f;
+                // after the prefilter (LF) every increment, the first included, runs on FP32 rows
+                float p = LF ? 0.f : sv.p, part = 0.f;
                 bool alive = act;
                 const float *row = lbase + (int64_t)(cc.i0 + sv.idx) * 16 + lq * 4;
-                int jj = 1, bend = min(2 * a.gb, a.nb);
-                for (int wb = a.gb; wb < a.nb; wb += a.spec) {
+                int jj = LF ? 0 : 1, bend = min((LF ? 1 : 2) * a.gb, a.nb);
+                for (int wb = LF ? 0 : a.gb; wb < a.nb; wb += a.spec) {
                     if (!__any_sync(0xffffffffu, alive)) break;
                     float4 o[SPECB];
 #pragma unroll
@@ -301,24 +360,36 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
         __syncthreads();
         if (tid < 4) a.stats[qi * 4 + tid] = (int64_t)s_stats[tid];
     }
+    if (LF != 0 && a.lead_stats) {
+        if (st_lead) atomicAdd(&s_lead, st_lead);
+        __syncthreads();
+        if (tid == 0) a.lead_stats[qi] = (int64_t)s_lead;
+    }
 }
 
-template <int NT, bool FD, bool STATS>
+template <int NT, bool FD, bool STATS, int LF>
 dade_status launch(const ScanArgs &a, int64_t nq, size_t smem, cudaStream_t s) {
     static size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
-        DADE_TRY_CUDA(cudaFuncSetAttribute(k_scan<NT, FD, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        DADE_TRY_CUDA(cudaFuncSetAttribute(k_scan<NT, FD, STATS, LF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem));
         configured = smem;
     }
-    k_scan<NT, FD, STATS><<<(unsigned)nq, NT, smem, s>>>(a);
-    return launch_check(FD ? "k_scan<FD>" : "k_scan<DADE>");
+    k_scan<NT, FD, STATS, LF><<<(unsigned)nq, NT, smem, s>>>(a);
+    return launch_check(FD ? "k_scan<FD>" : (LF ? "k_scan<DADE, lead>" : "k_scan<DADE>"));
+}
+
+template <int NT, int LF>
+dade_status launch_dade(const ScanArgs &a, int64_t nq, size_t smem, bool stats, cudaStream_t s) {
+    return stats ? launch<NT, false, true, LF>(a, nq, smem, s) : launch<NT, false, false, LF>(a, nq, smem, s);
 }
 
 template <int NT>
-dade_status launch_nt(const ScanArgs &a, int64_t nq, size_t smem, bool fd, bool stats, cudaStream_t s) {
-    if (fd) return stats ? launch<NT, true, true>(a, nq, smem, s) : launch<NT, true, false>(a, nq, smem, s);
-    return stats ? launch<NT, false, true>(a, nq, smem, s) : launch<NT, false, false>(a, nq, smem, s);
+dade_status launch_nt(const ScanArgs &a, int64_t nq, size_t smem, bool fd, bool stats, int lf, cudaStream_t s) {
+    if (fd) return stats ? launch<NT, true, true, 0>(a, nq, smem, s) : launch<NT, true, false, 0>(a, nq, smem, s);
+    if (lf == DADE_LEAD_BF16) return launch_dade<NT, 1>(a, nq, smem, stats, s);
+    if (lf == DADE_LEAD_FP8) return launch_dade<NT, 2>(a, nq, smem, stats, s);
+    return launch_dade<NT, 0>(a, nq, smem, stats, s);
 }
 
 } // namespace
@@ -326,7 +397,7 @@ dade_status launch_nt(const ScanArgs &a, int64_t nq, size_t smem, bool fd, bool 
 dade_status scan_pipelined(const scanning::ScanArgs &a, int64_t nq, int threads, cudaStream_t s);
 int pipe_depth_limit();
 bool scan_fast_applies(const scanning::ScanArgs &a, bool fd);
-dade_status scan_fast(const scanning::ScanArgs &a, int64_t nq, bool fd, int threads, cudaStream_t s);
+dade_status scan_fast(const scanning::ScanArgs &a, int64_t nq, bool fd, int threads, int lf, cudaStream_t s);
 
 dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s) {
     if (nq == 0) return DADE_OK;
@@ -359,16 +430,26 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     }
     a.n_inc = (ix->nb + a.gb - 1) / a.gb;
     for (int j = 0; j < DADE_MAX_DIM / DADE_BLOCK; ++j) a.coef[j] = j < p.n_inc ? p.coef[j] : INFINITY;
-    if (!fd && p.schedule == DADE_SCHED_PIPELINED && a.n_inc <= pipe_depth_limit())
+    const int lf = (!fd && p.use_lead) ? ix->lead_format : 0;
+    if (lf) {
+        a.lead = ix->lead.as<unsigned char>();
+        a.lead_err = ix->lead_err.as<float>();
+        a.lead_scale = ix->lead_scale.as<float>();
+        a.cent = ix->cent.as<float>();
+        a.lead_stats = p.lead_stats;
+        a.lead_slots = ix->slots;
+        a.lead_nb = ix->lead_nb;
+    }
+    if (!fd && !lf && p.schedule == DADE_SCHED_PIPELINED && a.n_inc <= pipe_depth_limit())
         return scan_pipelined(a, nq, p.threads, s);
-    if (scan_fast_applies(a, fd) && !p.generic) return scan_fast(a, nq, fd, p.threads, s);
-    const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k, a.nprobe);
+    if (scan_fast_applies(a, fd) && !p.generic) return scan_fast(a, nq, fd, p.threads, lf, s);
+    const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k, a.nprobe, lf != 0);
     if (L.total > 227 * 1024) {
         set_error("scan configuration needs more than 227 KB of shared memory (reduce tile or delta_d)");
         return DADE_EUNSUPPORTED;
     }
-    if (p.threads == 256) return launch_nt<256>(a, nq, L.total, fd, p.stats != nullptr, s);
-    return launch_nt<128>(a, nq, L.total, fd, p.stats != nullptr, s);
+    if (p.threads == 256) return launch_nt<256>(a, nq, L.total, fd, p.stats != nullptr, lf, s);
+    return launch_nt<128>(a, nq, L.total, fd, p.stats != nullptr, lf, s);
 }
 
 } // namespace dade

@@ -7,6 +7,9 @@
 #include <cmath>
 #include <cstdint>
 
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "internal.cuh"
 
 namespace dade {
@@ -33,6 +36,14 @@ struct ScanArgs {
     int *err;
     int q_stride, nprobe, d, dp, nb, k, tile, gb, n_inc, ns, delta_d, spec;
     float coef[DADE_MAX_DIM / DADE_BLOCK];
+    // low-precision leading blocks (prefilter of the first increment)
+    const unsigned char *lead;   // residual codes, list region at slot * lead_nb * 16 * ES bytes
+    const float *lead_err;       // [lead_nb][lead_slots] cumulative error norms, rounded up
+    const float *lead_scale;     // [nc][lead_nb] FP8 scales
+    const float *cent;           // [nc][dp] rotated centroids
+    int64_t *lead_stats;         // [nq] candidates dropped by the prefilter, or null
+    int64_t lead_slots;
+    int lead_nb;
 };
 
 // ---------------------------------------------------------- PTX helpers ----
@@ -150,6 +161,61 @@ __device__ inline void issue(const ScanArgs &a, const int4 *sm, const int32_t *p
         bulk_g2s(su32(dst + (size_t)(b - b0) * a.tile * 16), src + (int64_t)b * m.w * 16, (uint32_t)(tn * 64), bar);
 }
 
+// ---------------------------------------------- low-precision leading blocks ----
+// Bytes per code: BF16 (format 1) 2, FP8 e4m3 (format 2) 1.
+template <int LF> struct LeadFmt { static constexpr int ES = LF == 1 ? 2 : 1; };
+
+// Lane lq's four codes of one candidate block, dequantised to FP32.  BF16 is
+// the high half of an FP32 word, so widening is exact; FP8 codes widen
+// exactly to half, then to float, and the product with the block scale is
+// rounded once (no fused multiply-add), as in the build's error norm.
+template <int LF>
+__device__ __forceinline__ float4 lead4(const unsigned char *p, float scale) {
+    if constexpr (LF == 1) {
+        const uint2 u = *reinterpret_cast<const uint2 *>(p);
+        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+    } else {
+        const uint32_t u = *reinterpret_cast<const uint32_t *>(p);
+        const float2 lo = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u & 0xffffu), __NV_E4M3)));
+        const float2 hi = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u >> 16), __NV_E4M3)));
+        return make_float4(__fmul_rn(scale, lo.x), __fmul_rn(scale, lo.y), __fmul_rn(scale, hi.x), __fmul_rn(scale, hi.y));
+    }
+}
+
+// Certified test of the prefilter.  p_lead is the FP32 sum of squares of
+// (q' - c') - dequant over the first increment's dims, e the stored error
+// norm of those dims and qcn = ||q' - c'|| there.  The true distance of the
+// candidate over the same dims is at least sqrt(p_lead) - e, less FP32
+// rounding in forming q' - c', the differences and the sum, which the
+// factors below cover (relative 2^-16 on the root, 2^-20 ||q' - c'||).  The
+// candidate is dropped only when that lower bound squared exceeds thr by a
+// further relative 2^-15, more than the rounding of the FP32 exact partial,
+// so the exact test on FP32 data would drop it as well.
+__device__ __forceinline__ bool lead_prunes(float p_lead, float e, float qcn, float thr) {
+    const float L = sqrtf(p_lead) * (1.f - 0x1p-16f) - e - qcn * 0x1p-20f;
+    const float lb = L > 0.f ? L * L : 0.f;
+    return lb > thr * (1.f + 0x1p-15f);
+}
+
+// Queue the prefilter unit of a tile: gb blocks of tn codes (tn * 16 * ES
+// bytes each) plus the tile's error norms (rounded up to a multiple of 4
+// slots; the padded slots exist in every list).  dst layout: block b at
+// b * cap * 16 * ES bytes, norms at gb * cap * 16 * ES.
+template <int LF>
+__device__ inline void issue_lead(const ScanArgs &a, int4 m, int c0, int cn, int gb, int cap, unsigned char *dst,
+                                  uint32_t bar) {
+    constexpr int ES = LeadFmt<LF>::ES;
+    const int cn4 = (cn + 3) & ~3;
+    mbar_expect_tx(bar, (uint32_t)(gb * cn * 16 * ES + cn4 * 4));
+    const int64_t slot = (int64_t)(unsigned)m.y;
+    const unsigned char *src = a.lead + (slot * a.lead_nb * 16 + (int64_t)c0 * 16) * ES;
+    for (int b = 0; b < gb; ++b)
+        bulk_g2s(su32(dst + (size_t)b * cap * 16 * ES), src + (int64_t)b * m.w * 16 * ES, (uint32_t)(cn * 16 * ES), bar);
+    bulk_g2s(su32(dst + (size_t)gb * cap * 16 * ES), a.lead_err + (int64_t)(gb - 1) * a.lead_slots + slot + c0,
+             (uint32_t)(cn4 * 4), bar);
+}
+
 __device__ __forceinline__ int lower_bound_u64(const unsigned long long *v, int n, unsigned long long key) {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -161,7 +227,7 @@ __device__ __forceinline__ int lower_bound_u64(const unsigned long long *v, int 
 }
 
 struct SmemLayout {
-    size_t meta, qv, stage, l0, l1, fl, fraw, fsort, top, total;
+    size_t meta, qv, qc, stage, l0, l1, fl, fraw, fsort, top, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -171,11 +237,12 @@ __host__ __device__ inline int pow2_at_least(int x) {
     return n;
 }
 
-__host__ __device__ inline SmemLayout layout(int dp, int tile, int gb, int ns, int k, int nprobe) {
+__host__ __device__ inline SmemLayout layout(int dp, int tile, int gb, int ns, int k, int nprobe, bool lead = false) {
     SmemLayout L;
     size_t o = 64;                                  // mbarriers (up to 8)
     L.meta = o;  o = align_up(o + sizeof(int4) * (size_t)min(nprobe, PMETA), 16);
     L.qv = o;    o = align_up(o + sizeof(float) * dp, 128);
+    L.qc = o;    o = align_up(o + (lead ? sizeof(float) * (dp + 64) : 0), 128);   // q' - c', then <= 64 block scales
     L.stage = o; o = align_up(o + sizeof(float) * (size_t)ns * tile * gb * 16, 128);
     L.l0 = o;    o += sizeof(Surv) * tile;
     L.l1 = o;    o += sizeof(Surv) * tile;

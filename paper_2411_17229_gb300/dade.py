@@ -18,9 +18,11 @@ LIB_PATH = os.path.join(_HERE, "libdade.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EIO = range(7)
 MODE_DADE, MODE_FD = 0, 1
 SCHED_TILE, SCHED_PIPELINED = 0, 1
-FLAG_GENERIC_KERNEL = 1
+FLAG_GENERIC_KERNEL, FLAG_LEAD = 1, 2
+LEAD_NONE, LEAD_BF16, LEAD_FP8 = 0, 1, 2
 PIPE_MAX = 8
-FIELD_MEAN, FIELD_BASIS, FIELD_EIGVAL, FIELD_CENTROIDS, FIELD_ASSIGN, FIELD_ROTATED, FIELD_RHO, FIELD_KMEANS_OBJ = range(8)
+(FIELD_MEAN, FIELD_BASIS, FIELD_EIGVAL, FIELD_CENTROIDS, FIELD_ASSIGN, FIELD_ROTATED, FIELD_RHO, FIELD_KMEANS_OBJ,
+ FIELD_LEAD_DEQ, FIELD_LEAD_ERR, FIELD_LEAD_SCALE) = range(11)
 MAX_DIM, MAX_K = 1024, 256
 PROBE_NOALLOC_MAX = 4194304
 
@@ -34,19 +36,21 @@ class DadeError(RuntimeError):
 class BuildOpts(C.Structure):
     _fields_ = [("n_clusters", C.c_int32), ("kmeans_iters", C.c_int32), ("seed", C.c_uint64),
                 ("eps_pairs", C.c_int64), ("assign", C.c_void_p), ("kmeans_init", C.c_void_p),
-                ("pairs", C.c_void_p), ("reserved", C.c_int32 * 8)]
+                ("pairs", C.c_void_p), ("lead_format", C.c_int32), ("lead_dims", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class SearchOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tile", C.c_int32), ("stats", C.c_void_p), ("spec", C.c_int32),
                 ("threads", C.c_int32), ("schedule", C.c_int32), ("flags", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("lead_stats", C.c_void_p), ("reserved", C.c_int32 * 2)]
 
 
 class Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("d_pad", C.c_int32), ("n_clusters", C.c_int32),
                 ("max_list", C.c_int32), ("eps_kept", C.c_int64), ("device_bytes", C.c_int64),
-                ("data_bytes", C.c_int64), ("kmeans_iters", C.c_int32), ("reserved", C.c_int32)]
+                ("data_bytes", C.c_int64), ("kmeans_iters", C.c_int32), ("lead_format", C.c_int32),
+                ("lead_dims", C.c_int32), ("reserved", C.c_int32)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/dade.h
@@ -118,11 +122,12 @@ class Index:
     """A libdade index resident in device memory."""
 
     def __init__(self, base, n_clusters: int, kmeans_iters: int = 10, seed: int = 0, eps_pairs: int = 100000,
-                 assign=None, kmeans_init=None, pairs=None, stream=None):
+                 assign=None, kmeans_init=None, pairs=None, lead_format=LEAD_NONE, lead_dims=0, stream=None):
         L = lib()
         o = BuildOpts()
         L.dade_build_opts_default(C.byref(o))
         o.n_clusters, o.kmeans_iters, o.seed, o.eps_pairs = int(n_clusters), int(kmeans_iters), int(seed), int(eps_pairs)
+        o.lead_format, o.lead_dims = int(lead_format), int(lead_dims)
         keep = []
         if assign is not None:
             a = np.ascontiguousarray(assign, np.int32)
@@ -171,25 +176,25 @@ class Index:
         return out
 
     def search(self, q_rot, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-               threads=0, schedule=SCHED_TILE, flags=0, stream=None):
+               threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
-                       flags=flags)
+                       flags=flags, lead_stats=_ptr(lead_stats))
         _check(lib().dade_search(self._h, _ptr(q_rot), q_rot.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                  C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def scan(self, q_rot, probe, k, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-             threads=0, schedule=SCHED_TILE, flags=0, stream=None):
+             threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
-                       flags=flags)
+                       flags=flags, lead_stats=_ptr(lead_stats))
         _check(lib().dade_scan(self._h, _ptr(q_rot), _ptr(probe), q_rot.shape[0], int(k), probe.shape[1],
                                float(alpha), int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def query(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-              threads=0, schedule=SCHED_TILE, flags=0, stream=None):
+              threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
-                       flags=flags)
+                       flags=flags, lead_stats=_ptr(lead_stats))
         _check(lib().dade_query(self._h, _ptr(q), q.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                 C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
@@ -214,6 +219,10 @@ class Index:
                   FIELD_ROTATED: ((n, d), np.float32),
                   FIELD_RHO: ((max(0, self.info.d_pad // 16 - 1), self.info.eps_kept), np.float64)}
         shapes[FIELD_KMEANS_OBJ] = ((self.info.kmeans_iters,), np.float64)
+        ld = self.info.lead_dims
+        shapes[FIELD_LEAD_DEQ] = ((n, ld), np.float32)
+        shapes[FIELD_LEAD_ERR] = ((ld // 16, n), np.float32)
+        shapes[FIELD_LEAD_SCALE] = ((nc, ld // 16), np.float32)
         shape, dt = shapes[field]
         out = np.empty(shape, dt)
         _check(lib().dade_index_export(self._h, field, out.ctypes.data, out.nbytes))

@@ -39,10 +39,36 @@ def test_library_exports_every_declared_symbol(L):
     assert b"sm_103a" in L.dade_version()
 
 
-def test_struct_layouts_match_header(L):
-    assert C.sizeof(dade.BuildOpts) == 4 + 4 + 8 + 8 + 8 * 3 + 4 * 8
-    assert C.sizeof(dade.SearchOpts) == 4 + 4 + 8 + 4 * 8
-    assert C.sizeof(dade.Info) == 8 + 4 * 4 + 8 * 3 + 8
+def _c_layouts(tmp_path):
+    """sizeof / offsetof of every field of the ABI structs, from a C program
+    compiled against include/dade.h with the host C compiler."""
+    structs = {"dade_build_opts": dade.BuildOpts, "dade_search_opts": dade.SearchOpts, "dade_info": dade.Info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dade.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            cname, f, v = line.split()
+            got[(cname, f)] = int(v)
+    return structs, got
+
+
+def test_struct_layouts_match_header(L, tmp_path):
+    structs, got = _c_layouts(tmp_path)
+    for cname, py in structs.items():
+        assert C.sizeof(py) == got[(cname, "size")], cname
+        for f, _ in py._fields_:
+            assert getattr(py, f).offset == got[(cname, f)], (cname, f)
 
 
 def test_invalid_arguments_rejected_without_gpu(L):
@@ -64,6 +90,19 @@ def test_invalid_arguments_rejected_without_gpu(L):
                          None) == dade.EINVAL
     assert L.dade_sync(None, None) == dade.EINVAL
     assert L.dade_free_index(None) is None
+
+
+def test_lead_options_rejected_without_gpu(L):
+    h = C.c_void_p()
+    x = np.zeros((64, 40), np.float32)
+    for fmt, dims, msg in ((7, 16, b"lead_format"), (dade.LEAD_NONE, 16, b"lead_dims"),
+                           (dade.LEAD_BF16, 0, b"lead_dims"), (dade.LEAD_BF16, 24, b"lead_dims"),
+                           (dade.LEAD_FP8, 64, b"lead_dims")):   # D = 40 pads to 48
+        o = dade.BuildOpts()
+        L.dade_build_opts_default(C.byref(o))
+        o.n_clusters, o.lead_format, o.lead_dims = 2, fmt, dims
+        assert L.dade_build_index(x.ctypes.data, 64, 40, C.byref(o), C.byref(h), None) == dade.EINVAL
+        assert msg in L.dade_last_error()
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 7, 16, 64, 129])
