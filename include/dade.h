@@ -91,8 +91,10 @@ typedef enum {
 /* dade_search_opts.flags */
 enum {
     DADE_FLAG_GENERIC_KERNEL = 1,  /* skip the kernels specialised for D <= 128 (testing) */
-    DADE_FLAG_LEAD = 2             /* prefilter the first increment on the index's low-precision copy
+    DADE_FLAG_LEAD = 2,            /* prefilter the first increment on the index's low-precision copy
                                       (DADE mode, tile schedule, min(delta_d, D_pad) <= lead_dims) */
+    DADE_FLAG_QUERY_ORDER = 4      /* run the queries grouped by their first probed list (results are
+                                      the same in any order; grouped, they share list rows in L2) */
 };
 
 /*
@@ -202,6 +204,26 @@ dade_status dade_build_index(const float *base, int64_t n, int32_t d, const dade
 
 /* Release an index and its workspace.  NULL is ignored. */
 void dade_free_index(dade_index *ix);
+
+/*
+ * Write a built index to `path` as one binary file (this library's own
+ * format, version 1, little-endian; the paper stores no index): the FP64
+ * offline results (mean, basis, eigenvalues, rho_d sample), the list
+ * assignment and descriptors, and the device arrays (FP32 basis, centroids,
+ * packed vectors, ids, the optional low-precision leading blocks).
+ * Synchronous; the index is unchanged.  DADE_EIO if the file cannot be
+ * written.
+ */
+dade_status dade_save_index(const dade_index *ix, const char *path);
+
+/*
+ * Read an index written by dade_save_index onto the current device.  Every
+ * size is checked against the header and every list descriptor and slot id
+ * against the arrays it indexes before use: a damaged or foreign file gives
+ * DADE_EINVAL (DADE_EIO if unreadable or truncated) and no index.
+ * Synchronous.  The caller frees the result with dade_free_index.
+ */
+dade_status dade_load_index(const char *path, dade_index **out);
 
 /*
  * Query rotation q' = W^T (q - mu) (Lemma 1, Section 3.2): the transformed

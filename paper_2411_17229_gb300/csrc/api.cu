@@ -119,7 +119,8 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
                    "threads must be 0 (default), 128 or 256");
     DADE_CHECK_ARG(!opts || opts->schedule == DADE_SCHED_PIPELINED || opts->schedule == DADE_SCHED_TILE,
                    "unknown schedule");
-    DADE_CHECK_ARG(!opts || (opts->flags & ~(DADE_FLAG_GENERIC_KERNEL | DADE_FLAG_LEAD)) == 0, "unknown flag bits");
+    DADE_CHECK_ARG(!opts || (opts->flags & ~(DADE_FLAG_GENERIC_KERNEL | DADE_FLAG_LEAD | DADE_FLAG_QUERY_ORDER)) == 0,
+                   "unknown flag bits");
     if (opts && (opts->flags & DADE_FLAG_LEAD)) {
         DADE_CHECK_ARG(mode == DADE_MODE_DADE, "DADE_FLAG_LEAD needs mode DADE_MODE_DADE");
         DADE_CHECK_ARG(ix->lead_format != DADE_LEAD_NONE, "DADE_FLAG_LEAD on an index built without a lead copy");
@@ -184,6 +185,11 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.ids = ids_d;
     p.dists = dists_d;
     p.stats = opts ? opts->stats : nullptr;
+    if (opts && (opts->flags & DADE_FLAG_QUERY_ORDER)) {
+        DADE_TRY(ix->ws_order.ensure(sizeof(int32_t) * (size_t)nq));
+        DADE_TRY(dade::order_queries(ix, probe_dev, nq, nprobe, ix->ws_order.as<int32_t>(), s));
+        p.order = ix->ws_order.as<int32_t>();
+    }
     DADE_TRY(dade::scan(ix, nq, p, s));
     if (ids_host)
         DADE_TRY_CUDA(cudaMemcpyAsync(ids, ids_d, sizeof(int64_t) * (size_t)nq * k, cudaMemcpyDeviceToHost, s));
@@ -259,6 +265,36 @@ dade_status dade_build_index(const float *base, int64_t n, int32_t d, const dade
 }
 
 void dade_free_index(dade_index *ix) { delete ix; }
+
+dade_status dade_save_index(const dade_index *ix, const char *path) {
+    g_err.clear();
+    DADE_CHECK_ARG(ix != nullptr && path != nullptr, "NULL pointer");
+    return dade::save_index(ix, path);
+}
+
+dade_status dade_load_index(const char *path, dade_index **out) {
+    g_err.clear();
+    DADE_CHECK_ARG(path != nullptr && out != nullptr, "NULL pointer");
+    *out = nullptr;
+    dade_index *ix = new (std::nothrow) dade_index();
+    if (!ix) {
+        set_error("host allocation of the index failed");
+        return DADE_ENOMEM;
+    }
+    dade_status st;
+    try {
+        st = dade::load_index(path, ix);
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed while loading the index");
+        st = DADE_ENOMEM;
+    }
+    if (st != DADE_OK) {
+        delete ix;
+        return st;
+    }
+    *out = ix;
+    return DADE_OK;
+}
 
 dade_status dade_rotate_queries(const dade_index *ix, const float *q, int64_t nq, float *q_rot, dade_stream stream) {
     g_err.clear();
@@ -371,6 +407,8 @@ dade_status dade_reserve(dade_index *ix, int64_t max_nq, int32_t max_nprobe) {
     DADE_TRY(ix->ws_probe.ensure(sizeof(int32_t) * (size_t)max_nq * max_nprobe));
     DADE_TRY(ix->ws_qrot.ensure(sizeof(float) * (size_t)max_nq * ix->d));
     DADE_TRY(ix->ws_qin.ensure(sizeof(float) * (size_t)max_nq * ix->d));
+    DADE_TRY(ix->ws_order.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(max_nq, 1)));
+    DADE_TRY(ix->ws_ordcnt.ensure(sizeof(int) * (size_t)ix->nc));
     return DADE_OK;
 }
 

@@ -97,7 +97,7 @@ struct dade_index {
     dade::DevBuf lead_err;  // float [lead_nb][slots]: error norm over blocks 0..b (rounded up)
     int64_t data_floats = 0, slots = 0;
     // workspace (grown on demand, reused across calls)
-    mutable dade::DevBuf ws_dist, ws_probe, ws_qrot, ws_qin, ws_ids, ws_dists;
+    mutable dade::DevBuf ws_dist, ws_probe, ws_qrot, ws_qin, ws_ids, ws_dists, ws_order, ws_ordcnt;
 };
 
 namespace dade {
@@ -109,18 +109,28 @@ dade_status probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t 
                   int32_t nprobe, int32_t *probe_out, cudaStream_t s);
 dade_status centroid_norms(dade_index *ix, cudaStream_t s);
 
+// Permutation of the queries of a scan that groups them by first probed list
+// (order.cu); order[nq] on the device, written on stream s.
+dade_status order_queries(const dade_index *ix, const int32_t *probe, int64_t nq, int32_t nprobe, int32_t *order,
+                          cudaStream_t s);
+
 struct ScanParams {
     const float *q_rot;      // [nq][q_stride]
     int32_t q_stride;
     const int32_t *probe;    // [nq][nprobe]
     int32_t nprobe, k, tile, mode, delta_d, n_inc, spec, threads, schedule, generic, use_lead;
     int64_t *lead_stats;     // [nq] or null
+    const int32_t *order;    // [nq] execution order of the queries, or null (identity)
     float coef[DADE_MAX_DIM / DADE_BLOCK];   // per increment; prune iff P > coef[j] * r2
     int64_t *ids;            // [nq][k]
     float *dists;            // [nq][k]
     int64_t *stats;          // [nq][4] or null
 };
 dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s);
+
+// Index file (index_io.cpp).
+dade_status save_index(const dade_index *ix, const char *path);
+dade_status load_index(const char *path, dade_index *ix);
 
 // Host FP64 symmetric eigensolver (descending eigenvalues, column eigenvectors).
 bool sym_eig(int n, std::vector<double> &a, std::vector<double> &w, std::vector<double> &v);

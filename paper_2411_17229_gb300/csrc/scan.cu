@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
     __shared__ unsigned long long s_stats[4], s_lead;
 
     const int tid = threadIdx.x, quad = tid >> 2, lq = tid & 3;
-    const int64_t qi = blockIdx.x;
+    const int64_t qi = cta_query(a);
     const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k, a.nprobe, LF != 0);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     int4 *smeta = reinterpret_cast<int4 *>(smem + L.meta);
@@ -410,6 +410,7 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     a.out_ids = p.ids;
     a.out_d = p.dists;
     a.stats = p.stats;
+    a.order = p.order;
     a.err = ix->errflag.as<int>();
     a.q_stride = p.q_stride;
     a.nprobe = p.nprobe;

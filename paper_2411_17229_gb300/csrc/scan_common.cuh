@@ -44,7 +44,13 @@ struct ScanArgs {
     int64_t *lead_stats;         // [nq] candidates dropped by the prefilter, or null
     int64_t lead_slots;
     int lead_nb;
+    const int32_t *order;        // CTA b runs query order[b] (null: query b)
 };
+
+// The query a CTA runs.
+__device__ __forceinline__ int64_t cta_query(const ScanArgs &a) {
+    return a.order ? (int64_t)a.order[blockIdx.x] : (int64_t)blockIdx.x;
+}
 
 // ---------------------------------------------------------- PTX helpers ----
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }

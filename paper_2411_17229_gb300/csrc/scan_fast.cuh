@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_dade_fast(const ScanArgs a) {
     __shared__ unsigned long long s_stats[4], s_lead;
 
     const int tid = threadIdx.x, quad = tid >> 2, lq = tid & 3;
-    const int64_t qi = blockIdx.x;
+    const int64_t qi = cta_query(a);
     const FastLayout L = fast_layout(a.tile, SLOT, NSF, a.k, a.nprobe);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     int4 *smeta = reinterpret_cast<int4 *>(smem + L.meta);
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_fd_fast(const ScanArgs a) {
     __shared__ unsigned long long s_stats[4];
 
     const int tid = threadIdx.x, quad = tid >> 2, lq = tid & 3;
-    const int64_t qi = blockIdx.x;
+    const int64_t qi = cta_query(a);
     const SmemLayout L = layout(a.dp, a.tile, UB, a.ns, a.k, a.nprobe);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     int4 *smeta = reinterpret_cast<int4 *>(smem + L.meta);

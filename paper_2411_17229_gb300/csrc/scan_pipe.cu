@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_scan_pipe(const ScanArgs a) {
     __shared__ unsigned long long s_stats[4];
 
     const int tid = threadIdx.x, quad = tid >> 2, lq = tid & 3;
-    const int64_t qi = blockIdx.x;
+    const int64_t qi = cta_query(a);
     const int P = a.n_inc, T = a.tile, gb = a.gb;
     const PipeLayout L = pipe_layout(a.dp, T, gb, a.ns, a.k, a.nprobe, P);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libdade.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EIO = range(7)
 MODE_DADE, MODE_FD = 0, 1
 SCHED_TILE, SCHED_PIPELINED = 0, 1
-FLAG_GENERIC_KERNEL, FLAG_LEAD = 1, 2
+FLAG_GENERIC_KERNEL, FLAG_LEAD, FLAG_QUERY_ORDER = 1, 2, 4
 LEAD_NONE, LEAD_BF16, LEAD_FP8 = 0, 1, 2
 PIPE_MAX = 8
 (FIELD_MEAN, FIELD_BASIS, FIELD_EIGVAL, FIELD_CENTROIDS, FIELD_ASSIGN, FIELD_ROTATED, FIELD_RHO, FIELD_KMEANS_OBJ,
@@ -59,6 +59,8 @@ SIGNATURES = {
     "dade_build_opts_default": (None, [_vp]),
     "dade_build_index": (_i32, [_vp, _i64, _i32, _vp, _vp, _vp]),
     "dade_free_index": (None, [_vp]),
+    "dade_save_index": (_i32, [_vp, C.c_char_p]),
+    "dade_load_index": (_i32, [C.c_char_p, _vp]),
     "dade_rotate_queries": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "dade_probe": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
     "dade_search": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
@@ -150,6 +152,22 @@ class Index:
         _check(L.dade_index_info(h, C.byref(info)))
         self.info = info
         self.n, self.d, self.n_clusters = info.n, info.d, info.n_clusters
+
+    @classmethod
+    def load(cls, path):
+        """An index read back from a file written by save()."""
+        h = C.c_void_p()
+        _check(lib().dade_load_index(os.fsencode(path), C.byref(h)))
+        self = cls.__new__(cls)
+        self._h = h
+        info = Info()
+        _check(lib().dade_index_info(h, C.byref(info)))
+        self.info = info
+        self.n, self.d, self.n_clusters = info.n, info.d, info.n_clusters
+        return self
+
+    def save(self, path):
+        _check(lib().dade_save_index(self._h, os.fsencode(path)))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -127,3 +127,17 @@ def test_host_eigensolver_degenerate_and_diagonal(L):
     w, v = dade.host_sym_eig(B)
     assert np.allclose(w, [6, 0, 0, 0, 0, 0], atol=1e-12)
     assert np.allclose(B @ v, v * w[None, :], atol=1e-12)
+
+
+def test_load_rejects_foreign_files_without_gpu(L, tmp_path):
+    h = C.c_void_p()
+    assert L.dade_load_index(str(tmp_path / "none.dade").encode(), C.byref(h)) == dade.EIO
+    junk = tmp_path / "junk.dade"
+    junk.write_bytes(bytes(range(256)) * 4)
+    assert L.dade_load_index(str(junk).encode(), C.byref(h)) == dade.EINVAL
+    assert b"not a libdade index file" in L.dade_last_error()
+    hdr = tmp_path / "hdr.dade"    # right magic and version, impossible dimension
+    hdr.write_bytes(b"DADEIX01" + (1).to_bytes(4, "little") + (0x01020304).to_bytes(4, "little") + bytes(64))
+    assert L.dade_load_index(str(hdr).encode(), C.byref(h)) == dade.EINVAL
+    assert b"header out of range" in L.dade_last_error()
+    assert not h.value

@@ -262,3 +262,15 @@ def test_kmeans_parity():
     assert np.allclose(obj_g, o.kmeans_obj, rtol=1e-5)
     agree = np.mean(g.export(dade.FIELD_ASSIGN) == o.assign)
     assert agree > 0.995, agree
+
+
+@pytest.mark.parametrize("mode,delta_d,flags", [(dade.MODE_DADE, 32, 0), (dade.MODE_DADE, 64, 0),
+                                                (dade.MODE_FD, 32, 0),
+                                                (dade.MODE_DADE, 48, dade.FLAG_GENERIC_KERNEL)])
+def test_query_order_gives_same_results(c1, mode, delta_d, flags):
+    """Running the queries grouped by first probed list changes only the
+    order of the CTAs: ids, distance bits and statistics are unchanged."""
+    a = c1.gpu_search(10, 8, 0.1, delta_d, mode=mode, stats=True, flags=flags)
+    b = c1.gpu_search(10, 8, 0.1, delta_d, mode=mode, stats=True, flags=flags | dade.FLAG_QUERY_ORDER)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+    assert np.array_equal(a[2], b[2])
