@@ -209,8 +209,8 @@ void dade_free_index(dade_index *ix);
  * Write a built index to `path` as one binary file (this library's own
  * format, version 1, little-endian; the paper stores no index): the FP64
  * offline results (mean, basis, eigenvalues, rho_d sample), the list
- * assignment and descriptors, and the device arrays (FP32 basis, centroids,
- * packed vectors, ids, the optional low-precision leading blocks).
+ * assignment and descriptors, and the device arrays (centroids, packed
+ * vectors, ids, the optional low-precision leading blocks).
  * Synchronous; the index is unchanged.  DADE_EIO if the file cannot be
  * written.
  */

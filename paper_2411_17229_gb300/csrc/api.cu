@@ -312,7 +312,7 @@ dade_status dade_rotate_queries(const dade_index *ix, const float *q, int64_t nq
         DADE_TRY(ix->ws_qrot.ensure(sizeof(float) * (size_t)nq * ix->d));
         od = ix->ws_qrot.as<float>();
     }
-    DADE_TRY(dade::rotate(qd, nq, ix->d, ix->d, ix->W32.as<float>(), ix->mu32.as<float>(), ix->dp, od, s));
+    DADE_TRY(dade::rotate(ix, qd, nq, ix->d, od, s));
     if (out_host) {
         DADE_TRY_CUDA(cudaMemcpyAsync(q_rot, od, sizeof(float) * (size_t)nq * ix->d, cudaMemcpyDeviceToHost, s));
         DADE_TRY_CUDA(cudaStreamSynchronize(s));
@@ -394,8 +394,7 @@ dade_status dade_query(const dade_index *ix, const float *q, int64_t nq, int32_t
     const float *qd = stage_in(ix, q, (size_t)nq * ix->d, ix->ws_qin, s, &st);
     if (!qd) return st;
     DADE_TRY(ix->ws_qrot.ensure(sizeof(float) * (size_t)nq * ix->d));
-    DADE_TRY(dade::rotate(qd, nq, ix->d, ix->d, ix->W32.as<float>(), ix->mu32.as<float>(), ix->dp,
-                          ix->ws_qrot.as<float>(), s));
+    DADE_TRY(dade::rotate(ix, qd, nq, ix->d, ix->ws_qrot.as<float>(), s));
     return run_search(ix, ix->ws_qrot.as<float>(), nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
 }
 
@@ -409,6 +408,9 @@ dade_status dade_reserve(dade_index *ix, int64_t max_nq, int32_t max_nprobe) {
     DADE_TRY(ix->ws_qin.ensure(sizeof(float) * (size_t)max_nq * ix->d));
     DADE_TRY(ix->ws_order.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(max_nq, 1)));
     DADE_TRY(ix->ws_ordcnt.ensure(sizeof(int) * (size_t)ix->nc));
+    // tensor-core operand image of a query batch: 128-row tiles x 32-dim chunks x 32 KB
+    DADE_TRY(ix->ws_aimg.ensure((size_t)((max_nq + 127) / 128) * ((ix->d + 31) / 32) * 32768));
+    DADE_TRY(ix->ws_anorm.ensure(sizeof(float) * (size_t)std::max<int64_t>(max_nq, 1)));
     return DADE_OK;
 }
 
@@ -445,7 +447,7 @@ dade_status dade_index_info(const dade_index *ix, dade_info *info) {
     info->eps_kept = ix->eps_kept;
     info->data_bytes = (int64_t)ix->data.bytes;
     info->device_bytes = (int64_t)(ix->data.bytes + ix->ids.bytes + ix->meta.bytes + ix->cent.bytes + ix->cnorm.bytes +
-                                   ix->W32.bytes + ix->mu32.bytes + ix->errflag.bytes + ix->lead.bytes +
+                                   ix->WT32.bytes + ix->cent_img.bytes + ix->wt_img.bytes + ix->mu32.bytes + ix->errflag.bytes + ix->lead.bytes +
                                    ix->lead_err.bytes + ix->lead_scale.bytes);
     info->kmeans_iters = (int32_t)ix->kmeans_obj.size();
     info->lead_format = ix->lead_format;

@@ -293,49 +293,6 @@ __global__ void k_pair_prefix(const float *__restrict__ X, int dp, int nb, const
     }
 }
 
-// Rotation x' = W^T (x - mu) as a tiled FP32 GEMM: out[i][k] = sum_j (x[i][j] - mu[j]) W[j][k].
-__global__ void __launch_bounds__(256) k_rotate(const float *__restrict__ x, int64_t n, int d,
-                                                const float *__restrict__ W, const float *__restrict__ mu, int dp,
-                                                int out_cols, int out_stride, float *__restrict__ out) {
-    __shared__ __align__(16) float As[16][64];
-    __shared__ __align__(16) float Bs[16][64];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t r0 = (int64_t)blockIdx.x * 64;
-    const int c0 = blockIdx.y * 64;
-    float acc[4][4] = {};
-    for (int j0 = 0; j0 < d; j0 += 16) {
-        for (int e = tid; e < 64 * 16; e += 256) {
-            int row = e / 16, jj = e % 16;
-            int64_t r = r0 + row;
-            int j = j0 + jj;
-            As[jj][row] = (r < n && j < d) ? x[r * d + j] - mu[j] : 0.f;
-            int jb = j0 + e / 64, cb = c0 + e % 64;
-            Bs[e / 64][e % 64] = (jb < d && cb < dp) ? W[(int64_t)jb * dp + cb] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-            float4 a = *reinterpret_cast<const float4 *>(&As[jj][ty * 4]);
-            float4 b = *reinterpret_cast<const float4 *>(&Bs[jj][tx * 4]);
-            float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(av[i], bv[k], acc[i][k]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int64_t r = r0 + ty * 4 + i;
-        if (r >= n) continue;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            int c = c0 + tx * 4 + k;
-            if (c < out_cols) out[r * out_stride + c] = acc[i][k];
-        }
-    }
-}
 
 int grid_for(int64_t work, int threads) {
     int64_t g = (work + threads - 1) / threads;
@@ -343,15 +300,6 @@ int grid_for(int64_t work, int threads) {
 }
 
 } // namespace
-
-dade_status rotate(const float *x, int64_t n, int32_t d, int32_t out_stride, const float *W32, const float *mu32,
-                   int32_t dp, float *out, cudaStream_t s) {
-    if (n == 0) return DADE_OK;
-    int out_cols = out_stride < dp ? out_stride : dp;
-    dim3 grid((unsigned)((n + 63) / 64), (unsigned)((out_cols + 63) / 64));
-    k_rotate<<<grid, 256, 0, s>>>(x, n, d, W32, mu32, dp, out_cols, out_stride, out);
-    return launch_check("k_rotate");
-}
 
 dade_status launch_nearest(const float *X, int64_t n, int ldx, const float *cent, int nc, int ldc, int kdim,
                            int32_t *assign, double *obj, cudaStream_t s) {
@@ -430,22 +378,13 @@ dade_status build_index(const float *base, int64_t n, int32_t d, const dade_buil
     ix->Lam.assign(d + 1, 0.0);
     for (int k = 0; k < d; ++k) ix->Lam[k + 1] = ix->Lam[k] + ix->lam[k];
 
-    // ---- rotation of every base vector (FP32 GEMM) --------------------------------
-    {
-        std::vector<float> w32((size_t)d * dp, 0.f), m32(d);
-        for (int j = 0; j < d; ++j) {
-            m32[j] = (float)ix->mu[j];
-            for (int k = 0; k < d; ++k) w32[(size_t)j * dp + k] = (float)ix->W[(size_t)j * d + k];
-        }
-        DADE_TRY(ix->W32.alloc(sizeof(float) * w32.size()));
-        DADE_TRY(ix->mu32.alloc(sizeof(float) * d));
-        DADE_TRY_CUDA(cudaMemcpyAsync(ix->W32.p, w32.data(), sizeof(float) * w32.size(), cudaMemcpyHostToDevice, s));
-        DADE_TRY_CUDA(cudaMemcpyAsync(ix->mu32.p, m32.data(), sizeof(float) * d, cudaMemcpyHostToDevice, s));
-        DADE_TRY_CUDA(cudaStreamSynchronize(s));
-    }
+    // ---- rotation of every base vector (tensor-core GEMM) ---------------------------
+    DADE_TRY(upload_basis(ix, s));
+    DADE_TRY(ix->errflag.alloc(sizeof(int32_t) * 4));
+    DADE_TRY_CUDA(cudaMemsetAsync(ix->errflag.p, 0, sizeof(int32_t) * 4, s));
     DevBuf rot;
     DADE_TRY(rot.alloc(sizeof(float) * (size_t)n * dp));
-    DADE_TRY(rotate(x, n, d, dp, ix->W32.as<float>(), ix->mu32.as<float>(), dp, rot.as<float>(), s));
+    DADE_TRY(rotate_direct(ix, x, n, dp, rot.as<float>(), s));
     xbuf.release();
 
     // ---- inverted lists ----------------------------------------------------------
@@ -518,6 +457,7 @@ dade_status build_index(const float *base, int64_t n, int32_t d, const dade_buil
     lsum.release();
     lcnt.release();
     DADE_TRY(centroid_norms(ix, s));
+    DADE_TRY(prepare_tensor_operands(ix, s));
     ix->assign.resize(n);
     DADE_TRY_CUDA(cudaMemcpyAsync(ix->assign.data(), asg.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
     DADE_TRY_CUDA(cudaStreamSynchronize(s));
@@ -643,10 +583,29 @@ dade_status build_index(const float *base, int64_t n, int32_t d, const dade_buil
             std::sort(row, row + keep.size());
         }
     }
-    DADE_TRY(ix->errflag.alloc(sizeof(int32_t) * 4));
-    DADE_TRY_CUDA(cudaMemsetAsync(ix->errflag.p, 0, sizeof(int32_t) * 4, s));
     DADE_TRY_CUDA(cudaStreamSynchronize(s));
+    int32_t err = 0;
+    DADE_TRY_CUDA(cudaMemcpy(&err, ix->errflag.p, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err != 0) {
+        set_error("a bounded device-side wait gave up during the index build");
+        return DADE_ETIMEOUT;
+    }
     return DADE_OK;
+}
+
+// FP32 copies of the basis (as W^T, dp x dp, zero padded) and of the mean.
+dade_status upload_basis(dade_index *ix, cudaStream_t s) {
+    const int d = ix->d, dp = ix->dp;
+    std::vector<float> wt((size_t)dp * dp, 0.f), m32(d);
+    for (int j = 0; j < d; ++j) {
+        m32[j] = (float)ix->mu[j];
+        for (int k = 0; k < d; ++k) wt[(size_t)k * dp + j] = (float)ix->W[(size_t)j * d + k];
+    }
+    DADE_TRY(ix->WT32.alloc(sizeof(float) * wt.size()));
+    DADE_TRY(ix->mu32.alloc(sizeof(float) * d));
+    DADE_TRY_CUDA(cudaMemcpyAsync(ix->WT32.p, wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice, s));
+    DADE_TRY_CUDA(cudaMemcpyAsync(ix->mu32.p, m32.data(), sizeof(float) * d, cudaMemcpyHostToDevice, s));
+    return cudaStreamSynchronize(s) == cudaSuccess ? DADE_OK : launch_check("upload_basis");
 }
 
 } // namespace dade

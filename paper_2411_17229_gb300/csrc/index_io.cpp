@@ -4,9 +4,9 @@
 // scalar description of the index, then every array as (u64 byte count,
 // bytes): the host FP64 arrays (mean, basis, eigenvalues, their prefix sums,
 // the sorted rho_d sample, list of every vector, list descriptors, k-means
-// objectives) and the device arrays (FP32 basis and mean, rotated centroids
-// and their squared norms, the packed dimension-blocked vectors, slot ids and
-// the optional low-precision leading blocks).  Loading checks every size
+// objectives) and the device arrays (rotated centroids and their squared
+// norms, the packed dimension-blocked vectors, slot ids and the optional
+// low-precision leading blocks); the FP32 basis is rebuilt from the FP64 one.  Loading checks every size
 // against the scalars and every list descriptor and id against the arrays it
 // indexes before anything reaches the device, so a damaged file is refused
 // instead of producing out-of-range reads in the kernels.
@@ -120,8 +120,6 @@ dade_status save_index(const dade_index *ix, const char *path) {
         set_error("write failed");
         return DADE_EIO;
     }
-    DADE_TRY(put_dev(f, ix->W32, sizeof(float) * (size_t)s.d * s.dp));
-    DADE_TRY(put_dev(f, ix->mu32, sizeof(float) * (size_t)s.d));
     DADE_TRY(put_dev(f, ix->cent, sizeof(float) * (size_t)s.nc * s.dp));
     DADE_TRY(put_dev(f, ix->cnorm, sizeof(float) * (size_t)s.nc));
     DADE_TRY(put_dev(f, ix->data, sizeof(float) * (size_t)s.data_floats));
@@ -205,8 +203,6 @@ dade_status load_index(const char *path, dade_index *ix) {
     ix->eps_kept = s.eps_kept;
     ix->data_floats = s.data_floats;
     ix->slots = s.slots;
-    DADE_TRY(get_dev(f, ix->W32, sizeof(float) * d * s.dp, "FP32 basis"));
-    DADE_TRY(get_dev(f, ix->mu32, sizeof(float) * d, "FP32 mean"));
     DADE_TRY(get_dev(f, ix->cent, sizeof(float) * (size_t)s.nc * s.dp, "centroids"));
     DADE_TRY(get_dev(f, ix->cnorm, sizeof(float) * (size_t)s.nc, "centroid norms"));
     DADE_TRY(get_dev(f, ix->data, sizeof(float) * (size_t)s.data_floats, "packed vectors"));
@@ -231,6 +227,8 @@ dade_status load_index(const char *path, dade_index *ix) {
         DADE_TRY(get_dev(f, ix->lead_err, sizeof(float) * (size_t)s.slots * s.lead_nb, "lead error norms"));
         DADE_TRY(get_dev(f, ix->lead_scale, sizeof(float) * (size_t)s.nc * s.lead_nb, "lead scales"));
     }
+    DADE_TRY(upload_basis(ix, 0));
+    DADE_TRY(prepare_tensor_operands(ix, 0));
     DADE_TRY(ix->meta.alloc(sizeof(ListMeta) * (size_t)s.nc));
     DADE_TRY_CUDA(cudaMemcpy(ix->meta.p, ix->lists.data(), sizeof(ListMeta) * (size_t)s.nc, cudaMemcpyHostToDevice));
     DADE_TRY(ix->errflag.alloc(sizeof(int32_t) * 4));

@@ -82,7 +82,8 @@ struct dade_index {
     std::vector<dade::ListMeta> lists;      // [nc]
     std::vector<double> kmeans_obj;
     // device
-    dade::DevBuf W32;       // float [d][dp]: W^T applied as x' = sum_j (x_j - mu_j) W[j][k]
+    dade::DevBuf WT32;      // float [dp][dp]: W^T, row k = w_k (zero padded); x'_k = <w_k, x - mu>
+    dade::DevBuf cent_img, wt_img;   // centroids and W^T split into TF32 hi/lo tiles (tc_gemm.cu)
     dade::DevBuf mu32;      // float [d]
     dade::DevBuf cent;      // float [nc][dp] rotated centroids (zero padded)
     dade::DevBuf cnorm;     // float [nc] squared norms of the centroids
@@ -97,14 +98,26 @@ struct dade_index {
     dade::DevBuf lead_err;  // float [lead_nb][slots]: error norm over blocks 0..b (rounded up)
     int64_t data_floats = 0, slots = 0;
     // workspace (grown on demand, reused across calls)
-    mutable dade::DevBuf ws_dist, ws_probe, ws_qrot, ws_qin, ws_ids, ws_dists, ws_order, ws_ordcnt;
+    mutable dade::DevBuf ws_dist, ws_probe, ws_qrot, ws_qin, ws_ids, ws_dists, ws_order, ws_ordcnt, ws_aimg, ws_anorm;
 };
 
 namespace dade {
 
 // Kernel launchers (each returns DADE_OK or DADE_ECUDA after checking the launch).
-dade_status rotate(const float *x, int64_t n, int32_t d, int32_t out_stride, const float *W32,
-                   const float *mu32, int32_t dp, float *out, cudaStream_t s);
+// Tensor-core GEMMs (tc_gemm.cu).  x' = W^T (x - mu) for n rows of x (row
+// stride d): out[i * out_stride + k] for k < min(out_stride, dp); rotate()
+// uses the index's workspace, rotate_direct() none (build time).
+dade_status rotate(const dade_index *ix, const float *x, int64_t n, int32_t out_stride, float *out, cudaStream_t s);
+dade_status rotate_direct(const dade_index *ix, const float *x, int64_t n, int32_t out_stride, float *out,
+                          cudaStream_t s);
+// dist[i * nc + j] = max(0, ||q_i||^2 + ||c_j||^2 - 2 <q_i, c_j>); the
+// direct form allocates nothing (dade_probe_noalloc).
+dade_status probe_distances(const dade_index *ix, const float *q_rot, int64_t nq, int32_t q_stride, float *dist,
+                            cudaStream_t s);
+dade_status probe_distances_direct(const dade_index *ix, const float *q_rot, int64_t nq, int32_t q_stride, float *dist,
+                                   cudaStream_t s);
+// Operand images of the centroids and of W^T (after build or load).
+dade_status prepare_tensor_operands(dade_index *ix, cudaStream_t s);
 dade_status probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t q_stride,
                   int32_t nprobe, int32_t *probe_out, cudaStream_t s);
 dade_status centroid_norms(dade_index *ix, cudaStream_t s);
@@ -127,6 +140,9 @@ struct ScanParams {
     int64_t *stats;          // [nq][4] or null
 };
 dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s);
+
+// FP32 basis W^T and mean on the device, from the host FP64 copies (build.cu).
+dade_status upload_basis(dade_index *ix, cudaStream_t s);
 
 // Index file (index_io.cpp).
 dade_status save_index(const dade_index *ix, const char *path);

@@ -1,8 +1,9 @@
 // probe.cu -- IVF coarse probe (Section 3.4): the nprobe inverted lists whose
 // centroids are nearest to each rotated query, ordered by (distance, list id).
 //
-// Step 1 writes the query x centroid squared-distance matrix with a
-// register-blocked FP32 GEMM tile (||q||^2 + ||c||^2 - 2 <q, c>).
+// Step 1 writes the query x centroid squared-distance matrix
+// ||q||^2 + ||c||^2 - 2 <q, c> with the tensor-core GEMM of tc_gemm.cu
+// (3xTF32, FP32-accurate).
 // Step 2 selects, per query, the nprobe smallest 64-bit keys
 // (float bits of the distance << 32 | list id) by an 8-pass radix select over
 // 8-bit digits; keys are unique, so exactly nprobe keys are <= the selected
@@ -17,116 +18,6 @@ namespace dade {
 
 namespace {
 
-// Squared distance of every query to every centroid as
-// ||q||^2 + ||c||^2 - 2 <q, c> (FP32; cnorm precomputed at build), clamped at
-// 0.  Register-blocked GEMM tile: a CTA of 256 threads covers 128 queries x
-// 128 centroids, each thread 8 x 8 outputs; K advances in steps of 16 through
-// double-buffered shared memory (stored k-major, padded against bank
-// conflicts), so every pair of float4 shared loads feeds 64 FMAs.
-constexpr int PQ = 128, PC = 128, PBK = 16, PPAD = 4;
-
-__global__ void __launch_bounds__(256) k_probe_gemm(const float *__restrict__ Q, int64_t nq, int ldq, int kdim,
-                                                    const float *__restrict__ cent, int nc, int ldc,
-                                                    const float *__restrict__ cnorm, float *__restrict__ dist) {
-    __shared__ __align__(16) float As[2][PBK][PQ + PPAD];
-    __shared__ __align__(16) float Bs[2][PBK][PC + PPAD];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t q0 = (int64_t)blockIdx.x * PQ;
-    const int c0 = blockIdx.y * PC;
-    float acc[8][8], qn[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        qn[i] = 0.f;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    }
-    // each thread moves 2 float4 of A and 2 of B per K step: rows r = e / 4, k4 = (e % 4) * 4
-    float4 ra[2], rb[2];
-    auto gload = [&](int k0) {
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int e = tid + t * 256, row = e >> 2, k4 = (e & 3) * 4;
-            const int64_t qr = q0 + row;
-            const int cr = c0 + row;
-            float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
-            if (qr < nq) {
-                const float *src = Q + qr * ldq + k0 + k4;
-                va.x = k0 + k4 + 0 < kdim ? src[0] : 0.f;
-                va.y = k0 + k4 + 1 < kdim ? src[1] : 0.f;
-                va.z = k0 + k4 + 2 < kdim ? src[2] : 0.f;
-                va.w = k0 + k4 + 3 < kdim ? src[3] : 0.f;
-            }
-            if (cr < nc) {
-                const float *src = cent + (int64_t)cr * ldc + k0 + k4;
-                vb.x = k0 + k4 + 0 < kdim ? src[0] : 0.f;
-                vb.y = k0 + k4 + 1 < kdim ? src[1] : 0.f;
-                vb.z = k0 + k4 + 2 < kdim ? src[2] : 0.f;
-                vb.w = k0 + k4 + 3 < kdim ? src[3] : 0.f;
-            }
-            ra[t] = va;
-            rb[t] = vb;
-        }
-    };
-    auto sstore = [&](int buf) {
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int e = tid + t * 256, row = e >> 2, k4 = (e & 3) * 4;
-            As[buf][k4 + 0][row] = ra[t].x;
-            As[buf][k4 + 1][row] = ra[t].y;
-            As[buf][k4 + 2][row] = ra[t].z;
-            As[buf][k4 + 3][row] = ra[t].w;
-            Bs[buf][k4 + 0][row] = rb[t].x;
-            Bs[buf][k4 + 1][row] = rb[t].y;
-            Bs[buf][k4 + 2][row] = rb[t].z;
-            Bs[buf][k4 + 3][row] = rb[t].w;
-        }
-    };
-    gload(0);
-    sstore(0);
-    __syncthreads();
-    int buf = 0;
-    for (int k0 = 0; k0 < kdim; k0 += PBK) {
-        const bool more = k0 + PBK < kdim;
-        if (more) gload(k0 + PBK);
-#pragma unroll
-        for (int kk = 0; kk < PBK; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 8]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 8 + 4]);
-            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 8]);
-            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 8 + 4]);
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                qn[i] = fmaf(av[i], av[i], qn[i]);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-            }
-        }
-        if (more) {
-            sstore(buf ^ 1);
-            __syncthreads();
-            buf ^= 1;
-        }
-    }
-    float cn[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int c = c0 + tx * 8 + j;
-        cn[j] = c < nc ? cnorm[c] : 0.f;
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int64_t r = q0 + ty * 8 + i;
-        if (r >= nq) continue;
-        float *out = dist + r * nc + c0 + tx * 8;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (c0 + tx * 8 + j < nc) out[j] = fmaxf(0.f, fmaf(-2.f, acc[i][j], qn[i] + cn[j]));
-    }
-}
-
-// ||c||^2 of every centroid row (one warp per row).
 __global__ void k_row_sqnorm(const float *__restrict__ X, int n, int ld, int kdim, float *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -235,10 +126,7 @@ dade_status probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t 
                   int32_t *probe_out, cudaStream_t s) {
     if (nq == 0) return DADE_OK;
     DADE_TRY(ix->ws_dist.ensure(sizeof(float) * (size_t)nq * ix->nc));
-    dim3 g((unsigned)((nq + PQ - 1) / PQ), (unsigned)((ix->nc + PC - 1) / PC));
-    k_probe_gemm<<<g, 256, 0, s>>>(q_rot, nq, q_stride, ix->d, ix->cent.as<float>(), ix->nc, ix->dp,
-                                   ix->cnorm.as<float>(), ix->ws_dist.as<float>());
-    DADE_TRY(launch_check("k_probe_gemm"));
+    DADE_TRY(probe_distances(ix, q_rot, nq, q_stride, ix->ws_dist.as<float>(), s));
     size_t smem = sizeof(unsigned long long) * (size_t)nprobe;
     if (smem > 48 * 1024)
         DADE_TRY_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -327,10 +215,7 @@ extern "C" dade_status dade_probe_noalloc(const dade_index *ix, const float *q_r
     float *dist = nullptr;
     DADE_TRY(scratch_address(&dist));
     cudaStream_t s = (cudaStream_t)stream;
-    dim3 g((unsigned)((nq + PQ - 1) / PQ), (unsigned)((ix->nc + PC - 1) / PC));
-    k_probe_gemm<<<g, 256, 0, s>>>(q_rot, nq, ix->d, ix->d, ix->cent.as<float>(), ix->nc, ix->dp, ix->cnorm.as<float>(),
-                                   dist);
-    DADE_TRY(launch_check("k_probe_gemm"));
+    DADE_TRY(probe_distances_direct(ix, q_rot, nq, ix->d, dist, s));
     size_t smem = sizeof(unsigned long long) * (size_t)nprobe;
     if (smem > 48 * 1024)
         DADE_TRY_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
