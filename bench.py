@@ -65,6 +65,8 @@ def parse():
                     help="profiling run: fixed --point, no autotune, ground truth, baselines or e2e")
     ap.add_argument("--point", default="nprobe=20,alpha=0.3,delta_d=64,tile=256,threads=128",
                     help="operating point of --profile (comma-separated key=value)")
+    ap.add_argument("--tail-from", type=int, default=32,
+                    help="first dim of the index's row-major tail copy (0: none); survivors gather from it")
     ap.add_argument("--lead", default="bf16", choices=["none", "bf16", "fp8"],
                     help="low-precision copy of the leading 64 dims built into the index; the autotuner "
                          "tries the prefilter on it beside the FP32 path")
@@ -91,7 +93,7 @@ def run_profile(args):
     base, queries, _ = synth.make(w, n=n, nq=nq)
     lf, ld = lead_opts(args, dade, w.d)
     ix = dade.Index(torch.from_numpy(base).cuda(), nc, kmeans_iters=w.kmeans_iters, seed=synth.SEED_KMEANS,
-                    lead_format=lf, lead_dims=ld)
+                    lead_format=lf, lead_dims=ld, tail_from=tail_opt(args, w.d))
     q = torch.from_numpy(queries).cuda()
     pt = parse_point(args.point, dade)
     qr = torch.empty_like(q)
@@ -118,6 +120,11 @@ def run_profile(args):
 
 
 # ----------------------------------------------------------------- helpers --
+def tail_opt(args, d):
+    """tail_from of the index (0 when D is too small for it)."""
+    return args.tail_from if 0 < args.tail_from < (d + 15) // 16 * 16 else 0
+
+
 def lead_opts(args, dade, d):
     """Index build options of --lead: (format, leading dims)."""
     lf = {"none": dade.LEAD_NONE, "bf16": dade.LEAD_BF16, "fp8": dade.LEAD_FP8}[args.lead]
@@ -298,7 +305,11 @@ def run_ours(args):
     q = torch.from_numpy(queries).cuda()
     t0 = time.time()
     lf, ld = lead_opts(args, dade, w.d)
-    ix = dade.Index(xb, nc, kmeans_iters=w.kmeans_iters, seed=synth.SEED_KMEANS, lead_format=lf, lead_dims=ld)
+    tf = tail_opt(args, w.d)
+    ix = dade.Index(xb, nc, kmeans_iters=w.kmeans_iters, seed=synth.SEED_KMEANS, lead_format=lf, lead_dims=ld,
+                    tail_from=tf)
+    # flags every point uses: results do not depend on them (query order, tail copy)
+    fixed = dade.FLAG_QUERY_ORDER | (dade.FLAG_ROW_TAIL if tf else 0)
     torch.cuda.synchronize()
     log(f"[bench] index built in {time.time() - t0:.1f}s (max list {ix.info.max_list}, "
         f"{ix.info.data_bytes / 2**20:.0f} MiB packed)")
@@ -344,7 +355,8 @@ def run_ours(args):
     fd_best, fd_rec = None, {}
     for nprobe in grid:              # FD time grows with nprobe: the first point reaching the target wins
         for threads, tile in ((128, 64), (128, 128), (256, 128)):
-            pt = {"mode": dade.MODE_FD, "nprobe": nprobe, "tile": tile, "threads": threads}
+            pt = {"mode": dade.MODE_FD, "nprobe": nprobe, "tile": tile, "threads": threads,
+                  "flags": dade.FLAG_QUERY_ORDER}
             ms, rc = measure(pt)
             fd_rec[nprobe] = rc
             if rc >= RECALL_TARGET and (fd_best is None or ms < fd_best[0]):
@@ -361,7 +373,8 @@ def run_ours(args):
             for schedule, spec, tile, threads, fl in variants:
                     for nprobe in [p for p in grid if p >= n0][:3]:
                         pt = {"mode": dade.MODE_DADE, "nprobe": nprobe, "alpha": alpha, "delta_d": dd,
-                              "spec": spec, "tile": tile, "threads": threads, "schedule": schedule, "flags": fl}
+                              "spec": spec, "tile": tile, "threads": threads, "schedule": schedule,
+                              "flags": fl | fixed}
                         ms, rc = measure(pt)
                         tried.append((ms, rc, pt))
                         if rc >= RECALL_TARGET:
@@ -449,7 +462,8 @@ def run_ours(args):
     rc_timed = recall_at_k(torch, xb, q, ids, gt_kth, K)
 
     # ---- FD baseline timed the same way (same step structure) ------------------------
-    fd_pt = fd_best[2] if fd_best else {"mode": dade.MODE_FD, "nprobe": n0, "tile": 128, "threads": 128}
+    fd_pt = fd_best[2] if fd_best else {"mode": dade.MODE_FD, "nprobe": n0, "tile": 128, "threads": 128,
+                                        "flags": dade.FLAG_QUERY_ORDER}
     fd_ms = []
     pr_fd = torch.empty(nq, fd_pt["nprobe"], dtype=torch.int32, device="cuda")
     for i in range(args.warmup + args.steps):
@@ -459,7 +473,7 @@ def run_ours(args):
         ix.rotate(q, qr, stream=sh)
         ix.probe(qr, fd_pt["nprobe"], pr_fd, stream=sh)
         ix.scan(qr, pr_fd, K, 0.1, 32, ids, dists, mode=dade.MODE_FD, tile=fd_pt["tile"],
-                threads=fd_pt["threads"], stream=sh)
+                threads=fd_pt["threads"], flags=fd_pt["flags"], stream=sh)
         e1.record(stream)
         torch.cuda.synchronize()
         if i >= args.warmup:
@@ -507,6 +521,8 @@ def run_ours(args):
                        "spec": point.get("spec"), "tile": point["tile"], "threads": point["threads"],
                        "schedule": "tile" if point.get("schedule", 0) == 0 else "pipelined",
                        "lead_prefilter": ({"format": args.lead, "dims": ld} if use_lead else None),
+                       "flags": {"query_order": bool(point["flags"] & dade.FLAG_QUERY_ORDER),
+                                 "row_tail_from": tf if point["flags"] & dade.FLAG_ROW_TAIL else None},
                        "l2": "index 512 MB > L2; 256 MB flush written between timed steps",
                        "parallelism": f"replicas x{world}"},
             "recall": round(rc_timed, 5),

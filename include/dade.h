@@ -93,8 +93,11 @@ enum {
     DADE_FLAG_GENERIC_KERNEL = 1,  /* skip the kernels specialised for D <= 128 (testing) */
     DADE_FLAG_LEAD = 2,            /* prefilter the first increment on the index's low-precision copy
                                       (DADE mode, tile schedule, min(delta_d, D_pad) <= lead_dims) */
-    DADE_FLAG_QUERY_ORDER = 4      /* run the queries grouped by their first probed list (results are
+    DADE_FLAG_QUERY_ORDER = 4,     /* run the queries grouped by their first probed list (results are
                                       the same in any order; grouped, they share list rows in L2) */
+    DADE_FLAG_ROW_TAIL = 8         /* a candidate that survives the first increment reads its dims from
+                                      tail_from on from the index's row-major copy: one contiguous row
+                                      instead of one 64-byte piece per 16-dim slab.  Same results. */
 };
 
 /*
@@ -134,7 +137,9 @@ typedef struct {
     const int64_t *pairs;      /* host, optional [2 * eps_pairs]: pair ids (i != j) for eps_d */
     int32_t lead_format;       /* dade_lead_format: extra low-precision copy of the leading dims */
     int32_t lead_dims;         /* leading dims in that copy (multiple of 16, <= D; 0 = none) */
-    int32_t reserved[6];
+    int32_t tail_from;         /* keep a row-major FP32 copy of dims [tail_from, D) of every vector
+                                  (multiple of 16, < D; 0 = none), see DADE_FLAG_ROW_TAIL */
+    int32_t reserved[5];
 } dade_build_opts;
 
 /* Search options; NULL means all defaults. */
@@ -166,7 +171,7 @@ typedef struct {
     int32_t kmeans_iters;      /* Lloyd iterations run (0 when lists were given) */
     int32_t lead_format;       /* dade_lead_format of the index */
     int32_t lead_dims;
-    int32_t reserved;
+    int32_t tail_from;         /* 0 or the first dim of the row-major copy */
 } dade_info;
 
 /* Fields for dade_index_export (host copies, for inspection and tests). */

@@ -119,8 +119,11 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
                    "threads must be 0 (default), 128 or 256");
     DADE_CHECK_ARG(!opts || opts->schedule == DADE_SCHED_PIPELINED || opts->schedule == DADE_SCHED_TILE,
                    "unknown schedule");
-    DADE_CHECK_ARG(!opts || (opts->flags & ~(DADE_FLAG_GENERIC_KERNEL | DADE_FLAG_LEAD | DADE_FLAG_QUERY_ORDER)) == 0,
+    DADE_CHECK_ARG(!opts || (opts->flags & ~(DADE_FLAG_GENERIC_KERNEL | DADE_FLAG_LEAD | DADE_FLAG_QUERY_ORDER |
+                                             DADE_FLAG_ROW_TAIL)) == 0,
                    "unknown flag bits");
+    DADE_CHECK_ARG(!opts || !(opts->flags & DADE_FLAG_ROW_TAIL) || ix->tail_nb0 > 0,
+                   "DADE_FLAG_ROW_TAIL on an index built without tail_from");
     if (opts && (opts->flags & DADE_FLAG_LEAD)) {
         DADE_CHECK_ARG(mode == DADE_MODE_DADE, "DADE_FLAG_LEAD needs mode DADE_MODE_DADE");
         DADE_CHECK_ARG(ix->lead_format != DADE_LEAD_NONE, "DADE_FLAG_LEAD on an index built without a lead copy");
@@ -178,6 +181,7 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.schedule = opts ? opts->schedule : DADE_SCHED_TILE;
     p.generic = opts ? (opts->flags & DADE_FLAG_GENERIC_KERNEL) != 0 : 0;
     p.use_lead = opts ? (opts->flags & DADE_FLAG_LEAD) != 0 : 0;
+    p.use_tail = opts ? (opts->flags & DADE_FLAG_ROW_TAIL) != 0 : 0;
     p.lead_stats = opts ? opts->lead_stats : nullptr;
     p.delta_d = delta_d;
     if (p.mode == DADE_MODE_DADE) p.n_inc = coef_table(ix, alpha, delta_d, nullptr, p.coef);
@@ -249,6 +253,9 @@ dade_status dade_build_index(const float *base, int64_t n, int32_t d, const dade
     else
         DADE_CHECK_ARG(opts->lead_dims >= 16 && opts->lead_dims % 16 == 0 && opts->lead_dims <= (d + 15) / 16 * 16,
                        "lead_dims must be a multiple of 16 in [16, D rounded up to 16]");
+    DADE_CHECK_ARG(opts->tail_from == 0 || (opts->tail_from >= 16 && opts->tail_from % 16 == 0 &&
+                                            opts->tail_from < (d + 15) / 16 * 16),
+                   "tail_from must be 0 or a multiple of 16 in [16, D rounded up to 16)");
     *out = nullptr;
     dade_index *ix = new (std::nothrow) dade_index();
     if (!ix) {
@@ -448,11 +455,11 @@ dade_status dade_index_info(const dade_index *ix, dade_info *info) {
     info->data_bytes = (int64_t)ix->data.bytes;
     info->device_bytes = (int64_t)(ix->data.bytes + ix->ids.bytes + ix->meta.bytes + ix->cent.bytes + ix->cnorm.bytes +
                                    ix->WT32.bytes + ix->cent_img.bytes + ix->wt_img.bytes + ix->mu32.bytes + ix->errflag.bytes + ix->lead.bytes +
-                                   ix->lead_err.bytes + ix->lead_scale.bytes);
+                                   ix->lead_err.bytes + ix->lead_scale.bytes + ix->tail.bytes);
     info->kmeans_iters = (int32_t)ix->kmeans_obj.size();
     info->lead_format = ix->lead_format;
     info->lead_dims = ix->lead_dims;
-    info->reserved = 0;
+    info->tail_from = ix->tail_nb0 * 16;
     return DADE_OK;
 }
 

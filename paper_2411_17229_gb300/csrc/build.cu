@@ -264,6 +264,20 @@ __global__ void k_pack_lead(const float *__restrict__ X, int64_t n, int dp, int 
     }
 }
 
+// Row-major copy of dims [16 nb0, dp) of vector i at slot(list) + pos[i].
+__global__ void k_pack_tail(const float *__restrict__ X, int64_t n, int dp, int nb0, const int32_t *__restrict__ assign,
+                            const int32_t *__restrict__ pos, const ListMeta *__restrict__ meta, float *__restrict__ tail) {
+    const int tw = dp - 16 * nb0;
+    const int64_t total = n * (int64_t)(tw / 4);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / (tw / 4);
+        const int k4 = (int)(e % (tw / 4));
+        const ListMeta m = meta[assign[i]];
+        const float4 v = *reinterpret_cast<const float4 *>(X + i * dp + 16 * nb0 + 4 * k4);
+        *reinterpret_cast<float4 *>(tail + (m.slot + pos[i]) * tw + 4 * k4) = v;
+    }
+}
+
 // Prefix sums P_d (FP64) of one sampled pair's squared difference at every
 // d = 16 (b + 1); one warp per pair, each half-warp one 16-dim block.
 __global__ void k_pair_prefix(const float *__restrict__ X, int dp, int nb, const int64_t *__restrict__ pairs,
@@ -495,6 +509,16 @@ dade_status build_index(const float *base, int64_t n, int32_t d, const dade_buil
         k_pack<<<grid_for(n * nb, 256), 256, 0, s>>>(rot.as<float>(), n, dp, nb, asg.as<int32_t>(), posb.as<int32_t>(),
                                                     ix->meta.as<ListMeta>(), ix->data.as<float>(), ix->ids.as<int32_t>());
         DADE_TRY(launch_check("k_pack"));
+        if (o.tail_from > 0) {
+            ix->tail_nb0 = o.tail_from / 16;
+            ix->tail_w = dp - o.tail_from;
+            DADE_TRY(ix->tail.alloc(sizeof(float) * (size_t)ix->slots * ix->tail_w));
+            DADE_TRY_CUDA(cudaMemsetAsync(ix->tail.p, 0, sizeof(float) * (size_t)ix->slots * ix->tail_w, s));
+            k_pack_tail<<<grid_for(n * (ix->tail_w / 4), 256), 256, 0, s>>>(
+                rot.as<float>(), n, dp, ix->tail_nb0, asg.as<int32_t>(), posb.as<int32_t>(), ix->meta.as<ListMeta>(),
+                ix->tail.as<float>());
+            DADE_TRY(launch_check("k_pack_tail"));
+        }
         if (o.lead_format != DADE_LEAD_NONE) {
             const int lnb = o.lead_dims / 16, es = o.lead_format == DADE_LEAD_BF16 ? 2 : 1;
             ix->lead_format = o.lead_format;

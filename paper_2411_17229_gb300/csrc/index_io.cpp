@@ -5,8 +5,9 @@
 // bytes): the host FP64 arrays (mean, basis, eigenvalues, their prefix sums,
 // the sorted rho_d sample, list of every vector, list descriptors, k-means
 // objectives) and the device arrays (rotated centroids and their squared
-// norms, the packed dimension-blocked vectors, slot ids and the optional
-// low-precision leading blocks); the FP32 basis is rebuilt from the FP64 one.  Loading checks every size
+// norms, the packed dimension-blocked vectors, slot ids, the optional
+// low-precision leading blocks and the optional row-major tail copy); the
+// FP32 basis is rebuilt from the FP64 one.  Loading checks every size
 // against the scalars and every list descriptor and id against the arrays it
 // indexes before anything reaches the device, so a damaged file is refused
 // instead of producing out-of-range reads in the kernels.
@@ -28,7 +29,7 @@ constexpr uint32_t VERSION = 1, ENDIAN = 0x01020304u;
 
 struct Scalars {
     int64_t n, eps_kept, data_floats, slots;
-    int32_t d, dp, nb, nc, max_list, lead_format, lead_dims, lead_nb;
+    int32_t d, dp, nb, nc, max_list, lead_format, lead_dims, lead_nb, tail_nb0, tail_w;
 };
 
 struct File {
@@ -111,8 +112,8 @@ dade_status save_index(const dade_index *ix, const char *path) {
         return DADE_EIO;
     }
     FILE *f = fh.f;
-    Scalars s{ix->n, ix->eps_kept, ix->data_floats, ix->slots, ix->d, ix->dp, ix->nb, ix->nc, ix->max_list,
-              ix->lead_format, ix->lead_dims, ix->lead_nb};
+    Scalars s{ix->n,        ix->eps_kept,  ix->data_floats, ix->slots,   ix->d,        ix->dp,      ix->nb,
+              ix->nc,       ix->max_list,  ix->lead_format, ix->lead_dims, ix->lead_nb, ix->tail_nb0, ix->tail_w};
     bool ok = put(f, MAGIC, sizeof MAGIC) && put(f, &VERSION, 4) && put(f, &ENDIAN, 4) && put(f, &s, sizeof s) &&
               put_vec(f, ix->mu) && put_vec(f, ix->W) && put_vec(f, ix->lam) && put_vec(f, ix->Lam) &&
               put_vec(f, ix->rho) && put_vec(f, ix->assign) && put_vec(f, ix->lists) && put_vec(f, ix->kmeans_obj);
@@ -129,6 +130,7 @@ dade_status save_index(const dade_index *ix, const char *path) {
         DADE_TRY(put_dev(f, ix->lead_err, sizeof(float) * (size_t)s.slots * s.lead_nb));
         DADE_TRY(put_dev(f, ix->lead_scale, sizeof(float) * (size_t)s.nc * s.lead_nb));
     }
+    if (s.tail_nb0 > 0) DADE_TRY(put_dev(f, ix->tail, sizeof(float) * (size_t)s.slots * s.tail_w));
     if (fflush(f) != 0) {
         set_error("write failed");
         return DADE_EIO;
@@ -162,6 +164,9 @@ dade_status load_index(const char *path, dade_index *ix) {
                        ((s.lead_format == DADE_LEAD_BF16 || s.lead_format == DADE_LEAD_FP8) && s.lead_dims >= 16 &&
                         s.lead_dims % 16 == 0 && s.lead_dims <= s.dp && s.lead_nb == s.lead_dims / 16),
                    "index file lead description out of range");
+    DADE_CHECK_ARG((s.tail_nb0 == 0 && s.tail_w == 0) ||
+                       (s.tail_nb0 > 0 && s.tail_nb0 < s.nb && s.tail_w == s.dp - 16 * s.tail_nb0),
+                   "index file tail description out of range");
     const size_t d = s.d;
     DADE_TRY(get_vec(f, ix->mu, d, "mean"));
     DADE_TRY(get_vec(f, ix->W, d * d, "basis"));
@@ -226,6 +231,11 @@ dade_status load_index(const char *path, dade_index *ix) {
         DADE_TRY(get_dev(f, ix->lead, lead_code_bytes(s), "lead codes"));
         DADE_TRY(get_dev(f, ix->lead_err, sizeof(float) * (size_t)s.slots * s.lead_nb, "lead error norms"));
         DADE_TRY(get_dev(f, ix->lead_scale, sizeof(float) * (size_t)s.nc * s.lead_nb, "lead scales"));
+    }
+    if (s.tail_nb0 > 0) {
+        ix->tail_nb0 = s.tail_nb0;
+        ix->tail_w = s.tail_w;
+        DADE_TRY(get_dev(f, ix->tail, sizeof(float) * (size_t)s.slots * s.tail_w, "row-major tail"));
     }
     DADE_TRY(upload_basis(ix, 0));
     DADE_TRY(prepare_tensor_operands(ix, 0));

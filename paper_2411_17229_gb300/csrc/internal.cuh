@@ -96,6 +96,9 @@ struct dade_index {
     dade::DevBuf lead;      // codes; list c at slot_c * lead_nb * 16 * ES bytes, block b at + b * np * 16 * ES
     dade::DevBuf lead_scale;// float [nc][lead_nb] (FP8 only)
     dade::DevBuf lead_err;  // float [lead_nb][slots]: error norm over blocks 0..b (rounded up)
+    // row-major copy of dims [16 tail_nb0, dp) of every slot: tail[(slot) * tail_w + k - 16 tail_nb0]
+    int32_t tail_nb0 = 0, tail_w = 0;
+    dade::DevBuf tail;
     int64_t data_floats = 0, slots = 0;
     // workspace (grown on demand, reused across calls)
     mutable dade::DevBuf ws_dist, ws_probe, ws_qrot, ws_qin, ws_ids, ws_dists, ws_order, ws_ordcnt, ws_aimg, ws_anorm;
@@ -134,6 +137,7 @@ struct ScanParams {
     int32_t nprobe, k, tile, mode, delta_d, n_inc, spec, threads, schedule, generic, use_lead;
     int64_t *lead_stats;     // [nq] or null
     const int32_t *order;    // [nq] execution order of the queries, or null (identity)
+    int32_t use_tail;        // phase B reads the row-major tail copy
     float coef[DADE_MAX_DIM / DADE_BLOCK];   // per increment; prune iff P > coef[j] * r2
     int64_t *ids;            // [nq][k]
     float *dists;            // [nq][k]

@@ -411,6 +411,11 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     a.out_d = p.dists;
     a.stats = p.stats;
     a.order = p.order;
+    if (p.use_tail && ix->tail_nb0 > 0) {
+        a.tail = ix->tail.as<float>();
+        a.tail_nb0 = ix->tail_nb0;
+        a.tail_w = ix->tail_w;
+    }
     a.err = ix->errflag.as<int>();
     a.q_stride = p.q_stride;
     a.nprobe = p.nprobe;

@@ -45,6 +45,8 @@ struct ScanArgs {
     int64_t lead_slots;
     int lead_nb;
     const int32_t *order;        // CTA b runs query order[b] (null: query b)
+    const float *tail;           // row-major copy of blocks >= tail_nb0 (null: none)
+    int tail_nb0, tail_w;
 };
 
 // The query a CTA runs.

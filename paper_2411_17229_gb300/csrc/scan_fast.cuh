@@ -287,11 +287,17 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_dade_fast(const ScanArgs a) {
                 const bool act = sidx < nS;
                 const Surv sv = act ? l0[sidx] : Surv{0, 0.f};
                 const float *row = lbase + (int64_t)(cc.i0 + sv.idx) * 16 + lq * 4;
+                // blocks from tail_nb0 on: one contiguous row of the row-major copy
+                const float *trow = a.tail ? a.tail + ((int64_t)(unsigned)m.y + cc.i0 + sv.idx) * a.tail_w +
+                                                 lq * 4 - (int64_t)a.tail_nb0 * 16
+                                           : nullptr;
                 float4 o[NLOAD > 0 ? NLOAD : 1];
 #pragma unroll
-                for (int u = 0; u < NLOAD; ++u)
-                    o[u] = act ? __ldg(reinterpret_cast<const float4 *>(row + (int64_t)(B0 + u) * bstride))
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int u = 0; u < NLOAD; ++u) {
+                    const int b = B0 + u;
+                    const float *src = (trow && b >= a.tail_nb0) ? trow + b * 16 : row + (int64_t)b * bstride;
+                    o[u] = act ? __ldg(reinterpret_cast<const float4 *>(src)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 float p = LF ? 0.f : sv.p;
                 bool alive = act;
 #pragma unroll

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libdade.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EIO = range(7)
 MODE_DADE, MODE_FD = 0, 1
 SCHED_TILE, SCHED_PIPELINED = 0, 1
-FLAG_GENERIC_KERNEL, FLAG_LEAD, FLAG_QUERY_ORDER = 1, 2, 4
+FLAG_GENERIC_KERNEL, FLAG_LEAD, FLAG_QUERY_ORDER, FLAG_ROW_TAIL = 1, 2, 4, 8
 LEAD_NONE, LEAD_BF16, LEAD_FP8 = 0, 1, 2
 PIPE_MAX = 8
 (FIELD_MEAN, FIELD_BASIS, FIELD_EIGVAL, FIELD_CENTROIDS, FIELD_ASSIGN, FIELD_ROTATED, FIELD_RHO, FIELD_KMEANS_OBJ,
@@ -37,7 +37,7 @@ class BuildOpts(C.Structure):
     _fields_ = [("n_clusters", C.c_int32), ("kmeans_iters", C.c_int32), ("seed", C.c_uint64),
                 ("eps_pairs", C.c_int64), ("assign", C.c_void_p), ("kmeans_init", C.c_void_p),
                 ("pairs", C.c_void_p), ("lead_format", C.c_int32), ("lead_dims", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("tail_from", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class SearchOpts(C.Structure):
@@ -50,7 +50,7 @@ class Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("d_pad", C.c_int32), ("n_clusters", C.c_int32),
                 ("max_list", C.c_int32), ("eps_kept", C.c_int64), ("device_bytes", C.c_int64),
                 ("data_bytes", C.c_int64), ("kmeans_iters", C.c_int32), ("lead_format", C.c_int32),
-                ("lead_dims", C.c_int32), ("reserved", C.c_int32)]
+                ("lead_dims", C.c_int32), ("tail_from", C.c_int32)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/dade.h
@@ -124,12 +124,12 @@ class Index:
     """A libdade index resident in device memory."""
 
     def __init__(self, base, n_clusters: int, kmeans_iters: int = 10, seed: int = 0, eps_pairs: int = 100000,
-                 assign=None, kmeans_init=None, pairs=None, lead_format=LEAD_NONE, lead_dims=0, stream=None):
+                 assign=None, kmeans_init=None, pairs=None, lead_format=LEAD_NONE, lead_dims=0, tail_from=0, stream=None):
         L = lib()
         o = BuildOpts()
         L.dade_build_opts_default(C.byref(o))
         o.n_clusters, o.kmeans_iters, o.seed, o.eps_pairs = int(n_clusters), int(kmeans_iters), int(seed), int(eps_pairs)
-        o.lead_format, o.lead_dims = int(lead_format), int(lead_dims)
+        o.lead_format, o.lead_dims, o.tail_from = int(lead_format), int(lead_dims), int(tail_from)
         keep = []
         if assign is not None:
             a = np.ascontiguousarray(assign, np.int32)

@@ -137,7 +137,7 @@ def test_load_rejects_foreign_files_without_gpu(L, tmp_path):
     assert L.dade_load_index(str(junk).encode(), C.byref(h)) == dade.EINVAL
     assert b"not a libdade index file" in L.dade_last_error()
     hdr = tmp_path / "hdr.dade"    # right magic and version, impossible dimension
-    hdr.write_bytes(b"DADEIX01" + (1).to_bytes(4, "little") + (0x01020304).to_bytes(4, "little") + bytes(64))
+    hdr.write_bytes(b"DADEIX01" + (1).to_bytes(4, "little") + (0x01020304).to_bytes(4, "little") + bytes(72))
     assert L.dade_load_index(str(hdr).encode(), C.byref(h)) == dade.EINVAL
     assert b"header out of range" in L.dade_last_error()
     assert not h.value

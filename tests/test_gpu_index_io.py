@@ -23,7 +23,7 @@ def built():
     build.build()
     base, queries, _ = synth.make("c1_gauss_10k_d128", n=5000, nq=64)
     ix = dade.Index(torch.from_numpy(base).cuda(), 40, kmeans_iters=3, seed=7, eps_pairs=3000,
-                    lead_format=dade.LEAD_FP8, lead_dims=32)
+                    lead_format=dade.LEAD_FP8, lead_dims=32, tail_from=48)
     return ix, torch.from_numpy(queries).cuda()
 
 
@@ -41,12 +41,12 @@ def test_round_trip(built, tmp_path):
     ix.save(path)
     back = dade.Index.load(path)
     for f in ("n", "d", "d_pad", "n_clusters", "max_list", "eps_kept", "data_bytes", "kmeans_iters",
-              "lead_format", "lead_dims"):
+              "lead_format", "lead_dims", "tail_from"):
         assert getattr(back.info, f) == getattr(ix.info, f), f
     for field in range(11):
         a, b = ix.export(field), back.export(field)
         assert a.dtype == b.dtype and np.array_equal(a, b), field
-    for flags in (0, dade.FLAG_LEAD):
+    for flags in (0, dade.FLAG_LEAD, dade.FLAG_ROW_TAIL, dade.FLAG_LEAD | dade.FLAG_ROW_TAIL):
         i0, d0 = _search(ix, q, flags)
         i1, d1 = _search(back, q, flags)
         assert np.array_equal(i0, i1) and np.array_equal(d0.view(np.uint32), d1.view(np.uint32))
@@ -59,8 +59,8 @@ def test_damaged_files_refused(built, tmp_path):
     raw = bytearray(open(path, "rb").read())
     info = ix.info
     d, n, nc, nb = info.d, info.n, info.n_clusters, info.d_pad // 16
-    # header (80 B), then (u64 size, bytes) sections: mean, basis, eigenvalues, prefix sums, rho, assign, lists
-    off = 80
+    # header (88 B), then (u64 size, bytes) sections: mean, basis, eigenvalues, prefix sums, rho, assign, lists
+    off = 88
     for size in (8 * d, 8 * d * d, 8 * d, 8 * (d + 1), 8 * (nb - 1) * info.eps_kept, 4 * n):
         assert int.from_bytes(raw[off:off + 8], "little") == size
         off += 8 + size

@@ -274,3 +274,26 @@ def test_query_order_gives_same_results(c1, mode, delta_d, flags):
     b = c1.gpu_search(10, 8, 0.1, delta_d, mode=mode, stats=True, flags=flags | dade.FLAG_QUERY_ORDER)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
     assert np.array_equal(a[2], b[2])
+
+
+@pytest.mark.parametrize("tail_from,delta_d,flags", [(64, 64, 0), (32, 32, 0), (16, 16, 0), (32, 64, dade.FLAG_LEAD),
+                                                     (48, 32, dade.FLAG_GENERIC_KERNEL)])
+def test_row_tail_gives_same_results(tail_from, delta_d, flags):
+    """Survivors reading their later dims from the row-major tail copy get
+    the same bits as from the dimension-blocked slabs."""
+    base, queries, _ = synth.make("c1_gauss_10k_d128", n=6000, nq=80)
+    assign = synth.zipf_assign(6000, 30, s=0.7)
+    ix = dade.Index(torch.from_numpy(base).cuda(), 30, assign=assign, eps_pairs=3000, tail_from=tail_from,
+                    lead_format=dade.LEAD_BF16, lead_dims=64)
+    assert ix.info.tail_from == tail_from
+    q = torch.from_numpy(queries).cuda()
+    out = []
+    for extra in (0, dade.FLAG_ROW_TAIL):
+        ids = torch.empty(80, 20, dtype=torch.int64, device="cuda")
+        d = torch.empty(80, 20, dtype=torch.float32, device="cuda")
+        st = torch.zeros(80, 4, dtype=torch.int64, device="cuda")
+        ix.query(q, 20, 8, 0.1, delta_d, ids, d, stats=st, flags=flags | extra)
+        ix.sync()
+        out.append((ids.cpu().numpy(), d.cpu().numpy(), st.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
+    assert np.array_equal(out[0][2], out[1][2])
