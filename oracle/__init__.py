@@ -64,7 +64,7 @@ class Oracle:
             "or_eps_sample": (i64, [vp, i64, i32, vp, vp, i64, vp, i32, vp]),
             "or_eps_quantile": (f64, [vp, i64, f64]),
             "or_search": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, i64, i32, i32, i32, vp, i32, i32, i32,
-                                f64, vp, vp, vp, vp]),
+                                i32, f64, vp, vp, vp, vp]),
             "or_exact_knn": (None, [vp, i64, i32, vp, i64, i32, vp, vp]),
             "or_estimate_sq": (f64, [vp, vp, i32, i32, vp]),
             "or_dco": (i32, [vp, vp, i32, i32, f64, vp, vp, i32, f64, vp, vp, vp]),
@@ -171,8 +171,9 @@ class Oracle:
 
     # -- Algorithm 1 inside IVF -------------------------------------------
     def search(self, Xr, assign, cent, lam, Qr, K, nprobe, delta_d, eps, schedule=TILE, tile=128, lag=0,
-               tol=TIE_TOL):
-        """Returns ids [nq,K] int64, dists [nq,K] (squared), stats [nq,4], flags [nq]."""
+               tol=TIE_TOL, seed=0):
+        """Returns ids [nq,K] int64, dists [nq,K] (squared), stats [nq,4], flags [nq].
+        seed > 0: the seeded schedule (threshold frozen after the first `seed` lists)."""
         Xr, cent, Qr = _f64(Xr), _f64(cent), _f64(Qr)
         n, D = Xr.shape
         nq = Qr.shape[0]
@@ -181,7 +182,7 @@ class Oracle:
         stats, flags = np.empty((nq, 4), np.int64), np.empty(nq, np.int32)
         e = None if eps is None else _f64(eps)
         rc = self.lib.or_search(_p(Xr), n, D, _p(assign), cent.shape[0], _p(cent), _p(_f64(lam)),
-                                _p(Qr), nq, K, nprobe, delta_d, _p(e), schedule, tile, lag, tol,
+                                _p(Qr), nq, K, nprobe, delta_d, _p(e), schedule, tile, lag, seed, tol,
                                 _p(ids), _p(dists), _p(stats), _p(flags))
         if rc != 0:
             raise ValueError("or_search rejected its arguments")
@@ -260,8 +261,8 @@ class Index:
     def rotate(self, Q):
         return self.o.rotate(Q, self.mu, self.W)
 
-    def search(self, Q, K, nprobe, delta_d, alpha, schedule=TILE, tile=128, prune=True, lag=0):
+    def search(self, Q, K, nprobe, delta_d, alpha, schedule=TILE, tile=128, prune=True, lag=0, seed=0):
         Qr = self.rotate(Q)
         eps = self.eps(alpha, delta_d) if prune else None
         return self.o.search(self.Xr, self.assign, self.cent, self.lam, Qr, K, nprobe, delta_d, eps,
-                             schedule, tile, lag)
+                             schedule, tile, lag, seed=seed)

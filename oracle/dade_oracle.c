@@ -504,6 +504,11 @@ OR_API int or_dco(const double *q, const double *o, int D, int delta_d, double r
  * whole scan) is tested against r taken after tiles 0..t-1-L only: the
  * threshold of a pipeline that keeps L later tiles in flight.  L = 0 is the
  * plain tile schedule.
+ * With seed S > 0 (seeded schedule), the first S probed lists run as above
+ * and every candidate of the later lists is tested against r frozen at its
+ * value after those S lists (a stale r that is the same for all of them);
+ * accepted candidates still enter the K nearest.  S >= nprobe is the plain
+ * schedule.
  * Results are ordered by (squared distance, id); missing slots are (-1, +inf).
  * eps == NULL runs FDScanning.  eps is indexed by d (eps[d], d < D).
  * stats (nq x 4, may be NULL): candidates, sum of dims used, accepted, pruned.
@@ -516,9 +521,10 @@ OR_API int or_dco(const double *q, const double *o, int D, int delta_d, double r
 OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, int nc,
                      const double *cent, const double *lam, const double *Qr, int64_t nq,
                      int K, int nprobe, int delta_d, const double *eps, int schedule, int tile, int lag,
-                     double tol, int64_t *ids, double *dists, int64_t *stats, int32_t *flags)
+                     int seed, double tol, int64_t *ids, double *dists, int64_t *stats, int32_t *flags)
 {
-    if (K < 1 || nprobe < 1 || nprobe > nc || delta_d < 1 || (schedule == 1 && tile < 1) || lag < 0) return -1;
+    if (K < 1 || nprobe < 1 || nprobe > nc || delta_d < 1 || (schedule == 1 && tile < 1) || lag < 0 || seed < 0)
+        return -1;
     /* inverted lists, members in ascending id */
     int64_t *start = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
     int64_t *members = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -546,13 +552,16 @@ OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, 
             int64_t epoch = 0;
             double dropped = INFINITY;   /* best squared distance accepted but not kept */
             int64_t st[4] = {0, 0, 0, 0};
+            double r2_seed = INFINITY;
             for (int j = 0; j < nprobe; ++j) {
                 int c = probe[qi * nprobe + j];
+                if (seed > 0 && j == seed) r2_seed = ntop == K ? buf[K - 1].key : INFINITY;
                 int64_t len = start[c + 1] - start[c];
                 int64_t elen = schedule == 0 ? 1 : schedule == 1 ? tile : (len > 0 ? len : 1);
                 for (int64_t e0 = 0; e0 < len; e0 += elen) {
                     double r2 = ntop == K ? buf[K - 1].key : INFINITY;
                     if (lag > 0) r2 = epoch - 1 - lag >= 0 ? hist[(epoch - 1 - lag) % (lag + 1)] : INFINITY;
+                    if (seed > 0 && j >= seed) r2 = r2_seed;
                     double r = sqrt(r2);
                     int npend = 0;
                     int64_t e1 = e0 + elen < len ? e0 + elen : len;

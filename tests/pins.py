@@ -364,6 +364,60 @@ def pin_search_lagged_tiles(o):
     assert lagged[2][:, 3].sum() <= a[2][:, 3].sum()
 
 
+def pin_search_seeded_trace(o):
+    """Seeded schedule, worked by hand (Section 3.3 test with eps_d = 0 and
+    equal eigenvalues, so Lambda_32 / Lambda_16 = 2).  Query at the origin,
+    K = 1, two lists probed in order A, B, delta_d = 16, D = 32.
+    A = {a: |a| = 10}; B = {p1 (id 1): 5 in dim 16, p2 (id 2): 4 in dim 0,
+    p3 (id 3): 20 in dim 0}.
+    Running threshold (TILE(1)): r = 10 after A; p1 is not pruned
+    (P_16 = 0) and is accepted, r = 5; p2 has dis'_16 = sqrt(2) 4 = 5.66 > 5
+    and is pruned, as is p3 (28.3 > 5): the result is p1 at 25.  Frozen
+    threshold after A (seed 1): p2 is tested against r = 10, survives, and
+    is accepted at its exact 16; p3 (28.3 > 10) is pruned: the result is p2."""
+    D = 32
+    Xr = np.zeros((4, D))
+    Xr[0, 0] = 10.0
+    Xr[1, 16] = 5.0
+    Xr[2, 0] = 4.0
+    Xr[3, 0] = 20.0
+    assign = np.array([0, 1, 1, 1], np.int32)
+    cent = np.zeros((2, D))
+    cent[1, 0] = 100.0                     # list A (0) is probed first
+    lam = np.ones(D)
+    eps = np.zeros(D + 1)
+    Qr = np.zeros((1, D))
+    tile = o.search(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=1, tile=1)
+    assert tile[0][0, 0] == 1 and tile[1][0, 0] == 25.0
+    assert tile[2][0].tolist() == [4, 32 + 32 + 16 + 16, 2, 2]      # p2, p3 pruned at d = 16
+    seeded = o.search(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=1, tile=1, seed=1)
+    assert seeded[0][0, 0] == 2 and seeded[1][0, 0] == 16.0
+    assert seeded[2][0].tolist() == [4, 32 * 3 + 16, 3, 1]
+
+
+def pin_search_seeded_limits(o):
+    """Seeded schedule limits: seed >= nprobe is the plain tile schedule;
+    FDScanning does not depend on the schedule; freezing r after the seed
+    lists can only prune less than the running threshold."""
+    X, Xr, lam, cent, assign, Q, Qr = _tiny_index(o)
+    eps = _eps_for(o, Xr, lam, 8, 0.2)
+    a = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, eps, schedule=1, tile=16)
+    b = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, eps, schedule=1, tile=16, seed=4)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    fd = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, None, schedule=1, tile=16)
+    fds = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, None, schedule=1, tile=16, seed=1)
+    assert np.array_equal(fd[0], fds[0]) and np.array_equal(fd[1], fds[1])
+    for seed in (1, 2, 3):
+        s = o.search(Xr, assign, cent, lam, Qr, 8, 4, 8, eps, schedule=1, tile=16, seed=seed)
+        assert np.array_equal(s[2][:, 0], a[2][:, 0])
+        assert np.all(s[2][:, 3] <= a[2][:, 3])
+        for i in range(Qr.shape[0]):   # results: exact distances of distinct ids, ascending
+            ok = s[0][i] >= 0
+            ex = ((Xr[s[0][i][ok]] - Qr[i]) ** 2).sum(1)
+            assert np.allclose(s[1][i][ok], ex, rtol=1e-12) and np.all(np.diff(s[1][i][ok]) >= 0)
+            assert len(set(s[0][i][ok].tolist())) == int(ok.sum())
+
+
 def pin_search_short_lists(o):
     """Fewer candidates than K: the missing slots are (-1, +inf)."""
     X, Xr, lam, cent, assign, Q, Qr = _tiny_index(o, n=40, nc=7, dup=False)

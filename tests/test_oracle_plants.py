@@ -43,6 +43,8 @@ PLANTS = [
     ("threshold_not_refreshed", "double r2 = ntop == K ? buf[K - 1].key : INFINITY;", "double r2 = INFINITY;"),
     ("threshold_is_first_not_kth", "double r2 = ntop == K ? buf[K - 1].key : INFINITY;",
      "double r2 = ntop == K ? buf[0].key : INFINITY;"),
+    ("seed_threshold_one_list_late", "if (seed > 0 && j == seed) r2_seed", "if (seed > 0 && j == seed + 1) r2_seed"),
+    ("seed_threshold_not_frozen", "if (seed > 0 && j >= seed) r2 = r2_seed;", "if (seed > 0 && j > seed) r2 = r2_seed;"),
     ("probe_descending", "for (int j = 0; j < nprobe; ++j) {\n                probe[q * nprobe + j] = (int32_t)buf[j].id;",
      "for (int j = 0; j < nprobe; ++j) {\n                probe[q * nprobe + j] = (int32_t)buf[nc - 1 - j].id;"),
 ]
