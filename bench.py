@@ -211,6 +211,10 @@ def scan_kernel_name(point, d):
     if point["mode"] == 1:
         return f"k_fd_fast<{point['threads']}, 8>" if nb == 8 else "k_scan<FD>"
     lead = point.get("flags", 0) & 2
+    if point.get("schedule", 0) == 2 and nb == 8:
+        gb = min(point["delta_d"] // 16, 8)
+        return (f"k_dade_fast<{point['threads']}, 8, {gb}> (first {point.get('seed_lists')} lists) + "
+                f"k_lm<{gb}> (list-major) + k_lm_merge")
     if point.get("schedule", 0) == 0 and nb == 8 and point["delta_d"] // 16 in (1, 2, 4, 8):
         return f"k_dade_fast<{point['threads']}, 8, {min(point['delta_d'] // 16, 8)}{', lead' if lead else ''}>"
     if point.get("schedule", 0) == 1:
@@ -335,7 +339,8 @@ def run_ours(args):
     def scan(pt, st=None, lead_st=None):
         ix.scan(qr, probe_for(pt["nprobe"]), K, pt.get("alpha", 0.1), pt.get("delta_d", 32), ids, dists,
                 mode=pt["mode"], tile=pt["tile"], stats=st, spec=pt.get("spec", 8), threads=pt["threads"],
-                schedule=pt.get("schedule", 0), flags=pt.get("flags", 0), lead_stats=lead_st, stream=sh)
+                schedule=pt.get("schedule", 0), flags=pt.get("flags", 0), lead_stats=lead_st,
+                seed_lists=pt.get("seed_lists", 0), stream=sh)
 
     def measure(pt, reps=4):
         scan(pt)
@@ -354,9 +359,11 @@ def run_ours(args):
     grid = [8, 12, 16, 20, 24, 28, 32, 40, 48, 64, 96, 128]
     fd_best, fd_rec = None, {}
     for nprobe in grid:              # FD time grows with nprobe: the first point reaching the target wins
-        for threads, tile in ((128, 64), (128, 128), (256, 128)):
+        for threads, tile, sched, seed in ((128, 64, 0, 0), (128, 128, 0, 0), (256, 128, 0, 0),
+                                           (256, 128, dade.SCHED_SEEDED, 1), (256, 128, dade.SCHED_SEEDED, 2),
+                                           (256, 128, dade.SCHED_SEEDED, 3)):
             pt = {"mode": dade.MODE_FD, "nprobe": nprobe, "tile": tile, "threads": threads,
-                  "flags": dade.FLAG_QUERY_ORDER}
+                  "flags": dade.FLAG_QUERY_ORDER, "schedule": sched, "seed_lists": seed}
             ms, rc = measure(pt)
             fd_rec[nprobe] = rc
             if rc >= RECALL_TARGET and (fd_best is None or ms < fd_best[0]):
@@ -367,14 +374,15 @@ def run_ours(args):
     dade_best = None
     tried = []
     lead_flags = (0, dade.FLAG_LEAD) if lf else (0,)
-    variants = [(dade.SCHED_TILE, 8, tile, 128, fl) for tile in (128, 192, 256) for fl in lead_flags]
+    variants = [(dade.SCHED_TILE, 8, tile, 128, fl, 0) for tile in (128, 192, 256) for fl in lead_flags]
+    variants += [(dade.SCHED_SEEDED, 8, 256, 128, 0, seed) for seed in (2, 3, 4)]
     for dd in (16, 32, 64):
         for alpha in (0.05, 0.1, 0.2, 0.3):
-            for schedule, spec, tile, threads, fl in variants:
+            for schedule, spec, tile, threads, fl, seed in variants:
                     for nprobe in [p for p in grid if p >= n0][:3]:
                         pt = {"mode": dade.MODE_DADE, "nprobe": nprobe, "alpha": alpha, "delta_d": dd,
                               "spec": spec, "tile": tile, "threads": threads, "schedule": schedule,
-                              "flags": fl | fixed}
+                              "flags": fl | fixed, "seed_lists": seed}
                         ms, rc = measure(pt)
                         tried.append((ms, rc, pt))
                         if rc >= RECALL_TARGET:
@@ -420,7 +428,7 @@ def run_ours(args):
         ev[1].record(stream)
         ix.scan(qr, pr_step, K, point["alpha"], point["delta_d"], ids, dists, mode=point["mode"],
                 tile=point["tile"], spec=point["spec"], threads=point["threads"], schedule=point["schedule"],
-                flags=point["flags"], stream=sh)
+                flags=point["flags"], seed_lists=point.get("seed_lists", 0), stream=sh)
 
     for _ in range(args.warmup):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -473,7 +481,8 @@ def run_ours(args):
         ix.rotate(q, qr, stream=sh)
         ix.probe(qr, fd_pt["nprobe"], pr_fd, stream=sh)
         ix.scan(qr, pr_fd, K, 0.1, 32, ids, dists, mode=dade.MODE_FD, tile=fd_pt["tile"],
-                threads=fd_pt["threads"], flags=fd_pt["flags"], stream=sh)
+                threads=fd_pt["threads"], flags=fd_pt["flags"], schedule=fd_pt.get("schedule", 0),
+                seed_lists=fd_pt.get("seed_lists", 0), stream=sh)
         e1.record(stream)
         torch.cuda.synchronize()
         if i >= args.warmup:
@@ -490,7 +499,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         ix.query(q_host, K, point["nprobe"], point["alpha"], point["delta_d"], ids_host, d_host, mode=point["mode"],
                  tile=point["tile"], spec=point["spec"], threads=point["threads"], schedule=point["schedule"],
-                 flags=point["flags"], stream=sh)
+                 flags=point["flags"], seed_lists=point.get("seed_lists", 0), stream=sh)
         if i >= args.warmup:
             e2e_s.append(time.perf_counter() - t1)
     e2e_qps = world * nq / statistics.mean(e2e_s)
@@ -519,7 +528,8 @@ def run_ours(args):
             "config": {"workload": args.workload, "n": n, "d": w.d, "nq": nq, "n_clusters": nc, "k": K,
                        "nprobe": point["nprobe"], "alpha": point.get("alpha"), "delta_d": point.get("delta_d"),
                        "spec": point.get("spec"), "tile": point["tile"], "threads": point["threads"],
-                       "schedule": "tile" if point.get("schedule", 0) == 0 else "pipelined",
+                       "schedule": {0: "tile", 1: "pipelined", 2: "seeded"}[point.get("schedule", 0)],
+                       "seed_lists": point.get("seed_lists") if point.get("schedule", 0) == 2 else None,
                        "lead_prefilter": ({"format": args.lead, "dims": ld} if use_lead else None),
                        "flags": {"query_order": bool(point["flags"] & dade.FLAG_QUERY_ORDER),
                                  "row_tail_from": tf if point["flags"] & dade.FLAG_ROW_TAIL else None},
@@ -532,6 +542,8 @@ def run_ours(args):
                            "p99": round(float(np.percentile(step_ms, 99)), 4), "per": "batch step"},
             "fd_baseline": {"value": round(fd_qps, 1), "unit": UNIT, "recall": round(fd_recall, 5),
                             "nprobe": fd_pt["nprobe"], "threads": fd_pt["threads"],
+                            "schedule": {0: "tile", 2: "seeded"}[fd_pt.get("schedule", 0)],
+                            "seed_lists": fd_pt.get("seed_lists") or None,
                             "ms_per_step": round(statistics.mean(fd_ms), 4)},
             "dade_vs_fd": round(value / world / fd_qps, 3),
             "work": {"candidates": cand, "dims_per_candidate": round(dims_sum / max(1, cand), 2),
@@ -567,13 +579,14 @@ def oracle_index(base, w, nc, kmeans_iters=1):
 def oracle_qps(idx, queries, point, K, cpu_seconds, steps=1):
     """Time the oracle's search (probe + DCO scan) on a bounded query sample."""
     t0 = time.time()
-    idx.search(queries[:64], K, point["nprobe"], point["delta_d"], np.float32(point["alpha"]))
+    seed = point.get("seed_lists", 0) if point.get("schedule", 0) == 2 else 0
+    idx.search(queries[:64], K, point["nprobe"], point["delta_d"], np.float32(point["alpha"]), seed=seed)
     per_q = max(1e-6, (time.time() - t0) / 64)
     m = int(min(queries.shape[0], max(64, cpu_seconds / per_q / max(1, steps))))
     times = []
     for _ in range(steps):
         t0 = time.time()
-        idx.search(queries[:m], K, point["nprobe"], point["delta_d"], np.float32(point["alpha"]))
+        idx.search(queries[:m], K, point["nprobe"], point["delta_d"], np.float32(point["alpha"]), seed=seed)
         times.append(time.time() - t0)
     return m, times
 
@@ -581,11 +594,13 @@ def oracle_qps(idx, queries, point, K, cpu_seconds, steps=1):
 def cpu_baseline(base, queries, w, nc, point, K, cpu_seconds):
     try:
         idx = oracle_index(base, w, nc)
-        pt = {"nprobe": point["nprobe"], "alpha": point.get("alpha", 0.1), "delta_d": point.get("delta_d", 32)}
+        pt = {"nprobe": point["nprobe"], "alpha": point.get("alpha", 0.1), "delta_d": point.get("delta_d", 32),
+              "schedule": point.get("schedule", 0), "seed_lists": point.get("seed_lists", 0)}
         m, times = oracle_qps(idx, queries, pt, K, cpu_seconds)
+        sched = f"seeded, first {pt['seed_lists']} lists in TILE(128)" if pt["schedule"] == 2 else "TILE(128)"
         return {"value": round(m / times[0], 1), "unit": UNIT, "cores": idx.o.threads(), "kind": "oracle",
                 "sample": f"first {m} of {queries.shape[0]} queries, oracle FP64 DADE-IVF search (probe + DCO scan, "
-                          f"TILE(128) schedule) at nprobe={pt['nprobe']} alpha={pt['alpha']} delta_d={pt['delta_d']}; "
+                          f"{sched} schedule) at nprobe={pt['nprobe']} alpha={pt['alpha']} delta_d={pt['delta_d']}; "
                           f"oracle lists from 1 Lloyd iteration"}
     except Exception as e:  # noqa: BLE001 - the baseline must not sink the GPU line
         return {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}

@@ -81,11 +81,22 @@ typedef enum {
  *                         number of increments: up to n_inc tiles are in flight
  *                         at once, one per increment.  Used when n_inc <= 8,
  *                         otherwise the tile schedule runs.
- * A staler threshold can only prune less.  FDScanning ignores the schedule.
+ *   DADE_SCHED_SEEDED     the first opts->seed_lists probed lists as in
+ *                         DADE_SCHED_TILE; every candidate of the later lists
+ *                         is tested against r frozen after those lists.  The
+ *                         later lists are then scanned list-major: each list's
+ *                         rows are staged once for all the queries probing it
+ *                         (one persistent launch over (list, query group)
+ *                         items), and the K nearest are merged at the end.
+ *                         D <= 128 (16-dim blocks: 8); other shapes return
+ *                         DADE_EUNSUPPORTED.
+ * A staler threshold can only prune less.  FDScanning results do not depend
+ * on the schedule.
  */
 typedef enum {
     DADE_SCHED_TILE = 0,
-    DADE_SCHED_PIPELINED = 1
+    DADE_SCHED_PIPELINED = 1,
+    DADE_SCHED_SEEDED = 2
 } dade_schedule;
 
 /* dade_search_opts.flags */
@@ -155,7 +166,9 @@ typedef struct {
     int32_t flags;             /* DADE_FLAG_* bits */
     int64_t *lead_stats;       /* device, optional [nq]: candidates dropped by the low-precision prefilter
                                   (needs DADE_FLAG_LEAD) */
-    int32_t reserved[2];
+    int32_t seed_lists;        /* DADE_SCHED_SEEDED: lists scanned before r is frozen (0: 2; >= nprobe:
+                                  the tile schedule) */
+    int32_t reserved[1];
 } dade_search_opts;
 
 /* Description of a built index. */

@@ -117,8 +117,10 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
     DADE_CHECK_ARG(!opts || (opts->spec >= 0 && opts->spec <= 8), "spec outside 0..8");
     DADE_CHECK_ARG(!opts || opts->threads == 0 || opts->threads == 128 || opts->threads == 256,
                    "threads must be 0 (default), 128 or 256");
-    DADE_CHECK_ARG(!opts || opts->schedule == DADE_SCHED_PIPELINED || opts->schedule == DADE_SCHED_TILE,
+    DADE_CHECK_ARG(!opts || opts->schedule == DADE_SCHED_PIPELINED || opts->schedule == DADE_SCHED_TILE ||
+                       opts->schedule == DADE_SCHED_SEEDED,
                    "unknown schedule");
+    DADE_CHECK_ARG(!opts || opts->seed_lists >= 0, "seed_lists < 0");
     DADE_CHECK_ARG(!opts || (opts->flags & ~(DADE_FLAG_GENERIC_KERNEL | DADE_FLAG_LEAD | DADE_FLAG_QUERY_ORDER |
                                              DADE_FLAG_ROW_TAIL)) == 0,
                    "unknown flag bits");
@@ -127,7 +129,7 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
     if (opts && (opts->flags & DADE_FLAG_LEAD)) {
         DADE_CHECK_ARG(mode == DADE_MODE_DADE, "DADE_FLAG_LEAD needs mode DADE_MODE_DADE");
         DADE_CHECK_ARG(ix->lead_format != DADE_LEAD_NONE, "DADE_FLAG_LEAD on an index built without a lead copy");
-        DADE_CHECK_ARG(opts->schedule == DADE_SCHED_TILE, "DADE_FLAG_LEAD needs the tile schedule");
+        DADE_CHECK_ARG(opts->schedule != DADE_SCHED_PIPELINED, "DADE_FLAG_LEAD needs the tile or seeded schedule");
         DADE_CHECK_ARG(std::min(delta_d, ix->dp) <= ix->lead_dims,
                        "DADE_FLAG_LEAD needs min(delta_d, D rounded up to 16) <= the index's lead_dims");
     }
@@ -179,6 +181,7 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.spec = opts && opts->spec > 0 ? opts->spec : 8;
     p.threads = opts && opts->threads ? opts->threads : 128;
     p.schedule = opts ? opts->schedule : DADE_SCHED_TILE;
+    p.seed_lists = opts && opts->seed_lists > 0 ? opts->seed_lists : 2;
     p.generic = opts ? (opts->flags & DADE_FLAG_GENERIC_KERNEL) != 0 : 0;
     p.use_lead = opts ? (opts->flags & DADE_FLAG_LEAD) != 0 : 0;
     p.use_tail = opts ? (opts->flags & DADE_FLAG_ROW_TAIL) != 0 : 0;

@@ -102,6 +102,7 @@ struct dade_index {
     int64_t data_floats = 0, slots = 0;
     // workspace (grown on demand, reused across calls)
     mutable dade::DevBuf ws_dist, ws_probe, ws_qrot, ws_qin, ws_ids, ws_dists, ws_order, ws_ordcnt, ws_aimg, ws_anorm;
+    mutable dade::DevBuf ws_lm_cnt, ws_lm_items, ws_lm_acc, ws_lm_acnt;   // seeded schedule (lm.cu)
 };
 
 namespace dade {
@@ -138,12 +139,16 @@ struct ScanParams {
     int64_t *lead_stats;     // [nq] or null
     const int32_t *order;    // [nq] execution order of the queries, or null (identity)
     int32_t use_tail;        // phase B reads the row-major tail copy
+    int32_t pstride;         // row stride of probe (0: nprobe)
+    int32_t seed_lists;      // DADE_SCHED_SEEDED
     float coef[DADE_MAX_DIM / DADE_BLOCK];   // per increment; prune iff P > coef[j] * r2
     int64_t *ids;            // [nq][k]
     float *dists;            // [nq][k]
     int64_t *stats;          // [nq][4] or null
 };
 dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s);
+// DADE_SCHED_SEEDED with 0 < p.seed_lists < p.nprobe (lm.cu).
+dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s);
 
 // FP32 basis W^T and mean on the device, from the host FP64 copies (build.cu).
 dade_status upload_basis(dade_index *ix, cudaStream_t s);

@@ -1,0 +1,485 @@
+// lm.cu -- the seeded schedule (DADE_SCHED_SEEDED): the first S probed lists
+// of every query run in the tile schedule (scan.cu); r is then frozen at the
+// K-th distance found, and the later lists are scanned list-major.
+//
+// List-major: the (query, list) pairs of probe positions >= S are grouped by
+// list (counting sort), and the groups split into work items of at most 32
+// queries.  One persistent launch pops items from a counter.  For an item the
+// CTA stages the list's first increment tile by tile (cp.async.bulk, two
+// tiles in flight) once, and each warp runs Algorithm 1 for its queries of
+// the item against the staged rows: first increment from shared memory, the
+// survivors' later blocks gathered from global memory (the list is hot in L2
+// while the item runs), the Section 3.3 test against the query's frozen r,
+// the exact compare at d = D.  Accepted candidates are appended, as 64-bit
+// (distance bits, id) keys, to the query's own region of an accept buffer.
+// A candidate's outcome depends only on its query's frozen r, so the order in
+// which items and warps run does not change the result.  A final merge per
+// query takes the K smallest keys of the first-S-lists result and of its
+// accepted candidates (radix select, then rank sort).
+#include <algorithm>
+
+#include "internal.cuh"
+#include "scan_common.cuh"
+
+namespace dade {
+
+dade_status exclusive_scan_int(int *a, int n, cudaStream_t s);
+
+namespace {
+using namespace scanning;
+
+constexpr int LT = 64;          // candidates per staged tile
+constexpr int LG = 32;           // queries per work item
+constexpr int LNT = 256;         // threads per CTA
+constexpr int LNW = LNT / 32;    // warps
+constexpr int LNB = 8;           // 16-dim blocks (D in 113..128)
+
+struct LmArgs {
+    const float *data;
+    const int32_t *ids;
+    const ListMeta *meta;
+    const float *q_rot;
+    const int32_t *lq_items;     // queries grouped by list
+    const int *lq_off;           // [nc + 1] first entry of list c in lq_items
+    const int *item_off;         // [nc + 1] first work item of list c
+    unsigned *ctr;               // work counter
+    const float *r2src;          // first-phase squared distances [nq][k]; r^2 = entry k - 1
+    unsigned long long *acc;     // [nq][cap] accepted keys
+    int *acnt;                   // [nq]
+    int64_t *stats;              // [nq][4], added to; or null
+    int *err;
+    const float *tail;           // row-major tail copy or null
+    int64_t cap;
+    int q_stride, nc, k, d, tail_nb0, tail_w;
+    float coef[LNB];             // prune iff P > coef[j] r^2 after increment j
+};
+
+struct LmSmem {
+    static constexpr size_t stage(int gb) { return sizeof(float) * (size_t)gb * LT * 16; }
+    static size_t total(int gb) {
+        return 2 * stage(gb) + sizeof(float) * LG * 16 * LNB + sizeof(Surv) * LNW * LT;
+    }
+};
+
+__device__ __forceinline__ float quad_sum4(float p) {
+    p += __shfl_xor_sync(0xffffffffu, p, 1);
+    p += __shfl_xor_sync(0xffffffffu, p, 2);
+    return p;
+}
+
+// Warp-aggregated append of the lanes with `take` to query q's accept region.
+__device__ __forceinline__ void lm_append(const LmArgs &a, bool take, int q, unsigned long long key) {
+    const int lane = threadIdx.x & 31;
+    const unsigned mk = __ballot_sync(0xffffffffu, take);
+    if (mk == 0) return;
+    const int leader = __ffs(mk) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&a.acnt[q], __popc(mk));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (take) a.acc[(int64_t)q * a.cap + base + __popc(mk & ((1u << lane) - 1u))] = key;
+}
+
+template <int GB, bool STATS>
+__global__ void __launch_bounds__(LNT, 1) k_lm(const LmArgs a) {
+    constexpr int NINC = (LNB + GB - 1) / GB;
+    constexpr int NREST = LNB - GB;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_item, s_q[LG];
+    __shared__ float s_r2[LG];
+    float *stage = reinterpret_cast<float *>(smem);
+    float *qs = reinterpret_cast<float *>(smem + 2 * LmSmem::stage(GB));
+    Surv *survs = reinterpret_cast<Surv *>(smem + 2 * LmSmem::stage(GB) + sizeof(float) * LG * 16 * LNB);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, quad = lane >> 2, lq = lane & 3;
+
+    if (tid == 0) {
+        mbar_init(su32(&bars[0]), 1);
+        mbar_init(su32(&bars[1]), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t used[2] = {0u, 0u};   // completed waits per buffer (the same on every thread)
+    const int total = a.item_off[a.nc];
+
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(a.ctr, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = a.nc;   // the list c with item_off[c] <= item < item_off[c + 1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.item_off[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int c = lo;
+        const int qb = a.lq_off[c] + (item - a.item_off[c]) * LG;
+        const int ng = min(LG, a.lq_off[c + 1] - qb);
+        const ListMeta m = a.meta[c];
+        const int ntile = (m.len + LT - 1) / LT;
+        auto issue = [&](int t) {   // thread 0: first-increment slabs of tile t
+            const int buf = t & 1, i0 = t * LT, tn = min(LT, m.len - i0);
+            const uint32_t bar = su32(&bars[buf]);
+            mbar_expect_tx(bar, (uint32_t)(GB * tn * 64));
+            for (int b = 0; b < GB; ++b)
+                bulk_g2s(su32(stage + (size_t)buf * GB * LT * 16 + (size_t)b * LT * 16),
+                         a.data + m.base + (int64_t)b * m.np * 16 + (int64_t)i0 * 16, (uint32_t)(tn * 64), bar);
+        };
+        if (tid == 0)
+            for (int t = 0; t < 2 && t < ntile; ++t) issue(t);
+        for (int g = tid; g < ng; g += LNT) {
+            const int q = a.lq_items[qb + g];
+            s_q[g] = q;
+            s_r2[g] = a.r2src[(int64_t)q * a.k + a.k - 1];
+        }
+        for (int e = tid; e < ng * 16 * LNB; e += LNT) {
+            const int g = e / (16 * LNB), kk = e % (16 * LNB);
+            qs[e] = kk < a.d ? a.q_rot[(int64_t)a.lq_items[qb + g] * a.q_stride + kk] : 0.f;
+        }
+        __syncthreads();
+
+        for (int t = 0; t < ntile; ++t) {
+            const int buf = t & 1;
+            if (!wait_block(su32(&bars[buf]), used[buf] & 1u)) {
+                if (tid == 0) {
+                    atomicExch(a.err, (int)DADE_ETIMEOUT);
+                    if (t + 1 < ntile)   // the other buffer's copy may still be in flight
+                        wait_bounded(su32(&bars[buf ^ 1]), used[buf ^ 1] & 1u, 10000000ull);
+                }
+                return;
+            }
+            ++used[buf];
+            const int i0 = t * LT, tn = min(LT, m.len - i0);
+            const float *st = stage + (size_t)buf * GB * LT * 16;
+            for (int g = warp; g < ng; g += LNW) {
+                const int q = s_q[g];
+                const float r2 = s_r2[g];
+                const float *qv = qs + g * 16 * LNB;
+                float4 qa[GB];
+#pragma unroll
+                for (int b = 0; b < GB; ++b) qa[b] = *reinterpret_cast<const float4 *>(qv + b * 16 + lq * 4);
+                Surv *sv = survs + warp * LT;
+                int nsv = 0;
+                unsigned long long st_c = 0, st_d = 0, st_a = 0, st_p = 0;
+                const float c0 = a.coef[0] * r2;
+                for (int k0 = 0; k0 < tn; k0 += 8) {
+                    const int cand = k0 + quad;
+                    const bool act = cand < tn;
+                    float p = 0.f;
+                    if (act) {
+#pragma unroll
+                        for (int b = 0; b < GB; ++b)
+                            p += sqd4(qa[b], *reinterpret_cast<const float4 *>(st + ((size_t)b * LT + cand) * 16 + lq * 4));
+                    }
+                    p = quad_sum4(p);
+                    const bool lead = act && lq == 0;
+                    if (NINC == 1) {
+                        const bool take = lead && p <= r2;
+                        const int id = take ? a.ids[m.slot + i0 + cand] : 0;
+                        lm_append(a, take, q, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned)id);
+                        if (STATS && lead) { ++st_c; st_d += a.d; st_a += take; }
+                    } else {
+                        const bool keep = lead && !(p > c0);
+                        const unsigned mk = __ballot_sync(0xffffffffu, keep);
+                        if (keep) sv[nsv + __popc(mk & ((1u << lane) - 1u))] = Surv{cand, p};
+                        nsv += __popc(mk);
+                        if (STATS && lead) {
+                            ++st_c;
+                            if (!keep) { st_d += min(GB * 16, a.d); ++st_p; }
+                        }
+                    }
+                }
+                __syncwarp();
+                if (NINC > 1) {
+                    for (int r0 = 0; r0 < nsv; r0 += 8) {
+                        const int sidx = r0 + quad;
+                        const bool act = sidx < nsv;
+                        const Surv v = act ? sv[sidx] : Surv{0, 0.f};
+                        const int64_t i = i0 + v.idx;
+                        const float *row = a.data + m.base + i * 16 + lq * 4;
+                        const float *trow =
+                            a.tail ? a.tail + (m.slot + i) * a.tail_w + lq * 4 - (int64_t)a.tail_nb0 * 16 : nullptr;
+                        float4 o[NREST > 0 ? NREST : 1];
+#pragma unroll
+                        for (int u = 0; u < NREST; ++u) {
+                            const int b = GB + u;
+                            const float *src = (trow && b >= a.tail_nb0) ? trow + b * 16 : row + (int64_t)b * m.np * 16;
+                            o[u] = act ? __ldg(reinterpret_cast<const float4 *>(src)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                        float p = v.p;
+                        bool alive = act;
+#pragma unroll
+                        for (int j = 1; j < NINC; ++j) {
+                            float part = 0.f;
+#pragma unroll
+                            for (int b = j * GB; b < (j + 1) * GB && b < LNB; ++b)
+                                part += sqd4(*reinterpret_cast<const float4 *>(qv + b * 16 + lq * 4), o[b - GB]);
+                            part = quad_sum4(part);
+                            p += part;
+                            if (j < NINC - 1 && alive && p > a.coef[j] * r2) {
+                                alive = false;
+                                if (STATS && lq == 0) { st_d += min((j + 1) * GB * 16, a.d); ++st_p; }
+                            }
+                        }
+                        const bool take = alive && lq == 0 && p <= r2;
+                        if (STATS && alive && lq == 0) { st_d += a.d; st_a += take; }
+                        const int id = take ? a.ids[m.slot + i] : 0;
+                        lm_append(a, take, q, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned)id);
+                    }
+                }
+                if (STATS) {
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        st_c += __shfl_xor_sync(0xffffffffu, st_c, off);
+                        st_d += __shfl_xor_sync(0xffffffffu, st_d, off);
+                        st_a += __shfl_xor_sync(0xffffffffu, st_a, off);
+                        st_p += __shfl_xor_sync(0xffffffffu, st_p, off);
+                    }
+                    if (lane == 0) {
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 0]), st_c);
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 1]), st_d);
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 2]), st_a);
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 3]), st_p);
+                    }
+                }
+                __syncwarp();   // this warp's survivor list is reused by its next query
+            }
+            __syncthreads();    // every warp is done with buffer buf
+            if (tid == 0 && t + 2 < ntile) issue(t + 2);
+        }
+    }
+}
+
+// ---- work list -------------------------------------------------------------------
+__global__ void k_lm_count(const int32_t *__restrict__ probe, int64_t nq, int nprobe, int seed, int *__restrict__ cnt) {
+    const int64_t total = nq * (int64_t)(nprobe - seed);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e / (nprobe - seed);
+        const int j = seed + (int)(e % (nprobe - seed));
+        atomicAdd(&cnt[probe[q * nprobe + j]], 1);
+    }
+}
+
+// items[c] = ceil(cnt[c] / LG); both arrays get a trailing 0 for the scans.
+__global__ void k_lm_items(const int *__restrict__ cnt, int nc, int *__restrict__ off, int *__restrict__ items) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= nc; c += gridDim.x * blockDim.x) {
+        const int v = c < nc ? cnt[c] : 0;
+        off[c] = v;
+        items[c] = (v + LG - 1) / LG;
+    }
+}
+
+__global__ void k_lm_scatter(const int32_t *__restrict__ probe, int64_t nq, int nprobe, int seed, int *__restrict__ fill,
+                             int32_t *__restrict__ lq_items) {
+    const int64_t total = nq * (int64_t)(nprobe - seed);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e / (nprobe - seed);
+        const int j = seed + (int)(e % (nprobe - seed));
+        lq_items[atomicAdd(&fill[probe[q * nprobe + j]], 1)] = (int32_t)q;
+    }
+}
+
+// ---- final merge: the K smallest keys of the first-phase result and the
+// query's accepted keys.  Keys are unique (ids are), so a radix select on the
+// 64-bit key finds the K-th smallest exactly; the keys at most it are then
+// rank-sorted.  One CTA per query.
+constexpr int MT = 256;
+
+__global__ void __launch_bounds__(MT) k_lm_merge(int64_t *__restrict__ ids, float *__restrict__ dists, int k,
+                                                 const unsigned long long *__restrict__ acc,
+                                                 const int *__restrict__ acnt, int64_t cap) {
+    __shared__ unsigned long long s1[DADE_MAX_K], sel[DADE_MAX_K];
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long s_prefix;
+    __shared__ unsigned s_rank, s_cnt;
+    __shared__ int s_n1;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t q = blockIdx.x;
+    if (tid == 0) s_n1 = 0;
+    __syncthreads();
+    for (int j = tid; j < k; j += MT) {   // first-phase results: a sorted prefix of valid entries
+        const int64_t id = ids[q * k + j];
+        if (id >= 0) {
+            s1[j] = ((unsigned long long)__float_as_uint(dists[q * k + j]) << 32) | (unsigned)id;
+            atomicAdd(&s_n1, 1);
+        }
+    }
+    __syncthreads();
+    const int n1 = s_n1, n2 = acnt[q], n = n1 + n2;
+    const unsigned long long *a2 = acc + q * cap;
+    auto key = [&](int j) { return j < n1 ? s1[j] : a2[j - n1]; };
+    unsigned long long bound = ~0ull;   // select every key when n <= k
+    if (n > k) {
+        unsigned long long prefix = 0, mask = 0;
+        unsigned rank = (unsigned)k;
+        for (int pass = 0; pass < 8; ++pass) {
+            const int shift = 56 - 8 * pass;
+            hist[tid] = 0;
+            __syncthreads();
+            for (int j0 = 0; j0 < n; j0 += MT) {
+                const int j = j0 + tid;
+                const unsigned long long kk = j < n ? key(j) : 0ull;
+                const bool in = j < n && (kk & mask) == prefix;
+                const unsigned bin = in ? (unsigned)((kk >> shift) & 255u) : 256u;
+                const unsigned peers = __match_any_sync(0xffffffffu, bin);
+                if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
+            }
+            __syncthreads();
+            if (tid < 32) {
+                unsigned loc[8], s = 0;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) { loc[t] = hist[lane * 8 + t]; s += loc[t]; }
+                unsigned inc = s;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const unsigned v = __shfl_up_sync(0xffffffffu, inc, off);
+                    if (lane >= off) inc += v;
+                }
+                const unsigned before = inc - s;
+                if (before < rank && inc >= rank) {
+                    unsigned cc = before;
+                    int t = 0;
+                    while (cc + loc[t] < rank) { cc += loc[t]; ++t; }
+                    s_prefix = prefix | ((unsigned long long)(lane * 8 + t) << shift);
+                    s_rank = rank - cc;
+                }
+            }
+            __syncthreads();
+            prefix = s_prefix;
+            rank = s_rank;
+            mask |= 255ull << shift;
+            __syncthreads();
+        }
+        bound = prefix;   // the k-th smallest key
+    }
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    for (int j = tid; j < n; j += MT) {
+        const unsigned long long kk = key(j);
+        if (kk <= bound) {
+            const unsigned slot = atomicAdd(&s_cnt, 1u);
+            if (slot < (unsigned)k) sel[slot] = kk;
+        }
+    }
+    __syncthreads();
+    const int m = min((int)s_cnt, k);
+    for (int t = tid; t < k; t += MT) {
+        if (t < m) {
+            const unsigned long long kk = sel[t];
+            int r = 0;
+            for (int u = 0; u < m; ++u) r += sel[u] < kk;
+            ids[q * k + r] = (int64_t)(unsigned)(kk & 0xffffffffu);
+            dists[q * k + r] = __uint_as_float((unsigned)(kk >> 32));
+        } else {
+            ids[q * k + t] = -1;
+            dists[q * k + t] = INFINITY;
+        }
+    }
+}
+
+int grid_of(int64_t work, int threads) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((work + threads - 1) / threads, 152 * 16));
+}
+
+template <int GB, bool STATS>
+dade_status launch_lm(const LmArgs &a, cudaStream_t s) {
+    static int blocks = 0;
+    const size_t smem = LmSmem::total(GB);
+    if (blocks == 0) {
+        DADE_TRY_CUDA(cudaFuncSetAttribute(k_lm<GB, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int dev = 0, sms = 0, per = 0;
+        DADE_TRY_CUDA(cudaGetDevice(&dev));
+        DADE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        DADE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lm<GB, STATS>, LNT, smem));
+        blocks = std::max(1, sms * std::max(1, per));
+    }
+    k_lm<GB, STATS><<<blocks, LNT, smem, s>>>(a);
+    return launch_check("k_lm");
+}
+
+template <bool STATS>
+dade_status launch_lm_gb(const LmArgs &a, int gb, cudaStream_t s) {
+    switch (gb) {
+    case 1: return launch_lm<1, STATS>(a, s);
+    case 2: return launch_lm<2, STATS>(a, s);
+    case 4: return launch_lm<4, STATS>(a, s);
+    default: return launch_lm<8, STATS>(a, s);
+    }
+}
+
+} // namespace
+
+// The seeded schedule for queries [0, nq) of p (see the file comment).
+dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s) {
+    if (nq == 0) return DADE_OK;
+    const int S = p.seed_lists;
+    const int np = p.nprobe;
+    const bool fd = p.mode == DADE_MODE_FD;
+    const int gb = fd ? LNB : std::min(p.delta_d / 16, ix->nb);
+    if (ix->nb != LNB || (gb != 1 && gb != 2 && gb != 4 && gb != 8)) {
+        set_error("the seeded schedule needs D in 113..128 and delta_d in {16, 32, 64, >= 128}");
+        return DADE_EUNSUPPORTED;
+    }
+    // phase 1: the first S lists, tile schedule, straight into the outputs
+    ScanParams p1 = p;
+    p1.nprobe = S;
+    p1.pstride = np;
+    p1.schedule = DADE_SCHED_TILE;
+    DADE_TRY(scan(ix, nq, p1, s));
+    // work list: (query, list) pairs of positions >= S grouped by list
+    const int nc = ix->nc;
+    const int64_t pairs = nq * (int64_t)(np - S);
+    DADE_TRY(ix->ws_lm_cnt.ensure(sizeof(int) * (size_t)(nc + 1) * 4));
+    int *cnt = ix->ws_lm_cnt.as<int>(), *off = cnt + (nc + 1), *items = off + (nc + 1), *fill = items + (nc + 1);
+    DADE_TRY(ix->ws_lm_items.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(pairs, 1) + 16));
+    int32_t *lq_items = ix->ws_lm_items.as<int32_t>();
+    unsigned *ctr = reinterpret_cast<unsigned *>(lq_items + std::max<int64_t>(pairs, 1));
+    const int64_t cap = (int64_t)(np - S) * std::max(ix->max_list, 1);
+    DADE_TRY(ix->ws_lm_acc.ensure(sizeof(unsigned long long) * (size_t)(nq * cap)));
+    DADE_TRY(ix->ws_lm_acnt.ensure(sizeof(int) * (size_t)nq));
+    DADE_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(nc + 1), s));
+    DADE_TRY_CUDA(cudaMemsetAsync(ix->ws_lm_acnt.p, 0, sizeof(int) * (size_t)nq, s));
+    DADE_TRY_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned), s));
+    k_lm_count<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, S, cnt);
+    DADE_TRY(launch_check("k_lm_count"));
+    k_lm_items<<<grid_of(nc + 1, 256), 256, 0, s>>>(cnt, nc, off, items);
+    DADE_TRY(launch_check("k_lm_items"));
+    DADE_TRY(exclusive_scan_int(off, nc + 1, s));
+    DADE_TRY(exclusive_scan_int(items, nc + 1, s));
+    DADE_TRY_CUDA(cudaMemcpyAsync(fill, off, sizeof(int) * (size_t)(nc + 1), cudaMemcpyDeviceToDevice, s));
+    k_lm_scatter<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, S, fill, lq_items);
+    DADE_TRY(launch_check("k_lm_scatter"));
+    // phase 2: list-major, persistent
+    LmArgs a{};
+    a.data = ix->data.as<float>();
+    a.ids = ix->ids.as<int32_t>();
+    a.meta = ix->meta.as<ListMeta>();
+    a.q_rot = p.q_rot;
+    a.lq_items = lq_items;
+    a.lq_off = off;
+    a.item_off = items;
+    a.ctr = ctr;
+    a.r2src = p.dists;
+    a.acc = ix->ws_lm_acc.as<unsigned long long>();
+    a.acnt = ix->ws_lm_acnt.as<int>();
+    a.stats = p.stats;
+    a.err = ix->errflag.as<int>();
+    a.cap = cap;
+    a.q_stride = p.q_stride;
+    a.nc = nc;
+    a.k = p.k;
+    a.d = ix->d;
+    if (p.use_tail && ix->tail_nb0 > 0) {
+        a.tail = ix->tail.as<float>();
+        a.tail_nb0 = ix->tail_nb0;
+        a.tail_w = ix->tail_w;
+    }
+    const int n_inc = (LNB + gb - 1) / gb;
+    for (int j = 0; j < LNB; ++j) a.coef[j] = (!fd && j < n_inc - 1) ? p.coef[j] : INFINITY;
+    DADE_TRY(p.stats ? launch_lm_gb<true>(a, gb, s) : launch_lm_gb<false>(a, gb, s));
+    // final merge
+    k_lm_merge<<<(unsigned)nq, MT, 0, s>>>(p.ids, p.dists, p.k, a.acc, a.acnt, cap);
+    return launch_check("k_lm_merge");
+}
+
+} // namespace dade

@@ -55,6 +55,13 @@ __global__ void k_order_scatter(const int32_t *__restrict__ probe, int64_t nq, i
 
 } // namespace
 
+// Exclusive prefix sum of a[0..n) in place (n small: one CTA).
+dade_status exclusive_scan_int(int *a, int n, cudaStream_t s) {
+    if (n <= 0) return DADE_OK;
+    k_order_scan<<<1, 1024, 0, s>>>(a, n);
+    return launch_check("k_order_scan");
+}
+
 dade_status order_queries(const dade_index *ix, const int32_t *probe, int64_t nq, int32_t nprobe, int32_t *order,
                           cudaStream_t s) {
     if (nq == 0) return DADE_OK;

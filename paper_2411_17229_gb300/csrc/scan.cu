@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
     unsigned long long *top0 = reinterpret_cast<unsigned long long *>(smem + L.top);
     unsigned long long *top1 = top0 + a.k;
 
-    const int32_t *plist = a.probe + qi * a.nprobe;
+    const int32_t *plist = a.probe + qi * a.pstride;
     for (int k = tid; k < a.dp; k += NT) qv[k] = k < a.d ? a.q_rot[qi * a.q_stride + k] : 0.f;
     for (int p = tid; p < min(a.nprobe, PMETA); p += NT) {
         const ListMeta m = a.meta[plist[p]];
@@ -401,6 +401,8 @@ dade_status scan_fast(const scanning::ScanArgs &a, int64_t nq, bool fd, int thre
 
 dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s) {
     if (nq == 0) return DADE_OK;
+    if (p.schedule == DADE_SCHED_SEEDED && p.seed_lists > 0 && p.seed_lists < p.nprobe)
+        return scan_seeded(ix, nq, p, s);
     ScanArgs a{};
     a.data = ix->data.as<float>();
     a.ids = ix->ids.as<int32_t>();
@@ -419,6 +421,7 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     a.err = ix->errflag.as<int>();
     a.q_stride = p.q_stride;
     a.nprobe = p.nprobe;
+    a.pstride = p.pstride > 0 ? p.pstride : p.nprobe;
     a.d = ix->d;
     a.dp = ix->dp;
     a.nb = ix->nb;

@@ -34,7 +34,7 @@ struct ScanArgs {
     float *out_d;
     int64_t *stats;
     int *err;
-    int q_stride, nprobe, d, dp, nb, k, tile, gb, n_inc, ns, delta_d, spec;
+    int q_stride, nprobe, pstride, d, dp, nb, k, tile, gb, n_inc, ns, delta_d, spec;   // pstride: probe row stride
     float coef[DADE_MAX_DIM / DADE_BLOCK];
     // low-precision leading blocks (prefilter of the first increment)
     const unsigned char *lead;   // residual codes, list region at slot * lead_nb * 16 * ES bytes

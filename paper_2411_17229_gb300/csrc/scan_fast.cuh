@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_dade_fast(const ScanArgs a) {
 
     float4 qr[NB];
     load_q<NB>(a, qi, lq, qr);
-    const int32_t *plist = a.probe + qi * a.nprobe;
+    const int32_t *plist = a.probe + qi * a.pstride;
     for (int p = tid; p < min(a.nprobe, PMETA); p += NT) {
         const ListMeta m = a.meta[plist[p]];
         smeta[p] = make_int4((int)(m.base >> 6), (int)m.slot, m.len, m.np);
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_fd_fast(const ScanArgs a) {
 
     float4 qr[NB];
     load_q<NB>(a, qi, lq, qr);
-    const int32_t *plist = a.probe + qi * a.nprobe;
+    const int32_t *plist = a.probe + qi * a.pstride;
     for (int p = tid; p < min(a.nprobe, PMETA); p += NT) {
         const ListMeta m = a.meta[plist[p]];
         smeta[p] = make_int4((int)(m.base >> 6), (int)m.slot, m.len, m.np);

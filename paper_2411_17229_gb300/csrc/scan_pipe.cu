@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_scan_pipe(const ScanArgs a) {
     unsigned long long *top0 = reinterpret_cast<unsigned long long *>(smem + L.top);
     unsigned long long *top1 = top0 + a.k;
 
-    const int32_t *plist = a.probe + qi * a.nprobe;
+    const int32_t *plist = a.probe + qi * a.pstride;
     for (int k = tid; k < a.dp; k += NT) qv[k] = k < a.d ? a.q_rot[qi * a.q_stride + k] : 0.f;
     for (int p = tid; p < min(a.nprobe, PMETA); p += NT) {
         const ListMeta m = a.meta[plist[p]];

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libdade.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EIO = range(7)
 MODE_DADE, MODE_FD = 0, 1
-SCHED_TILE, SCHED_PIPELINED = 0, 1
+SCHED_TILE, SCHED_PIPELINED, SCHED_SEEDED = 0, 1, 2
 FLAG_GENERIC_KERNEL, FLAG_LEAD, FLAG_QUERY_ORDER, FLAG_ROW_TAIL = 1, 2, 4, 8
 LEAD_NONE, LEAD_BF16, LEAD_FP8 = 0, 1, 2
 PIPE_MAX = 8
@@ -43,7 +43,7 @@ class BuildOpts(C.Structure):
 class SearchOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tile", C.c_int32), ("stats", C.c_void_p), ("spec", C.c_int32),
                 ("threads", C.c_int32), ("schedule", C.c_int32), ("flags", C.c_int32),
-                ("lead_stats", C.c_void_p), ("reserved", C.c_int32 * 2)]
+                ("lead_stats", C.c_void_p), ("seed_lists", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class Info(C.Structure):
@@ -194,25 +194,25 @@ class Index:
         return out
 
     def search(self, q_rot, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-               threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, stream=None):
+               threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
-                       flags=flags, lead_stats=_ptr(lead_stats))
+                       flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists)
         _check(lib().dade_search(self._h, _ptr(q_rot), q_rot.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                  C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def scan(self, q_rot, probe, k, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-             threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, stream=None):
+             threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
-                       flags=flags, lead_stats=_ptr(lead_stats))
+                       flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists)
         _check(lib().dade_scan(self._h, _ptr(q_rot), _ptr(probe), q_rot.shape[0], int(k), probe.shape[1],
                                float(alpha), int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def query(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-              threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, stream=None):
+              threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
-                       flags=flags, lead_stats=_ptr(lead_stats))
+                       flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists)
         _check(lib().dade_query(self._h, _ptr(q), q.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                 C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists

@@ -43,22 +43,23 @@ class Case:
         self.scale = float(np.mean((self.orc.Xr ** 2).sum(1)))
 
     def gpu_search(self, k, nprobe, alpha, delta_d, mode=dade.MODE_DADE, tile=128, stats=False,
-                   schedule=dade.SCHED_TILE, threads=0, flags=0):
+                   schedule=dade.SCHED_TILE, threads=0, flags=0, seed_lists=0):
         nq = self.queries.shape[0]
         ids = torch.empty(nq, k, dtype=torch.int64, device="cuda")
         d = torch.empty(nq, k, dtype=torch.float32, device="cuda")
         st = torch.zeros(nq, 4, dtype=torch.int64, device="cuda") if stats else None
         self.gpu.search(self.q_rot, k, nprobe, alpha, delta_d, ids, d, mode=mode, tile=tile, stats=st,
-                        schedule=schedule, threads=threads, flags=flags)
+                        schedule=schedule, threads=threads, flags=flags, seed_lists=seed_lists)
         self.gpu.sync()
         out = ids.cpu().numpy(), d.cpu().numpy()
         return out + ((st.cpu().numpy(),) if stats else ())
 
-    def oracle_search(self, k, nprobe, alpha, delta_d, fd=False, tile=128, schedule=dade.SCHED_TILE):
+    def oracle_search(self, k, nprobe, alpha, delta_d, fd=False, tile=128, schedule=dade.SCHED_TILE, seed=0):
         eps = None if fd else self.orc.eps(np.float32(alpha), delta_d)
         lag = 0 if fd else dade.schedule_lag(self.base.shape[1], delta_d, schedule)
         return self.orc.o.search(self.orc.Xr, self.assign, self.orc.cent, self.orc.lam, self.Qr, k, nprobe,
-                                 delta_d if not fd else 64, eps, schedule=oracle.TILE, tile=tile, lag=lag)
+                                 delta_d if not fd else 64, eps, schedule=oracle.TILE, tile=tile, lag=lag,
+                                 seed=seed)
 
     def exact_d(self, q, ids):
         return ((self.orc.Xr[ids] - self.Qr[q]) ** 2).sum(1)
@@ -297,3 +298,53 @@ def test_row_tail_gives_same_results(tail_from, delta_d, flags):
         out.append((ids.cpu().numpy(), d.cpu().numpy(), st.cpu().numpy()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
     assert np.array_equal(out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("k,nprobe,alpha,delta_d,tile,seed", [
+    (10, 8, 0.05, 32, 128, 2),
+    (10, 8, 0.1, 16, 64, 1),
+    (100, 16, 0.3, 64, 256, 2),
+    (1, 4, 0.2, 32, 32, 3),
+    (256, 8, 0.1, 64, 128, 1),       # phase 1 finds fewer than K: r frozen at +inf
+    (20, 12, 0.1, 128, 128, 2),      # one increment
+])
+@pytest.mark.parametrize("flags", [0, dade.FLAG_QUERY_ORDER])
+def test_seeded_schedule_parity(c1, k, nprobe, alpha, delta_d, tile, seed, flags):
+    g_ids, g_d, g_st = c1.gpu_search(k, nprobe, alpha, delta_d, tile=tile, stats=True, schedule=dade.SCHED_SEEDED,
+                                     seed_lists=seed, flags=flags)
+    o_ids, o_d, o_st, oflags = c1.oracle_search(k, nprobe, alpha, delta_d, tile=tile, seed=seed)
+    parity.compare(g_ids, g_d, o_ids, o_d, oflags, c1.scale, c1.exact_d)
+    assert np.array_equal(g_st[:, 0], o_st[:, 0])
+    clean = oflags == 0
+    assert np.array_equal(g_st[clean, 1:], o_st[clean, 1:])
+
+
+@pytest.mark.parametrize("k,nprobe", [(10, 8), (100, 16)])
+def test_seeded_fd_is_fd(c1, k, nprobe):
+    """FDScanning under the seeded schedule is exact IVF: the same results as
+    the tile schedule, whatever the seed."""
+    a = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD)
+    b = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD, schedule=dade.SCHED_SEEDED, seed_lists=1)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+
+
+def test_seeded_schedule_mixture_and_limits():
+    """A 128-dim mixture whose lists are its 24 components (uneven, some
+    probed by many queries), and the limits of the seed."""
+    w = synth.Workload("mix128_test", 16000, 128, 90, 1.0, 24, 0.0, 3.0, 1.0, False, False, 24, (4,), 10, (16,), 0.1)
+    base, queries, labels = synth.make(w)
+    case = Case(base, queries, labels, 24, n_pairs=8000)
+    for k, nprobe, seed, dd in ((10, 6, 1, 32), (50, 8, 2, 16), (30, 12, 3, 64)):
+        g_ids, g_d = case.gpu_search(k, nprobe, 0.1, dd, schedule=dade.SCHED_SEEDED, seed_lists=seed)
+        o_ids, o_d, _, oflags = case.oracle_search(k, nprobe, 0.1, dd, seed=seed)
+        parity.compare(g_ids, g_d, o_ids, o_d, oflags, case.scale, case.exact_d)
+    # seed >= nprobe is the tile schedule
+    a = case.gpu_search(10, 4, 0.1, 32, stats=True)
+    b = case.gpu_search(10, 4, 0.1, 32, stats=True, schedule=dade.SCHED_SEEDED, seed_lists=4)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    # D = 64 is outside the list-major kernels
+    small = Case(*synth.make(synth.Workload("mix64", 3000, 64, 10, 1.0, 6, 0.0, 3.0, 1.0, False, False, 6, (4,),
+                                            10, (16,), 0.1))[:2], synth.zipf_assign(3000, 6, s=0.5), 6, n_pairs=1000)
+    with pytest.raises(dade.DadeError) as e:
+        small.gpu_search(5, 4, 0.1, 32, schedule=dade.SCHED_SEEDED, seed_lists=1)
+    assert e.value.status == dade.EUNSUPPORTED
