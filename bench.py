@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: fixed --point, no autotune, ground truth, baselines or e2e")
-    ap.add_argument("--point", default="nprobe=20,alpha=0.3,delta_d=64,tile=256,threads=128",
+    ap.add_argument("--point", default="nprobe=20,alpha=0.3,delta_d=64,tile=256,threads=128,schedule=2,seed_lists=3,"
+                                       "flags=12",
                     help="operating point of --profile (comma-separated key=value)")
     ap.add_argument("--tail-from", type=int, default=32,
                     help="first dim of the index's row-major tail copy (0: none); survivors gather from it")
@@ -74,7 +75,8 @@ def parse():
 
 
 def parse_point(text, dade):
-    pt = {"mode": dade.MODE_DADE, "spec": 8, "schedule": dade.SCHED_TILE, "tile": 128, "threads": 128, "flags": 0}
+    pt = {"mode": dade.MODE_DADE, "spec": 8, "schedule": dade.SCHED_TILE, "tile": 128, "threads": 128, "flags": 0,
+          "seed_lists": 0}
     for kv in text.split(","):
         k, v = kv.split("=")
         pt[k.strip()] = float(v) if k.strip() == "alpha" else int(v)
@@ -110,7 +112,7 @@ def run_profile(args):
         ix.probe(qr, pt["nprobe"], pr)
         ix.scan(qr, pr, w.k, pt.get("alpha", 0.1), pt.get("delta_d", 32), ids, dists, mode=pt["mode"],
                 tile=pt["tile"], spec=pt["spec"], threads=pt["threads"], schedule=pt["schedule"],
-                flags=pt["flags"])
+                flags=pt["flags"], seed_lists=pt["seed_lists"])
         e1.record()
         torch.cuda.synchronize()
         if i >= args.warmup:
@@ -195,7 +197,8 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-SCAN_SOURCES = ("scan.cu", "scan_fast.cu", "scan_fast.cuh", "scan_lead.cu", "scan_pipe.cu", "scan_common.cuh")
+SCAN_SOURCES = ("scan.cu", "scan_fast.cu", "scan_fast.cuh", "scan_lead.cu", "scan_pipe.cu", "scan_common.cuh", "lm.cu",
+                "order.cu")
 
 
 def scan_source_hash():
@@ -234,7 +237,8 @@ def recorded_traffic(point, workload):
     if rec.get("scan_cu_sha256_16") != scan_source_hash() or rec.get("workload") != workload:
         return None
     if any(rec.get("point", {}).get(k) != point.get(k) for k in ("nprobe", "alpha", "delta_d", "spec", "threads",
-                                                                  "tile", "mode", "schedule", "flags")):
+                                                                  "tile", "mode", "schedule", "flags",
+                                                                  "seed_lists")):
         return None
     return rec.get("dram_bytes_per_launch")
 

@@ -80,7 +80,7 @@ __device__ __forceinline__ void lm_append(const LmArgs &a, bool take, int q, uns
 }
 
 template <int GB, bool STATS>
-__global__ void __launch_bounds__(LNT, 1) k_lm(const LmArgs a) {
+__global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
     constexpr int NINC = (LNB + GB - 1) / GB;
     constexpr int NREST = LNB - GB;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -162,30 +162,41 @@ __global__ void __launch_bounds__(LNT, 1) k_lm(const LmArgs a) {
                 int nsv = 0;
                 unsigned long long st_c = 0, st_d = 0, st_a = 0, st_p = 0;
                 const float c0 = a.coef[0] * r2;
-                for (int k0 = 0; k0 < tn; k0 += 8) {
-                    const int cand = k0 + quad;
-                    const bool act = cand < tn;
-                    float p = 0.f;
-                    if (act) {
+                for (int k0 = 0; k0 < tn; k0 += 16) {
+                    float pp[2];
+                    bool aa[2];
 #pragma unroll
-                        for (int b = 0; b < GB; ++b)
-                            p += sqd4(qa[b], *reinterpret_cast<const float4 *>(st + ((size_t)b * LT + cand) * 16 + lq * 4));
+                    for (int h = 0; h < 2; ++h) {
+                        const int cand = k0 + 8 * h + quad;
+                        aa[h] = cand < tn;
+                        float p = 0.f;
+                        if (aa[h]) {
+#pragma unroll
+                            for (int b = 0; b < GB; ++b)
+                                p += sqd4(qa[b], *reinterpret_cast<const float4 *>(st + ((size_t)b * LT + cand) * 16 + lq * 4));
+                        }
+                        pp[h] = p;
                     }
-                    p = quad_sum4(p);
-                    const bool lead = act && lq == 0;
-                    if (NINC == 1) {
-                        const bool take = lead && p <= r2;
-                        const int id = take ? a.ids[m.slot + i0 + cand] : 0;
-                        lm_append(a, take, q, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned)id);
-                        if (STATS && lead) { ++st_c; st_d += a.d; st_a += take; }
-                    } else {
-                        const bool keep = lead && !(p > c0);
-                        const unsigned mk = __ballot_sync(0xffffffffu, keep);
-                        if (keep) sv[nsv + __popc(mk & ((1u << lane) - 1u))] = Surv{cand, p};
-                        nsv += __popc(mk);
-                        if (STATS && lead) {
-                            ++st_c;
-                            if (!keep) { st_d += min(GB * 16, a.d); ++st_p; }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int cand = k0 + 8 * h + quad;
+                        const bool act = aa[h];
+                        const float p = quad_sum4(pp[h]);
+                        const bool lead = act && lq == 0;
+                        if (NINC == 1) {
+                            const bool take = lead && p <= r2;
+                            const int id = take ? a.ids[m.slot + i0 + cand] : 0;
+                            lm_append(a, take, q, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned)id);
+                            if (STATS && lead) { ++st_c; st_d += a.d; st_a += take; }
+                        } else {
+                            const bool keep = lead && !(p > c0);
+                            const unsigned mk = __ballot_sync(0xffffffffu, keep);
+                            if (keep) sv[nsv + __popc(mk & ((1u << lane) - 1u))] = Surv{cand, p};
+                            nsv += __popc(mk);
+                            if (STATS && lead) {
+                                ++st_c;
+                                if (!keep) { st_d += min(GB * 16, a.d); ++st_p; }
+                            }
                         }
                     }
                 }
