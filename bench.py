@@ -472,6 +472,7 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = world * nq / (ms_per_step / 1e3)
     rc_timed = recall_at_k(torch, xb, q, ids, gt_kth, K)
+    ids_timed = ids.clone()
 
     # ---- FD baseline timed the same way (same step structure) ------------------------
     fd_pt = fd_best[2] if fd_best else {"mode": dade.MODE_FD, "nprobe": n0, "tile": 128, "threads": 128,
@@ -493,6 +494,31 @@ def run_ours(args):
             fd_ms.append(e0.elapsed_time(e1))
     fd_qps = nq / (statistics.mean(fd_ms) / 1e3)
     fd_recall = recall_at_k(torch, xb, q, ids, gt_kth, K)
+
+    # ---- the same step replayed as a captured CUDA graph (device buffers) ----------------
+    graph_ms = None
+    try:
+        gids = torch.empty(nq, K, dtype=torch.int64, device="cuda")
+        gd = torch.empty(nq, K, dtype=torch.float32, device="cuda")
+        g = ix.graph(q, K, point["nprobe"], point["alpha"], point["delta_d"], gids, gd, mode=point["mode"],
+                     tile=point["tile"], spec=point["spec"], threads=point["threads"], schedule=point["schedule"],
+                     flags=point["flags"], seed_lists=point.get("seed_lists", 0))
+        gms = []
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.launch(stream=sh)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                gms.append(e0.elapsed_time(e1))
+        graph_ms = statistics.mean(gms)
+        graph_same = bool(torch.equal(gids, ids_timed))
+        g.close()
+    except Exception as e:  # noqa: BLE001 - reported, not fatal
+        log(f"[bench] graph step failed: {e}")
+        graph_same = None
 
     # ---- end to end through the C ABI with host buffers -------------------------------
     q_host = torch.from_numpy(queries).pin_memory()
@@ -550,6 +576,8 @@ def run_ours(args):
                             "seed_lists": fd_pt.get("seed_lists") or None,
                             "ms_per_step": round(statistics.mean(fd_ms), 4)},
             "dade_vs_fd": round(value / world / fd_qps, 3),
+            "graph": ({"ms_per_step": round(graph_ms, 4), "value": round(world * nq / (graph_ms / 1e3), 1),
+                       "unit": UNIT, "same_ids_as_timed_step": graph_same} if graph_ms else None),
             "work": {"candidates": cand, "dims_per_candidate": round(dims_sum / max(1, cand), 2),
                      "accepted": accepted, "lead_dropped": lead_dropped},
             "roofline": roof,

@@ -224,6 +224,25 @@ dade_status dade_build_index(const float *base, int64_t n, int32_t d, const dade
 void dade_free_index(dade_index *ix);
 
 /*
+ * A query step captured into a CUDA graph (no counterpart in the paper; a
+ * launch-overhead device for small, repeated batches).  dade_graph_create
+ * runs dade_query(ix, q, nq, k, nprobe, alpha, delta_d, opts, ids, dists)
+ * once, then captures the same call on a private stream; q, ids, dists (and
+ * opts->stats, opts->lead_stats if set) must be device buffers, and stay
+ * bound to the graph: a launch reads whatever q holds at that time and
+ * overwrites ids and dists.  The graph uses the index's workspace: launch it
+ * while no other call on the same index is in flight, and free it before the
+ * index.  dade_graph_launch enqueues one replay on `stream`.  Errors:
+ * DADE_EINVAL (host buffers, bad arguments), DADE_ECUDA (capture refused).
+ */
+typedef struct dade_graph dade_graph;
+dade_status dade_graph_create(const dade_index *ix, const float *q, int64_t nq, int32_t k, int32_t nprobe,
+                              float alpha, int32_t delta_d, const dade_search_opts *opts, int64_t *ids, float *dists,
+                              dade_graph **out);
+dade_status dade_graph_launch(dade_graph *g, dade_stream stream);
+void dade_graph_free(dade_graph *g);
+
+/*
  * Write a built index to `path` as one binary file (this library's own
  * format, version 1, little-endian; the paper stores no index): the FP64
  * offline results (mean, basis, eigenvalues, rho_d sample), the list

@@ -60,6 +60,9 @@ SIGNATURES = {
     "dade_build_index": (_i32, [_vp, _i64, _i32, _vp, _vp, _vp]),
     "dade_free_index": (None, [_vp]),
     "dade_save_index": (_i32, [_vp, C.c_char_p]),
+    "dade_graph_create": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
+    "dade_graph_launch": (_i32, [_vp, _vp]),
+    "dade_graph_free": (None, [_vp]),
     "dade_load_index": (_i32, [C.c_char_p, _vp]),
     "dade_rotate_queries": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "dade_probe": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
@@ -217,6 +220,13 @@ class Index:
                                 C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
+    def graph(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
+              threads=0, schedule=SCHED_TILE, flags=0, seed_lists=0):
+        """A query step captured into a CUDA graph (device buffers, bound to the graph)."""
+        return Graph(self, q, k, nprobe, alpha, delta_d, ids, dists,
+                     SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads,
+                                schedule=schedule, flags=flags, seed_lists=seed_lists))
+
     def reserve(self, max_nq, max_nprobe):
         _check(lib().dade_reserve(self._h, int(max_nq), int(max_nprobe)))
 
@@ -261,3 +271,28 @@ def host_sym_eig(a):
     w, v = np.empty(n), np.empty((n, n))
     _check(lib().dade_host_sym_eig(a.ctypes.data, n, w.ctypes.data, v.ctypes.data))
     return w, v
+
+
+class Graph:
+    """A captured query step of an Index (see dade_graph_create)."""
+
+    def __init__(self, index, q, k, nprobe, alpha, delta_d, ids, dists, opts):
+        self._index, self._keep = index, (q, ids, dists, opts)
+        h = C.c_void_p()
+        _check(lib().dade_graph_create(index.handle, _ptr(q), q.shape[0], int(k), int(nprobe), float(alpha),
+                                       int(delta_d), C.byref(opts), _ptr(ids), _ptr(dists), C.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib().dade_graph_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dade_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
