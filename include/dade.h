@@ -243,6 +243,48 @@ dade_status dade_graph_launch(dade_graph *g, dade_stream stream);
 void dade_graph_free(dade_graph *g);
 
 /*
+ * Continuous-batching request server over one resident index (no counterpart
+ * in the paper).  Requests (host queries with their own K, nprobe, alpha,
+ * delta_d) are queued by dade_server_submit and admitted by a dispatcher
+ * thread into slots as slots free up: each slot is a CUDA stream with its
+ * own device workspace and pinned buffers, so batches in different slots
+ * overlap on the GPU.  A batch is the oldest pending request plus every
+ * later pending request with the same K, nprobe, alpha and delta_d, up to
+ * max_batch queries.  Every query's result depends only on that query, so a
+ * request gets the same result alone and in any mix.  The slot count is cut
+ * to what device_budget holds (an estimate per slot is reported in the
+ * statistics).  The caller's query and result buffers must stay valid until
+ * dade_server_wait returns for the ticket.  dade_server_free drains the
+ * queue and the slots.
+ */
+typedef struct dade_server dade_server;
+typedef struct {
+    int32_t slots;             /* batches in flight on the GPU at once (default 4) */
+    int32_t max_batch;         /* queries per batch, and per request (default 1024) */
+    int32_t max_k;             /* largest K of a request (default 100) */
+    int32_t max_nprobe;        /* largest nprobe of a request (default 128) */
+    int64_t device_budget;     /* device bytes for the slots (0: no limit); fewer slots if needed */
+    int32_t mode, tile, threads, schedule, seed_lists, flags;   /* dade_search_opts of every batch */
+    int32_t reserved[4];
+} dade_server_opts;
+typedef struct {
+    int64_t slots, slot_bytes;          /* slots created, device bytes budgeted per slot */
+    int64_t requests, requests_done;    /* submitted, completed */
+    int64_t batches, queries;           /* batches launched, queries in them */
+    int64_t max_inflight;               /* most batches on the GPU at once */
+} dade_server_stats;
+void dade_server_opts_default(dade_server_opts *o);
+dade_status dade_server_create(const dade_index *ix, const dade_server_opts *opts, dade_server **out);
+/* Queue a request: q host [nq * d] raw queries; ids, dists host [nq * k], written before the ticket completes. */
+dade_status dade_server_submit(dade_server *s, const float *q, int64_t nq, int32_t k, int32_t nprobe, float alpha,
+                               int32_t delta_d, int64_t *ids, float *dists, uint64_t *ticket);
+/* Wait for a ticket (timeout_ms < 0: no limit; DADE_ETIMEOUT if it expires, the ticket stays valid).
+ * latency_s (may be NULL): seconds from submit to completion. */
+dade_status dade_server_wait(dade_server *s, uint64_t ticket, int64_t timeout_ms, double *latency_s);
+dade_status dade_server_stats_get(dade_server *s, dade_server_stats *out);
+void dade_server_free(dade_server *s);
+
+/*
  * Write a built index to `path` as one binary file (this library's own
  * format, version 1, little-endian; the paper stores no index): the FP64
  * offline results (mean, basis, eigenvalues, rho_d sample), the list

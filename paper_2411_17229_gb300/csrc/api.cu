@@ -27,6 +27,14 @@ dade_status launch_check(const char *what) {
     return DADE_OK;
 }
 
+namespace {
+thread_local Workspace *t_ws = nullptr;
+} // namespace
+
+Workspace &ws(const dade_index *ix) { return t_ws ? *t_ws : ix->ws0; }
+WorkspaceScope::WorkspaceScope(Workspace *w) : prev(t_ws) { t_ws = w; }
+WorkspaceScope::~WorkspaceScope() { t_ws = prev; }
+
 dade_status DevBuf::alloc(size_t b) {
     release();
     if (b == 0) b = 16;
@@ -151,9 +159,9 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
 
 dade_status run_search(const dade_index *ix, const float *q_dev, int64_t nq, int32_t k, int32_t nprobe, float alpha,
                        int32_t delta_d, const dade_search_opts *opts, int64_t *ids, float *dists, cudaStream_t s) {
-    DADE_TRY(ix->ws_probe.ensure(sizeof(int32_t) * (size_t)nq * nprobe));
-    DADE_TRY(dade::probe(ix, q_dev, nq, ix->d, nprobe, ix->ws_probe.as<int32_t>(), s));
-    return run_scan(ix, q_dev, ix->ws_probe.as<int32_t>(), nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
+    DADE_TRY(ws(ix).probe.ensure(sizeof(int32_t) * (size_t)nq * nprobe));
+    DADE_TRY(dade::probe(ix, q_dev, nq, ix->d, nprobe, ws(ix).probe.as<int32_t>(), s));
+    return run_scan(ix, q_dev, ws(ix).probe.as<int32_t>(), nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
 }
 
 dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *probe_dev, int64_t nq, int32_t k,
@@ -163,12 +171,12 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     int64_t *ids_d = ids;
     float *dists_d = dists;
     if (ids_host) {
-        DADE_TRY(ix->ws_ids.ensure(sizeof(int64_t) * (size_t)nq * k));
-        ids_d = ix->ws_ids.as<int64_t>();
+        DADE_TRY(ws(ix).ids.ensure(sizeof(int64_t) * (size_t)nq * k));
+        ids_d = ws(ix).ids.as<int64_t>();
     }
     if (dists_host) {
-        DADE_TRY(ix->ws_dists.ensure(sizeof(float) * (size_t)nq * k));
-        dists_d = ix->ws_dists.as<float>();
+        DADE_TRY(ws(ix).dists.ensure(sizeof(float) * (size_t)nq * k));
+        dists_d = ws(ix).dists.as<float>();
     }
     ScanParams p{};
     p.q_rot = q_dev;
@@ -193,9 +201,9 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.dists = dists_d;
     p.stats = opts ? opts->stats : nullptr;
     if (opts && (opts->flags & DADE_FLAG_QUERY_ORDER)) {
-        DADE_TRY(ix->ws_order.ensure(sizeof(int32_t) * (size_t)nq));
-        DADE_TRY(dade::order_queries(ix, probe_dev, nq, nprobe, ix->ws_order.as<int32_t>(), s));
-        p.order = ix->ws_order.as<int32_t>();
+        DADE_TRY(ws(ix).order.ensure(sizeof(int32_t) * (size_t)nq));
+        DADE_TRY(dade::order_queries(ix, probe_dev, nq, nprobe, ws(ix).order.as<int32_t>(), s));
+        p.order = ws(ix).order.as<int32_t>();
     }
     DADE_TRY(dade::scan(ix, nq, p, s));
     if (ids_host)
@@ -314,13 +322,13 @@ dade_status dade_rotate_queries(const dade_index *ix, const float *q, int64_t nq
     DADE_CHECK_ARG(q != nullptr && q_rot != nullptr, "NULL pointer");
     cudaStream_t s = (cudaStream_t)stream;
     dade_status st;
-    const float *qd = stage_in(ix, q, (size_t)nq * ix->d, ix->ws_qin, s, &st);
+    const float *qd = stage_in(ix, q, (size_t)nq * ix->d, ws(ix).qin, s, &st);
     if (!qd) return st;
     const bool out_host = !is_device_ptr(q_rot);
     float *od = q_rot;
     if (out_host) {
-        DADE_TRY(ix->ws_qrot.ensure(sizeof(float) * (size_t)nq * ix->d));
-        od = ix->ws_qrot.as<float>();
+        DADE_TRY(ws(ix).qrot.ensure(sizeof(float) * (size_t)nq * ix->d));
+        od = ws(ix).qrot.as<float>();
     }
     DADE_TRY(dade::rotate(ix, qd, nq, ix->d, od, s));
     if (out_host) {
@@ -340,13 +348,13 @@ dade_status dade_probe(const dade_index *ix, const float *q_rot, int64_t nq, int
     DADE_CHECK_ARG(q_rot != nullptr && probe != nullptr, "NULL pointer");
     cudaStream_t s = (cudaStream_t)stream;
     dade_status st;
-    const float *qd = stage_in(ix, q_rot, (size_t)nq * ix->d, ix->ws_qrot, s, &st);
+    const float *qd = stage_in(ix, q_rot, (size_t)nq * ix->d, ws(ix).qrot, s, &st);
     if (!qd) return st;
     const bool out_host = !is_device_ptr(probe);
     int32_t *pd = probe;
     if (out_host) {
-        DADE_TRY(ix->ws_probe.ensure(sizeof(int32_t) * (size_t)nq * nprobe));
-        pd = ix->ws_probe.as<int32_t>();
+        DADE_TRY(ws(ix).probe.ensure(sizeof(int32_t) * (size_t)nq * nprobe));
+        pd = ws(ix).probe.as<int32_t>();
     }
     DADE_TRY(dade::probe(ix, qd, nq, ix->d, nprobe, pd, s));
     if (out_host) {
@@ -365,7 +373,7 @@ dade_status dade_search(const dade_index *ix, const float *q_rot, int64_t nq, in
     DADE_CHECK_ARG(q_rot != nullptr && ids != nullptr && dists != nullptr, "NULL pointer");
     cudaStream_t s = (cudaStream_t)stream;
     dade_status st;
-    const float *qd = stage_in(ix, q_rot, (size_t)nq * ix->d, ix->ws_qrot, s, &st);
+    const float *qd = stage_in(ix, q_rot, (size_t)nq * ix->d, ws(ix).qrot, s, &st);
     if (!qd) return st;
     return run_search(ix, qd, nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
 }
@@ -379,16 +387,16 @@ dade_status dade_scan(const dade_index *ix, const float *q_rot, const int32_t *p
     DADE_CHECK_ARG(q_rot != nullptr && probe != nullptr && ids != nullptr && dists != nullptr, "NULL pointer");
     cudaStream_t s = (cudaStream_t)stream;
     dade_status st;
-    const float *qd = stage_in(ix, q_rot, (size_t)nq * ix->d, ix->ws_qrot, s, &st);
+    const float *qd = stage_in(ix, q_rot, (size_t)nq * ix->d, ws(ix).qrot, s, &st);
     if (!qd) return st;
     const int32_t *pd = probe;
     if (!is_device_ptr(probe)) {
         for (int64_t t = 0; t < nq * (int64_t)nprobe; ++t)
             DADE_CHECK_ARG(probe[t] >= 0 && probe[t] < ix->nc, "probe[] holds a list id outside 0..n_clusters-1");
-        DADE_TRY(ix->ws_probe.ensure(sizeof(int32_t) * (size_t)nq * nprobe));
-        DADE_TRY_CUDA(cudaMemcpyAsync(ix->ws_probe.p, probe, sizeof(int32_t) * (size_t)nq * nprobe,
+        DADE_TRY(ws(ix).probe.ensure(sizeof(int32_t) * (size_t)nq * nprobe));
+        DADE_TRY_CUDA(cudaMemcpyAsync(ws(ix).probe.p, probe, sizeof(int32_t) * (size_t)nq * nprobe,
                                       cudaMemcpyHostToDevice, s));
-        pd = ix->ws_probe.as<int32_t>();
+        pd = ws(ix).probe.as<int32_t>();
     }
     return run_scan(ix, qd, pd, nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
 }
@@ -401,26 +409,26 @@ dade_status dade_query(const dade_index *ix, const float *q, int64_t nq, int32_t
     DADE_CHECK_ARG(q != nullptr && ids != nullptr && dists != nullptr, "NULL pointer");
     cudaStream_t s = (cudaStream_t)stream;
     dade_status st;
-    const float *qd = stage_in(ix, q, (size_t)nq * ix->d, ix->ws_qin, s, &st);
+    const float *qd = stage_in(ix, q, (size_t)nq * ix->d, ws(ix).qin, s, &st);
     if (!qd) return st;
-    DADE_TRY(ix->ws_qrot.ensure(sizeof(float) * (size_t)nq * ix->d));
-    DADE_TRY(dade::rotate(ix, qd, nq, ix->d, ix->ws_qrot.as<float>(), s));
-    return run_search(ix, ix->ws_qrot.as<float>(), nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
+    DADE_TRY(ws(ix).qrot.ensure(sizeof(float) * (size_t)nq * ix->d));
+    DADE_TRY(dade::rotate(ix, qd, nq, ix->d, ws(ix).qrot.as<float>(), s));
+    return run_search(ix, ws(ix).qrot.as<float>(), nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
 }
 
 dade_status dade_reserve(dade_index *ix, int64_t max_nq, int32_t max_nprobe) {
     g_err.clear();
     DADE_CHECK_ARG(ix != nullptr, "index is NULL");
     DADE_CHECK_ARG(max_nq >= 0 && max_nprobe >= 1 && max_nprobe <= ix->nc, "bad limits");
-    DADE_TRY(ix->ws_dist.ensure(sizeof(float) * (size_t)max_nq * ix->nc));
-    DADE_TRY(ix->ws_probe.ensure(sizeof(int32_t) * (size_t)max_nq * max_nprobe));
-    DADE_TRY(ix->ws_qrot.ensure(sizeof(float) * (size_t)max_nq * ix->d));
-    DADE_TRY(ix->ws_qin.ensure(sizeof(float) * (size_t)max_nq * ix->d));
-    DADE_TRY(ix->ws_order.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(max_nq, 1)));
-    DADE_TRY(ix->ws_ordcnt.ensure(sizeof(int) * (size_t)ix->nc));
+    DADE_TRY(ws(ix).dist.ensure(sizeof(float) * (size_t)max_nq * ix->nc));
+    DADE_TRY(ws(ix).probe.ensure(sizeof(int32_t) * (size_t)max_nq * max_nprobe));
+    DADE_TRY(ws(ix).qrot.ensure(sizeof(float) * (size_t)max_nq * ix->d));
+    DADE_TRY(ws(ix).qin.ensure(sizeof(float) * (size_t)max_nq * ix->d));
+    DADE_TRY(ws(ix).order.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(max_nq, 1)));
+    DADE_TRY(ws(ix).ordcnt.ensure(sizeof(int) * (size_t)ix->nc));
     // tensor-core operand image of a query batch: 128-row tiles x 32-dim chunks x 32 KB
-    DADE_TRY(ix->ws_aimg.ensure((size_t)((max_nq + 127) / 128) * ((ix->d + 31) / 32) * 32768));
-    DADE_TRY(ix->ws_anorm.ensure(sizeof(float) * (size_t)std::max<int64_t>(max_nq, 1)));
+    DADE_TRY(ws(ix).aimg.ensure((size_t)((max_nq + 127) / 128) * ((ix->d + 31) / 32) * 32768));
+    DADE_TRY(ws(ix).anorm.ensure(sizeof(float) * (size_t)std::max<int64_t>(max_nq, 1)));
     return DADE_OK;
 }
 

@@ -69,6 +69,14 @@ struct DevBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
+// Device workspace of a query call (grown on demand, reused across calls).
+// An index owns one; a server slot owns its own so that calls on different
+// streams never share scratch memory.
+struct Workspace {
+    DevBuf dist, probe, qrot, qin, ids, dists, order, ordcnt, aimg, anorm;
+    DevBuf lm_cnt, lm_items, lm_acc, lm_acnt;   // seeded schedule (lm.cu)
+};
+
 } // namespace dade
 
 struct dade_index {
@@ -101,11 +109,19 @@ struct dade_index {
     dade::DevBuf tail;
     int64_t data_floats = 0, slots = 0;
     // workspace (grown on demand, reused across calls)
-    mutable dade::DevBuf ws_dist, ws_probe, ws_qrot, ws_qin, ws_ids, ws_dists, ws_order, ws_ordcnt, ws_aimg, ws_anorm;
-    mutable dade::DevBuf ws_lm_cnt, ws_lm_items, ws_lm_acc, ws_lm_acnt;   // seeded schedule (lm.cu)
+    mutable dade::Workspace ws0;   // used unless a WorkspaceScope is active on the calling thread
 };
 
 namespace dade {
+
+// The workspace of the calling thread's current call: the one a
+// WorkspaceScope installed, else the index's own.
+Workspace &ws(const dade_index *ix);
+struct WorkspaceScope {
+    explicit WorkspaceScope(Workspace *w);
+    ~WorkspaceScope();
+    Workspace *prev;
+};
 
 // Kernel launchers (each returns DADE_OK or DADE_ECUDA after checking the launch).
 // Tensor-core GEMMs (tc_gemm.cu).  x' = W^T (x - mu) for n rows of x (row

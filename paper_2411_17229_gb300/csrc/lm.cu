@@ -440,16 +440,16 @@ dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, c
     // work list: (query, list) pairs of positions >= S grouped by list
     const int nc = ix->nc;
     const int64_t pairs = nq * (int64_t)(np - S);
-    DADE_TRY(ix->ws_lm_cnt.ensure(sizeof(int) * (size_t)(nc + 1) * 4));
-    int *cnt = ix->ws_lm_cnt.as<int>(), *off = cnt + (nc + 1), *items = off + (nc + 1), *fill = items + (nc + 1);
-    DADE_TRY(ix->ws_lm_items.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(pairs, 1) + 16));
-    int32_t *lq_items = ix->ws_lm_items.as<int32_t>();
+    DADE_TRY(ws(ix).lm_cnt.ensure(sizeof(int) * (size_t)(nc + 1) * 4));
+    int *cnt = ws(ix).lm_cnt.as<int>(), *off = cnt + (nc + 1), *items = off + (nc + 1), *fill = items + (nc + 1);
+    DADE_TRY(ws(ix).lm_items.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(pairs, 1) + 16));
+    int32_t *lq_items = ws(ix).lm_items.as<int32_t>();
     unsigned *ctr = reinterpret_cast<unsigned *>(lq_items + std::max<int64_t>(pairs, 1));
     const int64_t cap = (int64_t)(np - S) * std::max(ix->max_list, 1);
-    DADE_TRY(ix->ws_lm_acc.ensure(sizeof(unsigned long long) * (size_t)(nq * cap)));
-    DADE_TRY(ix->ws_lm_acnt.ensure(sizeof(int) * (size_t)nq));
+    DADE_TRY(ws(ix).lm_acc.ensure(sizeof(unsigned long long) * (size_t)(nq * cap)));
+    DADE_TRY(ws(ix).lm_acnt.ensure(sizeof(int) * (size_t)nq));
     DADE_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(nc + 1), s));
-    DADE_TRY_CUDA(cudaMemsetAsync(ix->ws_lm_acnt.p, 0, sizeof(int) * (size_t)nq, s));
+    DADE_TRY_CUDA(cudaMemsetAsync(ws(ix).lm_acnt.p, 0, sizeof(int) * (size_t)nq, s));
     DADE_TRY_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned), s));
     k_lm_count<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, S, cnt);
     DADE_TRY(launch_check("k_lm_count"));
@@ -471,8 +471,8 @@ dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, c
     a.item_off = items;
     a.ctr = ctr;
     a.r2src = p.dists;
-    a.acc = ix->ws_lm_acc.as<unsigned long long>();
-    a.acnt = ix->ws_lm_acnt.as<int>();
+    a.acc = ws(ix).lm_acc.as<unsigned long long>();
+    a.acnt = ws(ix).lm_acnt.as<int>();
     a.stats = p.stats;
     a.err = ix->errflag.as<int>();
     a.cap = cap;

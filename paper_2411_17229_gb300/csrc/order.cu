@@ -65,8 +65,8 @@ dade_status exclusive_scan_int(int *a, int n, cudaStream_t s) {
 dade_status order_queries(const dade_index *ix, const int32_t *probe, int64_t nq, int32_t nprobe, int32_t *order,
                           cudaStream_t s) {
     if (nq == 0) return DADE_OK;
-    DADE_TRY(ix->ws_ordcnt.ensure(sizeof(int) * (size_t)ix->nc));
-    int *cnt = ix->ws_ordcnt.as<int>();
+    DADE_TRY(ws(ix).ordcnt.ensure(sizeof(int) * (size_t)ix->nc));
+    int *cnt = ws(ix).ordcnt.as<int>();
     DADE_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)ix->nc, s));
     const unsigned g = (unsigned)std::min<int64_t>((nq + 255) / 256, 152 * 8);
     k_order_hist<<<g, 256, 0, s>>>(probe, nq, nprobe, cnt);

@@ -125,12 +125,12 @@ dade_status centroid_norms(dade_index *ix, cudaStream_t s) {
 dade_status probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t q_stride, int32_t nprobe,
                   int32_t *probe_out, cudaStream_t s) {
     if (nq == 0) return DADE_OK;
-    DADE_TRY(ix->ws_dist.ensure(sizeof(float) * (size_t)nq * ix->nc));
-    DADE_TRY(probe_distances(ix, q_rot, nq, q_stride, ix->ws_dist.as<float>(), s));
+    DADE_TRY(ws(ix).dist.ensure(sizeof(float) * (size_t)nq * ix->nc));
+    DADE_TRY(probe_distances(ix, q_rot, nq, q_stride, ws(ix).dist.as<float>(), s));
     size_t smem = sizeof(unsigned long long) * (size_t)nprobe;
     if (smem > 48 * 1024)
         DADE_TRY_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_probe_select<<<(unsigned)nq, SEL_THREADS, smem, s>>>(ix->ws_dist.as<float>(), ix->nc, nprobe, probe_out);
+    k_probe_select<<<(unsigned)nq, SEL_THREADS, smem, s>>>(ws(ix).dist.as<float>(), ix->nc, nprobe, probe_out);
     return launch_check("k_probe_select");
 }
 

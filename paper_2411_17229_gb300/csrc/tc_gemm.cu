@@ -454,8 +454,8 @@ dade_status prepare_tensor_operands(dade_index *ix, cudaStream_t s) {
 dade_status rotate(const dade_index *ix, const float *x, int64_t n, int32_t out_stride, float *out, cudaStream_t s) {
     if (n == 0) return DADE_OK;
     const int cols = std::min<int>(out_stride, ix->dp);
-    DADE_TRY(build_image(x, n, ix->d, ix->d, ix->mu32.as<float>(), ix->ws_aimg, s));
-    return launch_pipe<0>(ix->ws_aimg.as<uint32_t>(), n, ix->wt_img.as<uint32_t>(), ix->d, nullptr, nullptr, out,
+    DADE_TRY(build_image(x, n, ix->d, ix->d, ix->mu32.as<float>(), ws(ix).aimg, s));
+    return launch_pipe<0>(ws(ix).aimg.as<uint32_t>(), n, ix->wt_img.as<uint32_t>(), ix->d, nullptr, nullptr, out,
                           out_stride, cols, ix->errflag.as<int>(), s);
 }
 
@@ -471,13 +471,13 @@ dade_status rotate_direct(const dade_index *ix, const float *x, int64_t n, int32
 dade_status probe_distances(const dade_index *ix, const float *q_rot, int64_t nq, int32_t q_stride, float *dist,
                             cudaStream_t s) {
     if (nq == 0) return DADE_OK;
-    DADE_TRY(build_image(q_rot, nq, q_stride, ix->d, nullptr, ix->ws_aimg, s));
-    DADE_TRY(ix->ws_anorm.ensure(sizeof(float) * (size_t)nq));
+    DADE_TRY(build_image(q_rot, nq, q_stride, ix->d, nullptr, ws(ix).aimg, s));
+    DADE_TRY(ws(ix).anorm.ensure(sizeof(float) * (size_t)nq));
     k_sqnorm_rows<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, s>>>(q_rot, nq, q_stride, ix->d,
-                                                                   ix->ws_anorm.as<float>());
+                                                                   ws(ix).anorm.as<float>());
     DADE_TRY(launch_check("k_sqnorm_rows"));
-    return launch_pipe<1>(ix->ws_aimg.as<uint32_t>(), nq, ix->cent_img.as<uint32_t>(), ix->d,
-                          ix->ws_anorm.as<float>(), ix->cnorm.as<float>(), dist, ix->nc, ix->nc,
+    return launch_pipe<1>(ws(ix).aimg.as<uint32_t>(), nq, ix->cent_img.as<uint32_t>(), ix->d,
+                          ws(ix).anorm.as<float>(), ix->cnorm.as<float>(), dist, ix->nc, ix->nc,
                           ix->errflag.as<int>(), s);
 }
 

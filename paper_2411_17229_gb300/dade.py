@@ -46,6 +46,19 @@ class SearchOpts(C.Structure):
                 ("lead_stats", C.c_void_p), ("seed_lists", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("max_k", C.c_int32), ("max_nprobe", C.c_int32),
+                ("device_budget", C.c_int64), ("mode", C.c_int32), ("tile", C.c_int32), ("threads", C.c_int32),
+                ("schedule", C.c_int32), ("seed_lists", C.c_int32), ("flags", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("slots", C.c_int64), ("slot_bytes", C.c_int64), ("requests", C.c_int64),
+                ("requests_done", C.c_int64), ("batches", C.c_int64), ("queries", C.c_int64),
+                ("max_inflight", C.c_int64)]
+
+
 class Info(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("d_pad", C.c_int32), ("n_clusters", C.c_int32),
                 ("max_list", C.c_int32), ("eps_kept", C.c_int64), ("device_bytes", C.c_int64),
@@ -61,6 +74,12 @@ SIGNATURES = {
     "dade_free_index": (None, [_vp]),
     "dade_save_index": (_i32, [_vp, C.c_char_p]),
     "dade_graph_create": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
+    "dade_server_opts_default": (None, [_vp]),
+    "dade_server_create": (_i32, [_vp, _vp, _vp]),
+    "dade_server_submit": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp]),
+    "dade_server_wait": (_i32, [_vp, C.c_uint64, _i64, _vp]),
+    "dade_server_stats_get": (_i32, [_vp, _vp]),
+    "dade_server_free": (None, [_vp]),
     "dade_graph_launch": (_i32, [_vp, _vp]),
     "dade_graph_free": (None, [_vp]),
     "dade_load_index": (_i32, [C.c_char_p, _vp]),
@@ -289,6 +308,53 @@ class Graph:
     def close(self):
         if getattr(self, "_h", None):
             lib().dade_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+class Server:
+    """Continuous-batching request server over an Index (see dade_server_create)."""
+
+    def __init__(self, index, **opts):
+        o = ServerOpts()
+        lib().dade_server_opts_default(C.byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        h = C.c_void_p()
+        _check(lib().dade_server_create(index.handle, C.byref(o), C.byref(h)))
+        self._index, self._h, self.d = index, h, index.d
+        self._live = {}
+
+    def submit(self, q, k, nprobe, alpha=0.1, delta_d=32):
+        """Queue host queries q [nq, d]; returns a ticket.  result(ticket) gives (ids, dists, latency)."""
+        q = np.ascontiguousarray(q, np.float32)
+        ids = np.empty((q.shape[0], k), np.int64)
+        dists = np.empty((q.shape[0], k), np.float32)
+        t = C.c_uint64()
+        _check(lib().dade_server_submit(self._h, q.ctypes.data, q.shape[0], int(k), int(nprobe), float(alpha),
+                                        int(delta_d), ids.ctypes.data, dists.ctypes.data, C.byref(t)))
+        self._live[t.value] = (q, ids, dists)
+        return t.value
+
+    def result(self, ticket, timeout_ms=-1):
+        lat = C.c_double()
+        _check(lib().dade_server_wait(self._h, C.c_uint64(ticket), int(timeout_ms), C.byref(lat)))
+        q, ids, dists = self._live.pop(ticket)
+        return ids, dists, lat.value
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().dade_server_stats_get(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dade_server_free(self._h)
             self._h = None
 
     def __del__(self):
