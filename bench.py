@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--point", default="nprobe=20,alpha=0.3,delta_d=64,tile=256,threads=128,schedule=2,seed_lists=3,"
                                        "flags=12",
                     help="operating point of --profile (comma-separated key=value)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the request-server latency sweep")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="duration of each arrival rate")
     ap.add_argument("--tail-from", type=int, default=32,
                     help="first dim of the index's row-major tail copy (0: none); survivors gather from it")
     ap.add_argument("--lead", default="bf16", choices=["none", "bf16", "fp8"],
@@ -122,6 +124,50 @@ def run_profile(args):
 
 
 # ----------------------------------------------------------------- helpers --
+def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7):
+    """Requests of one query each, Poisson arrivals at each rate (requests/s),
+    K and nprobe drawn per request from {1, 10, 100} x {16, 64, 128}; the
+    server batches compatible requests and overlaps batches on 4 streams.
+    Returns per rate: offered and served request rates, p50 / p99 latency
+    (submit to results on the host, measured by the server)."""
+    n_lists = ix.info.n_clusters
+    nprobes = [p for p in (16, 64, 128) if p <= n_lists]
+    srv = dade.Server(ix, slots=4, max_batch=1024, max_k=100, max_nprobe=max(nprobes), tile=point["tile"],
+                      threads=point["threads"], schedule=point.get("schedule", 0),
+                      seed_lists=point.get("seed_lists", 0), flags=point["flags"])
+    rng = np.random.default_rng(seed)
+    out = []
+    for rate in rates:
+        n = max(50, int(rate * seconds))
+        gaps = rng.exponential(1.0 / rate, n)
+        ks = rng.choice([1, 10, 100], n)
+        nps = rng.choice(nprobes, n)
+        picks = rng.integers(0, queries.shape[0], n)
+        tickets = []
+        t_start = time.perf_counter()
+        due = t_start
+        for i in range(n):
+            due += gaps[i]
+            while time.perf_counter() < due:
+                pass
+            tickets.append(srv.submit(queries[picks[i]:picks[i] + 1], int(ks[i]), int(nps[i]),
+                                      point.get("alpha", 0.1), point.get("delta_d", 32)))
+        t_sub = time.perf_counter() - t_start
+        lats = [srv.result(t)[2] for t in tickets]
+        t_all = time.perf_counter() - t_start
+        out.append({"offered_rps": rate, "requests": n, "served_rps": round(n / t_all, 1),
+                    "submit_rps": round(n / t_sub, 1),
+                    "p50_ms": round(1e3 * float(np.percentile(lats, 50)), 3),
+                    "p99_ms": round(1e3 * float(np.percentile(lats, 99)), 3)})
+        if out[-1]["p99_ms"] > 200:   # saturated: stop the sweep
+            break
+    st = srv.stats()
+    srv.close()
+    return {"requests": "1 query each, K in {1, 10, 100}, nprobe in " + str(nprobes) + ", Poisson arrivals",
+            "slots": st["slots"], "batches": st["batches"], "mean_batch": round(st["queries"] / max(1, st["batches"]), 2),
+            "max_inflight": st["max_inflight"], "rates": out}
+
+
 def tail_opt(args, d):
     """tail_from of the index (0 when D is too small for it)."""
     return args.tail_from if 0 < args.tail_from < (d + 15) // 16 * 16 else 0
@@ -379,7 +425,7 @@ def run_ours(args):
     tried = []
     lead_flags = (0, dade.FLAG_LEAD) if lf else (0,)
     variants = [(dade.SCHED_TILE, 8, tile, 128, fl, 0) for tile in (128, 192, 256) for fl in lead_flags]
-    variants += [(dade.SCHED_SEEDED, 8, 256, 128, 0, seed) for seed in (2, 3, 4)]
+    variants += [(dade.SCHED_SEEDED, 8, tile, 128, 0, seed) for seed in (2, 3, 4) for tile in (64, 128, 256)]
     for dd in (16, 32, 64):
         for alpha in (0.05, 0.1, 0.2, 0.3):
             for schedule, spec, tile, threads, fl, seed in variants:
@@ -520,6 +566,14 @@ def run_ours(args):
         log(f"[bench] graph step failed: {e}")
         graph_same = None
 
+    # ---- serving: continuous batching of single-query requests, mixed K and nprobe ------
+    serving = None
+    if not args.no_serving:
+        try:
+            serving = serve_sweep(dade, ix, queries, point, (2000, 10000, 30000), args.serve_seconds)
+        except Exception as e:  # noqa: BLE001 - reported, not fatal
+            log(f"[bench] serving sweep failed: {e}")
+
     # ---- end to end through the C ABI with host buffers -------------------------------
     q_host = torch.from_numpy(queries).pin_memory()
     ids_host = torch.empty(nq, K, dtype=torch.int64).pin_memory()
@@ -570,6 +624,7 @@ def run_ours(args):
                              "scan": round(statistics.mean(scan_ms), 4)},
             "latency_ms": {"p50": round(float(np.percentile(step_ms, 50)), 4),
                            "p99": round(float(np.percentile(step_ms, 99)), 4), "per": "batch step"},
+            "serving": serving,
             "fd_baseline": {"value": round(fd_qps, 1), "unit": UNIT, "recall": round(fd_recall, 5),
                             "nprobe": fd_pt["nprobe"], "threads": fd_pt["threads"],
                             "schedule": {0: "tile", 2: "seeded"}[fd_pt.get("schedule", 0)],
