@@ -73,7 +73,7 @@ struct DevBuf {
 // An index owns one; a server slot owns its own so that calls on different
 // streams never share scratch memory.
 struct Workspace {
-    DevBuf dist, probe, qrot, qin, ids, dists, order, ordcnt, aimg, anorm;
+    DevBuf dist, probe, qrot, qin, ids, dists, order, ordcnt, aimg, anorm, selflag;
     DevBuf lm_cnt, lm_items, lm_acc, lm_acnt;   // seeded schedule (lm.cu)
 };
 

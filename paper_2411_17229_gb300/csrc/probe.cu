@@ -5,9 +5,11 @@
 // ||q||^2 + ||c||^2 - 2 <q, c> with the tensor-core GEMM of tc_gemm.cu
 // (3xTF32, FP32-accurate).
 // Step 2 selects, per query, the nprobe smallest 64-bit keys
-// (float bits of the distance << 32 | list id) by an 8-pass radix select over
-// 8-bit digits; keys are unique, so exactly nprobe keys are <= the selected
-// one, and a final rank sort orders them.  The result is deterministic.
+// (float bits of the distance << 32 | list id): a value-histogram threshold
+// and a rank sort of the keys below it (k_probe_hist), and, for the rows where
+// ties overflow that pass, an 8-pass radix select over 8-bit digits (keys are
+// unique, so exactly nprobe keys are <= the selected one).  Both give the
+// same, deterministic order.
 #include <mutex>
 #include <string>
 
@@ -35,7 +37,8 @@ __device__ __forceinline__ unsigned long long probe_key(const float *row, int j)
 }
 
 __global__ void __launch_bounds__(SEL_THREADS) k_probe_select(const float *__restrict__ dist, int nc, int nprobe,
-                                                              int32_t *__restrict__ out) {
+                                                              int32_t *__restrict__ out, const int *__restrict__ only) {
+    if (only && !only[blockIdx.x]) return;   // row already selected by k_probe_hist
     extern __shared__ unsigned long long sel[];        // [nprobe]
     __shared__ unsigned hist[256];
     __shared__ unsigned long long s_prefix;
@@ -113,6 +116,86 @@ __global__ void __launch_bounds__(SEL_THREADS) k_probe_select(const float *__res
     }
 }
 
+// Selection by value histogram: the row's distances are binned uniformly
+// between their minimum and maximum (a monotone map, so every distance below
+// the nprobe-th smallest falls in a bin at or below that one's), the bin
+// where the cumulative count reaches nprobe gives a threshold, and the keys at
+// or below it (typically nprobe plus part of one bin) are collected and
+// rank-sorted by (distance, id).  Three passes over the row, few barriers.  A
+// row whose threshold bin holds more than HCAP keys (massive ties) sets
+// *overflow for the radix path.
+constexpr int HBINS = 1024, HCAP = 1024;
+
+__global__ void __launch_bounds__(SEL_THREADS) k_probe_hist(const float *__restrict__ dist, int nc, int nprobe,
+                                                            int32_t *__restrict__ out, int *__restrict__ overflow) {
+    if (threadIdx.x == 0) overflow[blockIdx.x] = 0;
+    __shared__ unsigned hist[HBINS];
+    __shared__ unsigned long long cand[HCAP];
+    __shared__ float s_min[SEL_THREADS / 32], s_max[SEL_THREADS / 32];
+    __shared__ int s_bin, s_cnt;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float *row = dist + (int64_t)blockIdx.x * nc;
+    float lo = INFINITY, hi = -INFINITY;
+    for (int j = tid; j < nc; j += SEL_THREADS) {
+        const float v = row[j];
+        lo = fminf(lo, v);
+        hi = fmaxf(hi, v);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    }
+    if (lane == 0) { s_min[warp] = lo; s_max[warp] = hi; }
+    for (int b = tid; b < HBINS; b += SEL_THREADS) hist[b] = 0;
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    lo = s_min[0];
+    hi = s_max[0];
+    for (int w = 1; w < SEL_THREADS / 32; ++w) { lo = fminf(lo, s_min[w]); hi = fmaxf(hi, s_max[w]); }
+    const float scale = hi > lo ? (float)(HBINS - 1) / (hi - lo) : 0.f;
+    auto bin_of = [&](float v) { return min(HBINS - 1, (int)((v - lo) * scale)); };
+    for (int j = tid; j < nc; j += SEL_THREADS) atomicAdd(&hist[bin_of(row[j])], 1u);
+    __syncthreads();
+    if (warp == 0) {   // the bin where the cumulative count reaches nprobe
+        const int per = HBINS / 32;
+        unsigned loc = 0;
+        for (int t = 0; t < per; ++t) loc += hist[lane * per + t];
+        unsigned inc = loc;
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += v;
+        }
+        const unsigned before = inc - loc;
+        if (before < (unsigned)nprobe && inc >= (unsigned)nprobe) {
+            unsigned c = before;
+            int t = 0;
+            while (c + hist[lane * per + t] < (unsigned)nprobe) { c += hist[lane * per + t]; ++t; }
+            s_bin = lane * per + t;
+        }
+    }
+    __syncthreads();
+    const int bstar = s_bin;
+    for (int j = tid; j < nc; j += SEL_THREADS) {
+        const float v = row[j];
+        if (bin_of(v) <= bstar) {
+            const int slot = atomicAdd(&s_cnt, 1);
+            if (slot < HCAP) cand[slot] = ((unsigned long long)__float_as_uint(v) << 32) | (unsigned)j;
+        }
+    }
+    __syncthreads();
+    const int n = s_cnt;
+    if (n > HCAP) {
+        if (tid == 0) overflow[blockIdx.x] = 1;
+        return;
+    }
+    for (int t = tid; t < n; t += SEL_THREADS) {
+        const unsigned long long k = cand[t];
+        int r = 0;
+        for (int u = 0; u < n; ++u) r += cand[u] < k;
+        if (r < nprobe) out[(int64_t)blockIdx.x * nprobe + r] = (int32_t)(k & 0xffffffffu);
+    }
+}
+
 } // namespace
 
 dade_status centroid_norms(dade_index *ix, cudaStream_t s) {
@@ -127,10 +210,18 @@ dade_status probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t 
     if (nq == 0) return DADE_OK;
     DADE_TRY(ws(ix).dist.ensure(sizeof(float) * (size_t)nq * ix->nc));
     DADE_TRY(probe_distances(ix, q_rot, nq, q_stride, ws(ix).dist.as<float>(), s));
+    int *flags = nullptr;
+    if (nprobe <= HCAP) {
+        DADE_TRY(ws(ix).selflag.ensure(sizeof(int) * (size_t)nq));
+        flags = ws(ix).selflag.as<int>();
+        k_probe_hist<<<(unsigned)nq, SEL_THREADS, 0, s>>>(ws(ix).dist.as<float>(), ix->nc, nprobe, probe_out, flags);
+        DADE_TRY(launch_check("k_probe_hist"));
+    }
+    // radix select for the rows the histogram pass could not settle (or all rows)
     size_t smem = sizeof(unsigned long long) * (size_t)nprobe;
     if (smem > 48 * 1024)
         DADE_TRY_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_probe_select<<<(unsigned)nq, SEL_THREADS, smem, s>>>(ws(ix).dist.as<float>(), ix->nc, nprobe, probe_out);
+    k_probe_select<<<(unsigned)nq, SEL_THREADS, smem, s>>>(ws(ix).dist.as<float>(), ix->nc, nprobe, probe_out, flags);
     return launch_check("k_probe_select");
 }
 
@@ -219,6 +310,6 @@ extern "C" dade_status dade_probe_noalloc(const dade_index *ix, const float *q_r
     size_t smem = sizeof(unsigned long long) * (size_t)nprobe;
     if (smem > 48 * 1024)
         DADE_TRY_CUDA(cudaFuncSetAttribute(k_probe_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_probe_select<<<(unsigned)nq, SEL_THREADS, smem, s>>>(dist, ix->nc, nprobe, probe);
+    k_probe_select<<<(unsigned)nq, SEL_THREADS, smem, s>>>(dist, ix->nc, nprobe, probe, nullptr);
     return launch_check("k_probe_select");
 }
