@@ -156,7 +156,9 @@ typedef struct {
 /* Search options; NULL means all defaults. */
 typedef struct {
     int32_t mode;              /* dade_mode (default DADE_MODE_DADE) */
-    int32_t tile;              /* candidates per threshold refresh (default 128; 32..256, multiple of 32) */
+    int32_t tile;              /* candidates per threshold refresh (default 128; 32..256, multiple of 32;
+                                  DADE_SCHED_SEEDED also takes any tile >= the longest list: every seed
+                                  list is then one epoch and runs list-major too) */
     int64_t *stats;            /* device, optional [nq * 4]: per query candidates scanned, sum of
                                   dimensions used, candidates accepted by the DCO, candidates pruned */
     int32_t spec;              /* tile schedule: 16-dim blocks of a candidate that survived the first

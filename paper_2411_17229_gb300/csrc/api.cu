@@ -121,7 +121,10 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
                        "delta_d must be a multiple of 16 in [16, 1024]");
     }
     const int tile = opts && opts->tile ? opts->tile : 128;
-    DADE_CHECK_ARG(tile >= 32 && tile <= 256 && tile % 32 == 0, "tile must be a multiple of 32 in [32, 256]");
+    // the seeded schedule also takes a tile that holds every list (one epoch per list)
+    const bool whole_lists = opts && opts->schedule == DADE_SCHED_SEEDED && tile >= ix->max_list;
+    DADE_CHECK_ARG((tile >= 32 && tile <= 256 && tile % 32 == 0) || (whole_lists && tile >= 32),
+                   "tile must be a multiple of 32 in [32, 256] (seeded schedule: or at least the longest list)");
     DADE_CHECK_ARG(!opts || (opts->spec >= 0 && opts->spec <= 8), "spec outside 0..8");
     DADE_CHECK_ARG(!opts || opts->threads == 0 || opts->threads == 128 || opts->threads == 256,
                    "threads must be 0 (default), 128 or 256");

@@ -262,11 +262,13 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
 }
 
 // ---- work list -------------------------------------------------------------------
-__global__ void k_lm_count(const int32_t *__restrict__ probe, int64_t nq, int nprobe, int seed, int *__restrict__ cnt) {
-    const int64_t total = nq * (int64_t)(nprobe - seed);
+// (query, list) pairs of probe positions [c0, c1) (probe rows of nprobe).
+__global__ void k_lm_count(const int32_t *__restrict__ probe, int64_t nq, int nprobe, int c0, int c1,
+                           int *__restrict__ cnt) {
+    const int64_t total = nq * (int64_t)(c1 - c0);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = e / (nprobe - seed);
-        const int j = seed + (int)(e % (nprobe - seed));
+        const int64_t q = e / (c1 - c0);
+        const int j = c0 + (int)(e % (c1 - c0));
         atomicAdd(&cnt[probe[q * nprobe + j]], 1);
     }
 }
@@ -280,13 +282,21 @@ __global__ void k_lm_items(const int *__restrict__ cnt, int nc, int *__restrict_
     }
 }
 
-__global__ void k_lm_scatter(const int32_t *__restrict__ probe, int64_t nq, int nprobe, int seed, int *__restrict__ fill,
-                             int32_t *__restrict__ lq_items) {
-    const int64_t total = nq * (int64_t)(nprobe - seed);
+__global__ void k_lm_scatter(const int32_t *__restrict__ probe, int64_t nq, int nprobe, int c0, int c1,
+                             int *__restrict__ fill, int32_t *__restrict__ lq_items) {
+    const int64_t total = nq * (int64_t)(c1 - c0);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = e / (nprobe - seed);
-        const int j = seed + (int)(e % (nprobe - seed));
+        const int64_t q = e / (c1 - c0);
+        const int j = c0 + (int)(e % (c1 - c0));
         lq_items[atomicAdd(&fill[probe[q * nprobe + j]], 1)] = (int32_t)q;
+    }
+}
+
+// An empty K-nearest state: ids -1, distances +inf (the threshold of a first round).
+__global__ void k_lm_reset(int64_t *__restrict__ ids, float *__restrict__ dists, int64_t n) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        ids[e] = -1;
+        dists[e] = INFINITY;
     }
 }
 
@@ -420,47 +430,36 @@ dade_status launch_lm_gb(const LmArgs &a, int gb, cudaStream_t s) {
 
 } // namespace
 
-// The seeded schedule for queries [0, nq) of p (see the file comment).
-dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s) {
-    if (nq == 0) return DADE_OK;
-    const int S = p.seed_lists;
-    const int np = p.nprobe;
-    const bool fd = p.mode == DADE_MODE_FD;
-    const int gb = fd ? LNB : std::min(p.delta_d / 16, ix->nb);
-    if (ix->nb != LNB || (gb != 1 && gb != 2 && gb != 4 && gb != 8)) {
-        set_error("the seeded schedule needs D in 113..128 and delta_d in {16, 32, 64, >= 128}");
-        return DADE_EUNSUPPORTED;
-    }
-    // phase 1: the first S lists, tile schedule, straight into the outputs
-    ScanParams p1 = p;
-    p1.nprobe = S;
-    p1.pstride = np;
-    p1.schedule = DADE_SCHED_TILE;
-    DADE_TRY(scan(ix, nq, p1, s));
-    // work list: (query, list) pairs of positions >= S grouped by list
-    const int nc = ix->nc;
-    const int64_t pairs = nq * (int64_t)(np - S);
-    DADE_TRY(ws(ix).lm_cnt.ensure(sizeof(int) * (size_t)(nc + 1) * 4));
-    int *cnt = ws(ix).lm_cnt.as<int>(), *off = cnt + (nc + 1), *items = off + (nc + 1), *fill = items + (nc + 1);
-    DADE_TRY(ws(ix).lm_items.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(pairs, 1) + 16));
-    int32_t *lq_items = ws(ix).lm_items.as<int32_t>();
+// One list-major round: the lists at probe positions [c0, c1) of every query,
+// each candidate tested against the query's r^2 = dists[q][k - 1] as it is
+// when the round starts (frozen for the round), then the K nearest of the
+// previous result and the round's accepted candidates.  gb = 8 with no
+// pruning (coef +inf) is FDScanning.
+dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int c0, int c1, int gb, bool prune,
+                     cudaStream_t s) {
+    const int nc = ix->nc, np = p.nprobe;
+    const int64_t pairs = nq * (int64_t)(c1 - c0);
+    Workspace &w = ws(ix);
+    DADE_TRY(w.lm_cnt.ensure(sizeof(int) * (size_t)(nc + 1) * 4));
+    int *cnt = w.lm_cnt.as<int>(), *off = cnt + (nc + 1), *items = off + (nc + 1), *fill = items + (nc + 1);
+    DADE_TRY(w.lm_items.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(pairs, 1) + 16));
+    int32_t *lq_items = w.lm_items.as<int32_t>();
     unsigned *ctr = reinterpret_cast<unsigned *>(lq_items + std::max<int64_t>(pairs, 1));
-    const int64_t cap = (int64_t)(np - S) * std::max(ix->max_list, 1);
-    DADE_TRY(ws(ix).lm_acc.ensure(sizeof(unsigned long long) * (size_t)(nq * cap)));
-    DADE_TRY(ws(ix).lm_acnt.ensure(sizeof(int) * (size_t)nq));
+    const int64_t cap = (int64_t)(c1 - c0) * std::max(ix->max_list, 1);
+    DADE_TRY(w.lm_acc.ensure(sizeof(unsigned long long) * (size_t)(nq * cap)));
+    DADE_TRY(w.lm_acnt.ensure(sizeof(int) * (size_t)nq));
     DADE_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(nc + 1), s));
-    DADE_TRY_CUDA(cudaMemsetAsync(ws(ix).lm_acnt.p, 0, sizeof(int) * (size_t)nq, s));
+    DADE_TRY_CUDA(cudaMemsetAsync(w.lm_acnt.p, 0, sizeof(int) * (size_t)nq, s));
     DADE_TRY_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned), s));
-    k_lm_count<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, S, cnt);
+    k_lm_count<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, cnt);
     DADE_TRY(launch_check("k_lm_count"));
     k_lm_items<<<grid_of(nc + 1, 256), 256, 0, s>>>(cnt, nc, off, items);
     DADE_TRY(launch_check("k_lm_items"));
     DADE_TRY(exclusive_scan_int(off, nc + 1, s));
     DADE_TRY(exclusive_scan_int(items, nc + 1, s));
     DADE_TRY_CUDA(cudaMemcpyAsync(fill, off, sizeof(int) * (size_t)(nc + 1), cudaMemcpyDeviceToDevice, s));
-    k_lm_scatter<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, S, fill, lq_items);
+    k_lm_scatter<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, fill, lq_items);
     DADE_TRY(launch_check("k_lm_scatter"));
-    // phase 2: list-major, persistent
     LmArgs a{};
     a.data = ix->data.as<float>();
     a.ids = ix->ids.as<int32_t>();
@@ -471,8 +470,8 @@ dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, c
     a.item_off = items;
     a.ctr = ctr;
     a.r2src = p.dists;
-    a.acc = ws(ix).lm_acc.as<unsigned long long>();
-    a.acnt = ws(ix).lm_acnt.as<int>();
+    a.acc = w.lm_acc.as<unsigned long long>();
+    a.acnt = w.lm_acnt.as<int>();
     a.stats = p.stats;
     a.err = ix->errflag.as<int>();
     a.cap = cap;
@@ -486,11 +485,42 @@ dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, c
         a.tail_w = ix->tail_w;
     }
     const int n_inc = (LNB + gb - 1) / gb;
-    for (int j = 0; j < LNB; ++j) a.coef[j] = (!fd && j < n_inc - 1) ? p.coef[j] : INFINITY;
+    for (int j = 0; j < LNB; ++j) a.coef[j] = (prune && j < n_inc - 1) ? p.coef[j] : INFINITY;
     DADE_TRY(p.stats ? launch_lm_gb<true>(a, gb, s) : launch_lm_gb<false>(a, gb, s));
-    // final merge
     k_lm_merge<<<(unsigned)nq, MT, 0, s>>>(p.ids, p.dists, p.k, a.acc, a.acnt, cap);
     return launch_check("k_lm_merge");
+}
+
+// The seeded schedule for queries [0, nq) of p (see the file comment).  When
+// the tile holds every list (tile >= longest list), each of the first S lists
+// is one threshold epoch: list j of every query is tested against r after
+// lists 0..j-1.  Those lists then run list-major too, as S rounds: round 0
+// with r = +inf (every candidate exact, so FDScanning), round j against r
+// after round j - 1.  Otherwise the first S lists run in the tile schedule.
+dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s) {
+    if (nq == 0) return DADE_OK;
+    const int S = p.seed_lists;
+    const int np = p.nprobe;
+    const bool fd = p.mode == DADE_MODE_FD;
+    const int gb = fd ? LNB : std::min(p.delta_d / 16, ix->nb);
+    if (ix->nb != LNB || (gb != 1 && gb != 2 && gb != 4 && gb != 8)) {
+        set_error("the seeded schedule needs D in 113..128 and delta_d in {16, 32, 64, >= 128}");
+        return DADE_EUNSUPPORTED;
+    }
+    if (p.tile >= ix->max_list) {
+        k_lm_reset<<<grid_of(nq * (int64_t)p.k, 256), 256, 0, s>>>(p.ids, p.dists, nq * (int64_t)p.k);
+        DADE_TRY(launch_check("k_lm_reset"));
+        if (p.stats) DADE_TRY_CUDA(cudaMemsetAsync(p.stats, 0, sizeof(int64_t) * 4 * (size_t)nq, s));
+        DADE_TRY(lm_round(ix, nq, p, 0, 1, LNB, false, s));   // r = +inf: exact
+        for (int j = 1; j < S; ++j) DADE_TRY(lm_round(ix, nq, p, j, j + 1, gb, !fd, s));
+    } else {
+        ScanParams p1 = p;   // the first S lists, tile schedule, straight into the outputs
+        p1.nprobe = S;
+        p1.pstride = np;
+        p1.schedule = DADE_SCHED_TILE;
+        DADE_TRY(scan(ix, nq, p1, s));
+    }
+    return lm_round(ix, nq, p, S, np, gb, !fd, s);
 }
 
 } // namespace dade

@@ -307,6 +307,9 @@ def test_row_tail_gives_same_results(tail_from, delta_d, flags):
     (1, 4, 0.2, 32, 32, 3),
     (256, 8, 0.1, 64, 128, 1),       # phase 1 finds fewer than K: r frozen at +inf
     (20, 12, 0.1, 128, 128, 2),      # one increment
+    (10, 8, 0.1, 32, 4096, 3),       # whole-list epochs: the seed lists run list-major as rounds
+    (100, 16, 0.3, 64, 4096, 1),
+    (1, 6, 0.2, 16, 4096, 5),
 ])
 @pytest.mark.parametrize("flags", [0, dade.FLAG_QUERY_ORDER])
 def test_seeded_schedule_parity(c1, k, nprobe, alpha, delta_d, tile, seed, flags):
@@ -320,11 +323,12 @@ def test_seeded_schedule_parity(c1, k, nprobe, alpha, delta_d, tile, seed, flags
 
 
 @pytest.mark.parametrize("k,nprobe", [(10, 8), (100, 16)])
-def test_seeded_fd_is_fd(c1, k, nprobe):
+@pytest.mark.parametrize("tile", [128, 4096])
+def test_seeded_fd_is_fd(c1, k, nprobe, tile):
     """FDScanning under the seeded schedule is exact IVF: the same results as
     the tile schedule, whatever the seed."""
     a = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD)
-    b = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD, schedule=dade.SCHED_SEEDED, seed_lists=1)
+    b = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD, schedule=dade.SCHED_SEEDED, seed_lists=1, tile=tile)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
 
 
@@ -334,9 +338,10 @@ def test_seeded_schedule_mixture_and_limits():
     w = synth.Workload("mix128_test", 16000, 128, 90, 1.0, 24, 0.0, 3.0, 1.0, False, False, 24, (4,), 10, (16,), 0.1)
     base, queries, labels = synth.make(w)
     case = Case(base, queries, labels, 24, n_pairs=8000)
-    for k, nprobe, seed, dd in ((10, 6, 1, 32), (50, 8, 2, 16), (30, 12, 3, 64)):
-        g_ids, g_d = case.gpu_search(k, nprobe, 0.1, dd, schedule=dade.SCHED_SEEDED, seed_lists=seed)
-        o_ids, o_d, _, oflags = case.oracle_search(k, nprobe, 0.1, dd, seed=seed)
+    for k, nprobe, seed, dd, tile in ((10, 6, 1, 32, 128), (50, 8, 2, 16, 128), (30, 12, 3, 64, 128),
+                                      (30, 12, 3, 64, 1 << 20)):
+        g_ids, g_d = case.gpu_search(k, nprobe, 0.1, dd, schedule=dade.SCHED_SEEDED, seed_lists=seed, tile=tile)
+        o_ids, o_d, _, oflags = case.oracle_search(k, nprobe, 0.1, dd, seed=seed, tile=tile)
         parity.compare(g_ids, g_d, o_ids, o_d, oflags, case.scale, case.exact_d)
     # seed >= nprobe is the tile schedule
     a = case.gpu_search(10, 4, 0.1, 32, stats=True)
