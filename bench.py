@@ -411,10 +411,12 @@ def run_ours(args):
     grid = [8, 12, 16, 20, 24, 28, 32, 40, 48, 64, 96, 128]
     fd_best, fd_rec = None, {}
     for nprobe in grid:              # FD time grows with nprobe: the first point reaching the target wins
-        for threads, tile, sched, seed in ((128, 64, 0, 0), (128, 128, 0, 0), (256, 128, 0, 0),
-                                           (256, 128, dade.SCHED_SEEDED, 1), (256, 128, dade.SCHED_SEEDED, 2),
-                                           (256, 128, dade.SCHED_SEEDED, 3), (256, 1 << 20, dade.SCHED_SEEDED, 1),
-                                           (256, 1 << 20, dade.SCHED_SEEDED, 2)):
+        fd_variants = [(128, 64, 0, 0), (128, 128, 0, 0), (256, 128, 0, 0)]
+        if (w.d + 15) // 16 == 8:
+            fd_variants += [(256, 128, dade.SCHED_SEEDED, 1), (256, 128, dade.SCHED_SEEDED, 2),
+                            (256, 128, dade.SCHED_SEEDED, 3), (256, 1 << 20, dade.SCHED_SEEDED, 1),
+                            (256, 1 << 20, dade.SCHED_SEEDED, 2)]
+        for threads, tile, sched, seed in fd_variants:
             pt = {"mode": dade.MODE_FD, "nprobe": nprobe, "tile": tile, "threads": threads,
                   "flags": dade.FLAG_QUERY_ORDER, "schedule": sched, "seed_lists": seed}
             ms, rc = measure(pt)
@@ -428,8 +430,10 @@ def run_ours(args):
     tried = []
     lead_flags = (0, dade.FLAG_LEAD) if lf else (0,)
     variants = [(dade.SCHED_TILE, 8, tile, 128, fl, 0) for tile in (128, 192, 256) for fl in lead_flags]
-    variants += [(dade.SCHED_SEEDED, 8, tile, 128, 0, seed) for seed in (2, 3, 4)
-                 for tile in (64, 128, 256, 1 << 20)]   # 1 << 20: whole lists, seed lists list-major too
+    list_major = (w.d + 15) // 16 == 8   # the list-major kernels cover D in 113..128
+    if list_major:
+        variants += [(dade.SCHED_SEEDED, 8, tile, 128, 0, seed) for seed in (2, 3, 4)
+                     for tile in (64, 128, 256, 1 << 20)]   # 1 << 20: whole lists, seed lists list-major too
     for dd in (16, 32, 64):
         for alpha in (0.05, 0.1, 0.2, 0.3):
             for schedule, spec, tile, threads, fl, seed in variants:

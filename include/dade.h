@@ -136,6 +136,32 @@ typedef enum {
     DADE_LEAD_FP8 = 2          /* FP8 e4m3 with one FP32 scale per (list, 16-dim block) */
 } dade_lead_format;
 
+/*
+ * The orthogonal transformation of an index.  DADE's is the PCA basis with
+ * descending eigenvalues (Section 3.2).  The comparator ADSampling (Gao et
+ * al., the paper's baseline) uses a random orthogonal transformation instead:
+ * DADE_TRANSFORM_RANDOM draws a Haar-distributed one from `seed`
+ * (Gram-Schmidt of SplitMix64 Gaussians), DADE_TRANSFORM_GIVEN takes `basis`.
+ * lambda_k is then the data's variance along w_k (in the given order).
+ */
+typedef enum {
+    DADE_TRANSFORM_PCA = 0,
+    DADE_TRANSFORM_RANDOM = 1,
+    DADE_TRANSFORM_GIVEN = 2
+} dade_transform;
+
+/*
+ * Distance estimator and test of a search.  DADE: dis'^2 = Lambda_D/Lambda_d
+ * P_d (Eq. 13), prune iff dis' > (1 + eps_d) r with eps_d from the sampled
+ * pairs at significance alpha (Eq. 14).  ADSampling: dis'^2 = (D/d) P_d,
+ * prune iff dis' > (1 + eps0 / sqrt(d)) r, eps0 = opts->eps0 (data-oblivious;
+ * meant for an index with a random transformation).  FDScanning: opts->mode.
+ */
+typedef enum {
+    DADE_ESTIMATOR_DADE = 0,
+    DADE_ESTIMATOR_ADSAMPLING = 1
+} dade_estimator;
+
 /* Index construction options.  Zero-initialise, then call dade_build_opts_default(). */
 typedef struct {
     int32_t n_clusters;        /* N_c, number of inverted lists (>= 1) */
@@ -150,7 +176,10 @@ typedef struct {
     int32_t lead_dims;         /* leading dims in that copy (multiple of 16, <= D; 0 = none) */
     int32_t tail_from;         /* keep a row-major FP32 copy of dims [tail_from, D) of every vector
                                   (multiple of 16, < D; 0 = none), see DADE_FLAG_ROW_TAIL */
-    int32_t reserved[5];
+    int32_t transform;         /* dade_transform (default DADE_TRANSFORM_PCA) */
+    const double *basis;       /* host, optional [d * d] orthonormal columns (W[j*d + k] = component j of
+                                  w_k) for DADE_TRANSFORM_GIVEN */
+    int32_t reserved[2];
 } dade_build_opts;
 
 /* Search options; NULL means all defaults. */
@@ -170,6 +199,8 @@ typedef struct {
                                   (needs DADE_FLAG_LEAD) */
     int32_t seed_lists;        /* DADE_SCHED_SEEDED: lists scanned before r is frozen (0: 2; >= nprobe:
                                   the tile schedule) */
+    int32_t estimator;         /* dade_estimator (default DADE_ESTIMATOR_DADE) */
+    float eps0;                /* ADSampling's eps0 (> 0) */
     int32_t reserved[1];
 } dade_search_opts;
 

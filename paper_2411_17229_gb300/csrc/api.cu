@@ -57,13 +57,19 @@ dade_status DevBuf::ensure(size_t b) {
 dade_status build_index(const float *base, int64_t n, int32_t d, const dade_build_opts &o, dade_index *ix,
                         cudaStream_t s);
 
-int coef_table(const dade_index *ix, float alpha, int32_t delta_d, double *eps, float *coef) {
+int coef_table(const dade_index *ix, float alpha, int32_t delta_d, double *eps, float *coef, float eps0) {
     const int D = ix->d;
     const int gb = std::min(delta_d / 16, ix->nb);
     const int n_inc = (ix->nb + gb - 1) / gb;
     const double a = (double)alpha;   // alpha is an FP32 value; both sides of a comparison use it as such
     for (int j = 0; j + 1 < n_inc; ++j) {
         const int dd = (j + 1) * gb * 16;          // tested d < D
+        if (eps0 >= 0.f) {   // ADSampling: (D/d) P_d > (1 + eps0/sqrt(d))^2 r^2
+            const double e = (double)eps0 / std::sqrt((double)dd);
+            if (eps) eps[dd] = e;
+            coef[j] = (float)((1.0 + e) * (1.0 + e) * (double)dd / (double)D);
+            continue;
+        }
         double e = std::numeric_limits<double>::infinity();
         const int64_t m = ix->eps_kept;
         if (m > 0) {
@@ -115,8 +121,11 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
     DADE_CHECK_ARG(nprobe <= 8192, "nprobe > 8192");
     const int mode = opts ? opts->mode : DADE_MODE_DADE;
     DADE_CHECK_ARG(mode == DADE_MODE_DADE || mode == DADE_MODE_FD, "unknown mode");
+    const bool ads = opts && opts->estimator == DADE_ESTIMATOR_ADSAMPLING;
+    DADE_CHECK_ARG(!opts || opts->estimator == DADE_ESTIMATOR_DADE || ads, "unknown estimator");
+    DADE_CHECK_ARG(!ads || (opts->eps0 > 0.f && std::isfinite(opts->eps0)), "ADSampling needs eps0 > 0");
     if (mode == DADE_MODE_DADE) {
-        DADE_CHECK_ARG(alpha > 0.f && alpha < 1.f, "alpha outside (0, 1)");
+        DADE_CHECK_ARG(ads || (alpha > 0.f && alpha < 1.f), "alpha outside (0, 1)");
         DADE_CHECK_ARG(delta_d >= 16 && delta_d <= DADE_MAX_DIM && delta_d % 16 == 0,
                        "delta_d must be a multiple of 16 in [16, 1024]");
     }
@@ -198,7 +207,8 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.use_tail = opts ? (opts->flags & DADE_FLAG_ROW_TAIL) != 0 : 0;
     p.lead_stats = opts ? opts->lead_stats : nullptr;
     p.delta_d = delta_d;
-    if (p.mode == DADE_MODE_DADE) p.n_inc = coef_table(ix, alpha, delta_d, nullptr, p.coef);
+    const bool ads = opts && opts->estimator == DADE_ESTIMATOR_ADSAMPLING;
+    if (p.mode == DADE_MODE_DADE) p.n_inc = coef_table(ix, alpha, delta_d, nullptr, p.coef, ads ? opts->eps0 : -1.f);
     else p.n_inc = 0;
     p.ids = ids_d;
     p.dists = dists_d;
@@ -267,6 +277,9 @@ dade_status dade_build_index(const float *base, int64_t n, int32_t d, const dade
     else
         DADE_CHECK_ARG(opts->lead_dims >= 16 && opts->lead_dims % 16 == 0 && opts->lead_dims <= (d + 15) / 16 * 16,
                        "lead_dims must be a multiple of 16 in [16, D rounded up to 16]");
+    DADE_CHECK_ARG(opts->transform == DADE_TRANSFORM_PCA || opts->transform == DADE_TRANSFORM_RANDOM ||
+                       (opts->transform == DADE_TRANSFORM_GIVEN && opts->basis != nullptr),
+                   "unknown transform, or DADE_TRANSFORM_GIVEN without a basis");
     DADE_CHECK_ARG(opts->tail_from == 0 || (opts->tail_from >= 16 && opts->tail_from % 16 == 0 &&
                                             opts->tail_from < (d + 15) / 16 * 16),
                    "tail_from must be 0 or a multiple of 16 in [16, D rounded up to 16)");

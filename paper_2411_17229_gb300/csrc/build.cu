@@ -31,6 +31,12 @@ inline uint64_t draw(uint64_t key, uint64_t i) { return mix64(key + (i + 1) * 0x
 inline uint64_t uniform(uint64_t key, uint64_t i, uint64_t n) {   // in [0, n)
     return (uint64_t)(((unsigned __int128)draw(key, i) * n) >> 64);
 }
+// Standard normal draw i of stream `key` (Box-Muller on two 53-bit uniforms).
+inline double gaussian(uint64_t key, uint64_t i) {
+    const double u1 = ((double)(draw(key, 2 * i) >> 11) + 1.0) * 0x1.0p-53;   // (0, 1]
+    const double u2 = (double)(draw(key, 2 * i + 1) >> 11) * 0x1.0p-53;        // [0, 1)
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
 
 // ------------------------------------------------------------- kernels ------
 
@@ -383,10 +389,60 @@ dade_status build_index(const float *base, int64_t n, int32_t d, const dade_buil
                 if (j < i) C[(size_t)i * d + j] = C[(size_t)j * d + i];
             }
         for (auto &v : C) v /= (double)n;
-        // ---- eigendecomposition (host FP64), descending --------------------------
-        if (!sym_eig(d, C, ix->lam, ix->W)) {
-            set_error("eigendecomposition did not converge");
-            return DADE_ECUDA;
+        if (o.transform == DADE_TRANSFORM_PCA) {
+            // ---- eigendecomposition (host FP64), descending --------------------------
+            if (!sym_eig(d, C, ix->lam, ix->W)) {
+                set_error("eigendecomposition did not converge");
+                return DADE_ECUDA;
+            }
+        } else {
+            // ---- a given or random orthogonal basis; lambda_k = w_k^T C w_k --------------
+            ix->W.assign((size_t)d * d, 0.0);
+            if (o.transform == DADE_TRANSFORM_GIVEN) {
+                std::copy(o.basis, o.basis + (size_t)d * d, ix->W.begin());
+            } else {
+                uint64_t key = o.seed ^ 0x726f74617465ULL;
+                for (size_t e = 0; e < ix->W.size(); ++e) ix->W[e] = gaussian(key, e);
+            }
+            // Gram-Schmidt over the columns, twice (a given basis is only re-orthonormalised
+            // within rounding, a random one becomes Haar-distributed)
+            for (int pass = 0; pass < 2; ++pass)
+                for (int k = 0; k < d; ++k) {
+                    for (int j = 0; j < k; ++j) {
+                        double dot = 0.0;
+                        for (int i = 0; i < d; ++i) dot += ix->W[(size_t)i * d + j] * ix->W[(size_t)i * d + k];
+                        for (int i = 0; i < d; ++i) ix->W[(size_t)i * d + k] -= dot * ix->W[(size_t)i * d + j];
+                    }
+                    double nn = 0.0;
+                    for (int i = 0; i < d; ++i) nn += ix->W[(size_t)i * d + k] * ix->W[(size_t)i * d + k];
+                    if (!(nn > 0.0)) {
+                        set_error("invalid argument: the basis is singular");
+                        return DADE_EINVAL;
+                    }
+                    const double inv = 1.0 / std::sqrt(nn);
+                    for (int i = 0; i < d; ++i) ix->W[(size_t)i * d + k] *= inv;
+                }
+            if (o.transform == DADE_TRANSFORM_GIVEN) {   // the given columns must already be orthonormal
+                double worst = 0.0;
+                for (size_t e = 0; e < ix->W.size(); ++e) worst = std::max(worst, std::fabs(ix->W[e] - o.basis[e]));
+                if (worst > 1e-6) {
+                    set_error("invalid argument: the given basis is not orthonormal (columns differ by " +
+                              std::to_string(worst) + " after Gram-Schmidt)");
+                    return DADE_EINVAL;
+                }
+            }
+            ix->lam.assign(d, 0.0);
+            std::vector<double> cw(d);
+            for (int k = 0; k < d; ++k) {
+                for (int i = 0; i < d; ++i) {
+                    double t = 0.0;
+                    for (int j = 0; j < d; ++j) t += C[(size_t)i * d + j] * ix->W[(size_t)j * d + k];
+                    cw[i] = t;
+                }
+                double l = 0.0;
+                for (int i = 0; i < d; ++i) l += ix->W[(size_t)i * d + k] * cw[i];
+                ix->lam[k] = std::max(l, 0.0);
+            }
         }
     }
     ix->Lam.assign(d + 1, 0.0);

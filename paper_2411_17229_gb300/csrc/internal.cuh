@@ -176,7 +176,8 @@ dade_status load_index(const char *path, dade_index *ix);
 // Host FP64 symmetric eigensolver (descending eigenvalues, column eigenvectors).
 bool sym_eig(int n, std::vector<double> &a, std::vector<double> &w, std::vector<double> &v);
 
-// Pruning coefficients of one (alpha, delta_d); returns the number of increments.
-int coef_table(const dade_index *ix, float alpha, int32_t delta_d, double *eps, float *coef);
+// Pruning coefficients of one (alpha, delta_d) for the DADE estimator, or of
+// eps0 (>= 0 selects ADSampling); returns the number of increments.
+int coef_table(const dade_index *ix, float alpha, int32_t delta_d, double *eps, float *coef, float eps0 = -1.f);
 
 } // namespace dade

@@ -20,6 +20,8 @@ MODE_DADE, MODE_FD = 0, 1
 SCHED_TILE, SCHED_PIPELINED, SCHED_SEEDED = 0, 1, 2
 FLAG_GENERIC_KERNEL, FLAG_LEAD, FLAG_QUERY_ORDER, FLAG_ROW_TAIL = 1, 2, 4, 8
 LEAD_NONE, LEAD_BF16, LEAD_FP8 = 0, 1, 2
+TRANSFORM_PCA, TRANSFORM_RANDOM, TRANSFORM_GIVEN = 0, 1, 2
+ESTIMATOR_DADE, ESTIMATOR_ADSAMPLING = 0, 1
 PIPE_MAX = 8
 (FIELD_MEAN, FIELD_BASIS, FIELD_EIGVAL, FIELD_CENTROIDS, FIELD_ASSIGN, FIELD_ROTATED, FIELD_RHO, FIELD_KMEANS_OBJ,
  FIELD_LEAD_DEQ, FIELD_LEAD_ERR, FIELD_LEAD_SCALE) = range(11)
@@ -37,13 +39,15 @@ class BuildOpts(C.Structure):
     _fields_ = [("n_clusters", C.c_int32), ("kmeans_iters", C.c_int32), ("seed", C.c_uint64),
                 ("eps_pairs", C.c_int64), ("assign", C.c_void_p), ("kmeans_init", C.c_void_p),
                 ("pairs", C.c_void_p), ("lead_format", C.c_int32), ("lead_dims", C.c_int32),
-                ("tail_from", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("tail_from", C.c_int32), ("transform", C.c_int32), ("basis", C.c_void_p),
+                ("reserved", C.c_int32 * 2)]
 
 
 class SearchOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tile", C.c_int32), ("stats", C.c_void_p), ("spec", C.c_int32),
                 ("threads", C.c_int32), ("schedule", C.c_int32), ("flags", C.c_int32),
-                ("lead_stats", C.c_void_p), ("seed_lists", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("lead_stats", C.c_void_p), ("seed_lists", C.c_int32), ("estimator", C.c_int32),
+                ("eps0", C.c_float), ("reserved", C.c_int32 * 1)]
 
 
 class ServerOpts(C.Structure):
@@ -146,12 +150,14 @@ class Index:
     """A libdade index resident in device memory."""
 
     def __init__(self, base, n_clusters: int, kmeans_iters: int = 10, seed: int = 0, eps_pairs: int = 100000,
-                 assign=None, kmeans_init=None, pairs=None, lead_format=LEAD_NONE, lead_dims=0, tail_from=0, stream=None):
+                 assign=None, kmeans_init=None, pairs=None, lead_format=LEAD_NONE, lead_dims=0, tail_from=0,
+                 transform=TRANSFORM_PCA, basis=None, stream=None):
         L = lib()
         o = BuildOpts()
         L.dade_build_opts_default(C.byref(o))
         o.n_clusters, o.kmeans_iters, o.seed, o.eps_pairs = int(n_clusters), int(kmeans_iters), int(seed), int(eps_pairs)
         o.lead_format, o.lead_dims, o.tail_from = int(lead_format), int(lead_dims), int(tail_from)
+        o.transform = int(transform)
         keep = []
         if assign is not None:
             a = np.ascontiguousarray(assign, np.int32)
@@ -161,6 +167,11 @@ class Index:
             a = np.ascontiguousarray(kmeans_init, np.int64)
             keep.append(a)
             o.kmeans_init = a.ctypes.data
+        if basis is not None:
+            a = np.ascontiguousarray(basis, np.float64)
+            keep.append(a)
+            o.basis = a.ctypes.data
+            o.transform = TRANSFORM_GIVEN
         if pairs is not None:
             a = np.ascontiguousarray(pairs, np.int64).reshape(-1)
             keep.append(a)
@@ -216,35 +227,42 @@ class Index:
         return out
 
     def search(self, q_rot, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-               threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, stream=None):
+               threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, estimator=ESTIMATOR_DADE,
+               eps0=0.0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
-                       flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists)
+                       flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists, estimator=estimator,
+                       eps0=eps0)
         _check(lib().dade_search(self._h, _ptr(q_rot), q_rot.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                  C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def scan(self, q_rot, probe, k, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-             threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, stream=None):
+             threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, estimator=ESTIMATOR_DADE,
+               eps0=0.0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
-                       flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists)
+                       flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists, estimator=estimator,
+                       eps0=eps0)
         _check(lib().dade_scan(self._h, _ptr(q_rot), _ptr(probe), q_rot.shape[0], int(k), probe.shape[1],
                                float(alpha), int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def query(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-              threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, stream=None):
+              threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, estimator=ESTIMATOR_DADE,
+               eps0=0.0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
-                       flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists)
+                       flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists, estimator=estimator,
+                       eps0=eps0)
         _check(lib().dade_query(self._h, _ptr(q), q.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                 C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def graph(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
-              threads=0, schedule=SCHED_TILE, flags=0, seed_lists=0):
+              threads=0, schedule=SCHED_TILE, flags=0, seed_lists=0, estimator=ESTIMATOR_DADE, eps0=0.0):
         """A query step captured into a CUDA graph (device buffers, bound to the graph)."""
         return Graph(self, q, k, nprobe, alpha, delta_d, ids, dists,
                      SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads,
-                                schedule=schedule, flags=flags, seed_lists=seed_lists))
+                                schedule=schedule, flags=flags, seed_lists=seed_lists, estimator=estimator,
+                                eps0=eps0))
 
     def reserve(self, max_nq, max_nprobe):
         _check(lib().dade_reserve(self._h, int(max_nq), int(max_nprobe)))

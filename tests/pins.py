@@ -364,6 +364,32 @@ def pin_search_lagged_tiles(o):
     assert lagged[2][:, 3].sum() <= a[2][:, 3].sum()
 
 
+def pin_adsampling_as_uniform_spectrum(o):
+    """ADSampling (the paper's baseline, Section 5) estimates sqrt(D/d) times
+    the partial distance and prunes iff that exceeds (1 + eps0/sqrt(d)) r.
+    With every lambda equal, Eq. 13's ratio Lambda_D/Lambda_d is D/d, so the
+    oracle runs ADSampling through the same DCO with eps_d = eps0/sqrt(d).
+    Worked case: D = 32, d = 16, eps0 = 2.1, q = 0, o with |o_:16|^2 = 9 and
+    |o_16:|^2 = 16 (dis = 5): dis'_16 = sqrt(2 * 9) = 4.243; the bound is
+    (1 + 2.1/4) r = 1.525 r, so r = 2.7 prunes (4.118 < 4.243) and r = 2.8
+    does not (4.270), and then dis = 5 > 2.8 rejects at d = 32."""
+    D = 32
+    ones = np.ones(D)
+    q = np.zeros(D)
+    x = np.zeros(D)
+    x[0] = 3.0
+    x[16] = 4.0
+    assert abs(o.estimate_sq(q, x, 16, ones) - 2.0 * 9.0) < 1e-12
+    eps = np.zeros(D + 1)
+    eps[16] = 2.1 / np.sqrt(16)
+    acc, d2, dims, _ = o.dco(q, x, 16, 2.7, ones, eps)
+    assert not acc and dims == 16
+    acc, d2, dims, _ = o.dco(q, x, 16, 2.8, ones, eps)
+    assert not acc and dims == 32
+    acc, d2, dims, _ = o.dco(q, x, 16, 5.0, ones, eps)
+    assert acc and dims == 32 and abs(d2 - 25.0) < 1e-12
+
+
 def pin_search_seeded_trace(o):
     """Seeded schedule, worked by hand (Section 3.3 test with eps_d = 0 and
     equal eigenvalues, so Lambda_32 / Lambda_16 = 2).  Query at the origin,
