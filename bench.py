@@ -67,6 +67,7 @@ def parse():
                                        "flags=12",
                     help="operating point of --profile (comma-separated key=value)")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server latency sweep")
+    ap.add_argument("--no-adsampling", action="store_true", help="skip the ADSampling comparator")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="duration of each arrival rate")
     ap.add_argument("--tail-from", type=int, default=32,
                     help="first dim of the index's row-major tail copy (0: none); survivors gather from it")
@@ -124,6 +125,82 @@ def run_profile(args):
 
 
 # ----------------------------------------------------------------- helpers --
+def run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, stream, sh, tf):
+    """The paper's DCO baseline on the same GPU path: its own index over a
+    random orthogonal basis (same lists by k-means), autotuned over eps0,
+    delta_d, schedule and nprobe for recall@K >= the target, then timed as a
+    step like the others."""
+    nq = q.shape[0]
+    t0 = time.time()
+    ix = dade.Index(xb, nc, kmeans_iters=w.kmeans_iters, seed=synth.SEED_KMEANS, transform=dade.TRANSFORM_RANDOM,
+                    tail_from=tf)
+    qr = torch.empty_like(q)
+    ix.rotate(q, qr, stream=sh)
+    ids = torch.empty(nq, K, dtype=torch.int64, device="cuda")
+    dists = torch.empty(nq, K, dtype=torch.float32, device="cuda")
+    probes = {}
+    fixed = dade.FLAG_QUERY_ORDER | (dade.FLAG_ROW_TAIL if tf else 0)
+    list_major = (w.d + 15) // 16 == 8
+
+    def scan(pt):
+        if pt["nprobe"] not in probes:
+            pr = torch.empty(nq, pt["nprobe"], dtype=torch.int32, device="cuda")
+            ix.probe(qr, pt["nprobe"], pr, stream=sh)
+            probes[pt["nprobe"]] = pr
+        ix.scan(qr, probes[pt["nprobe"]], K, 0.5, pt["delta_d"], ids, dists, tile=pt["tile"], threads=128,
+                schedule=pt["schedule"], seed_lists=pt["seed_lists"], flags=fixed,
+                estimator=dade.ESTIMATOR_ADSAMPLING, eps0=pt["eps0"], stream=sh)
+
+    best = None
+    scheds = [(0, 0, 256)] + ([(2, 2, 256), (2, 3, 256)] if list_major else [])
+    for eps0 in (0.5, 0.75, 1.0, 1.5, 2.1):
+        for dd in (16, 32, 64):
+            for sched, seed, tile in scheds:
+                for nprobe in [p for p in grid if p >= n0][:3]:
+                    pt = {"nprobe": nprobe, "eps0": eps0, "delta_d": dd, "schedule": sched, "seed_lists": seed,
+                          "tile": tile}
+                    scan(pt)
+                    torch.cuda.synchronize()
+                    rc = recall_at_k(torch, xb, q, ids, gt_kth, K)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(3):
+                        scan(pt)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / 3
+                    if rc >= RECALL_TARGET:
+                        if best is None or ms < best[0]:
+                            best = (ms, rc, pt)
+                        break
+    if best is None:
+        return {"value": None, "note": "no point reached the recall target"}
+    pt = best[2]
+    pr = torch.empty(nq, pt["nprobe"], dtype=torch.int32, device="cuda")
+    ms_steps = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix.rotate(q, qr, stream=sh)
+        ix.probe(qr, pt["nprobe"], pr, stream=sh)
+        probes[pt["nprobe"]] = pr
+        scan(pt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ms_steps.append(e0.elapsed_time(e1))
+    rc = recall_at_k(torch, xb, q, ids, gt_kth, K)
+    log(f"[bench] ADSampling {pt} {statistics.mean(ms_steps):.3f} ms/step recall {rc:.4f} "
+        f"(setup and autotune {time.time() - t0:.1f}s)")
+    ix.close()
+    return {"value": round(nq / (statistics.mean(ms_steps) / 1e3), 1), "unit": UNIT, "recall": round(rc, 5),
+            "ms_per_step": round(statistics.mean(ms_steps), 4), "eps0": pt["eps0"], "delta_d": pt["delta_d"],
+            "nprobe": pt["nprobe"], "schedule": {0: "tile", 2: "seeded"}[pt["schedule"]],
+            "seed_lists": pt["seed_lists"] or None,
+            "index": "random orthogonal basis (seeded), same k-means recipe"}
+
+
 def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7):
     """Requests of one query each, Poisson arrivals at each rate (requests/s),
     K and nprobe drawn per request from {1, 10, 100} x {16, 64, 128}; the
@@ -549,6 +626,15 @@ def run_ours(args):
     fd_qps = nq / (statistics.mean(fd_ms) / 1e3)
     fd_recall = recall_at_k(torch, xb, q, ids, gt_kth, K)
 
+    # ---- ADSampling comparator: random orthogonal basis, sqrt(D/d) estimate, eps0 test -----
+    ads = None
+    if not args.no_adsampling:
+        try:
+            ads = run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, stream, sh,
+                                 tail_opt(args, w.d))
+        except Exception as e:  # noqa: BLE001 - reported, not fatal
+            log(f"[bench] ADSampling comparator failed: {e}")
+
     # ---- the same step replayed as a captured CUDA graph (device buffers) ----------------
     graph_ms = None
     try:
@@ -639,6 +725,8 @@ def run_ours(args):
                             "seed_lists": fd_pt.get("seed_lists") or None,
                             "ms_per_step": round(statistics.mean(fd_ms), 4)},
             "dade_vs_fd": round(value / world / fd_qps, 3),
+            "adsampling": ads,
+            "dade_vs_adsampling": round(value / world / ads["value"], 3) if ads else None,
             "graph": ({"ms_per_step": round(graph_ms, 4), "value": round(world * nq / (graph_ms / 1e3), 1),
                        "unit": UNIT, "same_ids_as_timed_step": graph_same} if graph_ms else None),
             "work": {"candidates": cand, "dims_per_candidate": round(dims_sum / max(1, cand), 2),
