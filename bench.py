@@ -140,7 +140,7 @@ def run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, 
     dists = torch.empty(nq, K, dtype=torch.float32, device="cuda")
     probes = {}
     fixed = dade.FLAG_QUERY_ORDER | (dade.FLAG_ROW_TAIL if tf else 0)
-    list_major = (w.d + 15) // 16 == 8
+    list_major = (w.d + 15) // 16 >= 8
 
     def scan(pt):
         if pt["nprobe"] not in probes:
@@ -489,7 +489,7 @@ def run_ours(args):
     fd_best, fd_rec = None, {}
     for nprobe in grid:              # FD time grows with nprobe: the first point reaching the target wins
         fd_variants = [(128, 64, 0, 0), (128, 128, 0, 0), (256, 128, 0, 0)]
-        if (w.d + 15) // 16 == 8:
+        if (w.d + 15) // 16 >= 8:
             fd_variants += [(256, 128, dade.SCHED_SEEDED, 1), (256, 128, dade.SCHED_SEEDED, 2),
                             (256, 128, dade.SCHED_SEEDED, 3), (256, 1 << 20, dade.SCHED_SEEDED, 1),
                             (256, 1 << 20, dade.SCHED_SEEDED, 2)]
@@ -507,7 +507,7 @@ def run_ours(args):
     tried = []
     lead_flags = (0, dade.FLAG_LEAD) if lf else (0,)
     variants = [(dade.SCHED_TILE, 8, tile, 128, fl, 0) for tile in (128, 192, 256) for fl in lead_flags]
-    list_major = (w.d + 15) // 16 == 8   # the list-major kernels cover D in 113..128
+    list_major = (w.d + 15) // 16 >= 8   # the list-major kernels cover D > 112
     if list_major:
         variants += [(dade.SCHED_SEEDED, 8, tile, 128, 0, seed) for seed in (2, 3, 4)
                      for tile in (64, 128, 256, 1 << 20)]   # 1 << 20: whole lists, seed lists list-major too

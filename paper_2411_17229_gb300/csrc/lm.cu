@@ -51,11 +51,15 @@ struct LmArgs {
     const float *tail;           // row-major tail copy or null
     int64_t cap;
     int q_stride, nc, k, d, tail_nb0, tail_w;
-    float coef[LNB];             // prune iff P > coef[j] r^2 after increment j
+    int nb, n_inc;               // 16-dim blocks of the layout, increments (k_lm_g)
+    float coef[DADE_MAX_DIM / DADE_BLOCK];   // prune iff P > coef[j] r^2 after increment j
 };
 
 struct LmSmem {
     static constexpr size_t stage(int gb) { return sizeof(float) * (size_t)gb * LT * 16; }
+    static size_t total_g(int gb) {   // k_lm_g: only the first increment of each query staged
+        return 2 * stage(gb) + sizeof(float) * LG * 16 * gb + sizeof(Surv) * LNW * LT;
+    }
     static size_t total(int gb) {
         return 2 * stage(gb) + sizeof(float) * LG * 16 * LNB + sizeof(Surv) * LNW * LT;
     }
@@ -261,6 +265,190 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
     }
 }
 
+// The list-major kernel for any D (blocks nb > GB): the same items, tiles
+// and phase A as k_lm, with only the first increment of each query staged in
+// shared memory; phase B walks a survivor's later blocks in windows of 8
+// (one round trip each, its query's blocks read through L1), testing at
+// every increment boundary, and a warp stops as soon as its 8 survivors are
+// all pruned.
+template <int GB, bool STATS>
+__global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
+    constexpr int WB = 8;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int s_item, s_q[LG];
+    __shared__ float s_r2[LG];
+    float *stage = reinterpret_cast<float *>(smem);
+    float *qs = reinterpret_cast<float *>(smem + 2 * LmSmem::stage(GB));
+    Surv *survs = reinterpret_cast<Surv *>(smem + 2 * LmSmem::stage(GB) + sizeof(float) * LG * 16 * GB);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, quad = lane >> 2, lq = lane & 3;
+
+    if (tid == 0) {
+        mbar_init(su32(&bars[0]), 1);
+        mbar_init(su32(&bars[1]), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t used[2] = {0u, 0u};
+    const int total = a.item_off[a.nc];
+    const int nb = a.nb, n_inc = a.n_inc;
+
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(a.ctr, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = a.nc;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.item_off[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int c = lo;
+        const int qb = a.lq_off[c] + (item - a.item_off[c]) * LG;
+        const int ng = min(LG, a.lq_off[c + 1] - qb);
+        const ListMeta m = a.meta[c];
+        const int ntile = (m.len + LT - 1) / LT;
+        auto issue = [&](int t) {
+            const int buf = t & 1, i0 = t * LT, tn = min(LT, m.len - i0);
+            const uint32_t bar = su32(&bars[buf]);
+            mbar_expect_tx(bar, (uint32_t)(GB * tn * 64));
+            for (int b = 0; b < GB; ++b)
+                bulk_g2s(su32(stage + (size_t)buf * GB * LT * 16 + (size_t)b * LT * 16),
+                         a.data + m.base + (int64_t)b * m.np * 16 + (int64_t)i0 * 16, (uint32_t)(tn * 64), bar);
+        };
+        if (tid == 0)
+            for (int t = 0; t < 2 && t < ntile; ++t) issue(t);
+        for (int g = tid; g < ng; g += LNT) {
+            const int q = a.lq_items[qb + g];
+            s_q[g] = q;
+            s_r2[g] = a.r2src[(int64_t)q * a.k + a.k - 1];
+        }
+        for (int e = tid; e < ng * 16 * GB; e += LNT) {
+            const int g = e / (16 * GB), kk = e % (16 * GB);
+            qs[e] = kk < a.d ? a.q_rot[(int64_t)a.lq_items[qb + g] * a.q_stride + kk] : 0.f;
+        }
+        for (int t = 0; t < ntile; ++t) {
+            const int buf = t & 1;
+            if (!wait_block(su32(&bars[buf]), used[buf] & 1u)) {
+                if (tid == 0) {
+                    atomicExch(a.err, (int)DADE_ETIMEOUT);
+                    if (t + 1 < ntile) wait_bounded(su32(&bars[buf ^ 1]), used[buf ^ 1] & 1u, 10000000ull);
+                }
+                return;
+            }
+            ++used[buf];
+            const int i0 = t * LT, tn = min(LT, m.len - i0);
+            const float *st = stage + (size_t)buf * GB * LT * 16;
+            for (int g = warp; g < ng; g += LNW) {
+                const int q = s_q[g];
+                const float r2 = s_r2[g];
+                float4 qa[GB];
+#pragma unroll
+                for (int b = 0; b < GB; ++b)
+                    qa[b] = *reinterpret_cast<const float4 *>(qs + g * 16 * GB + b * 16 + lq * 4);
+                Surv *sv = survs + warp * LT;
+                int nsv = 0;
+                unsigned long long st_c = 0, st_d = 0, st_a = 0, st_p = 0;
+                const float c0 = a.coef[0] * r2;
+                for (int k0 = 0; k0 < tn; k0 += 8) {
+                    const int cand = k0 + quad;
+                    const bool act = cand < tn;
+                    float p = 0.f;
+                    if (act) {
+#pragma unroll
+                        for (int b = 0; b < GB; ++b)
+                            p += sqd4(qa[b], *reinterpret_cast<const float4 *>(st + ((size_t)b * LT + cand) * 16 + lq * 4));
+                    }
+                    p = quad_sum4(p);
+                    const bool lead = act && lq == 0;
+                    const bool keep = lead && !(p > c0);
+                    const unsigned mk = __ballot_sync(0xffffffffu, keep);
+                    if (keep) sv[nsv + __popc(mk & ((1u << lane) - 1u))] = Surv{cand, p};
+                    nsv += __popc(mk);
+                    if (STATS && lead) {
+                        ++st_c;
+                        if (!keep) { st_d += min(GB * 16, a.d); ++st_p; }
+                    }
+                }
+                __syncwarp();
+                const float *qrow = a.q_rot + (int64_t)q * a.q_stride;
+                for (int r0 = 0; r0 < nsv; r0 += 8) {
+                    const int sidx = r0 + quad;
+                    const bool act = sidx < nsv;
+                    const Surv v = act ? sv[sidx] : Surv{0, 0.f};
+                    const int64_t i = i0 + v.idx;
+                    const float *row = a.data + m.base + i * 16 + lq * 4;
+                    const float *trow =
+                        a.tail ? a.tail + (m.slot + i) * a.tail_w + lq * 4 - (int64_t)a.tail_nb0 * 16 : nullptr;
+                    float p = v.p, part = 0.f;
+                    bool alive = act;
+                    int jj = 1, bend = min(2 * GB, nb);
+                    for (int wb = GB; wb < nb; wb += WB) {
+                        if (!__any_sync(0xffffffffu, alive)) break;
+                        float4 o[WB];
+#pragma unroll
+                        for (int u = 0; u < WB; ++u) {
+                            const int b = wb + u;
+                            const float *src = (trow && b >= a.tail_nb0) ? trow + b * 16 : row + (int64_t)b * m.np * 16;
+                            o[u] = (b < nb && alive) ? __ldg(reinterpret_cast<const float4 *>(src))
+                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < WB; ++u) {
+                            const int b = wb + u;
+                            if (b < nb) {
+                                float qv[4];
+#pragma unroll
+                                for (int t = 0; t < 4; ++t) {
+                                    const int kk = b * 16 + lq * 4 + t;
+                                    qv[t] = kk < a.d ? __ldg(qrow + kk) : 0.f;
+                                }
+                                part += sqd4(make_float4(qv[0], qv[1], qv[2], qv[3]), o[u]);
+                                if (b + 1 == bend) {   // end of increment jj
+                                    part = quad_sum4(part);
+                                    if (alive) {
+                                        p += part;
+                                        if (jj < n_inc - 1 && p > a.coef[jj] * r2) {
+                                            alive = false;
+                                            if (STATS && lq == 0) { st_d += min((jj + 1) * GB * 16, a.d); ++st_p; }
+                                        }
+                                    }
+                                    part = 0.f;
+                                    ++jj;
+                                    bend = min(bend + GB, nb);
+                                }
+                            }
+                        }
+                    }
+                    const bool take = alive && lq == 0 && p <= r2;
+                    if (STATS && alive && lq == 0) { st_d += a.d; st_a += take; }
+                    const int id = take ? a.ids[m.slot + i] : 0;
+                    lm_append(a, take, q, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned)id);
+                }
+                if (STATS) {
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        st_c += __shfl_xor_sync(0xffffffffu, st_c, off);
+                        st_d += __shfl_xor_sync(0xffffffffu, st_d, off);
+                        st_a += __shfl_xor_sync(0xffffffffu, st_a, off);
+                        st_p += __shfl_xor_sync(0xffffffffu, st_p, off);
+                    }
+                    if (lane == 0) {
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 0]), st_c);
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 1]), st_d);
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 2]), st_a);
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 3]), st_p);
+                    }
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+            if (tid == 0 && t + 2 < ntile) issue(t + 2);
+        }
+    }
+}
+
 // ---- work list -------------------------------------------------------------------
 // (query, list) pairs of probe positions [c0, c1) (probe rows of nprobe).
 __global__ void k_lm_count(const int32_t *__restrict__ probe, int64_t nq, int nprobe, int c0, int c1,
@@ -418,6 +606,32 @@ dade_status launch_lm(const LmArgs &a, cudaStream_t s) {
     return launch_check("k_lm");
 }
 
+template <int GB, bool STATS>
+dade_status launch_lm_g(const LmArgs &a, cudaStream_t s) {
+    static int blocks = 0;
+    const size_t smem = LmSmem::total_g(GB);
+    if (blocks == 0) {
+        DADE_TRY_CUDA(cudaFuncSetAttribute(k_lm_g<GB, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int dev = 0, sms = 0, per = 0;
+        DADE_TRY_CUDA(cudaGetDevice(&dev));
+        DADE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        DADE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lm_g<GB, STATS>, LNT, smem));
+        blocks = std::max(1, sms * std::max(1, per));
+    }
+    k_lm_g<GB, STATS><<<blocks, LNT, smem, s>>>(a);
+    return launch_check("k_lm_g");
+}
+
+template <bool STATS>
+dade_status launch_lm_gen(const LmArgs &a, int gb, cudaStream_t s) {
+    switch (gb) {
+    case 1: return launch_lm_g<1, STATS>(a, s);
+    case 2: return launch_lm_g<2, STATS>(a, s);
+    case 4: return launch_lm_g<4, STATS>(a, s);
+    default: return launch_lm_g<8, STATS>(a, s);
+    }
+}
+
 template <bool STATS>
 dade_status launch_lm_gb(const LmArgs &a, int gb, cudaStream_t s) {
     switch (gb) {
@@ -484,9 +698,14 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
         a.tail_nb0 = ix->tail_nb0;
         a.tail_w = ix->tail_w;
     }
-    const int n_inc = (LNB + gb - 1) / gb;
-    for (int j = 0; j < LNB; ++j) a.coef[j] = (prune && j < n_inc - 1) ? p.coef[j] : INFINITY;
-    DADE_TRY(p.stats ? launch_lm_gb<true>(a, gb, s) : launch_lm_gb<false>(a, gb, s));
+    const int n_inc = (ix->nb + gb - 1) / gb;
+    a.nb = ix->nb;
+    a.n_inc = n_inc;
+    for (int j = 0; j < DADE_MAX_DIM / DADE_BLOCK; ++j) a.coef[j] = (prune && j < n_inc - 1) ? p.coef[j] : INFINITY;
+    if (ix->nb == LNB)
+        DADE_TRY(p.stats ? launch_lm_gb<true>(a, gb, s) : launch_lm_gb<false>(a, gb, s));
+    else
+        DADE_TRY(p.stats ? launch_lm_gen<true>(a, gb, s) : launch_lm_gen<false>(a, gb, s));
     k_lm_merge<<<(unsigned)nq, MT, 0, s>>>(p.ids, p.dists, p.k, a.acc, a.acnt, cap);
     return launch_check("k_lm_merge");
 }
@@ -503,15 +722,17 @@ dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, c
     const int np = p.nprobe;
     const bool fd = p.mode == DADE_MODE_FD;
     const int gb = fd ? LNB : std::min(p.delta_d / 16, ix->nb);
-    if (ix->nb != LNB || (gb != 1 && gb != 2 && gb != 4 && gb != 8)) {
-        set_error("the seeded schedule needs D in 113..128 and delta_d in {16, 32, 64, >= 128}");
+    const bool ok = ix->nb == LNB ? (gb == 1 || gb == 2 || gb == 4 || gb == 8)
+                                  : (ix->nb > LNB && (gb == 1 || gb == 2 || gb == 4 || gb == 8));
+    if (!ok) {
+        set_error("the seeded schedule needs D > 112 and delta_d in {16, 32, 64, 128} (or >= D when D <= 128)");
         return DADE_EUNSUPPORTED;
     }
     if (p.tile >= ix->max_list) {
         k_lm_reset<<<grid_of(nq * (int64_t)p.k, 256), 256, 0, s>>>(p.ids, p.dists, nq * (int64_t)p.k);
         DADE_TRY(launch_check("k_lm_reset"));
         if (p.stats) DADE_TRY_CUDA(cudaMemsetAsync(p.stats, 0, sizeof(int64_t) * 4 * (size_t)nq, s));
-        DADE_TRY(lm_round(ix, nq, p, 0, 1, LNB, false, s));   // r = +inf: exact
+        DADE_TRY(lm_round(ix, nq, p, 0, 1, std::min(LNB, ix->nb), false, s));   // r = +inf: exact
         for (int j = 1; j < S; ++j) DADE_TRY(lm_round(ix, nq, p, j, j + 1, gb, !fd, s));
     } else {
         ScanParams p1 = p;   // the first S lists, tile schedule, straight into the outputs

@@ -347,9 +347,29 @@ def test_seeded_schedule_mixture_and_limits():
     a = case.gpu_search(10, 4, 0.1, 32, stats=True)
     b = case.gpu_search(10, 4, 0.1, 32, stats=True, schedule=dade.SCHED_SEEDED, seed_lists=4)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
-    # D = 64 is outside the list-major kernels
+    # D = 64 (fewer than 8 blocks) is outside the list-major kernels
     small = Case(*synth.make(synth.Workload("mix64", 3000, 64, 10, 1.0, 6, 0.0, 3.0, 1.0, False, False, 6, (4,),
                                             10, (16,), 0.1))[:2], synth.zipf_assign(3000, 6, s=0.5), 6, n_pairs=1000)
     with pytest.raises(dade.DadeError) as e:
         small.gpu_search(5, 4, 0.1, 32, schedule=dade.SCHED_SEEDED, seed_lists=1)
     assert e.value.status == dade.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("d,delta_d,seed,tile", [(160, 16, 2, 128), (160, 32, 1, 4096), (256, 64, 2, 128),
+                                                 (384, 128, 3, 128), (136, 16, 2, 128)])
+def test_seeded_schedule_any_dimension(d, delta_d, seed, tile):
+    """The list-major kernel for D > 128 (blocks walked in windows): parity
+    with the oracle's seeded schedule, and FDScanning unchanged."""
+    w = synth.Workload(f"mix{d}", 8000, d, 70, 1.0, 20, 0.0, 3.0, 1.0, False, False, 20, (4,), 10, (16,), 0.1)
+    base, queries, labels = synth.make(w)
+    case = Case(base, queries, labels, 20, n_pairs=4000)
+    for k, nprobe in ((10, 8), (60, 12)):
+        g_ids, g_d, g_st = case.gpu_search(k, nprobe, 0.1, delta_d, tile=tile, stats=True,
+                                           schedule=dade.SCHED_SEEDED, seed_lists=seed)
+        o_ids, o_d, o_st, oflags = case.oracle_search(k, nprobe, 0.1, delta_d, tile=tile, seed=seed)
+        parity.compare(g_ids, g_d, o_ids, o_d, oflags, case.scale, case.exact_d)
+        assert np.array_equal(g_st[:, 0], o_st[:, 0])
+        assert np.array_equal(g_st[oflags == 0, 1:], o_st[oflags == 0, 1:])
+    a = case.gpu_search(10, 8, 0.1, 32, mode=dade.MODE_FD)
+    b = case.gpu_search(10, 8, 0.1, 32, mode=dade.MODE_FD, schedule=dade.SCHED_SEEDED, seed_lists=2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
