@@ -79,7 +79,7 @@ def parse():
 
 def parse_point(text, dade):
     pt = {"mode": dade.MODE_DADE, "spec": 8, "schedule": dade.SCHED_TILE, "tile": 128, "threads": 128, "flags": 0,
-          "seed_lists": 0}
+          "seed_lists": 0, "stage_dims": 0}
     for kv in text.split(","):
         k, v = kv.split("=")
         pt[k.strip()] = float(v) if k.strip() == "alpha" else int(v)
@@ -113,9 +113,7 @@ def run_profile(args):
         e0.record()
         ix.rotate(q, qr)
         ix.probe(qr, pt["nprobe"], pr)
-        ix.scan(qr, pr, w.k, pt.get("alpha", 0.1), pt.get("delta_d", 32), ids, dists, mode=pt["mode"],
-                tile=pt["tile"], spec=pt["spec"], threads=pt["threads"], schedule=pt["schedule"],
-                flags=pt["flags"], seed_lists=pt["seed_lists"])
+        ix.scan(qr, pr, w.k, pt.get("alpha", 0.1), pt.get("delta_d", 32), ids, dists, **point_kw(pt))
         e1.record()
         torch.cuda.synchronize()
         if i >= args.warmup:
@@ -211,7 +209,8 @@ def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7):
     nprobes = [p for p in (16, 64, 128) if p <= n_lists]
     srv = dade.Server(ix, slots=4, max_batch=1024, max_k=100, max_nprobe=max(nprobes), tile=point["tile"],
                       threads=point["threads"], schedule=point.get("schedule", 0),
-                      seed_lists=point.get("seed_lists", 0), flags=point["flags"])
+                      seed_lists=point.get("seed_lists", 0), flags=point["flags"],
+                      stage_dims=point.get("stage_dims", 0))
     rng = np.random.default_rng(seed)
     out = []
     for rate in rates:
@@ -345,7 +344,9 @@ def scan_kernel_name(point, d):
         return f"k_dade_fast<{point['threads']}, 8, {min(point['delta_d'] // 16, 8)}{', lead' if lead else ''}>"
     if point.get("schedule", 0) == 1:
         return "k_scan_pipe"
-    return "k_scan<DADE, lead>" if lead else "k_scan<DADE>"
+    if lead:
+        return "k_scan<DADE, lead>"
+    return f"k_scan<DADE> ({point['stage_dims']} dims staged)" if point.get("stage_dims") else "k_scan<DADE>"
 
 
 def recorded_traffic(point, workload):
@@ -360,15 +361,23 @@ def recorded_traffic(point, workload):
     for r in rec if isinstance(rec, list) else [rec]:
         if r.get("scan_cu_sha256_16") != scan_source_hash() or r.get("workload") != workload:
             continue
-        if any(r.get("point", {}).get(k) != point.get(k) for k in ("nprobe", "alpha", "delta_d", "spec", "threads",
-                                                                    "tile", "mode", "schedule", "flags",
-                                                                    "seed_lists")):
+        keys = ("nprobe", "alpha", "delta_d", "spec", "threads", "tile", "mode", "schedule", "flags", "seed_lists")
+        if any(r.get("point", {}).get(k) != point.get(k) for k in keys):
+            continue
+        if r.get("point", {}).get("stage_dims", 0) != point.get("stage_dims", 0):
             continue
         return r.get("dram_bytes_per_launch")
     return None
 
 
 # ------------------------------------------------------------ ground truth --
+def point_kw(point):
+    """The scan options of an autotuned point, as keyword arguments of the binding."""
+    return dict(mode=point["mode"], tile=point["tile"], spec=point.get("spec", 8), threads=point["threads"],
+                schedule=point.get("schedule", 0), flags=point.get("flags", 0),
+                seed_lists=point.get("seed_lists", 0), stage_dims=point.get("stage_dims", 0))
+
+
 def ground_truth(torch, xb, q, K):
     """Exact K nearest (FP64 distances): an FP32 shortlist of K + 64 from a
     torch matmul (ground truth only, not the measured path), then an exact
@@ -467,9 +476,7 @@ def run_ours(args):
 
     def scan(pt, st=None, lead_st=None):
         ix.scan(qr, probe_for(pt["nprobe"]), K, pt.get("alpha", 0.1), pt.get("delta_d", 32), ids, dists,
-                mode=pt["mode"], tile=pt["tile"], stats=st, spec=pt.get("spec", 8), threads=pt["threads"],
-                schedule=pt.get("schedule", 0), flags=pt.get("flags", 0), lead_stats=lead_st,
-                seed_lists=pt.get("seed_lists", 0), stream=sh)
+                stats=st, lead_stats=lead_st, stream=sh, **point_kw(pt))
 
     def measure(pt, reps=4):
         scan(pt)
@@ -506,18 +513,24 @@ def run_ours(args):
     dade_best = None
     tried = []
     lead_flags = (0, dade.FLAG_LEAD) if lf else (0,)
-    variants = [(dade.SCHED_TILE, 8, tile, 128, fl, 0) for tile in (128, 192, 256) for fl in lead_flags]
+    variants = [(dade.SCHED_TILE, 8, tile, 128, fl, 0, 0) for tile in (128, 192, 256) for fl in lead_flags]
     list_major = (w.d + 15) // 16 >= 8   # the list-major kernels cover D > 112
     if list_major:
-        variants += [(dade.SCHED_SEEDED, 8, tile, 128, 0, seed) for seed in (2, 3, 4)
+        variants += [(dade.SCHED_SEEDED, 8, tile, 128, 0, seed, 0) for seed in (2, 3, 4)
                      for tile in (64, 128, 256, 1 << 20)]   # 1 << 20: whole lists, seed lists list-major too
+    if w.d > 128:   # generic tile kernel: stream several increments per tile (two stages <= 160 KB)
+        variants += [(dade.SCHED_TILE, 8, tile, 128, 0, 0, sd) for tile in (64, 128) for sd in (64, 128, 256)
+                     if tile * sd * 8 <= 160 * 1024]
     for dd in (16, 32, 64):
         for alpha in (0.05, 0.1, 0.2, 0.3):
-            for schedule, spec, tile, threads, fl, seed in variants:
+            for schedule, spec, tile, threads, fl, seed, sd in variants:
+                    if sd and (sd <= dd or sd % dd):
+                        continue
                     for nprobe in [p for p in grid if p >= n0][:3]:
                         pt = {"mode": dade.MODE_DADE, "nprobe": nprobe, "alpha": alpha, "delta_d": dd,
                               "spec": spec, "tile": tile, "threads": threads, "schedule": schedule,
-                              "flags": fl | fixed, "seed_lists": seed}
+                              "flags": (fl | fixed) | (dade.FLAG_GENERIC_KERNEL if sd else 0),
+                              "seed_lists": seed, "stage_dims": sd}
                         ms, rc = measure(pt)
                         tried.append((ms, rc, pt))
                         if rc >= RECALL_TARGET:
@@ -561,9 +574,7 @@ def run_ours(args):
         ev[3].record(stream)
         ix.probe(qr, point["nprobe"], pr_step, stream=sh)
         ev[1].record(stream)
-        ix.scan(qr, pr_step, K, point["alpha"], point["delta_d"], ids, dists, mode=point["mode"],
-                tile=point["tile"], spec=point["spec"], threads=point["threads"], schedule=point["schedule"],
-                flags=point["flags"], seed_lists=point.get("seed_lists", 0), stream=sh)
+        ix.scan(qr, pr_step, K, point["alpha"], point["delta_d"], ids, dists, stream=sh, **point_kw(point))
 
     for _ in range(args.warmup):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -640,9 +651,7 @@ def run_ours(args):
     try:
         gids = torch.empty(nq, K, dtype=torch.int64, device="cuda")
         gd = torch.empty(nq, K, dtype=torch.float32, device="cuda")
-        g = ix.graph(q, K, point["nprobe"], point["alpha"], point["delta_d"], gids, gd, mode=point["mode"],
-                     tile=point["tile"], spec=point["spec"], threads=point["threads"], schedule=point["schedule"],
-                     flags=point["flags"], seed_lists=point.get("seed_lists", 0))
+        g = ix.graph(q, K, point["nprobe"], point["alpha"], point["delta_d"], gids, gd, **point_kw(point))
         gms = []
         for i in range(args.warmup + args.steps):
             flush.zero_()
@@ -675,9 +684,8 @@ def run_ours(args):
     e2e_s = []
     for i in range(args.warmup + args.steps):
         t1 = time.perf_counter()
-        ix.query(q_host, K, point["nprobe"], point["alpha"], point["delta_d"], ids_host, d_host, mode=point["mode"],
-                 tile=point["tile"], spec=point["spec"], threads=point["threads"], schedule=point["schedule"],
-                 flags=point["flags"], seed_lists=point.get("seed_lists", 0), stream=sh)
+        ix.query(q_host, K, point["nprobe"], point["alpha"], point["delta_d"], ids_host, d_host, stream=sh,
+                 **point_kw(point))
         if i >= args.warmup:
             e2e_s.append(time.perf_counter() - t1)
     e2e_qps = world * nq / statistics.mean(e2e_s)
@@ -708,10 +716,11 @@ def run_ours(args):
                        "spec": point.get("spec"), "tile": point["tile"], "threads": point["threads"],
                        "schedule": {0: "tile", 1: "pipelined", 2: "seeded"}[point.get("schedule", 0)],
                        "seed_lists": point.get("seed_lists") if point.get("schedule", 0) == 2 else None,
+                       "stage_dims": point.get("stage_dims") or None,
                        "lead_prefilter": ({"format": args.lead, "dims": ld} if use_lead else None),
                        "flags": {"query_order": bool(point["flags"] & dade.FLAG_QUERY_ORDER),
                                  "row_tail_from": tf if point["flags"] & dade.FLAG_ROW_TAIL else None},
-                       "l2": "index 512 MB > L2; 256 MB flush written between timed steps",
+                       "l2": f"index {n * w.d * 4 / 2**20:.0f} MB > L2; 256 MB flush written between timed steps",
                        "parallelism": f"replicas x{world}"},
             "recall": round(rc_timed, 5),
             "breakdown_ms": {"rotate": round(statistics.mean(rot_ms), 4), "probe": round(statistics.mean(probe_ms), 4),

@@ -201,7 +201,11 @@ typedef struct {
                                   the tile schedule) */
     int32_t estimator;         /* dade_estimator (default DADE_ESTIMATOR_DADE) */
     float eps0;                /* ADSampling's eps0 (> 0) */
-    int32_t reserved[1];
+    int32_t stage_dims;        /* tile schedule, any D: dims of every candidate of a tile streamed into
+                                  shared memory at once (0: delta_d; else a multiple of delta_d), tested
+                                  at each increment inside; survivors then gather the rest.  Same
+                                  results; a deeper stage trades gathers for streaming when most
+                                  candidates outlive the first increments. */
 } dade_search_opts;
 
 /* Description of a built index. */
@@ -298,7 +302,8 @@ typedef struct {
     int32_t max_nprobe;        /* largest nprobe of a request (default 128) */
     int64_t device_budget;     /* device bytes for the slots (0: no limit); fewer slots if needed */
     int32_t mode, tile, threads, schedule, seed_lists, flags;   /* dade_search_opts of every batch */
-    int32_t reserved[4];
+    int32_t stage_dims;        /* dade_search_opts.stage_dims of every batch (0: delta_d) */
+    int32_t reserved[3];
 } dade_server_opts;
 typedef struct {
     int64_t slots, slot_bytes;          /* slots created, device bytes budgeted per slot */

@@ -141,6 +141,10 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
                        opts->schedule == DADE_SCHED_SEEDED,
                    "unknown schedule");
     DADE_CHECK_ARG(!opts || opts->seed_lists >= 0, "seed_lists < 0");
+    DADE_CHECK_ARG(!opts || opts->stage_dims == 0 ||
+                       (opts->stage_dims >= delta_d && delta_d > 0 && opts->stage_dims % delta_d == 0 &&
+                        opts->stage_dims <= DADE_MAX_DIM),
+                   "stage_dims must be 0 or a multiple of delta_d up to 1024");
     DADE_CHECK_ARG(!opts || (opts->flags & ~(DADE_FLAG_GENERIC_KERNEL | DADE_FLAG_LEAD | DADE_FLAG_QUERY_ORDER |
                                              DADE_FLAG_ROW_TAIL)) == 0,
                    "unknown flag bits");
@@ -202,6 +206,7 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.threads = opts && opts->threads ? opts->threads : 128;
     p.schedule = opts ? opts->schedule : DADE_SCHED_TILE;
     p.seed_lists = opts && opts->seed_lists > 0 ? opts->seed_lists : 2;
+    p.stage_dims = opts ? opts->stage_dims : 0;
     p.generic = opts ? (opts->flags & DADE_FLAG_GENERIC_KERNEL) != 0 : 0;
     p.use_lead = opts ? (opts->flags & DADE_FLAG_LEAD) != 0 : 0;
     p.use_tail = opts ? (opts->flags & DADE_FLAG_ROW_TAIL) != 0 : 0;

@@ -157,6 +157,7 @@ struct ScanParams {
     int32_t use_tail;        // phase B reads the row-major tail copy
     int32_t pstride;         // row stride of probe (0: nprobe)
     int32_t seed_lists;      // DADE_SCHED_SEEDED
+    int32_t stage_dims;      // FP32 DADE tile kernel: dims staged per tile (0: delta_d)
     float coef[DADE_MAX_DIM / DADE_BLOCK];   // per increment; prune iff P > coef[j] * r2
     int64_t *ids;            // [nq][k]
     float *dists;            // [nq][k]

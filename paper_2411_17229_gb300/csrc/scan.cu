@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
 
     const int tid = threadIdx.x, quad = tid >> 2, lq = tid & 3;
     const int64_t qi = cta_query(a);
-    const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k, a.nprobe, LF != 0);
+    const SmemLayout L = layout(a.dp, a.tile, a.ub, a.ns, a.k, a.nprobe, LF != 0);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     int4 *smeta = reinterpret_cast<int4 *>(smem + L.meta);
     float *qv = reinterpret_cast<float *>(smem + L.qv);
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
         if constexpr (LF != 0) {
             const int4 m = meta_of(a, smeta, plist, c.p);
             issue_lead<LF>(a, m, c.i0, min(a.tile, m.z - c.i0), a.gb, a.tile,
-                           reinterpret_cast<unsigned char *>(stage + (size_t)slot * a.tile * a.gb * 16),
+                           reinterpret_cast<unsigned char *>(stage + (size_t)slot * a.tile * a.ub * 16),
                            su32(&bars[slot]));
         } else {
             issue(a, smeta, plist, c, slot, stage, bars);
@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
                 const int slot = unit % a.ns;
                 if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1))) { aborted = true; break; }
                 if (j == 0) r2 = s_r2;
-                const float *st = stage + (size_t)slot * a.tile * a.gb * 16;
-                const int b0 = j * a.gb, b1 = min(b0 + a.gb, a.nb);
+                const float *st = stage + (size_t)slot * a.tile * a.ub * 16;
+                const int b0 = j * a.ub, b1 = min(b0 + a.ub, a.nb);
 #pragma unroll
                 for (int it = 0; it < MAXIT; ++it) {
                     const int c = quad + it * NQUAD;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
             if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1))) { aborted = true; break; }
             r2 = s_r2;
             if constexpr (LF != 0) {
-                const unsigned char *st = reinterpret_cast<const unsigned char *>(stage + (size_t)slot * a.tile * a.gb * 16);
+                const unsigned char *st = reinterpret_cast<const unsigned char *>(stage + (size_t)slot * a.tile * a.ub * 16);
                 const float *se = reinterpret_cast<const float *>(st + (size_t)a.gb * a.tile * 16 * ES);
                 const bool last0 = a.n_inc == 1;
                 const int d0 = min(a.delta_d, a.d);
@@ -204,26 +204,41 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
                     }
                 }
             } else {
-                const float *st = stage + (size_t)slot * a.tile * a.gb * 16;
-                const int b1 = min(a.gb, a.nb);
-                const bool last0 = a.n_inc == 1;
-                const int d0 = min(a.delta_d, a.d);
-                const float c0 = a.coef[0] * r2;
+                // the staged unit holds the first ub blocks (a whole number of increments):
+                // run every increment inside it, testing at each boundary; a candidate
+                // that survives them all goes to phase B, or, if the unit reaches D, to
+                // the exact compare
+                const float *st = stage + (size_t)slot * a.tile * a.ub * 16;
+                const int ninc_a = (min(a.ub, a.nb) + a.gb - 1) / a.gb;
+                const bool all_staged = a.ub >= a.nb;
                 for (int it = 0; it < nit; ++it) {
                     const int c = quad + it * NQUAD;
                     const bool act = c < tn;
-                    float p = act ? row_part(st + c * 16 + lq * 4, (int64_t)a.tile * 16, qv, 0, b1, lq, false) : 0.f;
-                    p += __shfl_xor_sync(0xffffffffu, p, 1);
-                    p += __shfl_xor_sync(0xffffffffu, p, 2);
+                    float p = 0.f;
+                    bool alive = act;
+                    int pruned_at = -1;
+                    for (int j = 0; j < ninc_a; ++j) {
+                        const int b0 = j * a.gb, b1 = min(b0 + a.gb, a.nb);
+                        float part = act ? row_part(st + (size_t)b0 * a.tile * 16 + c * 16 + lq * 4,
+                                                    (int64_t)a.tile * 16, qv, b0, b1, lq, false)
+                                         : 0.f;
+                        part += __shfl_xor_sync(0xffffffffu, part, 1);
+                        part += __shfl_xor_sync(0xffffffffu, part, 2);
+                        p += part;
+                        if (alive && b1 < a.nb && p > a.coef[j] * r2) {
+                            alive = false;
+                            pruned_at = j;
+                        }
+                    }
                     const bool lead = act && lq == 0;
-                    const bool toF = lead && last0 && p <= r2;
-                    const bool toN = lead && !last0 && !(p > c0);
+                    const bool toF = lead && alive && all_staged && p <= r2;
+                    const bool toN = lead && alive && !all_staged;
                     push(toF, fl, &s_cntF, c, p);
                     push(toN, l0, &s_cnt[0], c, p);
                     if (STATS && lead) {
                         ++st_cand;
-                        if (last0) { st_dims += a.d; st_acc += toF; }
-                        else if (!toN) { st_dims += d0; ++st_prn; }
+                        if (!alive) { st_dims += min((pruned_at + 1) * a.delta_d, a.d); ++st_prn; }
+                        else if (all_staged) { st_dims += a.d; st_acc += toF; }
                     }
                 }
             }
@@ -245,12 +260,14 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
                 const int sidx = r0 + quad;
                 const bool act = sidx < nS;
                 const Surv sv = act ? l0[sidx] : Surv{0, 0.f};
-                // after the prefilter (LF) every increment, the first included, runs on FP32 rows
+                // after the prefilter (LF) every increment, the first included, runs on FP32
+                // rows; otherwise phase B starts after the staged unit (ub blocks)
+                const int sb = LF ? 0 : a.ub;
                 float p = LF ? 0.f : sv.p, part = 0.f;
                 bool alive = act;
                 const float *row = lbase + (int64_t)(cc.i0 + sv.idx) * 16 + lq * 4;
-                int jj = LF ? 0 : 1, bend = min((LF ? 1 : 2) * a.gb, a.nb);
-                for (int wb = LF ? 0 : a.gb; wb < a.nb; wb += a.spec) {
+                int jj = sb / a.gb, bend = min(sb + a.gb, a.nb);
+                for (int wb = sb; wb < a.nb; wb += a.spec) {
                     if (!__any_sync(0xffffffffu, alive)) break;
                     float4 o[SPECB];
 #pragma unroll
@@ -438,6 +455,10 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
         a.delta_d = p.delta_d;
     }
     a.n_inc = (ix->nb + a.gb - 1) / a.gb;
+    // blocks per staged unit: FDScanning and the prefilter one increment; the FP32
+    // DADE tile kernel p.stage_dims (a whole number of increments, default one)
+    a.ub = a.gb;
+    if (!fd && !p.use_lead && p.stage_dims > a.delta_d) a.ub = std::min((p.stage_dims / 16) / a.gb * a.gb, ix->nb);
     for (int j = 0; j < DADE_MAX_DIM / DADE_BLOCK; ++j) a.coef[j] = j < p.n_inc ? p.coef[j] : INFINITY;
     const int lf = (!fd && p.use_lead) ? ix->lead_format : 0;
     if (lf) {
@@ -449,10 +470,10 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
         a.lead_slots = ix->slots;
         a.lead_nb = ix->lead_nb;
     }
-    if (!fd && !lf && p.schedule == DADE_SCHED_PIPELINED && a.n_inc <= pipe_depth_limit())
+    if (!fd && !lf && a.ub == a.gb && p.schedule == DADE_SCHED_PIPELINED && a.n_inc <= pipe_depth_limit())
         return scan_pipelined(a, nq, p.threads, s);
-    if (scan_fast_applies(a, fd) && !p.generic) return scan_fast(a, nq, fd, p.threads, lf, s);
-    const SmemLayout L = layout(a.dp, a.tile, a.gb, a.ns, a.k, a.nprobe, lf != 0);
+    if (scan_fast_applies(a, fd) && !p.generic && a.ub == a.gb) return scan_fast(a, nq, fd, p.threads, lf, s);
+    const SmemLayout L = layout(a.dp, a.tile, a.ub, a.ns, a.k, a.nprobe, lf != 0);
     if (L.total > 227 * 1024) {
         set_error("scan configuration needs more than 227 KB of shared memory (reduce tile or delta_d)");
         return DADE_EUNSUPPORTED;

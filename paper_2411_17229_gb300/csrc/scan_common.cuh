@@ -35,6 +35,7 @@ struct ScanArgs {
     int64_t *stats;
     int *err;
     int q_stride, nprobe, pstride, d, dp, nb, k, tile, gb, n_inc, ns, delta_d, spec;   // pstride: probe row stride
+    int ub;                      // blocks per staged unit (gb, or more for a deeper FP32 first stage)
     float coef[DADE_MAX_DIM / DADE_BLOCK];
     // low-precision leading blocks (prefilter of the first increment)
     const unsigned char *lead;   // residual codes, list region at slot * lead_nb * 16 * ES bytes
@@ -163,10 +164,10 @@ __device__ inline void issue(const ScanArgs &a, const int4 *sm, const int32_t *p
                       uint64_t *bars) {
     const int4 m = meta_of(a, sm, plist, c.p);
     const int tn = min(a.tile, m.z - c.i0);
-    const int b0 = c.j * a.gb, b1 = min(b0 + a.gb, a.nb);
+    const int b0 = c.j * a.ub, b1 = min(b0 + a.ub, a.nb);
     const uint32_t bar = su32(&bars[slot]);
     mbar_expect_tx(bar, (uint32_t)((b1 - b0) * tn * 64));
-    float *dst = stage + (size_t)slot * a.tile * a.gb * 16;
+    float *dst = stage + (size_t)slot * a.tile * a.ub * 16;
     const float *src = list_base(a, m) + (int64_t)c.i0 * 16;
     for (int b = b0; b < b1; ++b)
         bulk_g2s(su32(dst + (size_t)(b - b0) * a.tile * 16), src + (int64_t)b * m.w * 16, (uint32_t)(tn * 64), bar);

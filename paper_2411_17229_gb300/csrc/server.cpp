@@ -116,6 +116,7 @@ struct dade_server {
         so.schedule = o.schedule;
         so.seed_lists = o.seed_lists;
         so.flags = o.flags;
+        so.stage_dims = o.stage_dims;
         DADE_TRY(dade_query(ix, s.q_dev.as<float>(), nq, r0.k, r0.nprobe, r0.alpha, r0.delta_d, &so,
                             s.ids_dev.as<int64_t>(), s.dists_dev.as<float>(), (dade_stream)s.stream));
         DADE_TRY_CUDA(cudaMemcpyAsync(s.ids_host, s.ids_dev.p, sizeof(int64_t) * (size_t)nq * r0.k,
@@ -319,6 +320,7 @@ dade_status dade_server_submit(dade_server *sv, const float *q, int64_t nq, int3
     so.schedule = sv->o.schedule;
     so.seed_lists = sv->o.seed_lists;
     so.flags = sv->o.flags;
+    so.stage_dims = sv->o.stage_dims;
     // the same checks dade_search makes, before the request is queued
     dade_status vs = dade_scan(sv->ix, nullptr, nullptr, 0, k, nprobe, alpha, delta_d, &so, nullptr, nullptr,
                                nullptr);
