@@ -336,6 +336,12 @@ def scan_kernel_name(point, d):
     if point["mode"] == 1:
         return f"k_fd_fast<{point['threads']}, 8>" if nb == 8 else "k_scan<FD>"
     lead = point.get("flags", 0) & 2
+    if point.get("schedule", 0) == 2 and point.get("flags", 0) & 16:
+        return (f"k_scan<{point['threads']}, DADE{', lead' if lead else ''}> (first {point.get('seed_lists')} "
+                f"lists, then the later lists split over CTAs) + k_lm_merge")
+    if point.get("schedule", 0) == 2 and nb > 8:
+        return (f"k_scan<DADE> (first {point.get('seed_lists')} lists) + k_lm_g<{min(point['delta_d'] // 16, 8)}> "
+                f"(list-major) + k_lm_merge")
     if point.get("schedule", 0) == 2 and nb == 8:
         gb = min(point["delta_d"] // 16, 8)
         return (f"k_dade_fast<{point['threads']}, 8, {gb}> (first {point.get('seed_lists')} lists) + "
@@ -513,14 +519,18 @@ def run_ours(args):
     dade_best = None
     tried = []
     lead_flags = (0, dade.FLAG_LEAD) if lf else (0,)
-    variants = [(dade.SCHED_TILE, 8, tile, 128, fl, 0, 0) for tile in (128, 192, 256) for fl in lead_flags]
+    variants = [(dade.SCHED_TILE, 8, tile, nt, fl, 0, 0) for tile in (128, 192, 256) for fl in lead_flags
+                for nt in (128, 256)]
     list_major = (w.d + 15) // 16 >= 8   # the list-major kernels cover D > 112
     if list_major:
         variants += [(dade.SCHED_SEEDED, 8, tile, 128, 0, seed, 0) for seed in (2, 3, 4)
                      for tile in (64, 128, 256, 1 << 20)]   # 1 << 20: whole lists, seed lists list-major too
+    if list_major or w.d <= 112:   # passes with r frozen query-major, split over CTAs
+        variants += [(dade.SCHED_SEEDED, 8, 128, nt, dade.FLAG_SEED_SPLIT, seed, 0) for seed in (2, 3)
+                     for nt in (128, 256)]
     if w.d > 128:   # generic tile kernel: stream several increments per tile (two stages <= 160 KB)
-        variants += [(dade.SCHED_TILE, 8, tile, 128, 0, 0, sd) for tile in (64, 128) for sd in (64, 128, 256)
-                     if tile * sd * 8 <= 160 * 1024]
+        variants += [(dade.SCHED_TILE, 8, tile, nt, 0, 0, sd) for tile in (64, 128) for sd in (64, 128, 256)
+                     for nt in (128, 256) if tile * sd * 8 <= 160 * 1024]
     for dd in (16, 32, 64):
         for alpha in (0.05, 0.1, 0.2, 0.3):
             for schedule, spec, tile, threads, fl, seed, sd in variants:
@@ -719,6 +729,7 @@ def run_ours(args):
                        "stage_dims": point.get("stage_dims") or None,
                        "lead_prefilter": ({"format": args.lead, "dims": ld} if use_lead else None),
                        "flags": {"query_order": bool(point["flags"] & dade.FLAG_QUERY_ORDER),
+                                 "seed_split": bool(point["flags"] & dade.FLAG_SEED_SPLIT),
                                  "row_tail_from": tf if point["flags"] & dade.FLAG_ROW_TAIL else None},
                        "l2": f"index {n * w.d * 4 / 2**20:.0f} MB > L2; 256 MB flush written between timed steps",
                        "parallelism": f"replicas x{world}"},

@@ -106,9 +106,14 @@ enum {
                                       (DADE mode, tile schedule, min(delta_d, D_pad) <= lead_dims) */
     DADE_FLAG_QUERY_ORDER = 4,     /* run the queries grouped by their first probed list (results are
                                       the same in any order; grouped, they share list rows in L2) */
-    DADE_FLAG_ROW_TAIL = 8         /* a candidate that survives the first increment reads its dims from
+    DADE_FLAG_ROW_TAIL = 8,        /* a candidate that survives the first increment reads its dims from
                                       tail_from on from the index's row-major copy: one contiguous row
                                       instead of one 64-byte piece per 16-dim slab.  Same results. */
+    DADE_FLAG_SEED_SPLIT = 16      /* DADE_SCHED_SEEDED: every pass with r frozen (the lists after the
+                                      seeds; with whole-list tiles, each seed epoch too) runs query-major
+                                      on the tile kernel, each query's lists split into parts over
+                                      several thread blocks (the candidates are independent there),
+                                      instead of list-major.  Same tests and thresholds. */
 };
 
 /*

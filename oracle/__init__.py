@@ -266,3 +266,56 @@ class Index:
         eps = self.eps(alpha, delta_d) if prune else None
         return self.o.search(self.Xr, self.assign, self.cent, self.lam, Qr, K, nprobe, delta_d, eps,
                              schedule, tile, lag, seed=seed)
+
+
+class SampledIndex:
+    """The oracle's index for a sample of queries over a full-size base.
+
+    The same steps as ``Index`` with a given list assignment -- PCA over all
+    N objects (Section 3.2, Eq. 10-12), list centroids as member means, the
+    eps sample of the given pairs (Eq. 14) -- but only the objects a search
+    of the sampled queries can reach are rotated: the members of the lists
+    those queries probe (Section 3.4) and the sampled pairs' objects.  A list
+    centroid is computed as W^T (m - mu) from the list's raw FP64 mean m,
+    which is the mean of the rotated members (the rotation is affine); the
+    sums use numpy's reduction as a library step.  ``search`` returns ids of
+    the full base."""
+
+    def __init__(self, base, assign, n_clusters, pairs, queries, nprobe, oracle: Oracle | None = None,
+                 eps_step=16):
+        o = self.o = oracle or get()
+        X = np.ascontiguousarray(base, np.float32)
+        n, D = X.shape
+        self.D, self.nc = D, int(n_clusters)
+        self.mu, self.W, self.lam = o.pca(X)
+        assign = np.ascontiguousarray(assign, np.int32)
+        counts = np.bincount(assign, minlength=self.nc)
+        if (counts == 0).any():
+            raise ValueError("every list must have members")
+        order = np.argsort(assign, kind="stable")
+        starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+        means = np.add.reduceat(X[order], starts, axis=0, dtype=np.float64) / counts[:, None]
+        self.cent = (means - self.mu) @ self.W
+        self.Qr = o.rotate(queries, self.mu, self.W)
+        self.probe, self.probe_tie = o.probe(self.Qr, self.cent, nprobe)
+        lists = np.unique(self.probe)
+        self.rows = np.flatnonzero(np.isin(assign, lists))      # ascending ids: list order kept
+        self.Xr = o.rotate(X[self.rows], self.mu, self.W)
+        self.assign = assign[self.rows]
+        pairs = np.ascontiguousarray(pairs, np.int64).reshape(-1, 2)
+        prow, pinv = np.unique(pairs.ravel(), return_inverse=True)
+        self.dlist = list(range(eps_step, D, eps_step))
+        self.rho = o.eps_sample(o.rotate(X[prow], self.mu, self.W), self.lam, pinv.reshape(-1, 2), self.dlist)
+
+    def eps(self, alpha, delta_d):
+        eps = np.full(self.D + 1, np.nan)
+        for d in increments(self.D, delta_d):
+            eps[d] = self.o.eps_quantile(self.rho[self.dlist.index(d)], alpha)
+        return eps
+
+    def search(self, K, nprobe, delta_d, alpha, schedule=TILE, tile=128, prune=True, lag=0, seed=0):
+        eps = self.eps(alpha, delta_d) if prune else None
+        ids, dists, stats, flags = self.o.search(self.Xr, self.assign, self.cent, self.lam, self.Qr, K, nprobe,
+                                                 delta_d, eps, schedule, tile, lag, seed=seed)
+        ids = np.where(ids >= 0, self.rows[np.maximum(ids, 0)], -1)
+        return ids, dists, stats, flags

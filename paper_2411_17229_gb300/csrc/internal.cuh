@@ -158,6 +158,13 @@ struct ScanParams {
     int32_t pstride;         // row stride of probe (0: nprobe)
     int32_t seed_lists;      // DADE_SCHED_SEEDED
     int32_t stage_dims;      // FP32 DADE tile kernel: dims staged per tile (0: delta_d)
+    int32_t seed_split;      // SEEDED: lists after the seeds run query-major, split over CTAs
+    // split mode of the tile kernel (parts > 0; see ScanArgs)
+    int32_t parts, c0;
+    const float *r2src;
+    unsigned long long *acc;
+    int *acnt;
+    int64_t cap;
     float coef[DADE_MAX_DIM / DADE_BLOCK];   // per increment; prune iff P > coef[j] * r2
     int64_t *ids;            // [nq][k]
     float *dists;            // [nq][k]

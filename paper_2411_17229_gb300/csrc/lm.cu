@@ -710,6 +710,63 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     return launch_check("k_lm_merge");
 }
 
+// The seeded schedule with the lists after the seeds run query-major.  The
+// first S lists: in the tile schedule, straight into the outputs; or, with
+// whole-list tiles, as S threshold epochs (list j of every query tested
+// against r after lists 0..j-1, r = +inf for list 0).  Then every query's
+// later lists, with r frozen at the K-th distance after the seeds.  Wherever
+// r is frozen the candidates are independent, so those passes run the tile
+// kernel in split mode: each query's lists cut into parts over several CTAs
+// (enough for about eight waves), each appending what it accepts to the
+// query's buffer, then one merge into the K best.  The execution tile there
+// does not change the results (128 rows for whole-list epochs).
+static dade_status seeded_split(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s) {
+    const int S = p.seed_lists, np = p.nprobe, late = np - S;
+    const bool whole = p.tile >= ix->max_list;
+    Workspace &w = ws(ix);
+    const int64_t cap = (int64_t)late * std::max(ix->max_list, 1);   // >= one list (late >= 1)
+    DADE_TRY(w.lm_acc.ensure(sizeof(unsigned long long) * (size_t)(nq * cap)));
+    DADE_TRY(w.lm_acnt.ensure(sizeof(int) * (size_t)nq));
+    int dev = 0, sms = 0;
+    DADE_TRY_CUDA(cudaGetDevice(&dev));
+    DADE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t slots = (int64_t)sms * (768 / (p.threads == 256 ? 256 : 128));
+    ScanParams base = p;
+    base.schedule = DADE_SCHED_TILE;
+    base.seed_split = 0;
+    base.pstride = np;
+    if (whole) base.tile = 128;
+    base.r2src = p.dists;
+    base.acc = w.lm_acc.as<unsigned long long>();
+    base.acnt = w.lm_acnt.as<int>();
+    base.cap = cap;
+    auto frozen_pass = [&](int c0, int n, int parts) -> dade_status {
+        DADE_TRY_CUDA(cudaMemsetAsync(w.lm_acnt.p, 0, sizeof(int) * (size_t)nq, s));
+        ScanParams q = base;
+        q.c0 = c0;
+        q.nprobe = n;
+        q.parts = parts;
+        DADE_TRY(scan(ix, nq, q, s));
+        k_lm_merge<<<(unsigned)nq, MT, 0, s>>>(p.ids, p.dists, p.k, base.acc, base.acnt, cap);
+        return launch_check("k_lm_merge");
+    };
+    if (whole) {
+        k_lm_reset<<<grid_of(nq * (int64_t)p.k, 256), 256, 0, s>>>(p.ids, p.dists, nq * (int64_t)p.k);
+        DADE_TRY(launch_check("k_lm_reset"));
+        if (p.stats) DADE_TRY_CUDA(cudaMemsetAsync(p.stats, 0, sizeof(int64_t) * 4 * (size_t)nq, s));
+        if (p.lead_stats) DADE_TRY_CUDA(cudaMemsetAsync(p.lead_stats, 0, sizeof(int64_t) * (size_t)nq, s));
+        for (int j = 0; j < S; ++j) DADE_TRY(frozen_pass(j, 1, 1));
+    } else {
+        ScanParams p1 = p;
+        p1.nprobe = S;
+        p1.pstride = np;
+        p1.schedule = DADE_SCHED_TILE;
+        p1.seed_split = 0;
+        DADE_TRY(scan(ix, nq, p1, s));
+    }
+    return frozen_pass(S, late, (int)std::min<int64_t>(late, std::max<int64_t>(1, (8 * slots + nq - 1) / nq)));
+}
+
 // The seeded schedule for queries [0, nq) of p (see the file comment).  When
 // the tile holds every list (tile >= longest list), each of the first S lists
 // is one threshold epoch: list j of every query is tested against r after
@@ -722,13 +779,13 @@ dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, c
     const int np = p.nprobe;
     const bool fd = p.mode == DADE_MODE_FD;
     const int gb = fd ? LNB : std::min(p.delta_d / 16, ix->nb);
+    const bool whole = p.tile >= ix->max_list;
     const bool ok = ix->nb == LNB ? (gb == 1 || gb == 2 || gb == 4 || gb == 8)
                                   : (ix->nb > LNB && (gb == 1 || gb == 2 || gb == 4 || gb == 8));
-    if (!ok) {
-        set_error("the seeded schedule needs D > 112 and delta_d in {16, 32, 64, 128} (or >= D when D <= 128)");
-        return DADE_EUNSUPPORTED;
-    }
-    if (p.tile >= ix->max_list) {
+    // the list-major kernels cover D > 112 with delta_d of 1, 2, 4 or 8 blocks; elsewhere
+    // the passes with r frozen run query-major (the same tests, thresholds and results)
+    if (p.seed_split || !ok) return seeded_split(ix, nq, p, s);
+    if (whole) {
         k_lm_reset<<<grid_of(nq * (int64_t)p.k, 256), 256, 0, s>>>(p.ids, p.dists, nq * (int64_t)p.k);
         DADE_TRY(launch_check("k_lm_reset"));
         if (p.stats) DADE_TRY_CUDA(cudaMemsetAsync(p.stats, 0, sizeof(int64_t) * 4 * (size_t)nq, s));

@@ -65,7 +65,11 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
     unsigned long long *top0 = reinterpret_cast<unsigned long long *>(smem + L.top);
     unsigned long long *top1 = top0 + a.k;
 
-    const int32_t *plist = a.probe + qi * a.pstride;
+    const int32_t *plist = a.probe + qi * a.pstride + a.c0;
+    // split mode: this CTA's part of the probe positions
+    const int part = a.parts > 0 ? (int)(blockIdx.x % (unsigned)a.parts) : 0;
+    const int pbeg = a.parts > 0 ? (int)((int64_t)a.nprobe * part / a.parts) : 0;
+    const int pend = a.parts > 0 ? (int)((int64_t)a.nprobe * (part + 1) / a.parts) : a.nprobe;
     for (int k = tid; k < a.dp; k += NT) qv[k] = k < a.d ? a.q_rot[qi * a.q_stride + k] : 0.f;
     for (int p = tid; p < min(a.nprobe, PMETA); p += NT) {
         const ListMeta m = a.meta[plist[p]];
@@ -76,7 +80,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
         fence_mbar_init();
         s_ntop = 0;
         s_cur = 0;
-        s_r2 = INFINITY;
+        s_r2 = a.r2src ? a.r2src[qi * a.k + a.k - 1] : INFINITY;
     }
     if (STATS && tid < 4) s_stats[tid] = 0;
     if (tid == 0) s_lead = 0;
@@ -94,12 +98,12 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
             issue(a, smeta, plist, c, slot, stage, bars);
         }
     };
-    Cur cc{0, 0, 0};
+    Cur cc{pbeg, 0, 0};
     normalize(cc, a, smeta, plist);
     Cur ic = cc;          // issue cursor (thread 0 only)
     int issued = 0;       // units issued (thread 0 only)
     if (tid == 0)
-        for (int s = 0; s < a.ns && ic.p < a.nprobe; ++s) {
+        for (int s = 0; s < a.ns && ic.p < pend; ++s) {
             issue_unit(ic, s);
             advance(ic, units, a, smeta, plist);
             ++issued;
@@ -108,7 +112,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
     int unit = 0;
     bool aborted = false;
 
-    while (cc.p < a.nprobe) {
+    while (cc.p < pend) {
         const int4 m = meta_of(a, smeta, plist, cc.p);
         const int tn = min(a.tile, m.z - cc.i0);
         const int nit = (tn + NQUAD - 1) / NQUAD;
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
                     if (it < nit && c < tn) acc[it] += row_part(st + c * 16 + lq * 4, (int64_t)a.tile * 16, qv, b0, b1, lq, false);
                 }
                 __syncthreads();
-                if (tid == 0 && ic.p < a.nprobe) {
+                if (tid == 0 && ic.p < pend) {
                     issue_unit(ic, slot);
                     advance(ic, units, a, smeta, plist);
                     ++issued;
@@ -243,7 +247,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
                 }
             }
             __syncthreads();
-            if (tid == 0 && ic.p < a.nprobe) {
+            if (tid == 0 && ic.p < pend) {
                 issue_unit(ic, slot);
                 advance(ic, units, a, smeta, plist);
                 ++issued;
@@ -308,7 +312,18 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
 
         // ---- merge accepted candidates into the K best ------------------------------
         const int nF = s_cntF;
-        if (nF > 0) {
+        if (a.parts > 0) {   // split mode: r stays frozen; accepted keys go to the query's buffer
+            __shared__ int s_abase;
+            if (nF > 0) {
+                if (tid == 0) s_abase = atomicAdd(&a.acnt[qi], nF);
+                __syncthreads();
+                for (int t = tid; t < nF; t += NT) {
+                    const Surv f = fl[t];
+                    const unsigned id = (unsigned)a.ids[(int64_t)(unsigned)m.y + cc.i0 + f.idx];
+                    a.acc[qi * a.cap + s_abase + t] = ((unsigned long long)__float_as_uint(f.p) << 32) | id;
+                }
+            }
+        } else if (nF > 0) {
             for (int t = tid; t < nF; t += NT) {
                 const Surv f = fl[t];
                 const unsigned id = (unsigned)a.ids[(int64_t)(unsigned)m.y + cc.i0 + f.idx];
@@ -357,7 +372,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
     }
     const int nt = s_ntop;
     const unsigned long long *R = s_cur ? top1 : top0;
-    for (int t = tid; t < a.k; t += NT) {
+    for (int t = tid; a.parts == 0 && t < a.k; t += NT) {
         int64_t id = -1;
         float dv = INFINITY;
         if (t < nt) {
@@ -375,12 +390,20 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
             atomicAdd(&s_stats[3], st_prn);
         }
         __syncthreads();
-        if (tid < 4) a.stats[qi * 4 + tid] = (int64_t)s_stats[tid];
+        if (tid < 4) {
+            if (a.parts > 0)   // added to the seed lists' counts by every part
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[qi * 4 + tid]), s_stats[tid]);
+            else
+                a.stats[qi * 4 + tid] = (int64_t)s_stats[tid];
+        }
     }
     if (LF != 0 && a.lead_stats) {
         if (st_lead) atomicAdd(&s_lead, st_lead);
         __syncthreads();
-        if (tid == 0) a.lead_stats[qi] = (int64_t)s_lead;
+        if (tid == 0) {
+            if (a.parts > 0) atomicAdd(reinterpret_cast<unsigned long long *>(&a.lead_stats[qi]), s_lead);
+            else a.lead_stats[qi] = (int64_t)s_lead;
+        }
     }
 }
 
@@ -438,6 +461,14 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     a.err = ix->errflag.as<int>();
     a.q_stride = p.q_stride;
     a.nprobe = p.nprobe;
+    if (p.parts > 0) {
+        a.parts = p.parts;
+        a.c0 = p.c0;
+        a.r2src = p.r2src;
+        a.acc = p.acc;
+        a.acnt = p.acnt;
+        a.cap = p.cap;
+    }
     a.pstride = p.pstride > 0 ? p.pstride : p.nprobe;
     a.d = ix->d;
     a.dp = ix->dp;
@@ -470,16 +501,18 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
         a.lead_slots = ix->slots;
         a.lead_nb = ix->lead_nb;
     }
-    if (!fd && !lf && a.ub == a.gb && p.schedule == DADE_SCHED_PIPELINED && a.n_inc <= pipe_depth_limit())
+    const bool plain = a.ub == a.gb && a.parts == 0;   // the specialised kernels run neither mode
+    if (!fd && !lf && plain && p.schedule == DADE_SCHED_PIPELINED && a.n_inc <= pipe_depth_limit())
         return scan_pipelined(a, nq, p.threads, s);
-    if (scan_fast_applies(a, fd) && !p.generic && a.ub == a.gb) return scan_fast(a, nq, fd, p.threads, lf, s);
+    if (scan_fast_applies(a, fd) && !p.generic && plain) return scan_fast(a, nq, fd, p.threads, lf, s);
     const SmemLayout L = layout(a.dp, a.tile, a.ub, a.ns, a.k, a.nprobe, lf != 0);
     if (L.total > 227 * 1024) {
         set_error("scan configuration needs more than 227 KB of shared memory (reduce tile or delta_d)");
         return DADE_EUNSUPPORTED;
     }
-    if (p.threads == 256) return launch_nt<256>(a, nq, L.total, fd, p.stats != nullptr, lf, s);
-    return launch_nt<128>(a, nq, L.total, fd, p.stats != nullptr, lf, s);
+    const int64_t ctas = nq * std::max(a.parts, 1);
+    if (p.threads == 256) return launch_nt<256>(a, ctas, L.total, fd, p.stats != nullptr, lf, s);
+    return launch_nt<128>(a, ctas, L.total, fd, p.stats != nullptr, lf, s);
 }
 
 } // namespace dade

@@ -48,11 +48,20 @@ struct ScanArgs {
     const int32_t *order;        // CTA b runs query order[b] (null: query b)
     const float *tail;           // row-major copy of blocks >= tail_nb0 (null: none)
     int tail_nb0, tail_w;
+    // split mode (parts > 0): r frozen at r2src[q][k - 1]; CTA b runs part b % parts of the
+    // probe positions [c0, c0 + nprobe) of query b / parts and appends what it accepts
+    // to acc[q][cap] (count acnt[q]) instead of keeping a K-best list
+    const float *r2src;
+    unsigned long long *acc;
+    int *acnt;
+    int64_t cap;
+    int parts, c0;
 };
 
 // The query a CTA runs.
 __device__ __forceinline__ int64_t cta_query(const ScanArgs &a) {
-    return a.order ? (int64_t)a.order[blockIdx.x] : (int64_t)blockIdx.x;
+    const unsigned b = a.parts > 0 ? blockIdx.x / (unsigned)a.parts : blockIdx.x;
+    return a.order ? (int64_t)a.order[b] : (int64_t)b;
 }
 
 // ---------------------------------------------------------- PTX helpers ----

@@ -164,3 +164,17 @@ def zipf_assign(n: int, n_lists: int, s: float = 1.1, seed: int = SEED_BASE + 7)
     wts = wts[rng.permutation(n_lists)]
     wts /= wts.sum()
     return rng.choice(n_lists, size=n, p=wts).astype(np.int32)
+
+
+def component_lists(labels: np.ndarray, n_lists: int, seed: int = SEED_BASE + 11) -> np.ndarray:
+    """Seeded list labels that follow the mixture: each component's members
+    are dealt uniformly at random to n_lists / n_components lists of their
+    own (list = component * per + draw).  A fixed list assignment that both
+    sides of a full-size comparison can share."""
+    labels = np.asarray(labels, np.int64)
+    n_comp = int(labels.max()) + 1
+    per = n_lists // n_comp
+    if per < 1 or per * n_comp != n_lists:
+        raise ValueError("n_lists must be a multiple of the number of components")
+    rng = np.random.default_rng(seed)
+    return (labels * per + rng.integers(0, per, size=labels.size)).astype(np.int32)

@@ -514,4 +514,28 @@ def pin_exact_knn(o):
     assert _rel(dists, bd) < 1e-12
 
 
+def pin_sampled_index(o):
+    """The sampled index (PCA over all objects, only the reachable rows
+    rotated, centroids from raw means) answers exactly as the full index."""
+    import oracle
+    w = synth.Workload("pin_mix", 4000, 48, 12, 1.0, 8, 0.0, 3.0, 1.0, False, False, 32, (6,), 10, (16,), 0.1)
+    X, Q, lab = synth.make(w)
+    assign = synth.component_lists(lab, 32)
+    assert np.array_equal(assign // 4, lab)
+    pairs = synth.eps_pairs(4000, 3000, seed=141)
+    full = oracle.Index(X, n_clusters=32, assign=assign, pairs=pairs, oracle=o)
+    samp = oracle.SampledIndex(X, assign, 32, pairs, Q, 6, oracle=o)
+    assert samp.rows.size < 4000
+    for dd, seed, tile in ((16, 0, 64), (32, 2, 128), (16, 1, 1 << 20)):
+        a = full.search(Q, 10, 6, dd, 0.1, tile=tile, seed=seed)
+        b = samp.search(10, 6, dd, 0.1, tile=tile, seed=seed)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+        assert _rel(a[1], b[1]) < 1e-11
+    # every list probed, no pruning: exact nearest neighbours
+    allp = oracle.SampledIndex(X, assign, 32, pairs, Q, 32, oracle=o)
+    ids, dists, _, _ = allp.search(10, 32, 16, 0.1, prune=False)
+    bid, bd = _brute(X.astype(np.float64), Q.astype(np.float64), 10)
+    assert np.array_equal(ids, bid) and _rel(dists, bd) < 1e-10
+
+
 ALL = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

@@ -1,0 +1,159 @@
+"""Parity at the benchmark sizes (GPU only).
+
+Each workload is generated at its full size and indexed by both sides with
+the same seeded list assignment (every mixture component's members dealt to
+lists of their own) and the same eps pairs.  The CUDA path then runs the
+whole query batch in the launch configuration the benchmark times (rotate,
+probe, scan; the benchmark's schedule, tile, threads, delta_d, alpha and
+flags), and a seeded sample of its queries is compared with the oracle's
+sampled index element by element, under the tolerance of ``parity.py``.
+Every query of the batch is also checked against properties that hold at
+any size: distinct ids in range, ascending distances, and each distance
+equal to the FP64 squared distance of the raw vectors (the rotation is an
+isometry, Lemma 1).  The serving workload runs through the request server,
+with per-request K and nprobe.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import parity
+from paper_2411_17229_gb300 import dade, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+N_SAMPLE = 12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_17229_gb300 import build
+    build.build()
+
+
+def _build(w, n_pairs, **kw):
+    base, queries, labels = synth.make(w)
+    assign = synth.component_lists(labels, w.n_clusters)
+    pairs = synth.eps_pairs(w.n, n_pairs)
+    ix = dade.Index(torch.from_numpy(base).cuda(), w.n_clusters, assign=assign, pairs=pairs, **kw)
+    return base, queries, assign, pairs, ix
+
+
+def _check_properties(base, queries, ids, dists, scale):
+    """Any size: ids distinct and in range, ascending, distances exact."""
+    nq, K = ids.shape
+    valid = ids >= 0
+    assert valid.all(), "fewer than K results"
+    assert (ids < base.shape[0]).all()
+    srt = np.sort(ids, axis=1)
+    assert (srt[:, 1:] != srt[:, :-1]).all(), "repeated id in a result"
+    assert (np.diff(dists, axis=1) >= 0).all(), "distances not ascending"
+    for q0 in range(0, nq, 256):
+        q1 = min(nq, q0 + 256)
+        diff = base[ids[q0:q1]].astype(np.float64) - queries[q0:q1, None, :].astype(np.float64)
+        ex = (diff ** 2).sum(-1)
+        err = np.abs(dists[q0:q1].astype(np.float64) - ex)
+        assert (err <= parity.RTOL * ex + parity.ATOL_REL * scale).all(), f"distance error {err.max()}"
+
+
+def _scan_batch(ix, queries, K, pt):
+    """The benchmark's step: rotate, probe, scan over the whole batch."""
+    q = torch.from_numpy(queries).cuda()
+    nq = q.shape[0]
+    qr = torch.empty_like(q)
+    pr = torch.empty(nq, pt["nprobe"], dtype=torch.int32, device="cuda")
+    ids = torch.empty(nq, K, dtype=torch.int64, device="cuda")
+    d = torch.empty(nq, K, dtype=torch.float32, device="cuda")
+    ix.rotate(q, qr)
+    ix.probe(qr, pt["nprobe"], pr)
+    ix.scan(qr, pr, K, pt["alpha"], pt["delta_d"], ids, d, tile=pt["tile"], threads=pt["threads"],
+            schedule=pt["schedule"], seed_lists=pt["seed_lists"], flags=pt["flags"])
+    ix.sync()
+    return pr.cpu().numpy(), ids.cpu().numpy(), d.cpu().numpy()
+
+
+def _run_batch_case(wname, pt, n_pairs, **build_kw):
+    w = synth.WORKLOADS[wname]
+    base, queries, assign, pairs, ix = _build(w, n_pairs, **build_kw)
+    K = w.k
+    probe, ids, dists = _scan_batch(ix, queries, K, pt)
+    sample = np.sort(np.random.default_rng(17).choice(queries.shape[0], N_SAMPLE, replace=False))
+    orc = oracle.SampledIndex(base, assign, w.n_clusters, pairs, queries[sample], pt["nprobe"])
+    scale = float(orc.lam.sum())   # mean squared norm of the rotated base (trace of the covariance)
+    # the probe (Section 3.4): the oracle's nearest lists, by (distance, list id)
+    same = [np.array_equal(probe[s], orc.probe[i]) for i, s in enumerate(sample) if not orc.probe_tie[i]]
+    assert all(same) and len(same) >= N_SAMPLE // 2
+    seed = pt["seed_lists"] if pt["schedule"] == dade.SCHED_SEEDED else 0
+    o_ids, o_d, _, oflags = orc.search(K, pt["nprobe"], pt["delta_d"], pt["alpha"], tile=pt["tile"], seed=seed)
+
+    def exact_d(i, sel):
+        return ((base[sel].astype(np.float64) - queries[sample[i]].astype(np.float64)) ** 2).sum(-1)
+
+    # integer-valued data (C2) has exactly equal distances, and K = 100 over ~5,000
+    # candidates makes thousands of threshold decisions per query: more queries
+    # carry a near-tie flag (each is still validated) than in the small cases
+    parity.compare(ids[sample], dists[sample], o_ids, o_d, oflags, scale, exact_d, max_flagged_frac=0.5)
+    _check_properties(base, queries, ids, dists, scale)
+    ix.close()
+
+
+def test_c2_full_size_benchmark_point():
+    """1M x 128 integer mixture, 10,000 queries, K = 100, at the benchmark's
+    point: nprobe 20, seeded schedule (2 lists), tile 256, delta_d 64,
+    alpha 0.3, query order and row tail; index with the BF16 lead copy and
+    the row-major tail from dim 32, as the benchmark builds it."""
+    pt = {"nprobe": 20, "alpha": 0.3, "delta_d": 64, "tile": 256, "threads": 128, "schedule": dade.SCHED_SEEDED,
+          "seed_lists": 2, "flags": dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL}
+    _run_batch_case("c2_mix_1m_d128", pt, 100000, lead_format=dade.LEAD_BF16, lead_dims=64, tail_from=32)
+
+
+def test_c3_full_size_benchmark_point():
+    """1M x 960 mixture, 1,000 queries, K = 10, at the benchmark's point:
+    nprobe 24, seeded schedule (3 lists) with the later lists split over
+    thread blocks, tile 128, 256 threads, delta_d 32, alpha 0.2."""
+    pt = {"nprobe": 24, "alpha": 0.2, "delta_d": 32, "tile": 128, "threads": 256, "schedule": dade.SCHED_SEEDED,
+          "seed_lists": 3, "flags": dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL | dade.FLAG_SEED_SPLIT}
+    _run_batch_case("c3_mix_1m_d960", pt, 20000, lead_format=dade.LEAD_BF16, lead_dims=64, tail_from=32)
+
+
+def test_c5_full_size_serving():
+    """5M x 256 mixture, 8,192 lists, served: 240 single-query requests with
+    K in {1, 10, 100} and nprobe in {16, 64, 128} drawn per request, all in
+    flight together on the request server (4 slots, batches up to 1,024);
+    sampled requests against the oracle with their own K and nprobe."""
+    w = synth.WORKLOADS["c5_mix_5m_d256"]
+    base, queries, assign, pairs, ix = _build(w, 20000, tail_from=32)
+    rng = np.random.default_rng(23)
+    n_req = 240
+    picks = rng.choice(queries.shape[0], n_req, replace=False)
+    ks = rng.choice([1, 10, 100], n_req)
+    nps = rng.choice([16, 64, 128], n_req)
+    alpha, delta_d = 0.1, 32
+    srv = dade.Server(ix, slots=4, max_batch=1024, max_k=100, max_nprobe=128, tile=128, threads=128)
+    tickets = [srv.submit(queries[picks[i]:picks[i] + 1], int(ks[i]), int(nps[i]), alpha, delta_d)
+               for i in range(n_req)]
+    res = [srv.result(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["requests_done"] == n_req and st["batches"] < n_req
+    sample = np.sort(rng.choice(n_req, N_SAMPLE, replace=False))
+    orc = oracle.SampledIndex(base, assign, w.n_clusters, pairs, queries[picks[sample]], 128)
+    scale = float(orc.lam.sum())
+    for K, nprobe in sorted({(int(ks[i]), int(nps[i])) for i in sample}):
+        rows = [j for j, i in enumerate(sample) if ks[i] == K and nps[i] == nprobe]
+        o_ids, o_d, _, oflags = orc.search(K, nprobe, delta_d, alpha, tile=128)
+        g_ids = np.stack([res[sample[j]][0][0] for j in rows])
+        g_d = np.stack([res[sample[j]][1][0] for j in rows])
+
+        def exact_d(i, sel, rows=rows):
+            q = queries[picks[sample[rows[i]]]].astype(np.float64)
+            return ((base[sel].astype(np.float64) - q) ** 2).sum(-1)
+
+        parity.compare(g_ids, g_d, o_ids[rows], o_d[rows], oflags[rows], scale, exact_d,
+                       max_flagged_frac=0.5)
+    for i in range(n_req):
+        _check_properties(base, queries[picks[i]:picks[i] + 1], res[i][0], res[i][1], scale)
+    ix.close()

@@ -6,6 +6,8 @@ assignment (uneven random lists, or mixture labels), so both sides scan the
 same lists; k-means itself is compared separately (test_kmeans_parity).
 Tolerances are those of tests/parity.py.
 """
+import itertools
+
 import numpy as np
 import pytest
 
@@ -278,7 +280,9 @@ def test_query_order_gives_same_results(c1, mode, delta_d, flags):
 
 
 @pytest.mark.parametrize("tail_from,delta_d,flags", [(64, 64, 0), (32, 32, 0), (16, 16, 0), (32, 64, dade.FLAG_LEAD),
-                                                     (48, 32, dade.FLAG_GENERIC_KERNEL)])
+                                                     (48, 32, dade.FLAG_GENERIC_KERNEL),
+                                                     (16, 16, dade.FLAG_GENERIC_KERNEL | dade.FLAG_LEAD),
+                                                     (112, 64, dade.FLAG_GENERIC_KERNEL)])
 def test_row_tail_gives_same_results(tail_from, delta_d, flags):
     """Survivors reading their later dims from the row-major tail copy get
     the same bits as from the dimension-blocked slabs."""
@@ -311,7 +315,8 @@ def test_row_tail_gives_same_results(tail_from, delta_d, flags):
     (100, 16, 0.3, 64, 4096, 1),
     (1, 6, 0.2, 16, 4096, 5),
 ])
-@pytest.mark.parametrize("flags", [0, dade.FLAG_QUERY_ORDER])
+@pytest.mark.parametrize("flags", [0, dade.FLAG_QUERY_ORDER, dade.FLAG_SEED_SPLIT,
+                                   dade.FLAG_SEED_SPLIT | dade.FLAG_QUERY_ORDER])
 def test_seeded_schedule_parity(c1, k, nprobe, alpha, delta_d, tile, seed, flags):
     g_ids, g_d, g_st = c1.gpu_search(k, nprobe, alpha, delta_d, tile=tile, stats=True, schedule=dade.SCHED_SEEDED,
                                      seed_lists=seed, flags=flags)
@@ -330,6 +335,12 @@ def test_seeded_fd_is_fd(c1, k, nprobe, tile):
     a = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD)
     b = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD, schedule=dade.SCHED_SEEDED, seed_lists=1, tile=tile)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+    # split passes run the generic tile kernel, whose per-lane sums group 64 dims at a time
+    g = dade.FLAG_GENERIC_KERNEL
+    a = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD, flags=g)
+    b = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD, schedule=dade.SCHED_SEEDED, seed_lists=1, tile=tile,
+                      flags=g | dade.FLAG_SEED_SPLIT)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
 
 
 def test_seeded_schedule_mixture_and_limits():
@@ -347,12 +358,16 @@ def test_seeded_schedule_mixture_and_limits():
     a = case.gpu_search(10, 4, 0.1, 32, stats=True)
     b = case.gpu_search(10, 4, 0.1, 32, stats=True, schedule=dade.SCHED_SEEDED, seed_lists=4)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
-    # D = 64 (fewer than 8 blocks) is outside the list-major kernels
-    small = Case(*synth.make(synth.Workload("mix64", 3000, 64, 10, 1.0, 6, 0.0, 3.0, 1.0, False, False, 6, (4,),
-                                            10, (16,), 0.1))[:2], synth.zipf_assign(3000, 6, s=0.5), 6, n_pairs=1000)
-    with pytest.raises(dade.DadeError) as e:
-        small.gpu_search(5, 4, 0.1, 32, schedule=dade.SCHED_SEEDED, seed_lists=1)
-    assert e.value.status == dade.EUNSUPPORTED
+    # D = 64 and D = 40 (fewer than 8 blocks) are outside the list-major kernels: the
+    # passes with r frozen run query-major, tile and whole-list epochs alike
+    for d in (64, 40):
+        small = Case(*synth.make(synth.Workload(f"mix{d}", 3000, d, 10, 1.0, 6, 0.0, 3.0, 1.0, False, False, 6, (4,),
+                                                10, (16,), 0.1))[:2], synth.zipf_assign(3000, 6, s=0.5), 6,
+                     n_pairs=1000)
+        for tile, seed in ((64, 1), (1 << 20, 2)):
+            g_ids, g_d = small.gpu_search(5, 4, 0.1, 32, schedule=dade.SCHED_SEEDED, seed_lists=seed, tile=tile)
+            o_ids, o_d, _, oflags = small.oracle_search(5, 4, 0.1, 32, seed=seed, tile=tile)
+            parity.compare(g_ids, g_d, o_ids, o_d, oflags, small.scale, small.exact_d)
 
 
 @pytest.mark.parametrize("d,delta_d,seed,tile", [(160, 16, 2, 128), (160, 32, 1, 4096), (256, 64, 2, 128),
@@ -363,9 +378,9 @@ def test_seeded_schedule_any_dimension(d, delta_d, seed, tile):
     w = synth.Workload(f"mix{d}", 8000, d, 70, 1.0, 20, 0.0, 3.0, 1.0, False, False, 20, (4,), 10, (16,), 0.1)
     base, queries, labels = synth.make(w)
     case = Case(base, queries, labels, 20, n_pairs=4000)
-    for k, nprobe in ((10, 8), (60, 12)):
+    for (k, nprobe), fl in itertools.product(((10, 8), (60, 12)), (0, dade.FLAG_SEED_SPLIT)):
         g_ids, g_d, g_st = case.gpu_search(k, nprobe, 0.1, delta_d, tile=tile, stats=True,
-                                           schedule=dade.SCHED_SEEDED, seed_lists=seed)
+                                           schedule=dade.SCHED_SEEDED, seed_lists=seed, flags=fl)
         o_ids, o_d, o_st, oflags = case.oracle_search(k, nprobe, 0.1, delta_d, tile=tile, seed=seed)
         parity.compare(g_ids, g_d, o_ids, o_d, oflags, case.scale, case.exact_d)
         assert np.array_equal(g_st[:, 0], o_st[:, 0])
@@ -398,3 +413,69 @@ def test_staged_depth_gives_same_results(d, delta_d, stage):
     assert np.array_equal(out[0][2], out[1][2])
     o_ids, o_d, _, oflags = case.oracle_search(20, 6, 0.1, delta_d, tile=64)
     parity.compare(out[1][0], out[1][1], o_ids, o_d, oflags, case.scale, case.exact_d)
+
+
+@pytest.mark.parametrize("d,delta_d,tail_from,spec", [(160, 32, 32, 8), (256, 16, 64, 3), (200, 64, 16, 8),
+                                                      (960, 32, 32, 8)])
+def test_generic_kernel_row_tail_and_window(d, delta_d, tail_from, spec):
+    """D > 128 on the tile kernel, with and without the row-major tail in the
+    index and with several survivor window widths: same bits, same counters,
+    and oracle parity."""
+    n = 3000 if d > 512 else 6000
+    w = synth.Workload(f"tail{d}", n, d, 50, 1.0, 16, 0.0, 3.0, 1.0, False, False, 16, (4,), 10, (16,), 0.1)
+    base, queries, labels = synth.make(w)
+    case = Case(base, queries, labels, 16, n_pairs=3000)
+    ix = dade.Index(torch.from_numpy(base).cuda(), 16, assign=case.assign, pairs=case.pairs, tail_from=tail_from)
+    nq = queries.shape[0]
+    q_rot = torch.empty_like(case.q_dev)
+    ix.rotate(case.q_dev, q_rot)
+    out = []
+    for extra, sp in ((0, 8), (dade.FLAG_ROW_TAIL, 8), (dade.FLAG_ROW_TAIL, spec)):
+        ids = torch.empty(nq, 20, dtype=torch.int64, device="cuda")
+        dd = torch.empty(nq, 20, dtype=torch.float32, device="cuda")
+        st = torch.zeros(nq, 4, dtype=torch.int64, device="cuda")
+        ix.search(q_rot, 20, 6, 0.1, delta_d, ids, dd, tile=64, stats=st, spec=sp,
+                  flags=dade.FLAG_GENERIC_KERNEL | extra)
+        ix.sync()
+        out.append((ids.cpu().numpy(), dd.cpu().numpy(), st.cpu().numpy()))
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1].view(np.uint32), o[1].view(np.uint32))
+        assert np.array_equal(out[0][2], o[2])
+    o_ids, o_d, _, oflags = case.oracle_search(20, 6, 0.1, delta_d, tile=64)
+    parity.compare(out[0][0], out[0][1], o_ids, o_d, oflags, case.scale, case.exact_d)
+
+
+@pytest.mark.parametrize("delta_d,seed,flags", [(32, 2, 0), (16, 1, dade.FLAG_QUERY_ORDER), (64, 3, 0)])
+def test_seed_split_matches_list_major(c1, delta_d, seed, flags):
+    """The lists after the seeds, query-major and split over thread blocks,
+    against list-major: the same r, the same tests, so the same bits and
+    work counters."""
+    a = c1.gpu_search(50, 12, 0.1, delta_d, stats=True, schedule=dade.SCHED_SEEDED, seed_lists=seed, flags=flags)
+    b = c1.gpu_search(50, 12, 0.1, delta_d, stats=True, schedule=dade.SCHED_SEEDED, seed_lists=seed,
+                      flags=flags | dade.FLAG_SEED_SPLIT)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+    assert np.array_equal(a[2], b[2])
+
+
+def test_seed_split_with_prefilter():
+    """The split later lists with the low-precision prefilter: FP32 results
+    equal the FP32 path's, and the dropped-candidate counts add up over the
+    seed lists and every part."""
+    base, queries, _ = synth.make("c1_gauss_10k_d128", n=6000, nq=60)
+    assign = synth.zipf_assign(6000, 30, s=0.7)
+    ix = dade.Index(torch.from_numpy(base).cuda(), 30, assign=assign, eps_pairs=3000,
+                    lead_format=dade.LEAD_BF16, lead_dims=64)
+    q = torch.from_numpy(queries).cuda()
+    out = []
+    for fl in (dade.FLAG_SEED_SPLIT, dade.FLAG_SEED_SPLIT | dade.FLAG_LEAD):
+        ids = torch.empty(60, 20, dtype=torch.int64, device="cuda")
+        d = torch.empty(60, 20, dtype=torch.float32, device="cuda")
+        st = torch.zeros(60, 4, dtype=torch.int64, device="cuda")
+        ls = torch.zeros(60, dtype=torch.int64, device="cuda") if fl & dade.FLAG_LEAD else None
+        ix.query(q, 20, 10, 0.1, 32, ids, d, stats=st, flags=fl, schedule=dade.SCHED_SEEDED, seed_lists=2,
+                 tile=64, lead_stats=ls)
+        ix.sync()
+        out.append((ids.cpu().numpy(), d.cpu().numpy(), st.cpu().numpy(), None if ls is None else ls.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
+    assert np.array_equal(out[0][2][:, 0], out[1][2][:, 0])
+    assert (out[1][3] > 0).any() and (out[1][3] <= out[1][2][:, 0]).all()
