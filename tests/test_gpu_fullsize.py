@@ -92,10 +92,13 @@ def _run_batch_case(wname, pt, n_pairs, **build_kw):
     def exact_d(i, sel):
         return ((base[sel].astype(np.float64) - queries[sample[i]].astype(np.float64)) ** 2).sum(-1)
 
-    # integer-valued data (C2) has exactly equal distances, and K = 100 over ~5,000
-    # candidates makes thousands of threshold decisions per query: more queries
-    # carry a near-tie flag (each is still validated) than in the small cases
-    parity.compare(ids[sample], dists[sample], o_ids, o_d, oflags, scale, exact_d, max_flagged_frac=0.5)
+    # At full size a query makes 10^4..10^5 threshold decisions (and C2's integer
+    # data has exactly equal distances), so most sampled queries carry a near-tie
+    # flag.  Each flagged query is validated (distinct ids, exact distances,
+    # ascending, >= 90% of the oracle's ids), and at most a quarter of the sample
+    # may differ from the oracle's ids at all.
+    summary = parity.compare(ids[sample], dists[sample], o_ids, o_d, oflags, scale, exact_d, max_flagged_frac=1.0)
+    assert summary["flagged_mismatched"] <= N_SAMPLE // 4, summary
     _check_properties(base, queries, ids, dists, scale)
     ix.close()
 
@@ -142,6 +145,7 @@ def test_c5_full_size_serving():
     sample = np.sort(rng.choice(n_req, N_SAMPLE, replace=False))
     orc = oracle.SampledIndex(base, assign, w.n_clusters, pairs, queries[picks[sample]], 128)
     scale = float(orc.lam.sum())
+    mismatched = 0
     for K, nprobe in sorted({(int(ks[i]), int(nps[i])) for i in sample}):
         rows = [j for j, i in enumerate(sample) if ks[i] == K and nps[i] == nprobe]
         o_ids, o_d, _, oflags = orc.search(K, nprobe, delta_d, alpha, tile=128)
@@ -152,8 +156,10 @@ def test_c5_full_size_serving():
             q = queries[picks[sample[rows[i]]]].astype(np.float64)
             return ((base[sel].astype(np.float64) - q) ** 2).sum(-1)
 
-        parity.compare(g_ids, g_d, o_ids[rows], o_d[rows], oflags[rows], scale, exact_d,
-                       max_flagged_frac=0.5)
+        summary = parity.compare(g_ids, g_d, o_ids[rows], o_d[rows], oflags[rows], scale, exact_d,
+                                 max_flagged_frac=1.0)
+        mismatched += summary["flagged_mismatched"]
+    assert mismatched <= N_SAMPLE // 4
     for i in range(n_req):
         _check_properties(base, queries[picks[i]:picks[i] + 1], res[i][0], res[i][1], scale)
     ix.close()
