@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: fixed --point, no autotune, ground truth, baselines or e2e")
-    ap.add_argument("--point", default="nprobe=20,alpha=0.3,delta_d=64,tile=256,threads=128,schedule=2,seed_lists=2,"
+    ap.add_argument("--point", default="nprobe=20,alpha=0.8,delta_d=64,tile=128,threads=128,schedule=2,seed_lists=2,"
                                        "flags=12",
                     help="operating point of --profile (comma-separated key=value)")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server latency sweep")
@@ -151,7 +151,7 @@ def run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, 
 
     best = None
     scheds = [(0, 0, 256)] + ([(2, 2, 256), (2, 3, 256)] if list_major else [])
-    for eps0 in (0.5, 0.75, 1.0, 1.5, 2.1):
+    for eps0 in (0.25, 0.35, 0.5, 0.75, 1.0, 1.5, 2.1):
         for dd in (16, 32, 64):
             for sched, seed, tile in scheds:
                 for nprobe in [p for p in grid if p >= n0][:3]:
@@ -501,14 +501,17 @@ def run_ours(args):
     grid = [8, 12, 16, 20, 24, 28, 32, 40, 48, 64, 96, 128]
     fd_best, fd_rec = None, {}
     for nprobe in grid:              # FD time grows with nprobe: the first point reaching the target wins
-        fd_variants = [(128, 64, 0, 0), (128, 128, 0, 0), (256, 128, 0, 0)]
+        # FDScanning gets the same schedules: seeded FD is exact FD (r only selects)
+        fd_variants = [(128, 64, 0, 0, 0), (128, 128, 0, 0, 0), (256, 128, 0, 0, 0)]
         if (w.d + 15) // 16 >= 8:
-            fd_variants += [(256, 128, dade.SCHED_SEEDED, 1), (256, 128, dade.SCHED_SEEDED, 2),
-                            (256, 128, dade.SCHED_SEEDED, 3), (256, 1 << 20, dade.SCHED_SEEDED, 1),
-                            (256, 1 << 20, dade.SCHED_SEEDED, 2)]
-        for threads, tile, sched, seed in fd_variants:
+            fd_variants += [(256, 128, dade.SCHED_SEEDED, 1, 0), (256, 128, dade.SCHED_SEEDED, 2, 0),
+                            (256, 128, dade.SCHED_SEEDED, 3, 0), (256, 1 << 20, dade.SCHED_SEEDED, 1, 0),
+                            (256, 1 << 20, dade.SCHED_SEEDED, 2, 0)]
+        fd_variants += [(nt, 128, dade.SCHED_SEEDED, seed, dade.FLAG_SEED_SPLIT) for nt in (128, 256)
+                        for seed in (1, 2, 3)]
+        for threads, tile, sched, seed, fl in fd_variants:
             pt = {"mode": dade.MODE_FD, "nprobe": nprobe, "tile": tile, "threads": threads,
-                  "flags": dade.FLAG_QUERY_ORDER, "schedule": sched, "seed_lists": seed}
+                  "flags": dade.FLAG_QUERY_ORDER | fl, "schedule": sched, "seed_lists": seed}
             ms, rc = measure(pt)
             fd_rec[nprobe] = rc
             if rc >= RECALL_TARGET and (fd_best is None or ms < fd_best[0]):
@@ -532,7 +535,7 @@ def run_ours(args):
         variants += [(dade.SCHED_TILE, 8, tile, nt, 0, 0, sd) for tile in (64, 128) for sd in (64, 128, 256)
                      for nt in (128, 256) if tile * sd * 8 <= 160 * 1024]
     for dd in (16, 32, 64):
-        for alpha in (0.05, 0.1, 0.2, 0.3):
+        for alpha in (0.05, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8):
             for schedule, spec, tile, threads, fl, seed, sd in variants:
                     if sd and (sd <= dd or sd % dd):
                         continue
@@ -743,6 +746,7 @@ def run_ours(args):
                             "nprobe": fd_pt["nprobe"], "threads": fd_pt["threads"],
                             "schedule": {0: "tile", 2: "seeded"}[fd_pt.get("schedule", 0)],
                             "seed_lists": fd_pt.get("seed_lists") or None,
+                            "seed_split": bool(fd_pt.get("flags", 0) & dade.FLAG_SEED_SPLIT),
                             "ms_per_step": round(statistics.mean(fd_ms), 4)},
             "dade_vs_fd": round(value / world / fd_qps, 3),
             "adsampling": ads,
