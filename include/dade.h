@@ -211,6 +211,9 @@ typedef struct {
                                   at each increment inside; survivors then gather the rest.  Same
                                   results; a deeper stage trades gathers for streaming when most
                                   candidates outlive the first increments. */
+    int32_t list_chunk;        /* list-major passes of DADE_SCHED_SEEDED: rows of one list per work
+                                  item (0: 4096; else a multiple of 64); a long list becomes several
+                                  items run by different thread blocks.  Same results. */
 } dade_search_opts;
 
 /* Description of a built index. */

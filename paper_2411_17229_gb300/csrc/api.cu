@@ -106,7 +106,9 @@ dade_status check_device_errors(const dade_index *ix, cudaStream_t s) {
     DADE_TRY_CUDA(cudaStreamSynchronize(s));
     if (h != 0) {
         DADE_TRY_CUDA(cudaMemsetAsync(ix->errflag.p, 0, sizeof(int), s));
-        set_error("a bounded device-side wait gave up (status recorded by the scan kernel)");
+        set_error(h == DADE_ENOMEM ? "a query accepted more candidates than its accept buffer holds (65,536 per "
+                                     "pass; lower nprobe or K, or use the tile schedule)"
+                                   : "a bounded device-side wait gave up (status recorded by the scan kernel)");
         return (dade_status)h;
     }
     return DADE_OK;
@@ -141,6 +143,8 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
                        opts->schedule == DADE_SCHED_SEEDED,
                    "unknown schedule");
     DADE_CHECK_ARG(!opts || opts->seed_lists >= 0, "seed_lists < 0");
+    DADE_CHECK_ARG(!opts || opts->list_chunk == 0 || (opts->list_chunk >= 64 && opts->list_chunk % 64 == 0),
+                   "list_chunk must be 0 or a positive multiple of 64");
     DADE_CHECK_ARG(!opts || opts->stage_dims == 0 ||
                        (opts->stage_dims >= delta_d && delta_d > 0 && opts->stage_dims % delta_d == 0 &&
                         opts->stage_dims <= DADE_MAX_DIM),
@@ -207,6 +211,7 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.schedule = opts ? opts->schedule : DADE_SCHED_TILE;
     p.seed_lists = opts && opts->seed_lists > 0 ? opts->seed_lists : 2;
     p.stage_dims = opts ? opts->stage_dims : 0;
+    p.list_chunk = opts ? opts->list_chunk : 0;
     p.generic = opts ? (opts->flags & DADE_FLAG_GENERIC_KERNEL) != 0 : 0;
     p.use_lead = opts ? (opts->flags & DADE_FLAG_LEAD) != 0 : 0;
     p.use_tail = opts ? (opts->flags & DADE_FLAG_ROW_TAIL) != 0 : 0;

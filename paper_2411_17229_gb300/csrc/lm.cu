@@ -52,6 +52,7 @@ struct LmArgs {
     int64_t cap;
     int q_stride, nc, k, d, tail_nb0, tail_w;
     int nb, n_inc;               // 16-dim blocks of the layout, increments (k_lm_g)
+    int chunk_tiles;             // tiles of a list per work item (a long list is several items)
     float coef[DADE_MAX_DIM / DADE_BLOCK];   // prune iff P > coef[j] r^2 after increment j
 };
 
@@ -80,7 +81,11 @@ __device__ __forceinline__ void lm_append(const LmArgs &a, bool take, int q, uns
     int base = 0;
     if (lane == leader) base = atomicAdd(&a.acnt[q], __popc(mk));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (take) a.acc[(int64_t)q * a.cap + base + __popc(mk & ((1u << lane) - 1u))] = key;
+    const int64_t pos = (int64_t)base + __popc(mk & ((1u << lane) - 1u));
+    if (take) {
+        if (pos < a.cap) a.acc[(int64_t)q * a.cap + pos] = key;
+        else atomicExch(a.err, (int)DADE_ENOMEM);   // accept buffer full: the call reports it
+    }
 }
 
 template <int GB, bool STATS>
@@ -117,10 +122,14 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
             else hi = mid;
         }
         const int c = lo;
-        const int qb = a.lq_off[c] + (item - a.item_off[c]) * LG;
+        // item = (chunk of the list's tiles) x (group of up to LG of its queries)
+        const int ngroups = (a.lq_off[c + 1] - a.lq_off[c] + LG - 1) / LG;
+        const int local = item - a.item_off[c];
+        const int qb = a.lq_off[c] + (local % ngroups) * LG;
         const int ng = min(LG, a.lq_off[c + 1] - qb);
         const ListMeta m = a.meta[c];
-        const int ntile = (m.len + LT - 1) / LT;
+        const int t0 = (local / ngroups) * a.chunk_tiles;
+        const int ntile = min((m.len + LT - 1) / LT, t0 + a.chunk_tiles);   // end of this item's tiles
         auto issue = [&](int t) {   // thread 0: first-increment slabs of tile t
             const int buf = t & 1, i0 = t * LT, tn = min(LT, m.len - i0);
             const uint32_t bar = su32(&bars[buf]);
@@ -130,7 +139,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
                          a.data + m.base + (int64_t)b * m.np * 16 + (int64_t)i0 * 16, (uint32_t)(tn * 64), bar);
         };
         if (tid == 0)
-            for (int t = 0; t < 2 && t < ntile; ++t) issue(t);
+            for (int t = t0; t < t0 + 2 && t < ntile; ++t) issue(t);
         for (int g = tid; g < ng; g += LNT) {
             const int q = a.lq_items[qb + g];
             s_q[g] = q;
@@ -142,7 +151,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
         }
         __syncthreads();
 
-        for (int t = 0; t < ntile; ++t) {
+        for (int t = t0; t < ntile; ++t) {
             const int buf = t & 1;
             if (!wait_block(su32(&bars[buf]), used[buf] & 1u)) {
                 if (tid == 0) {
@@ -305,10 +314,14 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
             else hi = mid;
         }
         const int c = lo;
-        const int qb = a.lq_off[c] + (item - a.item_off[c]) * LG;
+        // item = (chunk of the list's tiles) x (group of up to LG of its queries)
+        const int ngroups = (a.lq_off[c + 1] - a.lq_off[c] + LG - 1) / LG;
+        const int local = item - a.item_off[c];
+        const int qb = a.lq_off[c] + (local % ngroups) * LG;
         const int ng = min(LG, a.lq_off[c + 1] - qb);
         const ListMeta m = a.meta[c];
-        const int ntile = (m.len + LT - 1) / LT;
+        const int t0 = (local / ngroups) * a.chunk_tiles;
+        const int ntile = min((m.len + LT - 1) / LT, t0 + a.chunk_tiles);   // end of this item's tiles
         auto issue = [&](int t) {
             const int buf = t & 1, i0 = t * LT, tn = min(LT, m.len - i0);
             const uint32_t bar = su32(&bars[buf]);
@@ -318,7 +331,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
                          a.data + m.base + (int64_t)b * m.np * 16 + (int64_t)i0 * 16, (uint32_t)(tn * 64), bar);
         };
         if (tid == 0)
-            for (int t = 0; t < 2 && t < ntile; ++t) issue(t);
+            for (int t = t0; t < t0 + 2 && t < ntile; ++t) issue(t);
         for (int g = tid; g < ng; g += LNT) {
             const int q = a.lq_items[qb + g];
             s_q[g] = q;
@@ -328,7 +341,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
             const int g = e / (16 * GB), kk = e % (16 * GB);
             qs[e] = kk < a.d ? a.q_rot[(int64_t)a.lq_items[qb + g] * a.q_stride + kk] : 0.f;
         }
-        for (int t = 0; t < ntile; ++t) {
+        for (int t = t0; t < ntile; ++t) {
             const int buf = t & 1;
             if (!wait_block(su32(&bars[buf]), used[buf] & 1u)) {
                 if (tid == 0) {
@@ -461,12 +474,15 @@ __global__ void k_lm_count(const int32_t *__restrict__ probe, int64_t nq, int np
     }
 }
 
-// items[c] = ceil(cnt[c] / LG); both arrays get a trailing 0 for the scans.
-__global__ void k_lm_items(const int *__restrict__ cnt, int nc, int *__restrict__ off, int *__restrict__ items) {
+// items[c] = ceil(cnt[c] / LG) query groups x ceil(tiles of c / chunk_tiles)
+// chunks; both arrays get a trailing 0 for the scans.
+__global__ void k_lm_items(const int *__restrict__ cnt, const ListMeta *__restrict__ meta, int nc, int chunk_tiles,
+                           int *__restrict__ off, int *__restrict__ items) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= nc; c += gridDim.x * blockDim.x) {
         const int v = c < nc ? cnt[c] : 0;
         off[c] = v;
-        items[c] = (v + LG - 1) / LG;
+        const int tiles = c < nc ? (meta[c].len + LT - 1) / LT : 0;
+        items[c] = v > 0 ? ((v + LG - 1) / LG) * max(1, (tiles + chunk_tiles - 1) / chunk_tiles) : 0;
     }
 }
 
@@ -514,7 +530,7 @@ __global__ void __launch_bounds__(MT) k_lm_merge(int64_t *__restrict__ ids, floa
         }
     }
     __syncthreads();
-    const int n1 = s_n1, n2 = acnt[q], n = n1 + n2;
+    const int n1 = s_n1, n2 = (int)min((int64_t)acnt[q], cap), n = n1 + n2;
     const unsigned long long *a2 = acc + q * cap;
     auto key = [&](int j) { return j < n1 ? s1[j] : a2[j - n1]; };
     unsigned long long bound = ~0ull;   // select every key when n <= k
@@ -649,6 +665,13 @@ dade_status launch_lm_gb(const LmArgs &a, int gb, cudaStream_t s) {
 // when the round starts (frozen for the round), then the K nearest of the
 // previous result and the round's accepted candidates.  gb = 8 with no
 // pruning (coef +inf) is FDScanning.
+// Accept-buffer entries per query for a pass over `lists` probe positions:
+// every candidate (lists x longest list) up to 65,536; a pass that accepts
+// more for one query (r = +inf over very long lists) reports DADE_ENOMEM.
+int64_t accept_cap(const dade_index *ix, int lists) {
+    return std::min<int64_t>((int64_t)lists * std::max(ix->max_list, 1), 1 << 16);
+}
+
 dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int c0, int c1, int gb, bool prune,
                      cudaStream_t s) {
     const int nc = ix->nc, np = p.nprobe;
@@ -659,7 +682,7 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     DADE_TRY(w.lm_items.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(pairs, 1) + 16));
     int32_t *lq_items = w.lm_items.as<int32_t>();
     unsigned *ctr = reinterpret_cast<unsigned *>(lq_items + std::max<int64_t>(pairs, 1));
-    const int64_t cap = (int64_t)(c1 - c0) * std::max(ix->max_list, 1);
+    const int64_t cap = accept_cap(ix, c1 - c0);
     DADE_TRY(w.lm_acc.ensure(sizeof(unsigned long long) * (size_t)(nq * cap)));
     DADE_TRY(w.lm_acnt.ensure(sizeof(int) * (size_t)nq));
     DADE_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(nc + 1), s));
@@ -667,7 +690,8 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     DADE_TRY_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned), s));
     k_lm_count<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, cnt);
     DADE_TRY(launch_check("k_lm_count"));
-    k_lm_items<<<grid_of(nc + 1, 256), 256, 0, s>>>(cnt, nc, off, items);
+    const int chunk_tiles = std::max(1, (p.list_chunk > 0 ? p.list_chunk : 4096) / LT);
+    k_lm_items<<<grid_of(nc + 1, 256), 256, 0, s>>>(cnt, ix->meta.as<ListMeta>(), nc, chunk_tiles, off, items);
     DADE_TRY(launch_check("k_lm_items"));
     DADE_TRY(exclusive_scan_int(off, nc + 1, s));
     DADE_TRY(exclusive_scan_int(items, nc + 1, s));
@@ -690,6 +714,7 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     a.err = ix->errflag.as<int>();
     a.cap = cap;
     a.q_stride = p.q_stride;
+    a.chunk_tiles = chunk_tiles;
     a.nc = nc;
     a.k = p.k;
     a.d = ix->d;
@@ -724,7 +749,7 @@ static dade_status seeded_split(const dade_index *ix, int64_t nq, const ScanPara
     const int S = p.seed_lists, np = p.nprobe, late = np - S;
     const bool whole = p.tile >= ix->max_list;
     Workspace &w = ws(ix);
-    const int64_t cap = (int64_t)late * std::max(ix->max_list, 1);   // >= one list (late >= 1)
+    const int64_t cap = accept_cap(ix, late);
     DADE_TRY(w.lm_acc.ensure(sizeof(unsigned long long) * (size_t)(nq * cap)));
     DADE_TRY(w.lm_acnt.ensure(sizeof(int) * (size_t)nq));
     int dev = 0, sms = 0;

@@ -320,7 +320,10 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
                 for (int t = tid; t < nF; t += NT) {
                     const Surv f = fl[t];
                     const unsigned id = (unsigned)a.ids[(int64_t)(unsigned)m.y + cc.i0 + f.idx];
-                    a.acc[qi * a.cap + s_abase + t] = ((unsigned long long)__float_as_uint(f.p) << 32) | id;
+                    if (s_abase + t < a.cap)
+                        a.acc[qi * a.cap + s_abase + t] = ((unsigned long long)__float_as_uint(f.p) << 32) | id;
+                    else
+                        atomicExch(a.err, (int)DADE_ENOMEM);   // accept buffer full: the call reports it
                 }
             }
         } else if (nF > 0) {

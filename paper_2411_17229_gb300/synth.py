@@ -52,6 +52,7 @@ class Workload:
     alpha: float
     kmeans_iters: int = 10
     shared_basis: bool = True
+    comp_zipf: float = 0.0   # > 0: component weights Zipf(comp_zipf) over a seeded rank permutation
 
 
 # Constants proposed for the workloads (sizes from the benchmark configs; the
@@ -65,6 +66,9 @@ WORKLOADS = {
     "c3_mix_1m_d960": Workload("c3_mix_1m_d960", 1_000_000, 960, 1_000, 0.8, 64,
                                0.0, 2.0, 1.0, False, False, 4096,
                                (32, 64, 128), 10, (32,), 0.05),
+    "c4_zipf_10m_d768": Workload("c4_zipf_10m_d768", 10_000_000, 768, 10_000, 1.5, 16384,
+                                 0.0, 2.0, 1.0, False, True, 16384,
+                                 (64,), 10, (32,), 0.05, comp_zipf=1.1),
     "c5_mix_5m_d256": Workload("c5_mix_5m_d256", 5_000_000, 256, 10_000, 1.0, 32,
                                0.0, 2.0, 1.0, False, False, 8192,
                                (16, 64, 128), 10, (32,), 0.05),
@@ -99,8 +103,51 @@ def _components(w: Workload):
     return lam, means, rots
 
 
+def component_weights(w: Workload) -> np.ndarray:
+    """Mixture weights: uniform, or Zipf(comp_zipf) by rank with the ranks
+    dealt to components by a seeded permutation."""
+    if w.comp_zipf <= 0:
+        return np.full(w.n_comp, 1.0 / w.n_comp)
+    rng = np.random.default_rng(SEED_BASIS + 5)
+    wts = np.arange(1, w.n_comp + 1, dtype=np.float64) ** (-w.comp_zipf)
+    wts = wts[rng.permutation(w.n_comp)]
+    return wts / wts.sum()
+
+
+def _draw_weighted(w: Workload, n: int, seed: int, comps):
+    """Shared-basis mixture with uneven weights, drawn in row chunks (FP32
+    products): x = m_c + s Q (sqrt(lambda) z), optionally L2-normalised.
+    Chunk k draws its z from its own generator seeded by (seed, k), so the
+    chunks can be drawn on several threads with the same result."""
+    import concurrent.futures as cf
+    import os
+    lam, means, rots = comps
+    rng = np.random.default_rng(seed)
+    labels = rng.choice(w.n_comp, size=n, p=component_weights(w)).astype(np.int32)
+    out = np.empty((n, w.d), np.float32)
+    sl = np.sqrt(lam).astype(np.float32)
+    QT = np.ascontiguousarray(rots[0].T, np.float32)
+    M = means.astype(np.float32)
+    chunk = 1 << 17
+
+    def one(k):
+        s, e = k * chunk, min(n, (k + 1) * chunk)
+        z = np.random.default_rng([seed, k]).standard_normal((e - s, w.d), dtype=np.float32)
+        z *= sl[None, :]
+        x = M[labels[s:e]] + np.float32(w.within_scale) * (z @ QT)
+        if w.normalise:
+            x /= np.linalg.norm(x, axis=1, keepdims=True)
+        out[s:e] = x
+
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(one, range((n + chunk - 1) // chunk)))
+    return out, labels
+
+
 def _draw(w: Workload, n: int, seed: int, comps=None):
     lam, means, rots = comps if comps is not None else _components(w)
+    if w.comp_zipf > 0:
+        return _draw_weighted(w, n, seed, (lam, means, rots))
     rng = np.random.default_rng(seed)
     labels = rng.integers(0, w.n_comp, size=n).astype(np.int32) if w.n_comp > 1 \
         else np.zeros(n, np.int32)

@@ -479,3 +479,53 @@ def test_seed_split_with_prefilter():
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
     assert np.array_equal(out[0][2][:, 0], out[1][2][:, 0])
     assert (out[1][3] > 0).any() and (out[1][3] <= out[1][2][:, 0]).all()
+
+
+@pytest.mark.parametrize("d,delta_d,tile,seed", [(128, 32, 128, 2), (128, 16, 4096, 2), (160, 32, 128, 2),
+                                                 (256, 64, 4096, 1)])
+def test_list_chunks_same_results(d, delta_d, tile, seed):
+    """List-major work items that cover a list in several chunks (other
+    thread blocks, other times) give the same bits and counters as one item
+    per list: r is frozen in those passes."""
+    w = synth.Workload(f"chunk{d}", 12000, d, 60, 1.0, 8, 0.0, 3.0, 1.0, False, False, 8, (4,), 10, (16,), 0.1)
+    base, queries, labels = synth.make(w)
+    case = Case(base, queries, labels, 8, n_pairs=3000)    # 8 lists of ~1,500 rows
+    out = []
+    for chunk in (0, 64, 192):
+        nq = queries.shape[0]
+        ids = torch.empty(nq, 20, dtype=torch.int64, device="cuda")
+        dd = torch.empty(nq, 20, dtype=torch.float32, device="cuda")
+        st = torch.zeros(nq, 4, dtype=torch.int64, device="cuda")
+        case.gpu.search(case.q_rot, 20, 5, 0.1, delta_d, ids, dd, tile=tile, stats=st,
+                        schedule=dade.SCHED_SEEDED, seed_lists=seed, list_chunk=chunk)
+        case.gpu.sync()
+        out.append((ids.cpu().numpy(), dd.cpu().numpy(), st.cpu().numpy()))
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1].view(np.uint32), o[1].view(np.uint32))
+        assert np.array_equal(out[0][2], o[2])
+    o_ids, o_d, _, oflags = case.oracle_search(20, 5, 0.1, delta_d, tile=tile, seed=seed)
+    parity.compare(out[1][0], out[1][1], o_ids, o_d, oflags, case.scale, case.exact_d, max_flagged_frac=0.5)
+
+
+def test_accept_buffer_overflow_is_reported():
+    """A pass with r = +inf over a list longer than the accept buffer
+    (65,536 entries per query) reports DADE_ENOMEM at the next sync instead
+    of returning partial results silently; the index stays usable."""
+    n, d = 70000, 16
+    rng = np.random.default_rng(5)
+    base = rng.standard_normal((n, d)).astype(np.float32)
+    assign = np.zeros(n, np.int32)
+    assign[:8] = 1                                            # list 0: 69,992 rows; list 1: 8, far away
+    base[:8, 0] += 100.0
+    ix = dade.Index(torch.from_numpy(base).cuda(), 2, assign=assign, eps_pairs=2000)
+    q = torch.from_numpy(base[8:12].copy()).cuda()            # list 0 is probed first
+    ids = torch.empty(4, 5, dtype=torch.int64, device="cuda")
+    dd = torch.empty(4, 5, dtype=torch.float32, device="cuda")
+    with pytest.raises(dade.DadeError) as e:
+        ix.query(q, 5, 2, 0.1, 16, ids, dd, schedule=dade.SCHED_SEEDED, seed_lists=1, tile=1 << 20,
+                 flags=dade.FLAG_SEED_SPLIT | dade.FLAG_GENERIC_KERNEL)
+        ix.sync()
+    assert e.value.status == dade.ENOMEM
+    ix.query(q, 5, 2, 0.1, 16, ids, dd)                      # the tile schedule still answers
+    ix.sync()
+    assert (ids.cpu().numpy()[:, 0] == np.arange(8, 12)).all()
