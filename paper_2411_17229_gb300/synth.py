@@ -53,6 +53,7 @@ class Workload:
     kmeans_iters: int = 10
     shared_basis: bool = True
     comp_zipf: float = 0.0   # > 0: component weights Zipf(comp_zipf) over a seeded rank permutation
+    lists_are_components: bool = False   # the IVF lists are the generating components (no k-means)
 
 
 # Constants proposed for the workloads (sizes from the benchmark configs; the
@@ -68,7 +69,7 @@ WORKLOADS = {
                                (32, 64, 128), 10, (32,), 0.05),
     "c4_zipf_10m_d768": Workload("c4_zipf_10m_d768", 10_000_000, 768, 10_000, 1.5, 16384,
                                  0.0, 2.0, 1.0, False, True, 16384,
-                                 (64,), 10, (32,), 0.05, comp_zipf=1.1),
+                                 (64,), 10, (32,), 0.05, comp_zipf=1.1, lists_are_components=True),
     "c5_mix_5m_d256": Workload("c5_mix_5m_d256", 5_000_000, 256, 10_000, 1.0, 32,
                                0.0, 2.0, 1.0, False, False, 8192,
                                (16, 64, 128), 10, (32,), 0.05),
