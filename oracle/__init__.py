@@ -278,7 +278,7 @@ class SampledIndex:
     those queries probe (Section 3.4) and the sampled pairs' objects.  A list
     centroid is computed as W^T (m - mu) from the list's raw FP64 mean m,
     which is the mean of the rotated members (the rotation is affine); the
-    sums use numpy's reduction as a library step.  ``search`` returns ids of
+    sums use numpy's weighted bincount as a library step.  ``search`` returns ids of
     the full base."""
 
     def __init__(self, base, assign, n_clusters, pairs, queries, nprobe, oracle: Oracle | None = None,
@@ -292,9 +292,10 @@ class SampledIndex:
         counts = np.bincount(assign, minlength=self.nc)
         if (counts == 0).any():
             raise ValueError("every list must have members")
-        order = np.argsort(assign, kind="stable")
-        starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
-        means = np.add.reduceat(X[order], starts, axis=0, dtype=np.float64) / counts[:, None]
+        sums = np.empty((self.nc, D))
+        for j in range(D):                       # one dimension at a time: no copy of the base
+            sums[:, j] = np.bincount(assign, weights=X[:, j], minlength=self.nc)
+        means = sums / counts[:, None]
         self.cent = (means - self.mu) @ self.W
         self.Qr = o.rotate(queries, self.mu, self.W)
         self.probe, self.probe_tie = o.probe(self.Qr, self.cent, nprobe)

@@ -163,3 +163,36 @@ def test_c5_full_size_serving():
     for i in range(n_req):
         _check_properties(base, queries[picks[i]:picks[i] + 1], res[i][0], res[i][1], scale)
     ix.close()
+
+
+def test_c4_full_size_benchmark_point():
+    """10M x 768 normalised mixture over 16,384 components with Zipf(1.1)
+    weights (largest list 1.47M, median 72), lists = the generating
+    components, 10,000 queries, K = 10, at the benchmark's point: tile
+    schedule (tile 128, 128 threads), delta_d 32, alpha 0.8, nprobe 8, query
+    order; index with the FP8 leading-block copy.  The FP8 prefilter at the
+    same point must return the FP32 path's results bit for bit."""
+    w = synth.WORKLOADS["c4_zipf_10m_d768"]
+    base, queries, labels = synth.make(w)
+    pairs = synth.eps_pairs(w.n, 20000)
+    ix = dade.Index(torch.from_numpy(base).cuda(), w.n_clusters, assign=labels, pairs=pairs,
+                    lead_format=dade.LEAD_FP8, lead_dims=64)
+    pt = {"nprobe": 8, "alpha": 0.8, "delta_d": 32, "tile": 128, "threads": 128, "schedule": dade.SCHED_TILE,
+          "seed_lists": 0, "flags": dade.FLAG_QUERY_ORDER}
+    probe, ids, dists = _scan_batch(ix, queries, w.k, pt)
+    _, ids8, dists8 = _scan_batch(ix, queries, w.k, dict(pt, flags=pt["flags"] | dade.FLAG_LEAD))
+    assert np.array_equal(ids, ids8) and np.array_equal(dists.view(np.uint32), dists8.view(np.uint32))
+    sample = np.sort(np.random.default_rng(17).choice(queries.shape[0], N_SAMPLE // 2, replace=False))
+    orc = oracle.SampledIndex(base, labels, w.n_clusters, pairs, queries[sample], pt["nprobe"])
+    scale = float(orc.lam.sum())
+    same = [np.array_equal(probe[s], orc.probe[i]) for i, s in enumerate(sample) if not orc.probe_tie[i]]
+    assert all(same)
+    o_ids, o_d, _, oflags = orc.search(w.k, pt["nprobe"], pt["delta_d"], pt["alpha"], tile=pt["tile"])
+
+    def exact_d(i, sel):
+        return ((base[sel].astype(np.float64) - queries[sample[i]].astype(np.float64)) ** 2).sum(-1)
+
+    summary = parity.compare(ids[sample], dists[sample], o_ids, o_d, oflags, scale, exact_d, max_flagged_frac=1.0)
+    assert summary["flagged_mismatched"] <= max(1, len(sample) // 4), summary
+    _check_properties(base, queries, ids, dists, scale)
+    ix.close()
