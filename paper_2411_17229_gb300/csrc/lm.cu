@@ -88,6 +88,69 @@ __device__ __forceinline__ void lm_append(const LmArgs &a, bool take, int q, uns
     }
 }
 
+// Per-item K-best staging of accepted keys (K <= KB_K): within one work item a
+// query's accepted keys are staged per (warp, query slot) and cut back to its
+// K smallest whenever the stage fills; only those reach the query's accept
+// buffer.  Exact: the final merge keeps the K smallest keys overall, and a key
+// beaten by K others of the same item cannot be among them.  This bounds what
+// an item adds per query (K), however many candidates pass a loose r.
+constexpr int KB = 64;            // staged keys per (warp, query slot)
+constexpr int KB_K = KB - 32;     // largest K staged (one append adds up to 32)
+constexpr int QSLOT = LG / LNW;   // query slots per warp: the item's queries warp + LNW * slot
+
+struct KBest {
+    unsigned long long key[LNW][QSLOT][KB];
+    int cnt[LNW][QSLOT];
+};
+
+// Keep the k smallest staged keys of (w, s) at the front (keys are unique). Whole warp.
+__device__ void kb_compact(KBest &kb, int w, int s, int k) {
+    const int lane = threadIdx.x & 31;
+    const int n = kb.cnt[w][s];
+    const unsigned long long v0 = lane < n ? kb.key[w][s][lane] : ~0ull;
+    const unsigned long long v1 = lane + 32 < n ? kb.key[w][s][lane + 32] : ~0ull;
+    int r0 = 0, r1 = 0;
+    for (int j = 0; j < n; ++j) {
+        const unsigned long long x = kb.key[w][s][j];
+        r0 += x < v0;
+        r1 += x < v1;
+    }
+    __syncwarp();
+    if (lane < n && r0 < k) kb.key[w][s][r0] = v0;
+    if (lane + 32 < n && r1 < k) kb.key[w][s][r1] = v1;
+    __syncwarp();
+    if (lane == 0) kb.cnt[w][s] = min(n, k);
+    __syncwarp();
+}
+
+// Stage the keys of the lanes with `take` for (w, s).  Whole warp.
+__device__ void kb_take(KBest &kb, int w, int s, int k, bool take, unsigned long long key) {
+    const int lane = threadIdx.x & 31;
+    const unsigned mk = __ballot_sync(0xffffffffu, take);
+    if (mk == 0) return;
+    if (kb.cnt[w][s] + __popc(mk) > KB) kb_compact(kb, w, s, k);
+    const int n = kb.cnt[w][s];
+    __syncwarp();
+    if (take) kb.key[w][s][n + __popc(mk & ((1u << lane) - 1u))] = key;
+    __syncwarp();
+    if (lane == 0) kb.cnt[w][s] = n + __popc(mk);
+    __syncwarp();
+}
+
+// Move the staged K best of (w, s) to query q's accept buffer.  Whole warp.
+__device__ void kb_flush(const LmArgs &a, KBest &kb, int w, int s, int q) {
+    const int lane = threadIdx.x & 31;
+    if (kb.cnt[w][s] > a.k) kb_compact(kb, w, s, a.k);
+    const int n = kb.cnt[w][s];
+    for (int b = 0; b < n; b += 32) {
+        const bool take = b + lane < n;
+        lm_append(a, take, q, take ? kb.key[w][s][b + lane] : 0ull);
+    }
+    __syncwarp();
+    if (lane == 0) kb.cnt[w][s] = 0;
+    __syncwarp();
+}
+
 template <int GB, bool STATS>
 __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
     constexpr int NINC = (LNB + GB - 1) / GB;
@@ -287,6 +350,8 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_item, s_q[LG];
     __shared__ float s_r2[LG];
+    __shared__ KBest kb;
+    const bool kbest = a.k <= KB_K;   // stage per item (small K), else append directly
     float *stage = reinterpret_cast<float *>(smem);
     float *qs = reinterpret_cast<float *>(smem + 2 * LmSmem::stage(GB));
     Surv *survs = reinterpret_cast<Surv *>(smem + 2 * LmSmem::stage(GB) + sizeof(float) * LG * 16 * GB);
@@ -297,6 +362,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
         mbar_init(su32(&bars[1]), 1);
         fence_mbar_init();
     }
+    if (tid < LNW * QSLOT) kb.cnt[tid / QSLOT][tid % QSLOT] = 0;
     __syncthreads();
     uint32_t used[2] = {0u, 0u};
     const int total = a.item_off[a.nc];
@@ -437,7 +503,9 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
                     const bool take = alive && lq == 0 && p <= r2;
                     if (STATS && alive && lq == 0) { st_d += a.d; st_a += take; }
                     const int id = take ? a.ids[m.slot + i] : 0;
-                    lm_append(a, take, q, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned)id);
+                    const unsigned long long key = ((unsigned long long)__float_as_uint(p) << 32) | (unsigned)id;
+                    if (kbest) kb_take(kb, warp, g / LNW, a.k, take, key);
+                    else lm_append(a, take, q, key);
                 }
                 if (STATS) {
 #pragma unroll
@@ -459,6 +527,8 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
             __syncthreads();
             if (tid == 0 && t + 2 < ntile) issue(t + 2);
         }
+        if (kbest)   // the item's K best per query go to the accept buffers
+            for (int g = warp; g < ng; g += LNW) kb_flush(a, kb, warp, g / LNW, s_q[g]);
     }
 }
 
