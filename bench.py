@@ -95,10 +95,11 @@ def run_profile(args):
     w = synth.WORKLOADS[args.workload]
     n, nq = args.n or w.n, args.nq or w.nq
     nc = w.n_clusters if n == w.n else max(16, n // 244)
-    base, queries, _ = synth.make(w, n=n, nq=nq)
+    base, queries, labels = synth.make(w, n=n, nq=nq)
+    given = {"assign": labels} if w.lists_are_components and n == w.n else {}
     lf, ld = lead_opts(args, dade, w.d)
     ix = dade.Index(torch.from_numpy(base).cuda(), nc, kmeans_iters=w.kmeans_iters, seed=synth.SEED_KMEANS,
-                    lead_format=lf, lead_dims=ld, tail_from=tail_opt(args, w.d))
+                    lead_format=lf, lead_dims=ld, tail_from=tail_opt(args, w.d), **given)
     q = torch.from_numpy(queries).cuda()
     pt = parse_point(args.point, dade)
     qr = torch.empty_like(q)
@@ -205,7 +206,7 @@ def run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, 
             "ms_per_step": round(statistics.mean(ms_steps), 4), "eps0": pt["eps0"], "delta_d": pt["delta_d"],
             "nprobe": pt["nprobe"], "schedule": {0: "tile", 2: "seeded"}[pt["schedule"]],
             "seed_lists": pt["seed_lists"] or None,
-            "index": "random orthogonal basis (seeded), same k-means recipe"}
+            "index": "random orthogonal basis (seeded), lists by the same recipe"}
 
 
 def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7):

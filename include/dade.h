@@ -214,6 +214,9 @@ typedef struct {
     int32_t list_chunk;        /* list-major passes of DADE_SCHED_SEEDED: rows of one list per work
                                   item (0: 4096; else a multiple of 64); a long list becomes several
                                   items run by different thread blocks.  Same results. */
+    int32_t stage_ring;        /* tile kernel for any D: staged tiles in flight per thread block (0: 2;
+                                  2..8); deeper rings hide more load latency for more shared memory.
+                                  Same results. */
 } dade_search_opts;
 
 /* Description of a built index. */

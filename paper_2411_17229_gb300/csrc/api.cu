@@ -145,6 +145,8 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
     DADE_CHECK_ARG(!opts || opts->seed_lists >= 0, "seed_lists < 0");
     DADE_CHECK_ARG(!opts || opts->list_chunk == 0 || (opts->list_chunk >= 64 && opts->list_chunk % 64 == 0),
                    "list_chunk must be 0 or a positive multiple of 64");
+    DADE_CHECK_ARG(!opts || opts->stage_ring == 0 || (opts->stage_ring >= 2 && opts->stage_ring <= 8),
+                   "stage_ring must be 0 or 2..8");
     DADE_CHECK_ARG(!opts || opts->stage_dims == 0 ||
                        (opts->stage_dims >= delta_d && delta_d > 0 && opts->stage_dims % delta_d == 0 &&
                         opts->stage_dims <= DADE_MAX_DIM),
@@ -212,6 +214,7 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.seed_lists = opts && opts->seed_lists > 0 ? opts->seed_lists : 2;
     p.stage_dims = opts ? opts->stage_dims : 0;
     p.list_chunk = opts ? opts->list_chunk : 0;
+    p.stage_ring = opts ? opts->stage_ring : 0;
     p.generic = opts ? (opts->flags & DADE_FLAG_GENERIC_KERNEL) != 0 : 0;
     p.use_lead = opts ? (opts->flags & DADE_FLAG_LEAD) != 0 : 0;
     p.use_tail = opts ? (opts->flags & DADE_FLAG_ROW_TAIL) != 0 : 0;

@@ -160,6 +160,7 @@ struct ScanParams {
     int32_t stage_dims;      // FP32 DADE tile kernel: dims staged per tile (0: delta_d)
     int32_t seed_split;      // SEEDED: lists after the seeds run query-major, split over CTAs
     int32_t list_chunk;      // list-major passes: rows of a list per work item (0: 4096)
+    int32_t stage_ring;      // tile kernel: staged units in flight per CTA (0: 2)
     // split mode of the tile kernel (parts > 0; see ScanArgs)
     int32_t parts, c0;
     const float *r2src;

@@ -508,6 +508,7 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     if (!fd && !lf && plain && p.schedule == DADE_SCHED_PIPELINED && a.n_inc <= pipe_depth_limit())
         return scan_pipelined(a, nq, p.threads, s);
     if (scan_fast_applies(a, fd) && !p.generic && plain) return scan_fast(a, nq, fd, p.threads, lf, s);
+    if (p.stage_ring >= 2) a.ns = std::min(p.stage_ring, 8);   // the tile kernel's ring depth
     const SmemLayout L = layout(a.dp, a.tile, a.ub, a.ns, a.k, a.nprobe, lf != 0);
     if (L.total > 227 * 1024) {
         set_error("scan configuration needs more than 227 KB of shared memory (reduce tile or delta_d)");

@@ -47,7 +47,8 @@ class SearchOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("tile", C.c_int32), ("stats", C.c_void_p), ("spec", C.c_int32),
                 ("threads", C.c_int32), ("schedule", C.c_int32), ("flags", C.c_int32),
                 ("lead_stats", C.c_void_p), ("seed_lists", C.c_int32), ("estimator", C.c_int32),
-                ("eps0", C.c_float), ("stage_dims", C.c_int32), ("list_chunk", C.c_int32)]
+                ("eps0", C.c_float), ("stage_dims", C.c_int32), ("list_chunk", C.c_int32),
+                ("stage_ring", C.c_int32)]
 
 
 class ServerOpts(C.Structure):
@@ -228,42 +229,46 @@ class Index:
 
     def search(self, q_rot, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
                threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, estimator=ESTIMATOR_DADE,
-             eps0=0.0, stage_dims=0, list_chunk=0, stream=None):
+             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
                        flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists, estimator=estimator,
-                       eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk)
+                       eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
+                       stage_ring=stage_ring)
         _check(lib().dade_search(self._h, _ptr(q_rot), q_rot.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                  C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def scan(self, q_rot, probe, k, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
              threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, estimator=ESTIMATOR_DADE,
-             eps0=0.0, stage_dims=0, list_chunk=0, stream=None):
+             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
                        flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists, estimator=estimator,
-                       eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk)
+                       eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
+                       stage_ring=stage_ring)
         _check(lib().dade_scan(self._h, _ptr(q_rot), _ptr(probe), q_rot.shape[0], int(k), probe.shape[1],
                                float(alpha), int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def query(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
               threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, estimator=ESTIMATOR_DADE,
-             eps0=0.0, stage_dims=0, list_chunk=0, stream=None):
+             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
                        flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists, estimator=estimator,
-                       eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk)
+                       eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
+                       stage_ring=stage_ring)
         _check(lib().dade_query(self._h, _ptr(q), q.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                 C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def graph(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
               threads=0, schedule=SCHED_TILE, flags=0, seed_lists=0, estimator=ESTIMATOR_DADE, eps0=0.0,
-              stage_dims=0, list_chunk=0):
+              stage_dims=0, list_chunk=0, stage_ring=0):
         """A query step captured into a CUDA graph (device buffers, bound to the graph)."""
         return Graph(self, q, k, nprobe, alpha, delta_d, ids, dists,
                      SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads,
                                 schedule=schedule, flags=flags, seed_lists=seed_lists, estimator=estimator,
-                                eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk))
+                                eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
+                       stage_ring=stage_ring))
 
     def reserve(self, max_nq, max_nprobe):
         _check(lib().dade_reserve(self._h, int(max_nq), int(max_nprobe)))

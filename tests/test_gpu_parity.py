@@ -551,3 +551,25 @@ def test_kbest_staging_bounds_a_loose_threshold():
         summary = parity.compare(g_ids, g_d, o_ids, o_d, oflags, case.scale, case.exact_d, max_flagged_frac=1.0)
         assert summary["flagged_mismatched"] <= 1, summary
         assert np.array_equal(g_st[:, 0], o_st[:, 0])
+
+
+@pytest.mark.parametrize("d,ring,flags", [(160, 4, 0), (128, 3, dade.FLAG_GENERIC_KERNEL), (256, 8, 0),
+                                          (128, 4, dade.FLAG_GENERIC_KERNEL | dade.FLAG_LEAD)])
+def test_stage_ring_gives_same_results(d, ring, flags):
+    """More staged tiles in flight per thread block changes when bytes
+    arrive, not the results."""
+    w = synth.Workload(f"ring{d}", 6000, d, 50, 1.0, 16, 0.0, 3.0, 1.0, False, False, 16, (4,), 10, (16,), 0.1)
+    base, queries, labels = synth.make(w)
+    ix = dade.Index(torch.from_numpy(base).cuda(), 16, assign=labels, eps_pairs=3000,
+                    lead_format=dade.LEAD_BF16, lead_dims=64)
+    q = torch.from_numpy(queries).cuda()
+    out = []
+    for r in (0, ring):
+        ids = torch.empty(q.shape[0], 20, dtype=torch.int64, device="cuda")
+        dd = torch.empty(q.shape[0], 20, dtype=torch.float32, device="cuda")
+        st = torch.zeros(q.shape[0], 4, dtype=torch.int64, device="cuda")
+        ix.query(q, 20, 6, 0.1, 32, ids, dd, tile=64, stats=st, flags=flags, stage_ring=r)
+        ix.sync()
+        out.append((ids.cpu().numpy(), dd.cpu().numpy(), st.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
+    assert np.array_equal(out[0][2], out[1][2])
