@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
             s_cntF = 0;
         }
         float r2 = 0.f;
+        bool quiet = false;   // DADE: no survivor and nothing accepted in this tile
 
         if (FD) {
             // ---- FDScanning: every increment staged, partials kept per lane ------
@@ -260,6 +261,10 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
             // pruned candidate stops loading; a warp whose candidates are all pruned
             // stops early.  Candidates alive at d = D are accepted iff P_D <= r^2.
             const int nS = s_cnt[0];
+            // a tile that leaves no survivor and accepts nothing skips the barriers of
+            // phase B and the merge (every thread sees the same two zero counts; the
+            // next tile's first barrier orders the rest)
+            quiet = nS == 0 && s_cntF == 0;
             for (int r0 = 0; r0 < nS; r0 += NQUAD) {
                 const int sidx = r0 + quad;
                 const bool act = sidx < nS;
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
                 if (STATS && alive && lq == 0) { st_dims += a.d; st_acc += take; }
                 push(take, fl, &s_cntF, sv.idx, p);
             }
-            __syncthreads();
+            if (!quiet) __syncthreads();
         }
 
         // ---- merge accepted candidates into the K best ------------------------------
@@ -359,7 +364,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
                 s_r2 = nn == a.k ? __uint_as_float((unsigned)(O[a.k - 1] >> 32)) : INFINITY;
             }
         }
-        __syncthreads();
+        if (!quiet) __syncthreads();
         cc.j = 0;
         cc.i0 += a.tile;
         normalize(cc, a, smeta, plist);
