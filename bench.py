@@ -209,12 +209,14 @@ def run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, 
             "index": "random orthogonal basis (seeded), lists by the same recipe"}
 
 
-def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7):
+def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7, torch=None, xb=None):
     """Requests of one query each, Poisson arrivals at each rate (requests/s),
     K and nprobe drawn per request from {1, 10, 100} x {16, 64, 128}; the
     server batches compatible requests and overlaps batches on 4 streams.
     Returns per rate: offered and served request rates, p50 / p99 latency
-    (submit to results on the host, measured by the server)."""
+    (submit to results on the host, measured by the server); with the base
+    on the device (xb), the served recall@K per nprobe against exact FP64
+    ground truth."""
     n_lists = ix.info.n_clusters
     nprobes = [p for p in (16, 64, 128) if p <= n_lists]
     srv = dade.Server(ix, slots=4, max_batch=1024, max_k=100, max_nprobe=max(nprobes), tile=point["tile"],
@@ -222,7 +224,7 @@ def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7):
                       seed_lists=point.get("seed_lists", 0), flags=point["flags"],
                       stage_dims=point.get("stage_dims", 0))
     rng = np.random.default_rng(seed)
-    out = []
+    out, served = [], []
     for rate in rates:
         n = max(50, int(rate * seconds))
         gaps = rng.exponential(1.0 / rate, n)
@@ -239,8 +241,10 @@ def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7):
             tickets.append(srv.submit(queries[picks[i]:picks[i] + 1], int(ks[i]), int(nps[i]),
                                       point.get("alpha", 0.1), point.get("delta_d", 32)))
         t_sub = time.perf_counter() - t_start
-        lats = [srv.result(t)[2] for t in tickets]
+        res = [srv.result(t) for t in tickets]
+        lats = [r[2] for r in res]
         t_all = time.perf_counter() - t_start
+        served.extend((int(picks[i]), int(ks[i]), int(nps[i]), res[i][0][0]) for i in range(n))
         out.append({"offered_rps": rate, "requests": n, "served_rps": round(n / t_all, 1),
                     "submit_rps": round(n / t_sub, 1),
                     "p50_ms": round(1e3 * float(np.percentile(lats, 50)), 3),
@@ -249,9 +253,29 @@ def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7):
             break
     st = srv.stats()
     srv.close()
+    recall = served_recall(torch, xb, queries, served, nprobes) if xb is not None else None
     return {"requests": "1 query each, K in {1, 10, 100}, nprobe in " + str(nprobes) + ", Poisson arrivals",
             "slots": st["slots"], "batches": st["batches"], "mean_batch": round(st["queries"] / max(1, st["batches"]), 2),
-            "max_inflight": st["max_inflight"], "rates": out}
+            "max_inflight": st["max_inflight"], "rates": out, "recall_by_nprobe": recall}
+
+
+def served_recall(torch, xb, queries, served, nprobes):
+    """Mean recall@K of served requests per nprobe: a returned id counts if its
+    exact distance is within the request's K-th true distance (1e-5 relative)."""
+    qi = sorted({s[0] for s in served})
+    row = {q: r for r, q in enumerate(qi)}
+    q = torch.from_numpy(queries[qi]).to(xb.device)
+    gt_ids, _ = ground_truth(torch, xb, q, 100)
+    true_d = ((q.double()[:, None, :] - xb[gt_ids].double()) ** 2).sum(-1).cpu().numpy()   # ascending
+    hits = {p: [0, 0] for p in nprobes}
+    for qid, k, nprobe, ids in served:
+        r = row[qid]
+        valid = ids >= 0
+        sel = torch.from_numpy(ids[valid]).to(xb.device)
+        d = ((q[r].double()[None, :] - xb[sel].double()) ** 2).sum(-1).cpu().numpy()
+        hits[nprobe][0] += int((d <= true_d[r, k - 1] * (1 + 1e-5)).sum())
+        hits[nprobe][1] += k
+    return {str(p): round(h / max(1, n), 4) for p, (h, n) in hits.items()}
 
 
 def tail_opt(args, d):
@@ -719,7 +743,8 @@ def run_ours(args):
     serving = None
     if not args.no_serving:
         try:
-            serving = serve_sweep(dade, ix, queries, point, (2000, 10000, 30000), args.serve_seconds)
+            serving = serve_sweep(dade, ix, queries, point, (2000, 10000, 30000), args.serve_seconds,
+                                  torch=torch, xb=xb)
         except Exception as e:  # noqa: BLE001 - reported, not fatal
             log(f"[bench] serving sweep failed: {e}")
 
