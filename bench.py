@@ -43,7 +43,15 @@ UNIT = "queries/s"
 RECALL_TARGET = 0.95
 # operating point used by the reference arm (the CPU oracle), which cannot
 # run the GPU autotuner; set from the autotuner's usual choice on this workload
-REFERENCE_POINT = {"nprobe": 20, "alpha": 0.3, "delta_d": 64}
+# The oracle arm's operating point per workload: the DADE point the autotuner picks there
+# (nprobe, alpha, delta_d, schedule); the oracle runs its own index at that point.
+REFERENCE_POINTS = {
+    "c1_gauss_10k_d128": {"nprobe": 8, "alpha": 0.05, "delta_d": 32, "schedule": 0, "seed_lists": 0},
+    "c2_mix_1m_d128": {"nprobe": 20, "alpha": 0.8, "delta_d": 64, "schedule": 2, "seed_lists": 2},
+    "c3_mix_1m_d960": {"nprobe": 24, "alpha": 0.8, "delta_d": 64, "schedule": 2, "seed_lists": 3},
+    "c4_zipf_10m_d768": {"nprobe": 8, "alpha": 0.8, "delta_d": 32, "schedule": 0, "seed_lists": 0},
+    "c5_mix_5m_d256": {"nprobe": 32, "alpha": 0.8, "delta_d": 64, "schedule": 2, "seed_lists": 4},
+}
 
 
 def log(*a):
@@ -775,7 +783,7 @@ def run_ours(args):
     clocks = clk.summary()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(base, queries, w, nc, point, K, args.cpu_seconds)
+        cpu = cpu_baseline(base, queries, w, nc, point, K, args.cpu_seconds, assign=given.get("assign"))
 
     if rank == 0:
         out = {
@@ -827,16 +835,20 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------- oracle ----
-def oracle_index(base, w, nc, kmeans_iters=1):
+def oracle_index(base, w, nc, kmeans_iters=1, assign=None):
     """The oracle's own index over the same base: PCA, rotation, k-means lists
     (fewer Lloyd iterations than the GPU index: the oracle's FP64 assignment
-    passes are the expensive part of its setup) and the eps sample."""
+    passes are the expensive part of its setup) or the given lists, and the
+    eps sample."""
     import oracle
     o = oracle.get()
     t0 = time.time()
-    init = synth.kmeans_init(base.shape[0], nc)
     pairs = synth.eps_pairs(base.shape[0], 100000)
-    idx = oracle.Index(base, init=init, iters=kmeans_iters, pairs=pairs, oracle=o)
+    if assign is not None:
+        idx = oracle.Index(base, n_clusters=nc, assign=assign, pairs=pairs, oracle=o)
+    else:
+        idx = oracle.Index(base, init=synth.kmeans_init(base.shape[0], nc), iters=kmeans_iters, pairs=pairs,
+                           oracle=o)
     log(f"[bench] oracle index ({o.threads()} threads) in {time.time() - t0:.1f}s")
     return idx
 
@@ -856,9 +868,9 @@ def oracle_qps(idx, queries, point, K, cpu_seconds, steps=1):
     return m, times
 
 
-def cpu_baseline(base, queries, w, nc, point, K, cpu_seconds):
+def cpu_baseline(base, queries, w, nc, point, K, cpu_seconds, assign=None):
     try:
-        idx = oracle_index(base, w, nc)
+        idx = oracle_index(base, w, nc, assign=assign)
         pt = {"nprobe": point["nprobe"], "alpha": point.get("alpha", 0.1), "delta_d": point.get("delta_d", 32),
               "schedule": point.get("schedule", 0), "seed_lists": point.get("seed_lists", 0)}
         m, times = oracle_qps(idx, queries, pt, K, cpu_seconds)
@@ -885,9 +897,9 @@ def run_reference(args):
     n = args.n or w.n
     nq = args.nq or w.nq
     nc = w.n_clusters if n == w.n else max(16, n // 244)
-    base, queries, _ = synth.make(w, n=n, nq=nq)
-    idx = oracle_index(base, w, nc)
-    pt = dict(REFERENCE_POINT)
+    base, queries, labels = synth.make(w, n=n, nq=nq)
+    idx = oracle_index(base, w, nc, assign=labels if w.lists_are_components and n == w.n else None)
+    pt = dict(REFERENCE_POINTS.get(args.workload, REFERENCE_POINTS["c2_mix_1m_d128"]))
     budget = min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup))
     m, times = oracle_qps(idx, queries, pt, w.k, budget * (args.steps + args.warmup), args.steps + args.warmup)
     times = times[args.warmup:]
