@@ -615,6 +615,15 @@ def run_ours(args):
                             if dade_best is None or ms < dade_best[0]:
                                 dade_best = (ms, rc, pt)
                             break
+    # the sweep times each point over 4 scans: re-time the fastest few over more
+    # scans before choosing, so that run-to-run noise does not pick the point
+    finalists = sorted((t for t in tried if t[1] >= RECALL_TARGET), key=lambda t: t[0])[:6]
+    if len(finalists) > 1:
+        dade_best = None
+        for ms_, rc_, pt_ in finalists:
+            r = measure(pt_, reps=16)
+            if r is not None and r[1] >= RECALL_TARGET and (dade_best is None or r[0] < dade_best[0]):
+                dade_best = (r[0], r[1], pt_)
     for ms_, rc_, pt_ in sorted(tried, key=lambda t: t[0])[:12]:
         log(f"[bench]   {ms_:.3f} ms recall {rc_:.4f} {pt_}")
     log(f"[bench] autotune {time.time() - t0:.1f}s: FD {fd_best[2] if fd_best else None} "
