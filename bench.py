@@ -584,8 +584,9 @@ def run_ours(args):
                 for nt in (128, 256)]
     list_major = (w.d + 15) // 16 >= 8   # the list-major kernels cover D > 112
     if list_major:
-        variants += [(dade.SCHED_SEEDED, 8, tile, 128, 0, seed, 0) for seed in (2, 3, 4)
-                     for tile in (64, 128, 256, 1 << 20)]   # 1 << 20: whole lists, seed lists list-major too
+        variants += [(dade.SCHED_SEEDED, 8, tile, nt, 0, seed, 0) for seed in (2, 3, 4)
+                     for tile in (64, 128, 256, 1 << 20) for nt in (128, 256)
+                     if nt == 128 or tile < (1 << 20)]   # 1 << 20: whole lists, seed lists list-major too
     if list_major or w.d <= 112:   # passes with r frozen query-major, split over CTAs
         variants += [(dade.SCHED_SEEDED, 8, 128, nt, dade.FLAG_SEED_SPLIT, seed, 0) for seed in (2, 3)
                      for nt in (128, 256)]

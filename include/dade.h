@@ -54,7 +54,7 @@ typedef enum {
     DADE_ENOMEM = 2,        /* a host or device allocation failed */
     DADE_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
     DADE_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
-    DADE_EUNSUPPORTED = 5,  /* valid request this build does not implement */
+    DADE_EUNSUPPORTED = 5,  /* valid request the library does not implement */
     DADE_EIO = 6            /* file could not be read or written */
 } dade_status;
 

@@ -1,0 +1,42 @@
+"""Host logic of the benchmark (CPU): the operating-point options, the kernel
+names it reports, and the lookup of committed DRAM-traffic records."""
+import json
+import os
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_point_options_round_trip():
+    from paper_2411_17229_gb300 import dade
+    pt = bench.parse_point("nprobe=20,alpha=0.8,delta_d=64,tile=128,threads=128,schedule=2,seed_lists=2,flags=12", dade)
+    kw = bench.point_kw(pt)
+    assert kw == {"mode": 0, "tile": 128, "spec": 8, "threads": 128, "schedule": 2, "flags": 12, "seed_lists": 2,
+                  "stage_dims": 0}
+    assert pt["alpha"] == 0.8 and pt["nprobe"] == 20
+
+
+def test_kernel_names_follow_the_schedule():
+    c2 = {"mode": 0, "threads": 128, "delta_d": 64, "schedule": 2, "seed_lists": 2, "flags": 12}
+    assert bench.scan_kernel_name(c2, 128).startswith("k_dade_fast<128, 8, 4>")
+    c3 = dict(c2, threads=256, seed_lists=3, flags=28)
+    assert "split" in bench.scan_kernel_name(c3, 960)
+    c4 = {"mode": 0, "threads": 128, "delta_d": 32, "schedule": 0, "flags": 4}
+    assert bench.scan_kernel_name(c4, 768) == "k_scan<DADE>"
+    assert bench.scan_kernel_name({"mode": 1, "threads": 256}, 128) == "k_fd_fast<256, 8>"
+
+
+def test_traffic_records_match_only_their_point_and_sources():
+    with open(os.path.join(ROOT, "profiles", "scan_traffic.json")) as f:
+        recs = json.load(f)
+    assert recs, "no committed traffic record"
+    for r in recs:
+        assert set(r) >= {"scan_cu_sha256_16", "workload", "point", "dram_bytes_per_launch", "kernels", "command"}
+        assert r["dram_bytes_per_launch"] == sum(k["dram_read"] + k["dram_write"] for k in r["kernels"].values())
+        assert "--clock-control none" in r["command"]
+    current = [r for r in recs if r["scan_cu_sha256_16"] == bench.scan_source_hash()]
+    for r in current:
+        assert bench.recorded_traffic(dict(r["point"]), r["workload"]) == r["dram_bytes_per_launch"]
+        other = dict(r["point"], nprobe=r["point"]["nprobe"] + 1)
+        assert bench.recorded_traffic(other, r["workload"]) is None
