@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--point", default="nprobe=20,alpha=0.8,delta_d=64,tile=128,threads=128,schedule=2,seed_lists=2,"
                                        "flags=12",
                     help="operating point of --profile (comma-separated key=value)")
+    ap.add_argument("--linear", action="store_true",
+                    help="linear-scan study: one list holding every vector (a flat index), DADE over a delta_d "
+                         "and alpha sweep: dims touched vs recall, and time, beside FDScanning")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server latency sweep")
     ap.add_argument("--no-adsampling", action="store_true", help="skip the ADSampling comparator")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="duration of each arrival rate")
@@ -927,11 +930,68 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_linear(args):
+    """DADE as a linear scan (a flat index: one list of all N vectors, probed
+    by every query), the feasibility setting of Section 5's last experiment:
+    for delta_d in {16, 32, 64} and a sweep of alpha, the fraction of the D
+    dimensions touched per candidate, recall@K against exact FP64 ground
+    truth, and the scan time, beside FDScanning over the same list."""
+    import torch
+    from paper_2411_17229_gb300 import build as libbuild
+    from paper_2411_17229_gb300 import dade
+    libbuild.build()
+    w = synth.WORKLOADS[args.workload]
+    n = args.n or w.n
+    nq = args.nq or 200
+    K = w.k
+    base, queries, _ = synth.make(w, n=n, nq=nq)
+    xb = torch.from_numpy(base).cuda()
+    q = torch.from_numpy(queries).cuda()
+    ix = dade.Index(xb, 1, assign=np.zeros(n, np.int32), seed=synth.SEED_KMEANS, tail_from=tail_opt(args, w.d))
+    gt_ids, gt_kth = ground_truth(torch, xb, q, K)
+    qr = torch.empty_like(q)
+    ix.rotate(q, qr)
+    pr = torch.zeros(nq, 1, dtype=torch.int32, device="cuda")
+    ids = torch.empty(nq, K, dtype=torch.int64, device="cuda")
+    dists = torch.empty(nq, K, dtype=torch.float32, device="cuda")
+    stats = torch.zeros(nq, 4, dtype=torch.int64, device="cuda")
+    fixed = dade.FLAG_ROW_TAIL if tail_opt(args, w.d) else 0
+
+    def run(mode, alpha, dd, reps=3):
+        kw = dict(mode=mode, tile=256, threads=256, flags=fixed)
+        stats.zero_()
+        ix.scan(qr, pr, K, alpha, dd, ids, dists, stats=stats, **kw)
+        ix.sync()
+        st = stats.sum(0).cpu().numpy()
+        rc = recall_at_k(torch, xb, q, ids, gt_kth, K)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ix.scan(qr, pr, K, alpha, dd, ids, dists, **kw)
+        e1.record()
+        torch.cuda.synchronize()
+        return {"recall": round(rc, 4), "dims_fraction": round(float(st[1]) / max(1, int(st[0])) / w.d, 4),
+                "ms": round(e0.elapsed_time(e1) / reps, 3)}
+
+    fd = run(dade.MODE_FD, 0.1, 32)
+    rows = []
+    for dd in (16, 32, 64):
+        for alpha in (0.01, 0.05, 0.1, 0.2, 0.3, 0.5, 0.8):
+            r = run(dade.MODE_DADE, alpha, dd)
+            rows.append(dict(delta_d=dd, alpha=alpha, **r))
+            log(f"[bench] linear delta_d {dd} alpha {alpha}: {r}")
+    print(json.dumps({"linear_scan": {"workload": args.workload, "n": n, "d": w.d, "nq": nq, "k": K,
+                                      "fd": fd, "dade": rows, "kernel": "k_scan (one list, tile 256, 256 threads)"}}),
+          flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.profile:
         run_profile(a)
+    elif a.linear:
+        run_linear(a)
     else:
         run_ours(a)

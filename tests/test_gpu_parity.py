@@ -573,3 +573,20 @@ def test_stage_ring_gives_same_results(d, ring, flags):
         out.append((ids.cpu().numpy(), dd.cpu().numpy(), st.cpu().numpy()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
     assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_flat_index_is_a_linear_scan():
+    """One list holding every vector (a flat index, Section 5's linear-scan
+    setting): DADE against the oracle for several delta_d and alpha, and
+    FDScanning against the oracle's (itself pinned to brute force)."""
+    base, queries, _ = synth.make("c1_gauss_10k_d128", n=6000, nq=30)
+    case = Case(base, queries, np.zeros(6000, np.int32), 1, n_pairs=4000)
+    for dd, alpha in ((16, 0.05), (32, 0.1), (64, 0.3)):
+        g_ids, g_d, g_st = case.gpu_search(10, 1, alpha, dd, tile=256, stats=True)
+        o_ids, o_d, o_st, oflags = case.oracle_search(10, 1, alpha, dd, tile=256)
+        summary = parity.compare(g_ids, g_d, o_ids, o_d, oflags, case.scale, case.exact_d, max_flagged_frac=1.0)
+        assert summary["flagged_mismatched"] <= 3, summary
+        assert np.array_equal(g_st[:, 0], o_st[:, 0])
+    f_ids, f_d = case.gpu_search(10, 1, 0.1, 32, mode=dade.MODE_FD)
+    o_ids, o_d, _, oflags = case.oracle_search(10, 1, 0.1, 32, fd=True)
+    parity.compare(f_ids, f_d, o_ids, o_d, oflags, case.scale, case.exact_d)
