@@ -421,6 +421,23 @@ def recorded_traffic(point, workload):
     return None
 
 
+# ------------------------------------------------------------ multi-rank --
+def max_over_ranks(torch, dist, x, world, device):
+    """The largest value of x over the ranks: the slowest replica sets the
+    whole job's time.  One process per GPU; with world 1 it is x itself."""
+    if world <= 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, nq_per_rank, ms_per_step):
+    """Queries per second of the whole job: every replica answers its own
+    batch of nq_per_rank queries per step (weak scaling)."""
+    return world * nq_per_rank / (ms_per_step / 1e3)
+
+
 # ------------------------------------------------------------ ground truth --
 def point_kw(point):
     """The scan options of an autotuned point, as keyword arguments of the binding."""
@@ -697,13 +714,9 @@ def run_ours(args):
     rot_ms = [e[0].elapsed_time(e[3]) for e in events]
     probe_ms = [e[3].elapsed_time(e[1]) for e in events]
     lib.dade_sync(ix.handle, sh)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(torch, dist, sum(step_ms), world, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * nq / (ms_per_step / 1e3)
+    value = job_rate(world, nq, ms_per_step)
     rc_timed = recall_at_k(torch, xb, q, ids, gt_kth, K)
     ids_timed = ids.clone()
 
@@ -780,7 +793,7 @@ def run_ours(args):
                  **point_kw(point))
         if i >= args.warmup:
             e2e_s.append(time.perf_counter() - t1)
-    e2e_qps = world * nq / statistics.mean(e2e_s)
+    e2e_qps = job_rate(world, nq, 1e3 * max_over_ranks(torch, dist, statistics.mean(e2e_s), world, "cuda"))
 
     peaks = measured_peaks()
     scan_mean = statistics.mean(scan_ms)
