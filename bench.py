@@ -400,6 +400,19 @@ def scan_kernel_name(point, d):
     return f"k_scan<DADE> ({point['stage_dims']} dims staged)" if point.get("stage_dims") else "k_scan<DADE>"
 
 
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0   # GB300: SMs, FP32 lanes per SM, maximum SM clock
+FLOPS_PER_DIM = 3                                # one subtract and one fused multiply-add per dimension
+
+
+def list_major_point(point, d):
+    """True where the scan's later lists run list-major (seeded schedule, not
+    split, D > 112, delta_d of 1, 2, 4 or 8 blocks)."""
+    nb = (d + 15) // 16
+    gb = 8 if point.get("mode", 0) == 1 else min(point.get("delta_d", 32) // 16, nb)
+    return (point.get("schedule", 0) == 2 and not point.get("flags", 0) & 16 and nb >= 8
+            and gb in (1, 2, 4, 8))
+
+
 def recorded_traffic(point, workload):
     """DRAM bytes per scan launch from the committed ncu summary, if it was
     taken on the current scan kernel source and on this operating point."""
@@ -799,14 +812,28 @@ def run_ours(args):
     scan_mean = statistics.mean(scan_ms)
     achieved = alg_bytes / (scan_mean / 1e3) / 1e9
     traffic = recorded_traffic(point, args.workload)
-    roof = {"bound": "hbm", "kernel": scan_kernel_name(point, w.d), "achieved": round(achieved, 1),
-            "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-            "frac": round(achieved / peaks.get("hbm_gbs", 6800.0), 4), "traffic": traffic,
-            "algorithmic_bytes_per_launch": alg_bytes,
-            "peak_source": "fallback" if peaks.get("_fallback") else "measured (MEASURED_PEAKS.json hbm_gbs)",
-            "scan_ms": round(scan_mean, 4)}
-
     clocks = clk.summary()
+    if list_major_point(point, w.d):
+        # each list is staged once for the ~R queries that probe it: the bytes touched
+        # come mostly from shared memory and L2, and the bound is FP32 arithmetic
+        mhz = clocks.get("sm_max_mhz") or SM_MAX_MHZ
+        peak = SMS * FP32_LANES * 2 * mhz / 1e6          # TFLOP/s (an FMA is 2 FLOPs)
+        flops = FLOPS_PER_DIM * dims_sum
+        got = flops / (scan_mean / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": scan_kernel_name(point, w.d), "achieved": round(got, 2), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(got / peak, 4), "traffic": traffic,
+                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": alg_bytes,
+                "bytes_touched_rate_gbs": round(achieved, 1),
+                "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 (FMA) x {mhz:.0f} MHz",
+                "scan_ms": round(scan_mean, 4)}
+    else:
+        roof = {"bound": "hbm", "kernel": scan_kernel_name(point, w.d), "achieved": round(achieved, 1),
+                "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": round(achieved / peaks.get("hbm_gbs", 6800.0), 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "peak_source": "fallback" if peaks.get("_fallback") else "measured (MEASURED_PEAKS.json hbm_gbs)",
+                "scan_ms": round(scan_mean, 4)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(base, queries, w, nc, point, K, args.cpu_seconds, assign=given.get("assign"))

@@ -40,3 +40,13 @@ def test_traffic_records_match_only_their_point_and_sources():
         assert bench.recorded_traffic(dict(r["point"]), r["workload"]) == r["dram_bytes_per_launch"]
         other = dict(r["point"], nprobe=r["point"]["nprobe"] + 1)
         assert bench.recorded_traffic(other, r["workload"]) is None
+
+
+def test_alu_bound_where_lists_are_shared():
+    c2 = {"mode": 0, "delta_d": 64, "schedule": 2, "flags": 12}
+    assert bench.list_major_point(c2, 128)
+    assert bench.list_major_point(dict(c2, delta_d=32), 256)
+    assert not bench.list_major_point(dict(c2, flags=28), 960)          # split: query-major
+    assert not bench.list_major_point(dict(c2, schedule=0), 128)        # tile schedule
+    assert not bench.list_major_point(c2, 64)                           # D <= 112: split fallback
+    assert bench.SMS * bench.FP32_LANES * 2 * bench.SM_MAX_MHZ / 1e6 > 80.0
