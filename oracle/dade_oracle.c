@@ -62,18 +62,26 @@ OR_API void or_mean_cov(const float *X, int64_t n, int d, double *mu, double *C)
         for (int j = 0; j < d; ++j) mu[j] += (double)X[i * d + j];
     for (int j = 0; j < d; ++j) mu[j] /= (double)n;
 
-    /* one covariance row per thread; each entry sums over i in order */
-    #pragma omp parallel for schedule(dynamic, 1)
-    for (int j = 0; j < d; ++j) {
-        double *row = C + (int64_t)j * d;
-        for (int k = 0; k < d; ++k) row[k] = 0.0;
-        for (int64_t i = 0; i < n; ++i) {
-            const float *x = X + i * d;
-            double yj = (double)x[j] - mu[j];
-            for (int k = j; k < d; ++k) row[k] += yj * ((double)x[k] - mu[k]);
+    /* Each entry sums over i in order.  The rows of X are visited in blocks
+     * that every thread reads while they are in cache (one covariance row j
+     * per thread within a block), so X streams from memory about once. */
+    for (int64_t t = 0; t < (int64_t)d * d; ++t) C[t] = 0.0;
+    const int64_t blk = 2048;
+    #pragma omp parallel
+    for (int64_t i0 = 0; i0 < n; i0 += blk) {
+        const int64_t i1 = i0 + blk < n ? i0 + blk : n;
+        #pragma omp for schedule(dynamic, 1)
+        for (int j = 0; j < d; ++j) {
+            double *row = C + (int64_t)j * d;
+            for (int64_t i = i0; i < i1; ++i) {
+                const float *x = X + i * d;
+                double yj = (double)x[j] - mu[j];
+                for (int k = j; k < d; ++k) row[k] += yj * ((double)x[k] - mu[k]);
+            }
         }
-        for (int k = j; k < d; ++k) row[k] /= (double)n;
     }
+    for (int j = 0; j < d; ++j)
+        for (int k = j; k < d; ++k) C[(int64_t)j * d + k] /= (double)n;
     for (int j = 0; j < d; ++j)
         for (int k = 0; k < j; ++k) C[(int64_t)j * d + k] = C[(int64_t)k * d + j];
 }
