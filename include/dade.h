@@ -396,6 +396,21 @@ dade_status dade_scan(const dade_index *ix, const float *q_rot, const int32_t *p
                       float *dists, dade_stream stream);
 
 /*
+ * Tune a scan shape: time, on the caller's batch, the execution options that
+ * leave the results unchanged -- opts->threads (128 or 256) and the flags
+ * DADE_FLAG_QUERY_ORDER, DADE_FLAG_ROW_TAIL (index built with tail_from) and,
+ * for DADE_SCHED_SEEDED, DADE_FLAG_SEED_SPLIT -- and write the fastest into
+ * *opts (every other field is kept).  The choice is cached per index and
+ * shape (nq, k, nprobe, alpha, delta_d and the result-changing options): a
+ * repeated shape returns at once.  q_rot, probe, ids and dists must be device
+ * buffers (ids and dists are scratch here and hold the last timed run's
+ * results); synchronous on `stream`.  DADE_EINVAL for NULL or host buffers.
+ */
+dade_status dade_tune(const dade_index *ix, const float *q_rot, const int32_t *probe, int64_t nq, int32_t k,
+                      int32_t nprobe, float alpha, int32_t delta_d, dade_search_opts *opts, int64_t *ids,
+                      float *dists, dade_stream stream);
+
+/*
  * End-to-end query: dade_rotate_queries followed by dade_search, on raw
  * queries.  q: host or device [nq * d].  Same outputs and limits as
  * dade_search.  With host buffers the call copies inputs in and results out

@@ -312,7 +312,10 @@ dade_status dade_build_index(const float *base, int64_t n, int32_t d, const dade
     return DADE_OK;
 }
 
-void dade_free_index(dade_index *ix) { delete ix; }
+void dade_free_index(dade_index *ix) {
+    dade::tune_forget(ix);
+    delete ix;
+}
 
 dade_status dade_save_index(const dade_index *ix, const char *path) {
     g_err.clear();

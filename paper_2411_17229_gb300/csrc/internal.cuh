@@ -179,6 +179,9 @@ dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, c
 // FP32 basis W^T and mean on the device, from the host FP64 copies (build.cu).
 dade_status upload_basis(dade_index *ix, cudaStream_t s);
 
+// Drop the tuning choices cached for an index (tune.cpp).
+void tune_forget(const dade_index *ix);
+
 // Index file (index_io.cpp).
 dade_status save_index(const dade_index *ix, const char *path);
 dade_status load_index(const char *path, dade_index *ix);

@@ -93,6 +93,7 @@ SIGNATURES = {
     "dade_search": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
     "dade_query": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
     "dade_scan": (_i32, [_vp, _vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
+    "dade_tune": (_i32, [_vp, _vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
     "dade_reserve": (_i32, [_vp, _i64, _i32]),
     "dade_eps_table": (_i32, [_vp, _f32, _i32, _vp, _vp]),
     "dade_index_info": (_i32, [_vp, _vp]),
@@ -269,6 +270,17 @@ class Index:
                                 schedule=schedule, flags=flags, seed_lists=seed_lists, estimator=estimator,
                                 eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
                        stage_ring=stage_ring))
+
+    def tune(self, q_rot, probe, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, spec=0,
+             threads=0, schedule=SCHED_TILE, flags=0, seed_lists=0, estimator=ESTIMATOR_DADE, eps0=0.0,
+             stage_dims=0, list_chunk=0, stage_ring=0, stream=None):
+        """dade_tune: the fastest result-neutral options for this shape, as {"threads", "flags"}."""
+        o = SearchOpts(mode=mode, tile=tile, spec=spec, threads=threads, schedule=schedule, flags=flags,
+                       seed_lists=seed_lists, estimator=estimator, eps0=eps0, stage_dims=stage_dims,
+                       list_chunk=list_chunk, stage_ring=stage_ring)
+        _check(lib().dade_tune(self._h, _ptr(q_rot), _ptr(probe), q_rot.shape[0], int(k), int(nprobe), float(alpha),
+                               int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
+        return {"threads": o.threads, "flags": o.flags}
 
     def reserve(self, max_nq, max_nprobe):
         _check(lib().dade_reserve(self._h, int(max_nq), int(max_nprobe)))

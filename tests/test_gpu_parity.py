@@ -590,3 +590,42 @@ def test_flat_index_is_a_linear_scan():
     f_ids, f_d = case.gpu_search(10, 1, 0.1, 32, mode=dade.MODE_FD)
     o_ids, o_d, _, oflags = case.oracle_search(10, 1, 0.1, 32, fd=True)
     parity.compare(f_ids, f_d, o_ids, o_d, oflags, case.scale, case.exact_d)
+
+
+@pytest.mark.parametrize("d,schedule,seed", [(128, dade.SCHED_TILE, 0), (128, dade.SCHED_SEEDED, 2),
+                                             (160, dade.SCHED_SEEDED, 2)])
+def test_tune_keeps_results_and_caches(d, schedule, seed):
+    """dade_tune picks among options that leave results unchanged: the tuned
+    options give the base options' bits and counters, and a repeated shape
+    returns the cached choice."""
+    w = synth.Workload(f"tune{d}", 8000, d, 64, 1.0, 16, 0.0, 3.0, 1.0, False, False, 16, (4,), 10, (16,), 0.1)
+    base, queries, labels = synth.make(w)
+    ix = dade.Index(torch.from_numpy(base).cuda(), 16, assign=labels, eps_pairs=3000, tail_from=32)
+    q = torch.from_numpy(queries).cuda()
+    qr = torch.empty_like(q)
+    ix.rotate(q, qr)
+    pr = torch.empty(q.shape[0], 10, dtype=torch.int32, device="cuda")
+    ix.probe(qr, 10, pr)
+    ids = torch.empty(q.shape[0], 20, dtype=torch.int64, device="cuda")
+    dd = torch.empty(q.shape[0], 20, dtype=torch.float32, device="cuda")
+    opts = dict(tile=128, threads=128, schedule=schedule, seed_lists=seed, flags=0)
+    tuned = ix.tune(qr, pr, 20, 10, 0.1, 32, ids, dd, **opts)
+    assert tuned["threads"] in (128, 256) and tuned["flags"] & ~(dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL |
+                                                                 dade.FLAG_SEED_SPLIT) == 0
+    assert ix.tune(qr, pr, 20, 10, 0.1, 32, ids, dd, **opts) == tuned
+    out = []
+    for o in (opts, dict(opts, **tuned)):
+        st = torch.zeros(q.shape[0], 4, dtype=torch.int64, device="cuda")
+        ix.scan(qr, pr, 20, 0.1, 32, ids, dd, stats=st, **o)
+        ix.sync()
+        out.append((ids.cpu().numpy(), dd.cpu().numpy(), st.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
+    assert np.array_equal(out[0][2], out[1][2])
+    # every candidate the tuner may choose gives the same bits (not only the winner)
+    for nt in (128, 256):
+        for fl in (dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL,
+                   dade.FLAG_SEED_SPLIT if schedule == dade.SCHED_SEEDED else dade.FLAG_ROW_TAIL):
+            ix.scan(qr, pr, 20, 0.1, 32, ids, dd, **dict(opts, threads=nt, flags=fl))
+            ix.sync()
+            assert np.array_equal(out[0][0], ids.cpu().numpy())
+            assert np.array_equal(out[0][1].view(np.uint32), dd.cpu().numpy().view(np.uint32))
