@@ -482,6 +482,10 @@ dade_status dade_host_sym_eig(double *a, int32_t n, double *w, double *v);
 /* Message of the last failure on the calling thread ("" if none). */
 const char *dade_last_error(void);
 
+/* Kernels this library has launched in this process (all streams, all
+ * indexes); the difference over a region counts that region's launches. */
+unsigned long long dade_launch_count(void);
+
 /* Library version string. */
 const char *dade_version(void);
 

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <limits>
 #include <new>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -18,7 +19,14 @@ static thread_local std::string g_err;
 
 void set_error(const std::string &msg) { g_err = msg; }
 
+// Kernels launched by this library in this process (every launch site calls
+// launch_check right after its launch).
+static std::atomic<unsigned long long> g_launches{0};
+
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 dade_status launch_check(const char *what) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error(std::string("launch of ") + what + " failed: " + cudaGetErrorString(e));
@@ -311,6 +319,8 @@ dade_status dade_build_index(const float *base, int64_t n, int32_t d, const dade
     *out = ix;
     return DADE_OK;
 }
+
+unsigned long long dade_launch_count(void) { return dade::launch_count(); }
 
 void dade_free_index(dade_index *ix) {
     dade::tune_forget(ix);

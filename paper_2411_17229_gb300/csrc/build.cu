@@ -685,7 +685,8 @@ dade_status upload_basis(dade_index *ix, cudaStream_t s) {
     DADE_TRY(ix->mu32.alloc(sizeof(float) * d));
     DADE_TRY_CUDA(cudaMemcpyAsync(ix->WT32.p, wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice, s));
     DADE_TRY_CUDA(cudaMemcpyAsync(ix->mu32.p, m32.data(), sizeof(float) * d, cudaMemcpyHostToDevice, s));
-    return cudaStreamSynchronize(s) == cudaSuccess ? DADE_OK : launch_check("upload_basis");
+    DADE_TRY_CUDA(cudaStreamSynchronize(s));
+    return DADE_OK;
 }
 
 } // namespace dade

@@ -37,7 +37,8 @@ void set_error(const std::string &msg);
         }                                                                                \
     } while (0)
 
-dade_status launch_check(const char *what);
+dade_status launch_check(const char *what);   // after every kernel launch: error check and launch count
+unsigned long long launch_count();
 
 // ----------------------------------------------------------- list layout ----
 // Per inverted list: offset of its region in the packed data (in floats,

@@ -94,6 +94,7 @@ SIGNATURES = {
     "dade_query": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
     "dade_scan": (_i32, [_vp, _vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
     "dade_tune": (_i32, [_vp, _vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
+    "dade_launch_count": (C.c_uint64, []),
     "dade_reserve": (_i32, [_vp, _i64, _i32]),
     "dade_eps_table": (_i32, [_vp, _f32, _i32, _vp, _vp]),
     "dade_index_info": (_i32, [_vp, _vp]),
