@@ -7,6 +7,7 @@
 
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -42,6 +43,8 @@ Shape shape_of(const dade_index *ix, int64_t nq, int32_t k, int32_t nprobe, floa
 }  // namespace
 
 namespace dade {
+void set_error(const std::string &msg);
+
 // The index is gone: its cached choices go too (called by dade_free_index).
 void tune_forget(const dade_index *ix) {
     std::lock_guard<std::mutex> lock(g_mu);
@@ -53,8 +56,15 @@ void tune_forget(const dade_index *ix) {
 extern "C" dade_status dade_tune(const dade_index *ix, const float *q_rot, const int32_t *probe, int64_t nq,
                                  int32_t k, int32_t nprobe, float alpha, int32_t delta_d, dade_search_opts *opts,
                                  int64_t *ids, float *dists, dade_stream stream) {
-    if (!ix || !q_rot || !probe || !opts || !ids || !dists) return DADE_EINVAL;
-    if (!on_device(q_rot) || !on_device(probe) || !on_device(ids) || !on_device(dists)) return DADE_EINVAL;
+    dade::set_error("");
+    if (!ix || !q_rot || !probe || !opts || !ids || !dists) {
+        dade::set_error("dade_tune: NULL pointer");
+        return DADE_EINVAL;
+    }
+    if (!on_device(q_rot) || !on_device(probe) || !on_device(ids) || !on_device(dists)) {
+        dade::set_error("dade_tune times the scan on device buffers: q_rot, probe, ids and dists must be device memory");
+        return DADE_EINVAL;
+    }
     if (nq <= 0) return DADE_OK;
     const dade_search_opts base = *opts;
     const Shape key = shape_of(ix, nq, k, nprobe, alpha, delta_d, base);
@@ -111,7 +121,9 @@ extern "C" dade_status dade_tune(const dade_index *ix, const float *q_rot, const
                 }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best_ms < 0.f) return st != DADE_OK ? st : DADE_EUNSUPPORTED;
+    if (best_ms < 0.f) {   // every candidate refused: the library's own message stands
+        return st != DADE_OK ? st : DADE_EUNSUPPORTED;
+    }
     opts->threads = best.threads;
     opts->flags = keep | best.flags;
     std::lock_guard<std::mutex> lock(g_mu);
