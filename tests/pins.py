@@ -421,6 +421,30 @@ def pin_search_seeded_trace(o):
     assert seeded[2][0].tolist() == [4, 32 * 3 + 16, 3, 1]
 
 
+def pin_search_whole_list_epochs(o):
+    """Tiles as threshold epochs, worked by hand (equal eigenvalues, eps_d = 0,
+    D = 32, delta_d = 16: prune iff 2 P_16 > r^2).  Query at the origin, K = 1,
+    lists probed A then B; A = {a1 (id 0): 10 in dim 0, a2 (id 1): 12 in dim 0},
+    B = {b1 (id 2): 5 in dim 16}.  Tile 1 (seed 1): a1 is exact (r = +inf) and
+    sets r = 10; a2 is pruned at d = 16 (2 x 144 > 100); b1 (P_16 = 0) is
+    accepted at 25.  Whole-list tiles (tile 4, seed 1): all of A is one epoch
+    with r = +inf, so a2 is computed exactly and accepted too; r = 10 after A
+    and b1 is accepted at 25 either way."""
+    D = 32
+    Xr = np.zeros((3, D))
+    Xr[0, 0], Xr[1, 0], Xr[2, 16] = 10.0, 12.0, 5.0
+    assign = np.array([0, 0, 1], np.int32)
+    cent = np.zeros((2, D))
+    cent[1, 0] = 100.0
+    lam, eps, Qr = np.ones(D), np.zeros(D + 1), np.zeros((1, D))
+    per = o.search(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=1, tile=1, seed=1)
+    whole = o.search(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=1, tile=4, seed=1)
+    for r in (per, whole):
+        assert r[0][0, 0] == 2 and r[1][0, 0] == 25.0
+    assert per[2][0].tolist() == [3, 32 + 16 + 32, 2, 1]
+    assert whole[2][0].tolist() == [3, 32 * 3, 3, 0]
+
+
 def pin_search_seeded_limits(o):
     """Seeded schedule limits: seed >= nprobe is the plain tile schedule;
     FDScanning does not depend on the schedule; freezing r after the seed
