@@ -95,11 +95,23 @@ OR_API void or_mean_cov(const float *X, int64_t n, int d, double *mu, double *C)
  */
 OR_API int or_jacobi_eig(double *A, int d, double *lam, double *V)
 {
+    /* the eigenproblem of a symmetric matrix: take (A + A^T) / 2 (a no-op on
+     * the exactly symmetric covariance of or_mean_cov) */
+    for (int i = 0; i < d; ++i)
+        for (int j = i + 1; j < d; ++j) {
+            double m = 0.5 * (A[(int64_t)i * d + j] + A[(int64_t)j * d + i]);
+            A[(int64_t)i * d + j] = m;
+            A[(int64_t)j * d + i] = m;
+        }
     double fro = 0.0;
     for (int64_t t = 0; t < (int64_t)d * d; ++t) fro += A[t] * A[t];
     fro = sqrt(fro);
+    /* VT = V^T: row k of VT is eigenvector column k, so the updates of two
+     * eigenvector columns touch two contiguous rows */
+    double *VT = (double *)malloc(sizeof(double) * (size_t)d * d);
+    if (!VT) return -1;
     for (int i = 0; i < d; ++i)
-        for (int j = 0; j < d; ++j) V[(int64_t)i * d + j] = (i == j) ? 1.0 : 0.0;
+        for (int j = 0; j < d; ++j) VT[(int64_t)i * d + j] = (i == j) ? 1.0 : 0.0;
 
     int sweep;
     for (sweep = 0; sweep < 100; ++sweep) {
@@ -109,34 +121,46 @@ OR_API int or_jacobi_eig(double *A, int d, double *lam, double *V)
         if (sqrt(off) <= 1e-14 * fro || fro == 0.0) break;
         for (int p = 0; p < d - 1; ++p) {
             for (int q = p + 1; q < d; ++q) {
-                double apq = A[(int64_t)p * d + q];
+                double *Ap = A + (int64_t)p * d, *Aq = A + (int64_t)q * d;
+                double apq = Ap[q];
                 if (apq == 0.0) continue;
-                double app = A[(int64_t)p * d + p], aqq = A[(int64_t)q * d + q];
+                double app = Ap[p], aqq = Aq[q];
                 /* rotation angle that annihilates a_pq */
                 double theta = (aqq - app) / (2.0 * apq);
                 double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
                 double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < d; ++k) {      /* A <- A J  (columns p, q) */
-                    double akp = A[(int64_t)k * d + p], akq = A[(int64_t)k * d + q];
-                    A[(int64_t)k * d + p] = c * akp - s * akq;
-                    A[(int64_t)k * d + q] = s * akp + c * akq;
+                /* A <- J^T A J.  A stays symmetric, so for k outside {p, q} the new
+                 * rows p, q and columns p, q hold the same values: compute them on
+                 * the rows, mirror them into the columns */
+                for (int k = 0; k < d; ++k) {
+                    if (k == p || k == q) continue;
+                    double apk = Ap[k], aqk = Aq[k];
+                    double np = c * apk - s * aqk, nq = s * apk + c * aqk;
+                    Ap[k] = np;
+                    Aq[k] = nq;
+                    A[(int64_t)k * d + p] = np;
+                    A[(int64_t)k * d + q] = nq;
                 }
-                for (int k = 0; k < d; ++k) {      /* A <- J^T A  (rows p, q) */
-                    double apk = A[(int64_t)p * d + k], aqk = A[(int64_t)q * d + k];
-                    A[(int64_t)p * d + k] = c * apk - s * aqk;
-                    A[(int64_t)q * d + k] = s * apk + c * aqk;
-                }
-                A[(int64_t)p * d + q] = 0.0;
-                A[(int64_t)q * d + p] = 0.0;
+                /* the 2 x 2 block: A J (columns p, q), then J^T (rows p, q) */
+                double bpp = c * app - s * apq, bpq = s * app + c * apq;
+                double bqp = c * apq - s * aqq, bqq = s * apq + c * aqq;
+                Ap[p] = c * bpp - s * bqp;
+                Aq[q] = s * bpq + c * bqq;
+                Ap[q] = 0.0;
+                Aq[p] = 0.0;
+                double *Vp = VT + (int64_t)p * d, *Vq = VT + (int64_t)q * d;
                 for (int k = 0; k < d; ++k) {      /* V <- V J */
-                    double vkp = V[(int64_t)k * d + p], vkq = V[(int64_t)k * d + q];
-                    V[(int64_t)k * d + p] = c * vkp - s * vkq;
-                    V[(int64_t)k * d + q] = s * vkp + c * vkq;
+                    double vkp = Vp[k], vkq = Vq[k];
+                    Vp[k] = c * vkp - s * vkq;
+                    Vq[k] = s * vkp + c * vkq;
                 }
             }
         }
     }
     for (int i = 0; i < d; ++i) lam[i] = A[(int64_t)i * d + i];
+    for (int i = 0; i < d; ++i)
+        for (int k = 0; k < d; ++k) V[(int64_t)k * d + i] = VT[(int64_t)i * d + k];
+    free(VT);
     /* order eigenpairs by descending eigenvalue (selection sort: plain) */
     for (int i = 0; i < d; ++i) {
         int best = i;

@@ -27,7 +27,8 @@ PLANTS = [
     ("covariance_not_centred", ["double yj = (double)x[j] - mu[j];", "row[k] += yj * ((double)x[k] - mu[k]);"],
      ["double yj = (double)x[j];", "row[k] += yj * ((double)x[k]);"]),
     ("eigen_ascending", "if (lam[j] > lam[best]) best = j;", "if (lam[j] < lam[best]) best = j;"),
-    ("jacobi_sign", "A[(int64_t)k * d + p] = c * akp - s * akq;", "A[(int64_t)k * d + p] = c * akp + s * akq;"),
+    ("jacobi_sign", "double np = c * apk - s * aqk, nq = s * apk + c * aqk;",
+     "double np = c * apk + s * aqk, nq = s * apk + c * aqk;"),
     ("quantile_floor", "(int64_t)ceil((1.0 - alpha) * (double)m);", "(int64_t)floor((1.0 - alpha) * (double)m);"),
     ("quantile_alpha_side", "(int64_t)ceil((1.0 - alpha) * (double)m);", "(int64_t)ceil(alpha * (double)m);"),
     ("rho_without_sqrt", "rho[(int64_t)t * m + kept] = sqrt(LD / Ld * Pd[dd - 1] / PD);",
