@@ -191,13 +191,17 @@ OR_API int or_pca(const float *X, int64_t n, int d, double *mu, double *W, doubl
 /* Rotation x' = W^T (x - mu): out_ik = sum_j W_jk (x_ij - mu_j)  (Lemma 1). */
 OR_API void or_rotate(const float *X, int64_t n, int d, const double *mu, const double *W, double *out)
 {
+    /* every out_ik sums over j in order; the j loop is outermost so that W is
+     * read a row at a time */
     #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         const float *x = X + i * d;
-        for (int k = 0; k < d; ++k) {
-            double s = 0.0;
-            for (int j = 0; j < d; ++j) s += W[(int64_t)j * d + k] * ((double)x[j] - mu[j]);
-            out[i * d + k] = s;
+        double *o = out + i * d;
+        for (int k = 0; k < d; ++k) o[k] = 0.0;
+        for (int j = 0; j < d; ++j) {
+            const double y = (double)x[j] - mu[j];
+            const double *w = W + (int64_t)j * d;
+            for (int k = 0; k < d; ++k) o[k] += w[k] * y;
         }
     }
 }

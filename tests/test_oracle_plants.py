@@ -20,8 +20,8 @@ PLANTS = [
     ("reject_on_equality", "if (est > bound) { *dims = d; return 0; }",
      "if (est >= bound) { *dims = d; return 0; }"),
     ("strict_accept", "            return P <= r2;\n        }", "            return P < r2;\n        }"),
-    ("rotation_transposed", "s += W[(int64_t)j * d + k] * ((double)x[j] - mu[j]);",
-     "s += W[(int64_t)k * d + j] * ((double)x[j] - mu[j]);"),
+    ("rotation_transposed", "for (int k = 0; k < d; ++k) o[k] += w[k] * y;",
+     "for (int k = 0; k < d; ++k) o[k] += W[(int64_t)k * d + j] * y;"),
     # E[X X^T] without the centring of Lemma 1 (both factors uncentred; one
     # uncentred factor alone is not a mistake since sum_i (x_ij - mu_j) = 0)
     ("covariance_not_centred", ["double yj = (double)x[j] - mu[j];", "row[k] += yj * ((double)x[k] - mu[k]);"],
