@@ -84,12 +84,16 @@ typedef enum {
  *   DADE_SCHED_SEEDED     the first opts->seed_lists probed lists as in
  *                         DADE_SCHED_TILE; every candidate of the later lists
  *                         is tested against r frozen after those lists.  The
- *                         later lists are then scanned list-major: each list's
- *                         rows are staged once for all the queries probing it
- *                         (one persistent launch over (list, query group)
- *                         items), and the K nearest are merged at the end.
- *                         D <= 128 (16-dim blocks: 8); other shapes return
- *                         DADE_EUNSUPPORTED.
+ *                         later lists are then scanned list-major where the
+ *                         list-major kernels apply (D > 112 and delta_d of 16,
+ *                         32, 64 or 128 dims): each list's rows are staged
+ *                         once for all the queries probing it (one persistent
+ *                         launch over (list chunk, query group) items), and
+ *                         the K nearest are merged at the end.  Any other D or
+ *                         delta_d, and DADE_FLAG_SEED_SPLIT, scan them
+ *                         query-major, each query's later lists split over
+ *                         several thread blocks.  Every D and delta_d is
+ *                         served, with the same results either way.
  * A staler threshold can only prune less.  FDScanning results do not depend
  * on the schedule.
  */
@@ -426,9 +430,8 @@ enum { DADE_PROBE_NOALLOC_MAX = 4194304 };
 /*
  * dade_probe without any device memory allocation (the paper has no
  * counterpart; this is a library facility).  For callers that must not call
- * cudaMalloc: code running while a stream is being captured into a CUDA
- * graph, a serving path that must not block on or fail in the allocator in
- * the middle of a request, or a process whose device memory belongs to
+ * cudaMalloc: a serving path that must not block on or fail in the allocator
+ * in the middle of a request, or a process whose device memory belongs to
  * another framework's arena.  Same inputs, outputs and results as
  * dade_probe, but q_rot and probe must be device pointers, and the query x
  * list distance matrix lives in a fixed 16 MiB array that the library holds

@@ -5,7 +5,10 @@
 #include <limits>
 #include <new>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -37,7 +40,40 @@ dade_status launch_check(const char *what) {
 
 namespace {
 thread_local Workspace *t_ws = nullptr;
+
+std::mutex g_attr_mu;
+std::map<std::pair<const void *, int>, size_t> g_smem_set;            // (kernel, device) -> bytes allowed
+std::map<std::tuple<const void *, int, int, size_t>, int> g_resident; // (kernel, device, threads, smem)
 } // namespace
+
+dade_status kernel_smem(const void *func, size_t smem) {
+    if (smem <= 48 * 1024) return DADE_OK;
+    int dev = 0;
+    DADE_TRY_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    size_t &have = g_smem_set[{func, dev}];
+    if (have >= smem) return DADE_OK;
+    DADE_TRY_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    have = smem;
+    return DADE_OK;
+}
+
+dade_status resident_blocks(const void *func, int threads, size_t smem, int *blocks) {
+    int dev = 0;
+    DADE_TRY_CUDA(cudaGetDevice(&dev));
+    DADE_TRY(kernel_smem(func, smem));
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto key = std::make_tuple(func, dev, threads, smem);
+    auto it = g_resident.find(key);
+    if (it == g_resident.end()) {
+        int sms = 0, per = 0;
+        DADE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        DADE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, func, threads, smem));
+        it = g_resident.emplace(key, std::max(1, sms * std::max(1, per))).first;
+    }
+    *blocks = it->second;
+    return DADE_OK;
+}
 
 Workspace &ws(const dade_index *ix) { return t_ws ? *t_ws : ix->ws0; }
 WorkspaceScope::WorkspaceScope(Workspace *w) : prev(t_ws) { t_ws = w; }

@@ -40,6 +40,14 @@ void set_error(const std::string &msg);
 dade_status launch_check(const char *what);   // after every kernel launch: error check and launch count
 unsigned long long launch_count();
 
+// Let kernel `func` use `smem` bytes of dynamic shared memory on the current
+// device.  The attribute is set once per (kernel, device) and size, under a
+// lock, so any host thread may launch on any device.
+dade_status kernel_smem(const void *func, size_t smem);
+// Thread blocks of `func` (threads, smem) resident on the whole current
+// device at once (SMs x blocks per SM, at least 1), cached per (kernel, device).
+dade_status resident_blocks(const void *func, int threads, size_t smem, int *blocks);
+
 // ----------------------------------------------------------- list layout ----
 // Per inverted list: offset of its region in the packed data (in floats,
 // 256-byte aligned), offset of its first slot in the id array, member count

@@ -678,32 +678,18 @@ int grid_of(int64_t work, int threads) {
 
 template <int GB, bool STATS>
 dade_status launch_lm(const LmArgs &a, cudaStream_t s) {
-    static int blocks = 0;
     const size_t smem = LmSmem::total(GB);
-    if (blocks == 0) {
-        DADE_TRY_CUDA(cudaFuncSetAttribute(k_lm<GB, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int dev = 0, sms = 0, per = 0;
-        DADE_TRY_CUDA(cudaGetDevice(&dev));
-        DADE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        DADE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lm<GB, STATS>, LNT, smem));
-        blocks = std::max(1, sms * std::max(1, per));
-    }
+    int blocks = 1;
+    DADE_TRY(resident_blocks((const void *)k_lm<GB, STATS>, LNT, smem, &blocks));
     k_lm<GB, STATS><<<blocks, LNT, smem, s>>>(a);
     return launch_check("k_lm");
 }
 
 template <int GB, bool STATS>
 dade_status launch_lm_g(const LmArgs &a, cudaStream_t s) {
-    static int blocks = 0;
     const size_t smem = LmSmem::total_g(GB);
-    if (blocks == 0) {
-        DADE_TRY_CUDA(cudaFuncSetAttribute(k_lm_g<GB, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int dev = 0, sms = 0, per = 0;
-        DADE_TRY_CUDA(cudaGetDevice(&dev));
-        DADE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        DADE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lm_g<GB, STATS>, LNT, smem));
-        blocks = std::max(1, sms * std::max(1, per));
-    }
+    int blocks = 1;
+    DADE_TRY(resident_blocks((const void *)k_lm_g<GB, STATS>, LNT, smem, &blocks));
     k_lm_g<GB, STATS><<<blocks, LNT, smem, s>>>(a);
     return launch_check("k_lm_g");
 }

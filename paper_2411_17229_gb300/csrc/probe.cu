@@ -230,12 +230,13 @@ dade_status probe(const dade_index *ix, const float *q_rot, int64_t nq, int32_t 
 //
 // dade_probe() keeps its query x centroid distance matrix in the index's
 // workspace, which grows with cudaMalloc on demand.  Some callers must not
-// allocate device memory at all: a call made while a stream is being captured
-// into a CUDA graph (cudaMalloc is not allowed during capture), a serving
-// path that must not block on or fail in the allocator in the middle of a
-// request, or a process whose device memory is owned by another framework's
-// arena.  dade_probe_noalloc() runs the same two kernels with the distance
-// matrix in the fixed array below instead.
+// allocate device memory at all: a serving path that must not block on or
+// fail in the allocator in the middle of a request, or a process whose device
+// memory is owned by another framework's arena.  dade_probe_noalloc() keeps
+// the distance matrix in the fixed array below instead, computes it with a
+// GEMM kernel that stages its operands itself (no operand images), with the
+// same products and the same query norms as dade_probe's kernels (the same
+// bits), and selects the nearest lists with the same exact radix select.
 //
 // The array is a file-scope device variable: every GPU that loads this
 // library reserves DADE_PROBE_NOALLOC_MAX floats (16 MiB) for it until the

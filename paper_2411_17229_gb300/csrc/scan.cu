@@ -417,12 +417,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
 
 template <int NT, bool FD, bool STATS, int LF>
 dade_status launch(const ScanArgs &a, int64_t nq, size_t smem, cudaStream_t s) {
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-        DADE_TRY_CUDA(cudaFuncSetAttribute(k_scan<NT, FD, STATS, LF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-        configured = smem;
-    }
+    DADE_TRY(kernel_smem((const void *)k_scan<NT, FD, STATS, LF>, smem));
     k_scan<NT, FD, STATS, LF><<<(unsigned)nq, NT, smem, s>>>(a);
     return launch_check(FD ? "k_scan<FD>" : (LF ? "k_scan<DADE, lead>" : "k_scan<DADE>"));
 }

@@ -256,12 +256,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_scan_pipe(const ScanArgs a) {
 
 template <int NT, bool STATS>
 dade_status launch_pipe(const ScanArgs &a, int64_t nq, size_t smem, cudaStream_t s) {
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-        DADE_TRY_CUDA(cudaFuncSetAttribute(k_scan_pipe<NT, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-        configured = smem;
-    }
+    DADE_TRY(kernel_smem((const void *)k_scan_pipe<NT, STATS>, smem));
     k_scan_pipe<NT, STATS><<<(unsigned)nq, NT, smem, s>>>(a);
     return launch_check("k_scan_pipe");
 }

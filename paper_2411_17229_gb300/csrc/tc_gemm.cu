@@ -146,7 +146,7 @@ __device__ __forceinline__ void store_tile(const float (&acc)[TN], float *tile, 
 
 // EPI 0: out[m][n] = C[m][n].  EPI 1 (probe distances):
 // out[m][n] = max(0, ||a_m||^2 + bnorm[n] - 2 C[m][n]), ||a_m||^2 summed in
-// FP32 in dimension order by the thread that owns row m.
+// FP32 in k_sqnorm_rows' order (see the epilogue).
 template <int EPI>
 __global__ void __launch_bounds__(128) k_tc_direct(const float *__restrict__ A, int64_t M, int lda,
                                                  const float *__restrict__ mu, const float *__restrict__ B, int nb_rows,
@@ -230,13 +230,19 @@ __global__ void __launch_bounds__(128) k_tc_direct(const float *__restrict__ A, 
         }
     } else {
         // thread tid owns row m0 + tid; the operand buffers are free (every
-        // MMA has completed) and hold the outgoing tile
-        const int64_t row = m0 + tid;
+        // MMA has completed) and hold the outgoing tile.  ||a_m||^2 is summed
+        // exactly as k_sqnorm_rows sums it for dade_probe (lane-strided FMAs
+        // by one warp per row, then an xor-shuffle tree), so both probes
+        // produce the same bits and order near-tied lists alike.
         float an = 0.f;
-        if (EPI == 1 && row < M)
-            for (int k = 0; k < K; ++k) {
-                const float v = A[row * lda + k];
-                an = fmaf(v, v, an);
+        if (EPI == 1)
+            for (int i = 0; i < 32; ++i) {
+                const int64_t r = m0 + warp * 32 + i;
+                float s = 0.f;
+                if (r < M)
+                    for (int k = lane; k < K; k += 32) s = fmaf(A[r * lda + k], A[r * lda + k], s);
+                for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                if (lane == i) an = s;
             }
         store_tile<EPI>(acc, reinterpret_cast<float *>(tc_smem), m0, n0, M, an, bnorm, out, ldo, ncols);
     }
@@ -249,11 +255,7 @@ __global__ void __launch_bounds__(128) k_tc_direct(const float *__restrict__ A, 
 template <int EPI>
 dade_status launch_direct(const float *A, int64_t M, int lda, const float *mu, const float *B, int nb_rows, int ldb, int K,
                       const float *bnorm, float *out, int64_t ldo, int ncols, int *err, cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        DADE_TRY_CUDA(cudaFuncSetAttribute(k_tc_direct<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-        configured = true;
-    }
+    DADE_TRY(kernel_smem((const void *)k_tc_direct<EPI>, TC_SMEM));
     dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)((ncols + TN - 1) / TN));
     k_tc_direct<EPI><<<grid, 128, TC_SMEM, s>>>(A, M, lda, mu, B, nb_rows, ldb, K, bnorm, out, ldo, ncols, err);
     return launch_check(EPI == 0 ? "k_tc_direct<rotate>" : "k_tc_direct<distances>");
@@ -422,11 +424,7 @@ dade_status build_image(const float *X, int64_t nrows, int ld, int K, const floa
 template <int EPI>
 dade_status launch_pipe(const uint32_t *aimg, int64_t M, const uint32_t *bimg, int K, const float *anorm,
                         const float *bnorm, float *out, int64_t ldo, int ncols, int *err, cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        DADE_TRY_CUDA(cudaFuncSetAttribute(k_tc_pipe<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PIPE_SMEM));
-        configured = true;
-    }
+    DADE_TRY(kernel_smem((const void *)k_tc_pipe<EPI>, PIPE_SMEM));
     dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)((ncols + TN - 1) / TN));
     k_tc_pipe<EPI><<<grid, 128, PIPE_SMEM, s>>>(aimg, M, bimg, chunks_of(K), anorm, bnorm, out, ldo, ncols, err);
     return launch_check(EPI == 0 ? "k_tc_pipe<rotate>" : "k_tc_pipe<distances>");

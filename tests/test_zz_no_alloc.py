@@ -1,10 +1,12 @@
 """dade_probe_noalloc against dade_probe (GPU only; collected last on purpose).
 
 dade_probe_noalloc serves callers that must not allocate device memory (for
-example code running while a stream is captured into a CUDA graph, or a
-serving path whose device memory is owned by another allocator).  It must
-give exactly the lists dade_probe gives, call after call, although every call
-reuses the same fixed scratch array.  This file builds what it needs, so it
+example a serving path that must not block on or fail in the allocator in the
+middle of a request, or a process whose device memory is owned by another
+framework's allocator).  It must give exactly the lists dade_probe gives, call
+after call, although every call reuses the same fixed scratch array, and also
+where two lists are tied for a query (both probes compute the same bits, so
+they break the tie alike).  This file builds what it needs, so it
 passes alone in a fresh process as well as after the other tests.
 """
 import ctypes as C
@@ -44,6 +46,24 @@ def test_noalloc_probe_matches_probe_twice(index):
     # first call's leftovers in the shared scratch array
     for rows, nprobe in ((slice(0, 96), 12), (slice(20, 70), 5)):
         q = q_rot[rows].contiguous()
+        expected = torch.empty(q.shape[0], nprobe, dtype=torch.int32, device="cuda")
+        ix.probe(q, nprobe, expected)
+        got = torch.full((q.shape[0], nprobe), -7, dtype=torch.int32, device="cuda")
+        assert _noalloc(ix, q, nprobe, got) == dade.OK, dade.lib().dade_last_error()
+        ix.sync()
+        assert torch.equal(got, expected)
+
+
+def test_noalloc_probe_planted_ties(index):
+    """Queries placed exactly between two centroids, on a centroid, and at the
+    origin: every distance pair that rounds to a tie must be ordered the same
+    way (by list id) by both probes."""
+    ix, q_rot = index
+    cent = torch.from_numpy(ix.export(dade.FIELD_CENTROIDS).reshape(ix.n_clusters, ix.d)).cuda()
+    rows = [0.5 * (cent[a] + cent[b]) for a, b in ((0, 1), (3, 7), (10, 11), (20, 40), (5, 6))]
+    rows += [cent[2].clone(), cent[9].clone(), torch.zeros(ix.d, device="cuda")]
+    q = torch.stack(rows).contiguous()
+    for nprobe in (1, 2, 7):
         expected = torch.empty(q.shape[0], nprobe, dtype=torch.int32, device="cuda")
         ix.probe(q, nprobe, expected)
         got = torch.full((q.shape[0], nprobe), -7, dtype=torch.int32, device="cuda")
