@@ -94,13 +94,29 @@ typedef enum {
  *                         query-major, each query's later lists split over
  *                         several thread blocks.  Every D and delta_d is
  *                         served, with the same results either way.
+ *   DADE_SCHED_ROUNDS     rows instead of lists: round e holds rows
+ *                         [R_e, R_{e+1}) of every probed list, with R_0 = 0,
+ *                         R_1 = opts->tile (any tile >= 1) and R_{e+1} = 2 R_e,
+ *                         and every candidate of round e is tested against r
+ *                         after rounds 0..e-1 (round 0: r = +inf, so its
+ *                         candidates get exact distances).  Every list
+ *                         advances through the same row windows, so a long
+ *                         list is scanned in doubling windows, each split into
+ *                         chunks over many thread blocks, while r tightens
+ *                         between the windows.  Each round runs list-major
+ *                         where the list-major kernels apply (see
+ *                         DADE_SCHED_SEEDED), else, and with
+ *                         DADE_FLAG_SEED_SPLIT or DADE_FLAG_LEAD, query-major
+ *                         split over thread blocks; same results either way.
+ *                         For indexes whose list sizes are very uneven.
  * A staler threshold can only prune less.  FDScanning results do not depend
  * on the schedule.
  */
 typedef enum {
     DADE_SCHED_TILE = 0,
     DADE_SCHED_PIPELINED = 1,
-    DADE_SCHED_SEEDED = 2
+    DADE_SCHED_SEEDED = 2,
+    DADE_SCHED_ROUNDS = 3
 } dade_schedule;
 
 /* dade_search_opts.flags */
@@ -117,7 +133,8 @@ enum {
                                       seeds; with whole-list tiles, each seed epoch too) runs query-major
                                       on the tile kernel, each query's lists split into parts over
                                       several thread blocks (the candidates are independent there),
-                                      instead of list-major.  Same tests and thresholds. */
+                                      instead of list-major.  Same tests and thresholds.  The same for
+                                      every round of DADE_SCHED_ROUNDS. */
 };
 
 /*
@@ -196,7 +213,8 @@ typedef struct {
     int32_t mode;              /* dade_mode (default DADE_MODE_DADE) */
     int32_t tile;              /* candidates per threshold refresh (default 128; 32..256, multiple of 32;
                                   DADE_SCHED_SEEDED also takes any tile >= the longest list: every seed
-                                  list is then one epoch and runs list-major too) */
+                                  list is then one epoch and runs list-major too; DADE_SCHED_ROUNDS:
+                                  rows of every list in the first round, any value >= 1) */
     int64_t *stats;            /* device, optional [nq * 4]: per query candidates scanned, sum of
                                   dimensions used, candidates accepted by the DCO, candidates pruned */
     int32_t spec;              /* tile schedule: 16-dim blocks of a candidate that survived the first

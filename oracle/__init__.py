@@ -20,8 +20,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(_HERE, "dade_oracle.c")
 LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
-SEQUENTIAL, TILE, PROBE_ROUNDS = 0, 1, 2
+SEQUENTIAL, TILE, PROBE_ROUNDS, ROW_ROUNDS = 0, 1, 2, 3
 TIE_TOL = 1e-5
+# Relative width of the decision bracket of ``search_bracket``: decisions of
+# the FP32 path whose two sides lie within this of each other may go either
+# way (the FP32 partial distances and thresholds carry relative errors of a
+# few 1e-6 on these workloads; the bracket covers them with a margin).
+BRACKET_TOL = 2e-5
 
 
 def build(src: str = SRC, out: str = LIB, extra: tuple = ()) -> str:
@@ -64,7 +69,7 @@ class Oracle:
             "or_eps_sample": (i64, [vp, i64, i32, vp, vp, i64, vp, i32, vp]),
             "or_eps_quantile": (f64, [vp, i64, f64]),
             "or_search": (i32, [vp, i64, i32, vp, i32, vp, vp, vp, i64, i32, i32, i32, vp, i32, i32, i32,
-                                i32, f64, vp, vp, vp, vp]),
+                                i32, f64, f64, vp, vp, vp, vp]),
             "or_exact_knn": (None, [vp, i64, i32, vp, i64, i32, vp, vp]),
             "or_estimate_sq": (f64, [vp, vp, i32, i32, vp]),
             "or_dco": (i32, [vp, vp, i32, i32, f64, vp, vp, i32, f64, vp, vp, vp]),
@@ -171,9 +176,11 @@ class Oracle:
 
     # -- Algorithm 1 inside IVF -------------------------------------------
     def search(self, Xr, assign, cent, lam, Qr, K, nprobe, delta_d, eps, schedule=TILE, tile=128, lag=0,
-               tol=TIE_TOL, seed=0):
+               tol=TIE_TOL, seed=0, bias=0.0):
         """Returns ids [nq,K] int64, dists [nq,K] (squared), stats [nq,4], flags [nq].
-        seed > 0: the seeded schedule (threshold frozen after the first `seed` lists)."""
+        seed > 0: the seeded schedule (threshold frozen after the first `seed` lists).
+        schedule ROW_ROUNDS: epochs of rows [R_e, R_{e+1}) of every probed list, R_1 = tile.
+        bias: every decision uses r^2 (1 + bias) (0: the method; see search_bracket)."""
         Xr, cent, Qr = _f64(Xr), _f64(cent), _f64(Qr)
         n, D = Xr.shape
         nq = Qr.shape[0]
@@ -183,10 +190,29 @@ class Oracle:
         e = None if eps is None else _f64(eps)
         rc = self.lib.or_search(_p(Xr), n, D, _p(assign), cent.shape[0], _p(cent), _p(_f64(lam)),
                                 _p(Qr), nq, K, nprobe, delta_d, _p(e), schedule, tile, lag, seed, tol,
-                                _p(ids), _p(dists), _p(stats), _p(flags))
+                                float(bias), _p(ids), _p(dists), _p(stats), _p(flags))
         if rc != 0:
             raise ValueError("or_search rejected its arguments")
         return ids, dists, stats, flags
+
+    def search_bracket(self, *args, btol=BRACKET_TOL, **kw):
+        """``search`` plus its decision bracket.  The search runs three times:
+        as the method (bias 0), with every test and final compare moved a
+        relative ``btol`` towards pruning (bias -btol), and towards keeping
+        (bias +btol).  A query is *stable* when the three runs return the same
+        ids and none of them has a near-tie that no bias moves (flag 4: the K-th
+        place of a merge; flag 8: the probe order, both at relative ``btol``):
+        a computation whose decisions err by less than ``btol`` returns exactly
+        those ids.  Its work counters are stable when the three runs count the
+        same.  Returns ids, dists, stats, flags, stable, stats_stable."""
+        kw = dict(kw, tol=btol)
+        ids, dists, stats, flags = self.search(*args, **kw, bias=0.0)
+        lo = self.search(*args, **kw, bias=-btol)
+        hi = self.search(*args, **kw, bias=btol)
+        boundary = (flags | lo[3] | hi[3]) & (4 | 8)     # in any of the three runs
+        stable = (ids == lo[0]).all(1) & (ids == hi[0]).all(1) & (boundary == 0)
+        stats_stable = (stats == lo[2]).all(1) & (stats == hi[2]).all(1)
+        return ids, dists, stats, flags, stable, stats_stable
 
     def estimate_sq(self, q, o, d, lam):
         """Eq. 13 for one pair from its first d rotated dimensions."""
@@ -261,11 +287,19 @@ class Index:
     def rotate(self, Q):
         return self.o.rotate(Q, self.mu, self.W)
 
-    def search(self, Q, K, nprobe, delta_d, alpha, schedule=TILE, tile=128, prune=True, lag=0, seed=0):
+    def search(self, Q, K, nprobe, delta_d, alpha, schedule=TILE, tile=128, prune=True, lag=0, seed=0, bias=0.0):
         Qr = self.rotate(Q)
         eps = self.eps(alpha, delta_d) if prune else None
         return self.o.search(self.Xr, self.assign, self.cent, self.lam, Qr, K, nprobe, delta_d, eps,
-                             schedule, tile, lag, seed=seed)
+                             schedule, tile, lag, seed=seed, bias=bias)
+
+    def search_bracket(self, Q, K, nprobe, delta_d, alpha, schedule=TILE, tile=128, prune=True, lag=0, seed=0,
+                       btol=BRACKET_TOL):
+        """``search`` with the decision bracket of ``Oracle.search_bracket``."""
+        Qr = self.rotate(Q)
+        eps = self.eps(alpha, delta_d) if prune else None
+        return self.o.search_bracket(self.Xr, self.assign, self.cent, self.lam, Qr, K, nprobe, delta_d, eps,
+                                     schedule, tile, lag, seed=seed, btol=btol)
 
 
 class SampledIndex:
@@ -314,9 +348,18 @@ class SampledIndex:
             eps[d] = self.o.eps_quantile(self.rho[self.dlist.index(d)], alpha)
         return eps
 
-    def search(self, K, nprobe, delta_d, alpha, schedule=TILE, tile=128, prune=True, lag=0, seed=0):
+    def search(self, K, nprobe, delta_d, alpha, schedule=TILE, tile=128, prune=True, lag=0, seed=0, bias=0.0):
         eps = self.eps(alpha, delta_d) if prune else None
         ids, dists, stats, flags = self.o.search(self.Xr, self.assign, self.cent, self.lam, self.Qr, K, nprobe,
-                                                 delta_d, eps, schedule, tile, lag, seed=seed)
+                                                 delta_d, eps, schedule, tile, lag, seed=seed, bias=bias)
         ids = np.where(ids >= 0, self.rows[np.maximum(ids, 0)], -1)
         return ids, dists, stats, flags
+
+    def search_bracket(self, K, nprobe, delta_d, alpha, schedule=TILE, tile=128, prune=True, lag=0, seed=0,
+                       btol=BRACKET_TOL):
+        """``search`` with the decision bracket of ``Oracle.search_bracket``; ids of the full base."""
+        eps = self.eps(alpha, delta_d) if prune else None
+        out = self.o.search_bracket(self.Xr, self.assign, self.cent, self.lam, self.Qr, K, nprobe, delta_d, eps,
+                                    schedule, tile, lag, seed=seed, btol=btol)
+        ids = np.where(out[0] >= 0, self.rows[np.maximum(out[0], 0)], -1)
+        return (ids,) + tuple(out[1:])

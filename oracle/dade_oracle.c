@@ -535,16 +535,27 @@ OR_API int or_dco(const double *q, const double *o, int D, int delta_d, double r
  * of an epoch is tested against r taken after all earlier epochs:
  *   schedule 0  SEQUENTIAL      one candidate per epoch (the paper's order);
  *   schedule 1  TILE(tile)      up to `tile` consecutive members of one list;
- *   schedule 2  PROBE_ROUNDS    one whole list per epoch.
+ *   schedule 2  PROBE_ROUNDS    one whole list per epoch;
+ *   schedule 3  ROW_ROUNDS      epoch e holds rows [R_e, R_{e+1}) of every
+ *                               probed list (probe order, then row), with
+ *                               R_0 = 0, R_1 = tile, R_{e+1} = 2 R_e: every
+ *                               list advances by the same rows per epoch, the
+ *                               epochs doubling, until the longest probed list
+ *                               is done.  Epoch 0 runs with r = +inf.
  * With schedule 1 and lag L > 0, tile t (tiles numbered over the query's
  * whole scan) is tested against r taken after tiles 0..t-1-L only: the
  * threshold of a pipeline that keeps L later tiles in flight.  L = 0 is the
  * plain tile schedule.
- * With seed S > 0 (seeded schedule), the first S probed lists run as above
- * and every candidate of the later lists is tested against r frozen at its
- * value after those S lists (a stale r that is the same for all of them);
- * accepted candidates still enter the K nearest.  S >= nprobe is the plain
- * schedule.
+ * With seed S > 0 (seeded schedule, schedules 0-2), the first S probed lists
+ * run as above and every candidate of the later lists is tested against r
+ * frozen at its value after those S lists (a stale r that is the same for all
+ * of them); accepted candidates still enter the K nearest.  S >= nprobe is
+ * the plain schedule.
+ * bias: every decision of the epoch uses r^2 (1 + bias) in place of r^2, both
+ * the test at d < D and the final compare.  bias = 0 is the method; runs at
+ * bias = -b and +b move every decision within a relative b of its threshold
+ * towards pruning and towards keeping, which brackets what a computation at
+ * lower precision (error below b) can decide.
  * Results are ordered by (squared distance, id); missing slots are (-1, +inf).
  * eps == NULL runs FDScanning.  eps is indexed by d (eps[d], d < D).
  * stats (nq x 4, may be NULL): candidates, sum of dims used, accepted, pruned.
@@ -554,12 +565,30 @@ OR_API int or_dco(const double *q, const double *o, int D, int delta_d, double r
  * can never return, so only the final boundary can change the result),
  * 8 near-tie in the probe order.
  */
+#define OR_PEND 4096   /* accepted candidates held before a merge into the K nearest */
+
+/* Merge the npend pending results behind the ntop kept ones into the K
+ * nearest by (distance, id).  Within one epoch the threshold is fixed, so
+ * merging part of an epoch's results early decides nothing differently. */
+static void merge_pending(kv_t *buf, int *ntop, int *npend, int K, double *dropped)
+{
+    if (*npend == 0) return;
+    int u = *ntop + *npend;
+    qsort(buf, (size_t)u, sizeof(kv_t), kv_cmp);
+    if (u > K && buf[K].key < *dropped) *dropped = buf[K].key;
+    *ntop = u < K ? u : K;
+    *npend = 0;
+}
+
 OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, int nc,
                      const double *cent, const double *lam, const double *Qr, int64_t nq,
                      int K, int nprobe, int delta_d, const double *eps, int schedule, int tile, int lag,
-                     int seed, double tol, int64_t *ids, double *dists, int64_t *stats, int32_t *flags)
+                     int seed, double tol, double bias, int64_t *ids, double *dists, int64_t *stats,
+                     int32_t *flags)
 {
-    if (K < 1 || nprobe < 1 || nprobe > nc || delta_d < 1 || (schedule == 1 && tile < 1) || lag < 0 || seed < 0)
+    if (K < 1 || nprobe < 1 || nprobe > nc || delta_d < 1 || schedule < 0 || schedule > 3 ||
+        ((schedule == 1 || schedule == 3) && tile < 1) || lag < 0 || seed < 0 ||
+        (schedule == 3 && (lag > 0 || seed > 0)) || !(bias > -1.0))
         return -1;
     /* inverted lists, members in ascending id */
     int64_t *start = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
@@ -577,51 +606,68 @@ OR_API int or_search(const double *Xr, int64_t n, int D, const int32_t *assign, 
 
     #pragma omp parallel
     {
-        int64_t maxlen = 0;
-        for (int c = 0; c < nc; ++c) if (start[c + 1] - start[c] > maxlen) maxlen = start[c + 1] - start[c];
-        kv_t *buf = (kv_t *)malloc(sizeof(kv_t) * (size_t)(K + maxlen + 1));
+        kv_t *buf = (kv_t *)malloc(sizeof(kv_t) * (size_t)(K + OR_PEND));
         double *hist = (double *)malloc(sizeof(double) * (size_t)(lag + 1));   /* r^2 after recent epochs */
         #pragma omp for schedule(dynamic, 1)
         for (int64_t qi = 0; qi < nq; ++qi) {
             const double *q = Qr + qi * D;
-            int ntop = 0, tie = 0;
+            const int32_t *pq = probe + qi * nprobe;
+            int ntop = 0, npend = 0, tie = 0;
             int64_t epoch = 0;
             double dropped = INFINITY;   /* best squared distance accepted but not kept */
             int64_t st[4] = {0, 0, 0, 0};
             double r2_seed = INFINITY;
-            for (int j = 0; j < nprobe; ++j) {
-                int c = probe[qi * nprobe + j];
-                if (seed > 0 && j == seed) r2_seed = ntop == K ? buf[K - 1].key : INFINITY;
-                int64_t len = start[c + 1] - start[c];
-                int64_t elen = schedule == 0 ? 1 : schedule == 1 ? tile : (len > 0 ? len : 1);
-                for (int64_t e0 = 0; e0 < len; e0 += elen) {
-                    double r2 = ntop == K ? buf[K - 1].key : INFINITY;
-                    if (lag > 0) r2 = epoch - 1 - lag >= 0 ? hist[(epoch - 1 - lag) % (lag + 1)] : INFINITY;
-                    if (seed > 0 && j >= seed) r2 = r2_seed;
-                    double r = sqrt(r2);
-                    int npend = 0;
-                    int64_t e1 = e0 + elen < len ? e0 + elen : len;
-                    for (int64_t t = e0; t < e1; ++t) {
-                        int64_t id = members[start[c] + t];
-                        double d2 = 0.0;
-                        int dims = 0;
-                        int acc = dco(q, Xr + id * D, D, delta_d, r, r2, Lam, eps, eps != NULL, tol,
-                                      &d2, &dims, &tie);
-                        st[0] += 1;
-                        st[1] += dims;
-                        if (acc) { st[2] += 1; buf[ntop + npend].key = d2; buf[ntop + npend].id = id; ++npend; }
-                        else if (dims < D) st[3] += 1;
+            /* one candidate against the epoch's threshold r2 (biased by the bracket) */
+            #define OR_VISIT(id_, r2_)                                                               \
+                do {                                                                                 \
+                    double r2b = (r2_) * (1.0 + bias), d2 = 0.0;                                     \
+                    int dims = 0;                                                                    \
+                    int acc = dco(q, Xr + (id_) * D, D, delta_d, sqrt(r2b), r2b, Lam, eps,           \
+                                  eps != NULL, tol, &d2, &dims, &tie);                               \
+                    st[0] += 1;                                                                      \
+                    st[1] += dims;                                                                   \
+                    if (acc) {                                                                       \
+                        st[2] += 1;                                                                  \
+                        if (npend == OR_PEND) merge_pending(buf, &ntop, &npend, K, &dropped);        \
+                        buf[ntop + npend].key = d2;                                                  \
+                        buf[ntop + npend].id = (id_);                                                \
+                        ++npend;                                                                     \
+                    } else if (dims < D) st[3] += 1;                                                 \
+                } while (0)
+            if (schedule == 3) {
+                int64_t lo = 0, hi = tile, longest = 0;
+                for (int j = 0; j < nprobe; ++j)
+                    if (start[pq[j] + 1] - start[pq[j]] > longest) longest = start[pq[j] + 1] - start[pq[j]];
+                while (lo < longest) {
+                    double r2 = ntop < K ? INFINITY : buf[K - 1].key;   /* after epochs 0..e-1 */
+                    for (int j = 0; j < nprobe; ++j) {
+                        int c = pq[j];
+                        int64_t len = start[c + 1] - start[c];
+                        for (int64_t t = lo; t < hi && t < len; ++t) OR_VISIT(members[start[c] + t], r2);
                     }
-                    if (npend > 0) {
-                        int u = ntop + npend;
-                        qsort(buf, (size_t)u, sizeof(kv_t), kv_cmp);
-                        if (u > K && buf[K].key < dropped) dropped = buf[K].key;
-                        ntop = u < K ? u : K;
+                    merge_pending(buf, &ntop, &npend, K, &dropped);
+                    lo = hi;
+                    hi = 2 * hi;
+                }
+            } else {
+                for (int j = 0; j < nprobe; ++j) {
+                    int c = pq[j];
+                    if (seed > 0 && j == seed) r2_seed = ntop == K ? buf[K - 1].key : INFINITY;
+                    int64_t len = start[c + 1] - start[c];
+                    int64_t elen = schedule == 0 ? 1 : schedule == 1 ? tile : (len > 0 ? len : 1);
+                    for (int64_t e0 = 0; e0 < len; e0 += elen) {
+                        double r2 = ntop == K ? buf[K - 1].key : INFINITY;
+                        if (lag > 0) r2 = epoch - 1 - lag >= 0 ? hist[(epoch - 1 - lag) % (lag + 1)] : INFINITY;
+                        if (seed > 0 && j >= seed) r2 = r2_seed;
+                        int64_t e1 = e0 + elen < len ? e0 + elen : len;
+                        for (int64_t t = e0; t < e1; ++t) OR_VISIT(members[start[c] + t], r2);
+                        merge_pending(buf, &ntop, &npend, K, &dropped);
+                        if (lag > 0) hist[epoch % (lag + 1)] = ntop == K ? buf[K - 1].key : INFINITY;
+                        ++epoch;
                     }
-                    if (lag > 0) hist[epoch % (lag + 1)] = ntop == K ? buf[K - 1].key : INFINITY;
-                    ++epoch;
                 }
             }
+            #undef OR_VISIT
             if (ntop == K && isfinite(dropped) && near_tie(buf[K - 1].key, dropped, tol)) tie |= 4;
             for (int s = 0; s < K; ++s) {
                 ids[qi * K + s] = s < ntop ? buf[s].id : -1;

@@ -178,13 +178,15 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
     const int tile = opts && opts->tile ? opts->tile : 128;
     // the seeded schedule also takes a tile that holds every list (one epoch per list)
     const bool whole_lists = opts && opts->schedule == DADE_SCHED_SEEDED && tile >= ix->max_list;
-    DADE_CHECK_ARG((tile >= 32 && tile <= 256 && tile % 32 == 0) || (whole_lists && tile >= 32),
-                   "tile must be a multiple of 32 in [32, 256] (seeded schedule: or at least the longest list)");
+    const bool rounds = opts && opts->schedule == DADE_SCHED_ROUNDS;
+    DADE_CHECK_ARG((tile >= 32 && tile <= 256 && tile % 32 == 0) || (whole_lists && tile >= 32) || (rounds && tile >= 1),
+                   "tile must be a multiple of 32 in [32, 256] (seeded schedule: or at least the longest list; "
+                   "row rounds: any first-round row count >= 1)");
     DADE_CHECK_ARG(!opts || (opts->spec >= 0 && opts->spec <= 8), "spec outside 0..8");
     DADE_CHECK_ARG(!opts || opts->threads == 0 || opts->threads == 128 || opts->threads == 256,
                    "threads must be 0 (default), 128 or 256");
     DADE_CHECK_ARG(!opts || opts->schedule == DADE_SCHED_PIPELINED || opts->schedule == DADE_SCHED_TILE ||
-                       opts->schedule == DADE_SCHED_SEEDED,
+                       opts->schedule == DADE_SCHED_SEEDED || opts->schedule == DADE_SCHED_ROUNDS,
                    "unknown schedule");
     DADE_CHECK_ARG(!opts || opts->seed_lists >= 0, "seed_lists < 0");
     DADE_CHECK_ARG(!opts || opts->list_chunk == 0 || (opts->list_chunk >= 64 && opts->list_chunk % 64 == 0),
@@ -203,7 +205,8 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
     if (opts && (opts->flags & DADE_FLAG_LEAD)) {
         DADE_CHECK_ARG(mode == DADE_MODE_DADE, "DADE_FLAG_LEAD needs mode DADE_MODE_DADE");
         DADE_CHECK_ARG(ix->lead_format != DADE_LEAD_NONE, "DADE_FLAG_LEAD on an index built without a lead copy");
-        DADE_CHECK_ARG(opts->schedule != DADE_SCHED_PIPELINED, "DADE_FLAG_LEAD needs the tile or seeded schedule");
+        DADE_CHECK_ARG(opts->schedule != DADE_SCHED_PIPELINED,
+                       "DADE_FLAG_LEAD needs the tile, seeded or row-rounds schedule");
         DADE_CHECK_ARG(std::min(delta_d, ix->dp) <= ix->lead_dims,
                        "DADE_FLAG_LEAD needs min(delta_d, D rounded up to 16) <= the index's lead_dims");
     }

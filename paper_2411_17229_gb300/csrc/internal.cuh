@@ -172,6 +172,7 @@ struct ScanParams {
     int32_t stage_ring;      // tile kernel: staged units in flight per CTA (0: 2)
     // split mode of the tile kernel (parts > 0; see ScanArgs)
     int32_t parts, c0;
+    int32_t row_lo, row_hi;  // split passes: rows [row_lo, min(len, row_hi)) of every list (row_hi 0: all)
     const float *r2src;
     unsigned long long *acc;
     int *acnt;
@@ -184,6 +185,8 @@ struct ScanParams {
 dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s);
 // DADE_SCHED_SEEDED with 0 < p.seed_lists < p.nprobe (lm.cu).
 dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s);
+// DADE_SCHED_ROUNDS (lm.cu).
+dade_status scan_rounds(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s);
 
 // FP32 basis W^T and mean on the device, from the host FP64 copies (build.cu).
 dade_status upload_basis(dade_index *ix, cudaStream_t s);

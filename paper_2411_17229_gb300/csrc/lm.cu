@@ -17,6 +17,7 @@
 // query takes the K smallest keys of the first-S-lists result and of its
 // accepted candidates (radix select, then rank sort).
 #include <algorithm>
+#include <climits>
 
 #include "internal.cuh"
 #include "scan_common.cuh"
@@ -53,8 +54,13 @@ struct LmArgs {
     int q_stride, nc, k, d, tail_nb0, tail_w;
     int nb, n_inc;               // 16-dim blocks of the layout, increments (k_lm_g)
     int chunk_tiles;             // tiles of a list per work item (a long list is several items)
+    int row_lo, row_hi;          // rows [row_lo, min(len, row_hi)) of every list are scanned; tiles
+                                 // of LT rows start at row_lo
     float coef[DADE_MAX_DIM / DADE_BLOCK];   // prune iff P > coef[j] r^2 after increment j
 };
+
+// End of the rows of a list of `len` members that a pass scans.
+__device__ __forceinline__ int lm_end(const LmArgs &a, int len) { return min(len, a.row_hi); }
 
 struct LmSmem {
     static constexpr size_t stage(int gb) { return sizeof(float) * (size_t)gb * LT * 16; }
@@ -191,10 +197,11 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
         const int qb = a.lq_off[c] + (local % ngroups) * LG;
         const int ng = min(LG, a.lq_off[c + 1] - qb);
         const ListMeta m = a.meta[c];
+        const int rend = lm_end(a, m.len);   // tile t: rows [row_lo + t LT, ...) up to rend
         const int t0 = (local / ngroups) * a.chunk_tiles;
-        const int ntile = min((m.len + LT - 1) / LT, t0 + a.chunk_tiles);   // end of this item's tiles
+        const int ntile = min(max(0, (rend - a.row_lo + LT - 1) / LT), t0 + a.chunk_tiles);   // end of this item's tiles
         auto issue = [&](int t) {   // thread 0: first-increment slabs of tile t
-            const int buf = t & 1, i0 = t * LT, tn = min(LT, m.len - i0);
+            const int buf = t & 1, i0 = a.row_lo + t * LT, tn = min(LT, rend - i0);
             const uint32_t bar = su32(&bars[buf]);
             mbar_expect_tx(bar, (uint32_t)(GB * tn * 64));
             for (int b = 0; b < GB; ++b)
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
                 return;
             }
             ++used[buf];
-            const int i0 = t * LT, tn = min(LT, m.len - i0);
+            const int i0 = a.row_lo + t * LT, tn = min(LT, rend - i0);
             const float *st = stage + (size_t)buf * GB * LT * 16;
             for (int g = warp; g < ng; g += LNW) {
                 const int q = s_q[g];
@@ -386,10 +393,11 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
         const int qb = a.lq_off[c] + (local % ngroups) * LG;
         const int ng = min(LG, a.lq_off[c + 1] - qb);
         const ListMeta m = a.meta[c];
+        const int rend = lm_end(a, m.len);   // tile t: rows [row_lo + t LT, ...) up to rend
         const int t0 = (local / ngroups) * a.chunk_tiles;
-        const int ntile = min((m.len + LT - 1) / LT, t0 + a.chunk_tiles);   // end of this item's tiles
+        const int ntile = min(max(0, (rend - a.row_lo + LT - 1) / LT), t0 + a.chunk_tiles);   // end of this item's tiles
         auto issue = [&](int t) {
-            const int buf = t & 1, i0 = t * LT, tn = min(LT, m.len - i0);
+            const int buf = t & 1, i0 = a.row_lo + t * LT, tn = min(LT, rend - i0);
             const uint32_t bar = su32(&bars[buf]);
             mbar_expect_tx(bar, (uint32_t)(GB * tn * 64));
             for (int b = 0; b < GB; ++b)
@@ -417,7 +425,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
                 return;
             }
             ++used[buf];
-            const int i0 = t * LT, tn = min(LT, m.len - i0);
+            const int i0 = a.row_lo + t * LT, tn = min(LT, rend - i0);
             const float *st = stage + (size_t)buf * GB * LT * 16;
             for (int g = warp; g < ng; g += LNW) {
                 const int q = s_q[g];
@@ -544,15 +552,18 @@ __global__ void k_lm_count(const int32_t *__restrict__ probe, int64_t nq, int np
     }
 }
 
-// items[c] = ceil(cnt[c] / LG) query groups x ceil(tiles of c / chunk_tiles)
-// chunks; both arrays get a trailing 0 for the scans.
+// items[c] = ceil(cnt[c] / LG) query groups x ceil(tiles of c in the row
+// window / chunk_tiles) chunks (none when the window holds no row of c);
+// both arrays get a trailing 0 for the scans.  off is written only when
+// `with_off` (the query groups do not change between the rounds of a pass).
 __global__ void k_lm_items(const int *__restrict__ cnt, const ListMeta *__restrict__ meta, int nc, int chunk_tiles,
-                           int *__restrict__ off, int *__restrict__ items) {
+                           int row_lo, int row_hi, int with_off, int *__restrict__ off, int *__restrict__ items) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= nc; c += gridDim.x * blockDim.x) {
         const int v = c < nc ? cnt[c] : 0;
-        off[c] = v;
-        const int tiles = c < nc ? (meta[c].len + LT - 1) / LT : 0;
-        items[c] = v > 0 ? ((v + LG - 1) / LG) * max(1, (tiles + chunk_tiles - 1) / chunk_tiles) : 0;
+        if (with_off) off[c] = v;
+        const int rows = c < nc ? min(meta[c].len, row_hi) - row_lo : 0;
+        const int tiles = rows > 0 ? (rows + LT - 1) / LT : 0;
+        items[c] = (v > 0 && tiles > 0) ? ((v + LG - 1) / LG) * ((tiles + chunk_tiles - 1) / chunk_tiles) : 0;
     }
 }
 
@@ -728,8 +739,11 @@ int64_t accept_cap(const dade_index *ix, int lists) {
     return std::min<int64_t>((int64_t)lists * std::max(ix->max_list, 1), 1 << 16);
 }
 
+// rows [row_lo, min(len, row_hi)) of every list (the row-rounds schedule);
+// `lists` = false reuses the (list, query) groups of the previous call with
+// the same probe positions and rebuilds only the work items of the window.
 dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int c0, int c1, int gb, bool prune,
-                     cudaStream_t s) {
+                     cudaStream_t s, int row_lo = 0, int row_hi = INT_MAX, bool lists = true) {
     const int nc = ix->nc, np = p.nprobe;
     const int64_t pairs = nq * (int64_t)(c1 - c0);
     Workspace &w = ws(ix);
@@ -741,19 +755,24 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     const int64_t cap = accept_cap(ix, c1 - c0);
     DADE_TRY(w.lm_acc.ensure(sizeof(unsigned long long) * (size_t)(nq * cap)));
     DADE_TRY(w.lm_acnt.ensure(sizeof(int) * (size_t)nq));
-    DADE_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(nc + 1), s));
+    if (lists) DADE_TRY_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(nc + 1), s));
     DADE_TRY_CUDA(cudaMemsetAsync(w.lm_acnt.p, 0, sizeof(int) * (size_t)nq, s));
     DADE_TRY_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned), s));
-    k_lm_count<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, cnt);
-    DADE_TRY(launch_check("k_lm_count"));
+    if (lists) {
+        k_lm_count<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, cnt);
+        DADE_TRY(launch_check("k_lm_count"));
+    }
     const int chunk_tiles = std::max(1, (p.list_chunk > 0 ? p.list_chunk : 4096) / LT);
-    k_lm_items<<<grid_of(nc + 1, 256), 256, 0, s>>>(cnt, ix->meta.as<ListMeta>(), nc, chunk_tiles, off, items);
+    k_lm_items<<<grid_of(nc + 1, 256), 256, 0, s>>>(cnt, ix->meta.as<ListMeta>(), nc, chunk_tiles, row_lo, row_hi,
+                                                    lists ? 1 : 0, off, items);
     DADE_TRY(launch_check("k_lm_items"));
-    DADE_TRY(exclusive_scan_int(off, nc + 1, s));
+    if (lists) DADE_TRY(exclusive_scan_int(off, nc + 1, s));
     DADE_TRY(exclusive_scan_int(items, nc + 1, s));
-    DADE_TRY_CUDA(cudaMemcpyAsync(fill, off, sizeof(int) * (size_t)(nc + 1), cudaMemcpyDeviceToDevice, s));
-    k_lm_scatter<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, fill, lq_items);
-    DADE_TRY(launch_check("k_lm_scatter"));
+    if (lists) {
+        DADE_TRY_CUDA(cudaMemcpyAsync(fill, off, sizeof(int) * (size_t)(nc + 1), cudaMemcpyDeviceToDevice, s));
+        k_lm_scatter<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, fill, lq_items);
+        DADE_TRY(launch_check("k_lm_scatter"));
+    }
     LmArgs a{};
     a.data = ix->data.as<float>();
     a.ids = ix->ids.as<int32_t>();
@@ -771,6 +790,8 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     a.cap = cap;
     a.q_stride = p.q_stride;
     a.chunk_tiles = chunk_tiles;
+    a.row_lo = row_lo;
+    a.row_hi = row_hi;
     a.nc = nc;
     a.k = p.k;
     a.d = ix->d;
@@ -880,6 +901,68 @@ dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, c
         DADE_TRY(scan(ix, nq, p1, s));
     }
     return lm_round(ix, nq, p, S, np, gb, !fd, s);
+}
+
+// The row-rounds schedule (DADE_SCHED_ROUNDS): round e holds rows
+// [R_e, R_{e+1}) of every probed list, R_0 = 0, R_1 = p.tile, R_{e+1} = 2 R_e,
+// and every candidate of the round is tested against the query's r after the
+// earlier rounds (r = +inf in round 0).  Within a round r is frozen, so the
+// round runs list-major (each list window staged once for all the queries
+// that probe it, a long window cut into chunks over many thread blocks) or,
+// where the list-major kernels do not apply and with DADE_FLAG_SEED_SPLIT,
+// query-major with each query's lists split over thread blocks; then the K
+// nearest are merged.  Rounds continue until they pass the longest list.
+dade_status scan_rounds(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s) {
+    if (nq == 0) return DADE_OK;
+    const int np = p.nprobe;
+    const bool fd = p.mode == DADE_MODE_FD;
+    const int gb = fd ? std::min(LNB, ix->nb) : std::min(p.delta_d / 16, ix->nb);
+    const bool lm_ok = ix->nb == LNB ? (gb == 1 || gb == 2 || gb == 4 || gb == 8)
+                                     : (ix->nb > LNB && (gb == 1 || gb == 2 || gb == 4 || gb == 8));
+    k_lm_reset<<<grid_of(nq * (int64_t)p.k, 256), 256, 0, s>>>(p.ids, p.dists, nq * (int64_t)p.k);
+    DADE_TRY(launch_check("k_lm_reset"));
+    if (p.stats) DADE_TRY_CUDA(cudaMemsetAsync(p.stats, 0, sizeof(int64_t) * 4 * (size_t)nq, s));
+    if (p.lead_stats) DADE_TRY_CUDA(cudaMemsetAsync(p.lead_stats, 0, sizeof(int64_t) * (size_t)nq, s));
+    const int64_t longest = std::max(ix->max_list, 1);
+    const int64_t r1 = std::max(p.tile, 1);
+    if (lm_ok && !p.seed_split && !p.use_lead) {
+        bool first = true;
+        for (int64_t lo = 0, hi = r1; lo < longest; lo = hi, hi *= 2) {
+            DADE_TRY(lm_round(ix, nq, p, 0, np, fd ? LNB : gb, !fd, s, (int)lo, (int)std::min<int64_t>(hi, INT_MAX),
+                              first));
+            first = false;
+        }
+        return DADE_OK;
+    }
+    // query-major: every round over all probe positions, each query's lists in parts over thread blocks
+    Workspace &w = ws(ix);
+    const int64_t cap = accept_cap(ix, np);
+    DADE_TRY(w.lm_acc.ensure(sizeof(unsigned long long) * (size_t)(nq * cap)));
+    DADE_TRY(w.lm_acnt.ensure(sizeof(int) * (size_t)nq));
+    int dev = 0, sms = 0;
+    DADE_TRY_CUDA(cudaGetDevice(&dev));
+    DADE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t slots = (int64_t)sms * (768 / (p.threads == 256 ? 256 : 128));
+    ScanParams q = p;
+    q.schedule = DADE_SCHED_TILE;
+    q.seed_split = 0;
+    q.pstride = np;
+    q.tile = 128;
+    q.r2src = p.dists;
+    q.acc = w.lm_acc.as<unsigned long long>();
+    q.acnt = w.lm_acnt.as<int>();
+    q.cap = cap;
+    q.c0 = 0;
+    q.parts = (int)std::min<int64_t>(np, std::max<int64_t>(1, (8 * slots + nq - 1) / nq));
+    for (int64_t lo = 0, hi = r1; lo < longest; lo = hi, hi *= 2) {
+        DADE_TRY_CUDA(cudaMemsetAsync(w.lm_acnt.p, 0, sizeof(int) * (size_t)nq, s));
+        q.row_lo = (int)lo;
+        q.row_hi = (int)std::min<int64_t>(hi, INT_MAX);
+        DADE_TRY(scan(ix, nq, q, s));
+        k_lm_merge<<<(unsigned)nq, MT, 0, s>>>(p.ids, p.dists, p.k, q.acc, q.acnt, cap);
+        DADE_TRY(launch_check("k_lm_merge"));
+    }
+    return DADE_OK;
 }
 
 } // namespace dade

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
     for (int k = tid; k < a.dp; k += NT) qv[k] = k < a.d ? a.q_rot[qi * a.q_stride + k] : 0.f;
     for (int p = tid; p < min(a.nprobe, PMETA); p += NT) {
         const ListMeta m = a.meta[plist[p]];
-        smeta[p] = make_int4((int)(m.base >> 6), (int)m.slot, m.len, m.np);
+        smeta[p] = make_int4((int)(m.base >> 6), (int)m.slot, list_end(a, m.len), m.np);
     }
     if (tid == 0) {
         for (int s = 0; s < a.ns; ++s) mbar_init(su32(&bars[s]), 1);
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
             issue(a, smeta, plist, c, slot, stage, bars);
         }
     };
-    Cur cc{pbeg, 0, 0};
+    Cur cc{pbeg, a.row_lo, 0};
     normalize(cc, a, smeta, plist);
     Cur ic = cc;          // issue cursor (thread 0 only)
     int issued = 0;       // units issued (thread 0 only)
@@ -446,6 +446,7 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     if (nq == 0) return DADE_OK;
     if (p.schedule == DADE_SCHED_SEEDED && p.seed_lists > 0 && p.seed_lists < p.nprobe)
         return scan_seeded(ix, nq, p, s);
+    if (p.schedule == DADE_SCHED_ROUNDS && p.parts == 0) return scan_rounds(ix, nq, p, s);
     ScanArgs a{};
     a.data = ix->data.as<float>();
     a.ids = ix->ids.as<int32_t>();
@@ -471,6 +472,8 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
         a.acc = p.acc;
         a.acnt = p.acnt;
         a.cap = p.cap;
+        a.row_lo = p.row_lo;
+        a.row_hi = p.row_hi;
     }
     a.pstride = p.pstride > 0 ? p.pstride : p.nprobe;
     a.d = ix->d;

@@ -56,7 +56,15 @@ struct ScanArgs {
     int *acnt;
     int64_t cap;
     int parts, c0;
+    // row window of every list (split passes of the row-rounds schedule): rows
+    // [row_lo, min(len, row_hi)) are scanned; row_hi = 0 means no upper limit
+    int row_lo, row_hi;
 };
+
+// Rows of a list of `len` members that a pass scans end here.
+__device__ __forceinline__ int list_end(const ScanArgs &a, int len) {
+    return a.row_hi > 0 ? min(len, a.row_hi) : len;
+}
 
 // The query a CTA runs.
 __device__ __forceinline__ int64_t cta_query(const ScanArgs &a) {
@@ -140,7 +148,7 @@ constexpr int PMETA = 1024;   // probes whose descriptors are preloaded
 __device__ __forceinline__ int4 meta_of(const ScanArgs &a, const int4 *sm, const int32_t *plist, int p) {
     if (p < PMETA) return sm[p];
     const ListMeta m = a.meta[plist[p]];
-    return make_int4((int)(m.base >> 6), (int)m.slot, m.len, m.np);
+    return make_int4((int)(m.base >> 6), (int)m.slot, list_end(a, m.len), m.np);
 }
 
 // Tile cursor: probe position p, first candidate i0, increment j.
@@ -151,7 +159,7 @@ struct Cur {
 __device__ __forceinline__ void normalize(Cur &c, const ScanArgs &a, const int4 *sm, const int32_t *plist) {
     while (c.p < a.nprobe && c.i0 >= meta_of(a, sm, plist, c.p).z) {
         ++c.p;
-        c.i0 = 0;
+        c.i0 = a.row_lo;
         c.j = 0;
     }
 }

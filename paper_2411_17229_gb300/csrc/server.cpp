@@ -263,7 +263,8 @@ dade_status dade_server_create(const dade_index *ix, const dade_server_opts *opt
     // accept buffer of the list-major phase
     const int64_t B = opts->max_batch, d = ix->d, np = opts->max_nprobe;
     int64_t per = B * (d * 4 * 2 + (int64_t)ix->nc * 4 + np * 4 + (int64_t)opts->max_k * 12 + d * 8 + 64);
-    if (opts->schedule == DADE_SCHED_SEEDED) per += B * np * (int64_t)std::max(ix->max_list, 1) * 8;
+    if (opts->schedule == DADE_SCHED_SEEDED || opts->schedule == DADE_SCHED_ROUNDS)
+        per += B * std::min<int64_t>(np * (int64_t)std::max(ix->max_list, 1), 1 << 16) * 8;
     int n = opts->slots;
     if (opts->device_budget > 0) n = (int)std::min<int64_t>(n, opts->device_budget / std::max<int64_t>(per, 1));
     if (n < 1) {

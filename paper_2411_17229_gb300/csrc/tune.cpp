@@ -82,7 +82,8 @@ extern "C" dade_status dade_tune(const dade_index *ix, const float *q_rot, const
     if (st != DADE_OK) return st;
     std::vector<int32_t> threads = {128, 256}, orders = {0, DADE_FLAG_QUERY_ORDER}, tails = {0}, splits = {0};
     if (info.tail_from > 0) tails.push_back(DADE_FLAG_ROW_TAIL);
-    if (base.schedule == DADE_SCHED_SEEDED && base.seed_lists < nprobe) splits.push_back(DADE_FLAG_SEED_SPLIT);
+    if ((base.schedule == DADE_SCHED_SEEDED && base.seed_lists < nprobe) || base.schedule == DADE_SCHED_ROUNDS)
+        splits.push_back(DADE_FLAG_SEED_SPLIT);
     const int32_t keep = base.flags & ~KNOB_FLAGS;
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;

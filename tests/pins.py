@@ -364,6 +364,168 @@ def pin_search_lagged_tiles(o):
     assert lagged[2][:, 3].sum() <= a[2][:, 3].sum()
 
 
+def _hand_lists(points, assign, nlists, D=32):
+    """Rotated points given by (dim, value) pairs, equal eigenvalues, eps_d = 0,
+    lists probed in index order (centroid j sits at 100 j along dim 0, the
+    query at the origin)."""
+    Xr = np.zeros((len(points), D))
+    for i, coords in enumerate(points):
+        for dim, v in coords:
+            Xr[i, dim] = v
+    cent = np.zeros((nlists, D))
+    cent[:, 0] = 100.0 * np.arange(nlists)
+    return Xr, np.array(assign, np.int32), cent, np.ones(D), np.zeros(D + 1), np.zeros((1, D))
+
+
+def pin_search_lagged_trace(o):
+    """Lagged tile schedule, worked by hand (tile 1: every candidate is a tile;
+    equal eigenvalues and eps_d = 0, D = 32, delta_d = 16, so a candidate is
+    pruned at d = 16 iff 2 P_16 > r^2).  Query at the origin, K = 1, one list
+    in id order: c0 = 10 (dim 0), c1 = 6 (dim 16), c2 = 5 (dim 0), c3 = 7
+    (dim 0), c4 = 9 (dim 0).  Tile t is tested against r^2 after tiles
+    0..t-1-L.
+    L = 0: c0 exact (r = +inf), r^2 = 100; c1 (P_16 = 0) accepted at 36;
+    c2 (2 x 25 = 50 > 36), c3 (98), c4 (162) pruned: id 1 at 36.
+    L = 1: c1 sees r after tiles <= -1 (+inf) and is accepted; c2 sees r^2 =
+    100 (after c0): 50 <= 100, exact 25 accepted, so id 2 at 25 wins; c3 sees
+    r^2 = 36 (after c1): pruned; c4 sees 25 (after c2): pruned.
+    L = 2: c1, c2 exact and accepted (+inf); c3 sees 100 (after c0): 98 <= 100,
+    exact 49 accepted; c4 sees 36 (after c1): pruned.  Result id 2 at 25.
+    Counters: (candidates, dims, accepted, pruned)."""
+    Xr, assign, cent, lam, eps, Qr = _hand_lists(
+        [[(0, 10.0)], [(16, 6.0)], [(0, 5.0)], [(0, 7.0)], [(0, 9.0)]], [0] * 5, 1)
+    want = {0: (1, 36.0, [5, 32 + 32 + 16 + 16 + 16, 2, 3]),
+            1: (2, 25.0, [5, 32 + 32 + 32 + 16 + 16, 3, 2]),
+            2: (2, 25.0, [5, 32 * 4 + 16, 4, 1])}
+    for lag, (wid, wd, wst) in want.items():
+        ids, dists, stats, _ = o.search(Xr, assign, cent, lam, Qr, 1, 1, 16, eps, schedule=1, tile=1, lag=lag)
+        assert ids[0, 0] == wid and dists[0, 0] == wd, (lag, ids, dists)
+        assert stats[0].tolist() == wst, (lag, stats)
+
+
+def _rerun_epochs(o, Xr, lam, eps, qr, K, dd, epochs):
+    """Brute-force IVF loop from single-pair DCOs: epochs is a list of
+    (candidate ids, index of the epoch whose result supplies r, or -1 for
+    +inf); the K nearest by (distance, id) after every epoch."""
+    heap, after, dims = [], [], 0
+    for cands, src in epochs:
+        r = math.sqrt(after[src]) if src >= 0 and math.isfinite(after[src]) else math.inf
+        for m in cands:
+            acc, d2, used, _ = o.dco(qr, Xr[m], dd, r, lam, eps)
+            dims += used
+            if acc:
+                heap.append((d2, int(m)))
+        heap = sorted(heap)[:K]
+        after.append(heap[-1][0] if len(heap) == K else math.inf)
+    return heap, dims
+
+
+def pin_search_lagged_bruteforce(o):
+    """Lagged tile schedule on a random index: tile t (tiles numbered over the
+    query's scan, a tile never spans lists) is tested against r after tiles
+    0..t-1-L; re-run from single-pair DCOs for L = 1, 2, 3."""
+    X, Xr, lam, cent, assign, Q, Qr = _tiny_index(o)
+    K, nprobe, dd, tile = 6, 3, 8, 16
+    eps = _eps_for(o, Xr, lam, dd, 0.2)
+    probe, _ = o.probe(Qr, cent, nprobe)
+    for lag in (1, 2, 3):
+        ids, dists, stats, _ = o.search(Xr, assign, cent, lam, Qr, K, nprobe, dd, eps, schedule=1, tile=tile,
+                                        lag=lag)
+        for i in range(0, Qr.shape[0], 3):
+            tiles = [m[t:t + tile] for c in probe[i] for m in [np.nonzero(assign == c)[0]]
+                     for t in range(0, len(m), tile)]
+            heap, dims = _rerun_epochs(o, Xr, lam, eps, Qr[i], K, dd,
+                                       [(tl, t - 1 - lag) for t, tl in enumerate(tiles)])
+            assert [h[1] for h in heap] == list(ids[i][:len(heap)]), (lag, i)
+            assert [h[0] for h in heap] == list(dists[i][:len(heap)])
+            assert dims == stats[i, 1]
+
+
+def pin_search_row_rounds_trace(o):
+    """Row rounds, worked by hand (equal eigenvalues, eps_d = 0, D = 32,
+    delta_d = 16: pruned at d = 16 iff 2 P_16 > r^2).  Query at the origin,
+    K = 1, lists A (probed first) = {a0 (id 0): 10 in dim 0, a1 (id 1): 5 in
+    dim 0}, B = {b0 (id 2): 6 in dim 16, b1 (id 3): 7 in dim 0}.
+    Rounds of rows [0, 1), [1, 2) (R_1 = 1): round 0 takes a0 and b0 with
+    r = +inf, both exact, r^2 = 36 (b0); round 1 tests a1 (2 x 25 = 50 > 36)
+    and b1 (98 > 36): both pruned at d = 16, result b0 at 36.
+    The sequential loop instead accepts a1 (50 <= 100 after a0) at 25.
+    R_1 = 2: one round holds every row, all exact: a1 at 25."""
+    Xr, assign, cent, lam, eps, Qr = _hand_lists(
+        [[(0, 10.0)], [(0, 5.0)], [(16, 6.0)], [(0, 7.0)]], [0, 0, 1, 1], 2)
+    r1 = o.search(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=3, tile=1)
+    assert r1[0][0, 0] == 2 and r1[1][0, 0] == 36.0
+    assert r1[2][0].tolist() == [4, 32 + 32 + 16 + 16, 2, 2]
+    seq = o.search(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=0)
+    assert seq[0][0, 0] == 1 and seq[1][0, 0] == 25.0
+    assert seq[2][0].tolist() == [4, 32 * 3 + 16, 2, 1]
+    r2 = o.search(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=3, tile=2)
+    assert r2[0][0, 0] == 1 and r2[1][0, 0] == 25.0
+    assert r2[2][0].tolist() == [4, 32 * 4, 4, 0]
+
+
+def pin_search_row_rounds_bruteforce(o):
+    """Row rounds on a random index with uneven lists: round e holds rows
+    [R_e, R_{e+1}) of every probed list (probe order, then row), R_0 = 0,
+    R_1 = tile, R_{e+1} = 2 R_e, tested against r after the earlier rounds;
+    re-run from single-pair DCOs.  FDScanning does not depend on the rounds,
+    and R_1 above every list length is one exact round."""
+    X, Xr, lam, cent, assign, Q, Qr = _tiny_index(o)
+    K, nprobe, dd = 6, 4, 8
+    eps = _eps_for(o, Xr, lam, dd, 0.2)
+    probe, _ = o.probe(Qr, cent, nprobe)
+    for tile in (1, 3, 16):
+        ids, dists, stats, _ = o.search(Xr, assign, cent, lam, Qr, K, nprobe, dd, eps, schedule=3, tile=tile)
+        for i in range(0, Qr.shape[0], 2):
+            lists = [np.nonzero(assign == c)[0] for c in probe[i]]
+            bounds, lo, hi = [], 0, tile
+            while lo < max(len(m) for m in lists):
+                bounds.append((lo, hi))
+                lo, hi = hi, 2 * hi
+            epochs = [([x for m in lists for x in m[a:b]], e - 1) for e, (a, b) in enumerate(bounds)]
+            heap, dims = _rerun_epochs(o, Xr, lam, eps, Qr[i], K, dd, epochs)
+            assert [h[1] for h in heap] == list(ids[i][:len(heap)]), (tile, i)
+            assert [h[0] for h in heap] == list(dists[i][:len(heap)])
+            assert dims == stats[i, 1] and stats[i, 0] == sum(len(m) for m in lists)
+    fd = o.search(Xr, assign, cent, lam, Qr, K, nprobe, dd, None, schedule=1, tile=16)
+    fdr = o.search(Xr, assign, cent, lam, Qr, K, nprobe, dd, None, schedule=3, tile=2)
+    assert np.array_equal(fd[0], fdr[0]) and np.array_equal(fd[1], fdr[1])
+    one = o.search(Xr, assign, cent, lam, Qr, K, nprobe, dd, eps, schedule=3, tile=X.shape[0])
+    assert np.array_equal(one[0], fd[0]) and np.all(one[2][:, 3] == 0)
+
+
+def pin_search_bracket(o):
+    """The decision bracket (bias moves r^2 to r^2 (1 + bias) in every test
+    and final compare), worked by hand: equal eigenvalues, eps_d = 0, D = 32,
+    delta_d = 16, K = 1, query at the origin, list A = {a (id 0): 10 in dim 0}
+    probed before B = {b (id 1): sqrt(50.0005) in dim 0}.  After a, r^2 = 100;
+    b's estimate 2 x 50.0005 = 100.001 exceeds 100 by 1e-5 relative: pruned
+    by the method (result a) and under bias -2e-5, kept under +2e-5 and then
+    accepted at its exact 50.0005 (result b).  A final compare within the
+    bracket: b' (id 1) = 10.000025 in dim 16 (P_16 = 0, exact 100.0005) is
+    rejected by the method, accepted under +2e-5 but pushed out of the K
+    nearest by a, which only the flag of a near-tie at the K-th place shows."""
+    Xr, assign, cent, lam, eps, Qr = _hand_lists([[(0, 10.0)], [(0, math.sqrt(50.0005))]], [0, 1], 2)
+    runs = {b: o.search(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=1, tile=1, bias=b, tol=2e-5)
+            for b in (0.0, -2e-5, 2e-5)}
+    assert runs[0.0][0][0, 0] == 0 and runs[-2e-5][0][0, 0] == 0 and runs[2e-5][0][0, 0] == 1
+    assert abs(runs[2e-5][1][0, 0] - 50.0005) < 1e-12
+    *_, stable, _ = o.search_bracket(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=1, tile=1, btol=2e-5)
+    assert not stable[0]
+    Xr, assign, cent, lam, eps, Qr = _hand_lists([[(0, 10.0)], [(16, 10.000025)]], [0, 1], 2)
+    base = o.search(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=1, tile=1, tol=2e-5)
+    keep = o.search(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=1, tile=1, bias=2e-5, tol=2e-5)
+    assert base[0][0, 0] == 0 and base[2][0].tolist() == [2, 64, 1, 0] and base[3][0] & 4 == 0
+    assert keep[0][0, 0] == 0 and keep[2][0].tolist() == [2, 64, 2, 0] and keep[3][0] & 4
+    *_, stable, sstable = o.search_bracket(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=1, tile=1,
+                                           btol=2e-5)
+    assert not stable[0] and not sstable[0]
+    # far from every threshold the three runs agree: stable
+    Xr, assign, cent, lam, eps, Qr = _hand_lists([[(0, 10.0)], [(0, 2.0)]], [0, 1], 2)
+    *_, stable, sstable = o.search_bracket(Xr, assign, cent, lam, Qr, 1, 2, 16, eps, schedule=1, tile=1)
+    assert stable[0] and sstable[0]
+
+
 def pin_adsampling_as_uniform_spectrum(o):
     """ADSampling (the paper's baseline, Section 5) estimates sqrt(D/d) times
     the partial distance and prunes iff that exceeds (1 + eps0/sqrt(d)) r.

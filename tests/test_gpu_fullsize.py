@@ -6,7 +6,9 @@ lists of their own) and the same eps pairs.  The CUDA path then runs the
 whole query batch in the launch configuration the benchmark times (rotate,
 probe, scan; the benchmark's schedule, tile, threads, delta_d, alpha and
 flags), and a seeded sample of its queries is compared with the oracle's
-sampled index element by element, under the tolerance of ``parity.py``.
+sampled index element by element, under the tolerance of ``parity.py``: the
+oracle brackets every threshold decision, ids must match on every stable
+query, and at most a tenth of the sample may be unstable.
 Every query of the batch is also checked against properties that hold at
 any size: distinct ids in range, ascending distances, and each distance
 equal to the FP64 squared distance of the raw vectors (the rotation is an
@@ -23,7 +25,7 @@ from paper_2411_17229_gb300 import dade, synth
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-N_SAMPLE = 12
+N_SAMPLE = 24
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -42,7 +44,7 @@ def _build(w, n_pairs, **kw):
     return base, queries, assign, pairs, ix
 
 
-def _check_properties(base, queries, ids, dists, scale):
+def _check_properties(base, queries, ids, dists):
     """Any size: ids distinct and in range, ascending, distances exact."""
     nq, K = ids.shape
     valid = ids >= 0
@@ -56,7 +58,7 @@ def _check_properties(base, queries, ids, dists, scale):
         diff = base[ids[q0:q1]].astype(np.float64) - queries[q0:q1, None, :].astype(np.float64)
         ex = (diff ** 2).sum(-1)
         err = np.abs(dists[q0:q1].astype(np.float64) - ex)
-        assert (err <= parity.RTOL * ex + parity.ATOL_REL * scale).all(), f"distance error {err.max()}"
+        assert (err <= parity.RTOL * ex).all(), f"distance error {(err / np.maximum(ex, 1e-300)).max():.2e} relative"
 
 
 def _scan_batch(ix, queries, K, pt):
@@ -82,34 +84,36 @@ def _run_batch_case(wname, pt, n_pairs, **build_kw):
     probe, ids, dists = _scan_batch(ix, queries, K, pt)
     sample = np.sort(np.random.default_rng(17).choice(queries.shape[0], N_SAMPLE, replace=False))
     orc = oracle.SampledIndex(base, assign, w.n_clusters, pairs, queries[sample], pt["nprobe"])
-    scale = float(orc.lam.sum())   # mean squared norm of the rotated base (trace of the covariance)
     # the probe (Section 3.4): the oracle's nearest lists, by (distance, list id)
     same = [np.array_equal(probe[s], orc.probe[i]) for i, s in enumerate(sample) if not orc.probe_tie[i]]
     assert all(same) and len(same) >= N_SAMPLE // 2
-    seed = pt["seed_lists"] if pt["schedule"] == dade.SCHED_SEEDED else 0
-    o_ids, o_d, _, oflags = orc.search(K, pt["nprobe"], pt["delta_d"], pt["alpha"], tile=pt["tile"], seed=seed)
+    o = _oracle_point(orc, K, pt)
 
     def exact_d(i, sel):
         return ((base[sel].astype(np.float64) - queries[sample[i]].astype(np.float64)) ** 2).sum(-1)
 
-    # At full size a query makes 10^4..10^5 threshold decisions (and C2's integer
-    # data has exactly equal distances), so most sampled queries carry a near-tie
-    # flag.  Each flagged query is validated (distinct ids, exact distances,
-    # ascending, >= 90% of the oracle's ids), and at most a quarter of the sample
-    # may differ from the oracle's ids at all.
-    summary = parity.compare(ids[sample], dists[sample], o_ids, o_d, oflags, scale, exact_d, max_flagged_frac=1.0)
-    assert summary["flagged_mismatched"] <= N_SAMPLE // 4, summary
-    _check_properties(base, queries, ids, dists, scale)
+    summary = parity.compare(ids[sample], dists[sample], o, exact_d)
+    print(f"{wname}: {summary}")
+    _check_properties(base, queries, ids, dists)
     ix.close()
+
+
+def _oracle_point(orc, K, pt):
+    """The oracle's bracketed search in the schedule of a benchmark point."""
+    if pt["schedule"] == dade.SCHED_ROUNDS:
+        return orc.search_bracket(K, pt["nprobe"], pt["delta_d"], pt["alpha"], schedule=oracle.ROW_ROUNDS,
+                                  tile=pt["tile"])
+    seed = pt["seed_lists"] if pt["schedule"] == dade.SCHED_SEEDED else 0
+    return orc.search_bracket(K, pt["nprobe"], pt["delta_d"], pt["alpha"], tile=pt["tile"], seed=seed)
 
 
 def test_c2_full_size_benchmark_point():
     """1M x 128 integer mixture, 10,000 queries, K = 100, at the benchmark's
-    point: nprobe 20, seeded schedule (2 lists), tile 256, delta_d 64,
-    alpha 0.3, query order and row tail; index with the BF16 lead copy and
+    point: nprobe 20, seeded schedule (3 lists), tile 256, delta_d 64,
+    alpha 0.8, query order and row tail; index with the BF16 lead copy and
     the row-major tail from dim 32, as the benchmark builds it."""
-    pt = {"nprobe": 20, "alpha": 0.3, "delta_d": 64, "tile": 256, "threads": 128, "schedule": dade.SCHED_SEEDED,
-          "seed_lists": 2, "flags": dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL}
+    pt = {"nprobe": 20, "alpha": 0.8, "delta_d": 64, "tile": 256, "threads": 128, "schedule": dade.SCHED_SEEDED,
+          "seed_lists": 3, "flags": dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL}
     _run_batch_case("c2_mix_1m_d128", pt, 100000, lead_format=dade.LEAD_BF16, lead_dims=64, tail_from=32)
 
 
@@ -144,11 +148,10 @@ def test_c5_full_size_serving():
     assert st["requests_done"] == n_req and st["batches"] < n_req
     sample = np.sort(rng.choice(n_req, N_SAMPLE, replace=False))
     orc = oracle.SampledIndex(base, assign, w.n_clusters, pairs, queries[picks[sample]], 128)
-    scale = float(orc.lam.sum())
-    mismatched = 0
+    unstable = 0
     for K, nprobe in sorted({(int(ks[i]), int(nps[i])) for i in sample}):
         rows = [j for j, i in enumerate(sample) if ks[i] == K and nps[i] == nprobe]
-        o_ids, o_d, _, oflags = orc.search(K, nprobe, delta_d, alpha, tile=128)
+        o = orc.search_bracket(K, nprobe, delta_d, alpha, tile=128)
         g_ids = np.stack([res[sample[j]][0][0] for j in rows])
         g_d = np.stack([res[sample[j]][1][0] for j in rows])
 
@@ -156,12 +159,11 @@ def test_c5_full_size_serving():
             q = queries[picks[sample[rows[i]]]].astype(np.float64)
             return ((base[sel].astype(np.float64) - q) ** 2).sum(-1)
 
-        summary = parity.compare(g_ids, g_d, o_ids[rows], o_d[rows], oflags[rows], scale, exact_d,
-                                 max_flagged_frac=1.0)
-        mismatched += summary["flagged_mismatched"]
-    assert mismatched <= N_SAMPLE // 4
+        summary = parity.compare(g_ids, g_d, tuple(x[rows] for x in o), exact_d, max_unstable_frac=1.0)
+        unstable += summary["unstable"]
+    assert unstable <= max(1, N_SAMPLE // 10), unstable
     for i in range(n_req):
-        _check_properties(base, queries[picks[i]:picks[i] + 1], res[i][0], res[i][1], scale)
+        _check_properties(base, queries[picks[i]:picks[i] + 1], res[i][0], res[i][1])
     ix.close()
 
 
@@ -182,17 +184,16 @@ def test_c4_full_size_benchmark_point():
     probe, ids, dists = _scan_batch(ix, queries, w.k, pt)
     _, ids8, dists8 = _scan_batch(ix, queries, w.k, dict(pt, flags=pt["flags"] | dade.FLAG_LEAD))
     assert np.array_equal(ids, ids8) and np.array_equal(dists.view(np.uint32), dists8.view(np.uint32))
-    sample = np.sort(np.random.default_rng(17).choice(queries.shape[0], N_SAMPLE // 2, replace=False))
+    sample = np.sort(np.random.default_rng(17).choice(queries.shape[0], N_SAMPLE, replace=False))
     orc = oracle.SampledIndex(base, labels, w.n_clusters, pairs, queries[sample], pt["nprobe"])
-    scale = float(orc.lam.sum())
     same = [np.array_equal(probe[s], orc.probe[i]) for i, s in enumerate(sample) if not orc.probe_tie[i]]
     assert all(same)
-    o_ids, o_d, _, oflags = orc.search(w.k, pt["nprobe"], pt["delta_d"], pt["alpha"], tile=pt["tile"])
+    o = _oracle_point(orc, w.k, pt)
 
     def exact_d(i, sel):
         return ((base[sel].astype(np.float64) - queries[sample[i]].astype(np.float64)) ** 2).sum(-1)
 
-    summary = parity.compare(ids[sample], dists[sample], o_ids, o_d, oflags, scale, exact_d, max_flagged_frac=1.0)
-    assert summary["flagged_mismatched"] <= max(1, len(sample) // 4), summary
-    _check_properties(base, queries, ids, dists, scale)
+    summary = parity.compare(ids[sample], dists[sample], o, exact_d)
+    print(f"c4: {summary}")
+    _check_properties(base, queries, ids, dists)
     ix.close()

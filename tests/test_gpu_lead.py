@@ -90,8 +90,8 @@ class LeadCase:
 
     def oracle_search(self, k, nprobe, alpha, delta_d, tile=128):
         eps = self.orc.eps(np.float32(alpha), delta_d)
-        return self.orc.o.search(self.orc.Xr, self.assign, self.orc.cent, self.orc.lam, self.Qr, k, nprobe,
-                                 delta_d, eps, schedule=oracle.TILE, tile=tile, lag=0)
+        return self.orc.o.search_bracket(self.orc.Xr, self.assign, self.orc.cent, self.orc.lam, self.Qr, k, nprobe,
+                                         delta_d, eps, schedule=oracle.TILE, tile=tile, lag=0)
 
     def exact_d(self, q, ids):
         return ((self.orc.Xr[ids] - self.Qr[q]) ** 2).sum(1)
@@ -187,9 +187,9 @@ def test_lead_search_equals_fp32_and_oracle(name, k, nprobe, alpha, delta_d, til
         assert np.all(l_lead <= l_st[:, 3])
     assert l_lead.sum() > 0.05 * l_st[:, 0].sum()
     # and parity with the FP64 oracle
-    o_ids, o_d, o_st, flags = c.oracle_search(k, nprobe, alpha, delta_d, tile=tile)
-    parity.compare(l_ids, l_d, o_ids, o_d, flags, c.scale, c.exact_d)
-    assert np.array_equal(l_st[:, 0], o_st[:, 0])
+    o = c.oracle_search(k, nprobe, alpha, delta_d, tile=tile)
+    parity.compare(l_ids, l_d, o, c.exact_d)
+    parity.compare_stats(l_st, o)
 
 
 def test_lead_whole_vector_single_increment():
@@ -211,8 +211,8 @@ def test_lead_whole_vector_single_increment():
         assert np.array_equal(l[0], f[0]) and np.array_equal(l[1].view(np.uint32), f[1].view(np.uint32))
         assert np.array_equal(l[2], f[2])
         assert l[3].sum() > 0
-        o_ids, o_d, _, flags = case.oracle_search(k, nprobe, 0.1, 1024)
-        parity.compare(l[0], l[1], o_ids, o_d, flags, case.scale, case.exact_d)
+        o = case.oracle_search(k, nprobe, 0.1, 1024)
+        parity.compare(l[0], l[1], o, case.exact_d)
 
 
 def test_lead_invalid_requests():

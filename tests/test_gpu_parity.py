@@ -57,11 +57,16 @@ class Case:
         return out + ((st.cpu().numpy(),) if stats else ())
 
     def oracle_search(self, k, nprobe, alpha, delta_d, fd=False, tile=128, schedule=dade.SCHED_TILE, seed=0):
+        """The oracle's bracketed search (parity.compare's input) in the GPU schedule's epochs."""
         eps = None if fd else self.orc.eps(np.float32(alpha), delta_d)
+        if schedule == dade.SCHED_ROUNDS:
+            return self.orc.o.search_bracket(self.orc.Xr, self.assign, self.orc.cent, self.orc.lam, self.Qr, k,
+                                             nprobe, delta_d if not fd else 64, eps, schedule=oracle.ROW_ROUNDS,
+                                             tile=tile)
         lag = 0 if fd else dade.schedule_lag(self.base.shape[1], delta_d, schedule)
-        return self.orc.o.search(self.orc.Xr, self.assign, self.orc.cent, self.orc.lam, self.Qr, k, nprobe,
-                                 delta_d if not fd else 64, eps, schedule=oracle.TILE, tile=tile, lag=lag,
-                                 seed=seed)
+        return self.orc.o.search_bracket(self.orc.Xr, self.assign, self.orc.cent, self.orc.lam, self.Qr, k, nprobe,
+                                         delta_d if not fd else 64, eps, schedule=oracle.TILE, tile=tile, lag=lag,
+                                         seed=seed)
 
     def exact_d(self, q, ids):
         return ((self.orc.Xr[ids] - self.Qr[q]) ** 2).sum(1)
@@ -102,10 +107,13 @@ def _signs(c):
 def test_rotation_parity(c1):
     sg = _signs(c1)
     Xg = c1.gpu.export(dade.FIELD_ROTATED).astype(np.float64) * sg
-    scale = np.sqrt(c1.scale)
-    assert np.abs(Xg - c1.orc.Xr).max() < 2e-6 * scale
+    # every rotated vector within ROT_TOL of the exact one, relative to its own norm
+    # (the FP32 error the parity tolerances and the oracle's decision bracket assume)
+    err = np.linalg.norm(Xg - c1.orc.Xr, axis=1) / np.linalg.norm(c1.orc.Xr, axis=1)
+    assert err.max() < parity.ROT_TOL, err.max()
     Qg = c1.q_rot.cpu().numpy().astype(np.float64) * sg
-    assert np.abs(Qg - c1.Qr).max() < 2e-6 * scale
+    err = np.linalg.norm(Qg - c1.Qr, axis=1) / np.linalg.norm(c1.Qr, axis=1)
+    assert err.max() < parity.ROT_TOL, err.max()
     # host buffers in, host buffers out give the same bits
     qh = np.empty_like(c1.queries)
     c1.gpu.rotate(c1.queries, qh)
@@ -115,7 +123,8 @@ def test_rotation_parity(c1):
 def test_assignment_and_centroids(c1):
     assert np.array_equal(c1.gpu.export(dade.FIELD_ASSIGN), c1.assign)
     cg = c1.gpu.export(dade.FIELD_CENTROIDS).astype(np.float64) * _signs(c1)
-    assert np.abs(cg - c1.orc.cent).max() < 2e-6 * np.sqrt(c1.scale)
+    err = np.linalg.norm(cg - c1.orc.cent, axis=1) / np.linalg.norm(c1.orc.cent, axis=1)
+    assert err.max() < parity.ROT_TOL, err.max()
 
 
 def test_eps_parity(c1):
@@ -163,12 +172,10 @@ def test_probe_parity(c1, mix, nprobe):
 def test_search_parity_c1(c1, k, nprobe, alpha, delta_d, tile, schedule, threads, flags):
     g_ids, g_d, g_st = c1.gpu_search(k, nprobe, alpha, delta_d, tile=tile, stats=True, schedule=schedule,
                                      threads=threads, flags=flags)
-    o_ids, o_d, o_st, flags = c1.oracle_search(k, nprobe, alpha, delta_d, tile=tile, schedule=schedule)
-    parity.compare(g_ids, g_d, o_ids, o_d, flags, c1.scale, c1.exact_d)
-    # the work done is the same: candidates exactly, the rest where no near-tie occurred
-    assert np.array_equal(g_st[:, 0], o_st[:, 0])
-    clean = flags == 0
-    assert np.array_equal(g_st[clean, 1:], o_st[clean, 1:])
+    o = c1.oracle_search(k, nprobe, alpha, delta_d, tile=tile, schedule=schedule)
+    parity.compare(g_ids, g_d, o, c1.exact_d)
+    # the work done is the same: candidates exactly, the rest where the bracket counts the same
+    parity.compare_stats(g_st, o)
     if schedule == dade.SCHED_TILE:   # a deep pipeline on a short scan may never refresh its threshold
         assert np.all(g_st[:, 1] < g_st[:, 0] * 128)   # DADE used fewer dimensions than FDScanning
 
@@ -177,8 +184,8 @@ def test_search_parity_c1(c1, k, nprobe, alpha, delta_d, tile, schedule, threads
 @pytest.mark.parametrize("schedule", [dade.SCHED_TILE, dade.SCHED_PIPELINED])
 def test_search_parity_mixture(mix, k, nprobe, alpha, delta_d, schedule):
     g_ids, g_d = mix.gpu_search(k, nprobe, alpha, delta_d, schedule=schedule)
-    o_ids, o_d, _, flags = mix.oracle_search(k, nprobe, alpha, delta_d, schedule=schedule)
-    parity.compare(g_ids, g_d, o_ids, o_d, flags, mix.scale, mix.exact_d)
+    o = mix.oracle_search(k, nprobe, alpha, delta_d, schedule=schedule)
+    parity.compare(g_ids, g_d, o, mix.exact_d)
 
 
 @pytest.mark.parametrize("k,nprobe", [(10, 8), (100, 16)])
@@ -186,9 +193,9 @@ def test_search_parity_mixture(mix, k, nprobe, alpha, delta_d, schedule):
 def test_fd_parity(c1, k, nprobe, threads, flags):
     g_ids, g_d, g_st = c1.gpu_search(k, nprobe, 0.1, 32, mode=dade.MODE_FD, stats=True, threads=threads,
                                      flags=flags)
-    o_ids, o_d, o_st, flags = c1.oracle_search(k, nprobe, 0.1, 32, fd=True)
-    parity.compare(g_ids, g_d, o_ids, o_d, flags, c1.scale, c1.exact_d)
-    assert np.array_equal(g_st[:, 0], o_st[:, 0])
+    o = c1.oracle_search(k, nprobe, 0.1, 32, fd=True)
+    parity.compare(g_ids, g_d, o, c1.exact_d)
+    parity.compare_stats(g_st, o)
     assert np.all(g_st[:, 1] == g_st[:, 0] * 128)
 
 
@@ -235,8 +242,8 @@ def test_odd_shapes(d, nlists, delta_d):
     for k, nprobe in ((5, 1), (200, 2), (10, nlists)):
         for schedule in (dade.SCHED_TILE, dade.SCHED_PIPELINED):
             g_ids, g_d = case.gpu_search(k, nprobe, 0.1, delta_d, tile=32, schedule=schedule)
-            o_ids, o_d, _, flags = case.oracle_search(k, nprobe, 0.1, delta_d, tile=32, schedule=schedule)
-            parity.compare(g_ids, g_d, o_ids, o_d, flags, case.scale, case.exact_d)
+            o = case.oracle_search(k, nprobe, 0.1, delta_d, tile=32, schedule=schedule)
+            parity.compare(g_ids, g_d, o, case.exact_d)
 
 
 def test_empty_batch_and_invalid(c1):
@@ -320,11 +327,9 @@ def test_row_tail_gives_same_results(tail_from, delta_d, flags):
 def test_seeded_schedule_parity(c1, k, nprobe, alpha, delta_d, tile, seed, flags):
     g_ids, g_d, g_st = c1.gpu_search(k, nprobe, alpha, delta_d, tile=tile, stats=True, schedule=dade.SCHED_SEEDED,
                                      seed_lists=seed, flags=flags)
-    o_ids, o_d, o_st, oflags = c1.oracle_search(k, nprobe, alpha, delta_d, tile=tile, seed=seed)
-    parity.compare(g_ids, g_d, o_ids, o_d, oflags, c1.scale, c1.exact_d)
-    assert np.array_equal(g_st[:, 0], o_st[:, 0])
-    clean = oflags == 0
-    assert np.array_equal(g_st[clean, 1:], o_st[clean, 1:])
+    o = c1.oracle_search(k, nprobe, alpha, delta_d, tile=tile, seed=seed)
+    parity.compare(g_ids, g_d, o, c1.exact_d)
+    parity.compare_stats(g_st, o)
 
 
 @pytest.mark.parametrize("k,nprobe", [(10, 8), (100, 16)])
@@ -352,8 +357,8 @@ def test_seeded_schedule_mixture_and_limits():
     for k, nprobe, seed, dd, tile in ((10, 6, 1, 32, 128), (50, 8, 2, 16, 128), (30, 12, 3, 64, 128),
                                       (30, 12, 3, 64, 1 << 20)):
         g_ids, g_d = case.gpu_search(k, nprobe, 0.1, dd, schedule=dade.SCHED_SEEDED, seed_lists=seed, tile=tile)
-        o_ids, o_d, _, oflags = case.oracle_search(k, nprobe, 0.1, dd, seed=seed, tile=tile)
-        parity.compare(g_ids, g_d, o_ids, o_d, oflags, case.scale, case.exact_d)
+        o = case.oracle_search(k, nprobe, 0.1, dd, seed=seed, tile=tile)
+        parity.compare(g_ids, g_d, o, case.exact_d)
     # seed >= nprobe is the tile schedule
     a = case.gpu_search(10, 4, 0.1, 32, stats=True)
     b = case.gpu_search(10, 4, 0.1, 32, stats=True, schedule=dade.SCHED_SEEDED, seed_lists=4)
@@ -366,8 +371,8 @@ def test_seeded_schedule_mixture_and_limits():
                      n_pairs=1000)
         for tile, seed in ((64, 1), (1 << 20, 2)):
             g_ids, g_d = small.gpu_search(5, 4, 0.1, 32, schedule=dade.SCHED_SEEDED, seed_lists=seed, tile=tile)
-            o_ids, o_d, _, oflags = small.oracle_search(5, 4, 0.1, 32, seed=seed, tile=tile)
-            parity.compare(g_ids, g_d, o_ids, o_d, oflags, small.scale, small.exact_d)
+            o = small.oracle_search(5, 4, 0.1, 32, seed=seed, tile=tile)
+            parity.compare(g_ids, g_d, o, small.exact_d)
 
 
 @pytest.mark.parametrize("d,delta_d,seed,tile", [(160, 16, 2, 128), (160, 32, 1, 4096), (256, 64, 2, 128),
@@ -381,10 +386,9 @@ def test_seeded_schedule_any_dimension(d, delta_d, seed, tile):
     for (k, nprobe), fl in itertools.product(((10, 8), (60, 12)), (0, dade.FLAG_SEED_SPLIT)):
         g_ids, g_d, g_st = case.gpu_search(k, nprobe, 0.1, delta_d, tile=tile, stats=True,
                                            schedule=dade.SCHED_SEEDED, seed_lists=seed, flags=fl)
-        o_ids, o_d, o_st, oflags = case.oracle_search(k, nprobe, 0.1, delta_d, tile=tile, seed=seed)
-        parity.compare(g_ids, g_d, o_ids, o_d, oflags, case.scale, case.exact_d)
-        assert np.array_equal(g_st[:, 0], o_st[:, 0])
-        assert np.array_equal(g_st[oflags == 0, 1:], o_st[oflags == 0, 1:])
+        o = case.oracle_search(k, nprobe, 0.1, delta_d, tile=tile, seed=seed)
+        parity.compare(g_ids, g_d, o, case.exact_d)
+        parity.compare_stats(g_st, o)
     a = case.gpu_search(10, 8, 0.1, 32, mode=dade.MODE_FD)
     b = case.gpu_search(10, 8, 0.1, 32, mode=dade.MODE_FD, schedule=dade.SCHED_SEEDED, seed_lists=2)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
@@ -411,8 +415,8 @@ def test_staged_depth_gives_same_results(d, delta_d, stage):
         out.append((ids.cpu().numpy(), dd.cpu().numpy(), st.cpu().numpy()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
     assert np.array_equal(out[0][2], out[1][2])
-    o_ids, o_d, _, oflags = case.oracle_search(20, 6, 0.1, delta_d, tile=64)
-    parity.compare(out[1][0], out[1][1], o_ids, o_d, oflags, case.scale, case.exact_d)
+    o = case.oracle_search(20, 6, 0.1, delta_d, tile=64)
+    parity.compare(out[1][0], out[1][1], o, case.exact_d)
 
 
 @pytest.mark.parametrize("d,delta_d,tail_from,spec", [(160, 32, 32, 8), (256, 16, 64, 3), (200, 64, 16, 8),
@@ -441,8 +445,8 @@ def test_generic_kernel_row_tail_and_window(d, delta_d, tail_from, spec):
     for o in out[1:]:
         assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1].view(np.uint32), o[1].view(np.uint32))
         assert np.array_equal(out[0][2], o[2])
-    o_ids, o_d, _, oflags = case.oracle_search(20, 6, 0.1, delta_d, tile=64)
-    parity.compare(out[0][0], out[0][1], o_ids, o_d, oflags, case.scale, case.exact_d)
+    o = case.oracle_search(20, 6, 0.1, delta_d, tile=64)
+    parity.compare(out[0][0], out[0][1], o, case.exact_d)
 
 
 @pytest.mark.parametrize("delta_d,seed,flags", [(32, 2, 0), (16, 1, dade.FLAG_QUERY_ORDER), (64, 3, 0)])
@@ -503,8 +507,8 @@ def test_list_chunks_same_results(d, delta_d, tile, seed):
     for o in out[1:]:
         assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1].view(np.uint32), o[1].view(np.uint32))
         assert np.array_equal(out[0][2], o[2])
-    o_ids, o_d, _, oflags = case.oracle_search(20, 5, 0.1, delta_d, tile=tile, seed=seed)
-    parity.compare(out[1][0], out[1][1], o_ids, o_d, oflags, case.scale, case.exact_d, max_flagged_frac=0.5)
+    o = case.oracle_search(20, 5, 0.1, delta_d, tile=tile, seed=seed)
+    parity.compare(out[1][0], out[1][1], o, case.exact_d)
 
 
 def test_accept_buffer_overflow_is_reported():
@@ -546,11 +550,9 @@ def test_kbest_staging_bounds_a_loose_threshold():
     for tile, seed in ((1 << 20, 1), (128, 1)):
         g_ids, g_d, g_st = case.gpu_search(10, 2, 0.1, 32, tile=tile, stats=True, schedule=dade.SCHED_SEEDED,
                                            seed_lists=seed)
-        o_ids, o_d, o_st, oflags = case.oracle_search(10, 2, 0.1, 32, tile=tile, seed=seed)
-        # 70,000 candidates per query: most queries carry a near-tie flag (validated)
-        summary = parity.compare(g_ids, g_d, o_ids, o_d, oflags, case.scale, case.exact_d, max_flagged_frac=1.0)
-        assert summary["flagged_mismatched"] <= 1, summary
-        assert np.array_equal(g_st[:, 0], o_st[:, 0])
+        o = case.oracle_search(10, 2, 0.1, 32, tile=tile, seed=seed)
+        parity.compare(g_ids, g_d, o, case.exact_d)
+        parity.compare_stats(g_st, o)
 
 
 @pytest.mark.parametrize("d,ring,flags", [(160, 4, 0), (128, 3, dade.FLAG_GENERIC_KERNEL), (256, 8, 0),
@@ -583,13 +585,12 @@ def test_flat_index_is_a_linear_scan():
     case = Case(base, queries, np.zeros(6000, np.int32), 1, n_pairs=4000)
     for dd, alpha in ((16, 0.05), (32, 0.1), (64, 0.3)):
         g_ids, g_d, g_st = case.gpu_search(10, 1, alpha, dd, tile=256, stats=True)
-        o_ids, o_d, o_st, oflags = case.oracle_search(10, 1, alpha, dd, tile=256)
-        summary = parity.compare(g_ids, g_d, o_ids, o_d, oflags, case.scale, case.exact_d, max_flagged_frac=1.0)
-        assert summary["flagged_mismatched"] <= 3, summary
-        assert np.array_equal(g_st[:, 0], o_st[:, 0])
+        o = case.oracle_search(10, 1, alpha, dd, tile=256)
+        parity.compare(g_ids, g_d, o, case.exact_d)
+        parity.compare_stats(g_st, o)
     f_ids, f_d = case.gpu_search(10, 1, 0.1, 32, mode=dade.MODE_FD)
-    o_ids, o_d, _, oflags = case.oracle_search(10, 1, 0.1, 32, fd=True)
-    parity.compare(f_ids, f_d, o_ids, o_d, oflags, case.scale, case.exact_d)
+    o = case.oracle_search(10, 1, 0.1, 32, fd=True)
+    parity.compare(f_ids, f_d, o, case.exact_d)
 
 
 @pytest.mark.parametrize("d,schedule,seed", [(128, dade.SCHED_TILE, 0), (128, dade.SCHED_SEEDED, 2),
@@ -629,3 +630,92 @@ def test_tune_keeps_results_and_caches(d, schedule, seed):
             ix.sync()
             assert np.array_equal(out[0][0], ids.cpu().numpy())
             assert np.array_equal(out[0][1].view(np.uint32), dd.cpu().numpy().view(np.uint32))
+
+
+# ---- the row-rounds schedule -------------------------------------------------------
+
+@pytest.mark.parametrize("k,nprobe,alpha,delta_d,r1", [
+    (10, 8, 0.05, 32, 64), (10, 8, 0.1, 16, 1), (100, 16, 0.3, 64, 32), (1, 4, 0.2, 32, 7),
+    (256, 8, 0.1, 64, 64),          # round 0 finds fewer than K: the next round runs with r = +inf
+    (20, 12, 0.1, 128, 100),        # one increment
+    (10, 8, 0.1, 32, 4096),         # one round holds every row: exact
+])
+@pytest.mark.parametrize("flags", [0, dade.FLAG_QUERY_ORDER, dade.FLAG_SEED_SPLIT])
+def test_rounds_schedule_parity(c1, k, nprobe, alpha, delta_d, r1, flags):
+    g_ids, g_d, g_st = c1.gpu_search(k, nprobe, alpha, delta_d, tile=r1, stats=True, schedule=dade.SCHED_ROUNDS,
+                                     flags=flags)
+    o = c1.oracle_search(k, nprobe, alpha, delta_d, tile=r1, schedule=dade.SCHED_ROUNDS)
+    parity.compare(g_ids, g_d, o, c1.exact_d)
+    parity.compare_stats(g_st, o)
+
+
+@pytest.mark.parametrize("d,delta_d,r1", [(160, 16, 64), (256, 64, 16), (384, 128, 64), (136, 32, 1), (64, 32, 16),
+                                          (40, 16, 8)])
+def test_rounds_schedule_any_dimension(d, delta_d, r1):
+    """List-major rounds for D > 112 (blocks walked in windows), query-major
+    split rounds below: parity with the oracle's row rounds, the split form
+    equal to the list-major one bit for bit, FDScanning unchanged."""
+    w = synth.Workload(f"mix{d}", 8000, d, 70, 1.0, 20, 0.0, 3.0, 1.0, False, False, 20, (4,), 10, (16,), 0.1)
+    base, queries, labels = synth.make(w)
+    case = Case(base, queries, labels, 20, n_pairs=4000)
+    for k, nprobe in ((10, 8), (60, 12)):
+        outs = []
+        for fl in (0, dade.FLAG_SEED_SPLIT):
+            outs.append(case.gpu_search(k, nprobe, 0.1, delta_d, tile=r1, stats=True, schedule=dade.SCHED_ROUNDS,
+                                        flags=fl))
+        o = case.oracle_search(k, nprobe, 0.1, delta_d, tile=r1, schedule=dade.SCHED_ROUNDS)
+        parity.compare(outs[0][0], outs[0][1], o, case.exact_d)
+        parity.compare_stats(outs[0][2], o)
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][2], outs[1][2])
+        assert np.array_equal(outs[0][1].view(np.uint32), outs[1][1].view(np.uint32))
+    a = case.gpu_search(10, 8, 0.1, 32, mode=dade.MODE_FD)
+    b = case.gpu_search(10, 8, 0.1, 32, mode=dade.MODE_FD, schedule=dade.SCHED_ROUNDS, tile=16)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+
+
+def test_rounds_schedule_dominant_list():
+    """Zipf(1.1) list sizes over 64 lists of a 60,000 x 192 mixture (the
+    largest list holds about a fifth of the data): rounds of doubling row
+    windows cut it into chunks over many thread blocks; any chunk size gives
+    the same bits and counters, and the oracle's results."""
+    w = synth.Workload("zipf192", 60000, 192, 80, 1.5, 64, 0.0, 2.0, 1.0, False, True, 64, (4,), 10, (32,), 0.1,
+                       comp_zipf=1.1, lists_are_components=True)
+    base, queries, labels = synth.make(w)
+    case = Case(base, queries, labels, 64, n_pairs=4000)
+    assert np.bincount(labels).max() > 0.15 * base.shape[0]
+    out = []
+    for chunk in (0, 64, 256):
+        nq = queries.shape[0]
+        ids = torch.empty(nq, 10, dtype=torch.int64, device="cuda")
+        dd = torch.empty(nq, 10, dtype=torch.float32, device="cuda")
+        st = torch.zeros(nq, 4, dtype=torch.int64, device="cuda")
+        case.gpu.search(case.q_rot, 10, 6, 0.1, 32, ids, dd, tile=64, stats=st, schedule=dade.SCHED_ROUNDS,
+                        list_chunk=chunk)
+        case.gpu.sync()
+        out.append((ids.cpu().numpy(), dd.cpu().numpy(), st.cpu().numpy()))
+    for o2 in out[1:]:
+        assert np.array_equal(out[0][0], o2[0]) and np.array_equal(out[0][1].view(np.uint32), o2[1].view(np.uint32))
+        assert np.array_equal(out[0][2], o2[2])
+    o = case.oracle_search(10, 6, 0.1, 32, tile=64, schedule=dade.SCHED_ROUNDS)
+    parity.compare(out[0][0], out[0][1], o, case.exact_d)
+    parity.compare_stats(out[0][2], o)
+
+
+def test_rounds_schedule_with_prefilter():
+    """Row rounds with the low-precision prefilter (query-major rounds): the
+    FP32 path's bits and counters."""
+    base, queries, _ = synth.make("c1_gauss_10k_d128", n=6000, nq=60)
+    assign = synth.zipf_assign(6000, 30, s=1.0)
+    ix = dade.Index(torch.from_numpy(base).cuda(), 30, assign=assign, eps_pairs=3000,
+                    lead_format=dade.LEAD_FP8, lead_dims=64)
+    q = torch.from_numpy(queries).cuda()
+    out = []
+    for fl in (dade.FLAG_SEED_SPLIT, dade.FLAG_LEAD):
+        ids = torch.empty(60, 20, dtype=torch.int64, device="cuda")
+        d = torch.empty(60, 20, dtype=torch.float32, device="cuda")
+        st = torch.zeros(60, 4, dtype=torch.int64, device="cuda")
+        ix.query(q, 20, 10, 0.1, 32, ids, d, stats=st, flags=fl, schedule=dade.SCHED_ROUNDS, tile=32)
+        ix.sync()
+        out.append((ids.cpu().numpy(), d.cpu().numpy(), st.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
+    assert np.array_equal(out[0][2], out[1][2])

@@ -46,6 +46,17 @@ PLANTS = [
      "double r2 = ntop == K ? buf[0].key : INFINITY;"),
     ("seed_threshold_one_list_late", "if (seed > 0 && j == seed) r2_seed", "if (seed > 0 && j == seed + 1) r2_seed"),
     ("seed_threshold_not_frozen", "if (seed > 0 && j >= seed) r2 = r2_seed;", "if (seed > 0 && j > seed) r2 = r2_seed;"),
+    # lagged tile schedule: r of tile t taken one tile late / written to the wrong ring slot
+    ("lag_off_by_one", "epoch - 1 - lag >= 0 ? hist[(epoch - 1 - lag) % (lag + 1)]",
+     "epoch - lag >= 0 ? hist[(epoch - lag) % (lag + 1)]"),
+    ("lag_ring_index", "hist[epoch % (lag + 1)] = ", "hist[(epoch + 1) % (lag + 1)] = "),
+    # row rounds: threshold never refreshed, rounds growing linearly, a row skipped per round
+    ("rounds_threshold_not_refreshed", "double r2 = ntop < K ? INFINITY : buf[K - 1].key;", "double r2 = INFINITY;"),
+    ("rounds_not_doubling", "hi = 2 * hi;", "hi = hi + tile;"),
+    ("rounds_first_row_skipped", "for (int64_t t = lo; t < hi && t < len; ++t)",
+     "for (int64_t t = lo + (lo > 0); t < hi && t < len; ++t)"),
+    # the decision bracket moves the threshold the wrong way
+    ("bias_sign", "double r2b = (r2_) * (1.0 + bias)", "double r2b = (r2_) * (1.0 - bias)"),
     ("probe_descending", "for (int j = 0; j < nprobe; ++j) {\n                probe[q * nprobe + j] = (int32_t)buf[j].id;",
      "for (int j = 0; j < nprobe; ++j) {\n                probe[q * nprobe + j] = (int32_t)buf[nc - 1 - j].id;"),
 ]
