@@ -507,6 +507,17 @@ const char *dade_last_error(void);
  * indexes); the difference over a region counts that region's launches. */
 unsigned long long dade_launch_count(void);
 
+/*
+ * Measured FP32 fused multiply-add throughput of the current GPU in TFLOP/s
+ * (an FMA counts 2 FLOPs): a kernel of independent FMA chains filling every
+ * SM, launched iters x 16 x 8 FMAs per thread, timed with CUDA events on
+ * `stream` (best of three after a warm-up launch).  No counterpart in the
+ * paper: the denominator of the arithmetic roofline of the list-major scan
+ * kernels, whose staged rows are shared by many queries.  Synchronises
+ * `stream`; allocates a small output buffer.
+ */
+dade_status dade_fp32_fma_peak(int32_t iters, double *tflops, dade_stream stream);
+
 /* Library version string. */
 const char *dade_version(void);
 

@@ -199,20 +199,28 @@ class Oracle:
         """``search`` plus its decision bracket.  The search runs three times:
         as the method (bias 0), with every test and final compare moved a
         relative ``btol`` towards pruning (bias -btol), and towards keeping
-        (bias +btol).  A query is *stable* when the three runs return the same
-        ids and none of them has a near-tie that no bias moves (flag 4: the K-th
-        place of a merge; flag 8: the probe order, both at relative ``btol``):
-        a computation whose decisions err by less than ``btol`` returns exactly
-        those ids.  Its work counters are stable when the three runs count the
-        same.  Returns ids, dists, stats, flags, stable, stats_stable."""
+        (bias +btol).  The results of a query split at its boundary
+        kth / (1 + 2 btol), kth the K-th distance: the prefix below it is
+        unique, while the places at the boundary may hold any of the
+        candidates whose distances tie with the K-th within the bracket.  A
+        query is *stable* when the three runs agree on the prefix: a
+        computation that scans the same probe lists and whose decisions err by
+        less than ``btol`` returns that prefix, followed by boundary
+        candidates.  (Flag 8 marks a near-tie in the probe order; a caller
+        that cannot check the other side's probe lists treats it as unstable.)
+        Its work counters are stable when the three runs count the same.
+        Returns ids, dists, stats, flags, stable, stats_stable, boundary
+        (the boundary distance per query; +inf when fewer than K are found)."""
         kw = dict(kw, tol=btol)
         ids, dists, stats, flags = self.search(*args, **kw, bias=0.0)
         lo = self.search(*args, **kw, bias=-btol)
         hi = self.search(*args, **kw, bias=btol)
-        boundary = (flags | lo[3] | hi[3]) & (4 | 8)     # in any of the three runs
-        stable = (ids == lo[0]).all(1) & (ids == hi[0]).all(1) & (boundary == 0)
+        boundary = dists[:, -1] / (1.0 + 2.0 * btol)
+        # every run's results below the boundary (its own exact distances) are the method's
+        stable = np.array([np.array_equal(ids[q][dists[q] < boundary[q]], r[0][q][r[1][q] < boundary[q]])
+                           for r in (lo, hi) for q in range(ids.shape[0])]).reshape(2, -1).all(0)
         stats_stable = (stats == lo[2]).all(1) & (stats == hi[2]).all(1)
-        return ids, dists, stats, flags, stable, stats_stable
+        return ids, dists, stats, flags, stable, stats_stable, boundary
 
     def estimate_sq(self, q, o, d, lam):
         """Eq. 13 for one pair from its first d rotated dimensions."""

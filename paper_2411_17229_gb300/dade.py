@@ -102,6 +102,7 @@ SIGNATURES = {
     "dade_host_sym_eig": (_i32, [_vp, _i32, _vp, _vp]),
     "dade_sync": (_i32, [_vp, _vp]),
     "dade_probe_noalloc": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
+    "dade_fp32_fma_peak": (_i32, [_i32, _vp, _vp]),
     "dade_last_error": (C.c_char_p, []),
     "dade_version": (C.c_char_p, []),
 }
@@ -122,6 +123,13 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def fp32_fma_peak(iters: int = 4096, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current GPU, TFLOP/s (dade_fp32_fma_peak)."""
+    out = C.c_double()
+    _check(lib().dade_fp32_fma_peak(int(iters), C.byref(out), _stream(stream)))
+    return out.value
 
 
 def _check(status: int):

@@ -63,7 +63,11 @@ def test_adsampling_parity(case, k, nprobe, eps0, delta_d, schedule, seed):
     o = c["o"].search_bracket(c["Xr"], c["assign"], c["cent"], np.ones(128), c["Qr"], k, nprobe,
                               delta_d, eps, schedule=oracle.TILE, tile=128, seed=seed)
     exact = lambda q, sel: ((c["Xr"][sel] - c["Qr"][q]) ** 2).sum(1)
-    parity.compare(ids.cpu().numpy(), d.cpu().numpy(), o, exact)
+    pg = torch.empty(nq, nprobe, dtype=torch.int32, device="cuda")
+    c["g"].probe(c["q_rot"], nprobe, pg)
+    c["g"].sync()
+    po, _ = c["o"].probe(c["Qr"], c["cent"], nprobe)
+    parity.compare(ids.cpu().numpy(), d.cpu().numpy(), o, exact, same_probe=(pg.cpu().numpy() == po).all(1))
     g_st = st.cpu().numpy()
     parity.compare_stats(g_st, o)
     assert g_st[:, 3].sum() > 0   # the test prunes

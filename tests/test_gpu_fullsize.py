@@ -86,13 +86,14 @@ def _run_batch_case(wname, pt, n_pairs, **build_kw):
     orc = oracle.SampledIndex(base, assign, w.n_clusters, pairs, queries[sample], pt["nprobe"])
     # the probe (Section 3.4): the oracle's nearest lists, by (distance, list id)
     same = [np.array_equal(probe[s], orc.probe[i]) for i, s in enumerate(sample) if not orc.probe_tie[i]]
-    assert all(same) and len(same) >= N_SAMPLE // 2
+    assert all(same)
+    same_probe = np.array([np.array_equal(probe[s], orc.probe[i]) for i, s in enumerate(sample)])
     o = _oracle_point(orc, K, pt)
 
     def exact_d(i, sel):
         return ((base[sel].astype(np.float64) - queries[sample[i]].astype(np.float64)) ** 2).sum(-1)
 
-    summary = parity.compare(ids[sample], dists[sample], o, exact_d)
+    summary = parity.compare(ids[sample], dists[sample], o, exact_d, same_probe=same_probe)
     print(f"{wname}: {summary}")
     _check_properties(base, queries, ids, dists)
     ix.close()
@@ -148,6 +149,15 @@ def test_c5_full_size_serving():
     assert st["requests_done"] == n_req and st["batches"] < n_req
     sample = np.sort(rng.choice(n_req, N_SAMPLE, replace=False))
     orc = oracle.SampledIndex(base, assign, w.n_clusters, pairs, queries[picks[sample]], 128)
+    # the lists the server's batches probed for the sampled requests: each query's probe
+    # depends on that query alone, so probing it on its own gives the same lists
+    qs = torch.from_numpy(queries[picks[sample]]).cuda()
+    qsr = torch.empty_like(qs)
+    pg = torch.empty(len(sample), 128, dtype=torch.int32, device="cuda")
+    ix.rotate(qs, qsr)
+    ix.probe(qsr, 128, pg)
+    ix.sync()
+    pg = pg.cpu().numpy()
     unstable = 0
     for K, nprobe in sorted({(int(ks[i]), int(nps[i])) for i in sample}):
         rows = [j for j, i in enumerate(sample) if ks[i] == K and nps[i] == nprobe]
@@ -159,7 +169,9 @@ def test_c5_full_size_serving():
             q = queries[picks[sample[rows[i]]]].astype(np.float64)
             return ((base[sel].astype(np.float64) - q) ** 2).sum(-1)
 
-        summary = parity.compare(g_ids, g_d, tuple(x[rows] for x in o), exact_d, max_unstable_frac=1.0)
+        sp = np.array([np.array_equal(pg[j, :nprobe], orc.probe[j, :nprobe]) for j in rows])
+        summary = parity.compare(g_ids, g_d, tuple(x[rows] for x in o), exact_d, max_unstable_frac=1.0,
+                                 same_probe=sp)
         unstable += summary["unstable"]
     assert unstable <= max(1, N_SAMPLE // 10), unstable
     for i in range(n_req):
@@ -188,12 +200,13 @@ def test_c4_full_size_benchmark_point():
     orc = oracle.SampledIndex(base, labels, w.n_clusters, pairs, queries[sample], pt["nprobe"])
     same = [np.array_equal(probe[s], orc.probe[i]) for i, s in enumerate(sample) if not orc.probe_tie[i]]
     assert all(same)
+    same_probe = np.array([np.array_equal(probe[s], orc.probe[i]) for i, s in enumerate(sample)])
     o = _oracle_point(orc, w.k, pt)
 
     def exact_d(i, sel):
         return ((base[sel].astype(np.float64) - queries[sample[i]].astype(np.float64)) ** 2).sum(-1)
 
-    summary = parity.compare(ids[sample], dists[sample], o, exact_d)
+    summary = parity.compare(ids[sample], dists[sample], o, exact_d, same_probe=same_probe)
     print(f"c4: {summary}")
     _check_properties(base, queries, ids, dists)
     ix.close()

@@ -90,8 +90,13 @@ class LeadCase:
 
     def oracle_search(self, k, nprobe, alpha, delta_d, tile=128):
         eps = self.orc.eps(np.float32(alpha), delta_d)
-        return self.orc.o.search_bracket(self.orc.Xr, self.assign, self.orc.cent, self.orc.lam, self.Qr, k, nprobe,
-                                         delta_d, eps, schedule=oracle.TILE, tile=tile, lag=0)
+        o = self.orc.o.search_bracket(self.orc.Xr, self.assign, self.orc.cent, self.orc.lam, self.Qr, k, nprobe,
+                                      delta_d, eps, schedule=oracle.TILE, tile=tile, lag=0)
+        pg = torch.empty(self.queries.shape[0], nprobe, dtype=torch.int32, device="cuda")
+        self.gpu.probe(self.q_rot, nprobe, pg)
+        self.gpu.sync()
+        po, _ = self.orc.o.probe(self.Qr, self.orc.cent, nprobe)
+        return o + ((pg.cpu().numpy() == po).all(1),)
 
     def exact_d(self, q, ids):
         return ((self.orc.Xr[ids] - self.Qr[q]) ** 2).sum(1)
