@@ -47,7 +47,8 @@ std::map<std::tuple<const void *, int, int, size_t>, int> g_resident; // (kernel
 } // namespace
 
 dade_status kernel_smem(const void *func, size_t smem) {
-    if (smem <= 48 * 1024) return DADE_OK;
+    // set even below 48 KB: a kernel whose static shared memory brings the total
+    // above 48 KB needs the attribute for its dynamic part as well
     int dev = 0;
     DADE_TRY_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(g_attr_mu);
