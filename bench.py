@@ -1,19 +1,24 @@
 #!/usr/bin/env python3
 """DADE-IVF vs a full-dimension FP32 IVF scan on GB300: QPS at recall@K >= 0.95.
 
-Workload (default ``c2_mix_1m_d128``): 1,000,000 base vectors of dimension 128,
-nonnegative integers 0..255 stored as FP32, from a 64-component anisotropic
-Gaussian mixture (lambda_i ~ i^-1); 10,000 held-out queries; IVF with 4096
-k-means lists (seeded, 10 Lloyd iterations); K = 100.  Synthetic, seeded.
+Headline workload (default ``c4_zipf_10m_d768``, the largest single-GPU
+configuration): 10,000,000 unit-normalised base vectors of dimension 768 from
+a 16,384-component Gaussian mixture (lambda_i ~ i^-1.5) with Zipf(1.1)
+component weights; the IVF lists are the generating components (largest
+1.47M rows, median 72); 10,000 queries; K = 10.  Synthetic, seeded.  The
+1M x 128 integer mixture (K = 100), the 1M x 960 mixture (K = 10) and the 5M x
+256 serving index follow as extra keys (``--extra``), each measured the same
+way; the request-server sweep runs on the serving index.
 
 A step is one pass of the whole hot path over the query batch, through the C
 ABI: query rotation (dade_rotate_queries), coarse probe (dade_probe) and the
 DADE scan with its per-query top-K (dade_scan).  Before timing, an autotuner
-sweeps nprobe, delta_d in {16, 32, 64}, alpha, shared-memory staging depth and
-CTA width, and keeps the point with the highest QPS whose recall@K (against
-exact FP64 ground truth) is >= 0.95; the FDScanning baseline (same kernels,
-no pruning) gets the same treatment.  The index (512 MB) is larger than L2,
-and L2 is also flushed (256 MB write) between timed steps.
+sweeps nprobe, delta_d, alpha, the threshold schedule (tile, seeded, row
+rounds) and its execution options, and keeps the point with the highest QPS
+whose recall@K (against exact FP64 ground truth) is >= 0.95; the FDScanning
+baseline (same kernels, no pruning) and ADSampling (same kernels, random
+basis) get the same treatment.  Indexes are larger than L2, and L2 is also
+flushed (256 MB write) between timed steps.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the host cores instead (the reference arm).
@@ -64,7 +69,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2_mix_1m_d128")
+    ap.add_argument("--workload", default="c4_zipf_10m_d768")
+    ap.add_argument("--extra", default="c2_mix_1m_d128,c3_mix_1m_d960,c5_mix_5m_d256",
+                    help="further workloads measured after the headline (comma list, or none)")
     ap.add_argument("--n", type=int, default=None, help="shrink the base (testing only)")
     ap.add_argument("--nq", type=int, default=None, help="shrink the query batch (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -135,7 +142,8 @@ def run_profile(args):
 
 
 # ----------------------------------------------------------------- helpers --
-def run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, stream, sh, tf, given=None):
+def run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, stream, sh, tf, given=None,
+                   steps=20, warm=5):
     """The paper's DCO baseline on the same GPU path: its own index over a
     random orthogonal basis (same lists by k-means), autotuned over eps0,
     delta_d, schedule and nprobe for recall@K >= the target, then timed as a
@@ -158,18 +166,21 @@ def run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, 
             ix.probe(qr, pt["nprobe"], pr, stream=sh)
             probes[pt["nprobe"]] = pr
         ix.scan(qr, probes[pt["nprobe"]], K, 0.5, pt["delta_d"], ids, dists, tile=pt["tile"], threads=128,
-                schedule=pt["schedule"], seed_lists=pt["seed_lists"], flags=fixed,
+                schedule=pt["schedule"], seed_lists=pt["seed_lists"], flags=fixed, list_chunk=pt.get("list_chunk", 0),
                 estimator=dade.ESTIMATOR_ADSAMPLING, eps0=pt["eps0"], stream=sh)
 
     best = None
-    scheds = [(0, 0, 256)] + ([(2, 2, 256), (2, 3, 256)] if list_major else [])
+    scheds = [(0, 0, 256, 0)] + ([(2, 2, 256, 0), (2, 3, 256, 0)] if list_major else [])
     eps0s, dds = (0.25, 0.35, 0.5, 0.75, 1.0, 1.5, 2.1), (16, 32, 64)
+    if w.comp_zipf > 0:   # very uneven lists: the row-rounds schedule, as for DADE
+        scheds = [(3, 0, 64, 1024)] if list_major else [(3, 0, 64, 0)]
+        eps0s, dds = (0.5, 1.0, 1.5, 2.1), (32, 64)
     for eps0 in eps0s:
         for dd in dds:
-            for sched, seed, tile in scheds:
+            for sched, seed, tile, chunk in scheds:
                 for nprobe in [p for p in grid if p >= n0][:3]:
                     pt = {"nprobe": nprobe, "eps0": eps0, "delta_d": dd, "schedule": sched, "seed_lists": seed,
-                          "tile": tile}
+                          "tile": tile, "list_chunk": chunk}
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     try:
                         e0.record(stream)
@@ -197,7 +208,7 @@ def run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, 
     pt = best[2]
     pr = torch.empty(nq, pt["nprobe"], dtype=torch.int32, device="cuda")
     ms_steps = []
-    for i in range(args.warmup + args.steps):
+    for i in range(warm + steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -207,7 +218,7 @@ def run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, 
         scan(pt)
         e1.record(stream)
         torch.cuda.synchronize()
-        if i >= args.warmup:
+        if i >= warm:
             ms_steps.append(e0.elapsed_time(e1))
     rc = recall_at_k(torch, xb, q, ids, gt_kth, K)
     log(f"[bench] ADSampling {pt} {statistics.mean(ms_steps):.3f} ms/step recall {rc:.4f} "
@@ -215,7 +226,7 @@ def run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, 
     ix.close()
     return {"value": round(nq / (statistics.mean(ms_steps) / 1e3), 1), "unit": UNIT, "recall": round(rc, 5),
             "ms_per_step": round(statistics.mean(ms_steps), 4), "eps0": pt["eps0"], "delta_d": pt["delta_d"],
-            "nprobe": pt["nprobe"], "schedule": {0: "tile", 2: "seeded"}[pt["schedule"]],
+            "nprobe": pt["nprobe"], "schedule": SCHED_NAMES[pt["schedule"]],
             "seed_lists": pt["seed_lists"] or None,
             "index": "random orthogonal basis (seeded), lists by the same recipe"}
 
@@ -381,6 +392,12 @@ def scan_kernel_name(point, d):
     if point["mode"] == 1:
         return f"k_fd_fast<{point['threads']}, 8>" if nb == 8 else "k_scan<FD>"
     lead = point.get("flags", 0) & 2
+    if point.get("schedule", 0) == 3:
+        if point.get("flags", 0) & 16 or nb < 8:
+            return f"k_scan<DADE{', lead' if lead else ''}> (row rounds split over CTAs) + k_lm_merge"
+        if lead:
+            return f"k_lm_tc<{min(point['delta_d'] // 16, 8)}> (row rounds, tensor-core prefilter) + k_lm_merge"
+        return f"k_lm_g<{min(point['delta_d'] // 16, 8)}> (row rounds, list-major) + k_lm_merge"
     if point.get("schedule", 0) == 2 and point.get("flags", 0) & 16:
         return (f"k_scan<{point['threads']}, DADE{', lead' if lead else ''}> (first {point.get('seed_lists')} "
                 f"lists, then the later lists split over CTAs) + k_lm_merge")
@@ -400,16 +417,16 @@ def scan_kernel_name(point, d):
     return f"k_scan<DADE> ({point['stage_dims']} dims staged)" if point.get("stage_dims") else "k_scan<DADE>"
 
 
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0   # GB300: SMs, FP32 lanes per SM, maximum SM clock
-FLOPS_PER_DIM = 3                                # one subtract and one fused multiply-add per dimension
+SERVING_WORKLOAD = "c5_mix_5m_d256"
 
 
 def list_major_point(point, d):
-    """True where the scan's later lists run list-major (seeded schedule, not
-    split, D > 112, delta_d of 1, 2, 4 or 8 blocks)."""
+    """True where the scan runs list-major (seeded schedule's later lists, or
+    every round of the row-rounds schedule; not split, D > 112, delta_d of 1,
+    2, 4 or 8 blocks)."""
     nb = (d + 15) // 16
     gb = 8 if point.get("mode", 0) == 1 else min(point.get("delta_d", 32) // 16, nb)
-    return (point.get("schedule", 0) == 2 and not point.get("flags", 0) & 16 and nb >= 8
+    return (point.get("schedule", 0) in (2, 3) and not point.get("flags", 0) & 16 and nb >= 8
             and gb in (1, 2, 4, 8))
 
 
@@ -456,7 +473,8 @@ def point_kw(point):
     """The scan options of an autotuned point, as keyword arguments of the binding."""
     return dict(mode=point["mode"], tile=point["tile"], spec=point.get("spec", 8), threads=point["threads"],
                 schedule=point.get("schedule", 0), flags=point.get("flags", 0),
-                seed_lists=point.get("seed_lists", 0), stage_dims=point.get("stage_dims", 0))
+                seed_lists=point.get("seed_lists", 0), stage_dims=point.get("stage_dims", 0),
+                list_chunk=point.get("list_chunk", 0))
 
 
 def ground_truth(torch, xb, q, K):
@@ -493,32 +511,69 @@ def recall_at_k(torch, xb, q, ids, gt_kth, K):
 
 
 # ------------------------------------------------------------------- ours ----
-def run_ours(args):
+SCHED_NAMES = {0: "tile", 1: "pipelined", 2: "seeded", 3: "rounds"}
+
+
+def dade_variants(dade, w, lf):
+    """Execution variants the autotuner tries on a workload: (schedule, tile,
+    threads, flags, seed_lists, stage_dims, list_chunk).  tile is the first
+    round's rows for the row-rounds schedule."""
+    nb = (w.d + 15) // 16
+    list_major = nb >= 8
+    lead = (dade.FLAG_LEAD,) if lf else ()
+    v = []
+    if w.comp_zipf > 0:   # very uneven lists: doubling row windows, split over many thread blocks
+        v += [(dade.SCHED_ROUNDS, r1, 128, fl, 0, 0, ch) for r1 in (32, 64) for ch in (1024, 4096)
+              for fl in (0,) + (lead if lf == dade.LEAD_BF16 else ())]
+        v += [(dade.SCHED_TILE, 128, 128, 0, 0, 0, 0)]
+        return v
+    v += [(dade.SCHED_TILE, tile, nt, fl, 0, 0, 0) for tile in (128, 256) for fl in (0,) + lead for nt in (128, 256)]
+    if list_major:
+        v += [(dade.SCHED_SEEDED, tile, 128, fl, seed, 0, 0) for seed in (2, 3, 4) for tile in (128, 256)
+              for fl in (0,) + (lead if lf == dade.LEAD_BF16 else ())]
+        v += [(dade.SCHED_ROUNDS, r1, 128, fl, 0, 0, 0) for r1 in (16, 32, 64)
+              for fl in (0,) + (lead if lf == dade.LEAD_BF16 else ())]
+    v += [(dade.SCHED_SEEDED, 128, nt, dade.FLAG_SEED_SPLIT, seed, 0, 0) for seed in (2, 3) for nt in (128, 256)]
+    if w.d > 128:
+        v += [(dade.SCHED_TILE, 128, 256, 0, 0, sd, 0) for sd in (64, 128)]
+    return v
+
+
+def precision_of(point, lf, dade):
+    if not point.get("flags", 0) & dade.FLAG_LEAD:
+        return "fp32"
+    return {dade.LEAD_BF16: "bf16 lead blocks", dade.LEAD_FP8: "fp8-e4m3 lead blocks"}.get(lf, "fp32")
+
+
+def dist_error(torch, xb, q, ids, dists):
+    """Largest relative error of the returned FP32 distances against the FP64
+    distances of the same ids in the original coordinates (Lemma 1)."""
+    worst = 0.0
+    for s in range(0, q.shape[0], 512):
+        idb = ids[s:s + 512]
+        valid = idb >= 0
+        rows = xb[idb.clamp(min=0)].double()
+        ex = ((q[s:s + 512].double()[:, None, :] - rows) ** 2).sum(-1)
+        err = (dists[s:s + 512].double() - ex).abs() / ex.clamp(min=1e-300)
+        worst = max(worst, float(err[valid].max().item()) if bool(valid.any()) else 0.0)
+    return worst
+
+
+def measure_workload(args, wname, rank, world, dist, headline):
+    """Autotune, time and describe one workload.  Returns the fields of the
+    JSON line (headline) or of its per-workload extra key."""
     import torch
-    import torch.distributed as dist
-    from paper_2411_17229_gb300 import build as libbuild
     from paper_2411_17229_gb300 import dade
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if rank == 0:
-        libbuild.build()
-    if world > 1:
-        dist.barrier()
     lib = dade.lib()
-
-    w = synth.WORKLOADS[args.workload]
-    n = args.n or w.n
-    nq = args.nq or w.nq
+    w = synth.WORKLOADS[wname]
+    n = (args.n or w.n) if headline else w.n
+    nq = (args.nq or w.nq) if headline else w.nq
     K = w.k
     nc = w.n_clusters if n == w.n else max(16, n // 244)
+    t_all = time.time()
     t0 = time.time()
     base, queries, labels = synth.make(w, n=n, nq=nq)
-    log(f"[bench] data {n}x{w.d}, {nq} queries in {time.time() - t0:.1f}s")
+    log(f"[bench] {wname}: data {n}x{w.d}, {nq} queries in {time.time() - t0:.1f}s")
     # lists: k-means, or the generating components (uneven Zipf lists) where the workload says so
     given = {"assign": labels} if w.lists_are_components and n == w.n else {}
     xb = torch.from_numpy(base).cuda()
@@ -528,10 +583,10 @@ def run_ours(args):
     tf = tail_opt(args, w.d)
     ix = dade.Index(xb, nc, kmeans_iters=w.kmeans_iters, seed=synth.SEED_KMEANS, lead_format=lf, lead_dims=ld,
                     tail_from=tf, **given)
-    # flags every point uses: results do not depend on them (query order, tail copy)
-    fixed = dade.FLAG_QUERY_ORDER | (dade.FLAG_ROW_TAIL if tf else 0)
+    fixed = dade.FLAG_QUERY_ORDER | (dade.FLAG_ROW_TAIL if tf else 0)   # results do not depend on these
     torch.cuda.synchronize()
-    log(f"[bench] index built in {time.time() - t0:.1f}s (max list {ix.info.max_list}, "
+    build_s = time.time() - t0
+    log(f"[bench] {wname}: index built in {build_s:.1f}s (max list {ix.info.max_list}, "
         f"{ix.info.data_bytes / 2**20:.0f} MiB packed)")
     gt_ids, gt_kth = ground_truth(torch, xb, q, K)
 
@@ -557,8 +612,7 @@ def run_ours(args):
                 stats=st, lead_stats=lead_st, stream=sh, **point_kw(pt))
 
     def measure(pt, reps=4):
-        """(ms per scan, recall) of a point, or None if the library refuses it
-        (e.g. a pass that would accept more than the accept buffer holds)."""
+        """(ms per scan, recall) of a point, or None if the library refuses it."""
         try:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -570,8 +624,10 @@ def run_ours(args):
             return None
         torch.cuda.synchronize()
         rc = recall_at_k(torch, xb, q, ids, gt_kth, K)
-        if e0.elapsed_time(e1) > 20.0:   # slow point: the first run is the measurement
-            return e0.elapsed_time(e1), rc
+        first = e0.elapsed_time(e1)
+        if first > 200.0:   # slow point: the first run is the measurement
+            return first, rc
+        reps = 2 if first > 20.0 else reps
         e0.record(stream)
         for _ in range(reps):
             scan(pt)
@@ -581,9 +637,8 @@ def run_ours(args):
 
     # ---- autotune (untimed) ------------------------------------------------------
     t0 = time.time()
-    grid = [8, 12, 16, 20, 24, 28, 32, 40, 48, 64, 96, 128]
-    # FDScanning: the smallest nprobe that reaches the target on the plain tile
-    # schedule, then every schedule at that nprobe (seeded FD is exact FD: r only selects)
+    grid = [8, 10, 12, 16, 20, 24, 28, 32, 40, 48, 64, 96, 128]
+    # FDScanning: the smallest nprobe that reaches the target, then its schedules
     fd_best, fd_rec = None, {}
     base_fd = {"mode": dade.MODE_FD, "tile": 128, "threads": 256, "flags": dade.FLAG_QUERY_ORDER, "schedule": 0,
                "seed_lists": 0}
@@ -596,13 +651,13 @@ def run_ours(args):
             fd_best = (r[0], r[1], dict(base_fd, nprobe=nprobe))
             break
     if fd_best is not None:
-        fd_variants = [(128, 64, 0, 0, 0), (128, 128, 0, 0, 0)]
-        if (w.d + 15) // 16 >= 8:
-            fd_variants += [(256, 128, dade.SCHED_SEEDED, 1, 0), (256, 128, dade.SCHED_SEEDED, 2, 0),
-                            (256, 128, dade.SCHED_SEEDED, 3, 0), (256, 1 << 20, dade.SCHED_SEEDED, 1, 0),
-                            (256, 1 << 20, dade.SCHED_SEEDED, 2, 0)]
-        fd_variants += [(nt, 128, dade.SCHED_SEEDED, seed, dade.FLAG_SEED_SPLIT) for nt in (128, 256)
-                        for seed in (1, 2, 3)]
+        nb = (w.d + 15) // 16
+        fd_variants = [(128, 128, 0, 0, 0)]
+        if nb >= 8 and fd_best[0] < 200.0:
+            fd_variants += [(256, 128, dade.SCHED_SEEDED, s_, 0) for s_ in (1, 2, 3)]
+            fd_variants += [(256, 1 << 20, dade.SCHED_SEEDED, 1, 0)]
+        if fd_best[0] < 200.0:
+            fd_variants += [(nt, 128, dade.SCHED_SEEDED, s_, dade.FLAG_SEED_SPLIT) for nt in (128, 256) for s_ in (1, 2)]
         for threads, tile, sched, seed, fl in fd_variants:
             pt = {"mode": dade.MODE_FD, "nprobe": fd_best[2]["nprobe"], "tile": tile, "threads": threads,
                   "flags": dade.FLAG_QUERY_ORDER | fl, "schedule": sched, "seed_lists": seed}
@@ -610,64 +665,45 @@ def run_ours(args):
             if r is not None and r[1] >= RECALL_TARGET and r[0] < fd_best[0]:
                 fd_best = (r[0], r[1], pt)
     n0 = min(p for p in grid if fd_rec.get(p, 0) >= RECALL_TARGET) if fd_best else grid[-1]
-    dade_best = None
+    variants = dade_variants(dade, w, lf)
+    dds, alphas = (16, 32, 64), (0.1, 0.3, 0.5, 0.8, 0.9, 0.95, 0.98)
+    if fd_best is not None and fd_best[0] > 50.0:   # a large workload: a narrower sweep
+        dds, alphas = (32, 64), (0.5, 0.8, 0.9, 0.95)
     tried = []
-    lead_flags = (0, dade.FLAG_LEAD) if lf else (0,)
-    variants = [(dade.SCHED_TILE, 8, tile, nt, fl, 0, 0) for tile in (128, 192, 256) for fl in lead_flags
-                for nt in (128, 256)]
-    list_major = (w.d + 15) // 16 >= 8   # the list-major kernels cover D > 112
-    if list_major:
-        variants += [(dade.SCHED_SEEDED, 8, tile, nt, 0, seed, 0) for seed in (2, 3, 4)
-                     for tile in (64, 128, 256, 1 << 20) for nt in (128, 256)
-                     if nt == 128 or tile < (1 << 20)]   # 1 << 20: whole lists, seed lists list-major too
-    if list_major or w.d <= 112:   # passes with r frozen query-major, split over CTAs
-        variants += [(dade.SCHED_SEEDED, 8, 128, nt, dade.FLAG_SEED_SPLIT, seed, 0) for seed in (2, 3)
-                     for nt in (128, 256)]
-    if w.d > 128:   # generic tile kernel: stream several increments per tile (two stages <= 160 KB)
-        variants += [(dade.SCHED_TILE, 8, tile, nt, 0, 0, sd) for tile in (64, 128) for sd in (64, 128, 256)
-                     for nt in (128, 256) if tile * sd * 8 <= 160 * 1024]
-    dds, alphas = (16, 32, 64), (0.05, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8)
-    if fd_best is not None and fd_best[0] > 50.0:   # a large workload: a coarser sweep
-        dds, alphas = (32, 64), (0.1, 0.3, 0.8)
-        variants = [v for v in variants if v[0] == dade.SCHED_TILE and v[2] == 128 and not v[6]]
     for dd in dds:
         for alpha in alphas:
-            for schedule, spec, tile, threads, fl, seed, sd in variants:
-                    if sd and (sd <= dd or sd % dd):
+            for schedule, tile, threads, fl, seed, sd, chunk in variants:
+                if sd and (sd <= dd or sd % dd):
+                    continue
+                if fl & dade.FLAG_LEAD and min(dd, (w.d + 15) // 16 * 16) > ld:
+                    continue
+                for nprobe in [p for p in grid if p >= n0][:3]:
+                    pt = {"mode": dade.MODE_DADE, "nprobe": nprobe, "alpha": alpha, "delta_d": dd, "spec": 8,
+                          "tile": tile, "threads": threads, "schedule": schedule,
+                          "flags": (fl | fixed) | (dade.FLAG_GENERIC_KERNEL if sd else 0),
+                          "seed_lists": seed, "stage_dims": sd, "list_chunk": chunk}
+                    r = measure(pt)
+                    if r is None:
                         continue
-                    for nprobe in [p for p in grid if p >= n0][:3]:
-                        pt = {"mode": dade.MODE_DADE, "nprobe": nprobe, "alpha": alpha, "delta_d": dd,
-                              "spec": spec, "tile": tile, "threads": threads, "schedule": schedule,
-                              "flags": (fl | fixed) | (dade.FLAG_GENERIC_KERNEL if sd else 0),
-                              "seed_lists": seed, "stage_dims": sd}
-                        r = measure(pt)
-                        if r is None:
-                            continue
-                        ms, rc = r
-                        tried.append((ms, rc, pt))
-                        if rc >= RECALL_TARGET:
-                            if dade_best is None or ms < dade_best[0]:
-                                dade_best = (ms, rc, pt)
-                            break
-    # the sweep times each point over 4 scans: re-time the fastest few over more
-    # scans before choosing, so that run-to-run noise does not pick the point
-    finalists = sorted((t for t in tried if t[1] >= RECALL_TARGET), key=lambda t: t[0])[:6]
-    if len(finalists) > 1:
-        dade_best = None
-        for ms_, rc_, pt_ in finalists:
-            r = measure(pt_, reps=16)
-            if r is not None and r[1] >= RECALL_TARGET and (dade_best is None or r[0] < dade_best[0]):
-                dade_best = (r[0], r[1], pt_)
-    for ms_, rc_, pt_ in sorted(tried, key=lambda t: t[0])[:12]:
+                    tried.append((r[0], r[1], pt))
+                    if r[1] >= RECALL_TARGET:
+                        break
+    # re-time the fastest few over more scans before choosing
+    dade_best = None
+    for ms_, rc_, pt_ in sorted((t for t in tried if t[1] >= RECALL_TARGET), key=lambda t: t[0])[:6]:
+        r = measure(pt_, reps=12)
+        if r is not None and r[1] >= RECALL_TARGET and (dade_best is None or r[0] < dade_best[0]):
+            dade_best = (r[0], r[1], pt_)
+    for ms_, rc_, pt_ in sorted(tried, key=lambda t: t[0])[:8]:
         log(f"[bench]   {ms_:.3f} ms recall {rc_:.4f} {pt_}")
-    log(f"[bench] autotune {time.time() - t0:.1f}s: FD {fd_best[2] if fd_best else None} "
-        f"{fd_best[0] if fd_best else 0:.3f} ms; DADE {dade_best[2] if dade_best else None} "
-        f"{dade_best[0] if dade_best else 0:.3f} ms")
     if dade_best is None:
         dade_best = min(tried, key=lambda t: (-t[1], t[0]))
     point = dade_best[2]
+    tune_s = time.time() - t0
+    log(f"[bench] {wname}: autotune {tune_s:.1f}s: FD {fd_best[2] if fd_best else None} "
+        f"{fd_best[0] if fd_best else 0:.3f} ms; DADE {point} {dade_best[0]:.3f} ms")
 
-    # ---- algorithmic bytes of the chosen point (stats pass, untimed) -----------------
+    # ---- algorithmic work of the chosen point (stats pass, untimed) -------------------
     stats.zero_()
     use_lead = bool(point.get("flags", 0) & dade.FLAG_LEAD)
     lead_st = torch.zeros(nq, dtype=torch.int64, device="cuda") if use_lead else None
@@ -675,7 +711,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     st = stats.sum(0).cpu().numpy()
     cand, dims_sum, accepted = int(st[0]), int(st[1]), int(st[2])
-    # FP32 rows touched + ids of accepted candidates; with the prefilter, every
+    # FP32 rows touched + ids of accepted candidates; with the prefilter every
     # candidate reads its low-precision first increment and error norm, and the
     # candidates it drops read no FP32 row at all
     alg_bytes = 4 * dims_sum + 4 * accepted
@@ -685,6 +721,7 @@ def run_ours(args):
         d0 = min(point["delta_d"], w.d)
         es = 2 if lf == dade.LEAD_BF16 else 1
         alg_bytes += (es * d0 + 4) * cand - 4 * d0 * lead_dropped
+    alg_flops = 2 * dims_sum   # a subtract and a multiply-add per dimension touched
 
     # ---- timed region: K steps of rotate + probe + scan -------------------------------
     flush = torch.empty(64 * 2**20, dtype=torch.float32, device="cuda")
@@ -697,21 +734,23 @@ def run_ours(args):
         ev[1].record(stream)
         ix.scan(qr, pr_step, K, point["alpha"], point["delta_d"], ids, dists, stream=sh, **point_kw(point))
 
-    for _ in range(args.warmup):
+    steps = args.steps if headline else max(5, min(args.steps, 20))
+    warm = args.warmup if headline else 3
+    for _ in range(warm):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         flush.zero_()
         ev[0].record(stream)
         step(ev)
         ev[2].record(stream)
     torch.cuda.synchronize()
-    if world > 1:
+    if world > 1 and headline:
         dist.barrier()
     torch.cuda.synchronize()
     events = []
     launches0 = lib.dade_launch_count()
     wall0 = time.perf_counter()
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for _ in range(steps):
             flush.zero_()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             ev[0].record(stream)
@@ -719,7 +758,7 @@ def run_ours(args):
             ev[2].record(stream)
             events.append(ev)
         torch.cuda.synchronize()
-    if world > 1:
+    if world > 1 and headline:
         dist.barrier()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -729,18 +768,32 @@ def run_ours(args):
     rot_ms = [e[0].elapsed_time(e[3]) for e in events]
     probe_ms = [e[3].elapsed_time(e[1]) for e in events]
     lib.dade_sync(ix.handle, sh)
-    total_ms = max_over_ranks(torch, dist, sum(step_ms), world, "cuda")
-    ms_per_step = total_ms / args.steps
-    value = job_rate(world, nq, ms_per_step)
+    total_ms = max_over_ranks(torch, dist, sum(step_ms), world if headline else 1, "cuda")
+    ms_per_step = total_ms / steps
+    value = job_rate(world if headline else 1, nq, ms_per_step)
     rc_timed = recall_at_k(torch, xb, q, ids, gt_kth, K)
+    err_timed = dist_error(torch, xb, q, ids, dists)
     ids_timed = ids.clone()
+
+    # ---- precision configurations at the chosen point: recall and distance error ------
+    precision = {precision_of(point, lf, dade): {"recall": round(rc_timed, 5), "max_rel_dist_error": err_timed,
+                                                 "ms_per_scan": round(statistics.mean(scan_ms), 4)}}
+    alt = dict(point, flags=point["flags"] ^ dade.FLAG_LEAD) if lf else None
+    if alt is not None and (not alt["flags"] & dade.FLAG_LEAD or min(point["delta_d"], w.d) <= ld):
+        r = measure(alt, reps=4)
+        if r is not None:
+            precision[precision_of(alt, lf, dade)] = {"recall": round(r[1], 5),
+                                                      "max_rel_dist_error": dist_error(torch, xb, q, ids, dists),
+                                                      "ms_per_scan": round(r[0], 4),
+                                                      "same_ids_as_timed_step": bool(torch.equal(ids, ids_timed))}
 
     # ---- FD baseline timed the same way (same step structure) ------------------------
     fd_pt = fd_best[2] if fd_best else {"mode": dade.MODE_FD, "nprobe": n0, "tile": 128, "threads": 128,
                                         "flags": dade.FLAG_QUERY_ORDER}
     fd_ms = []
     pr_fd = torch.empty(nq, fd_pt["nprobe"], dtype=torch.int32, device="cuda")
-    for i in range(args.warmup + args.steps):
+    fd_steps = steps if (fd_best is None or fd_best[0] < 200.0) else max(3, min(steps, 8))
+    for i in range(warm + fd_steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -751,7 +804,7 @@ def run_ours(args):
                 seed_lists=fd_pt.get("seed_lists", 0), stream=sh)
         e1.record(stream)
         torch.cuda.synchronize()
-        if i >= args.warmup:
+        if i >= warm:
             fd_ms.append(e0.elapsed_time(e1))
     fd_qps = nq / (statistics.mean(fd_ms) / 1e3)
     fd_recall = recall_at_k(torch, xb, q, ids, gt_kth, K)
@@ -760,37 +813,38 @@ def run_ours(args):
     ads = None
     if not args.no_adsampling:
         try:
-            ads = run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, stream, sh,
-                                 tail_opt(args, w.d), given)
+            ads = run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, stream, sh, tf, given,
+                                 steps=steps, warm=warm)
         except Exception as e:  # noqa: BLE001 - reported, not fatal
             log(f"[bench] ADSampling comparator failed: {e}")
 
     # ---- the same step replayed as a captured CUDA graph (device buffers) ----------------
-    graph_ms = None
-    try:
-        gids = torch.empty(nq, K, dtype=torch.int64, device="cuda")
-        gd = torch.empty(nq, K, dtype=torch.float32, device="cuda")
-        g = ix.graph(q, K, point["nprobe"], point["alpha"], point["delta_d"], gids, gd, **point_kw(point))
-        gms = []
-        for i in range(args.warmup + args.steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            g.launch(stream=sh)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if i >= args.warmup:
-                gms.append(e0.elapsed_time(e1))
-        graph_ms = statistics.mean(gms)
-        graph_same = bool(torch.equal(gids, ids_timed))
-        g.close()
-    except Exception as e:  # noqa: BLE001 - reported, not fatal
-        log(f"[bench] graph step failed: {e}")
-        graph_same = None
+    graph = None
+    if headline:
+        try:
+            gids = torch.empty(nq, K, dtype=torch.int64, device="cuda")
+            gd = torch.empty(nq, K, dtype=torch.float32, device="cuda")
+            g = ix.graph(q, K, point["nprobe"], point["alpha"], point["delta_d"], gids, gd, **point_kw(point))
+            gms = []
+            for i in range(warm + steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.launch(stream=sh)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i >= warm:
+                    gms.append(e0.elapsed_time(e1))
+            graph = {"ms_per_step": round(statistics.mean(gms), 4),
+                     "value": round(nq / (statistics.mean(gms) / 1e3), 1), "unit": UNIT,
+                     "same_ids_as_timed_step": bool(torch.equal(gids, ids_timed))}
+            g.close()
+        except Exception as e:  # noqa: BLE001 - reported, not fatal
+            log(f"[bench] graph step failed: {e}")
 
     # ---- serving: continuous batching of single-query requests, mixed K and nprobe ------
     serving = None
-    if not args.no_serving:
+    if wname == SERVING_WORKLOAD and not args.no_serving:
         try:
             serving = serve_sweep(dade, ix, queries, point, (2000, 10000, 30000), args.serve_seconds,
                                   torch=torch, xb=xb)
@@ -802,88 +856,136 @@ def run_ours(args):
     ids_host = torch.empty(nq, K, dtype=torch.int64).pin_memory()
     d_host = torch.empty(nq, K, dtype=torch.float32).pin_memory()
     e2e_s = []
-    for i in range(args.warmup + args.steps):
+    for i in range(warm + steps):
         t1 = time.perf_counter()
         ix.query(q_host, K, point["nprobe"], point["alpha"], point["delta_d"], ids_host, d_host, stream=sh,
                  **point_kw(point))
-        if i >= args.warmup:
+        if i >= warm:
             e2e_s.append(time.perf_counter() - t1)
-    e2e_qps = job_rate(world, nq, 1e3 * max_over_ranks(torch, dist, statistics.mean(e2e_s), world, "cuda"))
+    e2e_qps = job_rate(world if headline else 1, nq,
+                       1e3 * max_over_ranks(torch, dist, statistics.mean(e2e_s), world if headline else 1, "cuda"))
 
+    # ---- roofline of the scan ---------------------------------------------------------
     peaks = measured_peaks()
     scan_mean = statistics.mean(scan_ms)
-    achieved = alg_bytes / (scan_mean / 1e3) / 1e9
-    traffic = recorded_traffic(point, args.workload)
+    bytes_rate = alg_bytes / (scan_mean / 1e3) / 1e9
+    traffic = recorded_traffic(point, wname)
     clocks = clk.summary()
+    fp32_peak = dade.fp32_fma_peak(stream=sh)
+    flops_rate = alg_flops / (scan_mean / 1e3) / 1e12
+    kname = scan_kernel_name(point, w.d)
     if list_major_point(point, w.d):
-        # each list is staged once for the ~R queries that probe it: the bytes touched
-        # come mostly from shared memory and L2, and the bound is FP32 arithmetic
-        mhz = clocks.get("sm_max_mhz") or SM_MAX_MHZ
-        peak = SMS * FP32_LANES * 2 * mhz / 1e6          # TFLOP/s (an FMA is 2 FLOPs)
-        flops = FLOPS_PER_DIM * dims_sum
-        got = flops / (scan_mean / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": scan_kernel_name(point, w.d), "achieved": round(got, 2), "peak": round(peak, 1),
-                "unit": "TFLOP/s", "frac": round(got / peak, 4), "traffic": traffic,
-                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": alg_bytes,
-                "bytes_touched_rate_gbs": round(achieved, 1),
-                "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 (FMA) x {mhz:.0f} MHz",
+        # each list window is staged once for all the queries that probe it: the bytes
+        # touched come mostly from shared memory and L2, the bound is FP32 arithmetic
+        roof = {"bound": "alu", "kernel": kname, "achieved": round(flops_rate, 3), "peak": round(fp32_peak, 1),
+                "unit": "TFLOP/s", "frac": round(flops_rate / fp32_peak, 4), "traffic": traffic,
+                "algorithmic_flops_per_launch": alg_flops, "algorithmic_bytes_per_launch": alg_bytes,
+                "bytes_touched_rate_gbs": round(bytes_rate, 1),
+                "bytes_touched_frac_of_hbm": round(bytes_rate / peaks.get("hbm_gbs", 6800.0), 4),
+                "dram_rate_gbs": round(traffic / (scan_mean / 1e3) / 1e9, 1) if traffic else None,
+                "peak_source": "measured (dade_fp32_fma_peak on this GPU: FP32 FMA chains filling every SM)",
                 "scan_ms": round(scan_mean, 4)}
     else:
-        roof = {"bound": "hbm", "kernel": scan_kernel_name(point, w.d), "achieved": round(achieved, 1),
-                "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                "frac": round(achieved / peaks.get("hbm_gbs", 6800.0), 4), "traffic": traffic,
-                "algorithmic_bytes_per_launch": alg_bytes,
+        roof = {"bound": "hbm", "kernel": kname, "achieved": round(bytes_rate, 1), "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": round(bytes_rate / peaks.get("hbm_gbs", 6800.0), 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": alg_bytes, "algorithmic_flops_per_launch": alg_flops,
+                "flops_rate_tflops": round(flops_rate, 3), "flops_frac_of_fp32": round(flops_rate / fp32_peak, 4),
+                "dram_rate_gbs": round(traffic / (scan_mean / 1e3) / 1e9, 1) if traffic else None,
                 "peak_source": "fallback" if peaks.get("_fallback") else "measured (MEASURED_PEAKS.json hbm_gbs)",
                 "scan_ms": round(scan_mean, 4)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(base, queries, w, nc, point, K, args.cpu_seconds, assign=given.get("assign"))
+        cpu = cpu_baseline(base, queries, w, nc, point, K, args.cpu_seconds if headline else args.cpu_seconds / 2,
+                           assign=given.get("assign"))
 
+    out = {
+        "value": round(value, 1), "ms_per_step": round(ms_per_step, 4), "steps": steps, "warmup": warm,
+        "config": {"workload": wname, "n": n, "d": w.d, "nq": nq, "n_clusters": nc, "k": K,
+                   "nprobe": point["nprobe"], "alpha": point.get("alpha"), "delta_d": point.get("delta_d"),
+                   "tile": point["tile"], "threads": point["threads"],
+                   "schedule": SCHED_NAMES[point.get("schedule", 0)],
+                   "seed_lists": point.get("seed_lists") if point.get("schedule", 0) == 2 else None,
+                   "first_round_rows": point["tile"] if point.get("schedule", 0) == 3 else None,
+                   "list_chunk": point.get("list_chunk") or None,
+                   "stage_dims": point.get("stage_dims") or None,
+                   "precision": precision_of(point, lf, dade),
+                   "lead_copy": {"format": args.lead, "dims": ld} if lf else None,
+                   "flags": {"query_order": bool(point["flags"] & dade.FLAG_QUERY_ORDER),
+                             "seed_split": bool(point["flags"] & dade.FLAG_SEED_SPLIT),
+                             "lead_prefilter": bool(point["flags"] & dade.FLAG_LEAD),
+                             "row_tail_from": tf if point["flags"] & dade.FLAG_ROW_TAIL else None},
+                   "l2": f"index {n * w.d * 4 / 2**20:.0f} MB > L2; 256 MB flush written between timed steps",
+                   "parallelism": f"replicas x{world}" if headline else "1 GPU"},
+        "recall": round(rc_timed, 5),
+        "max_rel_dist_error": err_timed,
+        "breakdown_ms": {"rotate": round(statistics.mean(rot_ms), 4), "probe": round(statistics.mean(probe_ms), 4),
+                         "scan": round(statistics.mean(scan_ms), 4)},
+        "latency_ms": {"p50": round(float(np.percentile(step_ms, 50)), 4),
+                       "p99": round(float(np.percentile(step_ms, 99)), 4), "per": "batch step"},
+        "precision_points": precision,
+        "serving": serving,
+        "fd_baseline": {"value": round(fd_qps, 1), "unit": UNIT, "recall": round(fd_recall, 5),
+                        "nprobe": fd_pt["nprobe"], "threads": fd_pt["threads"],
+                        "schedule": SCHED_NAMES[fd_pt.get("schedule", 0)],
+                        "seed_lists": fd_pt.get("seed_lists") or None,
+                        "seed_split": bool(fd_pt.get("flags", 0) & dade.FLAG_SEED_SPLIT),
+                        "ms_per_step": round(statistics.mean(fd_ms), 4)},
+        "dade_vs_fd": round(value / (world if headline else 1) / fd_qps, 3),
+        "adsampling": ads,
+        "dade_vs_adsampling": round(value / (world if headline else 1) / ads["value"], 3)
+        if ads and ads.get("value") else None,
+        "graph": graph,
+        "work": {"candidates": cand, "dims_per_candidate": round(dims_sum / max(1, cand), 2),
+                 "accepted": accepted, "lead_dropped": lead_dropped},
+        "roofline": roof,
+        "e2e": {"value": round(e2e_qps, 1), "unit": UNIT, "h2d_bytes_per_step": nq * w.d * 4,
+                "d2h_bytes_per_step": nq * K * 12 + 4},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "wall_s_timed_region": round(wall, 3),
+        "setup_s": {"index_build": round(build_s, 1), "autotune": round(tune_s, 1),
+                    "total": round(time.time() - t_all, 1)},
+    }
+    ix.close()
+    del xb, q, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2411_17229_gb300 import build as libbuild
+    from paper_2411_17229_gb300 import dade
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if rank == 0:
-        out = {
-            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "d": w.d, "nq": nq, "n_clusters": nc, "k": K,
-                       "nprobe": point["nprobe"], "alpha": point.get("alpha"), "delta_d": point.get("delta_d"),
-                       "spec": point.get("spec"), "tile": point["tile"], "threads": point["threads"],
-                       "schedule": {0: "tile", 1: "pipelined", 2: "seeded"}[point.get("schedule", 0)],
-                       "seed_lists": point.get("seed_lists") if point.get("schedule", 0) == 2 else None,
-                       "stage_dims": point.get("stage_dims") or None,
-                       "lead_prefilter": ({"format": args.lead, "dims": ld} if use_lead else None),
-                       "flags": {"query_order": bool(point["flags"] & dade.FLAG_QUERY_ORDER),
-                                 "seed_split": bool(point["flags"] & dade.FLAG_SEED_SPLIT),
-                                 "row_tail_from": tf if point["flags"] & dade.FLAG_ROW_TAIL else None},
-                       "l2": f"index {n * w.d * 4 / 2**20:.0f} MB > L2; 256 MB flush written between timed steps",
-                       "parallelism": f"replicas x{world}"},
-            "recall": round(rc_timed, 5),
-            "breakdown_ms": {"rotate": round(statistics.mean(rot_ms), 4), "probe": round(statistics.mean(probe_ms), 4),
-                             "scan": round(statistics.mean(scan_ms), 4)},
-            "latency_ms": {"p50": round(float(np.percentile(step_ms, 50)), 4),
-                           "p99": round(float(np.percentile(step_ms, 99)), 4), "per": "batch step"},
-            "serving": serving,
-            "fd_baseline": {"value": round(fd_qps, 1), "unit": UNIT, "recall": round(fd_recall, 5),
-                            "nprobe": fd_pt["nprobe"], "threads": fd_pt["threads"],
-                            "schedule": {0: "tile", 2: "seeded"}[fd_pt.get("schedule", 0)],
-                            "seed_lists": fd_pt.get("seed_lists") or None,
-                            "seed_split": bool(fd_pt.get("flags", 0) & dade.FLAG_SEED_SPLIT),
-                            "ms_per_step": round(statistics.mean(fd_ms), 4)},
-            "dade_vs_fd": round(value / world / fd_qps, 3),
-            "adsampling": ads,
-            "dade_vs_adsampling": round(value / world / ads["value"], 3) if ads else None,
-            "graph": ({"ms_per_step": round(graph_ms, 4), "value": round(world * nq / (graph_ms / 1e3), 1),
-                       "unit": UNIT, "same_ids_as_timed_step": graph_same} if graph_ms else None),
-            "work": {"candidates": cand, "dims_per_candidate": round(dims_sum / max(1, cand), 2),
-                     "accepted": accepted, "lead_dropped": lead_dropped},
-            "roofline": roof,
-            "e2e": {"value": round(e2e_qps, 1), "unit": UNIT, "h2d_bytes_per_step": nq * w.d * 4,
-                    "d2h_bytes_per_step": nq * K * 12 + 4},
-            "gpu_launches": int(launches),
-            "clocks": clocks,
-            "cpu_baseline": cpu,
-            "wall_s_timed_region": round(wall, 3),
-        }
+        libbuild.build()
+    if world > 1:
+        dist.barrier()
+    dade.lib()
+    head = measure_workload(args, args.workload, rank, world, dist, headline=True)
+    extras = {}
+    if world == 1 and args.extra and args.extra != "none":
+        for wn in [x for x in args.extra.split(",") if x and x != args.workload]:
+            try:
+                extras[wn] = measure_workload(args, wn, rank, world, dist, headline=False)
+            except Exception as e:  # noqa: BLE001 - an extra configuration must not sink the line
+                log(f"[bench] extra workload {wn} failed: {e}")
+                extras[wn] = {"error": str(e)[:200]}
+    if rank == 0:
+        out = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+        out.update({k: v for k, v in head.items() if k not in ("value", "ms_per_step", "steps", "warmup")})
+        out["extra_workloads"] = extras or None
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -55,6 +55,9 @@ dade_status kernel_smem(const void *func, size_t smem) {
     size_t &have = g_smem_set[{func, dev}];
     if (have >= smem) return DADE_OK;
     DADE_TRY_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // as much shared memory per SM as the carveout allows, so that several blocks fit
+    DADE_TRY_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared));
     have = smem;
     return DADE_OK;
 }

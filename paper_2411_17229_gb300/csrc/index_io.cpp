@@ -231,6 +231,7 @@ dade_status load_index(const char *path, dade_index *ix) {
         DADE_TRY(get_dev(f, ix->lead, lead_code_bytes(s), "lead codes"));
         DADE_TRY(get_dev(f, ix->lead_err, sizeof(float) * (size_t)s.slots * s.lead_nb, "lead error norms"));
         DADE_TRY(get_dev(f, ix->lead_scale, sizeof(float) * (size_t)s.nc * s.lead_nb, "lead scales"));
+        DADE_TRY(make_lead_tmap(ix));
     }
     if (s.tail_nb0 > 0) {
         ix->tail_nb0 = s.tail_nb0;

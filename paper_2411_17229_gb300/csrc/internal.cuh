@@ -1,6 +1,7 @@
 // internal.cuh -- shared declarations of libdade (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -113,6 +114,10 @@ struct dade_index {
     dade::DevBuf lead;      // codes; list c at slot_c * lead_nb * 16 * ES bytes, block b at + b * np * 16 * ES
     dade::DevBuf lead_scale;// float [nc][lead_nb] (FP8 only)
     dade::DevBuf lead_err;  // float [lead_nb][slots]: error norm over blocks 0..b (rounded up)
+    // TMA view of the BF16 codes as rows of 16 codes (32 B): row slot_c lead_nb + b np_c + i holds
+    // block b of member i of list c; boxes of 8 codes x 128 rows (the tensor-core prefilter, lm.cu)
+    CUtensorMap lead_tmap{};
+    bool lead_tmap_ok = false;
     // row-major copy of dims [16 tail_nb0, dp) of every slot: tail[(slot) * tail_w + k - 16 tail_nb0]
     int32_t tail_nb0 = 0, tail_w = 0;
     dade::DevBuf tail;
@@ -187,6 +192,8 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
 dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s);
 // DADE_SCHED_ROUNDS (lm.cu).
 dade_status scan_rounds(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s);
+// The TMA view of a BF16 lead copy (after build or load; no-op for other formats).
+dade_status make_lead_tmap(dade_index *ix);
 
 // FP32 basis W^T and mean on the device, from the host FP64 copies (build.cu).
 dade_status upload_basis(dade_index *ix, cudaStream_t s);

@@ -18,6 +18,10 @@
 // accepted candidates (radix select, then rank sort).
 #include <algorithm>
 #include <climits>
+#include <cmath>
+#include <mutex>
+
+#include <cuda_bf16.h>
 
 #include "internal.cuh"
 #include "scan_common.cuh"
@@ -56,6 +60,13 @@ struct LmArgs {
     int chunk_tiles;             // tiles of a list per work item (a long list is several items)
     int row_lo, row_hi;          // rows [row_lo, min(len, row_hi)) of every list are scanned; tiles
                                  // of LT rows start at row_lo
+    // tensor-core prefilter (k_lm_tc): BF16 lead copy of the index
+    const float *cent;           // [nc][dp] rotated centroids
+    const float *lead_err;       // [lead_nb][lead_slots] cumulative error norms
+    int64_t *lead_stats;         // [nq] candidates dropped by the prefilter (added to), or null
+    int64_t lead_slots;
+    int lead_nb, dp;
+    float tc_c1, tc_c2;          // error bound of the expanded partial distance (see k_lm_tc)
     float coef[DADE_MAX_DIM / DADE_BLOCK];   // prune iff P > coef[j] r^2 after increment j
 };
 
@@ -64,9 +75,7 @@ __device__ __forceinline__ int lm_end(const LmArgs &a, int len) { return min(len
 
 struct LmSmem {
     static constexpr size_t stage(int gb) { return sizeof(float) * (size_t)gb * LT * 16; }
-    static size_t total_g(int gb) {   // k_lm_g: only the first increment of each query staged
-        return 2 * stage(gb) + sizeof(float) * LG * 16 * gb + sizeof(Surv) * LNW * LT;
-    }
+    static size_t total_g(int gb);   // k_lm_g: only the first increment of each query staged (below)
     static size_t total(int gb) {
         return 2 * stage(gb) + sizeof(float) * LG * 16 * LNB + sizeof(Surv) * LNW * LT;
     }
@@ -344,6 +353,120 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
     }
 }
 
+// Survivors a warp has queued over the tiles of an item, finished in bulk:
+// entries (query slot g << 26 | row of the list, FP32 partial distance over
+// the first increment; with FIRST the first increment is still to be summed
+// from the FP32 rows, in the plain kernels' order, and tested).  One quad per
+// entry, eight entries per step: the later increments are walked in windows
+// of WB blocks (one round trip each, the query's blocks read through L1),
+// testing at every increment boundary against the entry's query's frozen
+// r^2, then the exact compare at d = D; accepted keys go to the query's
+// K-best stage (or its accept region).  Queueing takes the survivors' global
+// round trips out of the per-tile barrier: the warp that queued them drains
+// them when its queue fills or the item ends.
+constexpr int QCAP = 256;         // survivors queued per warp
+constexpr int QROW_BITS = 26;     // rows of a list below 2^26 (the query slot above)
+
+inline size_t LmSmem::total_g(int gb) {
+    return 2 * stage(gb) + sizeof(float) * LG * 16 * gb + sizeof(Surv) * LNW * QCAP;
+}
+
+template <int GB, bool STATS, bool FIRST>
+__device__ void lm_drain(const LmArgs &a, const ListMeta &m, const Surv *sv, int n, const int *s_q, const float *s_r2,
+                         const float *s_thr, const float *qs, bool kbest, KBest &kb) {
+    constexpr int WB = 8;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quad = lane >> 2, lq = lane & 3;
+    const int nb = a.nb, n_inc = a.n_inc;
+    for (int r0 = 0; r0 < n; r0 += 8) {
+        const int sidx = r0 + quad;
+        const bool act = sidx < n;
+        const Surv v = act ? sv[sidx] : Surv{0, 0.f};
+        const int g = v.idx >> QROW_BITS;
+        const int64_t i = v.idx & ((1 << QROW_BITS) - 1);
+        const int q = s_q[g];
+        const float r2 = s_r2[g];
+        const float *row = a.data + m.base + i * 16 + lq * 4;
+        float p = v.p;
+        bool alive = act;
+        if (FIRST) {
+            p = 0.f;
+            if (act) {
+#pragma unroll
+                for (int b = 0; b < GB; ++b)
+                    p += sqd4(*reinterpret_cast<const float4 *>(qs + g * 16 * GB + b * 16 + lq * 4),
+                              __ldg(reinterpret_cast<const float4 *>(row + (int64_t)b * m.np * 16)));
+            }
+            p = quad_sum4(p);
+            if (alive && p > s_thr[g]) {
+                alive = false;
+                if (STATS && lq == 0) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 1]),
+                              (unsigned long long)min(GB * 16, a.d));
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 3]), 1ull);
+                }
+            }
+        }
+        const float *qrow = a.q_rot + (int64_t)q * a.q_stride;
+        const float *trow = a.tail ? a.tail + (m.slot + i) * a.tail_w + lq * 4 - (int64_t)a.tail_nb0 * 16 : nullptr;
+        float part = 0.f;
+        int jj = 1, bend = min(2 * GB, nb);
+        for (int wb = GB; wb < nb; wb += WB) {
+            if (!__any_sync(0xffffffffu, alive)) break;
+            float4 o[WB];
+#pragma unroll
+            for (int u = 0; u < WB; ++u) {
+                const int b = wb + u;
+                const float *src = (trow && b >= a.tail_nb0) ? trow + b * 16 : row + (int64_t)b * m.np * 16;
+                o[u] = (b < nb && alive) ? __ldg(reinterpret_cast<const float4 *>(src)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < WB; ++u) {
+                const int b = wb + u;
+                if (b < nb) {
+                    float qv[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int kk = b * 16 + lq * 4 + t;
+                        qv[t] = kk < a.d ? __ldg(qrow + kk) : 0.f;
+                    }
+                    part += sqd4(make_float4(qv[0], qv[1], qv[2], qv[3]), o[u]);
+                    if (b + 1 == bend) {   // end of increment jj
+                        part = quad_sum4(part);
+                        if (alive) {
+                            p += part;
+                            if (jj < n_inc - 1 && p > a.coef[jj] * r2) {
+                                alive = false;
+                                if (STATS && lq == 0) {
+                                    atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 1]),
+                                              (unsigned long long)min((jj + 1) * GB * 16, a.d));
+                                    atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 3]), 1ull);
+                                }
+                            }
+                        }
+                        part = 0.f;
+                        ++jj;
+                        bend = min(bend + GB, nb);
+                    }
+                }
+            }
+        }
+        const bool take = alive && lq == 0 && p <= r2;
+        if (STATS && alive && lq == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 1]), (unsigned long long)a.d);
+            if (take) atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 2]), 1ull);
+        }
+        const int id = take ? a.ids[m.slot + i] : 0;
+        const unsigned long long key = ((unsigned long long)__float_as_uint(p) << 32) | (unsigned)id;
+        // the warp's queries are slots g = warp + LNW s; stage each slot's accepted keys together
+#pragma unroll
+        for (int sl = 0; sl < QSLOT; ++sl) {
+            const bool ts = take && g == warp + LNW * sl;
+            if (kbest) kb_take(kb, warp, sl, a.k, ts, key);
+            else lm_append(a, ts, s_q[warp + LNW * sl], key);
+        }
+    }
+}
+
 // The list-major kernel for any D (blocks nb > GB): the same items, tiles
 // and phase A as k_lm, with only the first increment of each query staged in
 // shared memory; phase B walks a survivor's later blocks in windows of 8
@@ -352,17 +475,18 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
 // all pruned.
 template <int GB, bool STATS>
 __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
-    constexpr int WB = 8;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_item, s_q[LG];
-    __shared__ float s_r2[LG];
+    __shared__ float s_r2[LG], s_thr[LG];
     __shared__ KBest kb;
     const bool kbest = a.k <= KB_K;   // stage per item (small K), else append directly
     float *stage = reinterpret_cast<float *>(smem);
     float *qs = reinterpret_cast<float *>(smem + 2 * LmSmem::stage(GB));
     Surv *survs = reinterpret_cast<Surv *>(smem + 2 * LmSmem::stage(GB) + sizeof(float) * LG * 16 * GB);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, quad = lane >> 2, lq = lane & 3;
+    Surv *queue = survs + warp * QCAP;   // this warp's survivors, drained when full or at the item's end
+    int qn = 0;                          // entries queued (the same on every lane of the warp)
 
     if (tid == 0) {
         mbar_init(su32(&bars[0]), 1);
@@ -373,7 +497,6 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
     __syncthreads();
     uint32_t used[2] = {0u, 0u};
     const int total = a.item_off[a.nc];
-    const int nb = a.nb, n_inc = a.n_inc;
 
     for (;;) {
         if (tid == 0) s_item = (int)atomicAdd(a.ctr, 1u);
@@ -409,7 +532,9 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
         for (int g = tid; g < ng; g += LNT) {
             const int q = a.lq_items[qb + g];
             s_q[g] = q;
-            s_r2[g] = a.r2src[(int64_t)q * a.k + a.k - 1];
+            const float r2 = a.r2src[(int64_t)q * a.k + a.k - 1];
+            s_r2[g] = r2;
+            s_thr[g] = a.coef[0] * r2;
         }
         for (int e = tid; e < ng * 16 * GB; e += LNT) {
             const int g = e / (16 * GB), kk = e % (16 * GB);
@@ -428,16 +553,18 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
             const int i0 = a.row_lo + t * LT, tn = min(LT, rend - i0);
             const float *st = stage + (size_t)buf * GB * LT * 16;
             for (int g = warp; g < ng; g += LNW) {
+                if (qn + LT > QCAP) {   // room for this query's survivors of the tile
+                    lm_drain<GB, STATS, false>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
+                    qn = 0;
+                    __syncwarp();
+                }
                 const int q = s_q[g];
-                const float r2 = s_r2[g];
                 float4 qa[GB];
 #pragma unroll
                 for (int b = 0; b < GB; ++b)
                     qa[b] = *reinterpret_cast<const float4 *>(qs + g * 16 * GB + b * 16 + lq * 4);
-                Surv *sv = survs + warp * LT;
-                int nsv = 0;
                 unsigned long long st_c = 0, st_d = 0, st_a = 0, st_p = 0;
-                const float c0 = a.coef[0] * r2;
+                const float c0 = s_thr[g];
                 for (int k0 = 0; k0 < tn; k0 += 8) {
                     const int cand = k0 + quad;
                     const bool act = cand < tn;
@@ -451,69 +578,12 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
                     const bool lead = act && lq == 0;
                     const bool keep = lead && !(p > c0);
                     const unsigned mk = __ballot_sync(0xffffffffu, keep);
-                    if (keep) sv[nsv + __popc(mk & ((1u << lane) - 1u))] = Surv{cand, p};
-                    nsv += __popc(mk);
+                    if (keep) queue[qn + __popc(mk & ((1u << lane) - 1u))] = Surv{(g << QROW_BITS) | (i0 + cand), p};
+                    qn += __popc(mk);
                     if (STATS && lead) {
                         ++st_c;
                         if (!keep) { st_d += min(GB * 16, a.d); ++st_p; }
                     }
-                }
-                __syncwarp();
-                const float *qrow = a.q_rot + (int64_t)q * a.q_stride;
-                for (int r0 = 0; r0 < nsv; r0 += 8) {
-                    const int sidx = r0 + quad;
-                    const bool act = sidx < nsv;
-                    const Surv v = act ? sv[sidx] : Surv{0, 0.f};
-                    const int64_t i = i0 + v.idx;
-                    const float *row = a.data + m.base + i * 16 + lq * 4;
-                    const float *trow =
-                        a.tail ? a.tail + (m.slot + i) * a.tail_w + lq * 4 - (int64_t)a.tail_nb0 * 16 : nullptr;
-                    float p = v.p, part = 0.f;
-                    bool alive = act;
-                    int jj = 1, bend = min(2 * GB, nb);
-                    for (int wb = GB; wb < nb; wb += WB) {
-                        if (!__any_sync(0xffffffffu, alive)) break;
-                        float4 o[WB];
-#pragma unroll
-                        for (int u = 0; u < WB; ++u) {
-                            const int b = wb + u;
-                            const float *src = (trow && b >= a.tail_nb0) ? trow + b * 16 : row + (int64_t)b * m.np * 16;
-                            o[u] = (b < nb && alive) ? __ldg(reinterpret_cast<const float4 *>(src))
-                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-                        }
-#pragma unroll
-                        for (int u = 0; u < WB; ++u) {
-                            const int b = wb + u;
-                            if (b < nb) {
-                                float qv[4];
-#pragma unroll
-                                for (int t = 0; t < 4; ++t) {
-                                    const int kk = b * 16 + lq * 4 + t;
-                                    qv[t] = kk < a.d ? __ldg(qrow + kk) : 0.f;
-                                }
-                                part += sqd4(make_float4(qv[0], qv[1], qv[2], qv[3]), o[u]);
-                                if (b + 1 == bend) {   // end of increment jj
-                                    part = quad_sum4(part);
-                                    if (alive) {
-                                        p += part;
-                                        if (jj < n_inc - 1 && p > a.coef[jj] * r2) {
-                                            alive = false;
-                                            if (STATS && lq == 0) { st_d += min((jj + 1) * GB * 16, a.d); ++st_p; }
-                                        }
-                                    }
-                                    part = 0.f;
-                                    ++jj;
-                                    bend = min(bend + GB, nb);
-                                }
-                            }
-                        }
-                    }
-                    const bool take = alive && lq == 0 && p <= r2;
-                    if (STATS && alive && lq == 0) { st_d += a.d; st_a += take; }
-                    const int id = take ? a.ids[m.slot + i] : 0;
-                    const unsigned long long key = ((unsigned long long)__float_as_uint(p) << 32) | (unsigned)id;
-                    if (kbest) kb_take(kb, warp, g / LNW, a.k, take, key);
-                    else lm_append(a, take, q, key);
                 }
                 if (STATS) {
 #pragma unroll
@@ -535,9 +605,328 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
             __syncthreads();
             if (tid == 0 && t + 2 < ntile) issue(t + 2);
         }
+        __syncwarp();
+        lm_drain<GB, STATS, false>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
+        qn = 0;
+        __syncwarp();
         if (kbest)   // the item's K best per query go to the accept buffers
             for (int g = warp; g < ng; g += LNW) kb_flush(a, kb, warp, g / LNW, s_q[g]);
     }
+}
+
+// ---- the first increment on the tensor cores (list-major passes, BF16 lead copy) -------
+// For a tile of LTC candidates of one list and the item's queries (up to LG),
+// the partial distance over the first increment is
+//     X = || (q' - c') - r^ ||^2 = ||q' - c'||^2 + ||r^||^2 - 2 (q' - c') . r^,
+// with r^ the candidate's BF16 residual code (o' - c' rounded, Section 3.2's
+// rotated coordinates relative to the list centroid c').  One thread issues
+// tcgen05.mma kind::f16 (A = the tile's codes, M = 128 candidates; B = the
+// queries' q' - c' split into BF16 hi + lo parts, N = 64; K = 16 dims per
+// 16-dim block, FP32 accumulation in tensor memory).  The codes arrive by TMA
+// in the canonical K-major layout without swizzle: per block b and 8-code
+// half kc, a box of 8 codes x 128 rows (16 B per row, core matrices of 8 rows
+// contiguous).  Every thread then reads its candidate's 32 accumulators
+// (tcgen05.ld) and tests each query with a certified bound: X - E is a lower
+// bound of the exact ||(q' - c') - r^||^2, E = c1 (||q' - c'||^2 + ||r^||^2) +
+// c2 ||q' - c'|| ||r^|| covering the BF16 split of q' - c' (2^-18), the FP32
+// sums and the tensor-core accumulation (host-side constants), and
+// lead_prunes adds the code error norm and the FP32 margins of the exact test
+// (the inequalities of the low-precision prefilter).  A candidate is dropped
+// only when the exact FP32 test would drop it; every other (query, candidate)
+// pair runs the FP32 path of k_lm_g from the first increment (its FP32 rows
+// read from global memory), so results and counters are those of k_lm_g.
+constexpr int LTC = 128;            // candidates per tile: M of the MMA
+constexpr int TCN = 2 * LG;         // N of the MMA: the hi and the lo BF16 parts of the item's queries
+constexpr uint32_t TC_COLS = 64;    // tensor-memory columns of the FP32 accumulator (N = 64)
+
+// Instruction descriptor of kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bits 17-22,
+// M / 16 at bits 24-28.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) |
+                              ((uint32_t)(LTC >> 4) << 24);
+
+struct TcSmem {   // dynamic shared memory of k_lm_tc (1024-byte aligned base)
+    static constexpr size_t a_bytes(int gb) { return (size_t)gb * 2 * LTC * 16; }   // codes of one tile
+    static constexpr size_t b_off(int gb) { return 2 * a_bytes(gb); }                // two tiles in flight
+    static constexpr size_t b_bytes(int gb) { return (size_t)gb * 2 * TCN * 16; }
+    static constexpr size_t qs_off(int gb) { return b_off(gb) + b_bytes(gb); }
+    static constexpr size_t sv_off(int gb) { return qs_off(gb) + sizeof(float) * LG * 16 * gb; }
+    static constexpr size_t mask_off(int gb) { return sv_off(gb) + sizeof(Surv) * LNW * QCAP; }
+    static constexpr size_t total(int gb) { return mask_off(gb) + 2 * sizeof(unsigned) * LTC; }
+};
+
+// Shared-memory matrix descriptor without swizzle: start address / 16 (bits
+// 0-13), K-direction core-matrix stride / 16 (bits 16-29), M/N-direction
+// 8-row group stride / 16 (bits 32-45), the fixed 0b001 at bits 46-48.
+__device__ __forceinline__ uint64_t lt_desc(uint32_t addr, uint32_t kstride, uint32_t mstride) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(kstride >> 4) << 16) | ((uint64_t)(mstride >> 4) << 32) |
+           (1ull << 46);
+}
+__device__ __forceinline__ void lt_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void lt_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void lt_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void lt_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void lt_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// 2D TMA load of one box (x = code within the 16-code row, y = row) into shared memory.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+
+template <int GB, bool STATS>
+__global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[2], mdone;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_item, s_q[LG];
+    __shared__ float s_r2[LG], s_qn[LG], s_qcn[LG], s_thr[LG];
+    __shared__ KBest kb;
+    const bool kbest = a.k <= KB_K;
+    unsigned char *abuf = smem;
+    unsigned char *bsm = smem + TcSmem::b_off(GB);
+    float *qs = reinterpret_cast<float *>(smem + TcSmem::qs_off(GB));
+    Surv *survs = reinterpret_cast<Surv *>(smem + TcSmem::sv_off(GB));
+    unsigned *mask = reinterpret_cast<unsigned *>(smem + TcSmem::mask_off(GB));   // [2][LTC] query halves
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    Surv *queue = survs + warp * QCAP;   // this warp's survivors, drained when full or at the item's end
+    int qn = 0;                          // entries queued (the same on every lane of the warp)
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "r"(TC_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(su32(&full[0]), 1);
+        mbar_init(su32(&full[1]), 1);
+        mbar_init(su32(&mdone), 1);
+        fence_mbar_init();
+    }
+    if (tid < LNW * QSLOT) kb.cnt[tid / QSLOT][tid % QSLOT] = 0;
+    lt_fence_before();
+    __syncthreads();
+    lt_fence_after();
+    const uint32_t tmem = tmem_base;
+    uint32_t used[2] = {0u, 0u}, mph = 0u;
+    int inflight[2] = {0, 0};   // thread 0: TMA loads issued into a buffer and not yet waited on
+    bool mma_pending = false;   // thread 0: MMAs committed and not yet waited on
+    bool failed = false;
+    const int total = a.item_off[a.nc];
+
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(a.ctr, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        int lo = 0, hi = a.nc;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.item_off[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int c = lo;
+        const int ngroups = (a.lq_off[c + 1] - a.lq_off[c] + LG - 1) / LG;
+        const int local = item - a.item_off[c];
+        const int qb = a.lq_off[c] + (local % ngroups) * LG;
+        const int ng = min(LG, a.lq_off[c + 1] - qb);
+        const ListMeta m = a.meta[c];
+        const int rend = lm_end(a, m.len);
+        const int t0 = (local / ngroups) * a.chunk_tiles;
+        const int ntile = min(max(0, (rend - a.row_lo + LTC - 1) / LTC), t0 + a.chunk_tiles);
+        const int64_t crow = m.slot * (int64_t)a.lead_nb;   // code row of block 0, member 0 of list c
+        auto issue = [&](int t) {   // thread 0: the tile's codes, GB blocks x 2 boxes
+            const int buf = t & 1, i0 = a.row_lo + t * LTC;
+            const uint32_t bar = su32(&full[buf]);
+            mbar_expect_tx(bar, (uint32_t)(GB * 2 * LTC * 16));
+            unsigned char *dst = abuf + (size_t)buf * TcSmem::a_bytes(GB);
+            for (int b = 0; b < GB; ++b)
+                for (int kc = 0; kc < 2; ++kc)
+                    tma_load_2d(su32(dst + (size_t)(b * 2 + kc) * LTC * 16), &tmap, kc * 8,
+                                (int)(crow + (int64_t)b * m.np + i0), bar);
+            ++inflight[buf];
+        };
+        if (tid == 0)
+            for (int t = t0; t < t0 + 2 && t < ntile; ++t) issue(t);
+        for (int g = tid; g < LG; g += LNT) {
+            const bool in = g < ng;
+            const int q = in ? a.lq_items[qb + g] : 0;
+            const float r2 = in ? a.r2src[(int64_t)q * a.k + a.k - 1] : 0.f;
+            s_q[g] = q;
+            s_r2[g] = r2;
+            s_thr[g] = a.coef[0] * r2;
+        }
+        // the queries' first increment: FP32 for the exact path, q' - c' split into BF16
+        // hi / lo for the MMA (B rows g and LG + g, K-major core matrices of 8 rows)
+        for (int e = tid; e < LG * 16 * GB; e += LNT) {
+            const int g = e / (16 * GB), kk = e % (16 * GB);
+            const bool in = g < ng && kk < a.d;
+            const float qv = in ? a.q_rot[(int64_t)a.lq_items[qb + g] * a.q_stride + kk] : 0.f;
+            qs[e] = qv;
+            const float v = in ? __fsub_rn(qv, a.cent[(int64_t)c * a.dp + kk]) : 0.f;
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(h)));
+            const int b = kk >> 4, kc = (kk >> 3) & 1, el = kk & 7;
+            reinterpret_cast<unsigned short *>(bsm + ((size_t)(b * 2 + kc) * TCN + g) * 16)[el] = __bfloat16_as_ushort(h);
+            reinterpret_cast<unsigned short *>(bsm + ((size_t)(b * 2 + kc) * TCN + LG + g) * 16)[el] =
+                __bfloat16_as_ushort(l);
+        }
+        __syncthreads();
+        for (int g = warp; g < LG; g += LNW) {   // ||q' - c'||^2 over the increment, from the same FP32 values
+            float acc = 0.f;
+            if (g < ng)
+                for (int kk = lane; kk < 16 * GB; kk += 32) {
+                    const float v = kk < a.d ? __fsub_rn(qs[g * 16 * GB + kk], a.cent[(int64_t)c * a.dp + kk]) : 0.f;
+                    acc = fmaf(v, v, acc);
+                }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) {
+                s_qn[g] = acc;
+                s_qcn[g] = sqrtf(acc);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B, written by threads, read by the MMA
+        __syncthreads();
+
+        for (int t = t0; t < ntile; ++t) {
+            const int buf = t & 1, i0 = a.row_lo + t * LTC, tn = min(LTC, rend - i0);
+            const unsigned char *ab = abuf + (size_t)buf * TcSmem::a_bytes(GB);
+            if (!wait_block(su32(&full[buf]), used[buf] & 1u)) {
+                failed = true;
+                break;
+            }
+            ++used[buf];
+            if (tid == 0) {
+                --inflight[buf];
+                lt_fence_after();
+#pragma unroll
+                for (int b = 0; b < GB; ++b)
+                    lt_mma(tmem, lt_desc(su32(ab) + (uint32_t)(b * 2 * LTC * 16), LTC * 16, 128),
+                           lt_desc(su32(bsm) + (uint32_t)(b * 2 * TCN * 16), TCN * 16, 128), b > 0 ? 1u : 0u);
+                lt_commit(su32(&mdone));
+                mma_pending = true;
+            }
+            if (!wait_block(su32(&mdone), mph)) {
+                failed = true;
+                break;
+            }
+            if (tid == 0) mma_pending = false;
+            mph ^= 1u;
+            lt_fence_after();
+            {   // epilogue: candidate mrow against the queries of half qh
+                const int mrow = 32 * (warp & 3) + lane, qh = warp >> 2;
+                uint32_t hi[16], lo2[16];
+                const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+                lt_ld16(tb + (uint32_t)(qh * 16), hi);
+                lt_ld16(tb + (uint32_t)(LG + qh * 16), lo2);
+                unsigned bits = 0u;
+                if (mrow < tn) {
+                    float rn = 0.f;   // ||r^||^2 of the candidate's codes (exact squares, FP32 sum)
+#pragma unroll
+                    for (int b = 0; b < GB; ++b)
+#pragma unroll
+                        for (int kc = 0; kc < 2; ++kc) {
+                            const uint4 u = *reinterpret_cast<const uint4 *>(ab + ((size_t)(b * 2 + kc) * LTC + mrow) * 16);
+                            const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                rn = fmaf(bf16_lo(w4[h]), bf16_lo(w4[h]), rn);
+                                rn = fmaf(bf16_hi(w4[h]), bf16_hi(w4[h]), rn);
+                            }
+                        }
+                    const float rcn = sqrtf(rn);
+                    const float e = __ldg(a.lead_err + (int64_t)(GB - 1) * a.lead_slots + m.slot + i0 + mrow);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int g = qh * 16 + j;
+                        if (g < ng) {
+                            const float dot = __uint_as_float(hi[j]) + __uint_as_float(lo2[j]);
+                            const float sq = s_qn[g] + rn;
+                            const float pt = fmaf(-2.f, dot, sq);
+                            const float err = fmaf(a.tc_c1, sq, a.tc_c2 * (s_qcn[g] * rcn));
+                            const bool drop = lead_prunes(fmaxf(pt - err, 0.f), e, s_qcn[g], s_thr[g]);
+                            bits |= (unsigned)(!drop) << j;
+                        }
+                    }
+                }
+                mask[qh * LTC + mrow] = bits;
+            }
+            lt_fence_before();
+            __syncthreads();
+            // the pairs the prefilter kept go to their warp's queue (the FP32 path finishes them in bulk)
+            for (int g = warp; g < ng; g += LNW) {
+                if (qn + LTC > QCAP) {
+                    lm_drain<GB, STATS, true>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
+                    qn = 0;
+                    __syncwarp();
+                }
+                const int qh = g >> 4, jb = g & 15;
+                int kept = 0;
+                for (int m0 = 0; m0 < tn; m0 += 32) {
+                    const int mm = m0 + lane;
+                    const bool keep = mm < tn && ((mask[qh * LTC + mm] >> jb) & 1u);
+                    const unsigned mk = __ballot_sync(0xffffffffu, keep);
+                    if (keep) queue[qn + __popc(mk & ((1u << lane) - 1u))] = Surv{(g << QROW_BITS) | (i0 + mm), 0.f};
+                    qn += __popc(mk);
+                    kept += __popc(mk);
+                }
+                const unsigned long long dropped = (unsigned long long)(tn - kept);
+                if (lane == 0) {
+                    const int q = s_q[g];
+                    if (STATS) {   // the dropped candidates count as pruned at the first test
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 0]),
+                                  (unsigned long long)tn);
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 1]),
+                                  dropped * (unsigned long long)min(GB * 16, a.d));
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 3]), dropped);
+                    }
+                    if (a.lead_stats && dropped > 0)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.lead_stats[q]), dropped);
+                }
+                __syncwarp();
+            }
+            __syncthreads();   // codes of buffer `buf` and the masks are free
+            if (tid == 0 && t + 2 < ntile) issue(t + 2);
+        }
+        if (failed) break;
+        __syncwarp();
+        lm_drain<GB, STATS, true>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
+        qn = 0;
+        __syncwarp();
+        if (kbest)   // the item's K best per query go to the accept buffers
+            for (int g = warp; g < ng; g += LNW) kb_flush(a, kb, warp, g / LNW, s_q[g]);
+    }
+    if (failed && tid == 0) {   // let the copies and MMAs in flight finish (bounded) before leaving
+        atomicExch(a.err, (int)DADE_ETIMEOUT);
+        for (int b = 0; b < 2; ++b)
+            if (inflight[b] > 0) wait_bounded(su32(&full[b]), used[b] & 1u, 10000000ull);
+        if (mma_pending) wait_bounded(su32(&mdone), mph, 10000000ull);
+    }
+    lt_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS) : "memory");
 }
 
 // ---- work list -------------------------------------------------------------------
@@ -557,12 +946,13 @@ __global__ void k_lm_count(const int32_t *__restrict__ probe, int64_t nq, int np
 // both arrays get a trailing 0 for the scans.  off is written only when
 // `with_off` (the query groups do not change between the rounds of a pass).
 __global__ void k_lm_items(const int *__restrict__ cnt, const ListMeta *__restrict__ meta, int nc, int chunk_tiles,
-                           int row_lo, int row_hi, int with_off, int *__restrict__ off, int *__restrict__ items) {
+                           int tile_rows, int row_lo, int row_hi, int with_off, int *__restrict__ off,
+                           int *__restrict__ items) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= nc; c += gridDim.x * blockDim.x) {
         const int v = c < nc ? cnt[c] : 0;
         if (with_off) off[c] = v;
         const int rows = c < nc ? min(meta[c].len, row_hi) - row_lo : 0;
-        const int tiles = rows > 0 ? (rows + LT - 1) / LT : 0;
+        const int tiles = rows > 0 ? (rows + tile_rows - 1) / tile_rows : 0;
         items[c] = (v > 0 && tiles > 0) ? ((v + LG - 1) / LG) * ((tiles + chunk_tiles - 1) / chunk_tiles) : 0;
     }
 }
@@ -705,6 +1095,24 @@ dade_status launch_lm_g(const LmArgs &a, cudaStream_t s) {
     return launch_check("k_lm_g");
 }
 
+template <int GB, bool STATS>
+dade_status launch_lm_tc(const LmArgs &a, const CUtensorMap &tmap, cudaStream_t s) {
+    const size_t smem = TcSmem::total(GB);
+    int blocks = 1;
+    DADE_TRY(resident_blocks((const void *)k_lm_tc<GB, STATS>, LNT, smem, &blocks));
+    k_lm_tc<GB, STATS><<<blocks, LNT, smem, s>>>(a, tmap);
+    return launch_check("k_lm_tc");
+}
+
+template <bool STATS>
+dade_status launch_lm_tc_gb(const LmArgs &a, const CUtensorMap &tmap, int gb, cudaStream_t s) {
+    switch (gb) {
+    case 1: return launch_lm_tc<1, STATS>(a, tmap, s);
+    case 2: return launch_lm_tc<2, STATS>(a, tmap, s);
+    default: return launch_lm_tc<4, STATS>(a, tmap, s);
+    }
+}
+
 template <bool STATS>
 dade_status launch_lm_gen(const LmArgs &a, int gb, cudaStream_t s) {
     switch (gb) {
@@ -726,6 +1134,36 @@ dade_status launch_lm_gb(const LmArgs &a, int gb, cudaStream_t s) {
 }
 
 } // namespace
+
+// The tensor-core prefilter runs a list-major DADE pass when the search asks
+// for the lead prefilter, the index holds a BF16 copy covering the first
+// increment (1, 2 or 4 blocks), and the increment is not the last one.
+bool tc_applies(const dade_index *ix, const ScanParams &p, int gb) {
+    return p.use_lead && p.mode == DADE_MODE_DADE && ix->lead_tmap_ok && ix->lead_format == DADE_LEAD_BF16 &&
+           (gb == 1 || gb == 2 || gb == 4) && gb <= ix->lead_nb && ix->nb > gb && ix->nb >= LNB;
+}
+
+// Error bound of the expanded partial distance of k_lm_tc over K = 16 gb dims,
+// E = c1 (||a||^2 + ||r^||^2) + c2 ||a|| ||r^|| with a = q' - c' (FP32) and r^
+// the BF16 codes, u = 2^-24:
+//   - the FP32 sums ||a||^2 (lane-strided FMAs and an xor tree) and ||r^||^2
+//     (exact squares, one FMA chain of K terms) and s = ||a||^2 + ||r^||^2:
+//     relative (K + 8) u together, with the rounding of 2 a.r^ - s: c1;
+//   - a = hi + lo + d, |d| <= 2^-18 |a| (two BF16 roundings); the products of
+//     BF16 values are exact, and the tensor core accumulates K of them per
+//     column in FP32: allowed 4 x 2u per addition (truncating adds with a
+//     factor 4 to spare), then hi + lo adds one rounding:
+//     |dot - a.r^| <= (2^-18 + (K + 2) 2^-21) sum |a_k||r^_k| <= ... ||a|| ||r^||,
+//     twice that for the -2 a.r^ term: c2.
+// Both are rounded up and carry a further 2^-20 for their own FP32 evaluation.
+void tc_constants(int gb, float *c1, float *c2) {
+    const double u = std::ldexp(1.0, -24), K = 16.0 * gb;
+    const double cs = (K + 8.0) * u * 1.01 + 3.0 * u;
+    const double cd = std::ldexp(1.0, -18) + (K + 2.0) * std::ldexp(1.0, -21);
+    const double grow = 1.0 + std::ldexp(1.0, -20);
+    *c1 = std::nextafter((float)(cs * grow), INFINITY);
+    *c2 = std::nextafter((float)(2.0 * cd * (1.0 + std::ldexp(1.0, -8) + std::ldexp(1.0, -9)) * grow), INFINITY);
+}
 
 // One list-major round: the lists at probe positions [c0, c1) of every query,
 // each candidate tested against the query's r^2 = dists[q][k - 1] as it is
@@ -762,9 +1200,11 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
         k_lm_count<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, cnt);
         DADE_TRY(launch_check("k_lm_count"));
     }
-    const int chunk_tiles = std::max(1, (p.list_chunk > 0 ? p.list_chunk : 4096) / LT);
-    k_lm_items<<<grid_of(nc + 1, 256), 256, 0, s>>>(cnt, ix->meta.as<ListMeta>(), nc, chunk_tiles, row_lo, row_hi,
-                                                    lists ? 1 : 0, off, items);
+    const bool tc = prune && tc_applies(ix, p, gb);
+    const int tile_rows = tc ? LTC : LT;
+    const int chunk_tiles = std::max(1, (p.list_chunk > 0 ? p.list_chunk : 4096) / tile_rows);
+    k_lm_items<<<grid_of(nc + 1, 256), 256, 0, s>>>(cnt, ix->meta.as<ListMeta>(), nc, chunk_tiles, tile_rows, row_lo,
+                                                    row_hi, lists ? 1 : 0, off, items);
     DADE_TRY(launch_check("k_lm_items"));
     if (lists) DADE_TRY(exclusive_scan_int(off, nc + 1, s));
     DADE_TRY(exclusive_scan_int(items, nc + 1, s));
@@ -804,7 +1244,17 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     a.nb = ix->nb;
     a.n_inc = n_inc;
     for (int j = 0; j < DADE_MAX_DIM / DADE_BLOCK; ++j) a.coef[j] = (prune && j < n_inc - 1) ? p.coef[j] : INFINITY;
-    if (ix->nb == LNB)
+    if (tc) {
+        a.cent = ix->cent.as<float>();
+        a.lead_err = ix->lead_err.as<float>();
+        a.lead_stats = p.lead_stats;
+        a.lead_slots = ix->slots;
+        a.lead_nb = ix->lead_nb;
+        a.dp = ix->dp;
+        tc_constants(gb, &a.tc_c1, &a.tc_c2);
+        DADE_TRY(p.stats ? launch_lm_tc_gb<true>(a, ix->lead_tmap, gb, s)
+                         : launch_lm_tc_gb<false>(a, ix->lead_tmap, gb, s));
+    } else if (ix->nb == LNB)
         DADE_TRY(p.stats ? launch_lm_gb<true>(a, gb, s) : launch_lm_gb<false>(a, gb, s));
     else
         DADE_TRY(p.stats ? launch_lm_gen<true>(a, gb, s) : launch_lm_gen<false>(a, gb, s));
@@ -903,6 +1353,51 @@ dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, c
     return lm_round(ix, nq, p, S, np, gb, !fd, s);
 }
 
+// TMA view of the BF16 lead copy: rows of 16 codes (32 B), row slot_c lead_nb
+// + b np_c + i for block b of member i of list c; boxes of 8 codes x 128 rows
+// land in shared memory as 128 contiguous 16-byte rows (core matrices of the
+// MMA's K-major layout without swizzle).
+dade_status make_lead_tmap(dade_index *ix) {
+    ix->lead_tmap_ok = false;
+    if (ix->lead_format != DADE_LEAD_BF16 || !ix->lead.p) return DADE_OK;
+    typedef CUresult (*encode_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static encode_fn encode = nullptr;
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!encode) {
+            void *fn = nullptr;
+            cudaDriverEntryPointQueryResult q{};
+            DADE_TRY_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+            if (q != cudaDriverEntryPointSuccess || !fn) {
+                set_error("cuTensorMapEncodeTiled is not available from the driver");
+                return DADE_ECUDA;
+            }
+            encode = reinterpret_cast<encode_fn>(fn);
+        }
+    }
+    const uint64_t rows = (uint64_t)ix->slots * (uint64_t)ix->lead_nb;
+    if (rows == 0 || rows >= (1ull << 31)) {
+        set_error("the BF16 lead copy has too many rows for the tensor-core prefilter's TMA view");
+        return DADE_EUNSUPPORTED;
+    }
+    const cuuint64_t dims[2] = {16, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {32};   // bytes between rows
+    const cuuint32_t box[2] = {8, (cuuint32_t)LTC};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&ix->lead_tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ix->lead.p, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed for the BF16 lead copy (CUresult " + std::to_string((int)r) + ")");
+        return DADE_ECUDA;
+    }
+    ix->lead_tmap_ok = true;
+    return DADE_OK;
+}
+
 // The row-rounds schedule (DADE_SCHED_ROUNDS): round e holds rows
 // [R_e, R_{e+1}) of every probed list, R_0 = 0, R_1 = p.tile, R_{e+1} = 2 R_e,
 // and every candidate of the round is tested against the query's r after the
@@ -925,7 +1420,7 @@ dade_status scan_rounds(const dade_index *ix, int64_t nq, const ScanParams &p, c
     if (p.lead_stats) DADE_TRY_CUDA(cudaMemsetAsync(p.lead_stats, 0, sizeof(int64_t) * (size_t)nq, s));
     const int64_t longest = std::max(ix->max_list, 1);
     const int64_t r1 = std::max(p.tile, 1);
-    if (lm_ok && !p.seed_split && !p.use_lead) {
+    if (lm_ok && !p.seed_split && (!p.use_lead || tc_applies(ix, p, gb))) {
         bool first = true;
         for (int64_t lo = 0, hi = r1; lo < longest; lo = hi, hi *= 2) {
             DADE_TRY(lm_round(ix, nq, p, 0, np, fd ? LNB : gb, !fd, s, (int)lo, (int)std::min<int64_t>(hi, INT_MAX),
