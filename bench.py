@@ -51,11 +51,11 @@ RECALL_TARGET = 0.95
 # The oracle arm's operating point per workload: the DADE point the autotuner picks there
 # (nprobe, alpha, delta_d, schedule); the oracle runs its own index at that point.
 REFERENCE_POINTS = {
-    "c1_gauss_10k_d128": {"nprobe": 8, "alpha": 0.05, "delta_d": 32, "schedule": 0, "seed_lists": 0},
-    "c2_mix_1m_d128": {"nprobe": 20, "alpha": 0.8, "delta_d": 64, "schedule": 2, "seed_lists": 2},
-    "c3_mix_1m_d960": {"nprobe": 24, "alpha": 0.8, "delta_d": 64, "schedule": 2, "seed_lists": 3},
-    "c4_zipf_10m_d768": {"nprobe": 8, "alpha": 0.8, "delta_d": 32, "schedule": 0, "seed_lists": 0},
-    "c5_mix_5m_d256": {"nprobe": 32, "alpha": 0.8, "delta_d": 64, "schedule": 2, "seed_lists": 4},
+    "c1_gauss_10k_d128": {"nprobe": 8, "alpha": 0.05, "delta_d": 32, "schedule": 0, "seed_lists": 0, "tile": 128},
+    "c2_mix_1m_d128": {"nprobe": 20, "alpha": 0.8, "delta_d": 64, "schedule": 2, "seed_lists": 3, "tile": 256},
+    "c3_mix_1m_d960": {"nprobe": 24, "alpha": 0.8, "delta_d": 64, "schedule": 2, "seed_lists": 3, "tile": 128},
+    "c4_zipf_10m_d768": {"nprobe": 8, "alpha": 0.8, "delta_d": 32, "schedule": 3, "seed_lists": 0, "tile": 64},
+    "c5_mix_5m_d256": {"nprobe": 32, "alpha": 0.8, "delta_d": 64, "schedule": 2, "seed_lists": 4, "tile": 128},
 }
 
 
@@ -896,8 +896,8 @@ def measure_workload(args, wname, rank, world, dist, headline):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(base, queries, w, nc, point, K, args.cpu_seconds if headline else args.cpu_seconds / 2,
-                           assign=given.get("assign"))
+        cpu = cpu_baseline(base, queries, labels, w, nc, point, K,
+                           args.cpu_seconds if headline else args.cpu_seconds / 2)
 
     out = {
         "value": round(value, 1), "ms_per_step": round(ms_per_step, 4), "steps": steps, "warmup": warm,
@@ -992,56 +992,92 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------- oracle ----
-def oracle_index(base, w, nc, kmeans_iters=1, assign=None):
-    """The oracle's own index over the same base: PCA, rotation, k-means lists
-    (fewer Lloyd iterations than the GPU index: the oracle's FP64 assignment
-    passes are the expensive part of its setup) or the given lists, and the
-    eps sample."""
+def oracle_index(base, queries, labels, w, nc, nprobe, n_sample):
+    """The oracle's index for timing on a query sample, built by the recipe of
+    the GPU index where the host can afford it: the generating components as
+    lists (Zipf workloads, as on the GPU), or the oracle's own seeded Lloyd
+    k-means with the GPU's 10 iterations (up to 1M x 128); for the larger
+    k-means workloads the seeded component lists (each mixture component's
+    members dealt to lists of their own), since an FP64 k-means over millions
+    of vectors and thousands of lists would take the host many minutes.  PCA
+    over all rows up to 1M x 256, else over the first 500,000 (independent
+    draws).  Only the rows the sample queries can reach are rotated."""
     import oracle
     o = oracle.get()
     t0 = time.time()
-    pairs = synth.eps_pairs(base.shape[0], 100000)
-    if assign is not None:
-        idx = oracle.Index(base, n_clusters=nc, assign=assign, pairs=pairs, oracle=o)
+    n = base.shape[0]
+    pairs = synth.eps_pairs(n, 100000 if w.d <= 256 else 20000)
+    pca_rows = None if n * w.d <= 256 * 1_000_000 else 500_000
+    if w.lists_are_components:
+        assign, recipe = labels, "lists = the generating components, as the GPU index"
+    elif n * w.d <= 128 * 1_000_000:
+        idx = oracle.Index(base, init=synth.kmeans_init(n, nc), iters=w.kmeans_iters, pairs=pairs, oracle=o)
+        idx.Qr_all = idx.rotate(queries[:n_sample])
+        log(f"[bench] oracle index ({o.threads()} threads) in {time.time() - t0:.1f}s")
+        return idx, f"the oracle's own lists: seeded Lloyd k-means, {w.kmeans_iters} iterations (the GPU index's recipe)"
     else:
-        idx = oracle.Index(base, init=synth.kmeans_init(base.shape[0], nc), iters=kmeans_iters, pairs=pairs,
-                           oracle=o)
+        assign, recipe = synth.component_lists(labels, nc), "lists = mixture components dealt to lists (seeded)"
+    idx = oracle.SampledIndex(base, assign, nc, pairs, queries[:n_sample], nprobe, oracle=o, pca_rows=pca_rows)
+    idx.Qr_all = idx.Qr
     log(f"[bench] oracle index ({o.threads()} threads) in {time.time() - t0:.1f}s")
-    return idx
+    return idx, recipe + ("" if pca_rows is None else f"; PCA over the first {pca_rows:,} vectors")
 
 
-def oracle_qps(idx, queries, point, K, cpu_seconds, steps=1):
+def oracle_search(idx, m, point, K):
+    """The oracle's search of the first m sample queries at a GPU operating point (same schedule)."""
+    import oracle
+    sched = point.get("schedule", 0)
+    kw = dict(schedule=oracle.ROW_ROUNDS, tile=point["tile"]) if sched == 3 else \
+        dict(tile=min(point.get("tile", 128), 256), seed=point.get("seed_lists", 0) if sched == 2 else 0)
+    eps = idx.eps(np.float32(point["alpha"]), point["delta_d"])
+    if isinstance(idx, oracle.SampledIndex):
+        return idx.o.search(idx.Xr, idx.assign, idx.cent, idx.lam, idx.Qr_all[:m], K, point["nprobe"],
+                            point["delta_d"], eps, **kw)
+    return idx.o.search(idx.Xr, idx.assign, idx.cent, idx.lam, idx.Qr_all[:m], K, point["nprobe"], point["delta_d"],
+                        eps, **kw)
+
+
+def oracle_qps(idx, point, K, cpu_seconds, steps=1):
     """Time the oracle's search (probe + DCO scan) on a bounded query sample."""
+    m0 = min(16, idx.Qr_all.shape[0])
     t0 = time.time()
-    seed = point.get("seed_lists", 0) if point.get("schedule", 0) == 2 else 0
-    idx.search(queries[:64], K, point["nprobe"], point["delta_d"], np.float32(point["alpha"]), seed=seed)
-    per_q = max(1e-6, (time.time() - t0) / 64)
-    m = int(min(queries.shape[0], max(64, cpu_seconds / per_q / max(1, steps))))
+    oracle_search(idx, m0, point, K)
+    per_q = max(1e-6, (time.time() - t0) / m0)
+    m = int(min(idx.Qr_all.shape[0], max(m0, cpu_seconds / per_q / max(1, steps))))
     times = []
     for _ in range(steps):
         t0 = time.time()
-        idx.search(queries[:m], K, point["nprobe"], point["delta_d"], np.float32(point["alpha"]), seed=seed)
+        oracle_search(idx, m, point, K)
         times.append(time.time() - t0)
     return m, times
 
 
-def cpu_baseline(base, queries, w, nc, point, K, cpu_seconds, assign=None):
+def cpu_point(point):
+    return {"nprobe": point["nprobe"], "alpha": point.get("alpha", 0.1), "delta_d": point.get("delta_d", 32),
+            "schedule": point.get("schedule", 0), "seed_lists": point.get("seed_lists", 0),
+            "tile": point.get("tile", 128)}
+
+
+def sched_text(pt):
+    return {0: "TILE(128)", 2: f"seeded, first {pt['seed_lists']} lists in TILE(128)",
+            3: f"row rounds from {pt['tile']} rows"}.get(pt["schedule"], "TILE(128)")
+
+
+def cpu_baseline(base, queries, labels, w, nc, point, K, cpu_seconds):
     try:
-        idx = oracle_index(base, w, nc, assign=assign)
-        pt = {"nprobe": point["nprobe"], "alpha": point.get("alpha", 0.1), "delta_d": point.get("delta_d", 32),
-              "schedule": point.get("schedule", 0), "seed_lists": point.get("seed_lists", 0)}
-        m, times = oracle_qps(idx, queries, pt, K, cpu_seconds)
-        sched = f"seeded, first {pt['seed_lists']} lists in TILE(128)" if pt["schedule"] == 2 else "TILE(128)"
-        # the paper's own methodology is one core: time a short sample on one thread too
+        pt = cpu_point(point)
+        n_sample = 2000 if base.shape[0] * w.d <= 256 * 1_000_000 else 256
+        idx, recipe = oracle_index(base, queries, labels, w, nc, pt["nprobe"], min(queries.shape[0], n_sample))
+        m, times = oracle_qps(idx, pt, K, cpu_seconds)
         cores = idx.o.threads()
-        idx.o.set_threads(1)
-        m1, t1 = oracle_qps(idx, queries, pt, K, min(5.0, cpu_seconds / 3))
+        idx.o.set_threads(1)   # the paper's own methodology is one core: a short sample on one thread too
+        m1, t1 = oracle_qps(idx, pt, K, min(5.0, cpu_seconds / 3))
         idx.o.set_threads(cores)
         return {"value": round(m / times[0], 1), "unit": UNIT, "cores": cores, "kind": "oracle",
                 "single_core": {"value": round(m1 / t1[0], 1), "unit": UNIT, "cores": 1, "sample": f"first {m1} queries"},
                 "sample": f"first {m} of {queries.shape[0]} queries, oracle FP64 DADE-IVF search (probe + DCO scan, "
-                          f"{sched} schedule) at nprobe={pt['nprobe']} alpha={pt['alpha']} delta_d={pt['delta_d']}; "
-                          f"oracle lists from 1 Lloyd iteration"}
+                          f"{sched_text(pt)} schedule) at nprobe={pt['nprobe']} alpha={pt['alpha']} "
+                          f"delta_d={pt['delta_d']}; {recipe}"}
     except Exception as e:  # noqa: BLE001 - the baseline must not sink the GPU line
         return {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
 
@@ -1055,10 +1091,11 @@ def run_reference(args):
     nq = args.nq or w.nq
     nc = w.n_clusters if n == w.n else max(16, n // 244)
     base, queries, labels = synth.make(w, n=n, nq=nq)
-    idx = oracle_index(base, w, nc, assign=labels if w.lists_are_components and n == w.n else None)
     pt = dict(REFERENCE_POINTS.get(args.workload, REFERENCE_POINTS["c2_mix_1m_d128"]))
+    idx, recipe = oracle_index(base, queries, labels, w, nc, pt["nprobe"],
+                               min(nq, 2000 if n * w.d <= 256 * 1_000_000 else 256))
     budget = min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup))
-    m, times = oracle_qps(idx, queries, pt, w.k, budget * (args.steps + args.warmup), args.steps + args.warmup)
+    m, times = oracle_qps(idx, pt, w.k, budget * (args.steps + args.warmup), args.steps + args.warmup)
     times = times[args.warmup:]
     qps = m / statistics.mean(times)
     out = {"impl": "reference", "metric": METRIC, "value": round(qps, 1), "unit": UNIT, "n_gpus": args.gpus,
@@ -1066,10 +1103,10 @@ def run_reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "n": n, "d": w.d, "nq": nq, "n_clusters": nc, "k": w.k,
                       "nprobe": pt["nprobe"], "alpha": pt["alpha"], "delta_d": pt["delta_d"],
-                      "parallelism": "host cores"},
+                      "schedule": SCHED_NAMES[pt["schedule"]], "parallelism": "host cores"},
            "cpu_baseline": {"value": round(qps, 1), "unit": UNIT, "cores": idx.o.threads(), "kind": "oracle",
-                            "sample": f"first {m} of {nq} queries per step, FP64 oracle DADE-IVF search; "
-                                      f"oracle lists from 1 Lloyd iteration"},
+                            "sample": f"first {m} of {nq} queries per step, FP64 oracle DADE-IVF search "
+                                      f"({sched_text(pt)} schedule); {recipe}"},
            "e2e": {"value": round(qps, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

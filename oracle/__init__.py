@@ -324,12 +324,15 @@ class SampledIndex:
     the full base."""
 
     def __init__(self, base, assign, n_clusters, pairs, queries, nprobe, oracle: Oracle | None = None,
-                 eps_step=16):
+                 eps_step=16, pca_rows=None):
         o = self.o = oracle or get()
         X = np.ascontiguousarray(base, np.float32)
         n, D = X.shape
         self.D, self.nc = D, int(n_clusters)
-        self.mu, self.W, self.lam = o.pca(X)
+        # PCA over all N objects, or (pca_rows) over the first rows only: the rows are
+        # independent draws, so they form a random sample of the data (a timing setup
+        # that keeps the FP64 covariance affordable at 10M x 768)
+        self.mu, self.W, self.lam = o.pca(X if pca_rows is None or pca_rows >= n else X[:pca_rows])
         assign = np.ascontiguousarray(assign, np.int32)
         counts = np.bincount(assign, minlength=self.nc)
         if (counts == 0).any():

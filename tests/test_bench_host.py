@@ -13,7 +13,7 @@ def test_point_options_round_trip():
     pt = bench.parse_point("nprobe=20,alpha=0.8,delta_d=64,tile=128,threads=128,schedule=2,seed_lists=2,flags=12", dade)
     kw = bench.point_kw(pt)
     assert kw == {"mode": 0, "tile": 128, "spec": 8, "threads": 128, "schedule": 2, "flags": 12, "seed_lists": 2,
-                  "stage_dims": 0}
+                  "stage_dims": 0, "list_chunk": 0}
     assert pt["alpha"] == 0.8 and pt["nprobe"] == 20
 
 
@@ -25,6 +25,10 @@ def test_kernel_names_follow_the_schedule():
     c4 = {"mode": 0, "threads": 128, "delta_d": 32, "schedule": 0, "flags": 4}
     assert bench.scan_kernel_name(c4, 768) == "k_scan<DADE>"
     assert bench.scan_kernel_name({"mode": 1, "threads": 256}, 128) == "k_fd_fast<256, 8>"
+    rounds = {"mode": 0, "threads": 128, "delta_d": 32, "schedule": 3, "flags": 4}
+    assert bench.scan_kernel_name(rounds, 768).startswith("k_lm_g<2> (row rounds")
+    assert bench.scan_kernel_name(dict(rounds, flags=6), 768).startswith("k_lm_tc<2>")
+    assert "split" in bench.scan_kernel_name(dict(rounds, flags=20), 768)
 
 
 def test_traffic_records_match_only_their_point_and_sources():
@@ -49,4 +53,5 @@ def test_alu_bound_where_lists_are_shared():
     assert not bench.list_major_point(dict(c2, flags=28), 960)          # split: query-major
     assert not bench.list_major_point(dict(c2, schedule=0), 128)        # tile schedule
     assert not bench.list_major_point(c2, 64)                           # D <= 112: split fallback
-    assert bench.SMS * bench.FP32_LANES * 2 * bench.SM_MAX_MHZ / 1e6 > 80.0
+    assert bench.list_major_point(dict(c2, schedule=3, delta_d=32), 768)   # row rounds
+    assert not bench.list_major_point(dict(c2, schedule=3, flags=20), 768)
