@@ -320,7 +320,7 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -335,7 +335,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
@@ -669,6 +669,8 @@ def measure_workload(args, wname, rank, world, dist, headline):
     dds, alphas = (16, 32, 64), (0.1, 0.3, 0.5, 0.8, 0.9, 0.95, 0.98)
     if fd_best is not None and fd_best[0] > 50.0:   # a large workload: a narrower sweep
         dds, alphas = (32, 64), (0.5, 0.8, 0.9, 0.95)
+    elif not headline:                              # an extra key: a shorter sweep
+        dds, alphas = (32, 64), (0.5, 0.8, 0.95, 0.98)
     tried = []
     for dd in dds:
         for alpha in alphas:
@@ -786,6 +788,36 @@ def measure_workload(args, wname, rank, world, dist, headline):
                                                       "max_rel_dist_error": dist_error(torch, xb, q, ids, dists),
                                                       "ms_per_scan": round(r[0], 4),
                                                       "same_ids_as_timed_step": bool(torch.equal(ids, ids_timed))}
+
+    # FP8-e4m3 leading blocks (the uneven-list workload's configured precision): an index
+    # with the FP8 copy, the prefilter at the chosen point (query-major rounds on the tile kernel)
+    if headline and w.comp_zipf > 0 and lf != dade.LEAD_FP8:
+        try:
+            ix8 = dade.Index(xb, nc, kmeans_iters=w.kmeans_iters, seed=synth.SEED_KMEANS, lead_format=dade.LEAD_FP8,
+                             lead_dims=64, tail_from=tf, **given)
+            p8 = dict(point, flags=(point["flags"] & ~dade.FLAG_LEAD) | dade.FLAG_LEAD)
+            pr8 = probe_for(p8["nprobe"])
+            ls8 = torch.zeros(nq, dtype=torch.int64, device="cuda")
+            ix8.scan(qr, pr8, K, p8["alpha"], p8["delta_d"], ids, dists, lead_stats=ls8, stream=sh, **point_kw(p8))
+            ix8.sync(stream=sh)
+            rc8, err8 = recall_at_k(torch, xb, q, ids, gt_kth, K), dist_error(torch, xb, q, ids, dists)
+            same8 = bool(torch.equal(ids, ids_timed))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                ix8.scan(qr, pr8, K, p8["alpha"], p8["delta_d"], ids, dists, stream=sh, **point_kw(p8))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            precision["fp8-e4m3 lead blocks"] = {"recall": round(rc8, 5), "max_rel_dist_error": err8,
+                                                 "ms_per_scan": round(e0.elapsed_time(e1) / 3, 4),
+                                                 "same_ids_as_timed_step": same8,
+                                                 "dropped_by_prefilter": int(ls8.sum().item()),
+                                                 "kernel": scan_kernel_name(p8, w.d)}
+            ix8.close()
+            del ix8
+            torch.cuda.empty_cache()
+        except Exception as e:  # noqa: BLE001 - reported, not fatal
+            log(f"[bench] FP8 precision point failed: {e}")
 
     # ---- FD baseline timed the same way (same step structure) ------------------------
     fd_pt = fd_best[2] if fd_best else {"mode": dade.MODE_FD, "nprobe": n0, "tile": 128, "threads": 128,
@@ -1011,10 +1043,18 @@ def oracle_index(base, queries, labels, w, nc, nprobe, n_sample):
     if w.lists_are_components:
         assign, recipe = labels, "lists = the generating components, as the GPU index"
     elif n * w.d <= 128 * 1_000_000:
-        idx = oracle.Index(base, init=synth.kmeans_init(n, nc), iters=w.kmeans_iters, pairs=pairs, oracle=o)
+        # the GPU index's recipe (seeded Lloyd k-means, its iterations, nearest-centroid lists),
+        # with the centroids fitted on a seeded sample of 200,000 vectors to bound the FP64 setup
+        idx = oracle.Index(base, n_clusters=nc, assign=np.zeros(n, np.int32), pairs=pairs, oracle=o)
+        fit = np.sort(np.random.default_rng(synth.SEED_KMEANS).permutation(n)[:200_000])
+        init = synth.kmeans_init(fit.size, nc)
+        cent, _, _, _ = o.kmeans(idx.Xr[fit], init, w.kmeans_iters)
+        idx.assign, _ = o.assign(idx.Xr, cent)
+        idx.cent = o.list_means(idx.Xr, idx.assign, nc)
         idx.Qr_all = idx.rotate(queries[:n_sample])
         log(f"[bench] oracle index ({o.threads()} threads) in {time.time() - t0:.1f}s")
-        return idx, f"the oracle's own lists: seeded Lloyd k-means, {w.kmeans_iters} iterations (the GPU index's recipe)"
+        return idx, (f"the oracle's own lists: seeded Lloyd k-means ({w.kmeans_iters} iterations, as the GPU index) "
+                     f"fitted on 200,000 sampled vectors, every vector in its nearest list")
     else:
         assign, recipe = synth.component_lists(labels, nc), "lists = mixture components dealt to lists (seeded)"
     idx = oracle.SampledIndex(base, assign, nc, pairs, queries[:n_sample], nprobe, oracle=o, pca_rows=pca_rows)
@@ -1066,7 +1106,7 @@ def sched_text(pt):
 def cpu_baseline(base, queries, labels, w, nc, point, K, cpu_seconds):
     try:
         pt = cpu_point(point)
-        n_sample = 2000 if base.shape[0] * w.d <= 256 * 1_000_000 else 256
+        n_sample = 2000 if base.shape[0] * w.d <= 256 * 1_000_000 else 64
         idx, recipe = oracle_index(base, queries, labels, w, nc, pt["nprobe"], min(queries.shape[0], n_sample))
         m, times = oracle_qps(idx, pt, K, cpu_seconds)
         cores = idx.o.threads()
@@ -1093,7 +1133,7 @@ def run_reference(args):
     base, queries, labels = synth.make(w, n=n, nq=nq)
     pt = dict(REFERENCE_POINTS.get(args.workload, REFERENCE_POINTS["c2_mix_1m_d128"]))
     idx, recipe = oracle_index(base, queries, labels, w, nc, pt["nprobe"],
-                               min(nq, 2000 if n * w.d <= 256 * 1_000_000 else 256))
+                               min(nq, 2000 if n * w.d <= 256 * 1_000_000 else 64))
     budget = min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup))
     m, times = oracle_qps(idx, pt, w.k, budget * (args.steps + args.warmup), args.steps + args.warmup)
     times = times[args.warmup:]
