@@ -395,8 +395,9 @@ def scan_kernel_name(point, d):
     if point.get("schedule", 0) == 3:
         if point.get("flags", 0) & 16 or nb < 8:
             return f"k_scan<DADE{', lead' if lead else ''}> (row rounds split over CTAs) + k_lm_merge"
-        if lead:
-            return f"k_lm_tc<{min(point['delta_d'] // 16, 8)}> (row rounds, tensor-core prefilter) + k_lm_merge"
+        if point.get("flags", 0) & 32:
+            return (f"k_lm_g<{min(point['delta_d'] // 16, 8)}> (first round) + k_lm_tc<{min(point['delta_d'] // 16, 8)}> "
+                    f"(row rounds, tensor-core prefilter) + k_lm_merge")
         return f"k_lm_g<{min(point['delta_d'] // 16, 8)}> (row rounds, list-major) + k_lm_merge"
     if point.get("schedule", 0) == 2 and point.get("flags", 0) & 16:
         return (f"k_scan<{point['threads']}, DADE{', lead' if lead else ''}> (first {point.get('seed_lists')} "
@@ -522,17 +523,17 @@ def dade_variants(dade, w, lf):
     list_major = nb >= 8
     lead = (dade.FLAG_LEAD,) if lf else ()
     v = []
+    tc = (dade.FLAG_TC_PREFILTER,) if list_major else ()
     if w.comp_zipf > 0:   # very uneven lists: doubling row windows, split over many thread blocks
-        v += [(dade.SCHED_ROUNDS, r1, 128, fl, 0, 0, ch) for r1 in (32, 64) for ch in (1024, 4096)
-              for fl in (0,) + (lead if lf == dade.LEAD_BF16 else ())]
+        v += [(dade.SCHED_ROUNDS, r1, 128, fl, 0, 0, ch) for r1 in (16, 32, 64) for ch in (512, 1024)
+              for fl in (0,) + tc]
         v += [(dade.SCHED_TILE, 128, 128, 0, 0, 0, 0)]
         return v
     v += [(dade.SCHED_TILE, tile, nt, fl, 0, 0, 0) for tile in (128, 256) for fl in (0,) + lead for nt in (128, 256)]
     if list_major:
         v += [(dade.SCHED_SEEDED, tile, 128, fl, seed, 0, 0) for seed in (2, 3, 4) for tile in (128, 256)
-              for fl in (0,) + (lead if lf == dade.LEAD_BF16 else ())]
-        v += [(dade.SCHED_ROUNDS, r1, 128, fl, 0, 0, 0) for r1 in (16, 32, 64)
-              for fl in (0,) + (lead if lf == dade.LEAD_BF16 else ())]
+              for fl in (0,) + tc]
+        v += [(dade.SCHED_ROUNDS, r1, 128, fl, 0, 0, 0) for r1 in (16, 32, 64) for fl in (0,) + tc]
     v += [(dade.SCHED_SEEDED, 128, nt, dade.FLAG_SEED_SPLIT, seed, 0, 0) for seed in (2, 3) for nt in (128, 256)]
     if w.d > 128:
         v += [(dade.SCHED_TILE, 128, 256, 0, 0, sd, 0) for sd in (64, 128)]
@@ -540,6 +541,8 @@ def dade_variants(dade, w, lf):
 
 
 def precision_of(point, lf, dade):
+    if point.get("flags", 0) & dade.FLAG_TC_PREFILTER:
+        return "fp32 (first increment bounded on the tensor cores, TF32)"
     if not point.get("flags", 0) & dade.FLAG_LEAD:
         return "fp32"
     return {dade.LEAD_BF16: "bf16 lead blocks", dade.LEAD_FP8: "fp8-e4m3 lead blocks"}.get(lf, "fp32")
@@ -781,6 +784,12 @@ def measure_workload(args, wname, rank, world, dist, headline):
     precision = {precision_of(point, lf, dade): {"recall": round(rc_timed, 5), "max_rel_dist_error": err_timed,
                                                  "ms_per_scan": round(statistics.mean(scan_ms), 4)}}
     alt = dict(point, flags=point["flags"] ^ dade.FLAG_LEAD) if lf else None
+    if point.get("flags", 0) & dade.FLAG_TC_PREFILTER:   # the same point on the CUDA cores alone
+        r = measure(dict(point, flags=point["flags"] & ~dade.FLAG_TC_PREFILTER), reps=4)
+        if r is not None:
+            precision["fp32"] = {"recall": round(r[1], 5), "max_rel_dist_error": dist_error(torch, xb, q, ids, dists),
+                                 "ms_per_scan": round(r[0], 4),
+                                 "same_ids_as_timed_step": bool(torch.equal(ids, ids_timed))}
     if alt is not None and (not alt["flags"] & dade.FLAG_LEAD or min(point["delta_d"], w.d) <= ld):
         r = measure(alt, reps=4)
         if r is not None:

@@ -129,6 +129,14 @@ enum {
     DADE_FLAG_ROW_TAIL = 8,        /* a candidate that survives the first increment reads its dims from
                                       tail_from on from the index's row-major copy: one contiguous row
                                       instead of one 64-byte piece per 16-dim slab.  Same results. */
+    DADE_FLAG_TC_PREFILTER = 32,   /* list-major passes (DADE_SCHED_SEEDED, DADE_SCHED_ROUNDS; D > 112,
+                                      delta_d of 16, 32 or 64 dims): the first increment's inner products
+                                      q'.o' on the tensor cores (the FP32 rows read as TF32, the query
+                                      split into two TF32 parts), and a certified lower bound of each
+                                      partial distance; a candidate is dropped only where the bound
+                                      exceeds the threshold by more than the FP32 path's rounding, every
+                                      other one runs the FP32 path.  Same results; opts->lead_stats
+                                      counts the candidates the bound dropped. */
     DADE_FLAG_SEED_SPLIT = 16      /* DADE_SCHED_SEEDED: every pass with r frozen (the lists after the
                                       seeds; with whole-list tiles, each seed epoch too) runs query-major
                                       on the tile kernel, each query's lists split into parts over
@@ -223,7 +231,7 @@ typedef struct {
     int32_t schedule;          /* dade_schedule (default DADE_SCHED_TILE) */
     int32_t flags;             /* DADE_FLAG_* bits */
     int64_t *lead_stats;       /* device, optional [nq]: candidates dropped by the low-precision prefilter
-                                  (needs DADE_FLAG_LEAD) */
+                                  (DADE_FLAG_LEAD) or by the tensor-core prefilter (DADE_FLAG_TC_PREFILTER) */
     int32_t seed_lists;        /* DADE_SCHED_SEEDED: lists scanned before r is frozen (0: 2; >= nprobe:
                                   the tile schedule) */
     int32_t estimator;         /* dade_estimator (default DADE_ESTIMATOR_DADE) */

@@ -202,7 +202,7 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
                         opts->stage_dims <= DADE_MAX_DIM),
                    "stage_dims must be 0 or a multiple of delta_d up to 1024");
     DADE_CHECK_ARG(!opts || (opts->flags & ~(DADE_FLAG_GENERIC_KERNEL | DADE_FLAG_LEAD | DADE_FLAG_QUERY_ORDER |
-                                             DADE_FLAG_ROW_TAIL | DADE_FLAG_SEED_SPLIT)) == 0,
+                                             DADE_FLAG_ROW_TAIL | DADE_FLAG_SEED_SPLIT | DADE_FLAG_TC_PREFILTER)) == 0,
                    "unknown flag bits");
     DADE_CHECK_ARG(!opts || !(opts->flags & DADE_FLAG_ROW_TAIL) || ix->tail_nb0 > 0,
                    "DADE_FLAG_ROW_TAIL on an index built without tail_from");
@@ -214,7 +214,8 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
         DADE_CHECK_ARG(std::min(delta_d, ix->dp) <= ix->lead_dims,
                        "DADE_FLAG_LEAD needs min(delta_d, D rounded up to 16) <= the index's lead_dims");
     }
-    DADE_CHECK_ARG(!opts || !opts->lead_stats || (opts->flags & DADE_FLAG_LEAD), "lead_stats needs DADE_FLAG_LEAD");
+    DADE_CHECK_ARG(!opts || !opts->lead_stats || (opts->flags & (DADE_FLAG_LEAD | DADE_FLAG_TC_PREFILTER)),
+                   "lead_stats needs DADE_FLAG_LEAD or DADE_FLAG_TC_PREFILTER");
     return DADE_OK;
 }
 
@@ -270,6 +271,7 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.use_lead = opts ? (opts->flags & DADE_FLAG_LEAD) != 0 : 0;
     p.use_tail = opts ? (opts->flags & DADE_FLAG_ROW_TAIL) != 0 : 0;
     p.seed_split = opts ? (opts->flags & DADE_FLAG_SEED_SPLIT) != 0 : 0;
+    p.use_tc = opts ? (opts->flags & DADE_FLAG_TC_PREFILTER) != 0 : 0;
     p.lead_stats = opts ? opts->lead_stats : nullptr;
     p.delta_d = delta_d;
     const bool ads = opts && opts->estimator == DADE_ESTIMATOR_ADSAMPLING;
@@ -283,6 +285,9 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
         DADE_TRY(dade::order_queries(ix, probe_dev, nq, nprobe, ws(ix).order.as<int32_t>(), s));
         p.order = ws(ix).order.as<int32_t>();
     }
+    // counts of the tensor-core prefilter are added up by its passes; without the
+    // low-precision prefilter (which writes them) they start from zero
+    if (p.lead_stats && !p.use_lead) DADE_TRY_CUDA(cudaMemsetAsync(p.lead_stats, 0, sizeof(int64_t) * (size_t)nq, s));
     DADE_TRY(dade::scan(ix, nq, p, s));
     if (ids_host)
         DADE_TRY_CUDA(cudaMemcpyAsync(ids, ids_d, sizeof(int64_t) * (size_t)nq * k, cudaMemcpyDeviceToHost, s));

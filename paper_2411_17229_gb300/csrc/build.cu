@@ -608,8 +608,8 @@ dade_status build_index(const float *base, int64_t n, int32_t d, const dade_buil
                                                          ix->lead_scale.as<float>(), ix->lead.as<unsigned char>(),
                                                          ix->lead_err.as<float>(), ix->slots);
             DADE_TRY(launch_check("k_pack_lead"));
-            DADE_TRY(make_lead_tmap(ix));
         }
+        DADE_TRY(make_data_tmap(ix));
         DADE_TRY_CUDA(cudaStreamSynchronize(s));
     }
 

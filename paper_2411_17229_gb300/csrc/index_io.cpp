@@ -231,7 +231,6 @@ dade_status load_index(const char *path, dade_index *ix) {
         DADE_TRY(get_dev(f, ix->lead, lead_code_bytes(s), "lead codes"));
         DADE_TRY(get_dev(f, ix->lead_err, sizeof(float) * (size_t)s.slots * s.lead_nb, "lead error norms"));
         DADE_TRY(get_dev(f, ix->lead_scale, sizeof(float) * (size_t)s.nc * s.lead_nb, "lead scales"));
-        DADE_TRY(make_lead_tmap(ix));
     }
     if (s.tail_nb0 > 0) {
         ix->tail_nb0 = s.tail_nb0;
@@ -240,6 +239,7 @@ dade_status load_index(const char *path, dade_index *ix) {
     }
     DADE_TRY(upload_basis(ix, 0));
     DADE_TRY(prepare_tensor_operands(ix, 0));
+    DADE_TRY(make_data_tmap(ix));
     DADE_TRY(ix->meta.alloc(sizeof(ListMeta) * (size_t)s.nc));
     DADE_TRY_CUDA(cudaMemcpy(ix->meta.p, ix->lists.data(), sizeof(ListMeta) * (size_t)s.nc, cudaMemcpyHostToDevice));
     DADE_TRY(ix->errflag.alloc(sizeof(int32_t) * 4));

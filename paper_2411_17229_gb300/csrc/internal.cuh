@@ -114,10 +114,10 @@ struct dade_index {
     dade::DevBuf lead;      // codes; list c at slot_c * lead_nb * 16 * ES bytes, block b at + b * np * 16 * ES
     dade::DevBuf lead_scale;// float [nc][lead_nb] (FP8 only)
     dade::DevBuf lead_err;  // float [lead_nb][slots]: error norm over blocks 0..b (rounded up)
-    // TMA view of the BF16 codes as rows of 16 codes (32 B): row slot_c lead_nb + b np_c + i holds
-    // block b of member i of list c; boxes of 8 codes x 128 rows (the tensor-core prefilter, lm.cu)
-    CUtensorMap lead_tmap{};
-    bool lead_tmap_ok = false;
+    // TMA view of the packed FP32 data as rows of 16 floats (64 B): row base_c / 16 + b np_c + i holds
+    // block b of member i of list c; boxes of 4 floats x 128 rows (the tensor-core prefilter, lm.cu)
+    CUtensorMap data_tmap{};
+    bool data_tmap_ok = false;
     // row-major copy of dims [16 tail_nb0, dp) of every slot: tail[(slot) * tail_w + k - 16 tail_nb0]
     int32_t tail_nb0 = 0, tail_w = 0;
     dade::DevBuf tail;
@@ -178,6 +178,7 @@ struct ScanParams {
     // split mode of the tile kernel (parts > 0; see ScanArgs)
     int32_t parts, c0;
     int32_t row_lo, row_hi;  // split passes: rows [row_lo, min(len, row_hi)) of every list (row_hi 0: all)
+    int32_t use_tc;          // list-major passes: the first increment's tensor-core prefilter
     const float *r2src;
     unsigned long long *acc;
     int *acnt;
@@ -192,8 +193,8 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
 dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s);
 // DADE_SCHED_ROUNDS (lm.cu).
 dade_status scan_rounds(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s);
-// The TMA view of a BF16 lead copy (after build or load; no-op for other formats).
-dade_status make_lead_tmap(dade_index *ix);
+// The TMA view of the packed FP32 data (after build or load).
+dade_status make_data_tmap(dade_index *ix);
 
 // FP32 basis W^T and mean on the device, from the host FP64 copies (build.cu).
 dade_status upload_basis(dade_index *ix, cudaStream_t s);

@@ -60,12 +60,8 @@ struct LmArgs {
     int chunk_tiles;             // tiles of a list per work item (a long list is several items)
     int row_lo, row_hi;          // rows [row_lo, min(len, row_hi)) of every list are scanned; tiles
                                  // of LT rows start at row_lo
-    // tensor-core prefilter (k_lm_tc): BF16 lead copy of the index
-    const float *cent;           // [nc][dp] rotated centroids
-    const float *lead_err;       // [lead_nb][lead_slots] cumulative error norms
+    // tensor-core prefilter (k_lm_tc)
     int64_t *lead_stats;         // [nq] candidates dropped by the prefilter (added to), or null
-    int64_t lead_slots;
-    int lead_nb, dp;
     float tc_c1, tc_c2;          // error bound of the expanded partial distance (see k_lm_tc)
     float coef[DADE_MAX_DIM / DADE_BLOCK];   // prune iff P > coef[j] r^2 after increment j
 };
@@ -614,41 +610,42 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
     }
 }
 
-// ---- the first increment on the tensor cores (list-major passes, BF16 lead copy) -------
+// ---- the first increment on the tensor cores (list-major passes) -----------------------
 // For a tile of LTC candidates of one list and the item's queries (up to LG),
-// the partial distance over the first increment is
-//     X = || (q' - c') - r^ ||^2 = ||q' - c'||^2 + ||r^||^2 - 2 (q' - c') . r^,
-// with r^ the candidate's BF16 residual code (o' - c' rounded, Section 3.2's
-// rotated coordinates relative to the list centroid c').  One thread issues
-// tcgen05.mma kind::f16 (A = the tile's codes, M = 128 candidates; B = the
-// queries' q' - c' split into BF16 hi + lo parts, N = 64; K = 16 dims per
-// 16-dim block, FP32 accumulation in tensor memory).  The codes arrive by TMA
-// in the canonical K-major layout without swizzle: per block b and 8-code
-// half kc, a box of 8 codes x 128 rows (16 B per row, core matrices of 8 rows
-// contiguous).  Every thread then reads its candidate's 32 accumulators
-// (tcgen05.ld) and tests each query with a certified bound: X - E is a lower
-// bound of the exact ||(q' - c') - r^||^2, E = c1 (||q' - c'||^2 + ||r^||^2) +
-// c2 ||q' - c'|| ||r^|| covering the BF16 split of q' - c' (2^-18), the FP32
-// sums and the tensor-core accumulation (host-side constants), and
-// lead_prunes adds the code error norm and the FP32 margins of the exact test
-// (the inequalities of the low-precision prefilter).  A candidate is dropped
-// only when the exact FP32 test would drop it; every other (query, candidate)
-// pair runs the FP32 path of k_lm_g from the first increment (its FP32 rows
-// read from global memory), so results and counters are those of k_lm_g.
+// the partial distance over the first increment is expanded as
+//     X = ||q'||^2 + ||o'||^2 - 2 q'.o'   (FP32 rows q', o' of the index).
+// The tile's FP32 rows arrive by TMA in the tensor cores' canonical K-major
+// layout without swizzle: per 16-dim block b and 4-float chunk kc, a box of
+// 4 floats x 128 rows (16 B per row; core matrices of 8 rows contiguous).  One
+// thread issues tcgen05.mma kind::tf32 (A = the tile, M = 128 candidates, read
+// by the tensor core as TF32; B = the queries split into TF32 hi + lo parts,
+// N = 64; K = 8 dims per instruction; FP32 accumulation in tensor memory),
+// two accumulators in turn, so that the MMA of the next tile runs while the
+// threads read this one's (tcgen05.ld).  Every (query, candidate) pair is then
+// tested with a certified bound: X - E is a lower bound of the exact partial
+// distance, E = c1 (||q'||^2 + ||o'||^2) + c2 ||q'|| ||o'|| covering the TF32
+// reading of the rows (2^-10), the split of the queries (2^-22), the FP32 sums
+// and the tensor-core accumulation (host-side constants); a pair is dropped
+// only when X - E exceeds the FP32 threshold by 2^-15 relative, more than the
+// rounding of the FP32 path's own partial sum, so the FP32 test would drop it
+// too.  Every other pair runs the FP32 path from the staged rows (the same
+// float4 per lane and the same order as the plain kernels) and its
+// survivors are queued for the later increments: results and counters are
+// those of the FP32 list-major path.
 constexpr int LTC = 128;            // candidates per tile: M of the MMA
-constexpr int TCN = 2 * LG;         // N of the MMA: the hi and the lo BF16 parts of the item's queries
-constexpr uint32_t TC_COLS = 64;    // tensor-memory columns of the FP32 accumulator (N = 64)
+constexpr int TCN = 2 * LG;         // N of the MMA: the hi and the lo TF32 parts of the item's queries
+constexpr uint32_t TC_COLS = 128;   // tensor-memory columns: two FP32 accumulators of N = 64
 
-// Instruction descriptor of kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bits 17-22,
+// Instruction descriptor of kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
+// (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N / 8 at bits 17-22,
 // M / 16 at bits 24-28.
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TCN >> 3) << 17) |
+constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TCN >> 3) << 17) |
                               ((uint32_t)(LTC >> 4) << 24);
 
 struct TcSmem {   // dynamic shared memory of k_lm_tc (1024-byte aligned base)
-    static constexpr size_t a_bytes(int gb) { return (size_t)gb * 2 * LTC * 16; }   // codes of one tile
+    static constexpr size_t a_bytes(int gb) { return (size_t)gb * 4 * LTC * 16; }   // FP32 rows of one tile
     static constexpr size_t b_off(int gb) { return 2 * a_bytes(gb); }                // two tiles in flight
-    static constexpr size_t b_bytes(int gb) { return (size_t)gb * 2 * TCN * 16; }
+    static constexpr size_t b_bytes(int gb) { return (size_t)gb * 4 * TCN * 16; }
     static constexpr size_t qs_off(int gb) { return b_off(gb) + b_bytes(gb); }
     static constexpr size_t sv_off(int gb) { return qs_off(gb) + sizeof(float) * LG * 16 * gb; }
     static constexpr size_t mask_off(int gb) { return sv_off(gb) + sizeof(Surv) * LNW * QCAP; }
@@ -667,7 +664,7 @@ __device__ __forceinline__ void lt_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void lt_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
         : "memory");
 }
@@ -683,23 +680,26 @@ __device__ __forceinline__ void lt_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-// 2D TMA load of one box (x = code within the 16-code row, y = row) into shared memory.
+// 2D TMA load of one box (x = float within the 16-float row, y = row) into shared memory.
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
             "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
-__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
-__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+__device__ __forceinline__ uint32_t tf32_rna_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
 
 template <int GB, bool STATS>
 __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_constant__ CUtensorMap tmap) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[2], mdone;
+    __shared__ __align__(8) uint64_t full[2], mdone[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_item, s_q[LG];
-    __shared__ float s_r2[LG], s_qn[LG], s_qcn[LG], s_thr[LG];
+    __shared__ float s_r2[LG], s_qn[LG], s_qcn[LG], s_thr[LG], s_thr2[LG];
     __shared__ KBest kb;
     const bool kbest = a.k <= KB_K;
     unsigned char *abuf = smem;
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
     float *qs = reinterpret_cast<float *>(smem + TcSmem::qs_off(GB));
     Surv *survs = reinterpret_cast<Surv *>(smem + TcSmem::sv_off(GB));
     unsigned *mask = reinterpret_cast<unsigned *>(smem + TcSmem::mask_off(GB));   // [2][LTC] query halves
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, quad = lane >> 2, lq = lane & 3;
     Surv *queue = survs + warp * QCAP;   // this warp's survivors, drained when full or at the item's end
     int qn = 0;                          // entries queued (the same on every lane of the warp)
 
@@ -718,9 +718,10 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(su32(&full[0]), 1);
-        mbar_init(su32(&full[1]), 1);
-        mbar_init(su32(&mdone), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(su32(&full[b]), 1);
+            mbar_init(su32(&mdone[b]), 1);
+        }
         fence_mbar_init();
     }
     if (tid < LNW * QSLOT) kb.cnt[tid / QSLOT][tid % QSLOT] = 0;
@@ -728,9 +729,9 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
     __syncthreads();
     lt_fence_after();
     const uint32_t tmem = tmem_base;
-    uint32_t used[2] = {0u, 0u}, mph = 0u;
-    int inflight[2] = {0, 0};   // thread 0: TMA loads issued into a buffer and not yet waited on
-    bool mma_pending = false;   // thread 0: MMAs committed and not yet waited on
+    uint32_t used[2] = {0u, 0u}, mph[2] = {0u, 0u};   // completed waits per copy buffer / accumulator
+    int inflight[2] = {0, 0};                         // thread 0: copies issued and not waited on
+    bool mpend[2] = {false, false};                   // thread 0: MMAs committed and not waited on
     bool failed = false;
     const int total = a.item_off[a.nc];
 
@@ -742,7 +743,7 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         int lo = 0, hi = a.nc;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (a.item_off[mid] <= item) lo = mid;
+            if (__ldg(a.item_off + mid) <= item) lo = mid;
             else hi = mid;
         }
         const int c = lo;
@@ -754,17 +755,36 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         const int rend = lm_end(a, m.len);
         const int t0 = (local / ngroups) * a.chunk_tiles;
         const int ntile = min(max(0, (rend - a.row_lo + LTC - 1) / LTC), t0 + a.chunk_tiles);
-        const int64_t crow = m.slot * (int64_t)a.lead_nb;   // code row of block 0, member 0 of list c
-        auto issue = [&](int t) {   // thread 0: the tile's codes, GB blocks x 2 boxes
+        const int64_t brow = m.base >> 4;   // row (16 floats) of block 0, member 0 of list c
+        auto issue = [&](int t) {   // thread 0: the tile's FP32 rows, GB blocks x 4 boxes
             const int buf = t & 1, i0 = a.row_lo + t * LTC;
             const uint32_t bar = su32(&full[buf]);
-            mbar_expect_tx(bar, (uint32_t)(GB * 2 * LTC * 16));
+            mbar_expect_tx(bar, (uint32_t)(GB * 4 * LTC * 16));
             unsigned char *dst = abuf + (size_t)buf * TcSmem::a_bytes(GB);
             for (int b = 0; b < GB; ++b)
-                for (int kc = 0; kc < 2; ++kc)
-                    tma_load_2d(su32(dst + (size_t)(b * 2 + kc) * LTC * 16), &tmap, kc * 8,
-                                (int)(crow + (int64_t)b * m.np + i0), bar);
+                for (int kc = 0; kc < 4; ++kc)
+                    tma_load_2d(su32(dst + (size_t)(b * 4 + kc) * LTC * 16), &tmap, kc * 4,
+                                (int)(brow + (int64_t)b * m.np + i0), bar);
             ++inflight[buf];
+        };
+        auto mma = [&](int t) -> bool {   // thread 0: wait for tile t's rows, then its MMAs
+            const int buf = t & 1;
+            if (!wait_bounded(su32(&full[buf]), used[buf] & 1u, WAIT_NS)) return false;
+            ++used[buf];
+            --inflight[buf];
+            lt_fence_after();
+            const uint32_t ab = su32(abuf + (size_t)buf * TcSmem::a_bytes(GB)), bb = su32(bsm);
+            const uint32_t d = tmem + (uint32_t)(buf * TCN);
+#pragma unroll
+            for (int b = 0; b < GB; ++b)
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2)
+                    lt_mma(d, lt_desc(ab + (uint32_t)((b * 4 + 2 * s2) * LTC * 16), LTC * 16, 128),
+                           lt_desc(bb + (uint32_t)((b * 4 + 2 * s2) * TCN * 16), TCN * 16, 128),
+                           (b > 0 || s2 > 0) ? 1u : 0u);
+            lt_commit(su32(&mdone[buf]));
+            mpend[buf] = true;
+            return true;
         };
         if (tid == 0)
             for (int t = t0; t < t0 + 2 && t < ntile; ++t) issue(t);
@@ -772,33 +792,29 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
             const bool in = g < ng;
             const int q = in ? a.lq_items[qb + g] : 0;
             const float r2 = in ? a.r2src[(int64_t)q * a.k + a.k - 1] : 0.f;
+            const float thr = a.coef[0] * r2;
             s_q[g] = q;
             s_r2[g] = r2;
-            s_thr[g] = a.coef[0] * r2;
+            s_thr[g] = thr;
+            s_thr2[g] = thr * (1.f + 0x1p-15f);
         }
-        // the queries' first increment: FP32 for the exact path, q' - c' split into BF16
-        // hi / lo for the MMA (B rows g and LG + g, K-major core matrices of 8 rows)
+        // the queries' first increment: FP32 for the FP32 path, TF32 hi / lo for the MMA
+        // (B rows g and LG + g, K-major core matrices of 8 rows x 4 floats)
         for (int e = tid; e < LG * 16 * GB; e += LNT) {
             const int g = e / (16 * GB), kk = e % (16 * GB);
             const bool in = g < ng && kk < a.d;
             const float qv = in ? a.q_rot[(int64_t)a.lq_items[qb + g] * a.q_stride + kk] : 0.f;
             qs[e] = qv;
-            const float v = in ? __fsub_rn(qv, a.cent[(int64_t)c * a.dp + kk]) : 0.f;
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(h)));
-            const int b = kk >> 4, kc = (kk >> 3) & 1, el = kk & 7;
-            reinterpret_cast<unsigned short *>(bsm + ((size_t)(b * 2 + kc) * TCN + g) * 16)[el] = __bfloat16_as_ushort(h);
-            reinterpret_cast<unsigned short *>(bsm + ((size_t)(b * 2 + kc) * TCN + LG + g) * 16)[el] =
-                __bfloat16_as_ushort(l);
+            const uint32_t h = tf32_rna_bits(qv);
+            const uint32_t l = tf32_rna_bits(__fsub_rn(qv, __uint_as_float(h)));
+            const int b = kk >> 4, kc = (kk >> 2) & 3, el = kk & 3;
+            reinterpret_cast<uint32_t *>(bsm + ((size_t)(b * 4 + kc) * TCN + g) * 16)[el] = h;
+            reinterpret_cast<uint32_t *>(bsm + ((size_t)(b * 4 + kc) * TCN + LG + g) * 16)[el] = l;
         }
         __syncthreads();
-        for (int g = warp; g < LG; g += LNW) {   // ||q' - c'||^2 over the increment, from the same FP32 values
+        for (int g = warp; g < LG; g += LNW) {   // ||q'||^2 over the increment
             float acc = 0.f;
-            if (g < ng)
-                for (int kk = lane; kk < 16 * GB; kk += 32) {
-                    const float v = kk < a.d ? __fsub_rn(qs[g * 16 * GB + kk], a.cent[(int64_t)c * a.dp + kk]) : 0.f;
-                    acc = fmaf(v, v, acc);
-                }
+            for (int kk = lane; kk < 16 * GB; kk += 32) acc = fmaf(qs[g * 16 * GB + kk], qs[g * 16 * GB + kk], acc);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
             if (lane == 0) {
@@ -808,110 +824,122 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B, written by threads, read by the MMA
         __syncthreads();
+        if (tid == 0 && t0 < ntile && !mma(t0)) failed = true;
 
         for (int t = t0; t < ntile; ++t) {
             const int buf = t & 1, i0 = a.row_lo + t * LTC, tn = min(LTC, rend - i0);
-            const unsigned char *ab = abuf + (size_t)buf * TcSmem::a_bytes(GB);
-            if (!wait_block(su32(&full[buf]), used[buf] & 1u)) {
+            const float *af = reinterpret_cast<const float *>(abuf + (size_t)buf * TcSmem::a_bytes(GB));
+            if (tid == 0 && !failed && t + 1 < ntile && !mma(t + 1)) failed = true;   // overlaps this tile's reads
+            bool ok = !failed;
+            if (tid == 0 && ok) {
+                ok = wait_bounded(su32(&mdone[buf]), mph[buf] & 1u, WAIT_NS);
+                if (ok) {
+                    ++mph[buf];
+                    mpend[buf] = false;
+                }
+            }
+            if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
             }
-            ++used[buf];
-            if (tid == 0) {
-                --inflight[buf];
-                lt_fence_after();
-#pragma unroll
-                for (int b = 0; b < GB; ++b)
-                    lt_mma(tmem, lt_desc(su32(ab) + (uint32_t)(b * 2 * LTC * 16), LTC * 16, 128),
-                           lt_desc(su32(bsm) + (uint32_t)(b * 2 * TCN * 16), TCN * 16, 128), b > 0 ? 1u : 0u);
-                lt_commit(su32(&mdone));
-                mma_pending = true;
-            }
-            if (!wait_block(su32(&mdone), mph)) {
-                failed = true;
-                break;
-            }
-            if (tid == 0) mma_pending = false;
-            mph ^= 1u;
             lt_fence_after();
-            {   // epilogue: candidate mrow against the queries of half qh
+            {   // candidate mrow against the queries of half qh
                 const int mrow = 32 * (warp & 3) + lane, qh = warp >> 2;
                 uint32_t hi[16], lo2[16];
-                const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+                const uint32_t tb = tmem + (uint32_t)(buf * TCN) + ((uint32_t)(32 * (warp & 3)) << 16);
                 lt_ld16(tb + (uint32_t)(qh * 16), hi);
                 lt_ld16(tb + (uint32_t)(LG + qh * 16), lo2);
                 unsigned bits = 0u;
                 if (mrow < tn) {
-                    float rn = 0.f;   // ||r^||^2 of the candidate's codes (exact squares, FP32 sum)
+                    float on = 0.f;   // ||o'||^2 over the increment, from the staged rows
 #pragma unroll
                     for (int b = 0; b < GB; ++b)
 #pragma unroll
-                        for (int kc = 0; kc < 2; ++kc) {
-                            const uint4 u = *reinterpret_cast<const uint4 *>(ab + ((size_t)(b * 2 + kc) * LTC + mrow) * 16);
-                            const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                            for (int h = 0; h < 4; ++h) {
-                                rn = fmaf(bf16_lo(w4[h]), bf16_lo(w4[h]), rn);
-                                rn = fmaf(bf16_hi(w4[h]), bf16_hi(w4[h]), rn);
-                            }
+                        for (int kc = 0; kc < 4; ++kc) {
+                            const float4 v = *reinterpret_cast<const float4 *>(af + ((size_t)(b * 4 + kc) * LTC + mrow) * 4);
+                            on = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, on))));
                         }
-                    const float rcn = sqrtf(rn);
-                    const float e = __ldg(a.lead_err + (int64_t)(GB - 1) * a.lead_slots + m.slot + i0 + mrow);
+                    const float ocn = sqrtf(on);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int g = qh * 16 + j;
-                        if (g < ng) {
-                            const float dot = __uint_as_float(hi[j]) + __uint_as_float(lo2[j]);
-                            const float sq = s_qn[g] + rn;
-                            const float pt = fmaf(-2.f, dot, sq);
-                            const float err = fmaf(a.tc_c1, sq, a.tc_c2 * (s_qcn[g] * rcn));
-                            const bool drop = lead_prunes(fmaxf(pt - err, 0.f), e, s_qcn[g], s_thr[g]);
-                            bits |= (unsigned)(!drop) << j;
-                        }
+                        const float dot = __uint_as_float(hi[j]) + __uint_as_float(lo2[j]);
+                        const float sq = s_qn[g] + on;
+                        const float pt = fmaf(-2.f, dot, sq);
+                        const float err = fmaf(a.tc_c1, sq, a.tc_c2 * (s_qcn[g] * ocn));
+                        const bool drop = pt - err > s_thr2[g];
+                        bits |= (unsigned)(g < ng && !drop) << j;
                     }
                 }
                 mask[qh * LTC + mrow] = bits;
             }
             lt_fence_before();
             __syncthreads();
-            // the pairs the prefilter kept go to their warp's queue (the FP32 path finishes them in bulk)
+            // the pairs the bound keeps: the FP32 first increment from the staged rows, and
+            // the survivors of its test to the warp's queue
             for (int g = warp; g < ng; g += LNW) {
                 if (qn + LTC > QCAP) {
-                    lm_drain<GB, STATS, true>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
+                    lm_drain<GB, STATS, false>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
                     qn = 0;
                     __syncwarp();
                 }
                 const int qh = g >> 4, jb = g & 15;
-                int kept = 0;
+                Surv *cand_list = queue + qn;   // kept candidates, compacted in place into survivors
+                int nk = 0;
                 for (int m0 = 0; m0 < tn; m0 += 32) {
                     const int mm = m0 + lane;
                     const bool keep = mm < tn && ((mask[qh * LTC + mm] >> jb) & 1u);
                     const unsigned mk = __ballot_sync(0xffffffffu, keep);
-                    if (keep) queue[qn + __popc(mk & ((1u << lane) - 1u))] = Surv{(g << QROW_BITS) | (i0 + mm), 0.f};
-                    qn += __popc(mk);
-                    kept += __popc(mk);
+                    if (keep) cand_list[nk + __popc(mk & ((1u << lane) - 1u))] = Surv{mm, 0.f};
+                    nk += __popc(mk);
                 }
-                const unsigned long long dropped = (unsigned long long)(tn - kept);
+                __syncwarp();
+                float4 qa[GB];
+#pragma unroll
+                for (int b = 0; b < GB; ++b)
+                    qa[b] = *reinterpret_cast<const float4 *>(qs + g * 16 * GB + b * 16 + lq * 4);
+                const float c0 = s_thr[g];
+                int ns = 0;
+                for (int r0 = 0; r0 < nk; r0 += 8) {   // the FP32 partial, as the plain kernels sum it
+                    const int sidx = r0 + quad;
+                    const bool act = sidx < nk;
+                    const int cand = act ? cand_list[sidx].idx : 0;
+                    float p = 0.f;
+                    if (act) {
+#pragma unroll
+                        for (int b = 0; b < GB; ++b)
+                            p += sqd4(qa[b], *reinterpret_cast<const float4 *>(af + ((size_t)(b * 4 + lq) * LTC + cand) * 4));
+                    }
+                    p = quad_sum4(p);
+                    const bool lead = act && lq == 0;
+                    const bool keep = lead && !(p > c0);
+                    __syncwarp();   // every lane has read its entry before the list is compacted in place
+                    const unsigned mk = __ballot_sync(0xffffffffu, keep);
+                    if (keep) cand_list[ns + __popc(mk & ((1u << lane) - 1u))] = Surv{(g << QROW_BITS) | (i0 + cand), p};
+                    ns += __popc(mk);
+                }
+                qn += ns;
                 if (lane == 0) {
                     const int q = s_q[g];
-                    if (STATS) {   // the dropped candidates count as pruned at the first test
+                    const unsigned long long pruned = (unsigned long long)(tn - ns);
+                    if (STATS) {   // every candidate the tile tested; pruned at the first test
                         atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 0]),
                                   (unsigned long long)tn);
                         atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 1]),
-                                  dropped * (unsigned long long)min(GB * 16, a.d));
-                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 3]), dropped);
+                                  pruned * (unsigned long long)min(GB * 16, a.d));
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.stats[(int64_t)q * 4 + 3]), pruned);
                     }
-                    if (a.lead_stats && dropped > 0)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.lead_stats[q]), dropped);
+                    if (a.lead_stats && tn > nk)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&a.lead_stats[q]), (unsigned long long)(tn - nk));
                 }
                 __syncwarp();
             }
-            __syncthreads();   // codes of buffer `buf` and the masks are free
+            __syncthreads();   // the rows of buffer `buf`, the masks and accumulator `buf` are free
             if (tid == 0 && t + 2 < ntile) issue(t + 2);
         }
         if (failed) break;
         __syncwarp();
-        lm_drain<GB, STATS, true>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
+        lm_drain<GB, STATS, false>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
         qn = 0;
         __syncwarp();
         if (kbest)   // the item's K best per query go to the accept buffers
@@ -919,9 +947,10 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
     }
     if (failed && tid == 0) {   // let the copies and MMAs in flight finish (bounded) before leaving
         atomicExch(a.err, (int)DADE_ETIMEOUT);
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < 2; ++b) {
             if (inflight[b] > 0) wait_bounded(su32(&full[b]), used[b] & 1u, 10000000ull);
-        if (mma_pending) wait_bounded(su32(&mdone), mph, 10000000ull);
+            if (mpend[b]) wait_bounded(su32(&mdone[b]), mph[b] & 1u, 10000000ull);
+        }
     }
     lt_fence_before();
     __syncthreads();
@@ -1098,8 +1127,15 @@ dade_status launch_lm_g(const LmArgs &a, cudaStream_t s) {
 template <int GB, bool STATS>
 dade_status launch_lm_tc(const LmArgs &a, const CUtensorMap &tmap, cudaStream_t s) {
     const size_t smem = TcSmem::total(GB);
-    int blocks = 1;
+    int blocks = 1, dev = 0, sms = 0;
     DADE_TRY(resident_blocks((const void *)k_lm_tc<GB, STATS>, LNT, smem, &blocks));
+    DADE_TRY_CUDA(cudaGetDevice(&dev));
+    DADE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // the kernel is sized for two blocks per SM (registers and shared memory; two
+    // accumulators of 128 tensor-memory columns each); the occupancy query answers one
+    // for it, so launch at least two per SM: a persistent block beyond what fits only
+    // starts when another leaves and then finds the work counter exhausted
+    blocks = std::max(blocks, 2 * sms);
     k_lm_tc<GB, STATS><<<blocks, LNT, smem, s>>>(a, tmap);
     return launch_check("k_lm_tc");
 }
@@ -1136,33 +1172,34 @@ dade_status launch_lm_gb(const LmArgs &a, int gb, cudaStream_t s) {
 } // namespace
 
 // The tensor-core prefilter runs a list-major DADE pass when the search asks
-// for the lead prefilter, the index holds a BF16 copy covering the first
-// increment (1, 2 or 4 blocks), and the increment is not the last one.
+// for it, the first increment is 1, 2 or 4 blocks and not the last one, and
+// the list-major kernels apply (D > 112).
 bool tc_applies(const dade_index *ix, const ScanParams &p, int gb) {
-    return p.use_lead && p.mode == DADE_MODE_DADE && ix->lead_tmap_ok && ix->lead_format == DADE_LEAD_BF16 &&
-           (gb == 1 || gb == 2 || gb == 4) && gb <= ix->lead_nb && ix->nb > gb && ix->nb >= LNB;
+    return p.use_tc && p.mode == DADE_MODE_DADE && ix->data_tmap_ok && (gb == 1 || gb == 2 || gb == 4) &&
+           ix->nb > gb && ix->nb >= LNB;
 }
 
 // Error bound of the expanded partial distance of k_lm_tc over K = 16 gb dims,
-// E = c1 (||a||^2 + ||r^||^2) + c2 ||a|| ||r^|| with a = q' - c' (FP32) and r^
-// the BF16 codes, u = 2^-24:
-//   - the FP32 sums ||a||^2 (lane-strided FMAs and an xor tree) and ||r^||^2
-//     (exact squares, one FMA chain of K terms) and s = ||a||^2 + ||r^||^2:
-//     relative (K + 8) u together, with the rounding of 2 a.r^ - s: c1;
-//   - a = hi + lo + d, |d| <= 2^-18 |a| (two BF16 roundings); the products of
-//     BF16 values are exact, and the tensor core accumulates K of them per
-//     column in FP32: allowed 4 x 2u per addition (truncating adds with a
-//     factor 4 to spare), then hi + lo adds one rounding:
-//     |dot - a.r^| <= (2^-18 + (K + 2) 2^-21) sum |a_k||r^_k| <= ... ||a|| ||r^||,
-//     twice that for the -2 a.r^ term: c2.
+// E = c1 (||q'||^2 + ||o'||^2) + c2 ||q'|| ||o'|| (FP32 rows q', o'), u = 2^-24:
+//   - the FP32 sums ||q'||^2 (lane-strided FMAs and an xor tree), ||o'||^2
+//     (one FMA chain of K terms) and s = ||q'||^2 + ||o'||^2: relative
+//     (K + 8) u together, with the rounding of s - 2 dot: c1;
+//   - the tensor core reads each row value o as TF32 (at most 2^-10 relative
+//     off, truncated or rounded), the query is split q = hi + lo + d with
+//     |d| <= 2^-22 |q| (two roundings to TF32), products of TF32 values are
+//     exact in FP32, and the K products of a column are accumulated in FP32:
+//     allowed 4 x 2u per addition (truncating adds with a factor 4 to spare);
+//     hi + lo adds one rounding:
+//     |dot - q'.o'| <= (2^-10 + 2^-22 + (K + 2) 2^-21) sum |q'_k||o'_k|,
+//     at most that times ||q'|| ||o'||; twice it for -2 dot: c2.
 // Both are rounded up and carry a further 2^-20 for their own FP32 evaluation.
 void tc_constants(int gb, float *c1, float *c2) {
     const double u = std::ldexp(1.0, -24), K = 16.0 * gb;
     const double cs = (K + 8.0) * u * 1.01 + 3.0 * u;
-    const double cd = std::ldexp(1.0, -18) + (K + 2.0) * std::ldexp(1.0, -21);
+    const double cd = std::ldexp(1.0, -10) + std::ldexp(1.0, -22) + (K + 2.0) * std::ldexp(1.0, -21);
     const double grow = 1.0 + std::ldexp(1.0, -20);
     *c1 = std::nextafter((float)(cs * grow), INFINITY);
-    *c2 = std::nextafter((float)(2.0 * cd * (1.0 + std::ldexp(1.0, -8) + std::ldexp(1.0, -9)) * grow), INFINITY);
+    *c2 = std::nextafter((float)(2.0 * cd * (1.0 + std::ldexp(1.0, -10)) * grow), INFINITY);
 }
 
 // One list-major round: the lists at probe positions [c0, c1) of every query,
@@ -1200,7 +1237,8 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
         k_lm_count<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, cnt);
         DADE_TRY(launch_check("k_lm_count"));
     }
-    const bool tc = prune && tc_applies(ix, p, gb);
+    // the tensor-core bound needs a finite threshold: not in a first round (r = +inf)
+    const bool tc = prune && tc_applies(ix, p, gb) && !(row_lo == 0 && c0 == 0 && p.schedule == DADE_SCHED_ROUNDS);
     const int tile_rows = tc ? LTC : LT;
     const int chunk_tiles = std::max(1, (p.list_chunk > 0 ? p.list_chunk : 4096) / tile_rows);
     k_lm_items<<<grid_of(nc + 1, 256), 256, 0, s>>>(cnt, ix->meta.as<ListMeta>(), nc, chunk_tiles, tile_rows, row_lo,
@@ -1245,15 +1283,10 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     a.n_inc = n_inc;
     for (int j = 0; j < DADE_MAX_DIM / DADE_BLOCK; ++j) a.coef[j] = (prune && j < n_inc - 1) ? p.coef[j] : INFINITY;
     if (tc) {
-        a.cent = ix->cent.as<float>();
-        a.lead_err = ix->lead_err.as<float>();
         a.lead_stats = p.lead_stats;
-        a.lead_slots = ix->slots;
-        a.lead_nb = ix->lead_nb;
-        a.dp = ix->dp;
         tc_constants(gb, &a.tc_c1, &a.tc_c2);
-        DADE_TRY(p.stats ? launch_lm_tc_gb<true>(a, ix->lead_tmap, gb, s)
-                         : launch_lm_tc_gb<false>(a, ix->lead_tmap, gb, s));
+        DADE_TRY(p.stats ? launch_lm_tc_gb<true>(a, ix->data_tmap, gb, s)
+                         : launch_lm_tc_gb<false>(a, ix->data_tmap, gb, s));
     } else if (ix->nb == LNB)
         DADE_TRY(p.stats ? launch_lm_gb<true>(a, gb, s) : launch_lm_gb<false>(a, gb, s));
     else
@@ -1353,13 +1386,13 @@ dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, c
     return lm_round(ix, nq, p, S, np, gb, !fd, s);
 }
 
-// TMA view of the BF16 lead copy: rows of 16 codes (32 B), row slot_c lead_nb
-// + b np_c + i for block b of member i of list c; boxes of 8 codes x 128 rows
+// TMA view of the packed FP32 data: rows of 16 floats (64 B), row base_c / 16
+// + b np_c + i for block b of member i of list c; boxes of 4 floats x 128 rows
 // land in shared memory as 128 contiguous 16-byte rows (core matrices of the
 // MMA's K-major layout without swizzle).
-dade_status make_lead_tmap(dade_index *ix) {
-    ix->lead_tmap_ok = false;
-    if (ix->lead_format != DADE_LEAD_BF16 || !ix->lead.p) return DADE_OK;
+dade_status make_data_tmap(dade_index *ix) {
+    ix->data_tmap_ok = false;
+    if (!ix->data.p || ix->data_floats == 0) return DADE_OK;
     typedef CUresult (*encode_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -1378,23 +1411,20 @@ dade_status make_lead_tmap(dade_index *ix) {
             encode = reinterpret_cast<encode_fn>(fn);
         }
     }
-    const uint64_t rows = (uint64_t)ix->slots * (uint64_t)ix->lead_nb;
-    if (rows == 0 || rows >= (1ull << 31)) {
-        set_error("the BF16 lead copy has too many rows for the tensor-core prefilter's TMA view");
-        return DADE_EUNSUPPORTED;
-    }
+    const uint64_t rows = (uint64_t)ix->data_floats / 16;
+    if (rows >= (1ull << 31)) return DADE_OK;   // beyond the kernels' 32-bit row coordinates: no prefilter
     const cuuint64_t dims[2] = {16, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {32};   // bytes between rows
-    const cuuint32_t box[2] = {8, (cuuint32_t)LTC};
+    const cuuint64_t strides[1] = {64};   // bytes between rows
+    const cuuint32_t box[2] = {4, (cuuint32_t)LTC};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(&ix->lead_tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ix->lead.p, dims, strides, box, estr,
+    CUresult r = encode(&ix->data_tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ix->data.p, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
-        set_error("cuTensorMapEncodeTiled failed for the BF16 lead copy (CUresult " + std::to_string((int)r) + ")");
+        set_error("cuTensorMapEncodeTiled failed for the packed data (CUresult " + std::to_string((int)r) + ")");
         return DADE_ECUDA;
     }
-    ix->lead_tmap_ok = true;
+    ix->data_tmap_ok = true;
     return DADE_OK;
 }
 
@@ -1420,7 +1450,7 @@ dade_status scan_rounds(const dade_index *ix, int64_t nq, const ScanParams &p, c
     if (p.lead_stats) DADE_TRY_CUDA(cudaMemsetAsync(p.lead_stats, 0, sizeof(int64_t) * (size_t)nq, s));
     const int64_t longest = std::max(ix->max_list, 1);
     const int64_t r1 = std::max(p.tile, 1);
-    if (lm_ok && !p.seed_split && (!p.use_lead || tc_applies(ix, p, gb))) {
+    if (lm_ok && !p.seed_split && !p.use_lead) {
         bool first = true;
         for (int64_t lo = 0, hi = r1; lo < longest; lo = hi, hi *= 2) {
             DADE_TRY(lm_round(ix, nq, p, 0, np, fd ? LNB : gb, !fd, s, (int)lo, (int)std::min<int64_t>(hi, INT_MAX),

@@ -740,33 +740,51 @@ def test_rounds_schedule_with_prefilter():
                                                      (384, 32, dade.SCHED_SEEDED, 128), (768, 32, dade.SCHED_ROUNDS, 64)])
 def test_tensor_core_prefilter_equals_fp32(d, delta_d, schedule, tile):
     """List-major passes with the first increment's inner products on the
-    tensor cores (BF16 lead codes, certified bound): ids, distance bits and
-    work counters equal the FP32 list-major path, the prefilter drops most
+    tensor cores (FP32 rows read as TF32, certified bound): ids, distance bits
+    and work counters equal the FP32 list-major path, the bound drops most
     candidates, and the results match the oracle."""
     n = 12000 if d <= 256 else 6000
     w = synth.Workload(f"tc{d}", n, d, 60, 1.2, 12, 0.0, 2.0, 1.0, False, True, 12, (4,), 10, (16,), 0.1,
                        comp_zipf=1.1, lists_are_components=True)
     base, queries, labels = synth.make(w)
     case = Case(base, queries, labels, 12, n_pairs=3000)
-    ix = dade.Index(torch.from_numpy(base).cuda(), 12, assign=case.assign, pairs=case.pairs,
-                    lead_format=dade.LEAD_BF16, lead_dims=64)
-    q_rot = torch.empty_like(case.q_dev)
-    ix.rotate(case.q_dev, q_rot)
     nq = queries.shape[0]
     out = []
-    for fl in (0, dade.FLAG_LEAD):
+    for fl in (0, dade.FLAG_TC_PREFILTER):
         ids = torch.empty(nq, 10, dtype=torch.int64, device="cuda")
         dd = torch.empty(nq, 10, dtype=torch.float32, device="cuda")
         st = torch.zeros(nq, 4, dtype=torch.int64, device="cuda")
-        ls = torch.zeros(nq, dtype=torch.int64, device="cuda") if fl else None
-        ix.search(q_rot, 10, 5, 0.1, delta_d, ids, dd, tile=tile, stats=st, schedule=schedule, seed_lists=2,
-                  flags=fl, lead_stats=ls, list_chunk=256)
-        ix.sync()
+        ls = torch.full((nq,), -1, dtype=torch.int64, device="cuda") if fl else None
+        case.gpu.search(case.q_rot, 10, 5, 0.1, delta_d, ids, dd, tile=tile, stats=st, schedule=schedule,
+                        seed_lists=2, flags=fl, lead_stats=ls, list_chunk=256)
+        case.gpu.sync()
         out.append((ids.cpu().numpy(), dd.cpu().numpy(), st.cpu().numpy(), None if ls is None else ls.cpu().numpy()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1].view(np.uint32), out[1][1].view(np.uint32))
     assert np.array_equal(out[0][2], out[1][2])
-    assert out[1][3].sum() > 0.3 * out[1][2][:, 0].sum(), (out[1][3].sum(), out[1][2][:, 0].sum())
-    assert (out[1][3] <= out[1][2][:, 3]).all()
+    assert (out[1][3] >= 0).all() and (out[1][3] <= out[1][2][:, 3]).all()
+    assert out[1][3].sum() > 0.3 * out[1][2][:, 3].sum(), (out[1][3].sum(), out[1][2][:, 3].sum())
     sched = dade.SCHED_ROUNDS if schedule == dade.SCHED_ROUNDS else dade.SCHED_SEEDED
     o = case.oracle_search(10, 5, 0.1, delta_d, tile=tile, schedule=sched, seed=2 if sched == dade.SCHED_SEEDED else 0)
     parity.compare(out[1][0], out[1][1], o, case.exact_d)
+
+
+def test_tensor_core_prefilter_integer_data_and_large_k():
+    """The bound on 1M-style integer data far from the origin (large norms,
+    small distances: the hardest case for the expanded form) and K = 100
+    (accepted keys appended directly): the FP32 path's bits and counters."""
+    w = synth.Workload("tcint", 20000, 128, 50, 1.0, 16, 40.0, 25.0, 20.0, True, False, 16, (4,), 100, (16,), 0.1)
+    base, queries, labels = synth.make(w)
+    ix = dade.Index(torch.from_numpy(base).cuda(), 16, assign=labels, eps_pairs=3000)
+    q = torch.from_numpy(queries).cuda()
+    out = []
+    for fl in (0, dade.FLAG_TC_PREFILTER):
+        for schedule in (dade.SCHED_SEEDED, dade.SCHED_ROUNDS):
+            ids = torch.empty(50, 100, dtype=torch.int64, device="cuda")
+            dd = torch.empty(50, 100, dtype=torch.float32, device="cuda")
+            st = torch.zeros(50, 4, dtype=torch.int64, device="cuda")
+            ix.query(q, 100, 6, 0.3, 64, ids, dd, stats=st, flags=fl, schedule=schedule, seed_lists=2, tile=128)
+            ix.sync()
+            out.append((ids.cpu().numpy(), dd.cpu().numpy(), st.cpu().numpy()))
+    for a_, b_ in ((out[0], out[2]), (out[1], out[3])):
+        assert np.array_equal(a_[0], b_[0]) and np.array_equal(a_[1].view(np.uint32), b_[1].view(np.uint32))
+        assert np.array_equal(a_[2], b_[2])
