@@ -247,6 +247,12 @@ typedef struct {
     int32_t stage_ring;        /* tile kernel for any D: staged tiles in flight per thread block (0: 2;
                                   2..8); deeper rings hide more load latency for more shared memory.
                                   Same results. */
+    int64_t wait_ns;           /* limit, in ns, of every bounded device-side wait of the scan kernels for a
+                                  copy or an MMA (0: 2 s).  A wait that runs out makes its thread block
+                                  record DADE_ETIMEOUT (reported by dade_sync or by the call, for host
+                                  outputs), let its copies in flight land (bounded), free what it holds
+                                  and leave; that query's results are then undefined, the index stays
+                                  usable.  Limits below 0.2 ms poll without suspending. */
 } dade_search_opts;
 
 /* Description of a built index. */
@@ -507,6 +513,17 @@ dade_status dade_index_export(const dade_index *ix, int32_t field, void *dst, si
  * descending; v: host [n * n], column k = unit eigenvector of w[k].
  */
 dade_status dade_host_sym_eig(double *a, int32_t n, double *w, double *v);
+
+/*
+ * Allocation-failure injection (no counterpart in the paper; for tests of the
+ * failure paths).  While a hook is set, every device allocation the library
+ * makes first calls hook(bytes, user); a nonzero return makes that
+ * allocation fail as a failed cudaMalloc would: the call returns DADE_ENOMEM
+ * with a message naming the hook, after freeing what it had allocated.
+ * NULL removes the hook.  Process-wide; set it while no call is running.
+ */
+typedef int (*dade_alloc_hook)(size_t bytes, void *user);
+void dade_set_alloc_hook(dade_alloc_hook hook, void *user);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char *dade_last_error(void);

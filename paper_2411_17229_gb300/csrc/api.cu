@@ -83,9 +83,20 @@ Workspace &ws(const dade_index *ix) { return t_ws ? *t_ws : ix->ws0; }
 WorkspaceScope::WorkspaceScope(Workspace *w) : prev(t_ws) { t_ws = w; }
 WorkspaceScope::~WorkspaceScope() { t_ws = prev; }
 
+namespace {
+std::atomic<dade_alloc_hook> g_alloc_hook{nullptr};
+std::atomic<void *> g_alloc_user{nullptr};
+} // namespace
+
 dade_status DevBuf::alloc(size_t b) {
     release();
     if (b == 0) b = 16;
+    if (dade_alloc_hook h = g_alloc_hook.load()) {
+        if (h(b, g_alloc_user.load()) != 0) {
+            set_error(std::string("device allocation of ") + std::to_string(b) + " bytes refused by the allocation hook");
+            return DADE_ENOMEM;
+        }
+    }
     cudaError_t e = cudaMalloc(&p, b);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -197,6 +208,7 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
                    "list_chunk must be 0 or a positive multiple of 64");
     DADE_CHECK_ARG(!opts || opts->stage_ring == 0 || (opts->stage_ring >= 2 && opts->stage_ring <= 8),
                    "stage_ring must be 0 or 2..8");
+    DADE_CHECK_ARG(!opts || opts->wait_ns >= 0, "wait_ns < 0");
     DADE_CHECK_ARG(!opts || opts->stage_dims == 0 ||
                        (opts->stage_dims >= delta_d && delta_d > 0 && opts->stage_dims % delta_d == 0 &&
                         opts->stage_dims <= DADE_MAX_DIM),
@@ -272,6 +284,7 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.use_tail = opts ? (opts->flags & DADE_FLAG_ROW_TAIL) != 0 : 0;
     p.seed_split = opts ? (opts->flags & DADE_FLAG_SEED_SPLIT) != 0 : 0;
     p.use_tc = opts ? (opts->flags & DADE_FLAG_TC_PREFILTER) != 0 : 0;
+    p.wait_ns = opts ? opts->wait_ns : 0;
     p.lead_stats = opts ? opts->lead_stats : nullptr;
     p.delta_d = delta_d;
     const bool ads = opts && opts->estimator == DADE_ESTIMATOR_ADSAMPLING;
@@ -699,3 +712,8 @@ dade_status dade_host_sym_eig(double *a, int32_t n, double *w, double *v) {
 }
 
 } // extern "C"
+
+extern "C" void dade_set_alloc_hook(dade_alloc_hook hook, void *user) {
+    g_alloc_user.store(user);
+    g_alloc_hook.store(hook);
+}

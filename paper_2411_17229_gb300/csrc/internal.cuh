@@ -179,6 +179,7 @@ struct ScanParams {
     int32_t parts, c0;
     int32_t row_lo, row_hi;  // split passes: rows [row_lo, min(len, row_hi)) of every list (row_hi 0: all)
     int32_t use_tc;          // list-major passes: the first increment's tensor-core prefilter
+    int64_t wait_ns;         // limit of the scan kernels' bounded waits (0: 2 s)
     const float *r2src;
     unsigned long long *acc;
     int *acnt;

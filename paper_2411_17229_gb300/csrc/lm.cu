@@ -58,6 +58,7 @@ struct LmArgs {
     int q_stride, nc, k, d, tail_nb0, tail_w;
     int nb, n_inc;               // 16-dim blocks of the layout, increments (k_lm_g)
     int chunk_tiles;             // tiles of a list per work item (a long list is several items)
+    uint64_t wait_ns;            // limit of every bounded wait on a copy or an MMA
     int row_lo, row_hi;          // rows [row_lo, min(len, row_hi)) of every list are scanned; tiles
                                  // of LT rows start at row_lo
     // tensor-core prefilter (k_lm_tc)
@@ -228,11 +229,11 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
 
         for (int t = t0; t < ntile; ++t) {
             const int buf = t & 1;
-            if (!wait_block(su32(&bars[buf]), used[buf] & 1u)) {
-                if (tid == 0) {
+            if (!wait_block(su32(&bars[buf]), used[buf] & 1u, a.wait_ns)) {
+                if (tid == 0) {   // both buffers' copies may still be in flight: let them land (bounded)
                     atomicExch(a.err, (int)DADE_ETIMEOUT);
-                    if (t + 1 < ntile)   // the other buffer's copy may still be in flight
-                        wait_bounded(su32(&bars[buf ^ 1]), used[buf ^ 1] & 1u, 10000000ull);
+                    wait_bounded(su32(&bars[buf]), used[buf] & 1u, 10000000ull);
+                    if (t + 1 < ntile) wait_bounded(su32(&bars[buf ^ 1]), used[buf ^ 1] & 1u, 10000000ull);
                 }
                 return;
             }
@@ -538,9 +539,10 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
         }
         for (int t = t0; t < ntile; ++t) {
             const int buf = t & 1;
-            if (!wait_block(su32(&bars[buf]), used[buf] & 1u)) {
-                if (tid == 0) {
+            if (!wait_block(su32(&bars[buf]), used[buf] & 1u, a.wait_ns)) {
+                if (tid == 0) {   // both buffers' copies may still be in flight: let them land (bounded)
                     atomicExch(a.err, (int)DADE_ETIMEOUT);
+                    wait_bounded(su32(&bars[buf]), used[buf] & 1u, 10000000ull);
                     if (t + 1 < ntile) wait_bounded(su32(&bars[buf ^ 1]), used[buf ^ 1] & 1u, 10000000ull);
                 }
                 return;
@@ -769,7 +771,7 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         };
         auto mma = [&](int t) -> bool {   // thread 0: wait for tile t's rows, then its MMAs
             const int buf = t & 1;
-            if (!wait_bounded(su32(&full[buf]), used[buf] & 1u, WAIT_NS)) return false;
+            if (!wait_bounded(su32(&full[buf]), used[buf] & 1u, a.wait_ns)) return false;
             ++used[buf];
             --inflight[buf];
             lt_fence_after();
@@ -832,7 +834,7 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
             if (tid == 0 && !failed && t + 1 < ntile && !mma(t + 1)) failed = true;   // overlaps this tile's reads
             bool ok = !failed;
             if (tid == 0 && ok) {
-                ok = wait_bounded(su32(&mdone[buf]), mph[buf] & 1u, WAIT_NS);
+                ok = wait_bounded(su32(&mdone[buf]), mph[buf] & 1u, a.wait_ns);
                 if (ok) {
                     ++mph[buf];
                     mpend[buf] = false;
@@ -1270,6 +1272,7 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     a.chunk_tiles = chunk_tiles;
     a.row_lo = row_lo;
     a.row_hi = row_hi;
+    a.wait_ns = p.wait_ns > 0 ? (uint64_t)p.wait_ns : WAIT_NS;
     a.nc = nc;
     a.k = p.k;
     a.d = ix->d;

@@ -59,6 +59,7 @@ struct ScanArgs {
     // row window of every list (split passes of the row-rounds schedule): rows
     // [row_lo, min(len, row_hi)) are scanned; row_hi = 0 means no upper limit
     int row_lo, row_hi;
+    uint64_t wait_ns;            // limit of every bounded wait on a copy
 };
 
 // Rows of a list of `len` members that a pass scans end here.
@@ -107,9 +108,28 @@ __device__ __forceinline__ uint64_t gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // One thread of the block waits; the others park on the block barrier that
 // follows (wait_block), which makes the bulk-copied data visible to them.
+// Limits below 0.2 ms (a caller trying the timeout path) poll without the
+// suspend hint, so that they can expire before a copy lands.
 __device__ inline bool wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    if (limit_ns < 200000ull) {
+        const uint64_t t0 = gtimer();
+        do {
+            if (mbar_test_wait(bar, parity)) return true;
+        } while (gtimer() - t0 <= limit_ns);
+        return false;
+    }
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (!mbar_try_wait(bar, parity))
@@ -119,9 +139,9 @@ __device__ inline bool wait_bounded(uint32_t bar, uint32_t parity, uint64_t limi
 
 // Block-wide wait for the mbarrier phase: thread 0 waits (bounded), then a
 // barrier.  Returns false on every thread if the wait timed out.
-__device__ __forceinline__ bool wait_block(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool wait_block(uint32_t bar, uint32_t parity, uint64_t limit_ns = WAIT_NS) {
     bool ok = true;
-    if (threadIdx.x == 0) ok = wait_bounded(bar, parity, WAIT_NS);
+    if (threadIdx.x == 0) ok = wait_bounded(bar, parity, limit_ns);
     return !__syncthreads_or(!ok);
 }
 

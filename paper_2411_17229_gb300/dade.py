@@ -49,7 +49,7 @@ class SearchOpts(C.Structure):
                 ("threads", C.c_int32), ("schedule", C.c_int32), ("flags", C.c_int32),
                 ("lead_stats", C.c_void_p), ("seed_lists", C.c_int32), ("estimator", C.c_int32),
                 ("eps0", C.c_float), ("stage_dims", C.c_int32), ("list_chunk", C.c_int32),
-                ("stage_ring", C.c_int32)]
+                ("stage_ring", C.c_int32), ("wait_ns", C.c_int64)]
 
 
 class ServerOpts(C.Structure):
@@ -104,6 +104,7 @@ SIGNATURES = {
     "dade_sync": (_i32, [_vp, _vp]),
     "dade_probe_noalloc": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
     "dade_fp32_fma_peak": (_i32, [_i32, _vp, _vp]),
+    "dade_set_alloc_hook": (None, [_vp, _vp]),
     "dade_last_error": (C.c_char_p, []),
     "dade_version": (C.c_char_p, []),
 }
@@ -240,46 +241,46 @@ class Index:
 
     def search(self, q_rot, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
                threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, estimator=ESTIMATOR_DADE,
-             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, stream=None):
+             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
                        flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists, estimator=estimator,
                        eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
-                       stage_ring=stage_ring)
+                       stage_ring=stage_ring, wait_ns=wait_ns)
         _check(lib().dade_search(self._h, _ptr(q_rot), q_rot.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                  C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def scan(self, q_rot, probe, k, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
              threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, estimator=ESTIMATOR_DADE,
-             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, stream=None):
+             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
                        flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists, estimator=estimator,
                        eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
-                       stage_ring=stage_ring)
+                       stage_ring=stage_ring, wait_ns=wait_ns)
         _check(lib().dade_scan(self._h, _ptr(q_rot), _ptr(probe), q_rot.shape[0], int(k), probe.shape[1],
                                float(alpha), int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def query(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
               threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, estimator=ESTIMATOR_DADE,
-             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, stream=None):
+             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
                        flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists, estimator=estimator,
                        eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
-                       stage_ring=stage_ring)
+                       stage_ring=stage_ring, wait_ns=wait_ns)
         _check(lib().dade_query(self._h, _ptr(q), q.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                 C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def graph(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
               threads=0, schedule=SCHED_TILE, flags=0, seed_lists=0, estimator=ESTIMATOR_DADE, eps0=0.0,
-              stage_dims=0, list_chunk=0, stage_ring=0):
+              stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0):
         """A query step captured into a CUDA graph (device buffers, bound to the graph)."""
         return Graph(self, q, k, nprobe, alpha, delta_d, ids, dists,
                      SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads,
                                 schedule=schedule, flags=flags, seed_lists=seed_lists, estimator=estimator,
                                 eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
-                       stage_ring=stage_ring))
+                                stage_ring=stage_ring, wait_ns=wait_ns))
 
     def tune(self, q_rot, probe, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, spec=0,
              threads=0, schedule=SCHED_TILE, flags=0, seed_lists=0, estimator=ESTIMATOR_DADE, eps0=0.0,
