@@ -137,12 +137,18 @@ enum {
                                       exceeds the threshold by more than the FP32 path's rounding, every
                                       other one runs the FP32 path.  Same results; opts->lead_stats
                                       counts the candidates the bound dropped. */
-    DADE_FLAG_SEED_SPLIT = 16      /* DADE_SCHED_SEEDED: every pass with r frozen (the lists after the
+    DADE_FLAG_SEED_SPLIT = 16,     /* DADE_SCHED_SEEDED: every pass with r frozen (the lists after the
                                       seeds; with whole-list tiles, each seed epoch too) runs query-major
                                       on the tile kernel, each query's lists split into parts over
                                       several thread blocks (the candidates are independent there),
                                       instead of list-major.  Same tests and thresholds.  The same for
                                       every round of DADE_SCHED_ROUNDS. */
+    DADE_FLAG_CHECK_TIMEOUT = 64   /* check of the failure path: the first wait on a copy of every thread
+                                      block of the scan waits instead on a device word that nothing
+                                      sets, so it runs out after wait_ns with the block's first copies in
+                                      flight.  The blocks let those copies land and leave; dade_sync
+                                      returns DADE_ETIMEOUT and the index serves the next search.  The
+                                      results of that search are undefined. */
 };
 
 /*
@@ -252,7 +258,8 @@ typedef struct {
                                   record DADE_ETIMEOUT (reported by dade_sync or by the call, for host
                                   outputs), let its copies in flight land (bounded), free what it holds
                                   and leave; that query's results are then undefined, the index stays
-                                  usable.  Limits below 0.2 ms poll without suspending. */
+                                  usable.  Limits below 0.2 ms poll without suspending, limits below
+                                  1 us poll once. */
 } dade_search_opts;
 
 /* Description of a built index. */

@@ -214,7 +214,8 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
                         opts->stage_dims <= DADE_MAX_DIM),
                    "stage_dims must be 0 or a multiple of delta_d up to 1024");
     DADE_CHECK_ARG(!opts || (opts->flags & ~(DADE_FLAG_GENERIC_KERNEL | DADE_FLAG_LEAD | DADE_FLAG_QUERY_ORDER |
-                                             DADE_FLAG_ROW_TAIL | DADE_FLAG_SEED_SPLIT | DADE_FLAG_TC_PREFILTER)) == 0,
+                                             DADE_FLAG_ROW_TAIL | DADE_FLAG_SEED_SPLIT | DADE_FLAG_TC_PREFILTER |
+                                             DADE_FLAG_CHECK_TIMEOUT)) == 0,
                    "unknown flag bits");
     DADE_CHECK_ARG(!opts || !(opts->flags & DADE_FLAG_ROW_TAIL) || ix->tail_nb0 > 0,
                    "DADE_FLAG_ROW_TAIL on an index built without tail_from");
@@ -285,6 +286,7 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.seed_split = opts ? (opts->flags & DADE_FLAG_SEED_SPLIT) != 0 : 0;
     p.use_tc = opts ? (opts->flags & DADE_FLAG_TC_PREFILTER) != 0 : 0;
     p.wait_ns = opts ? opts->wait_ns : 0;
+    p.check_timeout = opts ? (opts->flags & DADE_FLAG_CHECK_TIMEOUT) != 0 : 0;
     p.lead_stats = opts ? opts->lead_stats : nullptr;
     p.delta_d = delta_d;
     const bool ads = opts && opts->estimator == DADE_ESTIMATOR_ADSAMPLING;

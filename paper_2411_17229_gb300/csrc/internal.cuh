@@ -108,7 +108,8 @@ struct dade_index {
     dade::DevBuf data;      // packed rotated vectors
     dade::DevBuf ids;       // int32 per slot (padding slots -1)
     dade::DevBuf meta;      // ListMeta [nc]
-    dade::DevBuf errflag;   // int32 device error word (bounded waits)
+    dade::DevBuf errflag;   // int32 [4]: [0] device error word (bounded waits); [3] stays 0
+                            // (the word the failure-path check waits on)
     // low-precision copy of the leading dims (prefilter), see dade_lead_format
     int32_t lead_format = 0, lead_dims = 0, lead_nb = 0;
     dade::DevBuf lead;      // codes; list c at slot_c * lead_nb * 16 * ES bytes, block b at + b * np * 16 * ES
@@ -180,6 +181,7 @@ struct ScanParams {
     int32_t row_lo, row_hi;  // split passes: rows [row_lo, min(len, row_hi)) of every list (row_hi 0: all)
     int32_t use_tc;          // list-major passes: the first increment's tensor-core prefilter
     int64_t wait_ns;         // limit of the scan kernels' bounded waits (0: 2 s)
+    int32_t check_timeout;   // failure-path check: every block's first wait runs out
     const float *r2src;
     unsigned long long *acc;
     int *acnt;

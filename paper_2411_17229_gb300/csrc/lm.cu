@@ -59,6 +59,7 @@ struct LmArgs {
     int nb, n_inc;               // 16-dim blocks of the layout, increments (k_lm_g)
     int chunk_tiles;             // tiles of a list per work item (a long list is several items)
     uint64_t wait_ns;            // limit of every bounded wait on a copy or an MMA
+    const int *never;            // failure-path check: a device word nothing sets (else NULL)
     int row_lo, row_hi;          // rows [row_lo, min(len, row_hi)) of every list are scanned; tiles
                                  // of LT rows start at row_lo
     // tensor-core prefilter (k_lm_tc)
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
 
         for (int t = t0; t < ntile; ++t) {
             const int buf = t & 1;
-            if (!wait_block(su32(&bars[buf]), used[buf] & 1u, a.wait_ns)) {
+            if (!wait_block(su32(&bars[buf]), used[buf] & 1u, a.wait_ns, (used[0] | used[1]) == 0 ? a.never : nullptr)) {
                 if (tid == 0) {   // both buffers' copies may still be in flight: let them land (bounded)
                     atomicExch(a.err, (int)DADE_ETIMEOUT);
                     wait_bounded(su32(&bars[buf]), used[buf] & 1u, 10000000ull);
@@ -539,7 +540,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
         }
         for (int t = t0; t < ntile; ++t) {
             const int buf = t & 1;
-            if (!wait_block(su32(&bars[buf]), used[buf] & 1u, a.wait_ns)) {
+            if (!wait_block(su32(&bars[buf]), used[buf] & 1u, a.wait_ns, (used[0] | used[1]) == 0 ? a.never : nullptr)) {
                 if (tid == 0) {   // both buffers' copies may still be in flight: let them land (bounded)
                     atomicExch(a.err, (int)DADE_ETIMEOUT);
                     wait_bounded(su32(&bars[buf]), used[buf] & 1u, 10000000ull);
@@ -771,6 +772,7 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         };
         auto mma = [&](int t) -> bool {   // thread 0: wait for tile t's rows, then its MMAs
             const int buf = t & 1;
+            if ((used[0] | used[1]) == 0 && a.never != nullptr && !wait_word(a.never, a.wait_ns)) return false;
             if (!wait_bounded(su32(&full[buf]), used[buf] & 1u, a.wait_ns)) return false;
             ++used[buf];
             --inflight[buf];
@@ -1273,6 +1275,7 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     a.row_lo = row_lo;
     a.row_hi = row_hi;
     a.wait_ns = p.wait_ns > 0 ? (uint64_t)p.wait_ns : WAIT_NS;
+    a.never = p.check_timeout ? ix->errflag.as<int>() + 3 : nullptr;
     a.nc = nc;
     a.k = p.k;
     a.d = ix->d;

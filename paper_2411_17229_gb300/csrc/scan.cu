@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
             for (int it = 0; it < MAXIT; ++it) acc[it] = 0.f;
             for (int j = 0; j < a.n_inc; ++j) {
                 const int slot = unit % a.ns;
-                if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1), a.wait_ns)) { aborted = true; break; }
+                if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1), a.wait_ns, unit == 0 ? a.never : nullptr)) { aborted = true; break; }
                 if (j == 0) r2 = s_r2;
                 const float *st = stage + (size_t)slot * a.tile * a.ub * 16;
                 const int b0 = j * a.ub, b1 = min(b0 + a.ub, a.nb);
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
                 for (int b = tid; b < a.gb; b += NT)
                     qc[a.dp + b] = LF == 2 ? a.lead_scale[(int64_t)list * a.lead_nb + b] : 1.f;
             }
-            if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1), a.wait_ns)) { aborted = true; break; }
+            if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1), a.wait_ns, unit == 0 ? a.never : nullptr)) { aborted = true; break; }
             r2 = s_r2;
             if constexpr (LF != 0) {
                 const unsigned char *st = reinterpret_cast<const unsigned char *>(stage + (size_t)slot * a.tile * a.ub * 16);
@@ -464,6 +464,7 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     }
     a.err = ix->errflag.as<int>();
     a.wait_ns = p.wait_ns > 0 ? (uint64_t)p.wait_ns : WAIT_NS;
+    a.never = p.check_timeout ? ix->errflag.as<int>() + 3 : nullptr;
     a.q_stride = p.q_stride;
     a.nprobe = p.nprobe;
     if (p.parts > 0) {

@@ -60,6 +60,7 @@ struct ScanArgs {
     // [row_lo, min(len, row_hi)) are scanned; row_hi = 0 means no upper limit
     int row_lo, row_hi;
     uint64_t wait_ns;            // limit of every bounded wait on a copy
+    const int *never;            // failure-path check: a device word nothing sets (else NULL)
 };
 
 // Rows of a list of `len` members that a pass scans end here.
@@ -121,8 +122,10 @@ __device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
 // One thread of the block waits; the others park on the block barrier that
 // follows (wait_block), which makes the bulk-copied data visible to them.
 // Limits below 0.2 ms (a caller trying the timeout path) poll without the
-// suspend hint, so that they can expire before a copy lands.
+// suspend hint, so that they can expire before a copy lands; below 1 us (the
+// global timer's resolution) they poll exactly once.
 __device__ inline bool wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    if (limit_ns < 1000ull) return mbar_test_wait(bar, parity);
     if (limit_ns < 200000ull) {
         const uint64_t t0 = gtimer();
         do {
@@ -137,11 +140,24 @@ __device__ inline bool wait_bounded(uint32_t bar, uint32_t parity, uint64_t limi
     return true;
 }
 
+// Failure-path check (DADE_FLAG_CHECK_TIMEOUT): a bounded wait on a device
+// word that nothing sets.  It runs out after limit_ns, like a wait on a copy
+// that never lands, and the caller takes its timeout path.
+__device__ inline bool wait_word(const volatile int *w, uint64_t limit_ns) {
+    const uint64_t t0 = gtimer();
+    while (*w == 0)
+        if (gtimer() - t0 > limit_ns) return false;
+    return true;
+}
+
 // Block-wide wait for the mbarrier phase: thread 0 waits (bounded), then a
-// barrier.  Returns false on every thread if the wait timed out.
-__device__ __forceinline__ bool wait_block(uint32_t bar, uint32_t parity, uint64_t limit_ns = WAIT_NS) {
+// barrier.  Returns false on every thread if the wait timed out.  With `never`
+// set (a block's first wait under the failure-path check), thread 0 first
+// waits on that word.
+__device__ __forceinline__ bool wait_block(uint32_t bar, uint32_t parity, uint64_t limit_ns = WAIT_NS,
+                                           const int *never = nullptr) {
     bool ok = true;
-    if (threadIdx.x == 0) ok = wait_bounded(bar, parity, limit_ns);
+    if (threadIdx.x == 0) ok = (never == nullptr || wait_word(never, limit_ns)) && wait_bounded(bar, parity, limit_ns);
     return !__syncthreads_or(!ok);
 }
 

@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_dade_fast(const ScanArgs a) {
         const int nch = (tn + CH - 1) / CH;
         for (int j = 0; j < nch; ++j) {
             const int slot = unit % NSF;
-            if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / NSF) & 1), a.wait_ns)) { aborted = true; break; }
+            if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / NSF) & 1), a.wait_ns, unit == 0 ? a.never : nullptr)) { aborted = true; break; }
             if (j == 0) r2 = s_r2;
             const int cbase = j * CH, cn = min(CH, tn - cbase);
             if constexpr (LF != 0) {
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_fd_fast(const ScanArgs a) {
 #pragma unroll
         for (int u = 0; u < NU; ++u) {
             const int slot = unit % a.ns;
-            if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1), a.wait_ns)) { aborted = true; break; }
+            if (!wait_block(su32(&bars[slot]), (uint32_t)((unit / a.ns) & 1), a.wait_ns, unit == 0 ? a.never : nullptr)) { aborted = true; break; }
             if (u == 0) r2 = s_r2;
             const float *st = stage + (size_t)slot * a.tile * UB * 16 + lq * 4;
 #pragma unroll

@@ -159,7 +159,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_scan_pipe(const ScanArgs a) {
             }
         }
         bool ok = true;
-        if (enter && tid == 0) ok = wait_bounded(su32(&bars[ne % a.ns]), (uint32_t)((ne / a.ns) & 1), a.wait_ns);
+        if (enter && tid == 0)
+            ok = (ne != 0 || a.never == nullptr || wait_word(a.never, a.wait_ns)) &&
+                 wait_bounded(su32(&bars[ne % a.ns]), (uint32_t)((ne / a.ns) & 1), a.wait_ns);
         cp_async_wait_all();
         if (__syncthreads_or(!ok)) { aborted = true; break; }
         // ---- one increment for every work item of the step ---------------------------

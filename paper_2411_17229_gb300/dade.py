@@ -20,6 +20,7 @@ MODE_DADE, MODE_FD = 0, 1
 SCHED_TILE, SCHED_PIPELINED, SCHED_SEEDED, SCHED_ROUNDS = 0, 1, 2, 3
 FLAG_GENERIC_KERNEL, FLAG_LEAD, FLAG_QUERY_ORDER, FLAG_ROW_TAIL, FLAG_SEED_SPLIT = 1, 2, 4, 8, 16
 FLAG_TC_PREFILTER = 32
+FLAG_CHECK_TIMEOUT = 64
 LEAD_NONE, LEAD_BF16, LEAD_FP8 = 0, 1, 2
 TRANSFORM_PCA, TRANSFORM_RANDOM, TRANSFORM_GIVEN = 0, 1, 2
 ESTIMATOR_DADE, ESTIMATOR_ADSAMPLING = 0, 1
