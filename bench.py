@@ -541,11 +541,11 @@ def dade_variants(dade, w, lf):
 
 
 def precision_of(point, lf, dade):
+    if point.get("flags", 0) & dade.FLAG_LEAD:
+        return {dade.LEAD_BF16: "bf16 lead blocks", dade.LEAD_FP8: "fp8-e4m3 lead blocks"}.get(lf, "fp32")
     if point.get("flags", 0) & dade.FLAG_TC_PREFILTER:
         return "fp32 (first increment bounded on the tensor cores, TF32)"
-    if not point.get("flags", 0) & dade.FLAG_LEAD:
-        return "fp32"
-    return {dade.LEAD_BF16: "bf16 lead blocks", dade.LEAD_FP8: "fp8-e4m3 lead blocks"}.get(lf, "fp32")
+    return "fp32"
 
 
 def dist_error(torch, xb, q, ids, dists):
@@ -783,7 +783,10 @@ def measure_workload(args, wname, rank, world, dist, headline):
     # ---- precision configurations at the chosen point: recall and distance error ------
     precision = {precision_of(point, lf, dade): {"recall": round(rc_timed, 5), "max_rel_dist_error": err_timed,
                                                  "ms_per_scan": round(statistics.mean(scan_ms), 4)}}
-    alt = dict(point, flags=point["flags"] ^ dade.FLAG_LEAD) if lf else None
+    # the other precision of the index's lead copy (the low-precision prefilter replaces the
+    # tensor-core one where both were set)
+    alt = dict(point, flags=(point["flags"] ^ dade.FLAG_LEAD) & ~(dade.FLAG_TC_PREFILTER if not point["flags"]
+                                                                  & dade.FLAG_LEAD else 0)) if lf else None
     if point.get("flags", 0) & dade.FLAG_TC_PREFILTER:   # the same point on the CUDA cores alone
         r = measure(dict(point, flags=point["flags"] & ~dade.FLAG_TC_PREFILTER), reps=4)
         if r is not None:

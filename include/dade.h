@@ -397,6 +397,61 @@ dade_status dade_save_index(const dade_index *ix, const char *path);
 dade_status dade_load_index(const char *path, dade_index **out);
 
 /*
+ * ---- The index split by inverted lists (one shard per GPU) -------------------
+ * The IVF search of Section 3.4 visits whole inverted lists, so the lists can
+ * be dealt to G shards: each shard keeps the mean, the basis, the eigenvalue
+ * sums and the rho_d sample (so eps_d and the coefficients of the Section 3.3
+ * test are the full index's, Eq. 13-14) and every centroid (so every shard
+ * probes the same global lists), but only the rows of its own lists.  A
+ * search on a shard is the IVF loop over the probed lists it holds, with its
+ * own threshold r (the K-th distance among those lists: never below the
+ * unsharded search's r, so it prunes no more than that search would, and a
+ * stale r is safe).  The sharded result is the K nearest of the G shards'
+ * results, merged by dade_merge_shards.  In FD mode it equals the unsharded
+ * result exactly; in DADE mode it equals the merge of the per-shard searches.
+ */
+
+/*
+ * Deal n_lists lists of list_rows[c] rows to n_shards shards, balanced by
+ * rows: longest list first (ties by list id), each to the shard with the
+ * fewest rows so far (ties by the lower shard id).  Host only (no device
+ * call); deterministic, so every rank computes the same owner[] from the
+ * same sizes.  list_rows: host [n_lists] (>= 0); owner: host [n_lists],
+ * written with 0 .. n_shards - 1.  DADE_EINVAL on a NULL pointer, n_lists
+ * or n_shards < 1, or a negative size.
+ */
+dade_status dade_shard_lists(const int64_t *list_rows, int32_t n_lists, int32_t n_shards, int32_t *owner);
+
+/*
+ * A new index on the current device holding shard `shard` of ix: the lists
+ * c with owner[c] == shard keep their rows, ids and optional copies
+ * (low-precision lead, row-major tail); every other list is empty.
+ * Everything else is copied from ix (see above), so the shard's rotation,
+ * probe and eps table equal ix's.  owner: host [n_clusters] (from
+ * dade_shard_lists or the caller's own partition).  The shard keeps ix's id
+ * space: dade_index_info reports ix's n, and dade_index_export of the
+ * per-vector fields gives zeros for the vectors it does not hold.  A shard
+ * cannot be saved (dade_save_index returns DADE_EINVAL) or split again.
+ * Synchronous; ix is unchanged.  The caller frees the result with
+ * dade_free_index.
+ */
+dade_status dade_index_subset(const dade_index *ix, const int32_t *owner, int32_t shard, dade_index **out);
+
+/*
+ * Merge the results of n_shards searches of the same nq queries into the K
+ * nearest.  ids, dists: device [n_shards][nq][k] (shard-major, as an
+ * all-gather of the shards' [nq][k] results lays them out), each shard's row
+ * ascending by (distance, id) as dade_search writes it, empty places id -1 at
+ * +inf; out_ids, out_dists: device [nq][k], the k smallest (distance, id)
+ * pairs of the shards' rows, ascending (ties by id, then by shard).  A list
+ * that is on one shard only gives every id at most once.  Asynchronous on
+ * `stream`.  DADE_EINVAL on host buffers, NULL pointers or sizes out of range
+ * (1 <= k <= DADE_MAX_K, n_shards >= 1).
+ */
+dade_status dade_merge_shards(const int64_t *ids, const float *dists, int32_t n_shards, int64_t nq, int32_t k,
+                              int64_t *out_ids, float *out_dists, dade_stream stream);
+
+/*
  * Query rotation q' = W^T (q - mu) (Lemma 1, Section 3.2): the transformed
  * query that Algorithm 1 takes as input.  q: host or device [nq * d] FP32;
  * q_rot: host or device [nq * d] FP32 output.  nq = 0 is a no-op.

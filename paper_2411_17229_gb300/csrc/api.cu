@@ -626,6 +626,7 @@ dade_status dade_index_export(const dade_index *ix, int32_t field, void *dst, si
     }
     case DADE_FIELD_ROTATED: {
         DADE_TRY(need(sizeof(float) * (size_t)ix->n * d));
+        if (ix->shard >= 0) std::memset(dst, 0, bytes);   // rows of lists the shard does not hold
         std::vector<float> packed((size_t)ix->data_floats);
         std::vector<int32_t> ids((size_t)ix->slots);
         DADE_TRY_CUDA(cudaMemcpy(packed.data(), ix->data.p, sizeof(float) * packed.size(), cudaMemcpyDeviceToHost));
@@ -658,6 +659,7 @@ dade_status dade_index_export(const dade_index *ix, int32_t field, void *dst, si
         float *o = static_cast<float *>(dst);
         if (field == DADE_FIELD_LEAD_ERR) {
             DADE_TRY(need(sizeof(float) * (size_t)lnb * ix->n));
+            if (ix->shard >= 0) std::memset(dst, 0, bytes);
             std::vector<float> err((size_t)ix->slots * lnb);
             DADE_TRY_CUDA(cudaMemcpy(err.data(), ix->lead_err.p, sizeof(float) * err.size(), cudaMemcpyDeviceToHost));
             for (int c = 0; c < ix->nc; ++c) {
@@ -668,6 +670,7 @@ dade_status dade_index_export(const dade_index *ix, int32_t field, void *dst, si
             return DADE_OK;
         }
         DADE_TRY(need(sizeof(float) * (size_t)ix->n * ix->lead_dims));
+        if (ix->shard >= 0) std::memset(dst, 0, bytes);
         std::vector<unsigned char> codes(ix->lead.bytes);
         DADE_TRY_CUDA(cudaMemcpy(codes.data(), ix->lead.p, codes.size(), cudaMemcpyDeviceToHost));
         for (int c = 0; c < ix->nc; ++c) {

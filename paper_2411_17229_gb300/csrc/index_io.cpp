@@ -105,6 +105,8 @@ size_t lead_code_bytes(const Scalars &s) {
 } // namespace
 
 dade_status save_index(const dade_index *ix, const char *path) {
+    DADE_CHECK_ARG(ix->shard < 0, "a shard (dade_index_subset) is not saved: save the full index and take the "
+                                  "shard after loading it");
     File fh;
     fh.f = fopen(path, "wb");
     if (!fh.f) {

@@ -123,6 +123,7 @@ struct dade_index {
     int32_t tail_nb0 = 0, tail_w = 0;
     dade::DevBuf tail;
     int64_t data_floats = 0, slots = 0;
+    int32_t shard = -1;     // dade_index_subset: the shard this index holds (-1: every list)
     // workspace (grown on demand, reused across calls)
     mutable dade::Workspace ws0;   // used unless a WorkspaceScope is active on the calling thread
 };

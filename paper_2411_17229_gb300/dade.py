@@ -106,6 +106,9 @@ SIGNATURES = {
     "dade_probe_noalloc": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp]),
     "dade_fp32_fma_peak": (_i32, [_i32, _vp, _vp]),
     "dade_set_alloc_hook": (None, [_vp, _vp]),
+    "dade_shard_lists": (_i32, [_vp, _i32, _i32, _vp]),
+    "dade_index_subset": (_i32, [_vp, _vp, _i32, _vp]),
+    "dade_merge_shards": (_i32, [_vp, _vp, _i32, _i64, _i32, _vp, _vp, _vp]),
     "dade_last_error": (C.c_char_p, []),
     "dade_version": (C.c_char_p, []),
 }
@@ -126,6 +129,22 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def shard_lists(list_rows, n_shards: int):
+    """dade_shard_lists: owner[c] of every list, lists dealt to n_shards shards balanced by rows."""
+    rows = np.ascontiguousarray(list_rows, dtype=np.int64)
+    owner = np.empty(rows.shape[0], np.int32)
+    _check(lib().dade_shard_lists(rows.ctypes.data, int(rows.shape[0]), int(n_shards), owner.ctypes.data))
+    return owner
+
+
+def merge_shards(ids, dists, out_ids, out_dists, stream=None):
+    """dade_merge_shards: ids / dists device [G, nq, K] -> the K nearest per query in out_* [nq, K]."""
+    g, nq, k = ids.shape
+    _check(lib().dade_merge_shards(_ptr(ids), _ptr(dists), int(g), int(nq), int(k), _ptr(out_ids), _ptr(out_dists),
+                                   _stream(stream)))
+    return out_ids, out_dists
 
 
 def fp32_fma_peak(iters: int = 4096, stream=None) -> float:
@@ -215,6 +234,24 @@ class Index:
 
     def save(self, path):
         _check(lib().dade_save_index(self._h, os.fsencode(path)))
+
+    def list_sizes(self):
+        """Rows of every inverted list (from the exported assignment)."""
+        return np.bincount(self.export(FIELD_ASSIGN), minlength=self.n_clusters).astype(np.int64)
+
+    def subset(self, owner, shard):
+        """dade_index_subset: a new index holding the lists c with owner[c] == shard (the rest empty)."""
+        own = np.ascontiguousarray(owner, dtype=np.int32)
+        assert own.shape[0] == self.n_clusters
+        h = C.c_void_p()
+        _check(lib().dade_index_subset(self._h, own.ctypes.data, int(shard), C.byref(h)))
+        sub = Index.__new__(Index)
+        sub._h = h
+        info = Info()
+        _check(lib().dade_index_info(h, C.byref(info)))
+        sub.info = info
+        sub.n, sub.d, sub.n_clusters = info.n, info.d, info.n_clusters
+        return sub
 
     def close(self):
         if getattr(self, "_h", None):
