@@ -72,7 +72,8 @@ def _scan_batch(ix, queries, K, pt):
     ix.rotate(q, qr)
     ix.probe(qr, pt["nprobe"], pr)
     ix.scan(qr, pr, K, pt["alpha"], pt["delta_d"], ids, d, tile=pt["tile"], threads=pt["threads"],
-            schedule=pt["schedule"], seed_lists=pt["seed_lists"], flags=pt["flags"])
+            schedule=pt["schedule"], seed_lists=pt["seed_lists"], flags=pt["flags"],
+            list_chunk=pt.get("list_chunk", 0))
     ix.sync()
     return pr.cpu().numpy(), ids.cpu().numpy(), d.cpu().numpy()
 
@@ -182,20 +183,28 @@ def test_c5_full_size_serving():
 def test_c4_full_size_benchmark_point():
     """10M x 768 normalised mixture over 16,384 components with Zipf(1.1)
     weights (largest list 1.47M, median 72), lists = the generating
-    components, 10,000 queries, K = 10, at the benchmark's point: tile
-    schedule (tile 128, 128 threads), delta_d 32, alpha 0.8, nprobe 8, query
-    order; index with the FP8 leading-block copy.  The FP8 prefilter at the
-    same point must return the FP32 path's results bit for bit."""
+    components, 10,000 queries, K = 10, at the benchmark's point: row rounds
+    from 16 rows, work items of 1,024 rows, delta_d 32, alpha 0.95, nprobe 10,
+    query order, row-major tail from dim 32, the tensor-core prefilter; index
+    with the FP8 leading-block copy.  At full size the tensor-core prefilter
+    must return the FP32 list-major path's results bit for bit, and the FP8
+    prefilter (which runs the rounds query-major on the tile kernel) the
+    same kernel's FP32 results."""
     w = synth.WORKLOADS["c4_zipf_10m_d768"]
     base, queries, labels = synth.make(w)
     pairs = synth.eps_pairs(w.n, 20000)
     ix = dade.Index(torch.from_numpy(base).cuda(), w.n_clusters, assign=labels, pairs=pairs,
-                    lead_format=dade.LEAD_FP8, lead_dims=64)
-    pt = {"nprobe": 8, "alpha": 0.8, "delta_d": 32, "tile": 128, "threads": 128, "schedule": dade.SCHED_TILE,
-          "seed_lists": 0, "flags": dade.FLAG_QUERY_ORDER}
+                    lead_format=dade.LEAD_FP8, lead_dims=64, tail_from=32)
+    pt = {"nprobe": 10, "alpha": 0.95, "delta_d": 32, "tile": 16, "threads": 128, "schedule": dade.SCHED_ROUNDS,
+          "seed_lists": 0, "list_chunk": 1024,
+          "flags": dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL | dade.FLAG_TC_PREFILTER}
     probe, ids, dists = _scan_batch(ix, queries, w.k, pt)
-    _, ids8, dists8 = _scan_batch(ix, queries, w.k, dict(pt, flags=pt["flags"] | dade.FLAG_LEAD))
-    assert np.array_equal(ids, ids8) and np.array_equal(dists.view(np.uint32), dists8.view(np.uint32))
+    _, idsf, distsf = _scan_batch(ix, queries, w.k, dict(pt, flags=pt["flags"] & ~dade.FLAG_TC_PREFILTER))
+    assert np.array_equal(ids, idsf) and np.array_equal(dists.view(np.uint32), distsf.view(np.uint32))
+    split = dict(pt, flags=(pt["flags"] & ~dade.FLAG_TC_PREFILTER) | dade.FLAG_SEED_SPLIT)
+    _, idss, distss = _scan_batch(ix, queries, w.k, split)
+    _, ids8, dists8 = _scan_batch(ix, queries, w.k, dict(split, flags=split["flags"] | dade.FLAG_LEAD))
+    assert np.array_equal(idss, ids8) and np.array_equal(distss.view(np.uint32), dists8.view(np.uint32))
     sample = np.sort(np.random.default_rng(17).choice(queries.shape[0], N_SAMPLE, replace=False))
     orc = oracle.SampledIndex(base, labels, w.n_clusters, pairs, queries[sample], pt["nprobe"])
     same = [np.array_equal(probe[s], orc.probe[i]) for i, s in enumerate(sample) if not orc.probe_tie[i]]
@@ -208,5 +217,7 @@ def test_c4_full_size_benchmark_point():
 
     summary = parity.compare(ids[sample], dists[sample], o, exact_d, same_probe=same_probe)
     print(f"c4: {summary}")
+    summary = parity.compare(idss[sample], distss[sample], o, exact_d, same_probe=same_probe)
+    print(f"c4 (rounds on the tile kernel): {summary}")
     _check_properties(base, queries, ids, dists)
     ix.close()
