@@ -26,6 +26,7 @@ oracle on the host cores instead (the reference arm).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -112,9 +113,12 @@ def run_profile(args):
     libbuild.build()
     w = synth.WORKLOADS[args.workload]
     n, nq = args.n or w.n, args.nq or w.nq
-    nc = w.n_clusters if n == w.n else max(16, n // 244)
+    if w.lists_are_components and n != w.n:
+        # a scaled-down case of the same structure: components (= lists) in proportion to n
+        w = dataclasses.replace(w, n=n, n_comp=max(64, w.n_comp * n // w.n), n_clusters=max(64, w.n_comp * n // w.n))
+    nc = w.n_clusters if (n == w.n or w.lists_are_components) else max(16, n // 244)
     base, queries, labels = synth.make(w, n=n, nq=nq)
-    given = {"assign": labels} if w.lists_are_components and n == w.n else {}
+    given = {"assign": labels} if w.lists_are_components else {}
     lf, ld = lead_opts(args, dade, w.d)
     ix = dade.Index(torch.from_numpy(base).cuda(), nc, kmeans_iters=w.kmeans_iters, seed=synth.SEED_KMEANS,
                     lead_format=lf, lead_dims=ld, tail_from=tail_opt(args, w.d), **given)

@@ -645,9 +645,13 @@ constexpr uint32_t TC_COLS = 128;   // tensor-memory columns: two FP32 accumulat
 constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TCN >> 3) << 17) |
                               ((uint32_t)(LTC >> 4) << 24);
 
+// Staged tiles of k_lm_tc: a ring of four for increments of up to 32 dims, two
+// for 64 dims (two blocks per SM must fit; see the tile loop).
+constexpr int tc_ring(int gb) { return gb >= 4 ? 2 : 4; }
+
 struct TcSmem {   // dynamic shared memory of k_lm_tc (1024-byte aligned base)
     static constexpr size_t a_bytes(int gb) { return (size_t)gb * 4 * LTC * 16; }   // FP32 rows of one tile
-    static constexpr size_t b_off(int gb) { return 2 * a_bytes(gb); }                // two tiles in flight
+    static constexpr size_t b_off(int gb) { return tc_ring(gb) * a_bytes(gb); }     // the ring of tiles
     static constexpr size_t b_bytes(int gb) { return (size_t)gb * 4 * TCN * 16; }
     static constexpr size_t qs_off(int gb) { return b_off(gb) + b_bytes(gb); }
     static constexpr size_t sv_off(int gb) { return qs_off(gb) + sizeof(float) * LG * 16 * gb; }
@@ -696,12 +700,35 @@ __device__ __forceinline__ uint32_t tf32_rna_bits(float x) {
     return r;
 }
 
+// The list of work item `item`: the last c with item_off[c] <= item (warp-wide,
+// every lane returns it).  A block takes items in increasing order, so the search
+// starts at the list of its previous item (`from`, with item_off[from] <= item):
+// one round trip when the item is in one of the next 32 lists, then a 32-way
+// search (each step one round trip, the range shrinking 32-fold).
+__device__ __forceinline__ int find_list(const int *__restrict__ off, int nc, int item, int from, int lane) {
+    {
+        const int idx = from + 1 + lane;
+        const int cnt = __popc(__ballot_sync(0xffffffffu, idx < nc && __ldg(off + idx) <= item));
+        if (cnt < 32) return from + cnt;
+    }
+    int lo = from + 32, hi = nc;
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) >> 5;
+        const int idx = lo + (lane + 1) * step;
+        lo += __popc(__ballot_sync(0xffffffffu, idx < hi && __ldg(off + idx) <= item)) * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
+
 template <int GB, bool STATS>
 __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_constant__ CUtensorMap tmap) {
+    constexpr int NA = tc_ring(GB);                 // staged tiles
+    constexpr int PRE = NA == 2 ? 2 : NA - 1;       // tiles queued before an item's first MMA
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[2], mdone[2];
+    __shared__ __align__(8) uint64_t full[NA], mdone[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int s_item, s_q[LG];
+    __shared__ int s_item, s_next, s_c, s_q[LG];
     __shared__ float s_r2[LG], s_qn[LG], s_qcn[LG], s_thr[LG], s_thr2[LG];
     __shared__ KBest kb;
     const bool kbest = a.k <= KB_K;
@@ -721,35 +748,39 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(su32(&full[b]), 1);
-            mbar_init(su32(&mdone[b]), 1);
-        }
+        for (int b = 0; b < NA; ++b) mbar_init(su32(&full[b]), 1);
+        for (int b = 0; b < 2; ++b) mbar_init(su32(&mdone[b]), 1);
         fence_mbar_init();
+        s_item = (int)atomicAdd(a.ctr, 1u);
     }
     if (tid < LNW * QSLOT) kb.cnt[tid / QSLOT][tid % QSLOT] = 0;
     lt_fence_before();
     __syncthreads();
     lt_fence_after();
     const uint32_t tmem = tmem_base;
-    uint32_t used[2] = {0u, 0u}, mph[2] = {0u, 0u};   // completed waits per copy buffer / accumulator
-    int inflight[2] = {0, 0};                         // thread 0: copies issued and not waited on
-    bool mpend[2] = {false, false};                   // thread 0: MMAs committed and not waited on
+    uint32_t used[NA], mph[2] = {0u, 0u};   // completed waits per staged tile / accumulator
+    int inflight[NA];                       // thread 0: copies issued and not waited on
+#pragma unroll
+    for (int b = 0; b < NA; ++b) {
+        used[b] = 0u;
+        inflight[b] = 0;
+    }
+    bool mpend[2] = {false, false};         // thread 0: MMAs committed and not waited on
     bool failed = false;
     const int total = a.item_off[a.nc];
+    int c = 0;                              // the list of the previous item
 
     for (;;) {
-        if (tid == 0) s_item = (int)atomicAdd(a.ctr, 1u);
-        __syncthreads();
+        __syncthreads();   // s_item is set; the previous item's shared state is no longer read
         const int item = s_item;
         if (item >= total) break;
-        int lo = 0, hi = a.nc;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (__ldg(a.item_off + mid) <= item) lo = mid;
-            else hi = mid;
+        if (tid == 32) s_next = (int)atomicAdd(a.ctr, 1u);   // the next item, fetched while this one runs
+        if (warp == 0) {
+            const int cl = find_list(a.item_off, a.nc, item, c, lane);
+            if (lane == 0) s_c = cl;
         }
-        const int c = lo;
+        __syncthreads();
+        c = s_c;
         const int ngroups = (a.lq_off[c + 1] - a.lq_off[c] + LG - 1) / LG;
         const int local = item - a.item_off[c];
         const int qb = a.lq_off[c] + (local % ngroups) * LG;
@@ -760,7 +791,7 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         const int ntile = min(max(0, (rend - a.row_lo + LTC - 1) / LTC), t0 + a.chunk_tiles);
         const int64_t brow = m.base >> 4;   // row (16 floats) of block 0, member 0 of list c
         auto issue = [&](int t) {   // thread 0: the tile's FP32 rows, GB blocks x 4 boxes
-            const int buf = t & 1, i0 = a.row_lo + t * LTC;
+            const int buf = t % NA, i0 = a.row_lo + t * LTC;
             const uint32_t bar = su32(&full[buf]);
             mbar_expect_tx(bar, (uint32_t)(GB * 4 * LTC * 16));
             unsigned char *dst = abuf + (size_t)buf * TcSmem::a_bytes(GB);
@@ -771,14 +802,14 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
             ++inflight[buf];
         };
         auto mma = [&](int t) -> bool {   // thread 0: wait for tile t's rows, then its MMAs
-            const int buf = t & 1;
-            if ((used[0] | used[1]) == 0 && a.never != nullptr && !wait_word(a.never, a.wait_ns)) return false;
+            const int buf = t % NA;
+            if (a.never != nullptr && (used[0] | used[1]) == 0 && !wait_word(a.never, a.wait_ns)) return false;
             if (!wait_bounded(su32(&full[buf]), used[buf] & 1u, a.wait_ns)) return false;
             ++used[buf];
             --inflight[buf];
             lt_fence_after();
             const uint32_t ab = su32(abuf + (size_t)buf * TcSmem::a_bytes(GB)), bb = su32(bsm);
-            const uint32_t d = tmem + (uint32_t)(buf * TCN);
+            const uint32_t d = tmem + (uint32_t)((t & 1) * TCN);
 #pragma unroll
             for (int b = 0; b < GB; ++b)
 #pragma unroll
@@ -786,12 +817,12 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
                     lt_mma(d, lt_desc(ab + (uint32_t)((b * 4 + 2 * s2) * LTC * 16), LTC * 16, 128),
                            lt_desc(bb + (uint32_t)((b * 4 + 2 * s2) * TCN * 16), TCN * 16, 128),
                            (b > 0 || s2 > 0) ? 1u : 0u);
-            lt_commit(su32(&mdone[buf]));
-            mpend[buf] = true;
+            lt_commit(su32(&mdone[t & 1]));
+            mpend[t & 1] = true;
             return true;
         };
         if (tid == 0)
-            for (int t = t0; t < t0 + 2 && t < ntile; ++t) issue(t);
+            for (int t = t0; t < t0 + PRE && t < ntile; ++t) issue(t);
         for (int g = tid; g < LG; g += LNT) {
             const bool in = g < ng;
             const int q = in ? a.lq_items[qb + g] : 0;
@@ -830,9 +861,15 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         __syncthreads();
         if (tid == 0 && t0 < ntile && !mma(t0)) failed = true;
 
+        // Tile t: thread 0 queues tile t + 1's MMAs (they run during this tile's reads),
+        // waits for tile t's, and the block meets; with a ring of four, tile t + 3's rows
+        // are then queued into the slot tile t - 1 left (every thread is past its reads).
+        // The epilogue reads accumulator t & 1 and writes the masks; a second barrier;
+        // then the FP32 path of the kept pairs from the staged rows.  With a ring of two,
+        // a third barrier frees tile t's slot for tile t + 2.
         for (int t = t0; t < ntile; ++t) {
             const int buf = t & 1, i0 = a.row_lo + t * LTC, tn = min(LTC, rend - i0);
-            const float *af = reinterpret_cast<const float *>(abuf + (size_t)buf * TcSmem::a_bytes(GB));
+            const float *af = reinterpret_cast<const float *>(abuf + (size_t)(t % NA) * TcSmem::a_bytes(GB));
             if (tid == 0 && !failed && t + 1 < ntile && !mma(t + 1)) failed = true;   // overlaps this tile's reads
             bool ok = !failed;
             if (tid == 0 && ok) {
@@ -845,6 +882,9 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
+            }
+            if constexpr (NA > 2) {
+                if (tid == 0 && t + NA - 1 < ntile) issue(t + NA - 1);
             }
             lt_fence_after();
             {   // candidate mrow against the queries of half qh
@@ -938,8 +978,10 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
                 }
                 __syncwarp();
             }
-            __syncthreads();   // the rows of buffer `buf`, the masks and accumulator `buf` are free
-            if (tid == 0 && t + 2 < ntile) issue(t + 2);
+            if constexpr (NA == 2) {
+                __syncthreads();   // tile t's slot, the masks and accumulator `buf` are free
+                if (tid == 0 && t + 2 < ntile) issue(t + 2);
+            }
         }
         if (failed) break;
         __syncwarp();
@@ -948,13 +990,14 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         __syncwarp();
         if (kbest)   // the item's K best per query go to the accept buffers
             for (int g = warp; g < ng; g += LNW) kb_flush(a, kb, warp, g / LNW, s_q[g]);
+        if (tid == 32) s_item = s_next;
     }
     if (failed && tid == 0) {   // let the copies and MMAs in flight finish (bounded) before leaving
         atomicExch(a.err, (int)DADE_ETIMEOUT);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NA; ++b)
             if (inflight[b] > 0) wait_bounded(su32(&full[b]), used[b] & 1u, 10000000ull);
+        for (int b = 0; b < 2; ++b)
             if (mpend[b]) wait_bounded(su32(&mdone[b]), mph[b] & 1u, 10000000ull);
-        }
     }
     lt_fence_before();
     __syncthreads();
