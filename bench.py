@@ -519,31 +519,6 @@ def recall_at_k(torch, xb, q, ids, gt_kth, K):
 SCHED_NAMES = {0: "tile", 1: "pipelined", 2: "seeded", 3: "rounds"}
 
 
-def dade_variants(dade, w, lf):
-    """Execution variants the autotuner tries on a workload: (schedule, tile,
-    threads, flags, seed_lists, stage_dims, list_chunk).  tile is the first
-    round's rows for the row-rounds schedule."""
-    nb = (w.d + 15) // 16
-    list_major = nb >= 8
-    lead = (dade.FLAG_LEAD,) if lf else ()
-    v = []
-    tc = (dade.FLAG_TC_PREFILTER,) if list_major else ()
-    if w.comp_zipf > 0:   # very uneven lists: doubling row windows, split over many thread blocks
-        v += [(dade.SCHED_ROUNDS, r1, 128, fl, 0, 0, ch) for r1 in (16, 32, 64) for ch in (512, 1024)
-              for fl in (0,) + tc]
-        v += [(dade.SCHED_TILE, 128, 128, 0, 0, 0, 0)]
-        return v
-    v += [(dade.SCHED_TILE, tile, nt, fl, 0, 0, 0) for tile in (128, 256) for fl in (0,) + lead for nt in (128, 256)]
-    if list_major:
-        v += [(dade.SCHED_SEEDED, tile, 128, fl, seed, 0, 0) for seed in (2, 3, 4) for tile in (128, 256)
-              for fl in (0,) + tc]
-        v += [(dade.SCHED_ROUNDS, r1, 128, fl, 0, 0, 0) for r1 in (16, 32, 64) for fl in (0,) + tc]
-    v += [(dade.SCHED_SEEDED, 128, nt, dade.FLAG_SEED_SPLIT, seed, 0, 0) for seed in (2, 3) for nt in (128, 256)]
-    if w.d > 128:
-        v += [(dade.SCHED_TILE, 128, 256, 0, 0, sd, 0) for sd in (64, 128)]
-    return v
-
-
 def precision_of(point, lf, dade):
     if point.get("flags", 0) & dade.FLAG_LEAD:
         return {dade.LEAD_BF16: "bf16 lead blocks", dade.LEAD_FP8: "fp8-e4m3 lead blocks"}.get(lf, "fp32")
@@ -672,41 +647,17 @@ def measure_workload(args, wname, rank, world, dist, headline):
             if r is not None and r[1] >= RECALL_TARGET and r[0] < fd_best[0]:
                 fd_best = (r[0], r[1], pt)
     n0 = min(p for p in grid if fd_rec.get(p, 0) >= RECALL_TARGET) if fd_best else grid[-1]
-    variants = dade_variants(dade, w, lf)
-    dds, alphas = (16, 32, 64), (0.1, 0.3, 0.5, 0.8, 0.9, 0.95, 0.98)
-    if fd_best is not None and fd_best[0] > 50.0:   # a large workload: a narrower sweep
-        dds, alphas = (32, 64), (0.5, 0.8, 0.9, 0.95)
-    elif not headline:                              # an extra key: a shorter sweep
-        dds, alphas = (32, 64), (0.5, 0.8, 0.95, 0.98)
-    tried = []
-    for dd in dds:
-        for alpha in alphas:
-            for schedule, tile, threads, fl, seed, sd, chunk in variants:
-                if sd and (sd <= dd or sd % dd):
-                    continue
-                if fl & dade.FLAG_LEAD and min(dd, (w.d + 15) // 16 * 16) > ld:
-                    continue
-                for nprobe in [p for p in grid if p >= n0][:3]:
-                    pt = {"mode": dade.MODE_DADE, "nprobe": nprobe, "alpha": alpha, "delta_d": dd, "spec": 8,
-                          "tile": tile, "threads": threads, "schedule": schedule,
-                          "flags": (fl | fixed) | (dade.FLAG_GENERIC_KERNEL if sd else 0),
-                          "seed_lists": seed, "stage_dims": sd, "list_chunk": chunk}
-                    r = measure(pt)
-                    if r is None:
-                        continue
-                    tried.append((r[0], r[1], pt))
-                    if r[1] >= RECALL_TARGET:
-                        break
-    # re-time the fastest few over more scans before choosing
-    dade_best = None
-    for ms_, rc_, pt_ in sorted((t for t in tried if t[1] >= RECALL_TARGET), key=lambda t: t[0])[:6]:
-        r = measure(pt_, reps=12)
-        if r is not None and r[1] >= RECALL_TARGET and (dade_best is None or r[0] < dade_best[0]):
-            dade_best = (r[0], r[1], pt_)
-    for ms_, rc_, pt_ in sorted(tried, key=lambda t: t[0])[:8]:
-        log(f"[bench]   {ms_:.3f} ms recall {rc_:.4f} {pt_}")
-    if dade_best is None:
-        dade_best = min(tried, key=lambda t: (-t[1], t[0]))
+    # DADE: the library's autotuner (dade_autotune) on this batch against its exact
+    # neighbours; the bench then re-times the chosen point over more scans
+    t1 = time.time()
+    at = ix.autotune(q, K, gt_ids.cpu().numpy(), recall_target=RECALL_TARGET, reps=3, stream=sh)
+    point = {"mode": dade.MODE_DADE, "nprobe": at["nprobe"], "alpha": at["alpha"], "delta_d": at["delta_d"],
+             "spec": 8, "stage_dims": 0, **at["point"]}
+    r = measure(point, reps=12)
+    dade_best = (r[0], r[1], point)
+    tuner = {"entry_point": "dade_autotune", "seconds": round(time.time() - t1, 1),
+             "points_tried": at["points_tried"], "recall_on_batch": round(at["recall"], 5),
+             "ms_probe_and_scan": round(at["ms"], 4)}
     point = dade_best[2]
     tune_s = time.time() - t0
     log(f"[bench] {wname}: autotune {tune_s:.1f}s: FD {fd_best[2] if fd_best else None} "
@@ -993,6 +944,7 @@ def measure_workload(args, wname, rank, world, dist, headline):
         "clocks": clocks,
         "cpu_baseline": cpu,
         "wall_s_timed_region": round(wall, 3),
+        "autotune": tuner,
         "setup_s": {"index_build": round(build_s, 1), "autotune": round(tune_s, 1),
                     "total": round(time.time() - t_all, 1)},
     }

@@ -509,6 +509,68 @@ dade_status dade_tune(const dade_index *ix, const float *q_rot, const int32_t *p
                       float *dists, dade_stream stream);
 
 /*
+ * ---- Operating point for a recall target (library autotuner) -------------------
+ * The paper fixes P_s (alpha) and delta_d by hand (Section 4.1) and sweeps
+ * nprobe for its recall-QPS curves.  dade_autotune finds, on the caller's
+ * sample of queries and their exact K nearest ids, the fastest point whose
+ * recall@K reaches a target: the smallest rung of an nprobe ladder at which
+ * FDScanning (exact distances of the probed lists, the best any DCO can
+ * return there) reaches the target, and the next two rungs; at each, delta_d
+ * in {16, 32, 64} (<= D_pad), the execution variants the index serves (tile
+ * schedule, with the low-precision prefilter when the index has the copy;
+ * seeded schedule with 2 or 3 seed lists, later lists list-major or split over
+ * thread blocks; row rounds from 16 or 32 rows with
+ * work items of the default size or of 1,024 rows, and with the tensor-core
+ * prefilter where D > 112), and alpha from 0.98
+ * down to 0.05 until the recall is reached; every passing point is timed
+ * (dade_probe + dade_scan, CUDA events on `stream`) and the fastest kept,
+ * then dade_tune adds the result-neutral options.  The result is cached in
+ * the process and, with cache_path, appended to a JSON-lines file (one flat
+ * object per line), keyed by a fingerprint of the index (sizes, eigenvalues,
+ * list sizes, copies), K, the recall target, the sample size (power-of-two
+ * bucket) and the GPU (name, SM count); a later call with the same key
+ * returns the cached point without timing anything (from_cache = 1).
+ */
+enum {
+    DADE_AUTOTUNE_FORCE = 1    /* sweep even when the cache holds the key (and append the new point) */
+};
+
+typedef struct {
+    float recall_target;       /* recall@K the point must reach on the queries given (default 0.95) */
+    int32_t n_nprobe;          /* entries of nprobe_ladder; 0: 4, 6, 8, 10, 12, 16, ... up to min(N_c, 512) */
+    const int32_t *nprobe_ladder;  /* host [n_nprobe], ascending, within 1 .. n_clusters */
+    int32_t reps;              /* timed runs per point (default 3) */
+    int32_t flags;             /* DADE_AUTOTUNE_* */
+    const char *cache_path;    /* JSON-lines cache file, read and appended (NULL: the process cache only) */
+    int32_t reserved[4];
+} dade_autotune_opts;
+
+typedef struct {
+    int32_t nprobe, delta_d;
+    float alpha;
+    dade_search_opts opts;     /* mode, schedule, tile, seed_lists, list_chunk, threads, flags of the point;
+                                  stats and lead_stats NULL */
+    float recall;              /* recall@K on the queries given */
+    float ms;                  /* mean time of probe + scan of the queries given */
+    int32_t from_cache;        /* 1: returned from the cache, nothing was timed */
+    int32_t points_tried;      /* searches run by the sweep */
+} dade_autotune_result;
+
+void dade_autotune_opts_default(dade_autotune_opts *opts);
+
+/*
+ * q: host or device [nq * d] raw queries (rotated by the call); gt_ids: host
+ * [nq * k], each query's exact K nearest base ids (any order).  Synchronous
+ * on `stream`; allocates its scratch on the device (the allocation hook
+ * applies).  DADE_EINVAL on NULL pointers, a device gt_ids, sizes out of
+ * range or a ladder that does not ascend within 1 .. n_clusters;
+ * DADE_EUNSUPPORTED when no point of the ladder reaches the target (the
+ * message says whether the exact scan does).
+ */
+dade_status dade_autotune(const dade_index *ix, const float *q, int64_t nq, int32_t k, const int64_t *gt_ids,
+                          const dade_autotune_opts *opts, dade_autotune_result *out, dade_stream stream);
+
+/*
  * End-to-end query: dade_rotate_queries followed by dade_search, on raw
  * queries.  q: host or device [nq * d].  Same outputs and limits as
  * dade_search.  With host buffers the call copies inputs in and results out

@@ -21,6 +21,7 @@ SCHED_TILE, SCHED_PIPELINED, SCHED_SEEDED, SCHED_ROUNDS = 0, 1, 2, 3
 FLAG_GENERIC_KERNEL, FLAG_LEAD, FLAG_QUERY_ORDER, FLAG_ROW_TAIL, FLAG_SEED_SPLIT = 1, 2, 4, 8, 16
 FLAG_TC_PREFILTER = 32
 FLAG_CHECK_TIMEOUT = 64
+AUTOTUNE_FORCE = 1
 LEAD_NONE, LEAD_BF16, LEAD_FP8 = 0, 1, 2
 TRANSFORM_PCA, TRANSFORM_RANDOM, TRANSFORM_GIVEN = 0, 1, 2
 ESTIMATOR_DADE, ESTIMATOR_ADSAMPLING = 0, 1
@@ -51,6 +52,15 @@ class SearchOpts(C.Structure):
                 ("lead_stats", C.c_void_p), ("seed_lists", C.c_int32), ("estimator", C.c_int32),
                 ("eps0", C.c_float), ("stage_dims", C.c_int32), ("list_chunk", C.c_int32),
                 ("stage_ring", C.c_int32), ("wait_ns", C.c_int64)]
+
+class AutotuneOpts(C.Structure):
+    _fields_ = [("recall_target", C.c_float), ("n_nprobe", C.c_int32), ("nprobe_ladder", C.c_void_p),
+                ("reps", C.c_int32), ("flags", C.c_int32), ("cache_path", C.c_char_p), ("reserved", C.c_int32 * 4)]
+
+
+class AutotuneResult(C.Structure):
+    _fields_ = [("nprobe", C.c_int32), ("delta_d", C.c_int32), ("alpha", C.c_float), ("opts", SearchOpts),
+                ("recall", C.c_float), ("ms", C.c_float), ("from_cache", C.c_int32), ("points_tried", C.c_int32)]
 
 
 class ServerOpts(C.Structure):
@@ -107,6 +117,8 @@ SIGNATURES = {
     "dade_fp32_fma_peak": (_i32, [_i32, _vp, _vp]),
     "dade_set_alloc_hook": (None, [_vp, _vp]),
     "dade_shard_lists": (_i32, [_vp, _i32, _i32, _vp]),
+    "dade_autotune_opts_default": (None, [_vp]),
+    "dade_autotune": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp]),
     "dade_index_subset": (_i32, [_vp, _vp, _i32, _vp]),
     "dade_merge_shards": (_i32, [_vp, _vp, _i32, _i64, _i32, _vp, _vp, _vp]),
     "dade_last_error": (C.c_char_p, []),
@@ -234,6 +246,32 @@ class Index:
 
     def save(self, path):
         _check(lib().dade_save_index(self._h, os.fsencode(path)))
+
+    def autotune(self, q, k, gt_ids, recall_target=0.95, ladder=None, reps=3, force=False, cache_path=None,
+                 stream=None):
+        """dade_autotune: the fastest (nprobe, delta_d, alpha, options) whose recall@k on the queries q
+        (host or device [nq, d]) against their exact neighbours gt_ids (host [nq, k]) reaches the
+        target.  Returns a dict; ``point`` holds the keyword arguments of query()/search()."""
+        o = AutotuneOpts()
+        lib().dade_autotune_opts_default(C.byref(o))
+        o.recall_target, o.reps = float(recall_target), int(reps)
+        o.flags = AUTOTUNE_FORCE if force else 0
+        lad = None
+        if ladder is not None:
+            lad = np.ascontiguousarray(ladder, dtype=np.int32)
+            o.n_nprobe, o.nprobe_ladder = int(lad.shape[0]), lad.ctypes.data
+        if cache_path is not None:
+            o.cache_path = os.fsencode(cache_path)
+        gt = np.ascontiguousarray(gt_ids, dtype=np.int64)
+        assert gt.shape == (q.shape[0], k)
+        r = AutotuneResult()
+        _check(lib().dade_autotune(self._h, _ptr(q), q.shape[0], int(k), gt.ctypes.data, C.byref(o), C.byref(r),
+                                   _stream(stream)))
+        so = r.opts
+        point = dict(mode=so.mode, tile=so.tile, threads=so.threads, schedule=so.schedule, flags=so.flags,
+                     seed_lists=so.seed_lists, list_chunk=so.list_chunk)
+        return {"nprobe": r.nprobe, "delta_d": r.delta_d, "alpha": r.alpha, "point": point, "recall": r.recall,
+                "ms": r.ms, "from_cache": bool(r.from_cache), "points_tried": r.points_tried}
 
     def list_sizes(self):
         """Rows of every inverted list (from the exported assignment)."""
