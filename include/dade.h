@@ -55,7 +55,8 @@ typedef enum {
     DADE_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
     DADE_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
     DADE_EUNSUPPORTED = 5,  /* valid request the library does not implement */
-    DADE_EIO = 6            /* file could not be read or written */
+    DADE_EIO = 6,           /* file could not be read or written */
+    DADE_ECANCELLED = 7     /* a server request was cancelled (dade_server_cancel) */
 } dade_status;
 
 enum {
@@ -340,13 +341,18 @@ void dade_graph_free(dade_graph *g);
  * thread into slots as slots free up: each slot is a CUDA stream with its
  * own device workspace and pinned buffers, so batches in different slots
  * overlap on the GPU.  A batch is the oldest pending request plus every
- * later pending request with the same K, nprobe, alpha and delta_d, up to
- * max_batch queries.  Every query's result depends only on that query, so a
- * request gets the same result alone and in any mix.  The slot count is cut
- * to what device_budget holds (an estimate per slot is reported in the
- * statistics).  The caller's query and result buffers must stay valid until
- * dade_server_wait returns for the ticket.  dade_server_free drains the
- * queue and the slots.
+ * later pending request it can run with, up to max_batch queries: under the
+ * tile schedule every request with the same alpha and delta_d (mixed K and
+ * nprobe run in one launch, dade_query_mixed), under the other schedules the
+ * same K, nprobe, alpha and delta_d.  Every query's result depends only on
+ * that query, so a request gets the same result alone and in any mix.  With
+ * a device_budget, admission is by bytes: a batch starts only while every
+ * slot's staging buffers plus the workspace the slots' batches grew to (an
+ * estimate from the batch's queries, largest K and largest nprobe) stay
+ * within the budget; a request that cannot fit even alone completes with
+ * DADE_ENOMEM.  The caller's query and result buffers must stay valid until
+ * dade_server_wait returns for the ticket (or dade_server_cancel returns).
+ * dade_server_free drains the queue and the slots.
  */
 typedef struct dade_server dade_server;
 typedef struct {
@@ -354,13 +360,15 @@ typedef struct {
     int32_t max_batch;         /* queries per batch, and per request (default 1024) */
     int32_t max_k;             /* largest K of a request (default 100) */
     int32_t max_nprobe;        /* largest nprobe of a request (default 128) */
-    int64_t device_budget;     /* device bytes for the slots (0: no limit); fewer slots if needed */
+    int64_t device_budget;     /* device bytes of the server: slots' staging buffers and the workspace
+                                  admitted batches grow (0: no limit); fewer slots if even one request
+                                  would not fit beside their staging buffers */
     int32_t mode, tile, threads, schedule, seed_lists, flags;   /* dade_search_opts of every batch */
     int32_t stage_dims;        /* dade_search_opts.stage_dims of every batch (0: delta_d) */
     int32_t reserved[3];
 } dade_server_opts;
 typedef struct {
-    int64_t slots, slot_bytes;          /* slots created, device bytes budgeted per slot */
+    int64_t slots, slot_bytes;          /* slots created, device bytes of a slot running a full batch */
     int64_t requests, requests_done;    /* submitted, completed */
     int64_t batches, queries;           /* batches launched, queries in them */
     int64_t max_inflight;               /* most batches on the GPU at once */
@@ -373,6 +381,10 @@ dade_status dade_server_submit(dade_server *s, const float *q, int64_t nq, int32
 /* Wait for a ticket (timeout_ms < 0: no limit; DADE_ETIMEOUT if it expires, the ticket stays valid).
  * latency_s (may be NULL): seconds from submit to completion. */
 dade_status dade_server_wait(dade_server *s, uint64_t ticket, int64_t timeout_ms, double *latency_s);
+/* Cancel a request: a pending one leaves the queue, one in flight runs on but its results are not
+ * written to the caller's buffers; either way dade_server_wait returns DADE_ECANCELLED for it (and the
+ * caller's buffers are free once cancel returns).  DADE_EINVAL for an unknown or completed ticket. */
+dade_status dade_server_cancel(dade_server *s, uint64_t ticket);
 dade_status dade_server_stats_get(dade_server *s, dade_server_stats *out);
 void dade_server_free(dade_server *s);
 
@@ -579,6 +591,23 @@ dade_status dade_autotune(const dade_index *ix, const float *q, int64_t nq, int3
 dade_status dade_query(const dade_index *ix, const float *q, int64_t nq, int32_t k, int32_t nprobe,
                        float alpha, int32_t delta_d, const dade_search_opts *opts, int64_t *ids,
                        float *dists, dade_stream stream);
+
+/*
+ * dade_query with a K and an nprobe per query (the paper's IVF search,
+ * Section 3.4, run for each query with its own K and nprobe): one rotation,
+ * one probe of the nprobe_max nearest lists (a query's first nprobe[i] of
+ * them, in (distance, id) order, are its own nprobe[i] nearest) and one scan
+ * launch in which query i keeps its k[i] nearest, tests against its own
+ * k[i]-th distance and visits its nprobe[i] lists.  Every query's result is
+ * bit-identical to dade_query with that query's K and nprobe.  k, nprobe:
+ * host or device [nq] (host values are checked: 1..k_max, 1..nprobe_max;
+ * device values are clamped into those ranges).  ids, dists: [nq * k_max],
+ * row i holding query i's k[i] results, then id -1 / +inf.  The tile schedule
+ * only (opts NULL or schedule DADE_SCHED_TILE; DADE_EINVAL otherwise).
+ */
+dade_status dade_query_mixed(const dade_index *ix, const float *q, int64_t nq, const int32_t *k,
+                             const int32_t *nprobe, int32_t k_max, int32_t nprobe_max, float alpha, int32_t delta_d,
+                             const dade_search_opts *opts, int64_t *ids, float *dists, dade_stream stream);
 
 /* Largest nq * n_clusters one dade_probe_noalloc call accepts (16 MiB of floats). */
 enum { DADE_PROBE_NOALLOC_MAX = 4194304 };

@@ -242,7 +242,7 @@ struct Staged {
 
 dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *probe_dev, int64_t nq, int32_t k,
                      int32_t nprobe, float alpha, int32_t delta_d, const dade_search_opts *opts, int64_t *ids,
-                     float *dists, cudaStream_t s);
+                     float *dists, cudaStream_t s, const int32_t *qk_dev = nullptr, const int32_t *qnp_dev = nullptr);
 
 dade_status run_search(const dade_index *ix, const float *q_dev, int64_t nq, int32_t k, int32_t nprobe, float alpha,
                        int32_t delta_d, const dade_search_opts *opts, int64_t *ids, float *dists, cudaStream_t s) {
@@ -253,7 +253,7 @@ dade_status run_search(const dade_index *ix, const float *q_dev, int64_t nq, int
 
 dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *probe_dev, int64_t nq, int32_t k,
                      int32_t nprobe, float alpha, int32_t delta_d, const dade_search_opts *opts, int64_t *ids,
-                     float *dists, cudaStream_t s) {
+                     float *dists, cudaStream_t s, const int32_t *qk_dev, const int32_t *qnp_dev) {
     const bool ids_host = !is_device_ptr(ids), dists_host = !is_device_ptr(dists);
     int64_t *ids_d = ids;
     float *dists_d = dists;
@@ -287,6 +287,8 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.use_tc = opts ? (opts->flags & DADE_FLAG_TC_PREFILTER) != 0 : 0;
     p.wait_ns = opts ? opts->wait_ns : 0;
     p.check_timeout = opts ? (opts->flags & DADE_FLAG_CHECK_TIMEOUT) != 0 : 0;
+    p.q_k = qk_dev;
+    p.q_np = qnp_dev;
     p.lead_stats = opts ? opts->lead_stats : nullptr;
     p.delta_d = delta_d;
     const bool ads = opts && opts->estimator == DADE_ESTIMATOR_ADSAMPLING;
@@ -520,6 +522,43 @@ dade_status dade_query(const dade_index *ix, const float *q, int64_t nq, int32_t
     DADE_TRY(ws(ix).qrot.ensure(sizeof(float) * (size_t)nq * ix->d));
     DADE_TRY(dade::rotate(ix, qd, nq, ix->d, ws(ix).qrot.as<float>(), s));
     return run_search(ix, ws(ix).qrot.as<float>(), nq, k, nprobe, alpha, delta_d, opts, ids, dists, s);
+}
+
+dade_status dade_query_mixed(const dade_index *ix, const float *q, int64_t nq, const int32_t *k, const int32_t *nprobe,
+                             int32_t k_max, int32_t nprobe_max, float alpha, int32_t delta_d,
+                             const dade_search_opts *opts, int64_t *ids, float *dists, dade_stream stream) {
+    g_err.clear();
+    DADE_TRY(validate_search(ix, nq, k_max, nprobe_max, alpha, delta_d, opts));
+    DADE_CHECK_ARG(!opts || opts->schedule == DADE_SCHED_TILE, "per-query K and nprobe need the tile schedule");
+    if (nq == 0) return DADE_OK;
+    DADE_CHECK_ARG(q != nullptr && k != nullptr && nprobe != nullptr && ids != nullptr && dists != nullptr,
+                   "NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t *kd = k, *npd = nprobe;
+    if (!is_device_ptr(k)) {
+        for (int64_t i = 0; i < nq; ++i) DADE_CHECK_ARG(k[i] >= 1 && k[i] <= k_max, "k[i] outside 1..k_max");
+        DADE_TRY(ws(ix).qk.ensure(sizeof(int32_t) * (size_t)nq));
+        DADE_TRY_CUDA(cudaMemcpyAsync(ws(ix).qk.p, k, sizeof(int32_t) * (size_t)nq, cudaMemcpyHostToDevice, s));
+        kd = ws(ix).qk.as<int32_t>();
+    }
+    if (!is_device_ptr(nprobe)) {
+        for (int64_t i = 0; i < nq; ++i)
+            DADE_CHECK_ARG(nprobe[i] >= 1 && nprobe[i] <= nprobe_max, "nprobe[i] outside 1..nprobe_max");
+        DADE_TRY(ws(ix).qnp.ensure(sizeof(int32_t) * (size_t)nq));
+        DADE_TRY_CUDA(cudaMemcpyAsync(ws(ix).qnp.p, nprobe, sizeof(int32_t) * (size_t)nq, cudaMemcpyHostToDevice, s));
+        npd = ws(ix).qnp.as<int32_t>();
+    }
+    dade_status st;
+    const float *qd = stage_in(ix, q, (size_t)nq * ix->d, ws(ix).qin, s, &st);
+    if (!qd) return st;
+    DADE_TRY(ws(ix).qrot.ensure(sizeof(float) * (size_t)nq * ix->d));
+    DADE_TRY(dade::rotate(ix, qd, nq, ix->d, ws(ix).qrot.as<float>(), s));
+    // the nprobe_max nearest lists in (distance, id) order: a query's first nprobe[i]
+    // of them are its own nprobe[i] nearest
+    DADE_TRY(ws(ix).probe.ensure(sizeof(int32_t) * (size_t)nq * nprobe_max));
+    DADE_TRY(dade::probe(ix, ws(ix).qrot.as<float>(), nq, ix->d, nprobe_max, ws(ix).probe.as<int32_t>(), s));
+    return run_scan(ix, ws(ix).qrot.as<float>(), ws(ix).probe.as<int32_t>(), nq, k_max, nprobe_max, alpha, delta_d,
+                    opts, ids, dists, s, kd, npd);
 }
 
 dade_status dade_reserve(dade_index *ix, int64_t max_nq, int32_t max_nprobe) {

@@ -85,6 +85,7 @@ struct DevBuf {
 struct Workspace {
     DevBuf dist, probe, qrot, qin, ids, dists, order, ordcnt, aimg, anorm, selflag;
     DevBuf lm_cnt, lm_items, lm_acc, lm_acnt;   // seeded schedule (lm.cu)
+    DevBuf qk, qnp;                              // per-query K and nprobe (dade_query_mixed)
 };
 
 } // namespace dade
@@ -183,6 +184,7 @@ struct ScanParams {
     int32_t use_tc;          // list-major passes: the first increment's tensor-core prefilter
     int64_t wait_ns;         // limit of the scan kernels' bounded waits (0: 2 s)
     int32_t check_timeout;   // failure-path check: every block's first wait runs out
+    const int32_t *q_k = nullptr, *q_np = nullptr;   // per-query K and nprobe (tile schedule), or NULL
     const float *r2src;
     unsigned long long *acc;
     int *acnt;

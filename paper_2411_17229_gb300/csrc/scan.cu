@@ -51,6 +51,9 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
 
     const int tid = threadIdx.x, quad = tid >> 2, lq = tid & 3;
     const int64_t qi = cta_query(a);
+    // this query's K and nprobe, within the batch's largest (a.k, a.nprobe: buffer sizes and strides)
+    const int kq = a.q_k ? min(max(a.q_k[qi], 1), a.k) : a.k;
+    const int npq = a.q_np ? min(max(a.q_np[qi], 0), a.nprobe) : a.nprobe;
     const SmemLayout L = layout(a.dp, a.tile, a.ub, a.ns, a.k, a.nprobe, LF != 0);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     int4 *smeta = reinterpret_cast<int4 *>(smem + L.meta);
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
     // split mode: this CTA's part of the probe positions
     const int part = a.parts > 0 ? (int)(blockIdx.x % (unsigned)a.parts) : 0;
     const int pbeg = a.parts > 0 ? (int)((int64_t)a.nprobe * part / a.parts) : 0;
-    const int pend = a.parts > 0 ? (int)((int64_t)a.nprobe * (part + 1) / a.parts) : a.nprobe;
+    const int pend = a.parts > 0 ? (int)((int64_t)a.nprobe * (part + 1) / a.parts) : npq;
     for (int k = tid; k < a.dp; k += NT) qv[k] = k < a.d ? a.q_rot[qi * a.q_stride + k] : 0.f;
     for (int p = tid; p < min(a.nprobe, PMETA); p += NT) {
         const ListMeta m = a.meta[plist[p]];
@@ -98,7 +101,7 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
             issue(a, smeta, plist, c, slot, stage, bars);
         }
     };
-    Cur cc{pbeg, a.row_lo, 0};
+    Cur cc{pbeg, a.row_lo, 0, pend};
     normalize(cc, a, smeta, plist);
     Cur ic = cc;          // issue cursor (thread 0 only)
     int issued = 0;       // units issued (thread 0 only)
@@ -350,18 +353,18 @@ __global__ void __launch_bounds__(NT, FD ? 1024 / NT : 768 / NT) k_scan(const Sc
             unsigned long long *O = cur ? top0 : top1;
             for (int t = tid; t < nt; t += NT) {
                 const int pos = t + lower_bound_u64(fsort, nF, A[t]);
-                if (pos < a.k) O[pos] = A[t];
+                if (pos < kq) O[pos] = A[t];
             }
             for (int t = tid; t < nF; t += NT) {
                 const int pos = t + lower_bound_u64(A, nt, fsort[t]);
-                if (pos < a.k) O[pos] = fsort[t];
+                if (pos < kq) O[pos] = fsort[t];
             }
             __syncthreads();
             if (tid == 0) {
-                const int nn = min(a.k, nt + nF);
+                const int nn = min(kq, nt + nF);
                 s_ntop = nn;
                 s_cur = cur ^ 1;
-                s_r2 = nn == a.k ? __uint_as_float((unsigned)(O[a.k - 1] >> 32)) : INFINITY;
+                s_r2 = nn == kq ? __uint_as_float((unsigned)(O[kq - 1] >> 32)) : INFINITY;
             }
         }
         if (!quiet) __syncthreads();
@@ -444,6 +447,10 @@ dade_status scan_fast(const scanning::ScanArgs &a, int64_t nq, bool fd, int thre
 
 dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s) {
     if (nq == 0) return DADE_OK;
+    if ((p.q_k || p.q_np) && (p.schedule != DADE_SCHED_TILE || p.parts > 0)) {
+        set_error("per-query K and nprobe need the tile schedule");
+        return DADE_EUNSUPPORTED;
+    }
     if (p.schedule == DADE_SCHED_SEEDED && p.seed_lists > 0 && p.seed_lists < p.nprobe)
         return scan_seeded(ix, nq, p, s);
     if (p.schedule == DADE_SCHED_ROUNDS && p.parts == 0) return scan_rounds(ix, nq, p, s);
@@ -465,6 +472,8 @@ dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStre
     a.err = ix->errflag.as<int>();
     a.wait_ns = p.wait_ns > 0 ? (uint64_t)p.wait_ns : WAIT_NS;
     a.never = p.check_timeout ? ix->errflag.as<int>() + 3 : nullptr;
+    a.q_k = p.q_k;
+    a.q_np = p.q_np;
     a.q_stride = p.q_stride;
     a.nprobe = p.nprobe;
     if (p.parts > 0) {

@@ -61,6 +61,9 @@ struct ScanArgs {
     int row_lo, row_hi;
     uint64_t wait_ns;            // limit of every bounded wait on a copy
     const int *never;            // failure-path check: a device word nothing sets (else NULL)
+    // per-query K and nprobe (tile schedule, one CTA per query), or NULL for k and
+    // nprobe; k and nprobe are then the batch's largest (output row stride, probe rows)
+    const int32_t *q_k, *q_np;
 };
 
 // Rows of a list of `len` members that a pass scans end here.
@@ -187,13 +190,14 @@ __device__ __forceinline__ int4 meta_of(const ScanArgs &a, const int4 *sm, const
     return make_int4((int)(m.base >> 6), (int)m.slot, list_end(a, m.len), m.np);
 }
 
-// Tile cursor: probe position p, first candidate i0, increment j.
+// Tile cursor: probe position p, first candidate i0, increment j; probe
+// positions end at np (the query's nprobe, or the end of its part).
 struct Cur {
-    int p, i0, j;
+    int p, i0, j, np;
 };
 
 __device__ __forceinline__ void normalize(Cur &c, const ScanArgs &a, const int4 *sm, const int32_t *plist) {
-    while (c.p < a.nprobe && c.i0 >= meta_of(a, sm, plist, c.p).z) {
+    while (c.p < c.np && c.i0 >= meta_of(a, sm, plist, c.p).z) {
         ++c.p;
         c.i0 = a.row_lo;
         c.j = 0;
@@ -339,13 +343,13 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Merge the nF accepted candidates fl[0..nF) of the tile whose ids start at
-// slot `id0` into the K-best list (rank sort, then merge by rank); refresh
-// s_r2 from the K-th entry.  Every thread of the block calls it; nF is
+// slot `id0` into the query's kq-best list (rank sort, then merge by rank);
+// refresh s_r2 from the kq-th entry.  Every thread of the block calls it; nF is
 // uniform.  Ends with a barrier.
 template <int NT>
-__device__ inline void merge_topk(const ScanArgs &a, const Surv *fl, int nF, int64_t id0, unsigned long long *fraw,
-                           unsigned long long *fsort, unsigned long long *top0, unsigned long long *top1, int *s_ntop,
-                           int *s_cur, float *s_r2) {
+__device__ inline void merge_topk(const ScanArgs &a, int kq, const Surv *fl, int nF, int64_t id0,
+                                  unsigned long long *fraw, unsigned long long *fsort, unsigned long long *top0,
+                                  unsigned long long *top1, int *s_ntop, int *s_cur, float *s_r2) {
     const int tid = threadIdx.x;
     const int N = nF > 64 ? pow2_at_least(nF) : nF;
     for (int t = tid; t < N; t += NT) {
@@ -384,18 +388,18 @@ __device__ inline void merge_topk(const ScanArgs &a, const Surv *fl, int nF, int
     unsigned long long *O = cur ? top0 : top1;
     for (int t = tid; t < nt; t += NT) {
         const int pos = t + lower_bound_u64(fsort, nF, A[t]);
-        if (pos < a.k) O[pos] = A[t];
+        if (pos < kq) O[pos] = A[t];
     }
     for (int t = tid; t < nF; t += NT) {
         const int pos = t + lower_bound_u64(A, nt, fsort[t]);
-        if (pos < a.k) O[pos] = fsort[t];
+        if (pos < kq) O[pos] = fsort[t];
     }
     __syncthreads();
     if (tid == 0) {
-        const int nn = min(a.k, nt + nF);
+        const int nn = min(kq, nt + nF);
         *s_ntop = nn;
         *s_cur = cur ^ 1;
-        *s_r2 = nn == a.k ? __uint_as_float((unsigned)(O[a.k - 1] >> 32)) : INFINITY;
+        *s_r2 = nn == kq ? __uint_as_float((unsigned)(O[kq - 1] >> 32)) : INFINITY;
     }
     __syncthreads();
 }

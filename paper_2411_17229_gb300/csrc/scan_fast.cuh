@@ -133,6 +133,9 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_dade_fast(const ScanArgs a) {
 
     const int tid = threadIdx.x, quad = tid >> 2, lq = tid & 3;
     const int64_t qi = cta_query(a);
+    // this query's K and nprobe, within the batch's largest (a.k, a.nprobe: buffer sizes and strides)
+    const int kq = a.q_k ? min(max(a.q_k[qi], 1), a.k) : a.k;
+    const int npq = a.q_np ? min(max(a.q_np[qi], 0), a.nprobe) : a.nprobe;
     const FastLayout L = fast_layout(a.tile, SLOT, NSF, a.k, a.nprobe);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     int4 *smeta = reinterpret_cast<int4 *>(smem + L.meta);
@@ -162,12 +165,12 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_dade_fast(const ScanArgs a) {
     if (tid == 0) s_lead = 0;
     __syncthreads();
 
-    Cur cc{0, 0, 0};
+    Cur cc{0, 0, 0, npq};
     normalize(cc, a, smeta, plist);
     Cur ic = cc;           // next chunk to issue (thread 0)
     int issued = 0;
     if (tid == 0)
-        for (int s = 0; s < NSF && ic.p < a.nprobe; ++s) {
+        for (int s = 0; s < NSF && ic.p < npq; ++s) {
             issue_chunk<GB, LF>(a, smeta, plist, ic, s, stage, bars);
             chunk_advance(ic, a, smeta, plist);
             ++issued;
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_dade_fast(const ScanArgs a) {
     int unit = 0;
     bool aborted = false;
 
-    while (cc.p < a.nprobe) {
+    while (cc.p < npq) {
         const int4 m = meta_of(a, smeta, plist, cc.p);
         const int tn = min(a.tile, m.z - cc.i0);
         const float *lbase = list_base(a, m);
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_dade_fast(const ScanArgs a) {
                     }
                 }
                 __syncthreads();
-                if (tid == 0 && ic.p < a.nprobe) {
+                if (tid == 0 && ic.p < npq) {
                     issue_chunk<GB, LF>(a, smeta, plist, ic, slot, stage, bars);
                     chunk_advance(ic, a, smeta, plist);
                     ++issued;
@@ -271,7 +274,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_dade_fast(const ScanArgs a) {
                 }
             }
             __syncthreads();
-            if (tid == 0 && ic.p < a.nprobe) {
+            if (tid == 0 && ic.p < npq) {
                 issue_chunk<GB, LF>(a, smeta, plist, ic, slot, stage, bars);
                 chunk_advance(ic, a, smeta, plist);
                 ++issued;
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(NT, 640 / NT) k_dade_fast(const ScanArgs a) {
         // ---- merge --------------------------------------------------------------------
         const int nF = s_cntF;
         if (nF > 0)
-            merge_topk<NT>(a, fl, nF, (int64_t)(unsigned)m.y + cc.i0, fraw, fsort, top0, top1, &s_ntop, &s_cur, &s_r2);
+            merge_topk<NT>(a, kq, fl, nF, (int64_t)(unsigned)m.y + cc.i0, fraw, fsort, top0, top1, &s_ntop, &s_cur, &s_r2);
         cc.i0 += a.tile;
         normalize(cc, a, smeta, plist);
     }
@@ -365,6 +368,9 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_fd_fast(const ScanArgs a) {
 
     const int tid = threadIdx.x, quad = tid >> 2, lq = tid & 3;
     const int64_t qi = cta_query(a);
+    // this query's K and nprobe, within the batch's largest (a.k, a.nprobe: buffer sizes and strides)
+    const int kq = a.q_k ? min(max(a.q_k[qi], 1), a.k) : a.k;
+    const int npq = a.q_np ? min(max(a.q_np[qi], 0), a.nprobe) : a.nprobe;
     const SmemLayout L = layout(a.dp, a.tile, UB, a.ns, a.k, a.nprobe);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     int4 *smeta = reinterpret_cast<int4 *>(smem + L.meta);
@@ -392,12 +398,12 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_fd_fast(const ScanArgs a) {
     if (STATS && tid < 4) s_stats[tid] = 0;
     __syncthreads();
 
-    Cur cc{0, 0, 0};
+    Cur cc{0, 0, 0, npq};
     normalize(cc, a, smeta, plist);
     Cur ic = cc;
     int issued = 0;
     if (tid == 0)
-        for (int s = 0; s < a.ns && ic.p < a.nprobe; ++s) {
+        for (int s = 0; s < a.ns && ic.p < npq; ++s) {
             issue(a, smeta, plist, ic, s, stage, bars);
             advance(ic, NU, a, smeta, plist);
             ++issued;
@@ -406,7 +412,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_fd_fast(const ScanArgs a) {
     int unit = 0;
     bool aborted = false;
 
-    while (cc.p < a.nprobe) {
+    while (cc.p < npq) {
         const int4 m = meta_of(a, smeta, plist, cc.p);
         const int tn = min(a.tile, m.z - cc.i0);
         const int nit = (tn + NQUAD - 1) / NQUAD;
@@ -431,7 +437,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_fd_fast(const ScanArgs a) {
                 }
             }
             __syncthreads();
-            if (tid == 0 && ic.p < a.nprobe) {
+            if (tid == 0 && ic.p < npq) {
                 issue(a, smeta, plist, ic, slot, stage, bars);
                 advance(ic, NU, a, smeta, plist);
                 ++issued;
@@ -452,7 +458,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_fd_fast(const ScanArgs a) {
         __syncthreads();
         const int nF = s_cntF;
         if (nF > 0)
-            merge_topk<NT>(a, fl, nF, (int64_t)(unsigned)m.y + cc.i0, fraw, fsort, top0, top1, &s_ntop, &s_cur, &s_r2);
+            merge_topk<NT>(a, kq, fl, nF, (int64_t)(unsigned)m.y + cc.i0, fraw, fsort, top0, top1, &s_ntop, &s_cur, &s_r2);
         cc.i0 += a.tile;
         normalize(cc, a, smeta, plist);
     }

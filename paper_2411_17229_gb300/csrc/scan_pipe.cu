@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_scan_pipe(const ScanArgs a) {
     if (STATS && tid < 4) s_stats[tid] = 0;
     __syncthreads();
 
-    Cur cc{0, 0, 0};          // next tile to enter
+    Cur cc{0, 0, 0, a.nprobe};   // next tile to enter
     normalize(cc, a, smeta, plist);
     Cur ic = cc;              // next tile whose first increment to issue (thread 0)
     int issued = 0;
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_scan_pipe(const ScanArgs a) {
             const int slot = tl % P;
             const int nF = hdr[slot].cntF;
             if (nF > 0)
-                merge_topk<NT>(a, fin + (size_t)slot * T, nF, (int64_t)(unsigned)hdr[slot].m.y + hdr[slot].i0, fraw,
+                merge_topk<NT>(a, a.k, fin + (size_t)slot * T, nF, (int64_t)(unsigned)hdr[slot].m.y + hdr[slot].i0, fraw,
                                fsort, top0, top1, &s_ntop, &s_cur, &s_r2);
         }
         __syncthreads();

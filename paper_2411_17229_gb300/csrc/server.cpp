@@ -5,14 +5,21 @@
 // slot is a CUDA stream with its own device workspace, pinned staging
 // buffers and a completion event, so batches in different slots overlap on
 // the GPU.  When a slot is free the dispatcher forms a batch from the oldest
-// pending request and every later pending request with the same (K, nprobe,
-// alpha, delta_d), up to max_batch queries, copies the queries in, runs the
-// query step (rotation, probe, scan) on the slot's stream, copies the results
-// out and records the event.  A finished slot's results are scattered to the
-// requests' host buffers and their tickets complete; requests that arrived
-// meanwhile are admitted as slots free up.  Every query's result depends only
-// on that query (the step has no cross-query arithmetic), so a request gets
-// the same result alone and in any mix.
+// pending request and every later pending request it can run with, up to
+// max_batch queries: under the tile schedule any request with the same alpha
+// and delta_d (one launch serves a K and an nprobe per query,
+// dade_query_mixed), under the other schedules the same (K, nprobe, alpha,
+// delta_d).  It copies the queries in, runs the query step (rotation, probe,
+// scan) on the slot's stream, copies the results out and records the event.
+// A finished slot's results are scattered to the requests' host buffers and
+// their tickets complete; requests that arrived meanwhile are admitted as
+// slots free up.  Admission is by device bytes when a budget is set: a batch
+// starts only if the slots' fixed buffers and the workspace every slot has
+// grown to, plus what this batch adds, stay within the budget.  Every query's
+// result depends only on that query (the step has no cross-query arithmetic),
+// so a request gets the same result alone and in any mix.  A cancelled
+// request leaves the queue, or, in flight, completes without its results
+// being written to the caller's buffers.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -45,6 +52,7 @@ struct Request {
 
 struct Ticket {
     bool done = false;
+    bool cancelled = false;
     dade_status status = DADE_OK;
     double latency = 0.0;
 };
@@ -57,8 +65,10 @@ struct Slot {
     float *q_host = nullptr;
     int64_t *ids_host = nullptr;
     float *dists_host = nullptr;
+    int32_t *k_host = nullptr, *np_host = nullptr;   // per-query K and nprobe of a mixed batch
     bool busy = false;
-    int32_t k = 0;
+    int32_t k = 0;                                   // the batch's result row stride (largest K)
+    int64_t ws_bytes = 0;                            // workspace this slot's batches grew to (estimate)
     std::vector<Request> reqs;
 };
 
@@ -93,7 +103,33 @@ struct dade_server {
             if (s.q_host) cudaFreeHost(s.q_host);
             if (s.ids_host) cudaFreeHost(s.ids_host);
             if (s.dists_host) cudaFreeHost(s.dists_host);
+            if (s.k_host) cudaFreeHost(s.k_host);
+            if (s.np_host) cudaFreeHost(s.np_host);
         }
+    }
+
+    // One launch serves a K and an nprobe per query under the tile schedule.
+    bool mixed() const { return o.schedule == DADE_SCHED_TILE; }
+
+    // Workspace bytes of a batch of nq queries (estimate of what the query step grows it to):
+    // raw and rotated queries, probe distances and lists, results, the tensor-core operand
+    // image, query order and per-query arrays; with r frozen over whole lists, the accept buffer.
+    int64_t batch_bytes(int64_t nq, int32_t kmax, int32_t npmax) const {
+        const int64_t d = ix->d;
+        int64_t per = d * 4 * 2 + (int64_t)ix->nc * 4 + (int64_t)npmax * 4 + (int64_t)kmax * 12 + d * 8 + 72;
+        if (o.schedule == DADE_SCHED_SEEDED || o.schedule == DADE_SCHED_ROUNDS)
+            per += std::min<int64_t>((int64_t)npmax * std::max(ix->max_list, 1), 1 << 16) * 8;
+        return nq * per;
+    }
+    int64_t fixed_bytes() const { return (int64_t)o.max_batch * ((int64_t)ix->d * 4 + (int64_t)o.max_k * 12); }
+    int64_t used_bytes() const {
+        int64_t u = 0;
+        for (const auto &sp : slots) u += fixed_bytes() + sp->ws_bytes;
+        return u;
+    }
+    // Whether slot s may run a batch of `need` workspace bytes within the budget.
+    bool fits(const Slot &s, int64_t need) const {
+        return o.device_budget <= 0 || used_bytes() + std::max<int64_t>(0, need - s.ws_bytes) <= o.device_budget;
     }
 
     // Runs one batch on slot s (dispatcher thread).  Returns the status of the launches.
@@ -106,7 +142,17 @@ struct dade_server {
             nq += r.nq;
         }
         const Request &r0 = s.reqs.front();
-        s.k = r0.k;
+        int32_t kmax = 0, npmax = 0;
+        int64_t qi = 0;
+        for (const Request &r : s.reqs) {
+            kmax = std::max(kmax, r.k);
+            npmax = std::max(npmax, r.nprobe);
+            for (int64_t i = 0; i < r.nq; ++i, ++qi) {
+                s.k_host[qi] = r.k;
+                s.np_host[qi] = r.nprobe;
+            }
+        }
+        s.k = kmax;
         DADE_TRY_CUDA(cudaMemcpyAsync(s.q_dev.p, s.q_host, sizeof(float) * (size_t)nq * d, cudaMemcpyHostToDevice,
                                       s.stream));
         dade_search_opts so{};
@@ -117,11 +163,16 @@ struct dade_server {
         so.seed_lists = o.seed_lists;
         so.flags = o.flags;
         so.stage_dims = o.stage_dims;
-        DADE_TRY(dade_query(ix, s.q_dev.as<float>(), nq, r0.k, r0.nprobe, r0.alpha, r0.delta_d, &so,
-                            s.ids_dev.as<int64_t>(), s.dists_dev.as<float>(), (dade_stream)s.stream));
-        DADE_TRY_CUDA(cudaMemcpyAsync(s.ids_host, s.ids_dev.p, sizeof(int64_t) * (size_t)nq * r0.k,
+        if (mixed())
+            DADE_TRY(dade_query_mixed(ix, s.q_dev.as<float>(), nq, s.k_host, s.np_host, kmax, npmax, r0.alpha,
+                                      r0.delta_d, &so, s.ids_dev.as<int64_t>(), s.dists_dev.as<float>(),
+                                      (dade_stream)s.stream));
+        else
+            DADE_TRY(dade_query(ix, s.q_dev.as<float>(), nq, r0.k, r0.nprobe, r0.alpha, r0.delta_d, &so,
+                                s.ids_dev.as<int64_t>(), s.dists_dev.as<float>(), (dade_stream)s.stream));
+        DADE_TRY_CUDA(cudaMemcpyAsync(s.ids_host, s.ids_dev.p, sizeof(int64_t) * (size_t)nq * kmax,
                                       cudaMemcpyDeviceToHost, s.stream));
-        DADE_TRY_CUDA(cudaMemcpyAsync(s.dists_host, s.dists_dev.p, sizeof(float) * (size_t)nq * r0.k,
+        DADE_TRY_CUDA(cudaMemcpyAsync(s.dists_host, s.dists_dev.p, sizeof(float) * (size_t)nq * kmax,
                                       cudaMemcpyDeviceToHost, s.stream));
         DADE_TRY_CUDA(cudaEventRecord(s.done, s.stream));
         return DADE_OK;
@@ -132,14 +183,15 @@ struct dade_server {
         const auto now = Clock::now();
         int64_t off = 0;
         for (const Request &r : s.reqs) {
-            if (status == DADE_OK) {
-                std::memcpy(r.ids, s.ids_host + off * s.k, sizeof(int64_t) * (size_t)r.nq * s.k);
-                std::memcpy(r.dists, s.dists_host + off * s.k, sizeof(float) * (size_t)r.nq * s.k);
-            }
-            off += r.nq;
             Ticket &t = tickets[r.ticket];
+            if (status == DADE_OK && !t.cancelled)   // the request's own K columns of its rows
+                for (int64_t i = 0; i < r.nq; ++i) {
+                    std::memcpy(r.ids + i * r.k, s.ids_host + (off + i) * s.k, sizeof(int64_t) * (size_t)r.k);
+                    std::memcpy(r.dists + i * r.k, s.dists_host + (off + i) * s.k, sizeof(float) * (size_t)r.k);
+                }
+            off += r.nq;
             t.done = true;
-            t.status = status;
+            t.status = t.cancelled ? DADE_ECANCELLED : status;
             t.latency = std::chrono::duration<double>(now - r.t0).count();
         }
         st.requests_done += (int64_t)s.reqs.size();
@@ -173,19 +225,32 @@ struct dade_server {
                 Slot &s = *sp;
                 if (s.busy || pending.empty()) continue;
                 const Request first = pending.front();
+                int64_t nq = first.nq;
+                int32_t kmax = first.k, npmax = first.nprobe;
+                if (!fits(s, batch_bytes(nq, kmax, npmax))) {
+                    if (busy > 0) break;   // wait for a batch to finish and give its bytes back
+                    pending.pop_front();   // nothing runs and it still does not fit: it never will
+                    s.reqs.assign(1, first);
+                    finish(s, DADE_ENOMEM);
+                    continue;
+                }
                 pending.pop_front();
                 s.reqs.assign(1, first);
-                int64_t nq = first.nq;
                 for (auto it = pending.begin(); it != pending.end();) {
-                    if (it->k == first.k && it->nprobe == first.nprobe && it->alpha == first.alpha &&
-                        it->delta_d == first.delta_d && nq + it->nq <= o.max_batch) {
+                    const bool same = it->alpha == first.alpha && it->delta_d == first.delta_d &&
+                                      (mixed() || (it->k == first.k && it->nprobe == first.nprobe));
+                    const int32_t k2 = std::max(kmax, it->k), np2 = std::max(npmax, it->nprobe);
+                    if (same && nq + it->nq <= o.max_batch && fits(s, batch_bytes(nq + it->nq, k2, np2))) {
                         nq += it->nq;
+                        kmax = k2;
+                        npmax = np2;
                         s.reqs.push_back(*it);
                         it = pending.erase(it);
                     } else {
                         ++it;
                     }
                 }
+                s.ws_bytes = std::max(s.ws_bytes, batch_bytes(nq, kmax, npmax));
                 s.busy = true;
                 ++busy;
                 admitted = true;
@@ -261,19 +326,20 @@ dade_status dade_server_create(const dade_index *ix, const dade_server_opts *opt
     // device memory per slot: queries in and rotated, probe distances, probe
     // lists, results, tensor-core operand image, and (seeded schedule) the
     // accept buffer of the list-major phase
-    const int64_t B = opts->max_batch, d = ix->d, np = opts->max_nprobe;
-    int64_t per = B * (d * 4 * 2 + (int64_t)ix->nc * 4 + np * 4 + (int64_t)opts->max_k * 12 + d * 8 + 64);
-    if (opts->schedule == DADE_SCHED_SEEDED || opts->schedule == DADE_SCHED_ROUNDS)
-        per += B * std::min<int64_t>(np * (int64_t)std::max(ix->max_list, 1), 1 << 16) * 8;
+    // every slot holds its fixed staging buffers (max_batch queries and results); the
+    // workspace a slot's batches grow is admitted batch by batch against the budget
+    const int64_t B = opts->max_batch, d = ix->d;
+    const int64_t fixed = sv->fixed_bytes(), one = sv->batch_bytes(1, opts->max_k, opts->max_nprobe);
     int n = opts->slots;
-    if (opts->device_budget > 0) n = (int)std::min<int64_t>(n, opts->device_budget / std::max<int64_t>(per, 1));
+    if (opts->device_budget > 0)
+        n = (int)std::min<int64_t>(n, (opts->device_budget - one) / std::max<int64_t>(fixed, 1));
     if (n < 1) {
         delete sv;
-        set_error("device_budget holds no slot (" + std::to_string(per) + " bytes per slot)");
+        set_error("device_budget holds no slot (" + std::to_string(fixed + one) + " bytes for one request)");
         return DADE_ENOMEM;
     }
     sv->st.slots = n;
-    sv->st.slot_bytes = per;
+    sv->st.slot_bytes = fixed + sv->batch_bytes(B, opts->max_k, opts->max_nprobe);
     for (int i = 0; i < n; ++i) sv->slots.emplace_back(new (std::nothrow) Slot());
     for (auto &sp : sv->slots) {
         if (!sp) {
@@ -286,7 +352,9 @@ dade_status dade_server_create(const dade_index *ix, const dade_server_opts *opt
             cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMallocHost(&s.q_host, sizeof(float) * (size_t)(B * d)) != cudaSuccess ||
             cudaMallocHost(&s.ids_host, sizeof(int64_t) * (size_t)(B * opts->max_k)) != cudaSuccess ||
-            cudaMallocHost(&s.dists_host, sizeof(float) * (size_t)(B * opts->max_k)) != cudaSuccess) {
+            cudaMallocHost(&s.dists_host, sizeof(float) * (size_t)(B * opts->max_k)) != cudaSuccess ||
+            cudaMallocHost(&s.k_host, sizeof(int32_t) * (size_t)B) != cudaSuccess ||
+            cudaMallocHost(&s.np_host, sizeof(int32_t) * (size_t)B) != cudaSuccess) {
             cudaGetLastError();
             delete sv;
             set_error("stream, event or pinned host allocation failed");
@@ -353,8 +421,31 @@ dade_status dade_server_wait(dade_server *sv, uint64_t ticket, int64_t timeout_m
     const Ticket t = sv->tickets[ticket];
     sv->tickets.erase(ticket);
     if (latency_s) *latency_s = t.latency;
-    if (t.status != DADE_OK) set_error("the batch of this request failed on the device");
+    if (t.status == DADE_ECANCELLED) set_error("the request was cancelled");
+    else if (t.status != DADE_OK) set_error("the batch of this request failed on the device");
     return t.status;
+}
+
+dade_status dade_server_cancel(dade_server *sv, uint64_t ticket) {
+    using namespace dade;
+    set_error("");
+    DADE_CHECK_ARG(sv != nullptr, "NULL pointer");
+    std::lock_guard<std::mutex> g(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    DADE_CHECK_ARG(it != sv->tickets.end() && !it->second.done, "unknown or completed ticket");
+    it->second.cancelled = true;
+    for (auto p = sv->pending.begin(); p != sv->pending.end(); ++p)
+        if (p->ticket == ticket) {   // not admitted yet: it leaves the queue now
+            const Clock::time_point t0 = p->t0;
+            sv->pending.erase(p);
+            it->second.done = true;
+            it->second.status = DADE_ECANCELLED;
+            it->second.latency = std::chrono::duration<double>(Clock::now() - t0).count();
+            sv->st.requests_done += 1;
+            sv->cv_done.notify_all();
+            break;
+        }
+    return DADE_OK;
 }
 
 dade_status dade_server_stats_get(dade_server *sv, dade_server_stats *out) {

@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdade.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EIO = range(7)
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, EIO, ECANCELLED = range(8)
 MODE_DADE, MODE_FD = 0, 1
 SCHED_TILE, SCHED_PIPELINED, SCHED_SEEDED, SCHED_ROUNDS = 0, 1, 2, 3
 FLAG_GENERIC_KERNEL, FLAG_LEAD, FLAG_QUERY_ORDER, FLAG_ROW_TAIL, FLAG_SEED_SPLIT = 1, 2, 4, 8, 16
@@ -96,6 +96,7 @@ SIGNATURES = {
     "dade_server_submit": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp]),
     "dade_server_wait": (_i32, [_vp, C.c_uint64, _i64, _vp]),
     "dade_server_stats_get": (_i32, [_vp, _vp]),
+    "dade_server_cancel": (_i32, [_vp, C.c_uint64]),
     "dade_server_free": (None, [_vp]),
     "dade_graph_launch": (_i32, [_vp, _vp]),
     "dade_graph_free": (None, [_vp]),
@@ -118,6 +119,7 @@ SIGNATURES = {
     "dade_set_alloc_hook": (None, [_vp, _vp]),
     "dade_shard_lists": (_i32, [_vp, _i32, _i32, _vp]),
     "dade_autotune_opts_default": (None, [_vp]),
+    "dade_query_mixed": (_i32, [_vp, _vp, _i64, _vp, _vp, _i32, _i32, C.c_float, _i32, _vp, _vp, _vp, _vp]),
     "dade_autotune": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp]),
     "dade_index_subset": (_i32, [_vp, _vp, _i32, _vp]),
     "dade_merge_shards": (_i32, [_vp, _vp, _i32, _i64, _i32, _vp, _vp, _vp]),
@@ -348,6 +350,20 @@ class Index:
                                 C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
+    def query_mixed(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, threads=0, flags=0,
+                    stage_dims=0, wait_ns=0, stream=None):
+        """dade_query_mixed: per-query K and nprobe (int32 arrays [nq], host or device); ids / dists
+        [nq, max K].  Tile schedule."""
+        kk = k if hasattr(k, "data_ptr") else np.ascontiguousarray(k, dtype=np.int32)
+        pp = nprobe if hasattr(nprobe, "data_ptr") else np.ascontiguousarray(nprobe, dtype=np.int32)
+        k_max = int(kk.max().item() if hasattr(kk, "data_ptr") else kk.max())
+        np_max = int(pp.max().item() if hasattr(pp, "data_ptr") else pp.max())
+        o = SearchOpts(mode=mode, tile=tile, threads=threads, schedule=SCHED_TILE, flags=flags, stage_dims=stage_dims,
+                       wait_ns=wait_ns)
+        _check(lib().dade_query_mixed(self._h, _ptr(q), q.shape[0], _ptr(kk), _ptr(pp), k_max, np_max, float(alpha),
+                                      int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
+        return ids, dists
+
     def graph(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
               threads=0, schedule=SCHED_TILE, flags=0, seed_lists=0, estimator=ESTIMATOR_DADE, eps0=0.0,
               stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0):
@@ -466,9 +482,16 @@ class Server:
 
     def result(self, ticket, timeout_ms=-1):
         lat = C.c_double()
-        _check(lib().dade_server_wait(self._h, C.c_uint64(ticket), int(timeout_ms), C.byref(lat)))
+        rc = lib().dade_server_wait(self._h, C.c_uint64(ticket), int(timeout_ms), C.byref(lat))
+        if rc not in (OK, ETIMEOUT):   # the ticket is settled: its buffers are the caller's again
+            self._live.pop(ticket, None)
+        _check(rc)
         q, ids, dists = self._live.pop(ticket)
         return ids, dists, lat.value
+
+    def cancel(self, ticket):
+        """dade_server_cancel: result(ticket) then raises DadeError with status ECANCELLED."""
+        _check(lib().dade_server_cancel(self._h, C.c_uint64(ticket)))
 
     def stats(self):
         st = ServerStats()
