@@ -237,40 +237,32 @@ def run_adsampling(torch, dade, xb, q, w, nc, K, n0, grid, gt_kth, args, flush, 
 
 def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7, torch=None, xb=None):
     """Requests of one query each, Poisson arrivals at each rate (requests/s),
-    K and nprobe drawn per request from {1, 10, 100} x {16, 64, 128}; the
-    server batches compatible requests and overlaps batches on 4 streams.
-    Returns per rate: offered and served request rates, p50 / p99 latency
-    (submit to results on the host, measured by the server); with the base
-    on the device (xb), the served recall@K per nprobe against exact FP64
+    K and nprobe drawn per request from {1, 10, 100} x {16, 64, 128}, submitted
+    by the library's native load generator (dade_server_replay).  The server
+    runs the tile schedule at the chosen point's delta_d and alpha, so requests
+    of any K and nprobe share batches (dade_query_mixed), overlapped on 4
+    streams.  Returns per rate: offered and served request rates, p50 / p99
+    latency (submit to results on the host, measured by the server); with the
+    base on the device (xb), the served recall@K per nprobe against exact FP64
     ground truth."""
     n_lists = ix.info.n_clusters
     nprobes = [p for p in (16, 64, 128) if p <= n_lists]
-    srv = dade.Server(ix, slots=4, max_batch=1024, max_k=100, max_nprobe=max(nprobes), tile=point["tile"],
-                      threads=point["threads"], schedule=point.get("schedule", 0),
-                      seed_lists=point.get("seed_lists", 0), flags=point["flags"],
-                      stage_dims=point.get("stage_dims", 0))
+    keep = dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL
+    srv = dade.Server(ix, slots=4, max_batch=1024, max_k=100, max_nprobe=max(nprobes), tile=128,
+                      threads=point["threads"], schedule=dade.SCHED_TILE, flags=point["flags"] & keep)
     rng = np.random.default_rng(seed)
     out, served = [], []
     for rate in rates:
         n = max(50, int(rate * seconds))
-        gaps = rng.exponential(1.0 / rate, n)
-        ks = rng.choice([1, 10, 100], n)
-        nps = rng.choice(nprobes, n)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+        ks = rng.choice([1, 10, 100], n).astype(np.int32)
+        nps = rng.choice(nprobes, n).astype(np.int32)
         picks = rng.integers(0, queries.shape[0], n)
-        tickets = []
         t_start = time.perf_counter()
-        due = t_start
-        for i in range(n):
-            due += gaps[i]
-            while time.perf_counter() < due:
-                pass
-            tickets.append(srv.submit(queries[picks[i]:picks[i] + 1], int(ks[i]), int(nps[i]),
-                                      point.get("alpha", 0.1), point.get("delta_d", 32)))
-        t_sub = time.perf_counter() - t_start
-        res = [srv.result(t) for t in tickets]
-        lats = [r[2] for r in res]
+        ids, _, lats, t_sub = srv.replay(queries[picks], ks, nps, point.get("alpha", 0.1), point.get("delta_d", 32),
+                                         arrivals)
         t_all = time.perf_counter() - t_start
-        served.extend((int(picks[i]), int(ks[i]), int(nps[i]), res[i][0][0]) for i in range(n))
+        served.extend((int(picks[i]), int(ks[i]), int(nps[i]), ids[i, :ks[i]]) for i in range(n))
         out.append({"offered_rps": rate, "requests": n, "served_rps": round(n / t_all, 1),
                     "submit_rps": round(n / t_sub, 1),
                     "p50_ms": round(1e3 * float(np.percentile(lats, 50)), 3),
@@ -280,7 +272,9 @@ def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7, torch=None, xb
     st = srv.stats()
     srv.close()
     recall = served_recall(torch, xb, queries, served, nprobes) if xb is not None else None
-    return {"requests": "1 query each, K in {1, 10, 100}, nprobe in " + str(nprobes) + ", Poisson arrivals",
+    return {"requests": "1 query each, K in {1, 10, 100}, nprobe in " + str(nprobes) +
+                        ", Poisson arrivals, native submitter (dade_server_replay)",
+            "schedule": "tile (mixed K and nprobe in one launch)",
             "slots": st["slots"], "batches": st["batches"], "mean_batch": round(st["queries"] / max(1, st["batches"]), 2),
             "max_inflight": st["max_inflight"], "rates": out, "recall_by_nprobe": recall}
 
@@ -845,7 +839,7 @@ def measure_workload(args, wname, rank, world, dist, headline):
     serving = None
     if wname == SERVING_WORKLOAD and not args.no_serving:
         try:
-            serving = serve_sweep(dade, ix, queries, point, (2000, 10000, 30000), args.serve_seconds,
+            serving = serve_sweep(dade, ix, queries, point, (2000, 10000, 30000, 100000), args.serve_seconds,
                                   torch=torch, xb=xb)
         except Exception as e:  # noqa: BLE001 - reported, not fatal
             log(f"[bench] serving sweep failed: {e}")

@@ -385,6 +385,15 @@ dade_status dade_server_wait(dade_server *s, uint64_t ticket, int64_t timeout_ms
  * written to the caller's buffers; either way dade_server_wait returns DADE_ECANCELLED for it (and the
  * caller's buffers are free once cancel returns).  DADE_EINVAL for an unknown or completed ticket. */
 dade_status dade_server_cancel(dade_server *s, uint64_t ticket);
+/* A native load generator for measuring the server (no counterpart in the paper): request i is one
+ * query, q host [n * d] row i, with k[i] and nprobe[i], submitted from the calling thread at
+ * arrival_s[i] seconds after the call starts (non-decreasing; the thread spins until then), then
+ * every ticket is waited for.  ids, dists: host [n * k_stride], row i holding request i's k[i]
+ * results; latency_s: host [n], submit to completion (-1 if refused); submit_s (may be NULL): the
+ * seconds the submission took.  Returns the first error of any request (the others still run). */
+dade_status dade_server_replay(dade_server *s, const float *q, int64_t n, const int32_t *k, const int32_t *nprobe,
+                               float alpha, int32_t delta_d, const double *arrival_s, int32_t k_stride, int64_t *ids,
+                               float *dists, double *latency_s, double *submit_s);
 dade_status dade_server_stats_get(dade_server *s, dade_server_stats *out);
 void dade_server_free(dade_server *s);
 

@@ -426,6 +426,39 @@ dade_status dade_server_wait(dade_server *sv, uint64_t ticket, int64_t timeout_m
     return t.status;
 }
 
+dade_status dade_server_replay(dade_server *sv, const float *q, int64_t n, const int32_t *k, const int32_t *nprobe,
+                               float alpha, int32_t delta_d, const double *arrival_s, int32_t k_stride, int64_t *ids,
+                               float *dists, double *latency_s, double *submit_s) {
+    using namespace dade;
+    set_error("");
+    DADE_CHECK_ARG(sv && q && k && nprobe && arrival_s && ids && dists && latency_s, "NULL pointer");
+    DADE_CHECK_ARG(n >= 1, "n < 1");
+    for (int64_t i = 0; i < n; ++i) {
+        DADE_CHECK_ARG(k[i] >= 1 && k[i] <= k_stride, "k[i] outside 1..k_stride");
+        DADE_CHECK_ARG(i == 0 || arrival_s[i] >= arrival_s[i - 1], "arrival times must not decrease");
+    }
+    std::vector<uint64_t> tickets((size_t)n, 0);
+    const int64_t d = sv->ix->d;
+    const auto t0 = Clock::now();
+    dade_status first = DADE_OK;
+    for (int64_t i = 0; i < n; ++i) {
+        const auto due = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(arrival_s[i]));
+        while (Clock::now() < due) {
+        }
+        const dade_status st = dade_server_submit(sv, q + i * d, 1, k[i], nprobe[i], alpha, delta_d,
+                                                  ids + i * k_stride, dists + i * k_stride, &tickets[(size_t)i]);
+        if (st != DADE_OK && first == DADE_OK) first = st;
+    }
+    if (submit_s) *submit_s = std::chrono::duration<double>(Clock::now() - t0).count();
+    for (int64_t i = 0; i < n; ++i) {
+        latency_s[i] = -1.0;
+        if (tickets[(size_t)i] == 0) continue;   // refused at submission
+        const dade_status st = dade_server_wait(sv, tickets[(size_t)i], -1, &latency_s[i]);
+        if (st != DADE_OK && first == DADE_OK) first = st;
+    }
+    return first;
+}
+
 dade_status dade_server_cancel(dade_server *sv, uint64_t ticket) {
     using namespace dade;
     set_error("");

@@ -97,6 +97,7 @@ SIGNATURES = {
     "dade_server_wait": (_i32, [_vp, C.c_uint64, _i64, _vp]),
     "dade_server_stats_get": (_i32, [_vp, _vp]),
     "dade_server_cancel": (_i32, [_vp, C.c_uint64]),
+    "dade_server_replay": (_i32, [_vp, _vp, _i64, _vp, _vp, _f32, _i32, _vp, _i32, _vp, _vp, _vp, _vp]),
     "dade_server_free": (None, [_vp]),
     "dade_graph_launch": (_i32, [_vp, _vp]),
     "dade_graph_free": (None, [_vp]),
@@ -488,6 +489,23 @@ class Server:
         _check(rc)
         q, ids, dists = self._live.pop(ticket)
         return ids, dists, lat.value
+
+    def replay(self, q, k, nprobe, alpha, delta_d, arrival_s):
+        """dade_server_replay: one-query requests q [n, d] submitted natively at arrival_s [n] seconds;
+        returns ids, dists [n, max k] (row i: its k[i] results), latencies [n] and the submit time."""
+        q = np.ascontiguousarray(q, np.float32)
+        k = np.ascontiguousarray(k, np.int32)
+        nprobe = np.ascontiguousarray(nprobe, np.int32)
+        arr = np.ascontiguousarray(arrival_s, np.float64)
+        n, ks = q.shape[0], int(k.max())
+        ids = np.empty((n, ks), np.int64)
+        dists = np.empty((n, ks), np.float32)
+        lat = np.empty(n, np.float64)
+        sub = C.c_double()
+        _check(lib().dade_server_replay(self._h, q.ctypes.data, n, k.ctypes.data, nprobe.ctypes.data, float(alpha),
+                                        int(delta_d), arr.ctypes.data, ks, ids.ctypes.data, dists.ctypes.data,
+                                        lat.ctypes.data, C.byref(sub)))
+        return ids, dists, lat, sub.value
 
     def cancel(self, ticket):
         """dade_server_cancel: result(ticket) then raises DadeError with status ECANCELLED."""

@@ -133,6 +133,28 @@ def test_cancel(index):
     srv.close()
 
 
+def test_native_replay(index):
+    """dade_server_replay submits one-query requests at given times from C++; every request's
+    result equals dade_query's for it alone, and the latencies are measured."""
+    ix, queries = index
+    rng = np.random.default_rng(9)
+    n = 300
+    picks = rng.integers(0, queries.shape[0], n)
+    ks = rng.choice([1, 10, 100], n).astype(np.int32)
+    nps = rng.choice([16, 32, 64], n).astype(np.int32)
+    arrivals = np.cumsum(rng.exponential(1.0 / 20000, n))
+    srv = dade.Server(ix, slots=4, max_batch=1024, max_k=100, max_nprobe=64, tile=128)
+    ids, d, lat, t_sub = srv.replay(queries[picks], ks, nps, 0.1, 32, arrivals)
+    st = srv.stats()
+    srv.close()
+    assert (lat > 0).all() and t_sub >= arrivals[-1]
+    assert st["requests_done"] == n and st["batches"] < n
+    for i in range(0, n, 7):
+        e_ids, e_d = _direct(ix, queries[picks[i]:picks[i] + 1], int(ks[i]), int(nps[i]), tile=128)
+        assert np.array_equal(ids[i, :ks[i]], e_ids[0])
+        assert np.array_equal(d[i, :ks[i]].view(np.uint32), e_d[0].view(np.uint32))
+
+
 def test_admission_by_bytes(index):
     ix, queries = index
     d, nc = ix.d, ix.n_clusters
