@@ -239,17 +239,21 @@ def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7, torch=None, xb
     """Requests of one query each, Poisson arrivals at each rate (requests/s),
     K and nprobe drawn per request from {1, 10, 100} x {16, 64, 128}, submitted
     by the library's native load generator (dade_server_replay).  The server
-    runs the tile schedule at the chosen point's delta_d and alpha, so requests
-    of any K and nprobe share batches (dade_query_mixed), overlapped on 4
-    streams.  Returns per rate: offered and served request rates, p50 / p99
+    runs the chosen point's delta_d and alpha, and its row rounds where the
+    point has them (else the tile schedule), so requests of any K and nprobe
+    share batches (dade_query_mixed), overlapped on 4 streams.  Returns per rate: offered and served request rates, p50 / p99
     latency (submit to results on the host, measured by the server); with the
     base on the device (xb), the served recall@K per nprobe against exact FP64
     ground truth."""
     n_lists = ix.info.n_clusters
     nprobes = [p for p in (16, 64, 128) if p <= n_lists]
-    keep = dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL
-    srv = dade.Server(ix, slots=4, max_batch=1024, max_k=100, max_nprobe=max(nprobes), tile=128,
-                      threads=point["threads"], schedule=dade.SCHED_TILE, flags=point["flags"] & keep)
+    # the chosen point's schedule where one launch serves mixed K and nprobe (the tile
+    # schedule, the list-major row rounds), else the tile schedule
+    rounds = point.get("schedule", 0) == dade.SCHED_ROUNDS and ix.info.d_pad >= 128
+    keep = dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL | (dade.FLAG_TC_PREFILTER if rounds else 0)
+    srv = dade.Server(ix, slots=4, max_batch=1024, max_k=100, max_nprobe=max(nprobes),
+                      tile=point["tile"] if rounds else 128, threads=point["threads"],
+                      schedule=dade.SCHED_ROUNDS if rounds else dade.SCHED_TILE, flags=point["flags"] & keep)
     rng = np.random.default_rng(seed)
     out, served = [], []
     for rate in rates:
@@ -274,7 +278,7 @@ def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7, torch=None, xb
     recall = served_recall(torch, xb, queries, served, nprobes) if xb is not None else None
     return {"requests": "1 query each, K in {1, 10, 100}, nprobe in " + str(nprobes) +
                         ", Poisson arrivals, native submitter (dade_server_replay)",
-            "schedule": "tile (mixed K and nprobe in one launch)",
+            "schedule": ("row rounds" if rounds else "tile") + " (mixed K and nprobe in one launch)",
             "slots": st["slots"], "batches": st["batches"], "mean_batch": round(st["queries"] / max(1, st["batches"]), 2),
             "max_inflight": st["max_inflight"], "rates": out, "recall_by_nprobe": recall}
 

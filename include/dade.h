@@ -342,9 +342,9 @@ void dade_graph_free(dade_graph *g);
  * own device workspace and pinned buffers, so batches in different slots
  * overlap on the GPU.  A batch is the oldest pending request plus every
  * later pending request it can run with, up to max_batch queries: under the
- * tile schedule every request with the same alpha and delta_d (mixed K and
- * nprobe run in one launch, dade_query_mixed), under the other schedules the
- * same K, nprobe, alpha and delta_d.  Every query's result depends only on
+ * tile schedule, and the row rounds where they run list-major, every request
+ * with the same alpha and delta_d (mixed K and nprobe run in one launch,
+ * dade_query_mixed), otherwise the same K, nprobe, alpha and delta_d.  Every query's result depends only on
  * that query, so a request gets the same result alone and in any mix.  With
  * a device_budget, admission is by bytes: a batch starts only while every
  * slot's staging buffers plus the workspace the slots' batches grew to (an
@@ -612,7 +612,10 @@ dade_status dade_query(const dade_index *ix, const float *q, int64_t nq, int32_t
  * host or device [nq] (host values are checked: 1..k_max, 1..nprobe_max;
  * device values are clamped into those ranges).  ids, dists: [nq * k_max],
  * row i holding query i's k[i] results, then id -1 / +inf.  The tile schedule
- * only (opts NULL or schedule DADE_SCHED_TILE; DADE_EINVAL otherwise).
+ * (opts NULL or DADE_SCHED_TILE) or the row rounds (DADE_SCHED_ROUNDS) where
+ * they run list-major (D > 112, delta_d of 16, 32, 64 or 128 dims, neither
+ * DADE_FLAG_SEED_SPLIT nor DADE_FLAG_LEAD; DADE_EUNSUPPORTED otherwise);
+ * DADE_EINVAL for other schedules.
  */
 dade_status dade_query_mixed(const dade_index *ix, const float *q, int64_t nq, const int32_t *k,
                              const int32_t *nprobe, int32_t k_max, int32_t nprobe_max, float alpha, int32_t delta_d,

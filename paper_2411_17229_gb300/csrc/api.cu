@@ -529,7 +529,8 @@ dade_status dade_query_mixed(const dade_index *ix, const float *q, int64_t nq, c
                              const dade_search_opts *opts, int64_t *ids, float *dists, dade_stream stream) {
     g_err.clear();
     DADE_TRY(validate_search(ix, nq, k_max, nprobe_max, alpha, delta_d, opts));
-    DADE_CHECK_ARG(!opts || opts->schedule == DADE_SCHED_TILE, "per-query K and nprobe need the tile schedule");
+    DADE_CHECK_ARG(!opts || opts->schedule == DADE_SCHED_TILE || opts->schedule == DADE_SCHED_ROUNDS,
+                   "per-query K and nprobe need the tile schedule or the row rounds");
     if (nq == 0) return DADE_OK;
     DADE_CHECK_ARG(q != nullptr && k != nullptr && nprobe != nullptr && ids != nullptr && dists != nullptr,
                    "NULL pointer");

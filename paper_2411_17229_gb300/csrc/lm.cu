@@ -48,7 +48,8 @@ struct LmArgs {
     const int *lq_off;           // [nc + 1] first entry of list c in lq_items
     const int *item_off;         // [nc + 1] first work item of list c
     unsigned *ctr;               // work counter
-    const float *r2src;          // first-phase squared distances [nq][k]; r^2 = entry k - 1
+    const float *r2src;          // first-phase squared distances [nq][k]; r^2 = entry k - 1 (k: the query's)
+    const int32_t *q_k;          // per-query K (at most k, the row stride), or NULL for k
     unsigned long long *acc;     // [nq][cap] accepted keys
     int *acnt;                   // [nq]
     int64_t *stats;              // [nq][4], added to; or null
@@ -67,6 +68,11 @@ struct LmArgs {
     float tc_c1, tc_c2;          // error bound of the expanded partial distance (see k_lm_tc)
     float coef[DADE_MAX_DIM / DADE_BLOCK];   // prune iff P > coef[j] r^2 after increment j
 };
+
+// The K of query q (rows of r2src and of the results have k entries).
+__device__ __forceinline__ int lm_kq(const LmArgs &a, int64_t q) {
+    return a.q_k ? min(max(a.q_k[q], 1), a.k) : a.k;
+}
 
 // End of the rows of a list of `len` members that a pass scans.
 __device__ __forceinline__ int lm_end(const LmArgs &a, int len) { return min(len, a.row_hi); }
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
         for (int g = tid; g < ng; g += LNT) {
             const int q = a.lq_items[qb + g];
             s_q[g] = q;
-            s_r2[g] = a.r2src[(int64_t)q * a.k + a.k - 1];
+            s_r2[g] = a.r2src[(int64_t)q * a.k + lm_kq(a, q) - 1];
         }
         for (int e = tid; e < ng * 16 * LNB; e += LNT) {
             const int g = e / (16 * LNB), kk = e % (16 * LNB);
@@ -530,7 +536,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
         for (int g = tid; g < ng; g += LNT) {
             const int q = a.lq_items[qb + g];
             s_q[g] = q;
-            const float r2 = a.r2src[(int64_t)q * a.k + a.k - 1];
+            const float r2 = a.r2src[(int64_t)q * a.k + lm_kq(a, q) - 1];
             s_r2[g] = r2;
             s_thr[g] = a.coef[0] * r2;
         }
@@ -826,7 +832,7 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         for (int g = tid; g < LG; g += LNT) {
             const bool in = g < ng;
             const int q = in ? a.lq_items[qb + g] : 0;
-            const float r2 = in ? a.r2src[(int64_t)q * a.k + a.k - 1] : 0.f;
+            const float r2 = in ? a.r2src[(int64_t)q * a.k + lm_kq(a, q) - 1] : 0.f;
             const float thr = a.coef[0] * r2;
             s_q[g] = q;
             s_r2[g] = r2;
@@ -1008,11 +1014,12 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
 // ---- work list -------------------------------------------------------------------
 // (query, list) pairs of probe positions [c0, c1) (probe rows of nprobe).
 __global__ void k_lm_count(const int32_t *__restrict__ probe, int64_t nq, int nprobe, int c0, int c1,
-                           int *__restrict__ cnt) {
+                           const int32_t *__restrict__ q_np, int *__restrict__ cnt) {
     const int64_t total = nq * (int64_t)(c1 - c0);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = e / (c1 - c0);
         const int j = c0 + (int)(e % (c1 - c0));
+        if (q_np && j >= q_np[q]) continue;   // past this query's own nprobe
         atomicAdd(&cnt[probe[q * nprobe + j]], 1);
     }
 }
@@ -1034,11 +1041,12 @@ __global__ void k_lm_items(const int *__restrict__ cnt, const ListMeta *__restri
 }
 
 __global__ void k_lm_scatter(const int32_t *__restrict__ probe, int64_t nq, int nprobe, int c0, int c1,
-                             int *__restrict__ fill, int32_t *__restrict__ lq_items) {
+                             const int32_t *__restrict__ q_np, int *__restrict__ fill, int32_t *__restrict__ lq_items) {
     const int64_t total = nq * (int64_t)(c1 - c0);
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = e / (c1 - c0);
         const int j = c0 + (int)(e % (c1 - c0));
+        if (q_np && j >= q_np[q]) continue;
         lq_items[atomicAdd(&fill[probe[q * nprobe + j]], 1)] = (int32_t)q;
     }
 }
@@ -1059,7 +1067,8 @@ constexpr int MT = 256;
 
 __global__ void __launch_bounds__(MT) k_lm_merge(int64_t *__restrict__ ids, float *__restrict__ dists, int k,
                                                  const unsigned long long *__restrict__ acc,
-                                                 const int *__restrict__ acnt, int64_t cap) {
+                                                 const int *__restrict__ acnt, int64_t cap,
+                                                 const int32_t *__restrict__ q_k) {
     __shared__ unsigned long long s1[DADE_MAX_K], sel[DADE_MAX_K];
     __shared__ unsigned hist[256];
     __shared__ unsigned long long s_prefix;
@@ -1067,6 +1076,7 @@ __global__ void __launch_bounds__(MT) k_lm_merge(int64_t *__restrict__ ids, floa
     __shared__ int s_n1;
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t q = blockIdx.x;
+    const int kq = q_k ? min(max(q_k[q], 1), k) : k;   // this query's K; rows have k entries
     if (tid == 0) s_n1 = 0;
     __syncthreads();
     for (int j = tid; j < k; j += MT) {   // first-phase results: a sorted prefix of valid entries
@@ -1080,10 +1090,10 @@ __global__ void __launch_bounds__(MT) k_lm_merge(int64_t *__restrict__ ids, floa
     const int n1 = s_n1, n2 = (int)min((int64_t)acnt[q], cap), n = n1 + n2;
     const unsigned long long *a2 = acc + q * cap;
     auto key = [&](int j) { return j < n1 ? s1[j] : a2[j - n1]; };
-    unsigned long long bound = ~0ull;   // select every key when n <= k
-    if (n > k) {
+    unsigned long long bound = ~0ull;   // select every key when n <= kq
+    if (n > kq) {
         unsigned long long prefix = 0, mask = 0;
-        unsigned rank = (unsigned)k;
+        unsigned rank = (unsigned)kq;
         for (int pass = 0; pass < 8; ++pass) {
             const int shift = 56 - 8 * pass;
             hist[tid] = 0;
@@ -1130,11 +1140,11 @@ __global__ void __launch_bounds__(MT) k_lm_merge(int64_t *__restrict__ ids, floa
         const unsigned long long kk = key(j);
         if (kk <= bound) {
             const unsigned slot = atomicAdd(&s_cnt, 1u);
-            if (slot < (unsigned)k) sel[slot] = kk;
+            if (slot < (unsigned)kq) sel[slot] = kk;
         }
     }
     __syncthreads();
-    const int m = min((int)s_cnt, k);
+    const int m = min((int)s_cnt, kq);
     for (int t = tid; t < k; t += MT) {
         if (t < m) {
             const unsigned long long kk = sel[t];
@@ -1281,7 +1291,7 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     DADE_TRY_CUDA(cudaMemsetAsync(w.lm_acnt.p, 0, sizeof(int) * (size_t)nq, s));
     DADE_TRY_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned), s));
     if (lists) {
-        k_lm_count<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, cnt);
+        k_lm_count<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, p.q_np, cnt);
         DADE_TRY(launch_check("k_lm_count"));
     }
     // the tensor-core bound needs a finite threshold: not in a first round (r = +inf)
@@ -1295,7 +1305,7 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     DADE_TRY(exclusive_scan_int(items, nc + 1, s));
     if (lists) {
         DADE_TRY_CUDA(cudaMemcpyAsync(fill, off, sizeof(int) * (size_t)(nc + 1), cudaMemcpyDeviceToDevice, s));
-        k_lm_scatter<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, fill, lq_items);
+        k_lm_scatter<<<grid_of(pairs, 256), 256, 0, s>>>(p.probe, nq, np, c0, c1, p.q_np, fill, lq_items);
         DADE_TRY(launch_check("k_lm_scatter"));
     }
     LmArgs a{};
@@ -1308,6 +1318,7 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     a.item_off = items;
     a.ctr = ctr;
     a.r2src = p.dists;
+    a.q_k = p.q_k;
     a.acc = w.lm_acc.as<unsigned long long>();
     a.acnt = w.lm_acnt.as<int>();
     a.stats = p.stats;
@@ -1340,7 +1351,7 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
         DADE_TRY(p.stats ? launch_lm_gb<true>(a, gb, s) : launch_lm_gb<false>(a, gb, s));
     else
         DADE_TRY(p.stats ? launch_lm_gen<true>(a, gb, s) : launch_lm_gen<false>(a, gb, s));
-    k_lm_merge<<<(unsigned)nq, MT, 0, s>>>(p.ids, p.dists, p.k, a.acc, a.acnt, cap);
+    k_lm_merge<<<(unsigned)nq, MT, 0, s>>>(p.ids, p.dists, p.k, a.acc, a.acnt, cap, p.q_k);
     return launch_check("k_lm_merge");
 }
 
@@ -1381,7 +1392,7 @@ static dade_status seeded_split(const dade_index *ix, int64_t nq, const ScanPara
         q.nprobe = n;
         q.parts = parts;
         DADE_TRY(scan(ix, nq, q, s));
-        k_lm_merge<<<(unsigned)nq, MT, 0, s>>>(p.ids, p.dists, p.k, base.acc, base.acnt, cap);
+        k_lm_merge<<<(unsigned)nq, MT, 0, s>>>(p.ids, p.dists, p.k, base.acc, base.acnt, cap, nullptr);
         return launch_check("k_lm_merge");
     };
     if (whole) {
@@ -1509,6 +1520,11 @@ dade_status scan_rounds(const dade_index *ix, int64_t nq, const ScanParams &p, c
         return DADE_OK;
     }
     // query-major: every round over all probe positions, each query's lists in parts over thread blocks
+    if (p.q_k || p.q_np) {
+        set_error("per-query K and nprobe under the row rounds need the list-major passes (D > 112, delta_d of "
+                  "16, 32, 64 or 128 dims, no DADE_FLAG_SEED_SPLIT or DADE_FLAG_LEAD)");
+        return DADE_EUNSUPPORTED;
+    }
     Workspace &w = ws(ix);
     const int64_t cap = accept_cap(ix, np);
     DADE_TRY(w.lm_acc.ensure(sizeof(unsigned long long) * (size_t)(nq * cap)));
@@ -1533,7 +1549,7 @@ dade_status scan_rounds(const dade_index *ix, int64_t nq, const ScanParams &p, c
         q.row_lo = (int)lo;
         q.row_hi = (int)std::min<int64_t>(hi, INT_MAX);
         DADE_TRY(scan(ix, nq, q, s));
-        k_lm_merge<<<(unsigned)nq, MT, 0, s>>>(p.ids, p.dists, p.k, q.acc, q.acnt, cap);
+        k_lm_merge<<<(unsigned)nq, MT, 0, s>>>(p.ids, p.dists, p.k, q.acc, q.acnt, cap, nullptr);
         DADE_TRY(launch_check("k_lm_merge"));
     }
     return DADE_OK;

@@ -447,8 +447,8 @@ dade_status scan_fast(const scanning::ScanArgs &a, int64_t nq, bool fd, int thre
 
 dade_status scan(const dade_index *ix, int64_t nq, const ScanParams &p, cudaStream_t s) {
     if (nq == 0) return DADE_OK;
-    if ((p.q_k || p.q_np) && (p.schedule != DADE_SCHED_TILE || p.parts > 0)) {
-        set_error("per-query K and nprobe need the tile schedule");
+    if ((p.q_k || p.q_np) && ((p.schedule != DADE_SCHED_TILE && p.schedule != DADE_SCHED_ROUNDS) || p.parts > 0)) {
+        set_error("per-query K and nprobe need the tile schedule or the row rounds");
         return DADE_EUNSUPPORTED;
     }
     if (p.schedule == DADE_SCHED_SEEDED && p.seed_lists > 0 && p.seed_lists < p.nprobe)

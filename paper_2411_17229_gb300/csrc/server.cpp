@@ -6,10 +6,10 @@
 // buffers and a completion event, so batches in different slots overlap on
 // the GPU.  When a slot is free the dispatcher forms a batch from the oldest
 // pending request and every later pending request it can run with, up to
-// max_batch queries: under the tile schedule any request with the same alpha
-// and delta_d (one launch serves a K and an nprobe per query,
-// dade_query_mixed), under the other schedules the same (K, nprobe, alpha,
-// delta_d).  It copies the queries in, runs the query step (rotation, probe,
+// max_batch queries: under the tile schedule, and the row rounds where they
+// run list-major, any request with the same alpha and delta_d (one launch
+// serves a K and an nprobe per query, dade_query_mixed), otherwise the same
+// (K, nprobe, alpha, delta_d).  It copies the queries in, runs the query step (rotation, probe,
 // scan) on the slot's stream, copies the results out and records the event.
 // A finished slot's results are scattered to the requests' host buffers and
 // their tickets complete; requests that arrived meanwhile are admitted as
@@ -108,8 +108,16 @@ struct dade_server {
         }
     }
 
-    // One launch serves a K and an nprobe per query under the tile schedule.
-    bool mixed() const { return o.schedule == DADE_SCHED_TILE; }
+    // Whether one launch serves a K and an nprobe per query at this delta_d: the tile
+    // schedule, or the row rounds where they run list-major (D > 112, delta_d of 16, 32,
+    // 64 or 128 dims, neither the split passes nor the low-precision prefilter).
+    bool mixes(int32_t delta_d) const {
+        if (o.schedule == DADE_SCHED_TILE) return true;
+        if (o.schedule != DADE_SCHED_ROUNDS || ix->nb < 8 || (o.flags & (DADE_FLAG_SEED_SPLIT | DADE_FLAG_LEAD)))
+            return false;
+        const int gb = o.mode == DADE_MODE_FD ? 8 : std::min(delta_d / 16, ix->nb);
+        return gb == 1 || gb == 2 || gb == 4 || gb == 8;
+    }
 
     // Workspace bytes of a batch of nq queries (estimate of what the query step grows it to):
     // raw and rotated queries, probe distances and lists, results, the tensor-core operand
@@ -163,7 +171,7 @@ struct dade_server {
         so.seed_lists = o.seed_lists;
         so.flags = o.flags;
         so.stage_dims = o.stage_dims;
-        if (mixed())
+        if (mixes(r0.delta_d))
             DADE_TRY(dade_query_mixed(ix, s.q_dev.as<float>(), nq, s.k_host, s.np_host, kmax, npmax, r0.alpha,
                                       r0.delta_d, &so, s.ids_dev.as<int64_t>(), s.dists_dev.as<float>(),
                                       (dade_stream)s.stream));
@@ -238,7 +246,7 @@ struct dade_server {
                 s.reqs.assign(1, first);
                 for (auto it = pending.begin(); it != pending.end();) {
                     const bool same = it->alpha == first.alpha && it->delta_d == first.delta_d &&
-                                      (mixed() || (it->k == first.k && it->nprobe == first.nprobe));
+                                      (mixes(first.delta_d) || (it->k == first.k && it->nprobe == first.nprobe));
                     const int32_t k2 = std::max(kmax, it->k), np2 = std::max(npmax, it->nprobe);
                     if (same && nq + it->nq <= o.max_batch && fits(s, batch_bytes(nq + it->nq, k2, np2))) {
                         nq += it->nq;

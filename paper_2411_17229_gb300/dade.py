@@ -352,15 +352,15 @@ class Index:
         return ids, dists
 
     def query_mixed(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, threads=0, flags=0,
-                    stage_dims=0, wait_ns=0, stream=None):
+                    stage_dims=0, wait_ns=0, schedule=SCHED_TILE, list_chunk=0, stream=None):
         """dade_query_mixed: per-query K and nprobe (int32 arrays [nq], host or device); ids / dists
-        [nq, max K].  Tile schedule."""
+        [nq, max K].  Tile schedule or list-major row rounds."""
         kk = k if hasattr(k, "data_ptr") else np.ascontiguousarray(k, dtype=np.int32)
         pp = nprobe if hasattr(nprobe, "data_ptr") else np.ascontiguousarray(nprobe, dtype=np.int32)
         k_max = int(kk.max().item() if hasattr(kk, "data_ptr") else kk.max())
         np_max = int(pp.max().item() if hasattr(pp, "data_ptr") else pp.max())
-        o = SearchOpts(mode=mode, tile=tile, threads=threads, schedule=SCHED_TILE, flags=flags, stage_dims=stage_dims,
-                       wait_ns=wait_ns)
+        o = SearchOpts(mode=mode, tile=tile, threads=threads, schedule=schedule, flags=flags, stage_dims=stage_dims,
+                       wait_ns=wait_ns, list_chunk=list_chunk)
         _check(lib().dade_query_mixed(self._h, _ptr(q), q.shape[0], _ptr(kk), _ptr(pp), k_max, np_max, float(alpha),
                                       int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists

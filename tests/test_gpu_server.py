@@ -40,7 +40,9 @@ def _direct(ix, q, k, nprobe, **opts):
 
 
 @pytest.mark.parametrize("opts", [dict(tile=256), dict(tile=256, schedule=dade.SCHED_SEEDED, seed_lists=2,
-                                                        flags=dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL)])
+                                                        flags=dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL),
+                                  dict(tile=16, schedule=dade.SCHED_ROUNDS, flags=dade.FLAG_QUERY_ORDER)],
+                         ids=["tile", "seeded", "rounds"])
 def test_results_alone_and_in_the_mix(index, opts):
     ix, queries = index
     rng = np.random.default_rng(11)
@@ -69,13 +71,18 @@ def test_results_alone_and_in_the_mix(index, opts):
     assert np.array_equal(got[7][0], alone_ids) and np.array_equal(got[7][1].view(np.uint32), alone_d.view(np.uint32))
     assert st["requests_done"] == st["requests"] == 49
     assert st["batches"] < 49                # compatible requests were batched together
-    if opts.get("schedule", dade.SCHED_TILE) == dade.SCHED_TILE:
+    if opts.get("schedule", dade.SCHED_TILE) in (dade.SCHED_TILE, dade.SCHED_ROUNDS):
         assert st["batches"] <= 12           # mixed K and nprobe in the same batches
     assert st["max_inflight"] >= 2           # batches overlapped on the GPU
 
 
+SCHEDULES = {"tile": dict(tile=128), "rounds": dict(tile=16, schedule=dade.SCHED_ROUNDS),
+             "rounds-tc": dict(tile=16, schedule=dade.SCHED_ROUNDS, flags=dade.FLAG_TC_PREFILTER)}
+
+
+@pytest.mark.parametrize("sched", list(SCHEDULES))
 @pytest.mark.parametrize("mode", [dade.MODE_DADE, dade.MODE_FD])
-def test_query_mixed_equals_each_query_alone(index, mode):
+def test_query_mixed_equals_each_query_alone(index, mode, sched):
     ix, queries = index
     rng = np.random.default_rng(5)
     q = np.ascontiguousarray(queries[:200])
@@ -84,10 +91,11 @@ def test_query_mixed_equals_each_query_alone(index, mode):
     kmax = int(ks.max())
     ids = np.empty((q.shape[0], kmax), np.int64)
     d = np.empty((q.shape[0], kmax), np.float32)
-    ix.query_mixed(q, ks, nps, 0.1, 32, ids, d, mode=mode, tile=128)
+    kw = SCHEDULES[sched]
+    ix.query_mixed(q, ks, nps, 0.1, 32, ids, d, mode=mode, **kw)
     for (k, npr) in {(int(a), int(b)) for a, b in zip(ks, nps)}:
         rows = np.flatnonzero((ks == k) & (nps == npr))
-        e_ids, e_d = _direct(ix, q[rows], k, npr, mode=mode, tile=128)
+        e_ids, e_d = _direct(ix, q[rows], k, npr, mode=mode, **kw)
         assert np.array_equal(ids[rows, :k], e_ids)
         assert np.array_equal(d[rows, :k].view(np.uint32), e_d.view(np.uint32))
         assert (ids[rows, k:] == -1).all() and np.isinf(d[rows, k:]).all()
@@ -96,7 +104,7 @@ def test_query_mixed_equals_each_query_alone(index, mode):
     qd = torch.from_numpy(q).cuda()
     ids2 = torch.empty(q.shape[0], kmax, dtype=torch.int64, device="cuda")
     d2 = torch.empty(q.shape[0], kmax, dtype=torch.float32, device="cuda")
-    ix.query_mixed(qd, kt, nt, 0.1, 32, ids2, d2, mode=mode, tile=128)
+    ix.query_mixed(qd, kt, nt, 0.1, 32, ids2, d2, mode=mode, **kw)
     ix.sync()
     assert np.array_equal(ids2.cpu().numpy(), ids)
     assert np.array_equal(d2.cpu().numpy().view(np.uint32), d.view(np.uint32))
