@@ -662,7 +662,8 @@ struct TcSmem {   // dynamic shared memory of k_lm_tc (1024-byte aligned base)
     static constexpr size_t qs_off(int gb) { return b_off(gb) + b_bytes(gb); }
     static constexpr size_t sv_off(int gb) { return qs_off(gb) + sizeof(float) * LG * 16 * gb; }
     static constexpr size_t mask_off(int gb) { return sv_off(gb) + sizeof(Surv) * LNW * QCAP; }
-    static constexpr size_t total(int gb) { return mask_off(gb) + 2 * sizeof(unsigned) * LTC; }
+    // the kept-pair masks of a tile (two query halves), one buffer per tile parity with the ring of four
+    static constexpr size_t total(int gb) { return mask_off(gb) + (tc_ring(gb) > 2 ? 4 : 2) * sizeof(unsigned) * LTC; }
 };
 
 // Shared-memory matrix descriptor without swizzle: start address / 16 (bits
@@ -730,7 +731,7 @@ __device__ __forceinline__ int find_list(const int *__restrict__ off, int nc, in
 template <int GB, bool STATS>
 __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_constant__ CUtensorMap tmap) {
     constexpr int NA = tc_ring(GB);                 // staged tiles
-    constexpr int PRE = NA == 2 ? 2 : NA - 1;       // tiles queued before an item's first MMA
+    constexpr int PRE = 2;                          // tiles queued before an item's first MMA
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[NA], mdone[2];
     __shared__ uint32_t tmem_base;
@@ -867,66 +868,47 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         __syncthreads();
         if (tid == 0 && t0 < ntile && !mma(t0)) failed = true;
 
-        // Tile t: thread 0 queues tile t + 1's MMAs (they run during this tile's reads),
-        // waits for tile t's, and the block meets; with a ring of four, tile t + 3's rows
-        // are then queued into the slot tile t - 1 left (every thread is past its reads).
-        // The epilogue reads accumulator t & 1 and writes the masks; a second barrier;
-        // then the FP32 path of the kept pairs from the staged rows.  With a ring of two,
-        // a third barrier frees tile t's slot for tile t + 2.
-        for (int t = t0; t < ntile; ++t) {
-            const int buf = t & 1, i0 = a.row_lo + t * LTC, tn = min(LTC, rend - i0);
+        // Tile t's epilogue (every warp): candidate mrow against the queries of half qh,
+        // from accumulator t & 1; the kept pairs as bits of the tile's masks.
+        auto epilogue = [&](int t) {
+            const int i0 = a.row_lo + t * LTC, tn = min(LTC, rend - i0);
             const float *af = reinterpret_cast<const float *>(abuf + (size_t)(t % NA) * TcSmem::a_bytes(GB));
-            if (tid == 0 && !failed && t + 1 < ntile && !mma(t + 1)) failed = true;   // overlaps this tile's reads
-            bool ok = !failed;
-            if (tid == 0 && ok) {
-                ok = wait_bounded(su32(&mdone[buf]), mph[buf] & 1u, a.wait_ns);
-                if (ok) {
-                    ++mph[buf];
-                    mpend[buf] = false;
-                }
-            }
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-            if constexpr (NA > 2) {
-                if (tid == 0 && t + NA - 1 < ntile) issue(t + NA - 1);
-            }
-            lt_fence_after();
-            {   // candidate mrow against the queries of half qh
-                const int mrow = 32 * (warp & 3) + lane, qh = warp >> 2;
-                uint32_t hi[16], lo2[16];
-                const uint32_t tb = tmem + (uint32_t)(buf * TCN) + ((uint32_t)(32 * (warp & 3)) << 16);
-                lt_ld16(tb + (uint32_t)(qh * 16), hi);
-                lt_ld16(tb + (uint32_t)(LG + qh * 16), lo2);
-                unsigned bits = 0u;
-                if (mrow < tn) {
-                    float on = 0.f;   // ||o'||^2 over the increment, from the staged rows
+            unsigned *mk_t = mask + (NA > 2 ? (t & 1) : 0) * 2 * LTC;
+            const int mrow = 32 * (warp & 3) + lane, qh = warp >> 2;
+            uint32_t hi[16], lo2[16];
+            const uint32_t tb = tmem + (uint32_t)((t & 1) * TCN) + ((uint32_t)(32 * (warp & 3)) << 16);
+            lt_ld16(tb + (uint32_t)(qh * 16), hi);
+            lt_ld16(tb + (uint32_t)(LG + qh * 16), lo2);
+            unsigned bits = 0u;
+            if (mrow < tn) {
+                float on = 0.f;   // ||o'||^2 over the increment, from the staged rows
 #pragma unroll
-                    for (int b = 0; b < GB; ++b)
+                for (int b = 0; b < GB; ++b)
 #pragma unroll
-                        for (int kc = 0; kc < 4; ++kc) {
-                            const float4 v = *reinterpret_cast<const float4 *>(af + ((size_t)(b * 4 + kc) * LTC + mrow) * 4);
-                            on = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, on))));
-                        }
-                    const float ocn = sqrtf(on);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int g = qh * 16 + j;
-                        const float dot = __uint_as_float(hi[j]) + __uint_as_float(lo2[j]);
-                        const float sq = s_qn[g] + on;
-                        const float pt = fmaf(-2.f, dot, sq);
-                        const float err = fmaf(a.tc_c1, sq, a.tc_c2 * (s_qcn[g] * ocn));
-                        const bool drop = pt - err > s_thr2[g];
-                        bits |= (unsigned)(g < ng && !drop) << j;
+                    for (int kc = 0; kc < 4; ++kc) {
+                        const float4 v = *reinterpret_cast<const float4 *>(af + ((size_t)(b * 4 + kc) * LTC + mrow) * 4);
+                        on = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, on))));
                     }
+                const float ocn = sqrtf(on);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int g = qh * 16 + j;
+                    const float dot = __uint_as_float(hi[j]) + __uint_as_float(lo2[j]);
+                    const float sq = s_qn[g] + on;
+                    const float pt = fmaf(-2.f, dot, sq);
+                    const float err = fmaf(a.tc_c1, sq, a.tc_c2 * (s_qcn[g] * ocn));
+                    const bool drop = pt - err > s_thr2[g];
+                    bits |= (unsigned)(g < ng && !drop) << j;
                 }
-                mask[qh * LTC + mrow] = bits;
             }
-            lt_fence_before();
-            __syncthreads();
-            // the pairs the bound keeps: the FP32 first increment from the staged rows, and
-            // the survivors of its test to the warp's queue
+            mk_t[qh * LTC + mrow] = bits;
+        };
+        // Tile t's kept pairs (warp per query): the FP32 first increment from the staged
+        // rows, and the survivors of its test to the warp's queue.
+        auto recheck = [&](int t) {
+            const int i0 = a.row_lo + t * LTC, tn = min(LTC, rend - i0);
+            const float *af = reinterpret_cast<const float *>(abuf + (size_t)(t % NA) * TcSmem::a_bytes(GB));
+            const unsigned *mk_t = mask + (NA > 2 ? (t & 1) : 0) * 2 * LTC;
             for (int g = warp; g < ng; g += LNW) {
                 if (qn + LTC > QCAP) {
                     lm_drain<GB, STATS, false>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
@@ -938,7 +920,7 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
                 int nk = 0;
                 for (int m0 = 0; m0 < tn; m0 += 32) {
                     const int mm = m0 + lane;
-                    const bool keep = mm < tn && ((mask[qh * LTC + mm] >> jb) & 1u);
+                    const bool keep = mm < tn && ((mk_t[qh * LTC + mm] >> jb) & 1u);
                     const unsigned mk = __ballot_sync(0xffffffffu, keep);
                     if (keep) cand_list[nk + __popc(mk & ((1u << lane) - 1u))] = Surv{mm, 0.f};
                     nk += __popc(mk);
@@ -984,8 +966,62 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
                 }
                 __syncwarp();
             }
-            if constexpr (NA == 2) {
-                __syncthreads();   // tile t's slot, the masks and accumulator `buf` are free
+        };
+        // thread 0: tile t's MMAs done (bounded); the block meets (false: every thread leaves)
+        auto tile_ready = [&](int t) -> bool {
+            bool ok = !failed;
+            if (tid == 0 && ok) {
+                ok = wait_bounded(su32(&mdone[t & 1]), mph[t & 1] & 1u, a.wait_ns);
+                if (ok) {
+                    ++mph[t & 1];
+                    mpend[t & 1] = false;
+                }
+            }
+            return !__syncthreads_or(!ok);
+        };
+
+        if constexpr (NA > 2) {
+            // Ring of four, one block barrier per tile.  Iteration t: tile t's MMAs done and
+            // the block met, so every warp is past tile t - 1's epilogue and tile t - 2's
+            // FP32 pass; thread 0 then queues tile t + 1's MMAs into accumulator (t + 1) & 1
+            // (tile t - 1's, read) and tile t + 2's rows into tile t - 2's slot; the warps
+            // read tile t's accumulator into its masks (a buffer per tile parity) and run the
+            // FP32 pass of tile t - 1, whose rows and masks nothing touches before the next
+            // meeting.  Tile t's slot holds its rows through tile t + 1's pass.
+            for (int t = t0; t < ntile; ++t) {
+                if (!tile_ready(t)) {
+                    failed = true;
+                    break;
+                }
+                if (tid == 0) {
+                    if (t + 1 < ntile && !mma(t + 1)) failed = true;   // the next meeting reports it
+                    if (t + 2 < ntile) issue(t + 2);
+                }
+                lt_fence_after();
+                epilogue(t);
+                lt_fence_before();
+                if (t > t0) recheck(t - 1);
+            }
+            if (!failed && t0 < ntile) {
+                __syncthreads();   // the last tile's masks
+                recheck(ntile - 1);
+            }
+        } else {
+            // Ring of two: tile t + 1's MMAs queued, tile t's waited for, the block meets;
+            // the epilogue, a second barrier, the FP32 pass; a third barrier frees tile t's
+            // slot, the masks and accumulator t & 1 for tile t + 2.
+            for (int t = t0; t < ntile; ++t) {
+                if (tid == 0 && !failed && t + 1 < ntile && !mma(t + 1)) failed = true;   // overlaps this tile's reads
+                if (!tile_ready(t)) {
+                    failed = true;
+                    break;
+                }
+                lt_fence_after();
+                epilogue(t);
+                lt_fence_before();
+                __syncthreads();
+                recheck(t);
+                __syncthreads();
                 if (tid == 0 && t + 2 < ntile) issue(t + 2);
             }
         }
