@@ -59,6 +59,7 @@ struct LmArgs {
     int q_stride, nc, k, d, tail_nb0, tail_w;
     int nb, n_inc;               // 16-dim blocks of the layout, increments (k_lm_g)
     int chunk_tiles;             // tiles of a list per work item (a long list is several items)
+    int lg;                      // queries per work item (k_lm_tc: 32 or 64; the others LG)
     uint64_t wait_ns;            // limit of every bounded wait on a copy or an MMA
     const int *never;            // failure-path check: a device word nothing sets (else NULL)
     int row_lo, row_hi;          // rows [row_lo, min(len, row_hi)) of every list are scanned; tiles
@@ -369,15 +370,22 @@ __global__ void __launch_bounds__(LNT, 3) k_lm(const LmArgs a) {
 // round trips out of the per-tile barrier: the warp that queued them drains
 // them when its queue fills or the item ends.
 constexpr int QCAP = 256;         // survivors queued per warp
-constexpr int QROW_BITS = 26;     // rows of a list below 2^26 (the query slot above)
+// A queued survivor's idx packs the item's query slot (6 bits, 0..63) above its row in the
+// list (26 bits), read as an unsigned word: the list-major passes need lists below 2^26 rows.
+constexpr int QROW_BITS = 26;
+__device__ __forceinline__ int surv_key(int g, int row) {
+    return (int)(((unsigned)g << QROW_BITS) | (unsigned)row);
+}
 
 inline size_t LmSmem::total_g(int gb) {
     return 2 * stage(gb) + sizeof(float) * LG * 16 * gb + sizeof(Surv) * LNW * QCAP;
 }
 
-template <int GB, bool STATS, bool FIRST>
+// NSL: query slots per warp (the item's queries g = warp + LNW * slot); kb: the
+// per-item K-best stage, or NULL (accepted keys go straight to the accept buffers).
+template <int GB, bool STATS, bool FIRST, int NSL = QSLOT>
 __device__ void lm_drain(const LmArgs &a, const ListMeta &m, const Surv *sv, int n, const int *s_q, const float *s_r2,
-                         const float *s_thr, const float *qs, bool kbest, KBest &kb) {
+                         const float *s_thr, const float *qs, KBest *kb) {
     constexpr int WB = 8;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quad = lane >> 2, lq = lane & 3;
     const int nb = a.nb, n_inc = a.n_inc;
@@ -385,7 +393,7 @@ __device__ void lm_drain(const LmArgs &a, const ListMeta &m, const Surv *sv, int
         const int sidx = r0 + quad;
         const bool act = sidx < n;
         const Surv v = act ? sv[sidx] : Surv{0, 0.f};
-        const int g = v.idx >> QROW_BITS;
+        const int g = (int)((unsigned)v.idx >> QROW_BITS);
         const int64_t i = v.idx & ((1 << QROW_BITS) - 1);
         const int q = s_q[g];
         const float r2 = s_r2[g];
@@ -463,9 +471,9 @@ __device__ void lm_drain(const LmArgs &a, const ListMeta &m, const Surv *sv, int
         const unsigned long long key = ((unsigned long long)__float_as_uint(p) << 32) | (unsigned)id;
         // the warp's queries are slots g = warp + LNW s; stage each slot's accepted keys together
 #pragma unroll
-        for (int sl = 0; sl < QSLOT; ++sl) {
+        for (int sl = 0; sl < NSL; ++sl) {
             const bool ts = take && g == warp + LNW * sl;
-            if (kbest) kb_take(kb, warp, sl, a.k, ts, key);
+            if (kb) kb_take(*kb, warp, sl, a.k, ts, key);
             else lm_append(a, ts, s_q[warp + LNW * sl], key);
         }
     }
@@ -559,7 +567,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
             const float *st = stage + (size_t)buf * GB * LT * 16;
             for (int g = warp; g < ng; g += LNW) {
                 if (qn + LT > QCAP) {   // room for this query's survivors of the tile
-                    lm_drain<GB, STATS, false>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
+                    lm_drain<GB, STATS, false>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest ? &kb : nullptr);
                     qn = 0;
                     __syncwarp();
                 }
@@ -583,7 +591,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
                     const bool lead = act && lq == 0;
                     const bool keep = lead && !(p > c0);
                     const unsigned mk = __ballot_sync(0xffffffffu, keep);
-                    if (keep) queue[qn + __popc(mk & ((1u << lane) - 1u))] = Surv{(g << QROW_BITS) | (i0 + cand), p};
+                    if (keep) queue[qn + __popc(mk & ((1u << lane) - 1u))] = Surv{surv_key(g, i0 + cand), p};
                     qn += __popc(mk);
                     if (STATS && lead) {
                         ++st_c;
@@ -611,7 +619,7 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
             if (tid == 0 && t + 2 < ntile) issue(t + 2);
         }
         __syncwarp();
-        lm_drain<GB, STATS, false>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
+        lm_drain<GB, STATS, false>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest ? &kb : nullptr);
         qn = 0;
         __syncwarp();
         if (kbest)   // the item's K best per query go to the accept buffers
@@ -620,20 +628,20 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
 }
 
 // ---- the first increment on the tensor cores (list-major passes) -----------------------
-// For a tile of LTC candidates of one list and the item's queries (up to LG),
+// For a tile of LTC candidates of one list and the item's queries (up to LGT),
 // the partial distance over the first increment is expanded as
 //     X = ||q'||^2 + ||o'||^2 - 2 q'.o'   (FP32 rows q', o' of the index).
 // The tile's FP32 rows arrive by TMA in the tensor cores' canonical K-major
 // layout without swizzle: per 16-dim block b and 4-float chunk kc, a box of
 // 4 floats x 128 rows (16 B per row; core matrices of 8 rows contiguous).  One
 // thread issues tcgen05.mma kind::tf32 (A = the tile, M = 128 candidates, read
-// by the tensor core as TF32; B = the queries split into TF32 hi + lo parts,
-// N = 64; K = 8 dims per instruction; FP32 accumulation in tensor memory),
+// by the tensor core as TF32; B = the item's queries rounded to TF32, N = 64;
+// K = 8 dims per instruction; FP32 accumulation in tensor memory),
 // two accumulators in turn, so that the MMA of the next tile runs while the
 // threads read this one's (tcgen05.ld).  Every (query, candidate) pair is then
 // tested with a certified bound: X - E is a lower bound of the exact partial
 // distance, E = c1 (||q'||^2 + ||o'||^2) + c2 ||q'|| ||o'|| covering the TF32
-// reading of the rows (2^-10), the split of the queries (2^-22), the FP32 sums
+// reading of the rows (2^-10), the rounding of the queries to TF32 (2^-11), the FP32 sums
 // and the tensor-core accumulation (host-side constants); a pair is dropped
 // only when X - E exceeds the FP32 threshold by 2^-15 relative, more than the
 // rounding of the FP32 path's own partial sum, so the FP32 test would drop it
@@ -642,7 +650,8 @@ __global__ void __launch_bounds__(LNT, 3) k_lm_g(const LmArgs a) {
 // survivors are queued for the later increments: results and counters are
 // those of the FP32 list-major path.
 constexpr int LTC = 128;            // candidates per tile: M of the MMA
-constexpr int TCN = 2 * LG;         // N of the MMA: the hi and the lo TF32 parts of the item's queries
+constexpr int LGT = 64;             // queries per work item of k_lm_tc
+constexpr int TCN = LGT;            // N of the MMA: the item's queries, one TF32 part each
 constexpr uint32_t TC_COLS = 128;   // tensor-memory columns: two FP32 accumulators of N = 64
 
 // Instruction descriptor of kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
@@ -660,9 +669,9 @@ struct TcSmem {   // dynamic shared memory of k_lm_tc (1024-byte aligned base)
     static constexpr size_t b_off(int gb) { return tc_ring(gb) * a_bytes(gb); }     // the ring of tiles
     static constexpr size_t b_bytes(int gb) { return (size_t)gb * 4 * TCN * 16; }
     static constexpr size_t qs_off(int gb) { return b_off(gb) + b_bytes(gb); }
-    static constexpr size_t sv_off(int gb) { return qs_off(gb) + sizeof(float) * LG * 16 * gb; }
+    static constexpr size_t sv_off(int gb) { return qs_off(gb) + sizeof(float) * LGT * 16 * gb; }
     static constexpr size_t mask_off(int gb) { return sv_off(gb) + sizeof(Surv) * LNW * QCAP; }
-    // the kept-pair masks of a tile (two query halves), one buffer per tile parity with the ring of four
+    // the kept-pair masks of a tile (two query halves of 32 bits), one buffer per tile parity with the ring of four
     static constexpr size_t total(int gb) { return mask_off(gb) + (tc_ring(gb) > 2 ? 4 : 2) * sizeof(unsigned) * LTC; }
 };
 
@@ -691,6 +700,17 @@ __device__ __forceinline__ void lt_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         "%15}, [%16];\n"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void lt_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -735,15 +755,13 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[NA], mdone[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int s_item, s_next, s_c, s_q[LG];
-    __shared__ float s_r2[LG], s_qn[LG], s_qcn[LG], s_thr[LG], s_thr2[LG];
-    __shared__ KBest kb;
-    const bool kbest = a.k <= KB_K;
+    __shared__ int s_item, s_next, s_c, s_q[LGT];
+    __shared__ float s_r2[LGT], s_qn[LGT], s_qcn[LGT], s_thr[LGT], s_thr2[LGT];
     unsigned char *abuf = smem;
     unsigned char *bsm = smem + TcSmem::b_off(GB);
     float *qs = reinterpret_cast<float *>(smem + TcSmem::qs_off(GB));
     Surv *survs = reinterpret_cast<Surv *>(smem + TcSmem::sv_off(GB));
-    unsigned *mask = reinterpret_cast<unsigned *>(smem + TcSmem::mask_off(GB));   // [2][LTC] query halves
+    unsigned *mask = reinterpret_cast<unsigned *>(smem + TcSmem::mask_off(GB));   // [parity][half][LTC]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, quad = lane >> 2, lq = lane & 3;
     Surv *queue = survs + warp * QCAP;   // this warp's survivors, drained when full or at the item's end
     int qn = 0;                          // entries queued (the same on every lane of the warp)
@@ -760,7 +778,6 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         fence_mbar_init();
         s_item = (int)atomicAdd(a.ctr, 1u);
     }
-    if (tid < LNW * QSLOT) kb.cnt[tid / QSLOT][tid % QSLOT] = 0;
     lt_fence_before();
     __syncthreads();
     lt_fence_after();
@@ -788,10 +805,10 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         }
         __syncthreads();
         c = s_c;
-        const int ngroups = (a.lq_off[c + 1] - a.lq_off[c] + LG - 1) / LG;
+        const int ngroups = (a.lq_off[c + 1] - a.lq_off[c] + a.lg - 1) / a.lg;
         const int local = item - a.item_off[c];
-        const int qb = a.lq_off[c] + (local % ngroups) * LG;
-        const int ng = min(LG, a.lq_off[c + 1] - qb);
+        const int qb = a.lq_off[c] + (local % ngroups) * a.lg;
+        const int ng = min(a.lg, a.lq_off[c + 1] - qb);
         const ListMeta m = a.meta[c];
         const int rend = lm_end(a, m.len);
         const int t0 = (local / ngroups) * a.chunk_tiles;
@@ -830,7 +847,7 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         };
         if (tid == 0)
             for (int t = t0; t < t0 + PRE && t < ntile; ++t) issue(t);
-        for (int g = tid; g < LG; g += LNT) {
+        for (int g = tid; g < LGT; g += LNT) {
             const bool in = g < ng;
             const int q = in ? a.lq_items[qb + g] : 0;
             const float r2 = in ? a.r2src[(int64_t)q * a.k + lm_kq(a, q) - 1] : 0.f;
@@ -840,21 +857,18 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
             s_thr[g] = thr;
             s_thr2[g] = thr * (1.f + 0x1p-15f);
         }
-        // the queries' first increment: FP32 for the FP32 path, TF32 hi / lo for the MMA
-        // (B rows g and LG + g, K-major core matrices of 8 rows x 4 floats)
-        for (int e = tid; e < LG * 16 * GB; e += LNT) {
+        // the queries' first increment: FP32 for the FP32 path, rounded to TF32 for the MMA
+        // (B row g, K-major core matrices of 8 rows x 4 floats)
+        for (int e = tid; e < LGT * 16 * GB; e += LNT) {
             const int g = e / (16 * GB), kk = e % (16 * GB);
             const bool in = g < ng && kk < a.d;
             const float qv = in ? a.q_rot[(int64_t)a.lq_items[qb + g] * a.q_stride + kk] : 0.f;
             qs[e] = qv;
-            const uint32_t h = tf32_rna_bits(qv);
-            const uint32_t l = tf32_rna_bits(__fsub_rn(qv, __uint_as_float(h)));
             const int b = kk >> 4, kc = (kk >> 2) & 3, el = kk & 3;
-            reinterpret_cast<uint32_t *>(bsm + ((size_t)(b * 4 + kc) * TCN + g) * 16)[el] = h;
-            reinterpret_cast<uint32_t *>(bsm + ((size_t)(b * 4 + kc) * TCN + LG + g) * 16)[el] = l;
+            reinterpret_cast<uint32_t *>(bsm + ((size_t)(b * 4 + kc) * TCN + g) * 16)[el] = tf32_rna_bits(qv);
         }
         __syncthreads();
-        for (int g = warp; g < LG; g += LNW) {   // ||q'||^2 over the increment
+        for (int g = warp; g < LGT; g += LNW) {   // ||q'||^2 over the increment
             float acc = 0.f;
             for (int kk = lane; kk < 16 * GB; kk += 32) acc = fmaf(qs[g * 16 * GB + kk], qs[g * 16 * GB + kk], acc);
 #pragma unroll
@@ -874,12 +888,15 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
             const int i0 = a.row_lo + t * LTC, tn = min(LTC, rend - i0);
             const float *af = reinterpret_cast<const float *>(abuf + (size_t)(t % NA) * TcSmem::a_bytes(GB));
             unsigned *mk_t = mask + (NA > 2 ? (t & 1) : 0) * 2 * LTC;
+            // warp half qh takes the item's queries 16 qh + j and 32 + 16 qh + j (bits j and
+            // 16 + j of its masks), the second block only when the item has more than 32
             const int mrow = 32 * (warp & 3) + lane, qh = warp >> 2;
-            uint32_t hi[16], lo2[16];
-            const uint32_t tb = tmem + (uint32_t)((t & 1) * TCN) + ((uint32_t)(32 * (warp & 3)) << 16);
-            lt_ld16(tb + (uint32_t)(qh * 16), hi);
-            lt_ld16(tb + (uint32_t)(LG + qh * 16), lo2);
+            const int nblk = ng > 32 ? 2 : 1;   // uniform over the block
             unsigned bits = 0u;
+            uint32_t dv[32];
+            const uint32_t tb = tmem + (uint32_t)((t & 1) * TCN) + ((uint32_t)(32 * (warp & 3)) << 16);
+            lt_ld16(tb + (uint32_t)(qh * 16), *reinterpret_cast<uint32_t(*)[16]>(dv));
+            if (nblk == 2) lt_ld16(tb + (uint32_t)(32 + qh * 16), *reinterpret_cast<uint32_t(*)[16]>(dv + 16));
             if (mrow < tn) {
                 float on = 0.f;   // ||o'||^2 over the increment, from the staged rows
 #pragma unroll
@@ -891,9 +908,10 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
                     }
                 const float ocn = sqrtf(on);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int g = qh * 16 + j;
-                    const float dot = __uint_as_float(hi[j]) + __uint_as_float(lo2[j]);
+                for (int j = 0; j < 32; ++j) {
+                    if (j >= 16 * nblk) break;
+                    const int g = (j < 16 ? 0 : 32 - 16) + qh * 16 + j;
+                    const float dot = __uint_as_float(dv[j]);
                     const float sq = s_qn[g] + on;
                     const float pt = fmaf(-2.f, dot, sq);
                     const float err = fmaf(a.tc_c1, sq, a.tc_c2 * (s_qcn[g] * ocn));
@@ -911,11 +929,11 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
             const unsigned *mk_t = mask + (NA > 2 ? (t & 1) : 0) * 2 * LTC;
             for (int g = warp; g < ng; g += LNW) {
                 if (qn + LTC > QCAP) {
-                    lm_drain<GB, STATS, false>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
+                    lm_drain<GB, STATS, false, LGT / LNW>(a, m, queue, qn, s_q, s_r2, s_thr, qs, nullptr);
                     qn = 0;
                     __syncwarp();
                 }
-                const int qh = g >> 4, jb = g & 15;
+                const int gg = g & 31, qh = gg >> 4, jb = (gg & 15) + (g >= 32 ? 16 : 0);
                 Surv *cand_list = queue + qn;   // kept candidates, compacted in place into survivors
                 int nk = 0;
                 for (int m0 = 0; m0 < tn; m0 += 32) {
@@ -947,7 +965,7 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
                     const bool keep = lead && !(p > c0);
                     __syncwarp();   // every lane has read its entry before the list is compacted in place
                     const unsigned mk = __ballot_sync(0xffffffffu, keep);
-                    if (keep) cand_list[ns + __popc(mk & ((1u << lane) - 1u))] = Surv{(g << QROW_BITS) | (i0 + cand), p};
+                    if (keep) cand_list[ns + __popc(mk & ((1u << lane) - 1u))] = Surv{surv_key(g, i0 + cand), p};
                     ns += __popc(mk);
                 }
                 qn += ns;
@@ -1027,11 +1045,9 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
         }
         if (failed) break;
         __syncwarp();
-        lm_drain<GB, STATS, false>(a, m, queue, qn, s_q, s_r2, s_thr, qs, kbest, kb);
+        lm_drain<GB, STATS, false, LGT / LNW>(a, m, queue, qn, s_q, s_r2, s_thr, qs, nullptr);
         qn = 0;
         __syncwarp();
-        if (kbest)   // the item's K best per query go to the accept buffers
-            for (int g = warp; g < ng; g += LNW) kb_flush(a, kb, warp, g / LNW, s_q[g]);
         if (tid == 32) s_item = s_next;
     }
     if (failed && tid == 0) {   // let the copies and MMAs in flight finish (bounded) before leaving
@@ -1060,19 +1076,19 @@ __global__ void k_lm_count(const int32_t *__restrict__ probe, int64_t nq, int np
     }
 }
 
-// items[c] = ceil(cnt[c] / LG) query groups x ceil(tiles of c in the row
+// items[c] = ceil(cnt[c] / lg) query groups x ceil(tiles of c in the row
 // window / chunk_tiles) chunks (none when the window holds no row of c);
 // both arrays get a trailing 0 for the scans.  off is written only when
 // `with_off` (the query groups do not change between the rounds of a pass).
 __global__ void k_lm_items(const int *__restrict__ cnt, const ListMeta *__restrict__ meta, int nc, int chunk_tiles,
-                           int tile_rows, int row_lo, int row_hi, int with_off, int *__restrict__ off,
+                           int tile_rows, int lg, int row_lo, int row_hi, int with_off, int *__restrict__ off,
                            int *__restrict__ items) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= nc; c += gridDim.x * blockDim.x) {
         const int v = c < nc ? cnt[c] : 0;
         if (with_off) off[c] = v;
         const int rows = c < nc ? min(meta[c].len, row_hi) - row_lo : 0;
         const int tiles = rows > 0 ? (rows + tile_rows - 1) / tile_rows : 0;
-        items[c] = (v > 0 && tiles > 0) ? ((v + LG - 1) / LG) * ((tiles + chunk_tiles - 1) / chunk_tiles) : 0;
+        items[c] = (v > 0 && tiles > 0) ? ((v + lg - 1) / lg) * ((tiles + chunk_tiles - 1) / chunk_tiles) : 0;
     }
 }
 
@@ -1278,18 +1294,17 @@ bool tc_applies(const dade_index *ix, const ScanParams &p, int gb) {
 //     (one FMA chain of K terms) and s = ||q'||^2 + ||o'||^2: relative
 //     (K + 8) u together, with the rounding of s - 2 dot: c1;
 //   - the tensor core reads each row value o as TF32 (at most 2^-10 relative
-//     off, truncated or rounded), the query is split q = hi + lo + d with
-//     |d| <= 2^-22 |q| (two roundings to TF32), products of TF32 values are
-//     exact in FP32, and the K products of a column are accumulated in FP32:
-//     allowed 4 x 2u per addition (truncating adds with a factor 4 to spare);
-//     hi + lo adds one rounding:
-//     |dot - q'.o'| <= (2^-10 + 2^-22 + (K + 2) 2^-21) sum |q'_k||o'_k|,
+//     off, truncated or rounded), the query is rounded to TF32 (2^-11
+//     relative), products of TF32 values are exact in FP32, and the K
+//     products of a column are accumulated in FP32: allowed 4 x 2u per
+//     addition (truncating adds with a factor 4 to spare), K + 2 of them:
+//     |dot - q'.o'| <= (2^-10 + 2^-11 + (K + 2) 2^-21) sum |q'_k||o'_k|,
 //     at most that times ||q'|| ||o'||; twice it for -2 dot: c2.
 // Both are rounded up and carry a further 2^-20 for their own FP32 evaluation.
 void tc_constants(int gb, float *c1, float *c2) {
     const double u = std::ldexp(1.0, -24), K = 16.0 * gb;
     const double cs = (K + 8.0) * u * 1.01 + 3.0 * u;
-    const double cd = std::ldexp(1.0, -10) + std::ldexp(1.0, -22) + (K + 2.0) * std::ldexp(1.0, -21);
+    const double cd = std::ldexp(1.0, -10) + std::ldexp(1.0, -11) + (K + 2.0) * std::ldexp(1.0, -21);
     const double grow = 1.0 + std::ldexp(1.0, -20);
     *c1 = std::nextafter((float)(cs * grow), INFINITY);
     *c2 = std::nextafter((float)(2.0 * cd * (1.0 + std::ldexp(1.0, -10)) * grow), INFINITY);
@@ -1334,8 +1349,12 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     const bool tc = prune && tc_applies(ix, p, gb) && !(row_lo == 0 && c0 == 0 && p.schedule == DADE_SCHED_ROUNDS);
     const int tile_rows = tc ? LTC : LT;
     const int chunk_tiles = std::max(1, (p.list_chunk > 0 ? p.list_chunk : 4096) / tile_rows);
-    k_lm_items<<<grid_of(nc + 1, 256), 256, 0, s>>>(cnt, ix->meta.as<ListMeta>(), nc, chunk_tiles, tile_rows, row_lo,
-                                                    row_hi, lists ? 1 : 0, off, items);
+    // queries per work item: the tensor-core kernel takes 64 where the window spans at least 32
+    // work items of a list (only long lists reach it, with many queries each, and items stay
+    // plentiful), 32 elsewhere
+    const int lg = tc && (int64_t)row_hi - row_lo >= 32ll * chunk_tiles * tile_rows ? LGT : LG;
+    k_lm_items<<<grid_of(nc + 1, 256), 256, 0, s>>>(cnt, ix->meta.as<ListMeta>(), nc, chunk_tiles, tile_rows,
+                                                    lg, row_lo, row_hi, lists ? 1 : 0, off, items);
     DADE_TRY(launch_check("k_lm_items"));
     if (lists) DADE_TRY(exclusive_scan_int(off, nc + 1, s));
     DADE_TRY(exclusive_scan_int(items, nc + 1, s));
@@ -1362,6 +1381,7 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
     a.cap = cap;
     a.q_stride = p.q_stride;
     a.chunk_tiles = chunk_tiles;
+    a.lg = lg;
     a.row_lo = row_lo;
     a.row_hi = row_hi;
     a.wait_ns = p.wait_ns > 0 ? (uint64_t)p.wait_ns : WAIT_NS;
@@ -1461,8 +1481,9 @@ dade_status scan_seeded(const dade_index *ix, int64_t nq, const ScanParams &p, c
     const bool fd = p.mode == DADE_MODE_FD;
     const int gb = fd ? LNB : std::min(p.delta_d / 16, ix->nb);
     const bool whole = p.tile >= ix->max_list;
-    const bool ok = ix->nb == LNB ? (gb == 1 || gb == 2 || gb == 4 || gb == 8)
-                                  : (ix->nb > LNB && (gb == 1 || gb == 2 || gb == 4 || gb == 8));
+    const bool ok = (ix->nb == LNB ? (gb == 1 || gb == 2 || gb == 4 || gb == 8)
+                                   : (ix->nb > LNB && (gb == 1 || gb == 2 || gb == 4 || gb == 8))) &&
+                    ix->max_list < (1 << QROW_BITS);
     // the list-major kernels cover D > 112 with delta_d of 1, 2, 4 or 8 blocks; elsewhere
     // the passes with r frozen run query-major (the same tests, thresholds and results)
     if (p.seed_split || !ok) return seeded_split(ix, nq, p, s);
@@ -1538,8 +1559,9 @@ dade_status scan_rounds(const dade_index *ix, int64_t nq, const ScanParams &p, c
     const int np = p.nprobe;
     const bool fd = p.mode == DADE_MODE_FD;
     const int gb = fd ? std::min(LNB, ix->nb) : std::min(p.delta_d / 16, ix->nb);
-    const bool lm_ok = ix->nb == LNB ? (gb == 1 || gb == 2 || gb == 4 || gb == 8)
-                                     : (ix->nb > LNB && (gb == 1 || gb == 2 || gb == 4 || gb == 8));
+    const bool lm_ok = (ix->nb == LNB ? (gb == 1 || gb == 2 || gb == 4 || gb == 8)
+                                      : (ix->nb > LNB && (gb == 1 || gb == 2 || gb == 4 || gb == 8))) &&
+                       ix->max_list < (1 << QROW_BITS);
     k_lm_reset<<<grid_of(nq * (int64_t)p.k, 256), 256, 0, s>>>(p.ids, p.dists, nq * (int64_t)p.k);
     DADE_TRY(launch_check("k_lm_reset"));
     if (p.stats) DADE_TRY_CUDA(cudaMemsetAsync(p.stats, 0, sizeof(int64_t) * 4 * (size_t)nq, s));
