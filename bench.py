@@ -477,7 +477,7 @@ def point_kw(point):
     return dict(mode=point["mode"], tile=point["tile"], spec=point.get("spec", 8), threads=point["threads"],
                 schedule=point.get("schedule", 0), flags=point.get("flags", 0),
                 seed_lists=point.get("seed_lists", 0), stage_dims=point.get("stage_dims", 0),
-                list_chunk=point.get("list_chunk", 0))
+                list_chunk=point.get("list_chunk", 0), tc_min_rows=point.get("tc_min_rows", 0))
 
 
 def ground_truth(torch, xb, q, K):
@@ -905,6 +905,7 @@ def measure_workload(args, wname, rank, world, dist, headline):
                    "seed_lists": point.get("seed_lists") if point.get("schedule", 0) == 2 else None,
                    "first_round_rows": point["tile"] if point.get("schedule", 0) == 3 else None,
                    "list_chunk": point.get("list_chunk") or None,
+                   "tc_min_rows": point.get("tc_min_rows") or None,
                    "stage_dims": point.get("stage_dims") or None,
                    "precision": precision_of(point, lf, dade),
                    "lead_copy": {"format": args.lead, "dims": ld} if lf else None,

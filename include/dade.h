@@ -261,6 +261,10 @@ typedef struct {
                                   and leave; that query's results are then undefined, the index stays
                                   usable.  Limits below 0.2 ms poll without suspending, limits below
                                   1 us poll once. */
+    int32_t tc_min_rows;       /* DADE_FLAG_TC_PREFILTER under DADE_SCHED_ROUNDS: a round whose row window
+                                  is shorter runs the FP32 list-major kernel instead (its work items are
+                                  a few tiles, where the copy-MMA-read chain costs more than the bound
+                                  saves); 0: every round after the first.  Results are the same. */
 } dade_search_opts;
 
 /* Description of a built index. */

@@ -209,6 +209,7 @@ dade_status validate_search(const dade_index *ix, int64_t nq, int32_t k, int32_t
     DADE_CHECK_ARG(!opts || opts->stage_ring == 0 || (opts->stage_ring >= 2 && opts->stage_ring <= 8),
                    "stage_ring must be 0 or 2..8");
     DADE_CHECK_ARG(!opts || opts->wait_ns >= 0, "wait_ns < 0");
+    DADE_CHECK_ARG(!opts || opts->tc_min_rows >= 0, "tc_min_rows < 0");
     DADE_CHECK_ARG(!opts || opts->stage_dims == 0 ||
                        (opts->stage_dims >= delta_d && delta_d > 0 && opts->stage_dims % delta_d == 0 &&
                         opts->stage_dims <= DADE_MAX_DIM),
@@ -286,6 +287,7 @@ dade_status run_scan(const dade_index *ix, const float *q_dev, const int32_t *pr
     p.seed_split = opts ? (opts->flags & DADE_FLAG_SEED_SPLIT) != 0 : 0;
     p.use_tc = opts ? (opts->flags & DADE_FLAG_TC_PREFILTER) != 0 : 0;
     p.wait_ns = opts ? opts->wait_ns : 0;
+    p.tc_min_rows = opts ? opts->tc_min_rows : 0;
     p.check_timeout = opts ? (opts->flags & DADE_FLAG_CHECK_TIMEOUT) != 0 : 0;
     p.q_k = qk_dev;
     p.q_np = qnp_dev;

@@ -103,11 +103,11 @@ bool cache_file_lookup(const char *path, const std::string &key, dade_autotune_r
         const std::string line(buf.data());
         std::string kv;
         if (!json_string(line, "key", &kv) || kv != key) continue;
-        double v[12];
-        const char *names[12] = {"nprobe", "delta_d", "alpha", "schedule", "tile", "seed_lists",
-                                 "list_chunk", "threads", "flags", "recall", "ms", "mode"};
+        double v[13];
+        const char *names[13] = {"nprobe", "delta_d", "alpha", "schedule", "tile", "seed_lists",
+                                 "list_chunk", "threads", "flags", "recall", "ms", "mode", "tc_min_rows"};
         bool ok = true;
-        for (int i = 0; i < 12 && ok; ++i) ok = json_number(line, names[i], &v[i]);
+        for (int i = 0; i < 13 && ok; ++i) ok = json_number(line, names[i], &v[i]);
         if (!ok) continue;   // a damaged line: not a hit
         dade_autotune_result t{};
         t.nprobe = (int32_t)v[0];
@@ -122,6 +122,7 @@ bool cache_file_lookup(const char *path, const std::string &key, dade_autotune_r
         t.recall = (float)v[9];
         t.ms = (float)v[10];
         t.opts.mode = (int32_t)v[11];
+        t.opts.tc_min_rows = (int32_t)v[12];
         *r = t;   // the last matching line wins
         found = true;
     }
@@ -135,9 +136,10 @@ void cache_file_append(const char *path, const std::string &key, const dade_auto
     std::fprintf(f,
                  "{\"key\": \"%s\", \"nprobe\": %d, \"delta_d\": %d, \"alpha\": %.9g, \"schedule\": %d, "
                  "\"tile\": %d, \"seed_lists\": %d, \"list_chunk\": %d, \"threads\": %d, \"flags\": %d, "
-                 "\"recall\": %.6f, \"ms\": %.6f, \"mode\": %d}\n",
+                 "\"recall\": %.6f, \"ms\": %.6f, \"mode\": %d, \"tc_min_rows\": %d}\n",
                  key.c_str(), r.nprobe, r.delta_d, (double)r.alpha, r.opts.schedule, r.opts.tile, r.opts.seed_lists,
-                 r.opts.list_chunk, r.opts.threads, r.opts.flags, (double)r.recall, (double)r.ms, r.opts.mode);
+                 r.opts.list_chunk, r.opts.threads, r.opts.flags, (double)r.recall, (double)r.ms, r.opts.mode,
+                 r.opts.tc_min_rows);
     std::fclose(f);
 }
 
@@ -157,7 +159,7 @@ bool host_buffer(const void *p) {
 }
 
 struct Variant {
-    int32_t schedule, tile, seed_lists, flags, list_chunk;
+    int32_t schedule, tile, seed_lists, flags, list_chunk, tc_min_rows;
 };
 
 // The sweep's state: rotated queries, one probe at a time, scratch results.
@@ -289,16 +291,18 @@ dade_status autotune(const dade_index *ix, const float *q, int64_t nq, int32_t k
     }
     // 2. at that rung and the next two: every delta_d and variant, alpha from the most pruning down
     const int32_t qo = DADE_FLAG_QUERY_ORDER | tail;
-    std::vector<Variant> vars = {{DADE_SCHED_TILE, 128, 0, qo, 0}};
-    if (ix->lead_format != DADE_LEAD_NONE) vars.push_back({DADE_SCHED_TILE, 128, 0, qo | DADE_FLAG_LEAD, 0});
+    std::vector<Variant> vars = {{DADE_SCHED_TILE, 128, 0, qo, 0, 0}};
+    if (ix->lead_format != DADE_LEAD_NONE) vars.push_back({DADE_SCHED_TILE, 128, 0, qo | DADE_FLAG_LEAD, 0, 0});
     for (int32_t S : {2, 3}) {   // later lists list-major, or query-major split over thread blocks
-        vars.push_back({DADE_SCHED_SEEDED, 128, S, qo, 0});
-        if (wide) vars.push_back({DADE_SCHED_SEEDED, 128, S, qo | DADE_FLAG_SEED_SPLIT, 0});
+        vars.push_back({DADE_SCHED_SEEDED, 128, S, qo, 0, 0});
+        if (wide) vars.push_back({DADE_SCHED_SEEDED, 128, S, qo | DADE_FLAG_SEED_SPLIT, 0, 0});
     }
     for (int32_t r1 : {16, 32})
         for (int32_t chunk : {0, 1024}) {
-            vars.push_back({DADE_SCHED_ROUNDS, r1, 0, qo, chunk});
-            if (wide) vars.push_back({DADE_SCHED_ROUNDS, r1, 0, qo | DADE_FLAG_TC_PREFILTER, chunk});
+            vars.push_back({DADE_SCHED_ROUNDS, r1, 0, qo, chunk, 0});
+            if (wide)   // the tensor-core prefilter in every round, or only in windows of 16,384 rows on
+                for (int32_t tcr : {0, 16384})
+                    vars.push_back({DADE_SCHED_ROUNDS, r1, 0, qo | DADE_FLAG_TC_PREFILTER, chunk, tcr});
         }
     const float alphas[] = {0.98f, 0.95f, 0.9f, 0.8f, 0.6f, 0.4f, 0.2f, 0.1f, 0.05f};
     bool have = false;
@@ -317,6 +321,7 @@ dade_status autotune(const dade_index *ix, const float *q, int64_t nq, int32_t k
                 so.seed_lists = v.seed_lists;
                 so.flags = v.flags;
                 so.list_chunk = v.list_chunk;
+                so.tc_min_rows = v.tc_min_rows;
                 for (float a : alphas) {
                     double rc = 0.0;
                     if (t.recall_of(np, dd, a, so, &rc) != DADE_OK) break;   // a variant this shape refuses

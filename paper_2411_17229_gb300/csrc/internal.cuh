@@ -183,6 +183,7 @@ struct ScanParams {
     int32_t row_lo, row_hi;  // split passes: rows [row_lo, min(len, row_hi)) of every list (row_hi 0: all)
     int32_t use_tc;          // list-major passes: the first increment's tensor-core prefilter
     int64_t wait_ns;         // limit of the scan kernels' bounded waits (0: 2 s)
+    int32_t tc_min_rows;     // row rounds: the tensor-core prefilter only for windows this long
     int32_t check_timeout;   // failure-path check: every block's first wait runs out
     const int32_t *q_k = nullptr, *q_np = nullptr;   // per-query K and nprobe (tile schedule), or NULL
     const float *r2src;

@@ -1346,7 +1346,9 @@ dade_status lm_round(const dade_index *ix, int64_t nq, const ScanParams &p, int 
         DADE_TRY(launch_check("k_lm_count"));
     }
     // the tensor-core bound needs a finite threshold: not in a first round (r = +inf)
-    const bool tc = prune && tc_applies(ix, p, gb) && !(row_lo == 0 && c0 == 0 && p.schedule == DADE_SCHED_ROUNDS);
+    // and, in the row rounds, only for windows of at least tc_min_rows rows
+    const bool tc = prune && tc_applies(ix, p, gb) && !(row_lo == 0 && c0 == 0 && p.schedule == DADE_SCHED_ROUNDS) &&
+                    (p.schedule != DADE_SCHED_ROUNDS || (int64_t)row_hi - row_lo >= p.tc_min_rows);
     const int tile_rows = tc ? LTC : LT;
     const int chunk_tiles = std::max(1, (p.list_chunk > 0 ? p.list_chunk : 4096) / tile_rows);
     // queries per work item: the tensor-core kernel takes 64 where the window spans at least 32

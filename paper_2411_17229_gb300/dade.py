@@ -51,7 +51,7 @@ class SearchOpts(C.Structure):
                 ("threads", C.c_int32), ("schedule", C.c_int32), ("flags", C.c_int32),
                 ("lead_stats", C.c_void_p), ("seed_lists", C.c_int32), ("estimator", C.c_int32),
                 ("eps0", C.c_float), ("stage_dims", C.c_int32), ("list_chunk", C.c_int32),
-                ("stage_ring", C.c_int32), ("wait_ns", C.c_int64)]
+                ("stage_ring", C.c_int32), ("wait_ns", C.c_int64), ("tc_min_rows", C.c_int32)]
 
 class AutotuneOpts(C.Structure):
     _fields_ = [("recall_target", C.c_float), ("n_nprobe", C.c_int32), ("nprobe_ladder", C.c_void_p),
@@ -272,7 +272,7 @@ class Index:
                                    _stream(stream)))
         so = r.opts
         point = dict(mode=so.mode, tile=so.tile, threads=so.threads, schedule=so.schedule, flags=so.flags,
-                     seed_lists=so.seed_lists, list_chunk=so.list_chunk)
+                     seed_lists=so.seed_lists, list_chunk=so.list_chunk, tc_min_rows=so.tc_min_rows)
         return {"nprobe": r.nprobe, "delta_d": r.delta_d, "alpha": r.alpha, "point": point, "recall": r.recall,
                 "ms": r.ms, "from_cache": bool(r.from_cache), "points_tried": r.points_tried}
 
@@ -320,39 +320,39 @@ class Index:
 
     def search(self, q_rot, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
                threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, estimator=ESTIMATOR_DADE,
-             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0, stream=None):
+             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0, tc_min_rows=0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
                        flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists, estimator=estimator,
                        eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
-                       stage_ring=stage_ring, wait_ns=wait_ns)
+                       stage_ring=stage_ring, wait_ns=wait_ns, tc_min_rows=tc_min_rows)
         _check(lib().dade_search(self._h, _ptr(q_rot), q_rot.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                  C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def scan(self, q_rot, probe, k, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
              threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, estimator=ESTIMATOR_DADE,
-             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0, stream=None):
+             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0, tc_min_rows=0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
                        flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists, estimator=estimator,
                        eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
-                       stage_ring=stage_ring, wait_ns=wait_ns)
+                       stage_ring=stage_ring, wait_ns=wait_ns, tc_min_rows=tc_min_rows)
         _check(lib().dade_scan(self._h, _ptr(q_rot), _ptr(probe), q_rot.shape[0], int(k), probe.shape[1],
                                float(alpha), int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def query(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
               threads=0, schedule=SCHED_TILE, flags=0, lead_stats=None, seed_lists=0, estimator=ESTIMATOR_DADE,
-             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0, stream=None):
+             eps0=0.0, stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0, tc_min_rows=0, stream=None):
         o = SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads, schedule=schedule,
                        flags=flags, lead_stats=_ptr(lead_stats), seed_lists=seed_lists, estimator=estimator,
                        eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
-                       stage_ring=stage_ring, wait_ns=wait_ns)
+                       stage_ring=stage_ring, wait_ns=wait_ns, tc_min_rows=tc_min_rows)
         _check(lib().dade_query(self._h, _ptr(q), q.shape[0], int(k), int(nprobe), float(alpha), int(delta_d),
                                 C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def query_mixed(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, threads=0, flags=0,
-                    stage_dims=0, wait_ns=0, schedule=SCHED_TILE, list_chunk=0, stream=None):
+                    stage_dims=0, wait_ns=0, schedule=SCHED_TILE, list_chunk=0, tc_min_rows=0, stream=None):
         """dade_query_mixed: per-query K and nprobe (int32 arrays [nq], host or device); ids / dists
         [nq, max K].  Tile schedule or list-major row rounds."""
         kk = k if hasattr(k, "data_ptr") else np.ascontiguousarray(k, dtype=np.int32)
@@ -360,28 +360,28 @@ class Index:
         k_max = int(kk.max().item() if hasattr(kk, "data_ptr") else kk.max())
         np_max = int(pp.max().item() if hasattr(pp, "data_ptr") else pp.max())
         o = SearchOpts(mode=mode, tile=tile, threads=threads, schedule=schedule, flags=flags, stage_dims=stage_dims,
-                       wait_ns=wait_ns, list_chunk=list_chunk)
+                       wait_ns=wait_ns, list_chunk=list_chunk, tc_min_rows=tc_min_rows)
         _check(lib().dade_query_mixed(self._h, _ptr(q), q.shape[0], _ptr(kk), _ptr(pp), k_max, np_max, float(alpha),
                                       int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return ids, dists
 
     def graph(self, q, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, stats=None, spec=0,
               threads=0, schedule=SCHED_TILE, flags=0, seed_lists=0, estimator=ESTIMATOR_DADE, eps0=0.0,
-              stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0):
+              stage_dims=0, list_chunk=0, stage_ring=0, wait_ns=0, tc_min_rows=0):
         """A query step captured into a CUDA graph (device buffers, bound to the graph)."""
         return Graph(self, q, k, nprobe, alpha, delta_d, ids, dists,
                      SearchOpts(mode=mode, tile=tile, stats=_ptr(stats), spec=spec, threads=threads,
                                 schedule=schedule, flags=flags, seed_lists=seed_lists, estimator=estimator,
                                 eps0=eps0, stage_dims=stage_dims, list_chunk=list_chunk,
-                                stage_ring=stage_ring, wait_ns=wait_ns))
+                                stage_ring=stage_ring, wait_ns=wait_ns, tc_min_rows=tc_min_rows))
 
     def tune(self, q_rot, probe, k, nprobe, alpha, delta_d, ids, dists, mode=MODE_DADE, tile=0, spec=0,
              threads=0, schedule=SCHED_TILE, flags=0, seed_lists=0, estimator=ESTIMATOR_DADE, eps0=0.0,
-             stage_dims=0, list_chunk=0, stage_ring=0, stream=None):
+             stage_dims=0, list_chunk=0, stage_ring=0, tc_min_rows=0, stream=None):
         """dade_tune: the fastest result-neutral options for this shape, as {"threads", "flags"}."""
         o = SearchOpts(mode=mode, tile=tile, spec=spec, threads=threads, schedule=schedule, flags=flags,
                        seed_lists=seed_lists, estimator=estimator, eps0=eps0, stage_dims=stage_dims,
-                       list_chunk=list_chunk, stage_ring=stage_ring)
+                       list_chunk=list_chunk, stage_ring=stage_ring, tc_min_rows=tc_min_rows)
         _check(lib().dade_tune(self._h, _ptr(q_rot), _ptr(probe), q_rot.shape[0], int(k), int(nprobe), float(alpha),
                                int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
         return {"threads": o.threads, "flags": o.flags}

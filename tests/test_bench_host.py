@@ -13,7 +13,7 @@ def test_point_options_round_trip():
     pt = bench.parse_point("nprobe=20,alpha=0.8,delta_d=64,tile=128,threads=128,schedule=2,seed_lists=2,flags=12", dade)
     kw = bench.point_kw(pt)
     assert kw == {"mode": 0, "tile": 128, "spec": 8, "threads": 128, "schedule": 2, "flags": 12, "seed_lists": 2,
-                  "stage_dims": 0, "list_chunk": 0}
+                  "stage_dims": 0, "list_chunk": 0, "tc_min_rows": 0}
     assert pt["alpha"] == 0.8 and pt["nprobe"] == 20
 
 
