@@ -29,6 +29,7 @@ import argparse
 import dataclasses
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -67,7 +68,7 @@ def log(*a):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c4_zipf_10m_d768")
@@ -692,7 +693,8 @@ def measure_workload(args, wname, rank, world, dist, headline):
         ev[1].record(stream)
         ix.scan(qr, pr_step, K, point["alpha"], point["delta_d"], ids, dists, stream=sh, **point_kw(point))
 
-    steps = args.steps if headline else max(5, min(args.steps, 20))
+    # the headline times exactly --steps steps; an extra workload as many as fill about a second
+    steps = args.steps if headline else max(5, min(2000, int(math.ceil(1000.0 / max(dade_best[0], 1e-3)))))
     warm = args.warmup if headline else 3
     for _ in range(warm):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
