@@ -756,7 +756,9 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
     __shared__ __align__(8) uint64_t full[NA], mdone[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_item, s_next, s_c, s_q[LGT];
-    __shared__ float s_r2[LGT], s_qn[LGT], s_qcn[LGT], s_thr[LGT], s_thr2[LGT];
+    __shared__ float s_r2[LGT], s_thr[LGT];
+    __shared__ float4 s_qc[LGT];   // per query: ||q'||^2, ||q'||, the bound's threshold thr (1 + 2^-15)
+    __shared__ unsigned s_any[2][4][2];   // per tile parity, row quarter, query half: queries with a kept row
     unsigned char *abuf = smem;
     unsigned char *bsm = smem + TcSmem::b_off(GB);
     float *qs = reinterpret_cast<float *>(smem + TcSmem::qs_off(GB));
@@ -855,7 +857,7 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
             s_q[g] = q;
             s_r2[g] = r2;
             s_thr[g] = thr;
-            s_thr2[g] = thr * (1.f + 0x1p-15f);
+            s_qc[g].z = thr * (1.f + 0x1p-15f);
         }
         // the queries' first increment: FP32 for the FP32 path, rounded to TF32 for the MMA
         // (B row g, K-major core matrices of 8 rows x 4 floats)
@@ -874,8 +876,8 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
             if (lane == 0) {
-                s_qn[g] = acc;
-                s_qcn[g] = sqrtf(acc);
+                s_qc[g].x = acc;
+                s_qc[g].y = sqrtf(acc);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B, written by threads, read by the MMA
@@ -912,14 +914,17 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
                     if (j >= 16 * nblk) break;
                     const int g = (j < 16 ? 0 : 32 - 16) + qh * 16 + j;
                     const float dot = __uint_as_float(dv[j]);
-                    const float sq = s_qn[g] + on;
+                    const float4 qc = s_qc[g];
+                    const float sq = qc.x + on;
                     const float pt = fmaf(-2.f, dot, sq);
-                    const float err = fmaf(a.tc_c1, sq, a.tc_c2 * (s_qcn[g] * ocn));
-                    const bool drop = pt - err > s_thr2[g];
+                    const float err = fmaf(a.tc_c1, sq, a.tc_c2 * (qc.y * ocn));
+                    const bool drop = pt - err > qc.z;
                     bits |= (unsigned)(g < ng && !drop) << j;
                 }
             }
             mk_t[qh * LTC + mrow] = bits;
+            const unsigned any = __reduce_or_sync(0xffffffffu, bits);   // the warp's 32 rows
+            if (lane == 0) s_any[NA > 2 ? (t & 1) : 0][warp & 3][qh] = any;
         };
         // Tile t's kept pairs (warp per query): the FP32 first increment from the staged
         // rows, and the survivors of its test to the warp's queue.
@@ -937,6 +942,7 @@ __global__ void __launch_bounds__(LNT, 2) k_lm_tc(const LmArgs a, const __grid_c
                 Surv *cand_list = queue + qn;   // kept candidates, compacted in place into survivors
                 int nk = 0;
                 for (int m0 = 0; m0 < tn; m0 += 32) {
+                    if (!((s_any[NA > 2 ? (t & 1) : 0][m0 >> 5][qh] >> jb) & 1u)) continue;   // nothing kept
                     const int mm = m0 + lane;
                     const bool keep = mm < tn && ((mk_t[qh * LTC + mm] >> jb) & 1u);
                     const unsigned mk = __ballot_sync(0xffffffffu, keep);
