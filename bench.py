@@ -52,12 +52,12 @@ RECALL_TARGET = 0.95
 # run the GPU autotuner; set from the autotuner's usual choice on this workload
 # The oracle arm's operating point per workload: the DADE point the autotuner picks there
 # (nprobe, alpha, delta_d, schedule); the oracle runs its own index at that point.
-REFERENCE_POINTS = {
+REFERENCE_POINTS = {   # the operating points dade_autotune picks for the GPU arm
     "c1_gauss_10k_d128": {"nprobe": 8, "alpha": 0.05, "delta_d": 32, "schedule": 0, "seed_lists": 0, "tile": 128},
-    "c2_mix_1m_d128": {"nprobe": 20, "alpha": 0.8, "delta_d": 64, "schedule": 2, "seed_lists": 3, "tile": 256},
-    "c3_mix_1m_d960": {"nprobe": 24, "alpha": 0.8, "delta_d": 64, "schedule": 2, "seed_lists": 3, "tile": 128},
-    "c4_zipf_10m_d768": {"nprobe": 8, "alpha": 0.8, "delta_d": 32, "schedule": 3, "seed_lists": 0, "tile": 64},
-    "c5_mix_5m_d256": {"nprobe": 32, "alpha": 0.8, "delta_d": 64, "schedule": 2, "seed_lists": 4, "tile": 128},
+    "c2_mix_1m_d128": {"nprobe": 20, "alpha": 0.98, "delta_d": 64, "schedule": 2, "seed_lists": 2, "tile": 128},
+    "c3_mix_1m_d960": {"nprobe": 24, "alpha": 0.98, "delta_d": 16, "schedule": 2, "seed_lists": 2, "tile": 128},
+    "c4_zipf_10m_d768": {"nprobe": 12, "alpha": 0.98, "delta_d": 32, "schedule": 3, "seed_lists": 0, "tile": 16},
+    "c5_mix_5m_d256": {"nprobe": 32, "alpha": 0.98, "delta_d": 64, "schedule": 3, "seed_lists": 0, "tile": 16},
 }
 
 
