@@ -73,7 +73,7 @@ def _scan_batch(ix, queries, K, pt):
     ix.probe(qr, pt["nprobe"], pr)
     ix.scan(qr, pr, K, pt["alpha"], pt["delta_d"], ids, d, tile=pt["tile"], threads=pt["threads"],
             schedule=pt["schedule"], seed_lists=pt["seed_lists"], flags=pt["flags"],
-            list_chunk=pt.get("list_chunk", 0))
+            list_chunk=pt.get("list_chunk", 0), tc_min_rows=pt.get("tc_min_rows", 0))
     ix.sync()
     return pr.cpu().numpy(), ids.cpu().numpy(), d.cpu().numpy()
 
@@ -111,20 +111,20 @@ def _oracle_point(orc, K, pt):
 
 def test_c2_full_size_benchmark_point():
     """1M x 128 integer mixture, 10,000 queries, K = 100, at the benchmark's
-    point: nprobe 20, seeded schedule (3 lists), tile 256, delta_d 64,
-    alpha 0.8, query order and row tail; index with the BF16 lead copy and
-    the row-major tail from dim 32, as the benchmark builds it."""
-    pt = {"nprobe": 20, "alpha": 0.8, "delta_d": 64, "tile": 256, "threads": 128, "schedule": dade.SCHED_SEEDED,
-          "seed_lists": 3, "flags": dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL}
+    point: nprobe 20, seeded schedule (2 lists), tile 128, delta_d 64,
+    alpha 0.98, query order; index with the BF16 lead copy and the row-major
+    tail from dim 32, as the benchmark builds it."""
+    pt = {"nprobe": 20, "alpha": 0.98, "delta_d": 64, "tile": 128, "threads": 128, "schedule": dade.SCHED_SEEDED,
+          "seed_lists": 2, "flags": dade.FLAG_QUERY_ORDER}
     _run_batch_case("c2_mix_1m_d128", pt, 100000, lead_format=dade.LEAD_BF16, lead_dims=64, tail_from=32)
 
 
 def test_c3_full_size_benchmark_point():
     """1M x 960 mixture, 1,000 queries, K = 10, at the benchmark's point:
-    nprobe 24, seeded schedule (3 lists) with the later lists split over
-    thread blocks, tile 128, 256 threads, delta_d 32, alpha 0.2."""
-    pt = {"nprobe": 24, "alpha": 0.2, "delta_d": 32, "tile": 128, "threads": 256, "schedule": dade.SCHED_SEEDED,
-          "seed_lists": 3, "flags": dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL | dade.FLAG_SEED_SPLIT}
+    nprobe 24, seeded schedule (2 lists) with the later lists split over
+    thread blocks, tile 128, 128 threads, delta_d 16, alpha 0.98."""
+    pt = {"nprobe": 24, "alpha": 0.98, "delta_d": 16, "tile": 128, "threads": 128, "schedule": dade.SCHED_SEEDED,
+          "seed_lists": 2, "flags": dade.FLAG_SEED_SPLIT}
     _run_batch_case("c3_mix_1m_d960", pt, 20000, lead_format=dade.LEAD_BF16, lead_dims=64, tail_from=32)
 
 
@@ -184,9 +184,9 @@ def test_c4_full_size_benchmark_point():
     """10M x 768 normalised mixture over 16,384 components with Zipf(1.1)
     weights (largest list 1.47M, median 72), lists = the generating
     components, 10,000 queries, K = 10, at the benchmark's point: row rounds
-    from 16 rows, work items of 1,024 rows, delta_d 32, alpha 0.95, nprobe 10,
-    query order, row-major tail from dim 32, the tensor-core prefilter; index
-    with the FP8 leading-block copy.  At full size the tensor-core prefilter
+    from 16 rows, work items of 1,024 rows, delta_d 32, alpha 0.98, nprobe 12,
+    256 threads, row-major tail from dim 32, the tensor-core prefilter for
+    windows of 16,384 rows and more; index with the FP8 leading-block copy.  At full size the tensor-core prefilter
     must return the FP32 list-major path's results bit for bit, and the FP8
     prefilter (which runs the rounds query-major on the tile kernel) the
     same kernel's FP32 results."""
@@ -195,9 +195,9 @@ def test_c4_full_size_benchmark_point():
     pairs = synth.eps_pairs(w.n, 20000)
     ix = dade.Index(torch.from_numpy(base).cuda(), w.n_clusters, assign=labels, pairs=pairs,
                     lead_format=dade.LEAD_FP8, lead_dims=64, tail_from=32)
-    pt = {"nprobe": 10, "alpha": 0.95, "delta_d": 32, "tile": 16, "threads": 128, "schedule": dade.SCHED_ROUNDS,
-          "seed_lists": 0, "list_chunk": 1024,
-          "flags": dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL | dade.FLAG_TC_PREFILTER}
+    pt = {"nprobe": 12, "alpha": 0.98, "delta_d": 32, "tile": 16, "threads": 256, "schedule": dade.SCHED_ROUNDS,
+          "seed_lists": 0, "list_chunk": 1024, "tc_min_rows": 16384,
+          "flags": dade.FLAG_ROW_TAIL | dade.FLAG_TC_PREFILTER}
     probe, ids, dists = _scan_batch(ix, queries, w.k, pt)
     _, idsf, distsf = _scan_batch(ix, queries, w.k, dict(pt, flags=pt["flags"] & ~dade.FLAG_TC_PREFILTER))
     assert np.array_equal(ids, idsf) and np.array_equal(dists.view(np.uint32), distsf.view(np.uint32))
