@@ -1134,6 +1134,7 @@ __global__ void __launch_bounds__(MT) k_lm_merge(int64_t *__restrict__ ids, floa
     __shared__ int s_n1;
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t q = blockIdx.x;
+    if (acnt[q] == 0) return;   // nothing accepted in this pass: the row is already the K nearest, sorted
     const int kq = q_k ? min(max(q_k[q], 1), k) : k;   // this query's K; rows have k entries
     if (tid == 0) s_n1 = 0;
     __syncthreads();
