@@ -240,8 +240,9 @@ def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7, torch=None, xb
     """Requests of one query each, Poisson arrivals at each rate (requests/s),
     K and nprobe drawn per request from {1, 10, 100} x {16, 64, 128}, submitted
     by the library's native load generator (dade_server_replay).  The server
-    runs the chosen point's delta_d and alpha, and its row rounds where the
-    point has them (else the tile schedule), so requests of any K and nprobe
+    runs the chosen point's delta_d and alpha, and its row rounds (first-round
+    rows, chunk, tensor-core window) where the point has them (else the tile
+    schedule), so requests of any K and nprobe
     share batches (dade_query_mixed), overlapped on 4 streams.  Returns per rate: offered and served request rates, p50 / p99
     latency (submit to results on the host, measured by the server); with the
     base on the device (xb), the served recall@K per nprobe against exact FP64
@@ -254,7 +255,9 @@ def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7, torch=None, xb
     keep = dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL | (dade.FLAG_TC_PREFILTER if rounds else 0)
     srv = dade.Server(ix, slots=4, max_batch=1024, max_k=100, max_nprobe=max(nprobes),
                       tile=point["tile"] if rounds else 128, threads=point["threads"],
-                      schedule=dade.SCHED_ROUNDS if rounds else dade.SCHED_TILE, flags=point["flags"] & keep)
+                      schedule=dade.SCHED_ROUNDS if rounds else dade.SCHED_TILE, flags=point["flags"] & keep,
+                      list_chunk=point.get("list_chunk", 0) if rounds else 0,
+                      tc_min_rows=point.get("tc_min_rows", 0) if rounds else 0)
     rng = np.random.default_rng(seed)
     out, served = [], []
     for rate in rates:

@@ -248,7 +248,7 @@ typedef struct {
                                   at each increment inside; survivors then gather the rest.  Same
                                   results; a deeper stage trades gathers for streaming when most
                                   candidates outlive the first increments. */
-    int32_t list_chunk;        /* list-major passes of DADE_SCHED_SEEDED: rows of one list per work
+    int32_t list_chunk;        /* list-major passes of DADE_SCHED_SEEDED and DADE_SCHED_ROUNDS: rows of one list per work
                                   item (0: 4096; else a multiple of 64); a long list becomes several
                                   items run by different thread blocks.  Same results. */
     int32_t stage_ring;        /* tile kernel for any D: staged tiles in flight per thread block (0: 2;
@@ -369,7 +369,9 @@ typedef struct {
                                   would not fit beside their staging buffers */
     int32_t mode, tile, threads, schedule, seed_lists, flags;   /* dade_search_opts of every batch */
     int32_t stage_dims;        /* dade_search_opts.stage_dims of every batch (0: delta_d) */
-    int32_t reserved[3];
+    int32_t list_chunk;        /* dade_search_opts.list_chunk of every batch (0: 4096) */
+    int32_t tc_min_rows;       /* dade_search_opts.tc_min_rows of every batch (0: every round after the first) */
+    int32_t reserved;
 } dade_server_opts;
 typedef struct {
     int64_t slots, slot_bytes;          /* slots created, device bytes of a slot running a full batch */

@@ -171,6 +171,8 @@ struct dade_server {
         so.seed_lists = o.seed_lists;
         so.flags = o.flags;
         so.stage_dims = o.stage_dims;
+        so.list_chunk = o.list_chunk;
+        so.tc_min_rows = o.tc_min_rows;
         if (mixes(r0.delta_d))
             DADE_TRY(dade_query_mixed(ix, s.q_dev.as<float>(), nq, s.k_host, s.np_host, kmax, npmax, r0.alpha,
                                       r0.delta_d, &so, s.ids_dev.as<int64_t>(), s.dists_dev.as<float>(),
@@ -294,6 +296,9 @@ bool valid_opts(const dade_server_opts &o, std::string *why) {
     if (o.max_k < 1 || o.max_k > DADE_MAX_K) return *why = "max_k outside 1..DADE_MAX_K", false;
     if (o.max_nprobe < 1) return *why = "max_nprobe < 1", false;
     if (o.device_budget < 0) return *why = "device_budget < 0", false;
+    if (o.list_chunk != 0 && (o.list_chunk < 64 || o.list_chunk % 64 != 0))
+        return *why = "list_chunk must be 0 or a positive multiple of 64", false;
+    if (o.tc_min_rows < 0) return *why = "tc_min_rows < 0", false;
     return true;
 }
 
@@ -398,6 +403,8 @@ dade_status dade_server_submit(dade_server *sv, const float *q, int64_t nq, int3
     so.seed_lists = sv->o.seed_lists;
     so.flags = sv->o.flags;
     so.stage_dims = sv->o.stage_dims;
+    so.list_chunk = sv->o.list_chunk;
+    so.tc_min_rows = sv->o.tc_min_rows;
     // the same checks dade_search makes, before the request is queued
     dade_status vs = dade_scan(sv->ix, nullptr, nullptr, 0, k, nprobe, alpha, delta_d, &so, nullptr, nullptr,
                                nullptr);

@@ -67,7 +67,8 @@ class ServerOpts(C.Structure):
     _fields_ = [("slots", C.c_int32), ("max_batch", C.c_int32), ("max_k", C.c_int32), ("max_nprobe", C.c_int32),
                 ("device_budget", C.c_int64), ("mode", C.c_int32), ("tile", C.c_int32), ("threads", C.c_int32),
                 ("schedule", C.c_int32), ("seed_lists", C.c_int32), ("flags", C.c_int32),
-                ("stage_dims", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("stage_dims", C.c_int32), ("list_chunk", C.c_int32), ("tc_min_rows", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class ServerStats(C.Structure):

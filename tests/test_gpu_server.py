@@ -7,7 +7,8 @@ batches them (under the tile schedule all of them, in a few large batches;
 under the seeded schedule those with equal K and nprobe), runs batches on
 several streams at once, and every request's result must equal what a
 direct dade_query gives for that request alone, bit for bit.  The same
-request is also served alone and in the mix.  Cancelled requests complete
+request is also served alone and in the mix, under the row rounds also with
+a list chunk and a tensor-core window passed through.  Cancelled requests complete
 with DADE_ECANCELLED and leave the others untouched; with a device budget,
 batches are admitted by bytes and a request that cannot fit completes with
 DADE_ENOMEM.
@@ -41,8 +42,10 @@ def _direct(ix, q, k, nprobe, **opts):
 
 @pytest.mark.parametrize("opts", [dict(tile=256), dict(tile=256, schedule=dade.SCHED_SEEDED, seed_lists=2,
                                                         flags=dade.FLAG_QUERY_ORDER | dade.FLAG_ROW_TAIL),
-                                  dict(tile=16, schedule=dade.SCHED_ROUNDS, flags=dade.FLAG_QUERY_ORDER)],
-                         ids=["tile", "seeded", "rounds"])
+                                  dict(tile=16, schedule=dade.SCHED_ROUNDS, flags=dade.FLAG_QUERY_ORDER),
+                                  dict(tile=16, schedule=dade.SCHED_ROUNDS, flags=dade.FLAG_TC_PREFILTER,
+                                       list_chunk=1024, tc_min_rows=128)],
+                         ids=["tile", "seeded", "rounds", "rounds-tc-window"])
 def test_results_alone_and_in_the_mix(index, opts):
     ix, queries = index
     rng = np.random.default_rng(11)
@@ -113,6 +116,14 @@ def test_query_mixed_equals_each_query_alone(index, mode, sched):
     rc = dade.lib().dade_query_mixed(ix.handle, q.ctypes.data, q.shape[0], ks.ctypes.data, nps.ctypes.data, kmax,
                                      int(nps.max()), 0.1, 32, dade.C.byref(o), ids.ctypes.data, d.ctypes.data, None)
     assert rc == dade.EINVAL
+
+
+def test_server_options_checked(index):
+    ix, _ = index
+    for bad in (dict(list_chunk=100), dict(list_chunk=32), dict(tc_min_rows=-1)):
+        with pytest.raises(dade.DadeError) as e:
+            dade.Server(ix, **bad)
+        assert e.value.status == dade.EINVAL
 
 
 def test_cancel(index):
