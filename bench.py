@@ -399,7 +399,9 @@ def scan_kernel_name(point, d):
         return f"k_fd_fast<{point['threads']}, 8>" if nb == 8 else "k_scan<FD>"
     lead = point.get("flags", 0) & 2
     if point.get("schedule", 0) == 3:
-        if point.get("flags", 0) & 16 or nb < 8:
+        # list-major passes need D > 112, delta_d of 16, 32, 64 or 128 dims and neither the
+        # split passes nor the low-precision lead prefilter; otherwise the rounds run query-major
+        if point.get("flags", 0) & 16 or nb < 8 or lead or min(point["delta_d"] // 16, nb) not in (1, 2, 4, 8):
             return f"k_scan<DADE{', lead' if lead else ''}> (row rounds split over CTAs) + k_lm_merge"
         if point.get("flags", 0) & 32:
             return (f"k_lm_g<{min(point['delta_d'] // 16, 8)}> (first round) + k_lm_tc<{min(point['delta_d'] // 16, 8)}> "
@@ -430,11 +432,12 @@ SERVING_WORKLOAD = "c5_mix_5m_d256"
 def list_major_point(point, d):
     """True where the scan runs list-major (seeded schedule's later lists, or
     every round of the row-rounds schedule; not split, D > 112, delta_d of 1,
-    2, 4 or 8 blocks)."""
+    2, 4 or 8 blocks; the row rounds with the lead prefilter run query-major)."""
     nb = (d + 15) // 16
     gb = 8 if point.get("mode", 0) == 1 else min(point.get("delta_d", 32) // 16, nb)
+    lead_rounds = point.get("schedule", 0) == 3 and point.get("flags", 0) & 2
     return (point.get("schedule", 0) in (2, 3) and not point.get("flags", 0) & 16 and nb >= 8
-            and gb in (1, 2, 4, 8))
+            and gb in (1, 2, 4, 8) and not lead_rounds)
 
 
 def recorded_traffic(point, workload):

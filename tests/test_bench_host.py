@@ -29,6 +29,9 @@ def test_kernel_names_follow_the_schedule():
     assert bench.scan_kernel_name(rounds, 768).startswith("k_lm_g<2> (row rounds")
     assert "k_lm_tc<2>" in bench.scan_kernel_name(dict(rounds, flags=36), 768)
     assert "split" in bench.scan_kernel_name(dict(rounds, flags=20), 768)
+    lead_tc = bench.scan_kernel_name(dict(rounds, flags=38), 768)     # lead prefilter replaces the TC one
+    assert lead_tc.startswith("k_scan<DADE, lead>") and "split" in lead_tc
+    assert "split" in bench.scan_kernel_name(dict(rounds, delta_d=48), 768)
 
 
 def test_traffic_records_match_only_their_point_and_sources():
@@ -55,3 +58,5 @@ def test_alu_bound_where_lists_are_shared():
     assert not bench.list_major_point(c2, 64)                           # D <= 112: split fallback
     assert bench.list_major_point(dict(c2, schedule=3, delta_d=32), 768)   # row rounds
     assert not bench.list_major_point(dict(c2, schedule=3, flags=20), 768)
+    assert not bench.list_major_point(dict(c2, schedule=3, delta_d=32, flags=38), 768)   # lead: query-major
+    assert bench.list_major_point(dict(c2, delta_d=32, flags=14), 768)   # seeded: lead leaves it list-major
