@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for DADE-IVF -- TEST INFRASTRUCTURE ONLY.
+"""FP64 CPU oracle for DADE-IVF and HNSW* -- TEST INFRASTRUCTURE ONLY.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The CUDA library never calls it and it
@@ -21,6 +21,7 @@ SRC = os.path.join(_HERE, "dade_oracle.c")
 LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
 SEQUENTIAL, TILE, PROBE_ROUNDS, ROW_ROUNDS = 0, 1, 2, 3
+HNSW_SEQUENTIAL, HNSW_NODE = 0, 1   # beam-search threshold schedules (or_hnsw_search)
 TIE_TOL = 1e-5
 # Relative width of the decision bracket of ``search_bracket``: decisions of
 # the FP32 path whose two sides lie within this of each other may go either
@@ -32,7 +33,10 @@ BRACKET_TOL = 2e-5
 def build(src: str = SRC, out: str = LIB, extra: tuple = ()) -> str:
     """Compile the oracle with gcc (OpenMP across independent outputs only)."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
-    cmd = ["gcc", "-O3", "-fopenmp", "-fPIC", "-shared", "-std=c11", *extra, "-o", out, src, "-lm"]
+    # contraction off: no fused multiply-add merges a product into a sum (the FP32
+    # DCO of the beam search rounds every step, as the paper's scalar code does)
+    cmd = ["gcc", "-O3", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", *extra, "-o", out, src,
+           "-lm"]
     subprocess.run(cmd, check=True)
     return out
 
@@ -73,6 +77,9 @@ class Oracle:
             "or_exact_knn": (None, [vp, i64, i32, vp, i64, i32, vp, vp]),
             "or_estimate_sq": (f64, [vp, vp, i32, i32, vp]),
             "or_dco": (i32, [vp, vp, i32, i32, f64, vp, vp, i32, f64, vp, vp, vp]),
+            "or_hnsw_graph": (i32, [vp, i64, i32, i32, i32, i32, vp, vp, vp]),
+            "or_hnsw_search": (i32, [vp, vp, i64, i32, vp, i32, vp, vp, vp, i64, vp, i32, i32, i32, i32, vp, vp,
+                                     i32, i64, f64, f64, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -244,6 +251,59 @@ class Oracle:
         return ids, dists
 
 
+    # -- HNSW* (Section 3.4): layer-0 graph and beam search ------------------
+    def hnsw_graph(self, Xr, kc, M, M0):
+        """Layer-0 graph by the reading of ``or_hnsw_graph``: nbr [n, M0] int32
+        (-1 unused), gap_sel [n], gap_fin [n] (smallest relative gaps of the
+        decisions that built each node's lists)."""
+        Xr = _f64(Xr)
+        n, D = Xr.shape
+        nbr = np.empty((n, M0), np.int32)
+        gs, gf = np.empty(n), np.empty(n)
+        if self.lib.or_hnsw_graph(_p(Xr), n, D, int(kc), int(M), int(M0), _p(nbr), _p(gs), _p(gf)) != 0:
+            raise ValueError("or_hnsw_graph rejected its arguments")
+        return nbr, gs, gf
+
+    def hnsw_search(self, Xr, nbr, lam, Qr, entry, K, ef, delta_d, eps, schedule=HNSW_NODE, max_visits=0,
+                    tol=TIE_TOL, bias=0.0, coef32=None):
+        """Greedy beam search with DCOs (``or_hnsw_search``).  entry: [n_entry]
+        or [nq, n_entry] object ids.  FP64 arithmetic with eps (None:
+        FDScanning); with Xr, Qr given as float32 arrays, the FP32 arithmetic
+        of the paper's implementation with the FP32 coefficients coef32 (None:
+        FDScanning).  Returns ids [nq,K] int64, dists [nq,K] (squared),
+        stats [nq,5] (DCOs, dims, accepted, pruned, expansions), flags [nq]."""
+        f32 = np.asarray(Xr).dtype == np.float32
+        if f32:
+            Xr, Qr = np.ascontiguousarray(Xr, np.float32), np.ascontiguousarray(Qr, np.float32)
+        else:
+            Xr, Qr = _f64(Xr), _f64(Qr)
+        n, D = Xr.shape
+        nq = Qr.shape[0]
+        nbr = np.ascontiguousarray(nbr, np.int32)
+        entry = np.asarray(entry, np.int64)
+        if entry.ndim < 2:                       # the same entry objects for every query
+            entry = np.broadcast_to(entry.reshape(1, -1), (nq, entry.size))
+        entry = np.ascontiguousarray(entry)
+        ids, dists = np.empty((nq, K), np.int64), np.empty((nq, K))
+        stats, flags = np.empty((nq, 5), np.int64), np.empty(nq, np.int32)
+        e = None if (eps is None or f32) else _f64(eps)
+        c32 = None if (coef32 is None or not f32) else np.ascontiguousarray(coef32, np.float32)
+        rc = self.lib.or_hnsw_search(None if f32 else _p(Xr), _p(Xr) if f32 else None, n, D, _p(nbr), nbr.shape[1],
+                                     _p(_f64(lam)), None if f32 else _p(Qr), _p(Qr) if f32 else None, nq,
+                                     _p(entry), entry.shape[1], int(K), int(ef), int(delta_d), _p(e), _p(c32),
+                                     int(schedule), int(max_visits), float(tol), float(bias), _p(ids), _p(dists),
+                                     _p(stats), _p(flags))
+        if rc != 0:
+            raise ValueError("or_hnsw_search rejected its arguments")
+        return ids, dists, stats, flags
+
+
+# flags of hnsw_search that make a query's path depend on rounding: DCO,
+# pop-order and eviction near-ties (a search with no such decision within tol
+# takes the same path under any computation whose errors stay below tol)
+HNSW_PATH_TIES = 1 | 2 | 4 | 8
+
+
 _default: Oracle | None = None
 
 
@@ -252,6 +312,15 @@ def get() -> Oracle:
     if _default is None:
         _default = Oracle()
     return _default
+
+
+def coef_f32(lam, eps, D: int, delta_d: int):
+    """The Section 3.3 test in squared form, P_d > c_j r^2: c_j = (1 + eps_d)^2
+    Lambda_d / Lambda_D (Eq. 13 moved to the right-hand side) for the j-th
+    tested d = (j + 1) delta_d < D, computed in FP64 and rounded to FP32 (the
+    coefficients of the FP32 DCO of ``hnsw_search``)."""
+    Lam = np.concatenate([[0.0], np.cumsum(np.asarray(lam, np.float64))])
+    return np.array([(1.0 + eps[d]) ** 2 * Lam[d] / Lam[D] for d in increments(D, delta_d)], np.float32)
 
 
 def increments(D: int, delta_d: int):

@@ -1,5 +1,6 @@
 /*
- * dade_oracle.c -- plain FP64 CPU oracle for DADE inside an IVF scan.
+ * dade_oracle.c -- plain FP64 CPU oracle for DADE inside an IVF scan and
+ * inside HNSW's layer-0 beam search (HNSW*).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * CPU-baseline leg of the benchmark load this file.  It shares no code with
@@ -17,6 +18,11 @@
  * lambda_1 >= ... >= lambda_D, Lambda_d = sum_{k<=d} lambda_k,
  * P_d(q,o) = sum_{k<=d} (q'_k - o'_k)^2 in the rotated space, r the current
  * K-th nearest distance.  Row-major arrays throughout.
+ *
+ * The beam search also runs in the FP32 arithmetic of the paper's scalar
+ * implementation (dco_f32): the decisions of a graph search steer which
+ * objects are visited, so the CUDA path is compared with the oracle making
+ * them in the same precision; that mode is pinned to the FP64 one.
  *
  * Parity status: every routine is pinned by the CPU tests (closed forms,
  * library routines on special cases, brute force on tiny inputs, statistical
@@ -709,4 +715,372 @@ OR_API void or_exact_knn(const float *X, int64_t n, int d, const float *Q, int64
         }
         free(buf);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* HNSW with DADE DCOs (HNSW*, Section 3.4; the graph of Section 4.1).       */
+/* ------------------------------------------------------------------------ */
+
+/* The (squared distance, id) order of every set below: 1 iff (ka, ia) < (kb, ib). */
+static int kv_less(double ka, int64_t ia, double kb, int64_t ib)
+{
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+static double rel_gap(double a, double b)
+{
+    double m = fabs(a) > fabs(b) ? fabs(a) : fabs(b);
+    return m > 0.0 ? fabs(a - b) / m : INFINITY;
+}
+
+/*
+ * HNSW's neighbour selection heuristic (Malkov and Yashunin, "Efficient and
+ * robust approximate nearest neighbor search using Hierarchical Navigable
+ * Small World graphs", Algorithm 4, with neither candidate extension nor
+ * kept pruned connections): the m candidates, ascending by (squared distance
+ * to the node, id), are taken in order, and candidate e is kept iff it is
+ * nearer to the node than to every candidate kept before it, until cap are
+ * kept.  cand[i].key = squared distance of candidate i to the node.  Writes
+ * the kept ids to out and returns how many; *gap is lowered to the relative
+ * gap of every comparison made.
+ */
+static int select_heuristic(const double *Xr, int D, const kv_t *cand, int m, int cap, int64_t *out,
+                            double *gap)
+{
+    int kept = 0;
+    for (int i = 0; i < m && kept < cap; ++i) {
+        const double *xe = Xr + cand[i].id * D;
+        int keep = 1;
+        for (int s = 0; s < kept; ++s) {
+            double des = sqdist(xe, Xr + out[s] * D, D);
+            double g = rel_gap(des, cand[i].key);
+            if (g < *gap) *gap = g;
+            if (!(cand[i].key < des)) { keep = 0; break; }
+        }
+        if (keep) out[kept++] = cand[i].id;
+    }
+    return kept;
+}
+
+/*
+ * The layer-0 graph the beam search walks.  The paper takes HNSW's graph
+ * from its reference library (M = 16, Section 4.1) and changes only the
+ * DCOs of the search.  Reading: layer 0 built in one pass over exact
+ * neighbours instead of by incremental insertion:
+ *   1. C(u) = the kc nearest other objects of u, ascending by (squared
+ *      distance, id);
+ *   2. sel(u) = the heuristic over C(u), at most M kept;
+ *   3. U(v) = sel(v) and every u with v in sel(u), distinct, ascending by
+ *      (squared distance to v, id); the neighbours of v are U(v) when it
+ *      holds at most M0, else the heuristic over U(v) with cap M0.
+ * nbr: n x M0 ids in that order, unused slots -1.  gap_sel[u] (may be NULL):
+ * the smallest relative gap among the decisions of steps 1-2 for u (the
+ * kc-th / (kc+1)-th boundary, neighbouring candidates of C(u), every
+ * heuristic comparison); gap_fin[v] (may be NULL) the same for step 3 when
+ * the heuristic runs (neighbouring entries of U(v), its comparisons).
+ * Returns 0, or -1 on bad arguments.
+ */
+OR_API int or_hnsw_graph(const double *Xr, int64_t n, int D, int kc, int M, int M0, int32_t *nbr,
+                         double *gap_sel, double *gap_fin)
+{
+    if (n < 1 || kc < 1 || M < 1 || M0 < 1) return -1;
+    int64_t *sel = (int64_t *)malloc(sizeof(int64_t) * (size_t)n * M);
+    int *nsel = (int *)malloc(sizeof(int) * (size_t)n);
+    #pragma omp parallel
+    {
+        kv_t *buf = (kv_t *)malloc(sizeof(kv_t) * (size_t)n);
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t u = 0; u < n; ++u) {
+            int64_t m = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                if (i == u) continue;
+                buf[m].key = sqdist(Xr + u * D, Xr + i * D, D);
+                buf[m].id = i;
+                ++m;
+            }
+            qsort(buf, (size_t)m, sizeof(kv_t), kv_cmp);
+            int kk = (int)(m < kc ? m : kc);
+            double g = INFINITY;
+            if (kk < m) g = rel_gap(buf[kk - 1].key, buf[kk].key);
+            for (int i = 0; i + 1 < kk; ++i) {
+                double gi = rel_gap(buf[i].key, buf[i + 1].key);
+                if (gi < g) g = gi;
+            }
+            nsel[u] = select_heuristic(Xr, D, buf, kk, M, sel + u * M, &g);
+            if (gap_sel) gap_sel[u] = g;
+        }
+        free(buf);
+    }
+    /* reverse entries: u joins U(v) for every v in sel(u) */
+    int64_t *rstart = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    for (int64_t u = 0; u < n; ++u)
+        for (int s = 0; s < nsel[u]; ++s) rstart[sel[u * M + s] + 1] += 1;
+    for (int64_t v = 0; v < n; ++v) rstart[v + 1] += rstart[v];
+    int64_t *rev = (int64_t *)malloc(sizeof(int64_t) * (size_t)(rstart[n] > 0 ? rstart[n] : 1));
+    int64_t *rfill = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    for (int64_t u = 0; u < n; ++u)
+        for (int s = 0; s < nsel[u]; ++s) {
+            int64_t v = sel[u * M + s];
+            rev[rstart[v] + rfill[v]++] = u;
+        }
+    free(rfill);
+    #pragma omp parallel
+    {
+        int64_t cap = M;
+        for (int64_t v = 0; v < n; ++v)
+            if (rstart[v + 1] - rstart[v] + M > cap) cap = rstart[v + 1] - rstart[v] + M;
+        kv_t *U = (kv_t *)malloc(sizeof(kv_t) * (size_t)cap);
+        int64_t *kept = (int64_t *)malloc(sizeof(int64_t) * (size_t)M0);
+        #pragma omp for schedule(dynamic, 16)
+        for (int64_t v = 0; v < n; ++v) {
+            int64_t m = 0;
+            for (int s = 0; s < nsel[v]; ++s) {
+                U[m].id = sel[v * M + s];
+                U[m].key = sqdist(Xr + v * D, Xr + U[m].id * D, D);
+                ++m;
+            }
+            for (int64_t t = rstart[v]; t < rstart[v + 1]; ++t) {
+                U[m].id = rev[t];
+                U[m].key = sqdist(Xr + v * D, Xr + rev[t] * D, D);
+                ++m;
+            }
+            qsort(U, (size_t)m, sizeof(kv_t), kv_cmp);
+            int64_t w = 0;   /* distinct ids: an id met twice has the same key, so the copies are adjacent */
+            for (int64_t i = 0; i < m; ++i)
+                if (w == 0 || U[i].id != U[w - 1].id) U[w++] = U[i];
+            m = w;
+            double g = INFINITY;
+            int nk;
+            if (m <= M0) {
+                nk = (int)m;
+                for (int64_t i = 0; i < m; ++i) kept[i] = U[i].id;
+            } else {
+                for (int64_t i = 0; i + 1 < m; ++i) {
+                    double gi = rel_gap(U[i].key, U[i + 1].key);
+                    if (gi < g) g = gi;
+                }
+                nk = select_heuristic(Xr, D, U, (int)m, M0, kept, &g);
+            }
+            for (int s = 0; s < M0; ++s) nbr[v * M0 + s] = s < nk ? (int32_t)kept[s] : -1;
+            if (gap_fin) gap_fin[v] = g;
+        }
+        free(U);
+        free(kept);
+    }
+    free(sel); free(nsel); free(rstart); free(rev);
+    return 0;
+}
+
+/* R holds *nR objects ascending by (key, id), at most ef: put x in, dropping
+ * the farthest when it would hold ef + 1.  Flag 8 when the dropped object and
+ * the new farthest are within tol. */
+static void r_insert(kv_t *R, int *nR, int ef, kv_t x, double tol, int *tie)
+{
+    int p = *nR;
+    while (p > 0 && kv_less(x.key, x.id, R[p - 1].key, R[p - 1].id)) --p;
+    if (*nR == ef) {
+        if (p == ef) {
+            if (near_tie(x.key, R[ef - 1].key, tol)) *tie |= 8;
+            return;
+        }
+        double dropped = R[ef - 1].key;
+        memmove(R + p + 1, R + p, sizeof(kv_t) * (size_t)(ef - 1 - p));
+        R[p] = x;
+        if (near_tie(dropped, R[ef - 1].key, tol)) *tie |= 8;
+        return;
+    }
+    memmove(R + p + 1, R + p, sizeof(kv_t) * (size_t)(*nR - p));
+    R[p] = x;
+    *nR += 1;
+}
+
+/*
+ * Algorithm 1 in the arithmetic of the paper's implementation (scalar FP32
+ * C++, Section 4.1): t = q_k - o_k, t * t and the running sum each rounded to
+ * FP32, dimensions in order (this file is built with contraction off, so no
+ * fused multiply-add merges the steps).  The test of Section 3.3 in its
+ * squared form, P_d > c_j r^2 with c_j = (1 + eps_d)^2 Lambda_d / Lambda_D
+ * given in FP32 (coef[j] for the j-th tested d) and the product rounded to
+ * FP32; at d = D accept iff P_D <= r^2.  coef == NULL: FDScanning.  The
+ * result and tie bits as dco().
+ */
+static int dco_f32(const float *q, const float *o, int D, int delta_d, float r2, const float *coef, double tol,
+                   float *dist2, int *dims, int *tie)
+{
+    int d = 0, j = 0;
+    float P = 0.0f;
+    while (d < D) {
+        int dn = d + delta_d;
+        if (dn > D) dn = D;
+        for (int k = d; k < dn; ++k) {
+            float t = q[k] - o[k];
+            float sq = t * t;
+            P = P + sq;
+        }
+        d = dn;
+        if (d < D) {
+            if (coef) {
+                float bound = coef[j] * r2;
+                if (isfinite(r2) && near_tie(P, bound, tol)) *tie |= 1;
+                if (P > bound) { *dims = d; return 0; }
+            }
+            ++j;
+        } else {
+            if (isfinite(r2) && near_tie(P, r2, tol)) *tie |= 2;
+            break;
+        }
+    }
+    *dims = D;
+    *dist2 = P;
+    return P <= r2;
+}
+
+/*
+ * Greedy beam search on the layer-0 graph with one DCO per neighbour
+ * (Section 3.4): a search set S, unbounded, and a result set R of at most ef
+ * objects, both ordered by (squared distance, id).  First every entry object
+ * is visited with r = +inf (its exact distance) and enters S and R.  Then:
+ *   stop when the visit budget is spent (max_visits > 0 and max_visits DCOs
+ *       run) or S is empty;
+ *   pop c, the nearest object of S; stop when c is farther than the farthest
+ *       object of R (the search-layer stop of Malkov and Yashunin, Algorithm 2);
+ *   for each neighbour e of c, in slot order, not yet visited: mark e visited
+ *       and run the DCO (Algorithm 1) against r = the farthest distance in R
+ *       (+inf while R holds fewer than ef); on accept e enters S and R, and R
+ *       drops its farthest object when it would hold ef + 1.
+ * schedule 0 (SEQUENTIAL): r is read before every DCO, the paper's order.
+ * schedule 1 (NODE): r is read once when c is popped and serves all of c's
+ *   neighbours; the accepted ones then enter S and R together (R keeps the
+ *   ef nearest of R and them).  A stale r only accepts more.
+ * The entry objects form one such group against r = +inf in both schedules.
+ * Arithmetic: with Xr, Qr (FP64) the DCOs are dco() with eps (NULL:
+ * FDScanning) and bias as or_search; with Xr32, Qr32 (FP32, Xr and Qr NULL)
+ * they are dco_f32() with coef32 (NULL: FDScanning), every distance an FP32
+ * value, bias unused.
+ * Results: the K nearest of R by (squared distance, id); missing slots
+ * (-1, +inf).  entry: nq x n_entry object ids (negative or out-of-range slots
+ * skipped); nbr: n x M0 ids (-1 unused).
+ * stats (nq x 5, may be NULL): DCOs run, sum of dims used, accepted, pruned,
+ * objects popped and expanded.
+ * flags (nq, may be NULL): 1|2 DCO near-ties (see dco); 4 a near-tie in the
+ * pop order (another object of S within tol of the popped one) or in the stop
+ * compare; 8 a near-tie at an eviction from R; 16 the K-th and (K+1)-th of R
+ * within tol at the end; 32 the visit budget ended the search.
+ * Returns 0, or -1 on bad arguments.
+ */
+OR_API int or_hnsw_search(const double *Xr, const float *Xr32, int64_t n, int D, const int32_t *nbr, int M0,
+                          const double *lam, const double *Qr, const float *Qr32, int64_t nq, const int64_t *entry,
+                          int n_entry, int K, int ef, int delta_d, const double *eps, const float *coef32,
+                          int schedule, int64_t max_visits, double tol, double bias, int64_t *ids, double *dists,
+                          int64_t *stats, int32_t *flags)
+{
+    const int f32 = Xr32 != NULL;
+    if (n < 1 || K < 1 || ef < K || M0 < 1 || n_entry < 1 || delta_d < 1 || schedule < 0 || schedule > 1 ||
+        !(bias > -1.0) || (f32 ? (Qr32 == NULL || Xr != NULL || Qr != NULL) : (Xr == NULL || Qr == NULL)))
+        return -1;
+    double *Lam = prefix_lambda(lam, D);
+    #pragma omp parallel
+    {
+        unsigned char *vis = (unsigned char *)calloc((size_t)n, 1);
+        int64_t *touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+        kv_t *R = (kv_t *)malloc(sizeof(kv_t) * (size_t)(ef + M0 + n_entry + 1));
+        kv_t *S = (kv_t *)malloc(sizeof(kv_t) * (size_t)(n + 1));
+        kv_t *acc = (kv_t *)malloc(sizeof(kv_t) * (size_t)(M0 + n_entry));
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t qi = 0; qi < nq; ++qi) {
+            int nR = 0, nS = 0, tie = 0, na = 0;
+            int64_t nt = 0, st[5] = {0, 0, 0, 0, 0};
+            /* one DCO of object e_ against the squared threshold r2_ */
+            #define OR_HVISIT(e_, r2_)                                                                  \
+                do {                                                                                    \
+                    int dims = 0, ok;                                                                   \
+                    double d2 = 0.0;                                                                    \
+                    vis[e_] = 1;                                                                        \
+                    touched[nt++] = (e_);                                                               \
+                    if (f32) {                                                                          \
+                        float p32 = 0.0f;                                                               \
+                        ok = dco_f32(Qr32 + qi * D, Xr32 + (e_) * D, D, delta_d, (float)(r2_), coef32,  \
+                                     tol, &p32, &dims, &tie);                                           \
+                        d2 = p32;                                                                       \
+                    } else {                                                                            \
+                        double r2b = (r2_) * (1.0 + bias);                                              \
+                        ok = dco(Qr + qi * D, Xr + (e_) * D, D, delta_d, sqrt(r2b), r2b, Lam, eps,      \
+                                 eps != NULL, tol, &d2, &dims, &tie);                                   \
+                    }                                                                                   \
+                    st[0] += 1;                                                                         \
+                    st[1] += dims;                                                                      \
+                    if (ok) {                                                                           \
+                        st[2] += 1;                                                                     \
+                        acc[na].key = d2;                                                               \
+                        acc[na].id = (e_);                                                              \
+                        ++na;                                                                           \
+                    } else if (dims < D) st[3] += 1;                                                    \
+                } while (0)
+            /* the accepted group enters S and R together: R keeps the ef nearest */
+            #define OR_HADMIT()                                                                         \
+                do {                                                                                    \
+                    for (int a_ = 0; a_ < na; ++a_) S[nS++] = acc[a_];                                  \
+                    if (na > 0) {                                                                       \
+                        memcpy(R + nR, acc, sizeof(kv_t) * (size_t)na);                                 \
+                        qsort(R, (size_t)(nR + na), sizeof(kv_t), kv_cmp);                              \
+                        nR += na;                                                                       \
+                        if (nR > ef) {                                                                  \
+                            if (near_tie(R[ef - 1].key, R[ef].key, tol)) tie |= 8;                      \
+                            nR = ef;                                                                    \
+                        }                                                                               \
+                    }                                                                                   \
+                    na = 0;                                                                             \
+                } while (0)
+            for (int j = 0; j < n_entry; ++j) {
+                int64_t e = entry[qi * n_entry + j];
+                if (e < 0 || e >= n || vis[e]) continue;
+                OR_HVISIT(e, INFINITY);
+            }
+            OR_HADMIT();
+            for (;;) {
+                if (max_visits > 0 && st[0] >= max_visits) { tie |= 32; break; }
+                if (nS == 0) break;
+                int b = 0;
+                for (int i = 1; i < nS; ++i)
+                    if (kv_less(S[i].key, S[i].id, S[b].key, S[b].id)) b = i;
+                kv_t c = S[b];
+                for (int i = 0; i < nS; ++i)
+                    if (i != b && near_tie(S[i].key, c.key, tol)) { tie |= 4; break; }
+                S[b] = S[--nS];
+                const kv_t far = R[nR - 1];
+                if (far.id != c.id && near_tie(c.key, far.key, tol)) tie |= 4;
+                if (kv_less(far.key, far.id, c.key, c.id)) break;
+                st[4] += 1;
+                const double r2_node = nR == ef ? R[ef - 1].key : INFINITY;
+                for (int s = 0; s < M0; ++s) {
+                    int64_t e = nbr[c.id * M0 + s];
+                    if (e < 0 || e >= n || vis[e]) continue;
+                    if (schedule == 0) {
+                        OR_HVISIT(e, nR == ef ? R[ef - 1].key : INFINITY);
+                        if (na > 0) {
+                            S[nS++] = acc[0];
+                            r_insert(R, &nR, ef, acc[0], tol, &tie);
+                            na = 0;
+                        }
+                    } else {
+                        OR_HVISIT(e, r2_node);
+                    }
+                }
+                if (schedule == 1) OR_HADMIT();
+            }
+            #undef OR_HVISIT
+            #undef OR_HADMIT
+            if (nR > K && near_tie(R[K - 1].key, R[K].key, tol)) tie |= 16;
+            for (int s = 0; s < K; ++s) {
+                ids[qi * K + s] = s < nR ? R[s].id : -1;
+                dists[qi * K + s] = s < nR ? R[s].key : INFINITY;
+            }
+            if (stats) for (int s = 0; s < 5; ++s) stats[qi * 5 + s] = st[s];
+            if (flags) flags[qi] = tie;
+            for (int64_t t = 0; t < nt; ++t) vis[touched[t]] = 0;
+        }
+        free(vis); free(touched); free(R); free(S); free(acc);
+    }
+    free(Lam);
+    return 0;
 }

@@ -727,4 +727,170 @@ def pin_sampled_index(o):
     assert np.array_equal(ids, bid) and _rel(dists, bd) < 1e-10
 
 
+# --------------------------------------------------------------------------
+# Section 3.4: HNSW with DADE DCOs (HNSW*): the layer-0 graph and the beam search
+# --------------------------------------------------------------------------
+
+def pin_hnsw_graph_golden(o):
+    """Hand-worked layer-0 graphs on a line (tests/golden/hnsw_graph.json)."""
+    g = golden("hnsw_graph.json")
+    X = np.asarray(g["points"], float)
+    for c in g["cases"]:
+        nbr, gs, gf = o.hnsw_graph(X, c["kc"], c["M"], c["M0"])
+        assert nbr.tolist() == c["nbr"], c["name"]
+
+
+def pin_hnsw_trace(o):
+    """Hand-worked beam search with DCOs, both threshold schedules and
+    FDScanning (tests/golden/hnsw_trace.json)."""
+    g = golden("hnsw_trace.json")
+    X = np.asarray(g["points"], float)
+    q = np.asarray([g["query"]], float)
+    for c in g["cases"]:
+        eps = np.asarray(g["eps"], float) if c["prune"] else None
+        ids, dists, stats, flags = o.hnsw_search(X, np.asarray(g["nbr"]), np.asarray(g["lam"], float), q,
+                                                 g["entry"], g["K"], g["ef"], g["delta_d"], eps, c["schedule"])
+        assert ids[0].tolist() == c["ids"], c["name"]
+        assert _rel(dists[0], c["dists"]) < 1e-12, c["name"]
+        assert stats[0].tolist() == c["stats"], c["name"]
+        assert flags[0] == 0, c["name"]
+
+
+def _hnsw_setup(o, n=700, D=24, seed=201):
+    X, _, _ = synth.gaussian(n, D, 1.0, seed=seed, basis_seed=seed + 1)
+    Q, _, _ = synth.gaussian(25, D, 1.0, seed=seed + 2, basis_seed=seed + 1)
+    return X.astype(np.float64), Q.astype(np.float64)
+
+
+def _reachable(nbr, start):
+    seen, todo = {int(start)}, [int(start)]
+    while todo:
+        for v in nbr[todo.pop()]:
+            if v >= 0 and int(v) not in seen:
+                seen.add(int(v))
+                todo.append(int(v))
+    return seen
+
+
+def pin_hnsw_exhaustive_is_exact(o):
+    """With FDScanning and R as large as the data (ef = n), the search
+    expands every object reachable from the entry: on a connected graph it
+    returns the exact K nearest (brute force), in both schedules."""
+    X, Q = _hnsw_setup(o)
+    n = X.shape[0]
+    nbr, _, _ = o.hnsw_graph(X, 24, 8, 16)
+    assert len(_reachable(nbr, 0)) == n
+    bid, bd = _brute(X, Q, 10)
+    for sch in (0, 1):
+        ids, dists, stats, _ = o.hnsw_search(X, nbr, np.ones(X.shape[1]), Q, [0], 10, n, 8, None, sch)
+        assert np.array_equal(ids, bid) and _rel(dists, bd) < 1e-12
+        assert (stats[:, 0] == n).all() and (stats[:, 4] == n).all()
+
+
+def pin_hnsw_complete_graph(o):
+    """On the complete graph the entry's expansion visits every object with
+    r = +inf (R holds one object when the node schedule reads r), so even
+    ef = K returns the exact K nearest; DADE with eps = +inf (no test can
+    reject) gives FDScanning's results and counters."""
+    X, Q = _hnsw_setup(o, n=200, D=16, seed=211)
+    n, D = X.shape
+    nbr = np.array([[j for j in range(n) if j != i] for i in range(n)], np.int32)
+    bid, bd = _brute(X, Q, 7)
+    lam = np.linspace(3.0, 0.5, D)
+    fd = o.hnsw_search(X, nbr, lam, Q, [5], 7, 7, 4, None, 1)
+    assert np.array_equal(fd[0], bid) and _rel(fd[1], bd) < 1e-12
+    inf_eps = np.full(D + 1, np.inf)
+    dade = o.hnsw_search(X, nbr, lam, Q, [5], 7, 7, 4, inf_eps, 1)
+    assert np.array_equal(dade[0], fd[0]) and np.array_equal(dade[2], fd[2])
+
+
+def pin_hnsw_dade_prunes_only_beyond_r(o):
+    """Section 3.3: a pruned neighbour's estimate exceeded (1 + eps_d) r, and
+    every reported distance is exact; with the eps of a sampled
+    significance level the results stay near FDScanning's (recall of the
+    FDScanning results at least 0.9 over the batch) while fewer dims are
+    read."""
+    X, Q = _hnsw_setup(o, n=900, D=32, seed=221)
+    nbr, _, _ = o.hnsw_graph(X, 32, 8, 16)
+    mu, W, lam = o.pca(X.astype(np.float32))
+    Xr, Qr = o.rotate(X.astype(np.float32), mu, W), o.rotate(Q.astype(np.float32), mu, W)
+    eps = _eps_for(o, Xr, lam, 8, 0.1)
+    fd = o.hnsw_search(Xr, nbr, lam, Qr, [0], 10, 40, 8, None, 1)
+    dd = o.hnsw_search(Xr, nbr, lam, Qr, [0], 10, 40, 8, eps, 1)
+    exact = ((Qr[:, None, :] - Xr[dd[0]]) ** 2).sum(-1)
+    assert _rel(dd[1], exact) < 1e-12
+    hit = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(dd[0], fd[0])])
+    assert hit >= 0.9
+    assert dd[2][:, 1].sum() < fd[2][:, 1].sum() and dd[2][:, 3].sum() > 0
+
+
+def pin_hnsw_path_flags(o):
+    """A query with no path near-tie at tol takes the same path under every
+    threshold moved by less than tol: runs with r^2 scaled by 1 -/+ tol/2
+    return its ids and counters unchanged."""
+    X, Q = _hnsw_setup(o, n=900, D=32, seed=231)
+    nbr, _, _ = o.hnsw_graph(X, 32, 8, 16)
+    mu, W, lam = o.pca(X.astype(np.float32))
+    Xr, Qr = o.rotate(X.astype(np.float32), mu, W), o.rotate(Q.astype(np.float32), mu, W)
+    eps = _eps_for(o, Xr, lam, 8, 0.1)
+    Q = np.concatenate([Q] * 4) + 0.01 * np.random.default_rng(232).standard_normal((4 * Q.shape[0], Q.shape[1]))
+    Qr = o.rotate(Q.astype(np.float32), mu, W)
+    tol = 1e-4
+    base = o.hnsw_search(Xr, nbr, lam, Qr, [0], 10, 30, 8, eps, 1, tol=tol)
+    stable = (base[3] & 15) == 0
+    assert 10 <= stable.sum() < stable.size
+    moved = np.zeros(stable.size, bool)
+    for b in (-tol / 2, tol / 2):
+        r = o.hnsw_search(Xr, nbr, lam, Qr, [0], 10, 30, 8, eps, 1, tol=tol, bias=b)
+        assert np.array_equal(r[0][stable], base[0][stable]) and np.array_equal(r[2][stable], base[2][stable])
+        moved |= (r[2] != base[2]).any(1)
+    assert moved.any()        # the moved thresholds do change the path of some flagged queries
+
+
+def pin_hnsw_fp32_arithmetic(o):
+    """The FP32 DCO (the paper's scalar FP32 arithmetic, test in squared form
+    with FP32 c_j) decides as the FP64 DCO wherever no decision of the FP64
+    path lies within 1e-5: same ids and counters on those queries, distances
+    within FP32 rounding.  On the hand-worked trace it gives the golden
+    counters."""
+    import oracle
+    g = golden("hnsw_trace.json")
+    X32 = np.asarray(g["points"], np.float32)
+    q32 = np.asarray([g["query"]], np.float32)
+    lam, eps = np.asarray(g["lam"], float), np.asarray(g["eps"], float)
+    for c in g["cases"]:
+        coef = oracle.coef_f32(lam, eps, 2, g["delta_d"]) if c["prune"] else None
+        ids, dists, stats, _ = o.hnsw_search(X32, np.asarray(g["nbr"]), lam, q32, g["entry"], g["K"], g["ef"],
+                                             g["delta_d"], None, c["schedule"], coef32=coef)
+        assert ids[0].tolist() == c["ids"] and stats[0].tolist() == c["stats"], c["name"]
+        assert _rel(dists[0], c["dists"]) < 1e-6, c["name"]
+    X, Q = _hnsw_setup(o, n=1500, D=48, seed=251)
+    nbr, _, _ = o.hnsw_graph(X, 32, 8, 16)
+    mu, W, lam = o.pca(X.astype(np.float32))
+    Xr32 = o.rotate(X.astype(np.float32), mu, W).astype(np.float32)
+    Qr32 = o.rotate(Q.astype(np.float32), mu, W).astype(np.float32)
+    eps = _eps_for(o, Xr32.astype(np.float64), lam, 16, 0.1)
+    coef = oracle.coef_f32(lam, eps, 48, 16)
+    for sch in (0, 1):
+        a = o.hnsw_search(Xr32.astype(np.float64), nbr, lam, Qr32.astype(np.float64), [0], 10, 40, 16, eps, sch)
+        b = o.hnsw_search(Xr32, nbr, lam, Qr32, [0], 10, 40, 16, None, sch, coef32=coef)
+        stable = (a[3] & 15) == 0
+        assert stable.sum() >= 15
+        assert np.array_equal(a[0][stable], b[0][stable]) and np.array_equal(a[2][stable], b[2][stable])
+        assert _rel(b[1][stable], a[1][stable]) < 1e-5
+        assert b[2][:, 3].sum() > 0                       # the FP32 test does prune
+
+
+def pin_hnsw_visit_budget(o):
+    """The visit budget stops the search at the first pop after max_visits
+    DCOs (flag 32); without it the search is the same up to that point."""
+    X, Q = _hnsw_setup(o, n=500, D=16, seed=241)
+    nbr, _, _ = o.hnsw_graph(X, 24, 8, 16)
+    full = o.hnsw_search(X, nbr, np.ones(16), Q, [0], 5, 50, 16, None, 1)
+    cut = o.hnsw_search(X, nbr, np.ones(16), Q, [0], 5, 50, 16, None, 1, max_visits=40)
+    assert (cut[3] & 32).all() and not (full[3] & 32).any()
+    assert (cut[2][:, 0] >= 40).all() and (cut[2][:, 0] < 40 + 16 + 1).all()
+    assert (cut[2][:, 0] <= full[2][:, 0]).all()
+
+
 ALL = [v for k, v in sorted(globals().items()) if k.startswith("pin_")]

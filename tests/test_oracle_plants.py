@@ -56,7 +56,19 @@ PLANTS = [
     ("rounds_first_row_skipped", "for (int64_t t = lo; t < hi && t < len; ++t)",
      "for (int64_t t = lo + (lo > 0); t < hi && t < len; ++t)"),
     # the decision bracket moves the threshold the wrong way
-    ("bias_sign", "double r2b = (r2_) * (1.0 + bias)", "double r2b = (r2_) * (1.0 - bias)"),
+    ("bias_sign", "double r2b = (r2_) * (1.0 + bias), d2", "double r2b = (r2_) * (1.0 - bias), d2"),
+    # HNSW* beam search and graph (Section 3.4): stop rule, threshold, R bound, schedules, heuristic
+    ("hnsw_stop_at_the_farthest", "if (kv_less(far.key, far.id, c.key, c.id)) break;", "if (!(c.key < far.key)) break;"),
+    ("hnsw_threshold_is_nearest", "const double r2_node = nR == ef ? R[ef - 1].key : INFINITY;",
+     "const double r2_node = nR == ef ? R[0].key : INFINITY;"),
+    ("hnsw_result_set_unbounded", "if (nR > ef) {", "if (nR > ef + 1) {"),
+    ("hnsw_sequential_threshold_stale", "OR_HVISIT(e, nR == ef ? R[ef - 1].key : INFINITY);", "OR_HVISIT(e, r2_node);"),
+    ("hnsw_entry_not_exact", "OR_HVISIT(e, INFINITY);", "OR_HVISIT(e, 0.0);"),
+    ("hnsw_heuristic_reversed", "if (!(cand[i].key < des)) { keep = 0; break; }",
+     "if (!(cand[i].key > des)) { keep = 0; break; }"),
+    ("hnsw_reverse_edges_dropped", "for (int64_t t = rstart[v]; t < rstart[v + 1]; ++t) {",
+     "for (int64_t t = rstart[v]; t < rstart[v]; ++t) {"),
+    ("hnsw_fp32_test_unsquared", "float bound = coef[j] * r2;", "float bound = coef[j] * sqrtf(r2);"),
     ("probe_descending", "for (int j = 0; j < nprobe; ++j) {\n                probe[q * nprobe + j] = (int32_t)buf[j].id;",
      "for (int j = 0; j < nprobe; ++j) {\n                probe[q * nprobe + j] = (int32_t)buf[nc - 1 - j].id;"),
 ]
