@@ -686,6 +686,86 @@ dade_status dade_index_export(const dade_index *ix, int32_t field, void *dst, si
 dade_status dade_host_sym_eig(double *a, int32_t n, double *w, double *v);
 
 /*
+ * HNSW* (Section 3.4; the graph of Section 4.1): greedy beam search on a
+ * layer-0 graph with one DADE DCO per neighbour.  The search keeps a result
+ * set R of at most ef objects and repeatedly expands the nearest object of R
+ * not yet expanded: each of its neighbours not yet visited gets a DCO
+ * (Algorithm 1, the Section 3.3 test) against r = the farthest distance in R
+ * (+inf while R holds fewer than ef), read once per expanded object, and the
+ * accepted ones enter R, which keeps its ef nearest.  The search ends when
+ * every object of R is expanded or when max_visits DCOs have run; the K
+ * nearest of R are the result.  Distances are FP32 sums of squares taken in
+ * dimension order with every step rounded (the arithmetic of the paper's
+ * scalar implementation), the test in squared form P_d > c_j r^2 with
+ * c_j = (1 + eps_d)^2 Lambda_d / Lambda_D.  A structure serves one call at a
+ * time (its scratch is shared by its calls).
+ *
+ * The graph (dade_hnsw_build): for every object the kc nearest other objects
+ * by the index's FDScanning search over its nprobe nearest lists (exact when
+ * nprobe = n_clusters), HNSW's neighbour heuristic (Malkov and Yashunin,
+ * Algorithm 4: a candidate is kept iff it is nearer to the object than to
+ * every candidate kept before it) keeping at most M, then the reverse links,
+ * and over any list longer than M0 the heuristic again with cap M0.  Rows are
+ * the index's rotated vectors, row-major (n * dp floats, dp = d rounded up to
+ * 16), plus n * M0 int32 links.  The entry object is the one nearest the data
+ * mean (smallest rotated norm, lowest id on ties).
+ */
+typedef struct dade_hnsw dade_hnsw;
+typedef struct {
+    int32_t M;                 /* links the heuristic keeps per object (default 16) */
+    int32_t M0;                /* layer-0 degree cap (default 32; M <= M0 <= 32) */
+    int32_t kc;                /* candidates per object (default 64; M <= kc <= 255) */
+    int32_t nprobe;            /* lists of the candidate search (0: min(n_clusters, 64)) */
+    int32_t reserved[4];
+} dade_hnsw_build_opts;
+typedef struct {
+    int32_t mode;              /* DADE_MODE_DADE (default) or DADE_MODE_FD */
+    int32_t n_entry;           /* entry objects per query when entry is set (1..64) */
+    const int64_t *entry;      /* host or device [nq * n_entry] entry object ids (ids outside 0..n-1 are
+                                  skipped); NULL: the structure's entry object */
+    int64_t max_visits;        /* DCOs after which no object is expanded (0: min(n, 64 ef + 1024)) */
+    const float *coef;         /* host [ceil(d / delta_d) - 1] c_j of the j-th tested d = (j + 1) delta_d;
+                                  NULL: from the index's eps sample at alpha (as dade_eps_table) */
+    int64_t *stats;            /* host or device [nq * 5] or NULL: DCOs run, sum of dims used, accepted,
+                                  pruned (rejected before d = D), objects expanded */
+    int32_t reserved[4];
+} dade_hnsw_search_opts;
+typedef struct {
+    int64_t n;                 /* objects */
+    int32_t d;                 /* dimensions */
+    int32_t m0;                /* links per object */
+    int64_t entry;             /* default entry object */
+    int64_t device_bytes;      /* rows and links on the device */
+} dade_hnsw_info;
+void dade_hnsw_build_opts_default(dade_hnsw_build_opts *opts);
+void dade_hnsw_search_opts_default(dade_hnsw_search_opts *opts);
+/* Build over the index's own objects: base host or device [n * d] FP32, the vectors the index was built
+ * on (n = the index's n; not a shard).  The index must outlive the structure.  Synchronous. */
+dade_status dade_hnsw_build(const dade_index *ix, const float *base, int64_t n, const dade_hnsw_build_opts *opts,
+                            dade_hnsw **out);
+/* A structure over given rotated vectors x_rot (host or device [n * d] FP32) and links nbr (host or device
+ * [n * m0] int32, -1 unused; 1 <= m0 <= 32), entry object `entry`.  ix (may be NULL): the index whose
+ * rotation and eps sample dade_hnsw_query and a search without opts.coef use (d must match).
+ * Synchronous. */
+dade_status dade_hnsw_create(const dade_index *ix, const float *x_rot, int64_t n, int32_t d, const int32_t *nbr,
+                             int32_t m0, int64_t entry, dade_hnsw **out);
+/* Search on rotated queries q_rot (host or device [nq * d]).  1 <= k <= DADE_MAX_K, k <= ef <= 1024,
+ * delta_d a multiple of 16 in [16, 1024], alpha in (0, 1) unless opts.coef is set or mode is FD.
+ * ids, dists: host or device [nq * k], ascending by (squared distance, id), missing places -1 / +inf.
+ * Asynchronous on `stream` for device outputs; with a host output the call returns when it is written. */
+dade_status dade_hnsw_search(dade_hnsw *h, const float *q_rot, int64_t nq, int32_t k, int32_t ef, float alpha,
+                             int32_t delta_d, const dade_hnsw_search_opts *opts, int64_t *ids, float *dists,
+                             dade_stream stream);
+/* dade_hnsw_search on raw queries q (host or device [nq * d]), rotated with the structure's index. */
+dade_status dade_hnsw_query(dade_hnsw *h, const float *q, int64_t nq, int32_t k, int32_t ef, float alpha,
+                            int32_t delta_d, const dade_hnsw_search_opts *opts, int64_t *ids, float *dists,
+                            dade_stream stream);
+dade_status dade_hnsw_info_get(const dade_hnsw *h, dade_hnsw_info *out);
+/* The links, host or device [n * m0] int32.  Synchronous. */
+dade_status dade_hnsw_graph(const dade_hnsw *h, int32_t *nbr);
+void dade_hnsw_free(dade_hnsw *h);
+
+/*
  * Allocation-failure injection (no counterpart in the paper; for tests of the
  * failure paths).  While a hook is set, every device allocation the library
  * makes first calls hook(bytes, user); a nonzero return makes that

@@ -71,6 +71,21 @@ class ServerOpts(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class HnswBuildOpts(C.Structure):
+    _fields_ = [("M", C.c_int32), ("M0", C.c_int32), ("kc", C.c_int32), ("nprobe", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
+
+
+class HnswSearchOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("n_entry", C.c_int32), ("entry", C.c_void_p), ("max_visits", C.c_int64),
+                ("coef", C.c_void_p), ("stats", C.c_void_p), ("reserved", C.c_int32 * 4)]
+
+
+class HnswInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("m0", C.c_int32), ("entry", C.c_int64),
+                ("device_bytes", C.c_int64)]
+
+
 class ServerStats(C.Structure):
     _fields_ = [("slots", C.c_int64), ("slot_bytes", C.c_int64), ("requests", C.c_int64),
                 ("requests_done", C.c_int64), ("batches", C.c_int64), ("queries", C.c_int64),
@@ -100,6 +115,15 @@ SIGNATURES = {
     "dade_server_cancel": (_i32, [_vp, C.c_uint64]),
     "dade_server_replay": (_i32, [_vp, _vp, _i64, _vp, _vp, _f32, _i32, _vp, _i32, _vp, _vp, _vp, _vp]),
     "dade_server_free": (None, [_vp]),
+    "dade_hnsw_build_opts_default": (None, [_vp]),
+    "dade_hnsw_search_opts_default": (None, [_vp]),
+    "dade_hnsw_build": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "dade_hnsw_create": (_i32, [_vp, _vp, _i64, _i32, _vp, _i32, _i64, _vp]),
+    "dade_hnsw_search": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
+    "dade_hnsw_query": (_i32, [_vp, _vp, _i64, _i32, _i32, _f32, _i32, _vp, _vp, _vp, _vp]),
+    "dade_hnsw_info_get": (_i32, [_vp, _vp]),
+    "dade_hnsw_graph": (_i32, [_vp, _vp]),
+    "dade_hnsw_free": (None, [_vp]),
     "dade_graph_launch": (_i32, [_vp, _vp]),
     "dade_graph_free": (None, [_vp]),
     "dade_load_index": (_i32, [C.c_char_p, _vp]),
@@ -449,6 +473,88 @@ class Graph:
     def close(self):
         if getattr(self, "_h", None):
             lib().dade_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+class Hnsw:
+    """HNSW* (dade_hnsw_*): a layer-0 graph over rotated vectors, searched by
+    a greedy beam search with one DADE DCO per neighbour."""
+
+    def __init__(self, handle, index=None):
+        self._h, self._index = handle, index
+        info = HnswInfo()
+        _check(lib().dade_hnsw_info_get(self._h, C.byref(info)))
+        self.n, self.d, self.m0, self.entry = int(info.n), int(info.d), int(info.m0), int(info.entry)
+        self.device_bytes = int(info.device_bytes)
+
+    @classmethod
+    def build(cls, index, base, M=16, M0=32, kc=64, nprobe=0):
+        """Graph over the index's own vectors (base: those vectors, host or device [n, d])."""
+        o = HnswBuildOpts()
+        lib().dade_hnsw_build_opts_default(C.byref(o))
+        o.M, o.M0, o.kc, o.nprobe = int(M), int(M0), int(kc), int(nprobe)
+        h = C.c_void_p()
+        _check(lib().dade_hnsw_build(index.handle, _ptr(base), int(base.shape[0]), C.byref(o), C.byref(h)))
+        return cls(h, index)
+
+    @classmethod
+    def create(cls, x_rot, nbr, entry, index=None):
+        """From given rotated vectors [n, d] float32 and links [n, m0] int32 (host or device)."""
+        h = C.c_void_p()
+        _check(lib().dade_hnsw_create(index.handle if index is not None else None, _ptr(x_rot), int(x_rot.shape[0]),
+                                      int(x_rot.shape[1]), _ptr(nbr), int(nbr.shape[1]), int(entry), C.byref(h)))
+        return cls(h, index)
+
+    def _opts(self, mode, entry, max_visits, coef, stats):
+        o = HnswSearchOpts()
+        lib().dade_hnsw_search_opts_default(C.byref(o))
+        o.mode, o.max_visits = int(mode), int(max_visits)
+        keep = []
+        if entry is not None:
+            if not hasattr(entry, "data_ptr"):
+                entry = np.ascontiguousarray(entry, np.int64)
+                keep.append(entry)
+            o.entry, o.n_entry = _ptr(entry), int(entry.shape[1])
+        if coef is not None:
+            c = np.ascontiguousarray(coef, np.float32)
+            keep.append(c)
+            o.coef = c.ctypes.data
+        o.stats = _ptr(stats)
+        return o, keep
+
+    def search(self, q_rot, k, ef, alpha, delta_d, ids, dists, mode=MODE_DADE, entry=None, max_visits=0,
+               coef=None, stats=None, stream=None):
+        """dade_hnsw_search on rotated queries [nq, d]; ids [nq, k] int64, dists [nq, k] float32;
+        entry [nq, n_entry] int64; coef: FP32 c_j (None: the index's at alpha); stats [nq, 5] int64."""
+        o, keep = self._opts(mode, entry, max_visits, coef, stats)
+        _check(lib().dade_hnsw_search(self._h, _ptr(q_rot), int(q_rot.shape[0]), int(k), int(ef), float(alpha),
+                                      int(delta_d), C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
+        del keep
+        return ids, dists
+
+    def query(self, q, k, ef, alpha, delta_d, ids, dists, mode=MODE_DADE, entry=None, max_visits=0, coef=None,
+              stats=None, stream=None):
+        """dade_hnsw_query on raw queries [nq, d] (rotated with the structure's index)."""
+        o, keep = self._opts(mode, entry, max_visits, coef, stats)
+        _check(lib().dade_hnsw_query(self._h, _ptr(q), int(q.shape[0]), int(k), int(ef), float(alpha), int(delta_d),
+                                     C.byref(o), _ptr(ids), _ptr(dists), _stream(stream)))
+        del keep
+        return ids, dists
+
+    def graph(self):
+        nbr = np.empty((self.n, self.m0), np.int32)
+        _check(lib().dade_hnsw_graph(self._h, nbr.ctypes.data))
+        return nbr
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dade_hnsw_free(self._h)
             self._h = None
 
     def __del__(self):

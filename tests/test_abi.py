@@ -42,7 +42,9 @@ def test_library_exports_every_declared_symbol(L):
 def _c_layouts(tmp_path):
     """sizeof / offsetof of every field of the ABI structs, from a C program
     compiled against include/dade.h with the host C compiler."""
-    structs = {"dade_build_opts": dade.BuildOpts, "dade_search_opts": dade.SearchOpts, "dade_info": dade.Info}
+    structs = {"dade_build_opts": dade.BuildOpts, "dade_search_opts": dade.SearchOpts, "dade_info": dade.Info,
+               "dade_server_opts": dade.ServerOpts, "dade_hnsw_build_opts": dade.HnswBuildOpts,
+               "dade_hnsw_search_opts": dade.HnswSearchOpts, "dade_hnsw_info": dade.HnswInfo}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dade.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -90,6 +92,27 @@ def test_invalid_arguments_rejected_without_gpu(L):
                          None) == dade.EINVAL
     assert L.dade_sync(None, None) == dade.EINVAL
     assert L.dade_free_index(None) is None
+
+
+def test_hnsw_arguments_rejected_without_gpu(L):
+    o = dade.HnswBuildOpts()
+    L.dade_hnsw_build_opts_default(C.byref(o))
+    assert (o.M, o.M0, o.kc, o.nprobe) == (16, 32, 64, 0)
+    so = dade.HnswSearchOpts()
+    L.dade_hnsw_search_opts_default(C.byref(so))
+    assert so.mode == dade.MODE_DADE and so.max_visits == 0 and not so.entry and not so.coef
+    h = C.c_void_p()
+    x = np.zeros((4, 8), np.float32)
+    nbr = np.zeros((4, 2), np.int32)
+    assert L.dade_hnsw_build(None, x.ctypes.data, 4, C.byref(o), C.byref(h)) == dade.EINVAL
+    for n, d, m0, entry, msg in ((0, 8, 2, 0, b"n outside"), (4, 0, 2, 0, b"d outside"),
+                                 (4, 8, 33, 0, b"m0 outside"), (4, 8, 2, 4, b"entry outside")):
+        assert L.dade_hnsw_create(None, x.ctypes.data, n, d, nbr.ctypes.data, m0, entry, C.byref(h)) == dade.EINVAL
+        assert msg in L.dade_last_error()
+    ids, dists = np.zeros(10, np.int64), np.zeros(10, np.float32)
+    assert L.dade_hnsw_search(None, x.ctypes.data, 1, 10, 10, 0.1, 16, None, ids.ctypes.data, dists.ctypes.data,
+                              None) == dade.EINVAL
+    assert L.dade_hnsw_free(None) is None
 
 
 def test_lead_options_rejected_without_gpu(L):
