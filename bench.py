@@ -88,6 +88,7 @@ def parse():
                          "and alpha sweep: dims touched vs recall, and time, beside FDScanning")
     ap.add_argument("--no-serving", action="store_true", help="skip the request-server latency sweep")
     ap.add_argument("--no-adsampling", action="store_true", help="skip the ADSampling comparator")
+    ap.add_argument("--no-hnsw", action="store_true", help="skip the HNSW* graph search sweep")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="duration of each arrival rate")
     ap.add_argument("--tail-from", type=int, default=32,
                     help="first dim of the index's row-major tail copy (0: none); survivors gather from it")
@@ -285,6 +286,117 @@ def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7, torch=None, xb
             "schedule": ("row rounds" if rounds else "tile") + " (mixed K and nprobe in one launch)",
             "slots": st["slots"], "batches": st["batches"], "mean_batch": round(st["queries"] / max(1, st["batches"]), 2),
             "max_inflight": st["max_inflight"], "rates": out, "recall_by_nprobe": recall}
+
+
+HNSW_WORKLOAD = "c3_mix_1m_d960"
+HNSW_EFS = (16, 24, 32, 48, 64, 96, 128, 192, 256)
+
+
+def hnsw_pick(rows, target):
+    """The fastest row whose recall reaches the target, else the row of
+    highest recall (rows: dicts with "recall" and "ms")."""
+    ok = [r for r in rows if r["recall"] >= target]
+    if ok:
+        return min(ok, key=lambda r: r["ms"])
+    return max(rows, key=lambda r: (r["recall"], -r["ms"]))
+
+
+def hnsw_sweep(dade, torch, ix, xb, q, queries, gt_kth, K, flush, stream, reps=16, target=0.95, steps=10, warm=3):
+    """HNSW* (Section 3.4) on the workload's own vectors: the layer-0 graph
+    (dade_hnsw_build: M = 16, M0 = 32 as in the paper's HNSW, candidates from
+    the index's FDScanning search over 16 lists), then the beam search with
+    DADE DCOs over alpha x delta_d x ef and with FDScanning over ef; each
+    side's fastest point at recall@K >= target is timed on the query batch
+    repeated `reps` times (device inputs, 256 MB flush between steps)."""
+    sh = stream.cuda_stream
+    t0 = time.time()
+    h = dade.Hnsw.build(ix, xb, M=16, M0=32, kc=64, nprobe=16)
+    torch.cuda.synchronize()
+    build_s = time.time() - t0
+    log(f"[bench] HNSW* graph built in {build_s:.1f}s ({h.device_bytes / 2**20:.0f} MiB)")
+    nq = q.shape[0]
+    qr = torch.empty_like(q)
+    ix.rotate(q, qr, stream=sh)
+    ids = torch.empty(nq, K, dtype=torch.int64, device="cuda")
+    dists = torch.empty(nq, K, dtype=torch.float32, device="cuda")
+    stats = torch.empty(nq, 5, dtype=torch.int64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    name = {dade.MODE_DADE: "dade", dade.MODE_FD: "fd"}
+
+    def trial(mode, ef, alpha, dd):
+        h.search(qr, K, ef, alpha, dd, ids, dists, mode=mode, stats=stats, stream=sh)
+        flush.zero_()
+        e0.record(stream)
+        h.search(qr, K, ef, alpha, dd, ids, dists, mode=mode, stream=sh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = stats.sum(0).tolist()
+        return {"mode": name[mode], "ef": ef, "alpha": alpha if mode == dade.MODE_DADE else None,
+                "delta_d": dd if mode == dade.MODE_DADE else None,
+                "recall": round(recall_at_k(torch, xb, q, ids, gt_kth, K), 5), "ms": round(e0.elapsed_time(e1), 4),
+                "dcos_per_query": round(st[0] / nq, 1), "dims_per_dco": round(st[1] / max(1, st[0]), 2),
+                "expansions_per_query": round(st[4] / nq, 1), "_st": st}
+
+    rows = []
+    lines = [(dade.MODE_FD, 0.5, 16)] + [(dade.MODE_DADE, a, dd) for a in (0.1, 0.5, 0.9) for dd in (16, 32)]
+    for mode, alpha, dd in lines:
+        for ef in HNSW_EFS:
+            if ef < K:
+                continue
+            rows.append(trial(mode, ef, alpha, dd))
+            if rows[-1]["recall"] >= target:     # a larger ef is only slower
+                break
+    big = qr.repeat(reps, 1)
+    bi = torch.empty(nq * reps, K, dtype=torch.int64, device="cuda")
+    bd = torch.empty(nq * reps, K, dtype=torch.float32, device="cuda")
+    peaks = measured_peaks()
+
+    def timed(pt):
+        mode = dade.MODE_DADE if pt["mode"] == "dade" else dade.MODE_FD
+        alpha, dd = pt["alpha"] or 0.5, pt["delta_d"] or 16
+        ms = []
+        for i in range(warm + steps):
+            flush.zero_()
+            e0.record(stream)
+            h.search(big, K, pt["ef"], alpha, dd, bi, bd, mode=mode, stream=sh)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= warm:
+                ms.append(e0.elapsed_time(e1))
+        m = statistics.mean(ms)
+        st = pt["_st"]
+        # rows read by the DCOs (dims used x 4 bytes) and the expanded objects' link rows, per launch
+        moved = (st[1] * 4 + st[4] * h.m0 * 4) * reps
+        out = {k: v for k, v in pt.items() if k not in ("ms", "_st")}
+        out.update({"value": round(nq * reps / (m / 1e3), 1), "unit": UNIT, "ms_per_step": round(m, 4),
+                    "batch": nq * reps, "bytes_read_per_step": int(moved),
+                    "bytes_read_rate_gbs": round(moved / (m / 1e3) / 1e9, 1)})
+        if peaks.get("hbm_gbs"):
+            out["bytes_read_frac_of_hbm"] = round(out["bytes_read_rate_gbs"] / peaks["hbm_gbs"], 4)
+        return out
+
+    best = {m: hnsw_pick([r for r in rows if r["mode"] == m], target) for m in ("dade", "fd")}
+    res = {m: timed(best[m]) for m in best}
+    # end to end: raw host queries in, host results out, through dade_hnsw_query
+    qh = np.ascontiguousarray(np.tile(queries, (reps, 1)), np.float32)
+    ih, dh = np.empty((nq * reps, K), np.int64), np.empty((nq * reps, K), np.float32)
+    pd = best["dade"]
+    e2e_s = []
+    for i in range(warm + 3):
+        t1 = time.perf_counter()
+        h.query(qh, K, pd["ef"], pd["alpha"], pd["delta_d"], ih, dh, stream=sh)
+        if i >= warm:
+            e2e_s.append(time.perf_counter() - t1)
+    out = {"graph": {"M": 16, "M0": 32, "kc": 64, "candidate_nprobe": 16, "build_s": round(build_s, 1),
+                     "device_bytes": h.device_bytes, "entry": h.entry},
+           "k": K, "target_recall": target, "kernel": "k_hnsw_search (one warp per query, one lane per neighbour)",
+           "dade": res["dade"], "fd": res["fd"],
+           "dade_vs_fd": round(res["dade"]["value"] / res["fd"]["value"], 3),
+           "e2e": {"value": round(nq * reps / statistics.mean(e2e_s), 1), "unit": UNIT,
+                   "h2d_bytes_per_step": int(qh.nbytes), "d2h_bytes_per_step": int(ih.nbytes + dh.nbytes)},
+           "sweep": [{k: v for k, v in r.items() if k != "_st"} for r in rows]}
+    h.close()
+    return out
 
 
 def served_recall(torch, xb, queries, served, nprobes):
@@ -856,6 +968,14 @@ def measure_workload(args, wname, rank, world, dist, headline):
         except Exception as e:  # noqa: BLE001 - reported, not fatal
             log(f"[bench] serving sweep failed: {e}")
 
+    # ---- HNSW*: the beam search on a layer-0 graph with DADE DCOs ----------------------
+    hnsw = None
+    if wname == HNSW_WORKLOAD and not args.no_hnsw:
+        try:
+            hnsw = hnsw_sweep(dade, torch, ix, xb, q, queries, gt_kth, K, flush, stream)
+        except Exception as e:  # noqa: BLE001 - reported, not fatal
+            log(f"[bench] HNSW* sweep failed: {e}")
+
     # ---- end to end through the C ABI with host buffers -------------------------------
     q_host = torch.from_numpy(queries).pin_memory()
     ids_host = torch.empty(nq, K, dtype=torch.int64).pin_memory()
@@ -931,6 +1051,7 @@ def measure_workload(args, wname, rank, world, dist, headline):
                        "p99": round(float(np.percentile(step_ms, 99)), 4), "per": "batch step"},
         "precision_points": precision,
         "serving": serving,
+        "hnsw": hnsw,
         "fd_baseline": {"value": round(fd_qps, 1), "unit": UNIT, "recall": round(fd_recall, 5),
                         "nprobe": fd_pt["nprobe"], "threads": fd_pt["threads"],
                         "schedule": SCHED_NAMES[fd_pt.get("schedule", 0)],

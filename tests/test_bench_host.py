@@ -60,3 +60,12 @@ def test_alu_bound_where_lists_are_shared():
     assert not bench.list_major_point(dict(c2, schedule=3, flags=20), 768)
     assert not bench.list_major_point(dict(c2, schedule=3, delta_d=32, flags=38), 768)   # lead: query-major
     assert bench.list_major_point(dict(c2, delta_d=32, flags=14), 768)   # seeded: lead leaves it list-major
+
+
+def test_hnsw_point_choice():
+    rows = [{"recall": 0.93, "ms": 1.0}, {"recall": 0.96, "ms": 3.0}, {"recall": 0.97, "ms": 2.5},
+            {"recall": 0.99, "ms": 9.0}]
+    assert bench.hnsw_pick(rows, 0.95) == rows[2]          # fastest at the target
+    assert bench.hnsw_pick(rows[:1], 0.95) == rows[0]       # none reaches it: the best recall
+    assert bench.HNSW_WORKLOAD in bench.synth.WORKLOADS
+    assert all(ef >= 1 for ef in bench.HNSW_EFS) and list(bench.HNSW_EFS) == sorted(bench.HNSW_EFS)
