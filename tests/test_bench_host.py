@@ -69,3 +69,43 @@ def test_hnsw_point_choice():
     assert bench.hnsw_pick(rows[:1], 0.95) == rows[0]       # none reaches it: the best recall
     assert bench.HNSW_WORKLOAD in bench.synth.WORKLOADS
     assert all(ef >= 1 for ef in bench.HNSW_EFS) and list(bench.HNSW_EFS) == sorted(bench.HNSW_EFS)
+
+
+def test_serving_runs_the_tuned_round_options():
+    """The serving sweep hands the point's row-round options (first-round rows,
+    work-item chunk, tensor-core window) to the server, so its batches run the
+    launches the timed step runs; a tile point serves on the tile schedule."""
+    from unittest import mock
+
+    import numpy as np
+
+    from paper_2411_17229_gb300 import dade
+    made = []
+
+    class FakeServer:
+        def __init__(self, ix, **kw):
+            made.append(kw)
+
+        def replay(self, q, ks, nps, alpha, delta_d, arrivals):
+            n = q.shape[0]
+            return np.zeros((n, 100), np.int64), None, np.full(n, 1e-3), 1e-3
+
+        def stats(self):
+            return {"slots": 4, "batches": 1, "queries": 1, "max_inflight": 1}
+
+        def close(self):
+            pass
+
+    ix = mock.Mock()
+    ix.info.n_clusters, ix.info.d_pad = 8192, 256
+    q = np.zeros((10, 256), np.float32)
+    rounds = {"schedule": dade.SCHED_ROUNDS, "tile": 16, "threads": 256, "list_chunk": 1024, "tc_min_rows": 16384,
+              "flags": dade.FLAG_TC_PREFILTER | dade.FLAG_LEAD, "alpha": 0.98, "delta_d": 64}
+    tile = {"schedule": dade.SCHED_TILE, "tile": 128, "threads": 128, "flags": dade.FLAG_QUERY_ORDER}
+    with mock.patch.object(dade, "Server", FakeServer):
+        bench.serve_sweep(dade, ix, q, rounds, (2000,), 0.01)
+        bench.serve_sweep(dade, ix, q, tile, (2000,), 0.01)
+    assert made[0]["schedule"] == dade.SCHED_ROUNDS and made[0]["tile"] == 16
+    assert made[0]["list_chunk"] == 1024 and made[0]["tc_min_rows"] == 16384
+    assert made[0]["flags"] == dade.FLAG_TC_PREFILTER           # the lead prefilter is not a serving option
+    assert made[1]["schedule"] == dade.SCHED_TILE and made[1]["list_chunk"] == 0 and made[1]["tc_min_rows"] == 0
