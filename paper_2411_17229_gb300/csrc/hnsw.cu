@@ -375,6 +375,8 @@ __global__ void k_hnsw_select(const float *X, int dp, const int64_t *off, int st
     }
 }
 
+// Blocks of a grid-stride kernel over `items` (per_block per block), at most
+// 32 per SM of the 152.
 int grid_for(int64_t items, int per_block) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((items + per_block - 1) / per_block, 152 * 32));
 }
@@ -397,8 +399,8 @@ using namespace dade;
 
 namespace {
 
-// Copies count elements of `bytes_each` from src (host or device) into buf on
-// the device; returns the device pointer (src itself when it is on the device).
+// The device copy of count elements of src: src itself when it is device
+// memory, else buf (grown as needed) after an asynchronous copy on s.
 template <class T>
 const T *to_device(const T *src, size_t count, DevBuf &buf, cudaStream_t s, dade_status *st) {
     *st = DADE_OK;
