@@ -290,6 +290,7 @@ def serve_sweep(dade, ix, queries, point, rates, seconds, seed=7, torch=None, xb
 
 HNSW_WORKLOAD = "c3_mix_1m_d960"
 HNSW_EFS = (16, 24, 32, 48, 64, 96, 128, 192, 256)
+HNSW_ENTRIES = 4   # entry objects per query: the nearest members of its nearest IVF list
 
 
 def hnsw_pick(rows, target):
@@ -304,10 +305,13 @@ def hnsw_pick(rows, target):
 def hnsw_sweep(dade, torch, ix, xb, q, queries, gt_kth, K, flush, stream, reps=16, target=0.95, steps=10, warm=3):
     """HNSW* (Section 3.4) on the workload's own vectors: the layer-0 graph
     (dade_hnsw_build: M = 16, M0 = 32 as in the paper's HNSW, candidates from
-    the index's FDScanning search over 16 lists), then the beam search with
-    DADE DCOs over alpha x delta_d x ef and with FDScanning over ef; each
-    side's fastest point at recall@K >= target is timed on the query batch
-    repeated `reps` times (device inputs, 256 MB flush between steps)."""
+    the index's FDScanning search over 16 lists), then per query the IVF
+    search of its nearest list (the same DCO, K = 4) for the entry objects,
+    which stands in for HNSW's upper layers, and the beam search from them:
+    DADE over alpha x delta_d x ef and FDScanning over ef.  Each side's
+    fastest point at recall@K >= target is timed, both steps inside the
+    timed region, on the query batch repeated `reps` times (device inputs,
+    256 MB flush between steps)."""
     sh = stream.cuda_stream
     t0 = time.time()
     h = dade.Hnsw.build(ix, xb, M=16, M0=32, kc=64, nprobe=16)
@@ -320,22 +324,31 @@ def hnsw_sweep(dade, torch, ix, xb, q, queries, gt_kth, K, flush, stream, reps=1
     ids = torch.empty(nq, K, dtype=torch.int64, device="cuda")
     dists = torch.empty(nq, K, dtype=torch.float32, device="cuda")
     stats = torch.empty(nq, 5, dtype=torch.int64, device="cuda")
+    ent = torch.empty(nq, HNSW_ENTRIES, dtype=torch.int64, device="cuda")
+    ent_d = torch.empty(nq, HNSW_ENTRIES, dtype=torch.float32, device="cuda")
+    ent_st = torch.zeros(nq, 4, dtype=torch.int64, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     name = {dade.MODE_DADE: "dade", dade.MODE_FD: "fd"}
 
+    def step(mode, ef, alpha, dd, qq, e, ed, out_i, out_d, st=None, est=None):
+        # entry objects: the query's nearest list searched with the same DCO, then the beam search
+        ix.search(qq, HNSW_ENTRIES, 1, alpha, dd, e, ed, mode=mode, stats=est, stream=sh)
+        h.search(qq, K, ef, alpha, dd, out_i, out_d, mode=mode, entry=e, stats=st, stream=sh)
+
     def trial(mode, ef, alpha, dd):
-        h.search(qr, K, ef, alpha, dd, ids, dists, mode=mode, stats=stats, stream=sh)
+        step(mode, ef, alpha, dd, qr, ent, ent_d, ids, dists, stats, ent_st)
         flush.zero_()
         e0.record(stream)
-        h.search(qr, K, ef, alpha, dd, ids, dists, mode=mode, stream=sh)
+        step(mode, ef, alpha, dd, qr, ent, ent_d, ids, dists)
         e1.record(stream)
         torch.cuda.synchronize()
-        st = stats.sum(0).tolist()
+        st, es = stats.sum(0).tolist(), ent_st.sum(0).tolist()
         return {"mode": name[mode], "ef": ef, "alpha": alpha if mode == dade.MODE_DADE else None,
                 "delta_d": dd if mode == dade.MODE_DADE else None,
                 "recall": round(recall_at_k(torch, xb, q, ids, gt_kth, K), 5), "ms": round(e0.elapsed_time(e1), 4),
                 "dcos_per_query": round(st[0] / nq, 1), "dims_per_dco": round(st[1] / max(1, st[0]), 2),
-                "expansions_per_query": round(st[4] / nq, 1), "_st": st}
+                "expansions_per_query": round(st[4] / nq, 1),
+                "entry_scan_dims_per_query": round(es[1] / nq, 1), "_st": st, "_es": es}
 
     rows = []
     lines = [(dade.MODE_FD, 0.5, 16)] + [(dade.MODE_DADE, a, dd) for a in (0.1, 0.5, 0.9) for dd in (16, 32)]
@@ -349,6 +362,8 @@ def hnsw_sweep(dade, torch, ix, xb, q, queries, gt_kth, K, flush, stream, reps=1
     big = qr.repeat(reps, 1)
     bi = torch.empty(nq * reps, K, dtype=torch.int64, device="cuda")
     bd = torch.empty(nq * reps, K, dtype=torch.float32, device="cuda")
+    be = torch.empty(nq * reps, HNSW_ENTRIES, dtype=torch.int64, device="cuda")
+    bed = torch.empty(nq * reps, HNSW_ENTRIES, dtype=torch.float32, device="cuda")
     peaks = measured_peaks()
 
     def timed(pt):
@@ -358,16 +373,16 @@ def hnsw_sweep(dade, torch, ix, xb, q, queries, gt_kth, K, flush, stream, reps=1
         for i in range(warm + steps):
             flush.zero_()
             e0.record(stream)
-            h.search(big, K, pt["ef"], alpha, dd, bi, bd, mode=mode, stream=sh)
+            step(mode, pt["ef"], alpha, dd, big, be, bed, bi, bd)
             e1.record(stream)
             torch.cuda.synchronize()
             if i >= warm:
                 ms.append(e0.elapsed_time(e1))
         m = statistics.mean(ms)
-        st = pt["_st"]
-        # rows read by the DCOs (dims used x 4 bytes) and the expanded objects' link rows, per launch
-        moved = (st[1] * 4 + st[4] * h.m0 * 4) * reps
-        out = {k: v for k, v in pt.items() if k not in ("ms", "_st")}
+        st, es = pt["_st"], pt["_es"]
+        # rows read by the DCOs of both steps (dims used x 4 bytes) and the expanded objects' link rows
+        moved = ((st[1] + es[1]) * 4 + st[4] * h.m0 * 4) * reps
+        out = {k: v for k, v in pt.items() if k not in ("ms", "_st", "_es")}
         out.update({"value": round(nq * reps / (m / 1e3), 1), "unit": UNIT, "ms_per_step": round(m, 4),
                     "batch": nq * reps, "bytes_read_per_step": int(moved),
                     "bytes_read_rate_gbs": round(moved / (m / 1e3) / 1e9, 1)})
@@ -377,24 +392,29 @@ def hnsw_sweep(dade, torch, ix, xb, q, queries, gt_kth, K, flush, stream, reps=1
 
     best = {m: hnsw_pick([r for r in rows if r["mode"] == m], target) for m in ("dade", "fd")}
     res = {m: timed(best[m]) for m in best}
-    # end to end: raw host queries in, host results out, through dade_hnsw_query
+    # end to end: raw host queries in, host results out (dade_query for the entries, dade_hnsw_query)
     qh = np.ascontiguousarray(np.tile(queries, (reps, 1)), np.float32)
     ih, dh = np.empty((nq * reps, K), np.int64), np.empty((nq * reps, K), np.float32)
+    eh, edh = np.empty((nq * reps, HNSW_ENTRIES), np.int64), np.empty((nq * reps, HNSW_ENTRIES), np.float32)
     pd = best["dade"]
     e2e_s = []
     for i in range(warm + 3):
         t1 = time.perf_counter()
-        h.query(qh, K, pd["ef"], pd["alpha"], pd["delta_d"], ih, dh, stream=sh)
+        ix.query(qh, HNSW_ENTRIES, 1, pd["alpha"], pd["delta_d"], eh, edh, stream=sh)
+        h.query(qh, K, pd["ef"], pd["alpha"], pd["delta_d"], ih, dh, entry=eh, stream=sh)
         if i >= warm:
             e2e_s.append(time.perf_counter() - t1)
     out = {"graph": {"M": 16, "M0": 32, "kc": 64, "candidate_nprobe": 16, "build_s": round(build_s, 1),
-                     "device_bytes": h.device_bytes, "entry": h.entry},
+                     "device_bytes": h.device_bytes},
+           "entry": f"the {HNSW_ENTRIES} nearest objects of the query's nearest IVF list (dade_search, the same "
+                    "DCO), inside the timed region",
            "k": K, "target_recall": target, "kernel": "k_hnsw_search (one warp per query, one lane per neighbour)",
            "dade": res["dade"], "fd": res["fd"],
            "dade_vs_fd": round(res["dade"]["value"] / res["fd"]["value"], 3),
            "e2e": {"value": round(nq * reps / statistics.mean(e2e_s), 1), "unit": UNIT,
-                   "h2d_bytes_per_step": int(qh.nbytes), "d2h_bytes_per_step": int(ih.nbytes + dh.nbytes)},
-           "sweep": [{k: v for k, v in r.items() if k != "_st"} for r in rows]}
+                   "h2d_bytes_per_step": int(2 * qh.nbytes + eh.nbytes),
+                   "d2h_bytes_per_step": int(ih.nbytes + dh.nbytes + eh.nbytes + edh.nbytes)},
+           "sweep": [{k: v for k, v in r.items() if k not in ("_st", "_es")} for r in rows]}
     h.close()
     return out
 
